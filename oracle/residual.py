@@ -1,0 +1,203 @@
+"""FR/CPR residual R(q^p) of Sec. 3.1 on periodic structured quad meshes.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Discretised equation (Eq. unsteady_pre_mov_cdomain_GCL divided by |J|, i.e. the
+computational-domain form whose physical-domain statement is Eq. cpr_ns):
+
+    R = -(1/|J|) [ dF/dxi + dG/deta - q^c (d(|J| xi_t)/dxi + d(|J| eta_t)/deta) ]
+
+with F = |J|(q^c xi_t + f xi_x + g xi_y), G alike, f = f_inv - f_vis.  FR/CPR:
+F = F^loc + F^cor, F^loc the degree-p interpolant of the solution-point fluxes,
+F^cor = (F^num_L - F^loc(-1)) g_L + (F^num_R - F^loc(+1)) g_R, and
+F^num = |J||grad xi| f_n^com sign(n . grad xi) (Eq. norm_f_2), f_n^com =
+f_{n,inv}^com (Eq. Rosanov) - f_{n,vis}^com.
+
+Readings where the paper is silent (used identically by the CUDA library):
+* F^loc at a face is the interpolated flux polynomial, not the flux of the
+  interpolated state.
+* d(|J| xi_t)/dxi is the derivative of the degree-p interpolant of |J| xi_t.
+* Local gradients use the chain rule on the interpolant derivatives; the
+  corrected gradient adds, for each face f, (q^com - q^loc_f) S_f g_f'(xi) / |J|.
+* BR2 (Sec. 3.1): grad q^com = (grad q^+,loc + r^+ + grad q^-,loc + r^-)/2 with
+  r^+- = (q^com - q^+-) S_f g'_f(face end) / |J|^+-_f (face f's own jump only).
+* The common viscous flux is f_vis(q^com, grad q^com) . n.
+
+Mesh: element e = j*nx + i; faces in xi are "owned" by their left element (its
+R face, the '-' side), faces in eta by their bottom element (its T face).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import physics as ph
+from .basis import Basis, make_basis
+from .geometry import FACE_B, FACE_L, FACE_R, FACE_T, Geometry, element_geometry
+
+
+@dataclasses.dataclass
+class Mesh:
+    nx: int
+    ny: int
+    corners: np.ndarray        # [Ne, 4, 2]
+    vel: np.ndarray            # [Ne, 4, 2]
+    periodic: tuple = (True, True)
+
+    @property
+    def ne(self) -> int:
+        return self.nx * self.ny
+
+    def neighbours(self):
+        """(left, right, bottom, top) element index arrays, periodic wrap."""
+        if not all(self.periodic):
+            raise NotImplementedError("only periodic meshes")
+        e = np.arange(self.ne)
+        i, j = e % self.nx, e // self.nx
+        left = j * self.nx + (i - 1) % self.nx
+        right = j * self.nx + (i + 1) % self.nx
+        bottom = ((j - 1) % self.ny) * self.nx + i
+        top = ((j + 1) % self.ny) * self.nx + i
+        return left, right, bottom, top
+
+
+# ------------------------------------------------------------------ 1-D operators along lines
+# Arrays are [..., Ne, n(j), n(i)]: i is the xi index (last axis), j the eta index.
+
+def d_xi(b: Basis, a):
+    return np.einsum("ik,...jk->...ji", b.D, a)
+
+
+def d_eta(b: Basis, a):
+    return np.einsum("jk,...ki->...ji", b.D, a)
+
+
+def trace(b: Basis, a, face: int):
+    """Value of the degree-p interpolant at the flux points of ``face`` ([..., Ne, n])."""
+    if face == FACE_L:
+        return np.einsum("k,...jk->...j", b.lL, a)
+    if face == FACE_R:
+        return np.einsum("k,...jk->...j", b.lR, a)
+    if face == FACE_B:
+        return np.einsum("k,...ki->...i", b.lL, a)
+    return np.einsum("k,...ki->...i", b.lR, a)
+
+
+@dataclasses.dataclass
+class Parts:
+    """Intermediate quantities of one residual evaluation (for tests)."""
+    qc: np.ndarray
+    grad_loc: tuple
+    grad: tuple
+    F: np.ndarray
+    G: np.ndarray
+    Fnum_xi: np.ndarray     # [4, Ne, n]: common flux on the xi-face owned by e (its R face)
+    Fnum_eta: np.ndarray    # [4, Ne, n]: on the eta-face owned by e (its T face)
+    div: np.ndarray
+    R: np.ndarray
+
+
+def residual(q, mesh: Mesh, p: int, gas: ph.Gas, b: Basis | None = None,
+             geo: Geometry | None = None, parts: bool = False):
+    """R(q^p) at every solution point, ``[4, Ne, n, n]`` (q^c-equation rows)."""
+    b = b or make_basis(p)
+    geo = geo or element_geometry(mesh.corners, mesh.vel, b)
+    left, right, bottom, top = mesh.neighbours()
+    g = geo.sol
+    qs = tuple(q[k] for k in range(4))
+
+    # Pointwise state, conservative variables and inviscid fluxes (Eq. convection).
+    qc = ph.conservative(qs, gas)
+    finv, ginv = ph.inviscid_flux(qs, gas)
+
+    # Traces of the primitive state at the flux points of each face.
+    qf = [trace(b, q, f) for f in range(4)]           # each [4, Ne, n]
+
+    # Common solution on every face (Sec. 3.1): owned xi-faces (R of e, L of right[e]),
+    # owned eta-faces (T of e, B of top[e]).
+    qm_xi, qp_xi = qf[FACE_R], qf[FACE_L][:, right]
+    qm_eta, qp_eta = qf[FACE_T], qf[FACE_B][:, top]
+    qcom_xi = 0.5 * (qm_xi + qp_xi)
+    qcom_eta = 0.5 * (qm_eta + qp_eta)
+    # q^com seen from each face of each element
+    qcom_f = [qcom_xi[:, left], qcom_xi, qcom_eta[:, bottom], qcom_eta]
+
+    if gas.viscous:
+        # Local physical gradients by the chain rule.
+        q_xi, q_eta = d_xi(b, q), d_eta(b, q)
+        qx_loc = (g.Sxi[0] * q_xi + g.Seta[0] * q_eta) / g.J
+        qy_loc = (g.Sxi[1] * q_xi + g.Seta[1] * q_eta) / g.J
+        # Corrected gradient: add the lifted jumps of all four faces.
+        qx, qy = qx_loc.copy(), qy_loc.copy()
+        for f, dgv, along_i in ((FACE_L, b.dgL, True), (FACE_R, b.dgR, True),
+                                (FACE_B, b.dgL, False), (FACE_T, b.dgR, False)):
+            S = geo.faces[f].Sxi if along_i else geo.faces[f].Seta    # [2, Ne, n]
+            jump = qcom_f[f] - qf[f]                                   # [4, Ne, n]
+            if along_i:   # face value depends on j, correction function on i
+                cx = jump[:, :, :, None] * S[0][None, :, :, None] * dgv[None, None, None, :]
+                cy = jump[:, :, :, None] * S[1][None, :, :, None] * dgv[None, None, None, :]
+            else:         # face value depends on i, correction function on j
+                cx = jump[:, :, None, :] * S[0][None, :, None, :] * dgv[None, None, :, None]
+                cy = jump[:, :, None, :] * S[1][None, :, None, :] * dgv[None, None, :, None]
+            qx = qx + cx / g.J
+            qy = qy + cy / g.J
+        fv, gv = ph.viscous_flux(qs, tuple(qx), tuple(qy), gas)
+        f_all, g_all = finv - fv, ginv - gv
+        grad_loc, grad = (qx_loc, qy_loc), (qx, qy)
+    else:
+        f_all, g_all = finv, ginv
+        grad_loc = grad = (None, None)
+
+    # Computational fluxes at solution points (Eq. computational_flux).
+    F = g.Sxi[0] * f_all + g.Sxi[1] * g_all + g.St_xi * qc
+    G = g.Seta[0] * f_all + g.Seta[1] * g_all + g.St_eta * qc
+
+    # Common normal fluxes on owned faces.
+    def common(qm, qp, gf_m, gf_p, Jm, Jp, S, vg, dgm, dgp):
+        Smag = np.sqrt(S[0] * S[0] + S[1] * S[1])
+        nvec = (S[0] / Smag, S[1] / Smag)
+        qmt = tuple(qm[k] for k in range(4))
+        qpt = tuple(qp[k] for k in range(4))
+        fcom = ph.rusanov(qmt, qpt, nvec, vg, gas)
+        if gas.viscous:
+            qcom = 0.5 * (qm + qp)
+            rmx = (qcom - qm) * S[0] * dgm / Jm
+            rmy = (qcom - qm) * S[1] * dgm / Jm
+            rpx = (qcom - qp) * S[0] * dgp / Jp
+            rpy = (qcom - qp) * S[1] * dgp / Jp
+            gx = 0.5 * (gf_m[0] + rmx + gf_p[0] + rpx)
+            gy = 0.5 * (gf_m[1] + rmy + gf_p[1] + rpy)
+            fv, gv = ph.viscous_flux(tuple(qcom[k] for k in range(4)), tuple(gx), tuple(gy), gas)
+            fcom = fcom - (fv * nvec[0] + gv * nvec[1])
+        return Smag * fcom
+
+    if gas.viscous:
+        gtr = [(trace(b, grad_loc[0], f), trace(b, grad_loc[1], f)) for f in range(4)]
+        gm_xi = gtr[FACE_R]
+        gp_xi = (gtr[FACE_L][0][:, right], gtr[FACE_L][1][:, right])
+        gm_eta = gtr[FACE_T]
+        gp_eta = (gtr[FACE_B][0][:, top], gtr[FACE_B][1][:, top])
+    else:
+        gm_xi = gp_xi = gm_eta = gp_eta = None
+    fR, fL_of_right = geo.faces[FACE_R], geo.faces[FACE_L]
+    fT, fB_of_top = geo.faces[FACE_T], geo.faces[FACE_B]
+    Fnum_xi = common(qm_xi, qp_xi, gm_xi, gp_xi, fR.J, fL_of_right.J[right], fR.Sxi, fR.vg,
+                     b.dgR_end, b.dgL_end)
+    Fnum_eta = common(qm_eta, qp_eta, gm_eta, gp_eta, fT.J, fB_of_top.J[top], fT.Seta, fT.vg,
+                      b.dgR_end, b.dgL_end)
+    Fnum_f = [Fnum_xi[:, left], Fnum_xi, Fnum_eta[:, bottom], Fnum_eta]
+
+    # Divergence of F^loc + F^cor, GCL term, and R.
+    div = d_xi(b, F) + d_eta(b, G)
+    for f, dgv in ((FACE_L, b.dgL), (FACE_R, b.dgR)):
+        jump = Fnum_f[f] - trace(b, F, f)                # [4, Ne, n(j)]
+        div = div + jump[:, :, :, None] * dgv[None, None, None, :]
+    for f, dgv in ((FACE_B, b.dgL), (FACE_T, b.dgR)):
+        jump = Fnum_f[f] - trace(b, G, f)                # [4, Ne, n(i)]
+        div = div + jump[:, :, None, :] * dgv[None, None, :, None]
+    div = div - qc * (d_xi(b, g.St_xi) + d_eta(b, g.St_eta))
+    R = -div / g.J
+    if parts:
+        return Parts(qc, grad_loc, grad, F, G, Fnum_xi, Fnum_eta, div, R)
+    return R
