@@ -1,0 +1,187 @@
+/*
+ * fr.h -- C ABI of the GB300 preconditioned FR/CPR implicit hot path
+ * (Wang & Yu, "An Implicit High-Order Preconditioned Flux Reconstruction Method for
+ * Low-Mach-Number Flow Simulation with Dynamic Meshes", arXiv 1903.06304).
+ *
+ * Problem statement (Sec. 3.2): given a mesh with grid velocities at time t, the
+ * primitive state q^p = (p, u, v, T) and the BDF2 history q^c,n, q^c,n-1, evaluate the
+ * residual R(q^p), the Newton operator A = Gamma/dtau + (a0/dt) M - dR/dq^p applied to
+ * vectors, an element block-Jacobi preconditioner, and advance one BDF2 step by
+ * Newton-GMRES (Eq. unsteady_pre_discretized_3) or one steady PTC solve (Eqs.
+ * steady_pre_discretized_1, SER).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Element e = j*nx + i on a structured nx-by-ny quad mesh (periodic in both
+ *   directions); corners per element in the order (xi,eta) = (-1,-1), (1,-1), (1,1),
+ *   (-1,1).
+ * - Solution vectors (q^p, R, v, A v, q^c histories) are FP64, structure of arrays
+ *   [4][Ne][n][n] with n = p+1: variable, element, eta index j, xi index i.
+ *   Their length is fr_num_dof().  The caller owns them (device memory).
+ * - Element blocks use the local index d = var*n*n + j*n + i.
+ * - Pointers suffixed _d are device pointers, _h host pointers.  Every call that takes
+ *   a stream enqueues asynchronously on it unless stated; calls that return host
+ *   statistics synchronise the stream.
+ * - The library owns its workspace, allocated by fr_create / fr_set_mesh.  Hot calls
+ *   (residual, jvp, precond, steps) allocate nothing.
+ * - Return value: FR_OK or a negative FR_ERR_* code; fr_last_error() gives the text.
+ *   Calls never abort the process.  A context is not thread safe.
+ */
+#ifndef FR_H
+#define FR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FR_OK 0
+#define FR_ERR_ARG (-1)           /* invalid argument or call order */
+#define FR_ERR_CUDA (-2)          /* a CUDA runtime call failed */
+#define FR_ERR_NONFINITE (-3)     /* NaN/Inf met in a norm */
+#define FR_ERR_NOT_CONVERGED (-4) /* Newton loop hit maxit (stats still filled) */
+#define FR_ERR_TIMEOUT (-5)       /* a bounded device wait expired */
+
+#define FR_PREC_FP64 0
+#define FR_PREC_FP32 1
+#define FR_PREC_BF16 2
+
+typedef struct fr_ctx fr_ctx;
+
+/* Physical and solver parameters.
+ * gamma, Pr: Sec. 2.1 (1.4, 0.72); mu = 1.
+ * mach: reference Mach number Ma_ref = Ma_inf of the nondimensionalisation (Sec. 2.1).
+ * re: Re_ref (Eq. diffusion); re <= 0 turns the viscous flux off (Euler).
+ * kappa: cut-off factor of Eqs. eps_nonmove / eps_move; eps_floor: lower bound of eps.
+ * prec_dtype: FR_PREC_* storage/factorisation precision of the element blocks.
+ * restart: GMRES Krylov dimension (1..FR_MAX_RESTART); maxit_lin: GMRES iteration cap;
+ * tol_res: GMRES tolerance relative to ||b|| (Sec. 4);
+ * maxit_newton, tol_pseudo: pseudo-time loop cap and Res_m/Res_0 target (Sec. 4);
+ * lag: rebuild the blocks every `lag` pseudo-iterations (2 unsteady, 1 steady, Sec. 4);
+ * dtau0, dtau_min, dtau_max, r_ser: SER law (Eq. SER) for steady PTC;
+ * dtau_unsteady: the fixed pseudo step of BDF2 runs (1e20 in Sec. 3.2);
+ * gmres_side: FR_GMRES_LEFT (PETSc's default, the paper's solver: Krylov space of B^-1 A,
+ * tol_res relative to ||B^-1 b||) or FR_GMRES_RIGHT (Krylov space of A B^-1, tol_res
+ * relative to ||b||). */
+#define FR_MAX_RESTART 256
+#define FR_GMRES_LEFT 0
+#define FR_GMRES_RIGHT 1
+typedef struct fr_config {
+  int p;
+  double gamma, prandtl, mach, re, kappa, eps_floor;
+  int prec_dtype;
+  int restart, maxit_lin, maxit_newton, lag;
+  double tol_res, tol_pseudo;
+  double dtau0, dtau_min, dtau_max, r_ser, dtau_unsteady;
+  int gmres_side;
+} fr_config;
+
+/* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).
+ * res_history[m] = Res_m (2-norm of the continuity row of the pseudo-step residual,
+ * Sec. 3.2), m = 0..newton_iterations; gmres_iterations[m] per Newton step. */
+#define FR_MAX_NEWTON 64
+typedef struct fr_stats {
+  int newton_iterations;
+  int converged;
+  int gmres_iterations[FR_MAX_NEWTON];
+  double res_history[FR_MAX_NEWTON + 1];
+  double dtau_history[FR_MAX_NEWTON + 1];
+  int block_builds;
+} fr_stats;
+
+/* Fill *cfg with the paper's defaults (gamma 1.4, Pr 0.72, kappa 1, GMRES(30), tol_res
+ * 1e-6, tol_pseudo 1e-8, lag 2, SER 0.01/0.01/1e20/2, dtau_unsteady 1e20, FP64 blocks,
+ * left preconditioning). */
+void fr_default_config(fr_config* cfg);
+
+/* Create a context for polynomial degree cfg->p (1..4) on the current CUDA device.
+ * Computes the Gauss points, Lagrange derivative/extrapolation rows and Radau
+ * correction derivatives (Sec. 3.1).  *out receives the context.  FR_ERR_ARG on a bad
+ * config, FR_ERR_CUDA on a failed allocation. */
+int fr_create(const fr_config* cfg, fr_ctx** out);
+void fr_destroy(fr_ctx* ctx);
+
+/* Mesh topology: nx-by-ny elements, periodic in both directions (periodic_x,
+ * periodic_y must be 1).  Allocates all per-mesh workspace (geometry, traces, Krylov
+ * basis, blocks).  Must be called before any compute call; may be called again to
+ * resize. */
+int fr_set_mesh(fr_ctx* ctx, int nx, int ny, int periodic_x, int periodic_y);
+
+/* Update geometry at the current time (Sec. 2.3): corners_d and corner_vel_d are
+ * device [Ne][4][2] FP64 (corner coordinates and their grid velocities); the library
+ * evaluates |J|, |J| grad(xi), |J| grad(eta), v_g and |J| xi_t, |J| eta_t at solution and
+ * flux points of the bilinear map, plus the interpolant divergence of (|J| xi_t,
+ * |J| eta_t).  Static meshes pass zero velocities once. */
+int fr_update_mesh(fr_ctx* ctx, const double* corners_d, const double* corner_vel_d,
+                   void* stream);
+
+/* R(q^p) of Sec. 3.1 (Eq. cpr_ns in its computational-domain form Eq.
+ * unsteady_pre_mov_cdomain_GCL): R_d[4][Ne][n][n] = -(1/|J|)(dF/dxi + dG/deta -
+ * q^c div(|J| xi_t, |J| eta_t)) with FR correction by Radau g_L, g_R, preconditioned
+ * Rusanov (Eq. Rosanov) and BR2 viscous common fluxes. */
+int fr_residual(fr_ctx* ctx, const double* qp_d, double* R_d, void* stream);
+
+/* Pseudo-step right-hand side of Eq. unsteady_pre_discretized_3:
+ * r = -(a0 q^c(q^p) + a1 qc_n + a2 qc_nm1)/dt + R(q^p).  a = (1.5, -2, 0.5) for BDF2,
+ * (1, -1, 0) for BDF1; qc_nm1_d may be NULL when a2 == 0. */
+int fr_bdf_rhs(fr_ctx* ctx, const double* qp_d, const double* qc_n_d, const double* qc_nm1_d,
+               double a0, double a1, double a2, double dt, double* r_d, void* stream);
+
+/* q^c(q^p) pointwise (Sec. 2.1): (rho, rho u, rho v, E) into qc_d[4][Ne][n][n]. */
+int fr_conservative(fr_ctx* ctx, const double* qp_d, double* qc_d, void* stream);
+
+/* Newton operator applied to a vector (forward-mode, exact):
+ * Av = (1/dtau) Gamma(q) v + a0_dt M(q) v - (dR/dq^p)(q) v, Eq. unsteady_pre_discretized_3
+ * (a0_dt = a0/dt; a0_dt = 0 gives the steady Eq. steady_pre_discretized_1).
+ * Pass inv_dtau = a0_dt = 0 for the plain Jacobian action -(dR/dq) v. */
+int fr_jvp(fr_ctx* ctx, const double* qp_d, const double* v_d, double inv_dtau, double a0_dt,
+           double* Av_d, void* stream);
+
+/* Build the element block-Jacobi preconditioner at q (Sec. 4 parallel setting, element
+ * blocks replacing per-process ILU(0)):
+ * B_e = Gamma_e/dtau + a0_dt M_e - dR_e/dq_e (neighbours frozen), then factor it in the
+ * configured precision (FP64, FP32 or BF16 storage of the FP32 inverse). */
+int fr_precond_build(fr_ctx* ctx, const double* qp_d, double inv_dtau, double a0_dt,
+                     void* stream);
+/* Copy the unfactored FP64 blocks of the last build to B_d[Ne][b][b] (b = 4 n^2). */
+int fr_precond_blocks(fr_ctx* ctx, double* B_d, void* stream);
+/* z_e = B_e^-1 r_e for every element (FP64 in and out). */
+int fr_precond_apply(fr_ctx* ctx, const double* r_d, double* z_d, void* stream);
+
+/* Restarted block-Jacobi-preconditioned GMRES(m) with CGS2 (Sec. 3.2, PETSc's solver
+ * replaced; left or right preconditioning per cfg.gmres_side): solve A x = b at state q
+ * with the blocks of the last build; x_d receives the solution (zero initial guess).
+ * *iters (host) receives the iteration count.  Synchronises the stream. */
+int fr_gmres(fr_ctx* ctx, const double* qp_d, const double* b_d, double inv_dtau, double a0_dt,
+             double* x_d, int* iters, void* stream);
+
+/* One physical BDF2 step (Eq. unsteady_pre_discretized_3) by the pseudo-time Newton loop:
+ * qp_d holds q^n on entry (initial guess) and q^n+1 on return; qc_n_d, qc_nm1_d are the
+ * conservative histories; coefficients a0,a1,a2 as in fr_bdf_rhs.  stats (host) is
+ * filled.  Synchronises.  FR_ERR_NOT_CONVERGED if maxit_newton is reached. */
+int fr_bdf2_step(fr_ctx* ctx, double* qp_d, const double* qc_n_d, const double* qc_nm1_d,
+                 double a0, double a1, double a2, double dt, fr_stats* stats, void* stream);
+
+/* Steady pseudo-transient continuation with SER (Eqs. steady_pre_discretized_1, SER):
+ * qp_d updated in place.  Synchronises. */
+int fr_ptc_solve(fr_ctx* ctx, double* qp_d, fr_stats* stats, void* stream);
+
+/* Continuity-row 2-norm ||r[0]|| (Res_m of Sec. 3.2) and full 2-norm of a vector,
+ * written to host *res_mass, *res_all.  Synchronises. */
+int fr_residual_norms(fr_ctx* ctx, const double* r_d, double* res_mass, double* res_all,
+                      void* stream);
+
+/* Sizes: number of FP64 entries of a solution vector, block size b. */
+size_t fr_num_dof(const fr_ctx* ctx);
+int fr_block_size(const fr_ctx* ctx);
+/* Number of kernels this context has launched since creation (device work items). */
+long long fr_kernel_launches(const fr_ctx* ctx);
+
+const char* fr_last_error(const fr_ctx* ctx);
+const char* fr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FR_H */

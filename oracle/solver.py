@@ -18,9 +18,12 @@ Readings where the paper is silent:
 * The preconditioner is element block-Jacobi: B_e = Gamma_e/dtau + (a0/dt) M_e -
   dR_e/dq_e (neighbours frozen), inverted exactly.  It is rebuilt every ``lag``
   pseudo-iterations (2 for unsteady runs, 1 for steady runs, Sec. 4).
-* GMRES: right preconditioning, zero initial guess, classical Gram-Schmidt with one
-  re-orthogonalisation (CGS2), convergence when the residual estimate drops below
-  tol_res * ||b||; the true residual is recomputed at every restart.
+* GMRES: the paper solves with PETSc's restarted GMRES, whose default is left
+  preconditioning with the preconditioned residual norm: the Krylov space of
+  B^-1 A is built, ||B^-1 (b - A x)|| is minimised and convergence is tol_res
+  relative to ||B^-1 b|| (zero initial guess).  Classical Gram-Schmidt with one
+  re-orthogonalisation (CGS2); the residual is recomputed at every restart.  Right
+  preconditioning is kept as an option (side="right").
 * Res_m, "the relative residual of pressure", is the 2-norm of the first
   (continuity) row of r over all solution points.
 * SER: the step q^m -> q^m+1 uses dtau_m; dtau_0 = dtau0 and
@@ -158,10 +161,16 @@ class GmresResult:
     res_history: list
 
 
-def gmres(Aop, b, Minv, restart: int, tol: float, maxit: int) -> GmresResult:
-    """Restarted, right-preconditioned GMRES(m) with CGS2 Arnoldi (see module notes)."""
+def gmres(Aop, b, Minv, restart: int, tol: float, maxit: int, side: str = "left") -> GmresResult:
+    """Restarted preconditioned GMRES(m) with CGS2 Arnoldi (see module notes).
+
+    side="left" (the default of PETSc, whose solver the paper uses): Krylov space of
+    M^-1 A, the preconditioned residual M^-1 (b - A x) is minimised and tested against
+    tol * ||M^-1 b||.  side="right": Krylov space of A M^-1, x = M^-1 V y, the true
+    residual b - A x is minimised and tested against tol * ||b||."""
     shape = b.shape
-    bv = b.ravel()
+    left = side == "left"
+    bv = (Minv(b) if left else b).ravel()
     bnorm = np.linalg.norm(bv)
     x = np.zeros_like(bv)
     hist = [bnorm]
@@ -187,8 +196,10 @@ def gmres(Aop, b, Minv, restart: int, tol: float, maxit: int) -> GmresResult:
         V[0] = r / beta
         k = 0
         for j in range(m):
-            z = Minv(V[j].reshape(shape)).ravel()
-            w = Aop(z.reshape(shape)).ravel()
+            if left:
+                w = Minv(Aop(V[j].reshape(shape))).ravel()
+            else:
+                w = Aop(Minv(V[j].reshape(shape))).ravel()
             h1 = V[: j + 1] @ w
             w = w - V[: j + 1].T @ h1
             h2 = V[: j + 1] @ w
@@ -217,8 +228,12 @@ def gmres(Aop, b, Minv, restart: int, tol: float, maxit: int) -> GmresResult:
         y = np.zeros(k)
         for i in range(k - 1, -1, -1):
             y[i] = (g[i] - H[i, i + 1: k] @ y[i + 1: k]) / H[i, i]
-        x = x + Minv((V[:k].T @ y).reshape(shape)).ravel()
-        r = bv - Aop(x.reshape(shape)).ravel()
+        if left:
+            x = x + V[:k].T @ y
+            r = Minv((b.ravel() - Aop(x.reshape(shape)).ravel()).reshape(shape)).ravel()
+        else:
+            x = x + Minv((V[:k].T @ y).reshape(shape)).ravel()
+            r = bv - Aop(x.reshape(shape)).ravel()
         beta = np.linalg.norm(r)
     return GmresResult(x.reshape(shape), total, converged, hist)
 
@@ -236,7 +251,7 @@ class StepStats:
 
 def newton_solve(prob: Problem, q, rhs, a0_dt: float, dtau0: float, restart: int,
                  tol_res: float, maxit_lin: int, tol_pseudo: float, maxit_newton: int,
-                 lag: int, ser=None):
+                 lag: int, ser=None, side: str = "left"):
     """Pseudo-time Newton loop shared by BDF2 and PTC; ``ser`` = (dtau_min, dtau_max, r)."""
     q = q.copy()
     r = rhs(q)
@@ -255,7 +270,7 @@ def newton_solve(prob: Problem, q, rhs, a0_dt: float, dtau0: float, restart: int
             Binv = np.linalg.inv(block_jacobian(prob, q, inv_dtau, a0_dt))
         qm = q
         out = gmres(lambda v: apply_A(prob, qm, v, inv_dtau, a0_dt), r,
-                    lambda v: block_apply(Binv, v), restart, tol_res, maxit_lin)
+                    lambda v: block_apply(Binv, v), restart, tol_res, maxit_lin, side)
         its.append(out.iterations)
         q = q + out.x
         r = rhs(q)
@@ -271,21 +286,22 @@ def newton_solve(prob: Problem, q, rhs, a0_dt: float, dtau0: float, restart: int
 
 def bdf2_step(prob: Problem, q, qc_n, qc_nm1, dt: float, coeffs=BDF2, dtau: float = 1e20,
               restart: int = 30, tol_res: float = 1e-6, maxit_lin: int = 100,
-              tol_pseudo: float = 1e-8, maxit_newton: int = 20, lag: int = 2):
+              tol_pseudo: float = 1e-8, maxit_newton: int = 20, lag: int = 2,
+              side: str = "left"):
     """One physical BDF2 step (Eq. unsteady_pre_discretized_3) from q^n = q (initial guess)."""
     rhs = lambda s: time_rhs(prob, s, qc_n, qc_nm1, dt, coeffs)
     return newton_solve(prob, q, rhs, coeffs[0] / dt, dtau, restart, tol_res, maxit_lin,
-                        tol_pseudo, maxit_newton, lag)
+                        tol_pseudo, maxit_newton, lag, side=side)
 
 
 def ptc_solve(prob: Problem, q, dtau0: float = 0.01, dtau_min: float = 0.01,
               dtau_max: float = 1e20, r_ser: float = 2.0, restart: int = 20,
               tol_res: float = 1e-6, maxit_lin: int = 100, tol_pseudo: float = 1e-8,
-              maxit_newton: int = 10):
+              maxit_newton: int = 10, side: str = "left"):
     """Steady pseudo-transient continuation with SER (Eqs. steady_pre_discretized_1, SER)."""
     rhs = lambda s: prob.R(s)
     return newton_solve(prob, q, rhs, 0.0, dtau0, restart, tol_res, maxit_lin, tol_pseudo,
-                        maxit_newton, 1, ser=(dtau_min, dtau_max, r_ser))
+                        maxit_newton, 1, ser=(dtau_min, dtau_max, r_ser), side=side)
 
 
 # ------------------------------------------------------------------ norms (Sec. 4)

@@ -1,0 +1,521 @@
+// fr_api.cu -- C ABI of the GB300 preconditioned FR/CPR implicit hot path: context and
+// workspace, the 1-D FR basis (Sec. 3.1), restarted right-preconditioned GMRES with CGS2
+// and the pseudo-time Newton loops of Sec. 3.2 (BDF2 dual time, steady PTC with SER).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#include "fr_internal.h"
+
+namespace {
+
+// ------------------------------------------------------------------ 1-D basis (Sec. 3.1)
+// Legendre P_k(x) and P_k'(x) by the three-term recurrence.
+void legendre(int k, double x, double* P, double* dP) {
+  double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+  if (k == 0) { *P = 1.0; *dP = 0.0; return; }
+  for (int m = 1; m < k; ++m) {
+    const double p2 = ((2 * m + 1) * x * p1 - m * p0) / (m + 1);
+    const double d2 = d0 + (2 * m + 1) * p1;  // P'_{m+1} = P'_{m-1} + (2m+1) P_m
+    p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+  }
+  *P = p1;
+  *dP = d1;
+}
+
+// Gauss-Legendre points: roots of P_n by Newton iteration from Chebyshev-like guesses.
+void gauss_points(int n, double* xs) {
+  for (int k = 0; k < n; ++k) {
+    double x = -std::cos(M_PI * (k + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(n, x, &P, &dP);
+      const double dx = P / dP;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    xs[k] = x;
+  }
+}
+
+fr::Basis make_basis(int p) {
+  fr::Basis B;
+  std::memset(&B, 0, sizeof(B));
+  const int n = p + 1;
+  double xs[fr::MAXN];
+  gauss_points(n, xs);
+  for (int i = 0; i < n; ++i) B.xs[i] = xs[i];
+  // barycentric weights
+  double bw[fr::MAXN];
+  for (int k = 0; k < n; ++k) {
+    double prod = 1.0;
+    for (int m = 0; m < n; ++m) if (m != k) prod *= (xs[k] - xs[m]);
+    bw[k] = 1.0 / prod;
+  }
+  for (int i = 0; i < n; ++i) {
+    double diag = 0.0;
+    for (int k = 0; k < n; ++k) {
+      if (k == i) continue;
+      B.D[i][k] = (bw[k] / bw[i]) / (xs[i] - xs[k]);
+      diag -= B.D[i][k];
+    }
+    B.D[i][i] = diag;
+  }
+  for (int k = 0; k < n; ++k) {
+    double a = 1.0, b = 1.0;
+    for (int m = 0; m < n; ++m) {
+      if (m == k) continue;
+      a *= (-1.0 - xs[m]) / (xs[k] - xs[m]);
+      b *= (1.0 - xs[m]) / (xs[k] - xs[m]);
+    }
+    B.lL[k] = a;
+    B.lR[k] = b;
+  }
+  // g_R = (P_{p+1} + P_p)/2, g_L(x) = g_R(-x):  g_R'(x) = (P'_{p+1} + P'_p)/2,
+  // g_L'(x) = -g_R'(-x).
+  auto dgr = [p](double x) {
+    double P1, dP1, P0, dP0;
+    legendre(p + 1, x, &P1, &dP1);
+    legendre(p, x, &P0, &dP0);
+    return 0.5 * (dP1 + dP0);
+  };
+  for (int i = 0; i < n; ++i) {
+    B.dgR[i] = dgr(xs[i]);
+    B.dgL[i] = -dgr(-xs[i]);
+  }
+  B.dgR_end = 0.5 * (p + 1) * (p + 1);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) B.Dc[i][k] = B.D[i][k] - B.dgL[i] * B.lL[k] - B.dgR[i] * B.lR[k];
+  return B;
+}
+
+fr::Gas make_gas(const fr_config& c) {
+  fr::Gas g;
+  const double M2 = c.mach * c.mach;
+  g.gamma = c.gamma;
+  g.R = 1.0 / (c.gamma * M2);
+  g.inv_R = c.gamma * M2;
+  g.cp = 1.0 / ((c.gamma - 1.0) * M2);
+  g.inv_cp = (c.gamma - 1.0) * M2;
+  g.inv_gm1 = 1.0 / (c.gamma - 1.0);
+  g.mu = 1.0;
+  g.viscous = c.re > 0.0;
+  g.inv_re = g.viscous ? 1.0 / c.re : 0.0;
+  g.k_cond = g.mu * g.cp / c.prandtl;
+  g.kappa_minf = c.kappa * c.mach;
+  g.eps_floor = c.eps_floor;
+  return g;
+}
+
+template <class T> int dev_alloc(fr_ctx* c, T** p, size_t count) {
+  if (*p) { cudaFree(*p); *p = nullptr; }
+  if (count == 0) return FR_OK;
+  FR_CUDA_CHECK(c, cudaMalloc((void**)p, count * sizeof(T)));
+  return FR_OK;
+}
+
+void free_mesh(fr_ctx* c) {
+  double** ds[] = {&c->gs, &c->gf, &c->tq, &c->tg, &c->gl, &c->fn, &c->qcm, &c->tq_d, &c->tg_d,
+                   &c->gl_d, &c->fn_d, &c->qcm_d, &c->B64, &c->V, &c->w_r, &c->w_z, &c->w_x,
+                   &c->w_t, &c->w_u, &c->red};
+  for (double** p : ds) if (*p) { cudaFree(*p); *p = nullptr; }
+  if (c->Binv) { cudaFree(c->Binv); c->Binv = nullptr; }
+  if (c->Dr) { cudaFree(c->Dr); c->Dr = nullptr; }
+  if (c->Dc) { cudaFree(c->Dc); c->Dc = nullptr; }
+  if (c->info) { cudaFree(c->info); c->info = nullptr; }
+  c->blocks_ready = 0;
+}
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+#define FR_TRY(expr)                 \
+  do {                               \
+    int rc_ = (expr);                \
+    if (rc_ != FR_OK) return rc_;    \
+  } while (0)
+
+int check_ready(fr_ctx* c) {
+  if (!c) return FR_ERR_ARG;
+  if (c->ne <= 0) { snprintf(c->err, sizeof(c->err), "fr_set_mesh has not been called"); return FR_ERR_ARG; }
+  return FR_OK;
+}
+
+// host copies of the small device scalars
+int fetch(fr_ctx* c, int off, int count, cudaStream_t s) {
+  FR_CUDA_CHECK(c, cudaMemcpyAsync(c->hsc + off, c->dsc + off, count * sizeof(double),
+                                   cudaMemcpyDeviceToHost, s));
+  FR_CUDA_CHECK(c, cudaStreamSynchronize(s));
+  return FR_OK;
+}
+
+int norms_host(fr_ctx* c, const double* r, double* mass, double* all, cudaStream_t s) {
+  constexpr int off = 4 * FR_MAX_RESTART;
+  FR_TRY(frk::norms(c, r, c->dsc + off, s));
+  FR_TRY(fetch(c, off, 2, s));
+  *mass = std::sqrt(c->hsc[off]);
+  *all = std::sqrt(c->hsc[off + 1]);
+  if (!std::isfinite(*all)) { snprintf(c->err, sizeof(c->err), "non-finite residual norm"); return FR_ERR_NONFINITE; }
+  return FR_OK;
+}
+
+// Classical Gram-Schmidt with one re-orthogonalisation against V[0..nv): projections of
+// the first pass at dsc[0..nv), of the second at dsc[M..M+nv), ||w||^2 at dsc[2M]
+// (M = FR_MAX_RESTART).  Vectors are processed in chunks of 32 per launch.
+int cgs2(fr_ctx* c, int nv, double* w, cudaStream_t s) {
+  constexpr int CH = 32, M = FR_MAX_RESTART;
+  const size_t N = c->ndof;
+  if (nv <= CH) {
+    FR_TRY(frk::dots(c, c->V, nv, w, c->dsc, s));
+    FR_TRY(frk::axpy_dots(c, c->V, nv, c->dsc, w, c->dsc + M, s));
+    return frk::axpy_norm(c, c->V, nv, c->dsc + M, w, c->dsc + 2 * M, s);
+  }
+  for (int k0 = 0; k0 < nv; k0 += CH)
+    FR_TRY(frk::dots(c, c->V + (size_t)k0 * N, std::min(CH, nv - k0), w, c->dsc + k0, s));
+  for (int k0 = 0; k0 < nv; k0 += CH)
+    FR_TRY(frk::axpy(c, c->V + (size_t)k0 * N, std::min(CH, nv - k0), c->dsc + k0, w, s));
+  for (int k0 = 0; k0 < nv; k0 += CH)
+    FR_TRY(frk::dots(c, c->V + (size_t)k0 * N, std::min(CH, nv - k0), w, c->dsc + M + k0, s));
+  for (int k0 = 0; k0 + CH < nv; k0 += CH)
+    FR_TRY(frk::axpy(c, c->V + (size_t)k0 * N, CH, c->dsc + M + k0, w, s));
+  const int last = ((nv - 1) / CH) * CH;
+  return frk::axpy_norm(c, c->V + (size_t)last * N, nv - last, c->dsc + M + last, w, c->dsc + 2 * M, s);
+}
+
+// Restarted preconditioned GMRES(m), CGS2 Arnoldi, Givens rotations on the host.
+// Left preconditioning (PETSc's default): Krylov space of B^-1 A, minimises
+// ||B^-1 (b - A x)||, tolerance relative to ||B^-1 b||.  Right: Krylov space of A B^-1,
+// x = B^-1 V y, minimises ||b - A x||, tolerance relative to ||b||.
+// Layout of the device scalar area dsc (M = FR_MAX_RESTART): [0,M) first projections,
+// [M,2M) second projections, [2M] squared norm, [3M,4M) Krylov coefficients y,
+// [4M, 4M+2) norms.
+int gmres_solve(fr_ctx* c, const double* q, const double* b, double inv_dtau, double a0_dt,
+                double* x, int* iters, cudaStream_t s) {
+  const size_t N = c->ndof;
+  const int m = c->cfg.restart;
+  const double tol = c->cfg.tol_res;
+  const int maxit = c->cfg.maxit_lin;
+  const bool left = c->cfg.gmres_side == FR_GMRES_LEFT;
+  double* r = c->w_r;
+  if (left) FR_TRY(frk::block_apply(c, b, r, s));
+  else FR_CUDA_CHECK(c, cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double bm, bnorm;
+  FR_TRY(norms_host(c, r, &bm, &bnorm, s));
+  FR_CUDA_CHECK(c, cudaMemsetAsync(x, 0, N * sizeof(double), s));
+  *iters = 0;
+  if (bnorm == 0.0) return FR_OK;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  double beta = bnorm;
+  int total = 0;
+  while (true) {
+    if (beta <= tol * bnorm) break;
+    if (total >= maxit) break;
+    FR_TRY(frk::scale(c, r, 1.0 / beta, c->V, s));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      double* Vj = c->V + (size_t)j * N;
+      double* w = c->V + (size_t)(j + 1) * N;
+      if (left) {
+        FR_TRY(frk::jvp(c, q, Vj, inv_dtau, a0_dt, c->w_z, s));
+        FR_TRY(frk::block_apply(c, c->w_z, w, s));
+      } else {
+        FR_TRY(frk::block_apply(c, Vj, c->w_z, s));
+        FR_TRY(frk::jvp(c, q, c->w_z, inv_dtau, a0_dt, w, s));
+      }
+      FR_TRY(cgs2(c, j + 1, w, s));
+      FR_CUDA_CHECK(c, cudaMemcpyAsync(c->hsc, c->dsc, (2 * FR_MAX_RESTART + 1) * sizeof(double),
+                                       cudaMemcpyDeviceToHost, s));
+      FR_CUDA_CHECK(c, cudaStreamSynchronize(s));
+      for (int i = 0; i <= j; ++i) H[i * m + j] = c->hsc[i] + c->hsc[FR_MAX_RESTART + i];
+      const double hn = std::sqrt(c->hsc[2 * FR_MAX_RESTART]);
+      if (!std::isfinite(hn)) { snprintf(c->err, sizeof(c->err), "GMRES: non-finite Krylov vector"); return FR_ERR_NONFINITE; }
+      H[(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t;
+      }
+      const double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
+      cs[j] = H[j * m + j] / den;
+      sn[j] = H[(j + 1) * m + j] / den;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++total;
+      k = j + 1;
+      if (hn > 0.0) FR_TRY(frk::scale(c, w, 1.0 / hn, w, s));
+      if (std::fabs(g[j + 1]) <= tol * bnorm || total >= maxit || hn == 0.0) break;
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int l = i + 1; l < k; ++l) acc -= H[i * m + l] * y[l];
+      y[i] = acc / H[i * m + i];
+    }
+    std::memcpy(c->hsc + 3 * FR_MAX_RESTART, y.data(), k * sizeof(double));
+    FR_CUDA_CHECK(c, cudaMemcpyAsync(c->dsc + 3 * FR_MAX_RESTART, c->hsc + 3 * FR_MAX_RESTART,
+                                     k * sizeof(double), cudaMemcpyHostToDevice, s));
+    FR_TRY(frk::lincomb(c, c->V, k, c->dsc + 3 * FR_MAX_RESTART, c->w_u, s));
+    if (left) {
+      FR_TRY(frk::axpby(c, 1.0, c->w_u, 1.0, x, s));
+    } else {
+      FR_TRY(frk::block_apply(c, c->w_u, c->w_z, s));
+      FR_TRY(frk::axpby(c, 1.0, c->w_z, 1.0, x, s));
+    }
+    // residual of the restart: b - A x (left: preconditioned)
+    FR_TRY(frk::jvp(c, q, x, inv_dtau, a0_dt, c->w_t, s));
+    FR_TRY(frk::axpby(c, 1.0, b, -1.0, c->w_t, s));
+    if (left) FR_TRY(frk::block_apply(c, c->w_t, r, s));
+    else FR_CUDA_CHECK(c, cudaMemcpyAsync(r, c->w_t, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    double rm;
+    FR_TRY(norms_host(c, r, &rm, &beta, s));
+  }
+  *iters = total;
+  return FR_OK;
+}
+
+int newton_loop(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, double a0,
+                double a1, double a2, double dt, bool steady, fr_stats* st, cudaStream_t s) {
+  fr_stats local;
+  if (!st) st = &local;
+  std::memset(st, 0, sizeof(*st));
+  const int maxit = std::min(c->cfg.maxit_newton, FR_MAX_NEWTON);
+  const double a0dt = steady ? 0.0 : a0 / dt;
+  auto rhs = [&](double* out) -> int {
+    if (steady) return frk::residual(c, q, out, nullptr, nullptr, 0, 0, 0, s);
+    return frk::residual(c, q, out, qcn, a2 != 0.0 ? qcnm1 : nullptr, a0 / dt, a1 / dt, a2 / dt, s);
+  };
+  // pseudo-step residual in the spare vector after the Krylov basis (GMRES writes V[0..m],
+  // w_r, w_z, w_t, w_u, and its solution into w_x)
+  double* r = c->V + (size_t)(c->cfg.restart + 1) * c->ndof;
+  FR_TRY(rhs(r));
+  double rm, ra;
+  FR_TRY(norms_host(c, r, &rm, &ra, s));
+  const double res0 = rm;
+  st->res_history[0] = rm;
+  double dtau = steady ? c->cfg.dtau0 : c->cfg.dtau_unsteady;
+  st->dtau_history[0] = dtau;
+  int m = 0;
+  bool conv = false;
+  for (m = 0; m < maxit; ++m) {
+    if (rm <= c->cfg.tol_pseudo * res0) { conv = true; break; }
+    const double inv_dtau = 1.0 / dtau;
+    if (steady || m % std::max(1, c->cfg.lag) == 0) {
+      FR_TRY(frk::block_build(c, q, inv_dtau, a0dt, s));
+      c->blocks_ready = 1;
+      st->block_builds++;
+    }
+    int its = 0;
+    FR_TRY(gmres_solve(c, q, r, inv_dtau, a0dt, c->w_x, &its, s));
+    st->gmres_iterations[m] = its;
+    FR_TRY(frk::axpby(c, 1.0, c->w_x, 1.0, q, s));
+    FR_TRY(rhs(r));
+    const double prev = rm;
+    FR_TRY(norms_host(c, r, &rm, &ra, s));
+    st->res_history[m + 1] = rm;
+    if (steady) {
+      dtau = std::max(c->cfg.dtau_min, std::min(c->cfg.dtau_max, dtau * std::pow(prev / rm, c->cfg.r_ser)));
+    }
+    st->dtau_history[m + 1] = dtau;
+  }
+  if (!conv && rm <= c->cfg.tol_pseudo * res0) conv = true;
+  st->newton_iterations = m;
+  st->converged = conv ? 1 : 0;
+  return conv ? FR_OK : FR_ERR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fr_version(void) { return "fr-gb300 0.1 (sm_103a)"; }
+
+void fr_default_config(fr_config* c) {
+  std::memset(c, 0, sizeof(*c));
+  c->p = 3;
+  c->gamma = 1.4;
+  c->prandtl = 0.72;
+  c->mach = 0.05;
+  c->re = 0.0;
+  c->kappa = 1.0;
+  c->eps_floor = 1e-8;
+  c->prec_dtype = FR_PREC_FP64;
+  c->restart = 30;
+  c->maxit_lin = 100;
+  c->maxit_newton = 20;
+  c->lag = 2;
+  c->tol_res = 1e-6;
+  c->tol_pseudo = 1e-8;
+  c->dtau0 = 0.01;
+  c->dtau_min = 0.01;
+  c->dtau_max = 1e20;
+  c->r_ser = 2.0;
+  c->dtau_unsteady = 1e20;
+  c->gmres_side = FR_GMRES_LEFT;
+}
+
+int fr_create(const fr_config* cfg, fr_ctx** out) {
+  if (!cfg || !out) return FR_ERR_ARG;
+  *out = nullptr;
+  if (cfg->p < 1 || cfg->p > 4 || cfg->mach <= 0 || cfg->gamma <= 1.0 || cfg->restart < 1 ||
+      cfg->restart > FR_MAX_RESTART || cfg->prec_dtype < 0 || cfg->prec_dtype > 2 ||
+      (cfg->gmres_side != FR_GMRES_LEFT && cfg->gmres_side != FR_GMRES_RIGHT))
+    return FR_ERR_ARG;
+  fr_ctx* c = new fr_ctx();
+  c->cfg = *cfg;
+  c->p = cfg->p;
+  c->n = cfg->p + 1;
+  c->np2 = c->n * c->n;
+  c->bsz = 4 * c->np2;
+  c->ne = 0;
+  c->err[0] = 0;
+  c->basis = make_basis(cfg->p);
+  c->gas = make_gas(*cfg);
+  if (cudaMalloc((void**)&c->dsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->hsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess) {
+    delete c;
+    return FR_ERR_CUDA;
+  }
+  *out = c;
+  return FR_OK;
+}
+
+void fr_destroy(fr_ctx* c) {
+  if (!c) return;
+  free_mesh(c);
+  if (c->dsc) cudaFree(c->dsc);
+  if (c->hsc) cudaFreeHost(c->hsc);
+  delete c;
+}
+
+int fr_set_mesh(fr_ctx* c, int nx, int ny, int px, int py) {
+  if (!c) return FR_ERR_ARG;
+  if (nx < 2 || ny < 2 || px != 1 || py != 1) {
+    snprintf(c->err, sizeof(c->err), "fr_set_mesh: need nx, ny >= 2 and periodic_x = periodic_y = 1");
+    return FR_ERR_ARG;
+  }
+  free_mesh(c);
+  c->nx = nx; c->ny = ny; c->ne = nx * ny;
+  c->mesh.nx = nx; c->mesh.ny = ny; c->mesh.ne = c->ne;
+  const size_t ne = c->ne, n = c->n, np2 = c->np2, bs = c->bsz;
+  c->ndof = 4 * ne * np2;
+  c->red_blocks = 2 * 152;
+  FR_TRY(dev_alloc(c, &c->gs, (size_t)fr::GS_COUNT * ne * np2));
+  FR_TRY(dev_alloc(c, &c->gf, (size_t)fr::GF_COUNT * ne * 4 * n));
+  FR_TRY(dev_alloc(c, &c->tq, ne * 16 * n));
+  FR_TRY(dev_alloc(c, &c->tq_d, ne * 16 * n));
+  FR_TRY(dev_alloc(c, &c->tg, ne * 32 * n));
+  FR_TRY(dev_alloc(c, &c->tg_d, ne * 32 * n));
+  FR_TRY(dev_alloc(c, &c->gl, 8 * ne * np2));
+  FR_TRY(dev_alloc(c, &c->gl_d, 8 * ne * np2));
+  FR_TRY(dev_alloc(c, &c->fn, ne * 8 * n));
+  FR_TRY(dev_alloc(c, &c->fn_d, ne * 8 * n));
+  FR_TRY(dev_alloc(c, &c->qcm, ne * 8 * n));
+  FR_TRY(dev_alloc(c, &c->qcm_d, ne * 8 * n));
+  FR_TRY(dev_alloc(c, &c->B64, ne * bs * bs));
+  const size_t esz = c->cfg.prec_dtype == FR_PREC_FP64 ? 8 : c->cfg.prec_dtype == FR_PREC_FP32 ? 4 : 2;
+  FR_CUDA_CHECK(c, cudaMalloc(&c->Binv, ne * bs * bs * esz));
+  FR_TRY(dev_alloc(c, &c->Dr, ne * bs));
+  FR_TRY(dev_alloc(c, &c->Dc, ne * bs));
+  FR_TRY(dev_alloc(c, &c->info, ne));
+  // Krylov basis V[0..m] plus one extra vector holding the pseudo-step residual
+  FR_TRY(dev_alloc(c, &c->V, (size_t)(c->cfg.restart + 2) * c->ndof));
+  FR_TRY(dev_alloc(c, &c->w_r, c->ndof));
+  FR_TRY(dev_alloc(c, &c->w_z, c->ndof));
+  FR_TRY(dev_alloc(c, &c->w_x, c->ndof));
+  FR_TRY(dev_alloc(c, &c->w_t, c->ndof));
+  FR_TRY(dev_alloc(c, &c->w_u, c->ndof));
+  FR_TRY(dev_alloc(c, &c->red, (size_t)32 * c->red_blocks));
+  return FR_OK;
+}
+
+int fr_update_mesh(fr_ctx* c, const double* corners, const double* vel, void* s) {
+  FR_TRY(check_ready(c));
+  if (!corners || !vel) return FR_ERR_ARG;
+  return frk::geometry(c, corners, vel, S(s));
+}
+
+int fr_residual(fr_ctx* c, const double* q, double* R, void* s) {
+  FR_TRY(check_ready(c));
+  return frk::residual(c, q, R, nullptr, nullptr, 0, 0, 0, S(s));
+}
+
+int fr_bdf_rhs(fr_ctx* c, const double* q, const double* qcn, const double* qcnm1, double a0,
+               double a1, double a2, double dt, double* r, void* s) {
+  FR_TRY(check_ready(c));
+  if (!qcn || dt <= 0 || (a2 != 0.0 && !qcnm1)) return FR_ERR_ARG;
+  return frk::residual(c, q, r, qcn, a2 != 0.0 ? qcnm1 : nullptr, a0 / dt, a1 / dt, a2 / dt, S(s));
+}
+
+int fr_conservative(fr_ctx* c, const double* q, double* qc, void* s) {
+  FR_TRY(check_ready(c));
+  return frk::conservative(c, q, qc, S(s));
+}
+
+int fr_jvp(fr_ctx* c, const double* q, const double* v, double inv_dtau, double a0_dt, double* Av,
+           void* s) {
+  FR_TRY(check_ready(c));
+  return frk::jvp(c, q, v, inv_dtau, a0_dt, Av, S(s));
+}
+
+int fr_precond_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, void* s) {
+  FR_TRY(check_ready(c));
+  FR_TRY(frk::block_build(c, q, inv_dtau, a0_dt, S(s)));
+  c->blocks_ready = 1;
+  return FR_OK;
+}
+
+int fr_precond_blocks(fr_ctx* c, double* B, void* s) {
+  FR_TRY(check_ready(c));
+  if (!c->blocks_ready) { snprintf(c->err, sizeof(c->err), "no preconditioner built"); return FR_ERR_ARG; }
+  FR_CUDA_CHECK(c, cudaMemcpyAsync(B, c->B64, (size_t)c->ne * c->bsz * c->bsz * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, S(s)));
+  return FR_OK;
+}
+
+int fr_precond_apply(fr_ctx* c, const double* r, double* z, void* s) {
+  FR_TRY(check_ready(c));
+  if (!c->blocks_ready) { snprintf(c->err, sizeof(c->err), "no preconditioner built"); return FR_ERR_ARG; }
+  return frk::block_apply(c, r, z, S(s));
+}
+
+int fr_gmres(fr_ctx* c, const double* q, const double* b, double inv_dtau, double a0_dt, double* x,
+             int* iters, void* s) {
+  FR_TRY(check_ready(c));
+  if (!c->blocks_ready) { snprintf(c->err, sizeof(c->err), "no preconditioner built"); return FR_ERR_ARG; }
+  int its = 0;
+  FR_TRY(gmres_solve(c, q, b, inv_dtau, a0_dt, x, &its, S(s)));
+  if (iters) *iters = its;
+  return FR_OK;
+}
+
+int fr_bdf2_step(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, double a0, double a1,
+                 double a2, double dt, fr_stats* st, void* s) {
+  FR_TRY(check_ready(c));
+  if (!q || !qcn || dt <= 0 || (a2 != 0.0 && !qcnm1)) return FR_ERR_ARG;
+  return newton_loop(c, q, qcn, qcnm1, a0, a1, a2, dt, false, st, S(s));
+}
+
+int fr_ptc_solve(fr_ctx* c, double* q, fr_stats* st, void* s) {
+  FR_TRY(check_ready(c));
+  if (!q) return FR_ERR_ARG;
+  return newton_loop(c, q, nullptr, nullptr, 0, 0, 0, 1.0, true, st, S(s));
+}
+
+int fr_residual_norms(fr_ctx* c, const double* r, double* mass, double* all, void* s) {
+  FR_TRY(check_ready(c));
+  double m, a;
+  FR_TRY(norms_host(c, r, &m, &a, S(s)));
+  if (mass) *mass = m;
+  if (all) *all = a;
+  return FR_OK;
+}
+
+size_t fr_num_dof(const fr_ctx* c) { return c ? c->ndof : 0; }
+int fr_block_size(const fr_ctx* c) { return c ? c->bsz : 0; }
+long long fr_kernel_launches(const fr_ctx* c) { return c ? c->launches : 0; }
+const char* fr_last_error(const fr_ctx* c) { return c ? c->err : "null context"; }
+
+}  // extern "C"

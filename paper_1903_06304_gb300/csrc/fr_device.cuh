@@ -1,0 +1,247 @@
+// fr_device.cuh -- device building blocks of the preconditioned FR/CPR residual
+// (Wang & Yu, arXiv 1903.06304, Secs. 2-3) for sm_103a.
+//
+// Every arithmetic routine is a template on the scalar T: double for the residual,
+// Dual (value + one tangent) for the exact forward-mode Jacobian action.  The FP64
+// pipe is the binding resource on GB300, so the formulas are arranged to minimise
+// FP64 instructions: no unit normals (|S| f_n = f . S), the FR correction folded into
+// a corrected derivative matrix, BR2 liftings in closed form, one reciprocal per
+// temperature.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fr {
+
+constexpr int MAXN = 5;  // p <= 4
+
+// ---------------------------------------------------------------- constants
+// 1-D FR basis on [-1,1] with Gauss solution points (Sec. 3.1).
+struct Basis {
+  double D[MAXN][MAXN];   // D[i][k] = l_k'(x_i)
+  double Dc[MAXN][MAXN];  // D[i][k] - g_L'(x_i) l_k(-1) - g_R'(x_i) l_k(1)
+  double lL[MAXN], lR[MAXN];
+  double dgL[MAXN], dgR[MAXN];
+  double dgR_end;         // g_R'(1) = (p+1)^2/2; g_L'(-1) = -g_R'(1)
+  double xs[MAXN];        // solution points
+};
+
+// Nondimensional gas of Sec. 2.1 and preconditioning cut-off (Eqs. eps_nonmove/move).
+struct Gas {
+  double gamma, R, inv_R, cp, inv_cp, inv_gm1;
+  double mu, inv_re, k_cond;     // k_cond = mu C_p / Pr
+  double kappa_minf, eps_floor;
+  int viscous;
+};
+
+// Geometry at solution points: arrays gs[k][Ne*np2].
+enum { GS_SXX, GS_SXY, GS_SEX, GS_SEY, GS_STX, GS_STE, GS_INVJ, GS_DIVST, GS_UG, GS_VG, GS_J,
+       GS_COUNT };
+// Geometry at flux points: arrays gf[k][Ne][4 faces][n].  S is |J| grad(xi) on the
+// L/R faces and |J| grad(eta) on the B/T faces.
+enum { GF_SX, GF_SY, GF_J, GF_UG, GF_VG, GF_COUNT };
+enum { FACE_L = 0, FACE_R = 1, FACE_B = 2, FACE_T = 3 };
+
+struct Mesh {
+  int nx, ny, ne;
+  __device__ __forceinline__ int left(int e) const {
+    int i = e % nx, j = e / nx; return j * nx + (i == 0 ? nx - 1 : i - 1);
+  }
+  __device__ __forceinline__ int right(int e) const {
+    int i = e % nx, j = e / nx; return j * nx + (i == nx - 1 ? 0 : i + 1);
+  }
+  __device__ __forceinline__ int bottom(int e) const {
+    int i = e % nx, j = e / nx; return (j == 0 ? ny - 1 : j - 1) * nx + i;
+  }
+  __device__ __forceinline__ int top(int e) const {
+    int i = e % nx, j = e / nx; return (j == ny - 1 ? 0 : j + 1) * nx + i;
+  }
+};
+
+// ---------------------------------------------------------------- dual numbers
+struct Dual {
+  double v, d;
+};
+__device__ __forceinline__ Dual mk(double v, double d) { Dual r; r.v = v; r.d = d; return r; }
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return mk(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return mk(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ Dual operator-(Dual a) { return mk(-a.v, -a.d); }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return mk(a.v * b.v, fma(a.v, b.d, a.d * b.v)); }
+__device__ __forceinline__ Dual operator+(Dual a, double b) { return mk(a.v + b, a.d); }
+__device__ __forceinline__ Dual operator+(double a, Dual b) { return mk(a + b.v, b.d); }
+__device__ __forceinline__ Dual operator-(Dual a, double b) { return mk(a.v - b, a.d); }
+__device__ __forceinline__ Dual operator-(double a, Dual b) { return mk(a - b.v, -b.d); }
+__device__ __forceinline__ Dual operator*(Dual a, double b) { return mk(a.v * b, a.d * b); }
+__device__ __forceinline__ Dual operator*(double a, Dual b) { return mk(a * b.v, a * b.d); }
+__device__ __forceinline__ Dual inv(Dual a) {
+  double r = 1.0 / a.v;
+  return mk(r, -a.d * r * r);
+}
+__device__ __forceinline__ double inv(double a) { return 1.0 / a; }
+__device__ __forceinline__ Dual sqrt_(Dual a) {
+  double s = sqrt(a.v);
+  return mk(s, a.d * (0.5 / s));
+}
+__device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
+__device__ __forceinline__ double val(double a) { return a; }
+__device__ __forceinline__ double val(Dual a) { return a.v; }
+__device__ __forceinline__ double tan_(double) { return 0.0; }
+__device__ __forceinline__ double tan_(Dual a) { return a.d; }
+template <class T> __device__ __forceinline__ T abs_(T a) { return val(a) < 0 ? -a : a; }
+// max/min deciding on values; ties keep the first argument (same rule as the oracle).
+template <class T> __device__ __forceinline__ T vmax(T a, T b) { return val(a) >= val(b) ? a : b; }
+template <class T> __device__ __forceinline__ T vmin(T a, T b) { return val(a) <= val(b) ? a : b; }
+template <class T> __device__ __forceinline__ T fmadd(T a, T b, T c) { return a * b + c; }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+
+template <class T> __device__ __forceinline__ T from_parts(double v, double d);
+template <> __device__ __forceinline__ double from_parts<double>(double v, double) { return v; }
+template <> __device__ __forceinline__ Dual from_parts<Dual>(double v, double d) { return mk(v, d); }
+
+// A device buffer of T stored as separate value / tangent FP64 arrays.
+template <class T> struct Buf;
+template <> struct Buf<double> {
+  double* v;
+  __device__ __forceinline__ double ld(size_t i) const { return v[i]; }
+  __device__ __forceinline__ void st(size_t i, double x) const { v[i] = x; }
+};
+template <> struct Buf<Dual> {
+  double* v;
+  double* d;
+  __device__ __forceinline__ Dual ld(size_t i) const { return mk(v[i], d[i]); }
+  __device__ __forceinline__ void st(size_t i, Dual x) const { v[i] = x.v; d[i] = x.d; }
+};
+
+// ---------------------------------------------------------------- pointwise physics
+// State relations (Sec. 2.1): rho = p/(R T), q^c, inviscid fluxes (Eq. convection).
+template <class T>
+struct Thermo {
+  T rho, qc[4], f[4], g[4];
+};
+
+template <class T>
+__device__ __forceinline__ void thermo(const T q[4], const Gas& gs, Thermo<T>& o) {
+  const T invT = inv(q[3]);
+  o.rho = q[0] * invT * gs.inv_R;
+  const T ru = o.rho * q[1], rv = o.rho * q[2];
+  const T ke = 0.5 * (ru * q[1] + rv * q[2]);
+  const T E = q[0] * gs.inv_gm1 + ke;
+  const T H = E + q[0];
+  o.qc[0] = o.rho; o.qc[1] = ru; o.qc[2] = rv; o.qc[3] = E;
+  o.f[0] = ru; o.f[1] = ru * q[1] + q[0]; o.f[2] = ru * q[2]; o.f[3] = H * q[1];
+  o.g[0] = rv; o.g[1] = o.f[2];          o.g[2] = rv * q[2] + q[0]; o.g[3] = H * q[2];
+}
+
+// Viscous fluxes (Eqs. diffusion, shear_stress), added with the FR sign: the total
+// flux is f_inv - f_vis, so fv/gv here are returned as -f_vis, -g_vis.
+template <class T>
+__device__ __forceinline__ void neg_viscous_flux(const T q[4], const T qx[4], const T qy[4],
+                                                 const Gas& gs, T fv[4], T gv[4]) {
+  const double m43 = 4.0 / 3.0 * gs.mu * gs.inv_re, m23 = 2.0 / 3.0 * gs.mu * gs.inv_re;
+  const double m1 = gs.mu * gs.inv_re, kr = gs.k_cond * gs.inv_re;
+  const T txx = m43 * qx[1] - m23 * qy[2];
+  const T tyy = m43 * qy[2] - m23 * qx[1];
+  const T txy = m1 * (qy[1] + qx[2]);
+  fv[0] = from_parts<T>(0.0, 0.0);
+  fv[1] = -txx;
+  fv[2] = -txy;
+  fv[3] = -(q[1] * txx + q[2] * txy + kr * qx[3]);
+  gv[0] = from_parts<T>(0.0, 0.0);
+  gv[1] = -txy;
+  gv[2] = -tyy;
+  gv[3] = -(q[1] * txy + q[2] * tyy + kr * qy[3]);
+}
+
+// ---------------------------------------------------------------- common face flux
+// Owned-face common flux scaled by the face metric:  F^num = |S| f_n^com (Eq.
+// norm_f_2 with sign(n . grad xi) = +1 on structured meshes), where the normal is
+// S/|S| and S = |J| grad(xi) (or grad(eta)) on the '-' element's face.
+//   inviscid (Eq. Rosanov): |S| f_n,inv = f . S - (v_g . S) q^c on each side,
+//     dissipation 1/2 |lambda|max(S) Gamma~ (q+ - q-), all of eps, U_r, Gamma~ and
+//     |lambda| at the averaged primitive state; |lambda| is homogeneous in S.
+//   viscous (BR2, Sec. 3.1): q^com = (q+ + q-)/2, grad q^com = (grad q+ + r+ + grad q-
+//     + r-)/2 with r-+ = (q^com - q-+) S g'(end) / |J|-+, which sum to
+//     (q+ - q-) S g_R'(1) (1/|J|- + 1/|J|+) / 2;  |S| f_vis . n = f_vis . S.
+template <class T>
+__device__ __forceinline__ void face_common(const T qm[4], const T qp[4], const T gm[8],
+                                            const T gp[8], double Sx, double Sy, double ug,
+                                            double vg, double Jm, double Jp, const Gas& gs,
+                                            double dgR_end, T fnum[4], T qcom[4]) {
+  T dq[4], qa[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { dq[k] = qp[k] - qm[k]; qa[k] = 0.5 * (qp[k] + qm[k]); qcom[k] = qa[k]; }
+  // --- normal fluxes of both sides
+  T fm[4], fp[4];
+  {
+    Thermo<T> t;
+    thermo(qm, gs, t);
+    const double vgS = ug * Sx + vg * Sy;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fm[k] = t.f[k] * Sx + t.g[k] * Sy - vgS * t.qc[k];
+    thermo(qp, gs, t);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fp[k] = t.f[k] * Sx + t.g[k] * Sy - vgS * t.qc[k];
+  }
+  // --- averaged state: eps, U_r, alpha, c', |lambda|max, Gamma~ (Eqs. theta,
+  //     eigenvalues_para, eps_move)
+  const T invTa = inv(qa[3]);
+  const T rho = qa[0] * invTa * gs.inv_R;
+  const T c2 = gs.gamma * gs.R * qa[3];
+  const T wx = qa[1] - ug, wy = qa[2] - vg;
+  const T w2 = wx * wx + wy * wy;
+  // M_mov^2 = |v - v_g|^2 / c^2; eps = min(1, max(kappa M_inf, M_mov)), floored.
+  T eps = sqrt_(w2 * inv(c2));
+  eps = vmax(from_parts<T>(gs.kappa_minf, 0.0), eps);
+  eps = vmin(from_parts<T>(1.0, 0.0), eps);
+  eps = vmax(eps, from_parts<T>(gs.eps_floor, 0.0));
+  const T ur2 = eps * eps * c2;
+  const T beta = (gs.inv_R - gs.inv_cp) * invTa;     // rho_p + rho_T/(rho C_p)
+  const T alpha = 0.5 * (1.0 - beta * ur2);
+  const double S2 = Sx * Sx + Sy * Sy;
+  const T un = wx * Sx + wy * Sy;                     // |S| u_n
+  const T unp = un * (1.0 - alpha);
+  const T cpr = sqrt_(alpha * alpha * un * un + ur2 * S2);
+  T lmax = abs_(un);
+  lmax = vmax(lmax, abs_(un));
+  lmax = vmax(lmax, abs_(unp + cpr));
+  lmax = vmax(lmax, abs_(unp - cpr));
+  const T theta = inv(ur2) + invTa * gs.inv_cp;      // 1/U_r^2 - rho_T/(rho C_p)
+  const T h = gs.cp * qa[3] + 0.5 * (qa[1] * qa[1] + qa[2] * qa[2]);
+  const T rhoT = -rho * invTa;
+  // Gamma~ dq with Gamma~ of Eq. preconditioning, rows arranged around d0.
+  const T d0 = theta * dq[0] + rhoT * dq[3];
+  const T rdu = rho * dq[1], rdv = rho * dq[2];
+  T diss[4];
+  diss[0] = d0;
+  diss[1] = qa[1] * d0 + rdu;
+  diss[2] = qa[2] * d0 + rdv;
+  diss[3] = h * d0 - dq[0] + qa[1] * rdu + qa[2] * rdv + rho * gs.cp * dq[3];
+  const T hl = 0.5 * lmax;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) fnum[k] = 0.5 * (fm[k] + fp[k]) - hl * diss[k];
+  if (gs.viscous) {
+    // (r- + r+)/2 = (q+ - q-) S g_R'(1) (1/|J|- + 1/|J|+) / 4
+    const double lift = 0.25 * dgR_end * (1.0 / Jm + 1.0 / Jp);
+    T qx[4], qy[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const T jl = dq[k] * lift;
+      qx[k] = 0.5 * (gm[k] + gp[k]) + jl * Sx;
+      qy[k] = 0.5 * (gm[4 + k] + gp[4 + k]) + jl * Sy;
+    }
+    T fv[4], gv[4];
+    neg_viscous_flux(qa, qx, qy, gs, fv, gv);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fnum[k] = fnum[k] + fv[k] * Sx + gv[k] * Sy;
+  }
+}
+
+// ---------------------------------------------------------------- launch geometry
+// Elements per block for the point-parallel kernels (one thread per solution point).
+template <int N> struct Tile {
+  static constexpr int NP = N * N;
+  static constexpr int EPB = 128 / NP;
+  static constexpr int THREADS = EPB * NP;
+};
+
+}  // namespace fr

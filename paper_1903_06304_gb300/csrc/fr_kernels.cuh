@@ -1,0 +1,260 @@
+// fr_kernels.cuh -- the three point-parallel kernels of one residual / JVP evaluation
+// (trace, face, elem) and the pointwise (Gamma/dtau + a0/dt M) product; included by the
+// residual and the preconditioner translation units.
+#pragma once
+#include "fr_device.cuh"
+
+namespace fr {
+
+// ------------------------------------------------------------------ trace kernel
+// q^p (and the tangent) of EPB elements staged in shared memory; each thread owns one
+// solution point.  Outputs: gl[8][Ne*NP] local gradients (x comps then y comps),
+// tq[Ne][4][4][N] state traces, tg[Ne][4][8][N] gradient traces.
+template <class T, int N>
+__global__ void __launch_bounds__(Tile<N>::THREADS)
+k_trace(Buf<T> Q, int ne, Basis B, Gas gas, const double* __restrict__ gs, Buf<T> GL, Buf<T> TQ,
+        Buf<T> TG) {
+  constexpr int NP = N * N, EPB = Tile<N>::EPB;
+  __shared__ T sq[EPB][4][NP];
+  __shared__ T sg[EPB][8][NP];
+  const int le = threadIdx.x / NP, pt = threadIdx.x % NP;
+  const int e = blockIdx.x * EPB + le;
+  const bool live = (le < EPB) && (e < ne);
+  const int i = pt % N, j = pt / N;
+  const size_t SN = (size_t)ne * NP;
+  const size_t o = (size_t)e * NP + pt;
+  if (live) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sq[le][v][pt] = Q.ld(v * SN + o);
+  }
+  __syncthreads();
+  if (gas.viscous) {
+    if (live) {
+      const double sxx = gs[GS_SXX * SN + o], sxy = gs[GS_SXY * SN + o];
+      const double sex = gs[GS_SEX * SN + o], sey = gs[GS_SEY * SN + o];
+      const double ij = gs[GS_INVJ * SN + o];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        T dxi = B.D[i][0] * sq[le][v][j * N + 0];
+        T deta = B.D[j][0] * sq[le][v][0 * N + i];
+#pragma unroll
+        for (int k = 1; k < N; ++k) {
+          dxi = dxi + B.D[i][k] * sq[le][v][j * N + k];
+          deta = deta + B.D[j][k] * sq[le][v][k * N + i];
+        }
+        const T gx = (sxx * dxi + sex * deta) * ij;
+        const T gy = (sxy * dxi + sey * deta) * ij;
+        sg[le][v][pt] = gx;
+        sg[le][4 + v][pt] = gy;
+        GL.st(v * SN + o, gx);
+        GL.st((4 + v) * SN + o, gy);
+      }
+    }
+    __syncthreads();
+  }
+  if (!live) return;
+  for (int t = pt; t < 4 * N; t += NP) {
+    const int f = t / N, s = t % N;
+    const double* w = (f == FACE_L || f == FACE_B) ? B.lL : B.lR;
+    const bool row = (f == FACE_L || f == FACE_R);  // along xi at fixed eta index s
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      T acc = w[0] * sq[le][c][row ? s * N : s];
+#pragma unroll
+      for (int k = 1; k < N; ++k) acc = acc + w[k] * sq[le][c][row ? s * N + k : k * N + s];
+      TQ.st((((size_t)e * 4 + f) * 4 + c) * N + s, acc);
+    }
+    if (gas.viscous) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        T acc = w[0] * sg[le][c][row ? s * N : s];
+#pragma unroll
+        for (int k = 1; k < N; ++k) acc = acc + w[k] * sg[le][c][row ? s * N + k : k * N + s];
+        TG.st((((size_t)e * 4 + f) * 8 + c) * N + s, acc);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ face kernel
+// One thread per owned flux point: xi-faces are owned by their '-' (left) element (its R
+// face), eta-faces by their bottom element (its T face).  Outputs fn, qcm [Ne][2][4][N].
+template <class T, int N>
+__global__ void k_face(Mesh M, Basis B, Gas gas, const double* __restrict__ gf, Buf<T> TQ,
+                       Buf<T> TG, Buf<T> FN, Buf<T> QC) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M.ne * 2 * N) return;
+  const int e = idx / (2 * N), rem = idx % (2 * N), dir = rem / N, t = rem % N;
+  const int plus = dir == 0 ? M.right(e) : M.top(e);
+  const int fm = dir == 0 ? FACE_R : FACE_T, fp = dir == 0 ? FACE_L : FACE_B;
+  T qm[4], qp[4], gm[8], gp[8];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    qm[v] = TQ.ld((((size_t)e * 4 + fm) * 4 + v) * N + t);
+    qp[v] = TQ.ld((((size_t)plus * 4 + fp) * 4 + v) * N + t);
+  }
+  if (gas.viscous) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      gm[c] = TG.ld((((size_t)e * 4 + fm) * 8 + c) * N + t);
+      gp[c] = TG.ld((((size_t)plus * 4 + fp) * 8 + c) * N + t);
+    }
+  }
+  const size_t FNs = (size_t)M.ne * 4 * N;
+  const size_t om = ((size_t)e * 4 + fm) * N + t, op = ((size_t)plus * 4 + fp) * N + t;
+  T fnum[4], qcom[4];
+  face_common(qm, qp, gm, gp, gf[GF_SX * FNs + om], gf[GF_SY * FNs + om], gf[GF_UG * FNs + om],
+              gf[GF_VG * FNs + om], gf[GF_J * FNs + om], gf[GF_J * FNs + op], gas, B.dgR_end,
+              fnum, qcom);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const size_t oo = (((size_t)e * 2 + dir) * 4 + v) * N + t;
+    FN.st(oo, fnum[v]);
+    QC.st(oo, qcom[v]);
+  }
+}
+
+// ------------------------------------------------------------------ element kernel
+enum { MODE_RESID = 0, MODE_JVP = 1 };
+
+struct TimeTerms {           // r = R - (a0 q^c + a1 qc_n + a2 qc_nm1)/dt
+  const double* qcn;
+  const double* qcnm1;
+  double a0dt, a1dt, a2dt;
+};
+struct JvpTerms {            // A v = inv_dtau Gamma v + a0_dt M v - dR/dq v
+  double inv_dtau, a0_dt;
+};
+
+// (inv_dtau Gamma + a0_dt M) w at one point (Eqs. jacobian, preconditioning, theta),
+// eps from the point's own v - v_g (Eq. eps_move).
+__device__ __forceinline__ void gamma_m_apply(const double q[4], const double w[4], double ug,
+                                              double vg, const Gas& gs, double inv_dtau,
+                                              double a0_dt, double out[4]) {
+  const double invT = 1.0 / q[3];
+  const double rho = q[0] * invT * gs.inv_R;
+  const double c2 = gs.gamma * gs.R * q[3];
+  const double wx = q[1] - ug, wy = q[2] - vg;
+  double eps = sqrt((wx * wx + wy * wy) / c2);
+  eps = gs.kappa_minf >= eps ? gs.kappa_minf : eps;
+  eps = 1.0 <= eps ? 1.0 : eps;
+  eps = eps >= gs.eps_floor ? eps : gs.eps_floor;
+  const double ur2 = eps * eps * c2;
+  const double theta = 1.0 / ur2 + invT * gs.inv_cp;
+  const double rho_p = invT * gs.inv_R;
+  const double rhoT = -rho * invT;
+  const double h = gs.cp * q[3] + 0.5 * (q[1] * q[1] + q[2] * q[2]);
+  const double s = inv_dtau + a0_dt;
+  const double c0 = inv_dtau * theta + a0_dt * rho_p;
+  const double d0 = c0 * w[0] + s * rhoT * w[3];
+  const double sr = s * rho;
+  out[0] = d0;
+  out[1] = q[1] * d0 + sr * w[1];
+  out[2] = q[2] * d0 + sr * w[2];
+  out[3] = h * d0 - s * w[0] + sr * (q[1] * w[1] + q[2] * w[2]) + sr * gs.cp * w[3];
+}
+
+template <class T, int N, int MODE>
+__global__ void __launch_bounds__(Tile<N>::THREADS)
+k_elem(Buf<T> Q, Mesh M, Basis B, Gas gas, const double* __restrict__ gs,
+       const double* __restrict__ gf, Buf<T> GL, Buf<T> TQ, Buf<T> FN, Buf<T> QC,
+       double* __restrict__ out, TimeTerms tt, JvpTerms jt) {
+  constexpr int NP = N * N, EPB = Tile<N>::EPB;
+  __shared__ T sF[EPB][4][NP];
+  __shared__ T sG[EPB][4][NP];
+  const int le = threadIdx.x / NP, pt = threadIdx.x % NP;
+  const int e = blockIdx.x * EPB + le;
+  const bool live = (le < EPB) && (e < M.ne);
+  const int i = pt % N, j = pt / N;
+  const size_t SN = (size_t)M.ne * NP;
+  const size_t FNs = (size_t)M.ne * 4 * N;
+  const size_t o = (size_t)e * NP + pt;
+  T q[4];
+  Thermo<T> th;
+  double ij = 0.0;
+  if (live) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) q[v] = Q.ld(v * SN + o);
+    thermo(q, gas, th);
+    ij = gs[GS_INVJ * SN + o];
+    T fx[4], gy[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { fx[v] = th.f[v]; gy[v] = th.g[v]; }
+    if (gas.viscous) {
+      T qx[4], qy[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { qx[v] = GL.ld(v * SN + o); qy[v] = GL.ld((4 + v) * SN + o); }
+      // lifted jumps of the four faces: (q^com_f - q^loc_f) S_f g_f'(.) / |J|
+      const int nbL = M.left(e), nbB = M.bottom(e);
+      const int qsrc[4] = {nbL, e, nbB, e};
+      const int qdir[4] = {0, 0, 1, 1};
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int s = (f < 2) ? j : i;
+        const double w = (f == FACE_L) ? B.dgL[i] : (f == FACE_R) ? B.dgR[i]
+                       : (f == FACE_B) ? B.dgL[j] : B.dgR[j];
+        const size_t of = ((size_t)e * 4 + f) * N + s;
+        const double sx = gf[GF_SX * FNs + of] * w * ij, sy = gf[GF_SY * FNs + of] * w * ij;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const T jump = QC.ld((((size_t)qsrc[f] * 2 + qdir[f]) * 4 + v) * N + s) -
+                         TQ.ld((((size_t)e * 4 + f) * 4 + v) * N + s);
+          qx[v] = qx[v] + jump * sx;
+          qy[v] = qy[v] + jump * sy;
+        }
+      }
+      T fv[4], gv[4];
+      neg_viscous_flux(q, qx, qy, gas, fv, gv);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { fx[v] = fx[v] + fv[v]; gy[v] = gy[v] + gv[v]; }
+    }
+    const double sxx = gs[GS_SXX * SN + o], sxy = gs[GS_SXY * SN + o];
+    const double sex = gs[GS_SEX * SN + o], sey = gs[GS_SEY * SN + o];
+    const double stx = gs[GS_STX * SN + o], ste = gs[GS_STE * SN + o];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      sF[le][v][pt] = sxx * fx[v] + sxy * gy[v] + stx * th.qc[v];
+      sG[le][v][pt] = sex * fx[v] + sey * gy[v] + ste * th.qc[v];
+    }
+  }
+  __syncthreads();
+  if (!live) return;
+  const int nbL = M.left(e), nbB = M.bottom(e);
+  const double divst = gs[GS_DIVST * SN + o];
+  T R[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    T d = B.Dc[i][0] * sF[le][v][j * N + 0];
+#pragma unroll
+    for (int k = 1; k < N; ++k) d = d + B.Dc[i][k] * sF[le][v][j * N + k];
+#pragma unroll
+    for (int k = 0; k < N; ++k) d = d + B.Dc[j][k] * sG[le][v][k * N + i];
+    d = d + B.dgL[i] * FN.ld((((size_t)nbL * 2 + 0) * 4 + v) * N + j);
+    d = d + B.dgR[i] * FN.ld((((size_t)e * 2 + 0) * 4 + v) * N + j);
+    d = d + B.dgL[j] * FN.ld((((size_t)nbB * 2 + 1) * 4 + v) * N + i);
+    d = d + B.dgR[j] * FN.ld((((size_t)e * 2 + 1) * 4 + v) * N + i);
+    d = d - th.qc[v] * divst;
+    R[v] = -(d * ij);
+  }
+  if (MODE == MODE_RESID) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      double r = val(R[v]);
+      if (tt.qcn) {
+        double acc = tt.a0dt * val(th.qc[v]) + tt.a1dt * tt.qcn[v * SN + o];
+        if (tt.qcnm1) acc += tt.a2dt * tt.qcnm1[v * SN + o];
+        r -= acc;
+      }
+      out[v * SN + o] = r;
+    }
+  } else {
+    double qv[4], wv[4], gm[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { qv[v] = val(q[v]); wv[v] = tan_(q[v]); }
+    gamma_m_apply(qv, wv, gs[GS_UG * SN + o], gs[GS_VG * SN + o], gas, jt.inv_dtau, jt.a0_dt, gm);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[v * SN + o] = gm[v] - tan_(R[v]);
+  }
+}
+
+}  // namespace fr

@@ -1,0 +1,413 @@
+// fr_precond.cu -- element block-Jacobi preconditioner for the Newton operator
+//   A = Gamma/dtau + (a0/dt) M - dR/dq^p        (Eq. unsteady_pre_discretized_3)
+// Build:  B_e = Gamma_e/dtau + (a0/dt) M_e - dR_e/dq_e  (neighbour states frozen),
+//         exact by forward mode, one CTA per element, 8 tangent directions in flight.
+// Factor: power-of-two row/column equilibration, in-place Gauss-Jordan inversion with
+//         partial pivoting in FP64 or FP32; stored transposed, scaled, in FP64, FP32 or
+//         BF16 (the FP32 inverse rounded).
+// Apply:  z_e = Dc (B~_e^-1 (Dr r_e)), FP64 in/out, FP32 accumulation for FP32/BF16.
+#include <cstdio>
+#include <cuda_bf16.h>
+#include "fr_internal.h"
+#include "fr_kernels.cuh"
+
+namespace fr {
+
+constexpr int BG = 8;  // tangent directions processed concurrently per element
+
+// Dynamic shared memory of one direction group (all Dual).
+template <int N> struct BlkSmem {
+  static constexpr int NP = N * N;
+  static constexpr int Q = 0, GLs = Q + 4 * NP, TQs = GLs + 8 * NP, TGs = TQs + 16 * N,
+                       FNs = TGs + 32 * N, QCs = FNs + 16 * N, Fs = QCs + 16 * N,
+                       Gs = Fs + 4 * NP, SIZE = Gs + 4 * NP;
+};
+
+template <int N>
+__global__ void __launch_bounds__(BG * N * N)
+k_block(const double* __restrict__ q, Mesh M, Basis B, Gas gas, const double* __restrict__ gs,
+        const double* __restrict__ gf, const double* __restrict__ tqv,
+        const double* __restrict__ tgv, double inv_dtau, double a0_dt,
+        double* __restrict__ Bout) {
+  constexpr int NP = N * N, BS = 4 * NP;
+  using L = BlkSmem<N>;
+  extern __shared__ Dual smem_dual[];
+  const int e = blockIdx.x;
+  const int grp = threadIdx.x / NP, pt = threadIdx.x % NP;
+  const int i = pt % N, j = pt / N;
+  Dual* S = smem_dual + grp * L::SIZE;
+  Dual* sq = S + L::Q;     // [4][NP]
+  Dual* sg = S + L::GLs;   // [8][NP]
+  Dual* stq = S + L::TQs;  // [4 faces][4][N]
+  Dual* stg = S + L::TGs;  // [4 faces][8][N]
+  Dual* sfn = S + L::FNs;  // [4 faces][4][N]
+  Dual* sqc = S + L::QCs;  // [4 faces][4][N]
+  Dual* sF = S + L::Fs;    // [4][NP]
+  Dual* sG = S + L::Gs;    // [4][NP]
+  const size_t SN = (size_t)M.ne * NP;
+  const size_t FNs = (size_t)M.ne * 4 * N;
+  const size_t o = (size_t)e * NP + pt;
+  const int nbL = M.left(e), nbR = M.right(e), nbB = M.bottom(e), nbT = M.top(e);
+  double qv[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) qv[v] = q[v * SN + o];
+  const double sxx = gs[GS_SXX * SN + o], sxy = gs[GS_SXY * SN + o];
+  const double sex = gs[GS_SEX * SN + o], sey = gs[GS_SEY * SN + o];
+  const double stx = gs[GS_STX * SN + o], ste = gs[GS_STE * SN + o];
+  const double ij = gs[GS_INVJ * SN + o], divst = gs[GS_DIVST * SN + o];
+  const double ugp = gs[GS_UG * SN + o], vgp = gs[GS_VG * SN + o];
+
+  for (int d0 = 0; d0 < BS; d0 += BG) {
+    const int d = d0 + grp;
+    const bool act = d < BS;
+    // A: seeded state
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sq[v * NP + pt] = mk(qv[v], (v * NP + pt == d) ? 1.0 : 0.0);
+    __syncthreads();
+    // B: local gradients
+    if (gas.viscous) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        Dual dxi = B.D[i][0] * sq[v * NP + j * N];
+        Dual deta = B.D[j][0] * sq[v * NP + i];
+#pragma unroll
+        for (int k = 1; k < N; ++k) {
+          dxi = dxi + B.D[i][k] * sq[v * NP + j * N + k];
+          deta = deta + B.D[j][k] * sq[v * NP + k * N + i];
+        }
+        sg[v * NP + pt] = (sxx * dxi + sex * deta) * ij;
+        sg[(4 + v) * NP + pt] = (sxy * dxi + sey * deta) * ij;
+      }
+    }
+    __syncthreads();
+    // C: own traces
+    for (int t = pt; t < 4 * N; t += NP) {
+      const int f = t / N, s = t % N;
+      const double* w = (f == FACE_L || f == FACE_B) ? B.lL : B.lR;
+      const bool row = (f == FACE_L || f == FACE_R);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        Dual acc = w[0] * sq[c * NP + (row ? s * N : s)];
+#pragma unroll
+        for (int k = 1; k < N; ++k) acc = acc + w[k] * sq[c * NP + (row ? s * N + k : k * N + s)];
+        stq[(f * 4 + c) * N + s] = acc;
+      }
+      if (gas.viscous) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          Dual acc = w[0] * sg[c * NP + (row ? s * N : s)];
+#pragma unroll
+          for (int k = 1; k < N; ++k) acc = acc + w[k] * sg[c * NP + (row ? s * N + k : k * N + s)];
+          stg[(f * 8 + c) * N + s] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    // D: common fluxes on the 4 faces of e, neighbour traces frozen (tangent 0); the
+    //    geometry is that of the owning ('-') element, as in the residual.
+    for (int t = pt; t < 4 * N; t += NP) {
+      const int f = t / N, s = t % N;
+      Dual qm[4], qp[4], gm[8], gp[8];
+      int own_m;           // element owning the face (its R or T face)
+      int fo, fother, other;
+      if (f == FACE_R || f == FACE_T) { own_m = e; fo = f; other = (f == FACE_R) ? nbR : nbT; fother = (f == FACE_R) ? FACE_L : FACE_B; }
+      else { own_m = (f == FACE_L) ? nbL : nbB; fo = (f == FACE_L) ? FACE_R : FACE_T; other = e; fother = f; }
+      const bool e_minus = (own_m == e) && (f == FACE_R || f == FACE_T);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const Dual mine = stq[(f * 4 + v) * N + s];
+        const Dual theirs = e_minus ? mk(tqv[(((size_t)other * 4 + fother) * 4 + v) * N + s], 0.0)
+                                    : mk(tqv[(((size_t)own_m * 4 + fo) * 4 + v) * N + s], 0.0);
+        qm[v] = e_minus ? mine : theirs;
+        qp[v] = e_minus ? theirs : mine;
+      }
+      if (gas.viscous) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const Dual mine = stg[(f * 8 + c) * N + s];
+          const Dual theirs = e_minus ? mk(tgv[(((size_t)other * 4 + fother) * 8 + c) * N + s], 0.0)
+                                      : mk(tgv[(((size_t)own_m * 4 + fo) * 8 + c) * N + s], 0.0);
+          gm[c] = e_minus ? mine : theirs;
+          gp[c] = e_minus ? theirs : mine;
+        }
+      }
+      const size_t om = ((size_t)own_m * 4 + fo) * N + s;
+      const size_t op = ((size_t)other * 4 + fother) * N + s;
+      Dual fnum[4], qcom[4];
+      face_common(qm, qp, gm, gp, gf[GF_SX * FNs + om], gf[GF_SY * FNs + om], gf[GF_UG * FNs + om],
+                  gf[GF_VG * FNs + om], gf[GF_J * FNs + om], gf[GF_J * FNs + op], gas, B.dgR_end,
+                  fnum, qcom);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { sfn[(f * 4 + v) * N + s] = fnum[v]; sqc[(f * 4 + v) * N + s] = qcom[v]; }
+    }
+    __syncthreads();
+    // E: element part at each solution point
+    Dual qd[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qd[v] = sq[v * NP + pt];
+    Thermo<Dual> th;
+    thermo(qd, gas, th);
+    Dual fx[4], gy[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { fx[v] = th.f[v]; gy[v] = th.g[v]; }
+    if (gas.viscous) {
+      Dual qx[4], qy[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { qx[v] = sg[v * NP + pt]; qy[v] = sg[(4 + v) * NP + pt]; }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int s = (f < 2) ? j : i;
+        const double w = (f == FACE_L) ? B.dgL[i] : (f == FACE_R) ? B.dgR[i]
+                       : (f == FACE_B) ? B.dgL[j] : B.dgR[j];
+        const size_t of = ((size_t)e * 4 + f) * N + s;
+        const double sx = gf[GF_SX * FNs + of] * w * ij, sy = gf[GF_SY * FNs + of] * w * ij;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const Dual jump = sqc[(f * 4 + v) * N + s] - stq[(f * 4 + v) * N + s];
+          qx[v] = qx[v] + jump * sx;
+          qy[v] = qy[v] + jump * sy;
+        }
+      }
+      Dual fv[4], gv[4];
+      neg_viscous_flux(qd, qx, qy, gas, fv, gv);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { fx[v] = fx[v] + fv[v]; gy[v] = gy[v] + gv[v]; }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      sF[v * NP + pt] = sxx * fx[v] + sxy * gy[v] + stx * th.qc[v];
+      sG[v * NP + pt] = sex * fx[v] + sey * gy[v] + ste * th.qc[v];
+    }
+    __syncthreads();
+    if (act) {
+      double wt[4], gmv[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) wt[v] = qd[v].d;
+      gamma_m_apply(qv, wt, ugp, vgp, gas, inv_dtau, a0_dt, gmv);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        Dual dv = B.Dc[i][0] * sF[v * NP + j * N];
+#pragma unroll
+        for (int k = 1; k < N; ++k) dv = dv + B.Dc[i][k] * sF[v * NP + j * N + k];
+#pragma unroll
+        for (int k = 0; k < N; ++k) dv = dv + B.Dc[j][k] * sG[v * NP + k * N + i];
+        dv = dv + B.dgL[i] * sfn[(FACE_L * 4 + v) * N + j];
+        dv = dv + B.dgR[i] * sfn[(FACE_R * 4 + v) * N + j];
+        dv = dv + B.dgL[j] * sfn[(FACE_B * 4 + v) * N + i];
+        dv = dv + B.dgR[j] * sfn[(FACE_T * 4 + v) * N + i];
+        dv = dv - th.qc[v] * divst;
+        const double dR = -(dv.d * ij);
+        Bout[((size_t)e * BS + v * NP + pt) * BS + d] = gmv[v] - dR;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ factor
+template <class W> __device__ __forceinline__ W wabs(W x) { return x < 0 ? -x : x; }
+
+// In-place Gauss-Jordan inversion with partial (row) pivoting of the equilibrated block,
+// one CTA per element; writes the transposed scaled inverse and the scales.
+template <class W, class S>
+__global__ void k_factor(const double* __restrict__ Bin, int bs, S* __restrict__ Aout,
+                         float* __restrict__ Dr, float* __restrict__ Dc, int* __restrict__ info) {
+  extern __shared__ unsigned char smraw[];
+  W* A = reinterpret_cast<W*>(smraw);               // [bs][bs] row-major
+  W* col = A + bs * bs;                             // [bs]
+  float* dr = reinterpret_cast<float*>(col + bs);   // [bs]
+  float* dc = dr + bs;                              // [bs]
+  int* perm = reinterpret_cast<int*>(dc + bs);      // [bs]
+  __shared__ int s_piv;
+  __shared__ int s_bad;
+  const int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const double* Be = Bin + (size_t)e * bs * bs;
+  if (tid == 0) s_bad = 0;
+  // row scales: 2^-round(log2(max |B_ij|)) over the row
+  for (int r = tid; r < bs; r += nt) {
+    double m = 0.0;
+    for (int c2 = 0; c2 < bs; ++c2) m = fmax(m, fabs(Be[(size_t)r * bs + c2]));
+    int ex = 0;
+    if (m > 0.0) frexp(m, &ex);
+    dr[r] = m > 0.0 ? ldexpf(1.0f, -ex) : 1.0f;
+  }
+  __syncthreads();
+  for (int c2 = tid; c2 < bs; c2 += nt) {
+    double m = 0.0;
+    for (int r = 0; r < bs; ++r) m = fmax(m, fabs(Be[(size_t)r * bs + c2]) * (double)dr[r]);
+    int ex = 0;
+    if (m > 0.0) frexp(m, &ex);
+    dc[c2] = m > 0.0 ? ldexpf(1.0f, -ex) : 1.0f;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < bs * bs; idx += nt) {
+    const int r = idx / bs, c2 = idx % bs;
+    A[idx] = (W)(Be[idx] * (double)dr[r] * (double)dc[c2]);
+  }
+  __syncthreads();
+  for (int k = 0; k < bs; ++k) {
+    if (tid < 32) {  // pivot search in column k, rows k..bs-1 (first max wins)
+      W best = (W)-1;
+      int bi = k;
+      for (int r = k + tid; r < bs; r += 32) {
+        const W a = wabs(A[r * bs + k]);
+        if (a > best) { best = a; bi = r; }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const W ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) { s_piv = bi; perm[k] = bi; if (best == (W)0) s_bad = 1; }
+    }
+    __syncthreads();
+    const int pr = s_piv;
+    if (pr != k)
+      for (int c2 = tid; c2 < bs; c2 += nt) { const W t = A[k * bs + c2]; A[k * bs + c2] = A[pr * bs + c2]; A[pr * bs + c2] = t; }
+    __syncthreads();
+    const W piv = A[k * bs + k];
+    const W rp = piv != (W)0 ? (W)1 / piv : (W)0;
+    for (int r = tid; r < bs; r += nt) col[r] = A[r * bs + k];
+    __syncthreads();
+    for (int c2 = tid; c2 < bs; c2 += nt) A[k * bs + c2] = (c2 == k ? (W)1 : A[k * bs + c2]) * rp;
+    __syncthreads();
+    for (int idx = tid; idx < bs * bs; idx += nt) {
+      const int r = idx / bs, c2 = idx % bs;
+      if (r == k) continue;
+      const W f = col[r];
+      const W akc = A[k * bs + c2];
+      A[idx] = (c2 == k ? (W)0 : A[idx]) - f * akc;
+    }
+    __syncthreads();
+  }
+  // undo the column interchanges in reverse order
+  for (int k = bs - 1; k >= 0; --k) {
+    const int pr = perm[k];
+    if (pr != k)
+      for (int r = tid; r < bs; r += nt) { const W t = A[r * bs + k]; A[r * bs + k] = A[r * bs + pr]; A[r * bs + pr] = t; }
+    __syncthreads();
+  }
+  // inverse of Dr B Dc is A; store A transposed: Aout[col][row]
+  S* Ae = Aout + (size_t)e * bs * bs;
+  for (int idx = tid; idx < bs * bs; idx += nt) {
+    const int r = idx / bs, c2 = idx % bs;
+    Ae[(size_t)c2 * bs + r] = (S)A[idx];
+  }
+  for (int r = tid; r < bs; r += nt) { Dr[(size_t)e * bs + r] = dr[r]; Dc[(size_t)e * bs + r] = dc[r]; }
+  if (tid == 0) info[e] = s_bad;
+}
+
+template <class S> __device__ __forceinline__ float to_f(S x) { return (float)x; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// z_e = Dc (A^T_stored (Dr r_e)); one CTA per element, thread per row.
+template <class S, class Acc>
+__global__ void k_apply(const S* __restrict__ AT, const float* __restrict__ Dr,
+                        const float* __restrict__ Dc, const double* __restrict__ r, int ne,
+                        int np2, double* __restrict__ z) {
+  extern __shared__ unsigned char smraw[];
+  Acc* x = reinterpret_cast<Acc*>(smraw);
+  const int e = blockIdx.x, bs = 4 * np2, row = threadIdx.x;
+  const size_t SN = (size_t)ne * np2;
+  if (row < bs) {
+    const int v = row / np2, pt = row % np2;
+    x[row] = (Acc)(r[v * SN + (size_t)e * np2 + pt] * (double)Dr[(size_t)e * bs + row]);
+  }
+  __syncthreads();
+  if (row >= bs) return;
+  const S* A = AT + (size_t)e * bs * bs;
+  Acc acc = 0;
+  for (int c2 = 0; c2 < bs; ++c2) acc += (Acc)to_f(A[(size_t)c2 * bs + row]) * x[c2];
+  const int v = row / np2, pt = row % np2;
+  z[v * SN + (size_t)e * np2 + pt] = (double)acc * (double)Dc[(size_t)e * bs + row];
+}
+template <>
+__global__ void k_apply<double, double>(const double* __restrict__ AT, const float* __restrict__ Dr,
+                                        const float* __restrict__ Dc, const double* __restrict__ r,
+                                        int ne, int np2, double* __restrict__ z) {
+  extern __shared__ unsigned char smraw[];
+  double* x = reinterpret_cast<double*>(smraw);
+  const int e = blockIdx.x, bs = 4 * np2, row = threadIdx.x;
+  const size_t SN = (size_t)ne * np2;
+  if (row < bs) {
+    const int v = row / np2, pt = row % np2;
+    x[row] = r[v * SN + (size_t)e * np2 + pt] * (double)Dr[(size_t)e * bs + row];
+  }
+  __syncthreads();
+  if (row >= bs) return;
+  const double* A = AT + (size_t)e * bs * bs;
+  double acc = 0;
+  for (int c2 = 0; c2 < bs; ++c2) acc = fma(A[(size_t)c2 * bs + row], x[c2], acc);
+  const int v = row / np2, pt = row % np2;
+  z[v * SN + (size_t)e * np2 + pt] = acc * (double)Dc[(size_t)e * bs + row];
+}
+
+}  // namespace fr
+
+namespace frk {
+using namespace fr;
+
+template <int N>
+static int block_build_n(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s) {
+  // value traces of every element (neighbour data of the blocks)
+  constexpr int EPB = Tile<N>::EPB, TH = Tile<N>::THREADS;
+  const int nblk = (c->ne + EPB - 1) / EPB;
+  k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(q)}, c->ne, c->basis,
+                                         c->gas, c->gs, Buf<double>{c->gl}, Buf<double>{c->tq},
+                                         Buf<double>{c->tg});
+  FR_LAUNCH_CHECK(c);
+  const size_t smem = (size_t)BG * BlkSmem<N>::SIZE * sizeof(Dual);
+  FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_block<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_block<N><<<c->ne, BG * N * N, smem, s>>>(q, c->mesh, c->basis, c->gas, c->gs, c->gf, c->tq,
+                                             c->tg, inv_dtau, a0_dt, c->B64);
+  FR_LAUNCH_CHECK(c);
+  return FR_OK;
+}
+
+static int factor(fr_ctx* c, cudaStream_t s) {
+  const int bs = c->bsz;
+  const int nt = 256;
+  if (c->cfg.prec_dtype == FR_PREC_FP64) {
+    const size_t smem = (size_t)bs * bs * 8 + bs * 8 + bs * 4 * 2 + bs * 4;
+    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_factor<double, double><<<c->ne, nt, smem, s>>>(c->B64, bs, (double*)c->Binv, c->Dr, c->Dc, c->info);
+  } else if (c->cfg.prec_dtype == FR_PREC_FP32) {
+    const size_t smem = (size_t)bs * bs * 4 + bs * 4 + bs * 4 * 2 + bs * 4;
+    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_factor<float, float><<<c->ne, nt, smem, s>>>(c->B64, bs, (float*)c->Binv, c->Dr, c->Dc, c->info);
+  } else {
+    const size_t smem = (size_t)bs * bs * 4 + bs * 4 + bs * 4 * 2 + bs * 4;
+    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<float, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_factor<float, __nv_bfloat16><<<c->ne, nt, smem, s>>>(c->B64, bs, (__nv_bfloat16*)c->Binv, c->Dr, c->Dc, c->info);
+  }
+  FR_LAUNCH_CHECK(c);
+  return FR_OK;
+}
+
+int block_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s) {
+  int rc;
+  switch (c->n) {
+    case 2: rc = block_build_n<2>(c, q, inv_dtau, a0_dt, s); break;
+    case 3: rc = block_build_n<3>(c, q, inv_dtau, a0_dt, s); break;
+    case 4: rc = block_build_n<4>(c, q, inv_dtau, a0_dt, s); break;
+    case 5: rc = block_build_n<5>(c, q, inv_dtau, a0_dt, s); break;
+    default: return FR_ERR_ARG;
+  }
+  if (rc != FR_OK) return rc;
+  return factor(c, s);
+}
+
+int block_apply(fr_ctx* c, const double* r, double* z, cudaStream_t s) {
+  const int bs = c->bsz;
+  const int nt = (bs + 31) / 32 * 32;
+  if (c->cfg.prec_dtype == FR_PREC_FP64)
+    k_apply<double, double><<<c->ne, nt, bs * 8, s>>>((const double*)c->Binv, c->Dr, c->Dc, r, c->ne, c->np2, z);
+  else if (c->cfg.prec_dtype == FR_PREC_FP32)
+    k_apply<float, float><<<c->ne, nt, bs * 4, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->ne, c->np2, z);
+  else
+    k_apply<__nv_bfloat16, float><<<c->ne, nt, bs * 4, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->ne, c->np2, z);
+  FR_LAUNCH_CHECK(c);
+  return FR_OK;
+}
+
+}  // namespace frk

@@ -1,0 +1,266 @@
+"""Thin ctypes binding of the C-ABI library ``libfr.so`` (declared in ``include/fr.h``).
+
+Argument marshalling only: every step of the path runs in the library's CUDA kernels.
+Device arrays are torch CUDA tensors (float64, contiguous, layout [4][Ne][n][n] for
+solution vectors); the stream is torch's current CUDA stream unless one is given.
+The module raises if the library is missing or fails to load: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfr.so")
+
+FR_OK = 0
+ERRORS = {-1: "FR_ERR_ARG", -2: "FR_ERR_CUDA", -3: "FR_ERR_NONFINITE",
+          -4: "FR_ERR_NOT_CONVERGED", -5: "FR_ERR_TIMEOUT"}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+MAX_NEWTON = 64
+BDF2 = (1.5, -2.0, 0.5)
+BDF1 = (1.0, -1.0, 0.0)
+
+
+class FrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("prandtl", ctypes.c_double),
+                ("mach", ctypes.c_double), ("re", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("eps_floor", ctypes.c_double),
+                ("prec_dtype", ctypes.c_int),
+                ("restart", ctypes.c_int), ("maxit_lin", ctypes.c_int),
+                ("maxit_newton", ctypes.c_int), ("lag", ctypes.c_int),
+                ("tol_res", ctypes.c_double), ("tol_pseudo", ctypes.c_double),
+                ("dtau0", ctypes.c_double), ("dtau_min", ctypes.c_double),
+                ("dtau_max", ctypes.c_double), ("r_ser", ctypes.c_double),
+                ("dtau_unsteady", ctypes.c_double), ("gmres_side", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("newton_iterations", ctypes.c_int),
+                ("converged", ctypes.c_int),
+                ("gmres_iterations", ctypes.c_int * MAX_NEWTON),
+                ("res_history", ctypes.c_double * (MAX_NEWTON + 1)),
+                ("dtau_history", ctypes.c_double * (MAX_NEWTON + 1)),
+                ("block_builds", ctypes.c_int)]
+
+    def summary(self) -> dict:
+        n = self.newton_iterations
+        return {"newton_iterations": n, "converged": bool(self.converged),
+                "gmres_iterations": list(self.gmres_iterations[:n]),
+                "res_history": list(self.res_history[: n + 1]),
+                "dtau_history": list(self.dtau_history[: n + 1]),
+                "block_builds": self.block_builds}
+
+
+_lib = None
+
+_D = ctypes.c_double
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = {
+    "fr_default_config": (None, [ctypes.POINTER(_Config)]),
+    "fr_create": (_I, [ctypes.POINTER(_Config), ctypes.POINTER(_P)]),
+    "fr_destroy": (None, [_P]),
+    "fr_set_mesh": (_I, [_P, _I, _I, _I, _I]),
+    "fr_update_mesh": (_I, [_P, _P, _P, _P]),
+    "fr_residual": (_I, [_P, _P, _P, _P]),
+    "fr_bdf_rhs": (_I, [_P, _P, _P, _P, _D, _D, _D, _D, _P, _P]),
+    "fr_conservative": (_I, [_P, _P, _P, _P]),
+    "fr_jvp": (_I, [_P, _P, _P, _D, _D, _P, _P]),
+    "fr_precond_build": (_I, [_P, _P, _D, _D, _P]),
+    "fr_precond_blocks": (_I, [_P, _P, _P]),
+    "fr_precond_apply": (_I, [_P, _P, _P, _P]),
+    "fr_gmres": (_I, [_P, _P, _P, _D, _D, _P, ctypes.POINTER(_I), _P]),
+    "fr_bdf2_step": (_I, [_P, _P, _P, _P, _D, _D, _D, _D, ctypes.POINTER(Stats), _P]),
+    "fr_ptc_solve": (_I, [_P, _P, ctypes.POINTER(Stats), _P]),
+    "fr_residual_norms": (_I, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
+    "fr_num_dof": (ctypes.c_size_t, [_P]),
+    "fr_block_size": (_I, [_P]),
+    "fr_kernel_launches": (ctypes.c_longlong, [_P]),
+    "fr_last_error": (ctypes.c_char_p, [_P]),
+    "fr_version": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the library (building it first if it is absent or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    _build.build()
+    if not os.path.exists(path):
+        raise FrError(-1, f"{path} missing: the CUDA library was not built")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+@dataclasses.dataclass
+class Config:
+    p: int = 3
+    mach: float = 0.05
+    re: float = 0.0
+    kappa: float = 1.0
+    gamma: float = 1.4
+    prandtl: float = 0.72
+    eps_floor: float = 1e-8
+    prec: str = "fp64"
+    restart: int = 30
+    maxit_lin: int = 100
+    maxit_newton: int = 20
+    lag: int = 2
+    tol_res: float = 1e-6
+    tol_pseudo: float = 1e-8
+    dtau0: float = 0.01
+    dtau_min: float = 0.01
+    dtau_max: float = 1e20
+    r_ser: float = 2.0
+    dtau_unsteady: float = 1e20
+    gmres_side: str = "left"
+
+    def to_c(self) -> _Config:
+        c = _Config()
+        load().fr_default_config(ctypes.byref(c))
+        for f in dataclasses.fields(self):
+            if f.name == "prec":
+                c.prec_dtype = PREC[self.prec]
+            elif f.name == "gmres_side":
+                c.gmres_side = {"left": 0, "right": 1}[self.gmres_side]
+            else:
+                setattr(c, f.name, getattr(self, f.name))
+        return c
+
+
+class Solver:
+    """One library context: a mesh of nx-by-ny periodic bilinear quads at degree p."""
+
+    def __init__(self, cfg: Config, nx: int, ny: int):
+        self.lib = load()
+        self.cfg = cfg
+        self._cc = cfg.to_c()
+        h = ctypes.c_void_p()
+        self._check(self.lib.fr_create(ctypes.byref(self._cc), ctypes.byref(h)), None)
+        self.ctx = h
+        self.nx, self.ny = nx, ny
+        self._check(self.lib.fr_set_mesh(self.ctx, nx, ny, 1, 1))
+        self.n = cfg.p + 1
+        self.ne = nx * ny
+        self.ndof = int(self.lib.fr_num_dof(self.ctx))
+        self.block_size = int(self.lib.fr_block_size(self.ctx))
+
+    def _check(self, rc, ctx="self"):
+        if rc != FR_OK:
+            msg = self.lib.fr_last_error(self.ctx if ctx == "self" else None)
+            raise FrError(rc, (msg or b"").decode())
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.fr_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (4, self.ne, self.n, self.n)
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.lib.fr_kernel_launches(self.ctx))
+
+    # -- calls of include/fr.h
+    def update_mesh(self, corners, vel, stream=None):
+        self._check(self.lib.fr_update_mesh(self.ctx, _ptr(corners), _ptr(vel), _stream(stream)))
+
+    def residual(self, q, out, stream=None):
+        self._check(self.lib.fr_residual(self.ctx, _ptr(q), _ptr(out), _stream(stream)))
+        return out
+
+    def bdf_rhs(self, q, qc_n, qc_nm1, coeffs, dt, out, stream=None):
+        a0, a1, a2 = coeffs
+        pnm1 = _ptr(qc_nm1) if qc_nm1 is not None else None
+        self._check(self.lib.fr_bdf_rhs(self.ctx, _ptr(q), _ptr(qc_n), pnm1, a0, a1, a2, dt,
+                                         _ptr(out), _stream(stream)))
+        return out
+
+    def conservative(self, q, out, stream=None):
+        self._check(self.lib.fr_conservative(self.ctx, _ptr(q), _ptr(out), _stream(stream)))
+        return out
+
+    def jvp(self, q, v, out, inv_dtau=0.0, a0_dt=0.0, stream=None):
+        self._check(self.lib.fr_jvp(self.ctx, _ptr(q), _ptr(v), inv_dtau, a0_dt, _ptr(out),
+                                    _stream(stream)))
+        return out
+
+    def precond_build(self, q, inv_dtau=0.0, a0_dt=0.0, stream=None):
+        self._check(self.lib.fr_precond_build(self.ctx, _ptr(q), inv_dtau, a0_dt, _stream(stream)))
+
+    def precond_blocks(self, out, stream=None):
+        self._check(self.lib.fr_precond_blocks(self.ctx, _ptr(out), _stream(stream)))
+        return out
+
+    def precond_apply(self, r, out, stream=None):
+        self._check(self.lib.fr_precond_apply(self.ctx, _ptr(r), _ptr(out), _stream(stream)))
+        return out
+
+    def gmres(self, q, b, x, inv_dtau=0.0, a0_dt=0.0, stream=None) -> int:
+        its = ctypes.c_int(0)
+        self._check(self.lib.fr_gmres(self.ctx, _ptr(q), _ptr(b), inv_dtau, a0_dt, _ptr(x),
+                                      ctypes.byref(its), _stream(stream)))
+        return its.value
+
+    def bdf2_step(self, q, qc_n, qc_nm1, dt, coeffs=BDF2, stream=None, allow_unconverged=False):
+        st = Stats()
+        a0, a1, a2 = coeffs
+        pnm1 = _ptr(qc_nm1) if qc_nm1 is not None else None
+        rc = self.lib.fr_bdf2_step(self.ctx, _ptr(q), _ptr(qc_n), pnm1, a0, a1, a2, dt,
+                                   ctypes.byref(st), _stream(stream))
+        if not (allow_unconverged and rc == -4):
+            self._check(rc)
+        return st
+
+    def ptc_solve(self, q, stream=None, allow_unconverged=False):
+        st = Stats()
+        rc = self.lib.fr_ptc_solve(self.ctx, _ptr(q), ctypes.byref(st), _stream(stream))
+        if not (allow_unconverged and rc == -4):
+            self._check(rc)
+        return st
+
+    def residual_norms(self, r, stream=None):
+        m, a = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.fr_residual_norms(self.ctx, _ptr(r), ctypes.byref(m), ctypes.byref(a),
+                                               _stream(stream)))
+        return m.value, a.value

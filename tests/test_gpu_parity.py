@@ -1,0 +1,271 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU oracle on the same
+seeded inputs: geometry-dependent residual, BDF right-hand side, exact JVP, element
+blocks, block apply, GMRES and whole BDF2 / PTC Newton steps.  Sizes span several
+thread blocks with ragged tails; full workload sizes are checked too."""
+import numpy as np
+import pytest
+
+from gpu_helpers import (BLK_TOL, JVP_TOL, RES_TOL, block_errors, case, jvp_errors,
+                         oracle_problem, residual_errors, solver_for, to_dev, to_host)
+from oracle import solver as sv
+from paper_1903_06304_gb300 import inputs as inp
+
+pytestmark = pytest.mark.gpu
+
+# (nx, ny, p, mach, re, kappa, deforming): ragged tails (Ne not a multiple of the
+# elements per block: 14 at p=2, 8 at p=3, 5 at p=4), Euler and Navier-Stokes, static and
+# deforming, M from 0.01 to 0.3, kappa = 0 (vortex reading) and 1.
+CASES = [
+    (4, 3, 1, 0.1, 0.0, 1.0, False),
+    (5, 3, 2, 0.05, 10.0, 1.0, True),
+    (6, 5, 3, 0.01, 10.0, 1.0, True),
+    (3, 4, 4, 0.05, 10.0, 0.0, True),
+    (7, 5, 3, 0.3, 0.0, 1.0, False),
+    (9, 7, 2, 0.1, 100.0, 1.0, True),
+    (2, 2, 3, 0.05, 10.0, 1.0, True),
+]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.mark.parametrize("cfg", CASES)
+def test_residual_parity(torch, cfg):
+    nx, ny, p, mach, re, kappa, deforming = cfg
+    c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
+    prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
+    S = solver_for(c, v, nx, ny, p, mach, re, kappa)
+    out = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+    S.residual(to_dev(q), out)
+    err = residual_errors(to_host(out), prob.R(q), q, prob.mesh, p, prob.gas)
+    assert np.all(err <= RES_TOL), err
+
+
+@pytest.mark.parametrize("cfg", CASES[:4])
+def test_bdf_rhs_parity(torch, cfg):
+    nx, ny, p, mach, re, kappa, deforming = cfg
+    c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
+    prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
+    qn = inp.random_perturbation(q, 21, 0.05, mach)
+    qnm1 = inp.random_perturbation(q, 22, 0.05, mach)
+    qcn, qcnm1 = prob.qc(qn), prob.qc(qnm1)
+    dt = 0.01
+    want = sv.time_rhs(prob, q, qcn, qcnm1, dt, sv.BDF2)
+    S = solver_for(c, v, nx, ny, p, mach, re, kappa)
+    out = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+    S.bdf_rhs(to_dev(q), to_dev(qcn), to_dev(qcnm1), (1.5, -2.0, 0.5), dt, out)
+    got = to_host(out)
+    # the time term adds terms of size |a_i q^c_i| / dt to each equation's scale
+    from oracle import scale as sc
+    s = sc.residual_scale(q, prob.mesh, p, prob.gas)
+    tscale = (1.5 * np.abs(prob.qc(q)) + 2.0 * np.abs(qcn) + 0.5 * np.abs(qcnm1)).max(axis=(1, 2, 3)) / dt
+    err = np.abs(got - want).max(axis=(1, 2, 3))
+    assert np.all(err <= RES_TOL * (s + tscale)), (err, s, tscale)
+    qc = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+    S.conservative(to_dev(q), qc)
+    np.testing.assert_allclose(to_host(qc), prob.qc(q), rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("cfg", CASES)
+def test_jvp_parity(torch, cfg):
+    nx, ny, p, mach, re, kappa, deforming = cfg
+    c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
+    prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
+    w = inp.random_vector(q.shape, 9)
+    w[0] *= prob.gas.R * 1e-2
+    S = solver_for(c, v, nx, ny, p, mach, re, kappa)
+    out = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+    for inv_dtau, a0_dt in ((0.0, 0.0), (0.5, 150.0), (1e-20, 150.0)):
+        want = sv.apply_A(prob, q, w, inv_dtau, a0_dt)
+        S.jvp(to_dev(q), to_dev(w), out, inv_dtau, a0_dt)
+        err = jvp_errors(to_host(out), want)
+        assert np.all(err <= JVP_TOL), (inv_dtau, a0_dt, err)
+
+
+def test_jvp_of_zero_vector_is_zero(torch):
+    c, v, q = case(5, 4, 3, 0.05, 10.0, 1.0, True)
+    S = solver_for(c, v, 5, 4, 3, 0.05, 10.0, 1.0)
+    out = torch.full(S.shape, 7.0, dtype=torch.float64, device="cuda:0")
+    S.jvp(to_dev(q), torch.zeros(S.shape, dtype=torch.float64, device="cuda:0"), out, 0.3, 150.0)
+    assert np.all(to_host(out) == 0.0)
+
+
+@pytest.mark.parametrize("cfg", [CASES[i] for i in (0, 1, 2, 3, 6)])
+def test_block_parity(torch, cfg):
+    nx, ny, p, mach, re, kappa, deforming = cfg
+    c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
+    prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
+    inv_dtau, a0_dt = 0.5, 150.0
+    want = sv.block_jacobian(prob, q, inv_dtau, a0_dt)
+    S = solver_for(c, v, nx, ny, p, mach, re, kappa)
+    S.precond_build(to_dev(q), inv_dtau, a0_dt)
+    B = torch.empty((nx * ny, S.block_size, S.block_size), dtype=torch.float64, device="cuda:0")
+    S.precond_blocks(B)
+    err = block_errors(to_host(B), want, (p + 1) ** 2)
+    assert np.all(err <= BLK_TOL), err
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-4), ("bf16", 1e-1)])
+def test_block_apply(torch, prec, tol):
+    """z_e = B_e^-1 r_e against numpy's inverse of the oracle blocks; FP32/BF16 storage
+    within their unit round-off times the block condition (equilibrated)."""
+    nx, ny, p, mach, re, kappa, deforming = 5, 3, 2, 0.05, 10.0, 1.0, True
+    c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
+    prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
+    Bo = sv.block_jacobian(prob, q, 0.0, 150.0)
+    r = inp.random_vector(q.shape, 11)
+    want = sv.block_apply(np.linalg.inv(Bo), r)
+    S = solver_for(c, v, nx, ny, p, mach, re, kappa, prec=prec)
+    S.precond_build(to_dev(q), 0.0, 150.0)
+    z = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+    S.precond_apply(to_dev(r), z)
+    got = to_host(z)
+    # residual of the block system in the oracle's FP64 blocks, per element
+    ne, bs = Bo.shape[0], Bo.shape[1]
+    ge = got.transpose(1, 0, 2, 3).reshape(ne, bs)
+    re_ = r.transpose(1, 0, 2, 3).reshape(ne, bs)
+    rel = np.linalg.norm(np.einsum("eab,eb->ea", Bo, ge) - re_, axis=1) / np.linalg.norm(re_, axis=1)
+    assert rel.max() <= tol, rel.max()
+    if prec == "fp64":
+        assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("side", ["left", "right"])
+def test_gmres_parity(torch, side):
+    nx, ny, p, mach, re, kappa, deforming = 4, 4, 2, 0.05, 10.0, 1.0, True
+    c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
+    prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
+    inv_dtau, a0_dt = 1e-20, 150.0
+    b = inp.random_vector(q.shape, 13)
+    Binv = np.linalg.inv(sv.block_jacobian(prob, q, inv_dtau, a0_dt))
+    P = lambda x: sv.block_apply(Binv, x)
+    want = sv.gmres(lambda x: sv.apply_A(prob, q, x, inv_dtau, a0_dt), b, P, 10, 1e-8, 200,
+                    side=side)
+    S = solver_for(c, v, nx, ny, p, mach, re, kappa, restart=10, maxit_lin=200, tol_res=1e-8,
+                   gmres_side=side)
+    qd = to_dev(q)
+    S.precond_build(qd, inv_dtau, a0_dt)
+    x = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+    its = S.gmres(qd, to_dev(b), x, inv_dtau, a0_dt)
+    assert its == want.iterations
+    got = to_host(x)
+    assert np.abs(got - want.x).max() <= 1e-9 * np.abs(want.x).max()
+    # and it solves the system to the tolerance, in the norm the side minimises
+    res = b - sv.apply_A(prob, q, got, inv_dtau, a0_dt)
+    if side == "left":
+        assert np.linalg.norm(P(res)) <= 1.01e-8 * np.linalg.norm(P(b))
+    else:
+        assert np.linalg.norm(res) <= 1.01e-8 * np.linalg.norm(b)
+
+
+def test_gmres_zero_rhs(torch):
+    c, v, q = case(3, 3, 2, 0.05, 10.0, 1.0, False)
+    S = solver_for(c, v, 3, 3, 2, 0.05, 10.0, 1.0)
+    qd = to_dev(q)
+    S.precond_build(qd, 0.0, 150.0)
+    x = torch.full(S.shape, 3.0, dtype=torch.float64, device="cuda:0")
+    assert S.gmres(qd, torch.zeros_like(x), x, 0.0, 150.0) == 0
+    assert np.all(to_host(x) == 0.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_bdf2_step_parity(torch, prec):
+    """One BDF2 step (BDF1 start) of the vortex: same Newton/GMRES iteration counts and
+    Res_m history as the oracle, final states equal to the Newton tolerance."""
+    w = inp.Workload("t", 4, 4, 2, 0.05, 10.0, 0.0, (0.0, 10.0, 0.0, 10.0), dt=0.01)
+    c, v, q = inp.make_case(w)
+    prob = oracle_problem(c, v, w.nx, w.ny, w.p, w.mach, w.re, w.kappa)
+    qc = prob.qc(q)
+    q1, st = sv.bdf2_step(prob, q, qc, qc, w.dt, coeffs=sv.BDF1, restart=30, tol_res=1e-6,
+                          maxit_lin=100, tol_pseudo=1e-8, maxit_newton=10, lag=2)
+    S = solver_for(c, v, w.nx, w.ny, w.p, w.mach, w.re, w.kappa, prec=prec, restart=30,
+                   tol_res=1e-6, maxit_lin=100, tol_pseudo=1e-8, maxit_newton=10, lag=2)
+    qd = to_dev(q)
+    qcd = to_dev(qc)
+    sg = S.bdf2_step(qd, qcd, qcd, w.dt, coeffs=(1.0, -1.0, 0.0)).summary()
+    assert sg["converged"] and st.converged
+    res_o = np.array(st.res_history)
+    res_g = np.array(sg["res_history"])
+    if prec == "fp64":
+        assert sg["newton_iterations"] == st.newton_iterations
+        assert sg["gmres_iterations"] == st.gmres_iterations
+        np.testing.assert_allclose(res_g[:2], res_o[:2], rtol=1e-9)
+    else:
+        assert abs(sg["newton_iterations"] - st.newton_iterations) <= 1
+    got = to_host(qd)
+    scale = np.abs(q1 - q).max(axis=(1, 2, 3))
+    assert np.all(np.abs(got - q1).max(axis=(1, 2, 3)) <= 1e-5 * scale)
+
+
+def test_ptc_parity(torch):
+    """Steady PTC with SER on the Gaussian bump: Res_m and dtau histories follow the oracle."""
+    w = inp.Workload("b", 4, 4, 2, 0.1, 0.0, 1.0, (0.0, 1.0, 0.0, 1.0), ic="bump", restart=20)
+    c, v, q = inp.make_case(w)
+    prob = oracle_problem(c, v, w.nx, w.ny, w.p, w.mach, w.re, w.kappa)
+    _, st = sv.ptc_solve(prob, q, maxit_newton=12, restart=20, tol_res=1e-6, tol_pseudo=1e-8)
+    S = solver_for(c, v, w.nx, w.ny, w.p, w.mach, w.re, w.kappa, restart=20, tol_res=1e-6,
+                   maxit_newton=12, tol_pseudo=1e-8, lag=1)
+    sg = S.ptc_solve(to_dev(q), allow_unconverged=True).summary()
+    n = min(len(sg["res_history"]), len(st.res_history))
+    np.testing.assert_allclose(sg["res_history"][:n], st.res_history[:n], rtol=1e-6)
+    np.testing.assert_allclose(sg["dtau_history"][:n], st.dtau_history[:n], rtol=1e-5)
+    assert sg["gmres_iterations"][:n - 1] == st.gmres_iterations[:n - 1]
+
+
+# ------------------------------------------------------------------ full workload sizes
+
+@pytest.mark.parametrize("w", [inp.NS_VORTEX_64, inp.NS_DEFORM_128], ids=lambda w: w.name)
+def test_full_size_residual_and_jvp(torch, w):
+    """At the benchmark's full sizes, in the bench's launch configuration: every residual
+    and JVP entry against the oracle (vectorised, so it finishes in seconds)."""
+    c, v, q = inp.make_case(w, t=0.13)
+    prob = oracle_problem(c, v, w.nx, w.ny, w.p, w.mach, w.re, w.kappa)
+    S = solver_for(c, v, w.nx, w.ny, w.p, w.mach, w.re, w.kappa)
+    qd = to_dev(q)
+    out = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+    S.residual(qd, out)
+    err = residual_errors(to_host(out), prob.R(q), q, prob.mesh, w.p, prob.gas)
+    assert np.all(err <= RES_TOL), err
+    x = inp.random_vector(q.shape, 5)
+    x[0] *= prob.gas.R * 1e-2
+    S.jvp(qd, to_dev(x), out, 1e-20, 1.5 / w.dt)
+    err = jvp_errors(to_host(out), sv.apply_A(prob, q, x, 1e-20, 1.5 / w.dt))
+    assert np.all(err <= JVP_TOL), err
+
+
+@pytest.mark.parametrize("w", [inp.NS_VORTEX_64, inp.NS_DEFORM_128], ids=lambda w: w.name)
+def test_full_size_blocks_sampled(torch, w):
+    """Blocks at full size, sampled: for a vector supported on a set of mutually distant
+    elements, the oracle's operator rows on those elements equal B_e w_e."""
+    c, v, q = inp.make_case(w, t=0.13)
+    prob = oracle_problem(c, v, w.nx, w.ny, w.p, w.mach, w.re, w.kappa)
+    S = solver_for(c, v, w.nx, w.ny, w.p, w.mach, w.re, w.kappa)
+    a0_dt = 1.5 / w.dt
+    S.precond_build(to_dev(q), 1e-20, a0_dt)
+    B = torch.empty((w.ne, S.block_size, S.block_size), dtype=torch.float64, device="cuda:0")
+    S.precond_blocks(B)
+    B = to_host(B)
+    rng = np.random.default_rng(17)
+    picks = [j * w.nx + i for j in range(1, w.ny, 7) for i in range(3 * (j % 2) + 1, w.nx, 7)]
+    picks = rng.choice(picks, size=min(24, len(picks)), replace=False)
+    x = np.zeros(q.shape)
+    for e in picks:
+        x[:, e] = rng.standard_normal(x[:, e].shape)
+    Ax = sv.apply_A(prob, q, x, 1e-20, a0_dt)
+    bs = S.block_size
+    for e in picks:
+        xe = x[:, e].reshape(bs)
+        want = Ax[:, e].reshape(bs)
+        got = B[e] @ xe
+        assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_invalid_mesh_rejected(torch):
+    from paper_1903_06304_gb300 import fr
+    with pytest.raises(fr.FrError):
+        fr.Solver(fr.Config(p=3), 1, 4)

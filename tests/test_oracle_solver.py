@@ -92,25 +92,37 @@ def test_gmres_matches_direct_solve_with_restarts():
     A = np.eye(N) * 4 + rng.standard_normal((N, N)) * 0.3
     b = rng.standard_normal(N)
     P = np.diag(1 / np.diag(A))
-    out = sv.gmres(lambda v: A @ v, b, lambda v: P @ v, 10, 1e-12, 500)
-    assert out.converged
+    for side in ("left", "right"):
+        out = sv.gmres(lambda v: A @ v, b, lambda v: P @ v, 10, 1e-12, 500, side=side)
+        assert out.converged
+        np.testing.assert_allclose(out.x, np.linalg.solve(A, b), atol=1e-10)
     np.testing.assert_allclose(out.x, np.linalg.solve(A, b), atol=1e-10)
 
 
-def test_gmres_minimal_residual_property():
-    """Without restart, after k steps the right-preconditioned GMRES residual is the
-    least-squares minimum over x in P K_k(A P, b) (library lstsq on an explicit basis)."""
+@pytest.mark.parametrize("side", ["left", "right"])
+def test_gmres_minimal_residual_property(side):
+    """Without restart, after k steps GMRES attains the least-squares minimum over its
+    Krylov space (library lstsq on an explicit basis): right preconditioning minimises
+    ||b - A x|| over x in P K_k(A P, b); left preconditioning minimises ||P (b - A x)||
+    over x in K_k(P A, P b)."""
     rng = np.random.default_rng(1)
     N, k = 40, 7
     A = np.eye(N) * 3 + rng.standard_normal((N, N)) * 0.5
     P = np.diag(1.0 + rng.uniform(0, 1, N))
     b = rng.standard_normal(N)
-    out = sv.gmres(lambda v: A @ v, b, lambda v: P @ v, 50, 0.0, k)
-    K = np.stack([np.linalg.matrix_power(A @ P, i) @ b for i in range(k)], axis=1)
-    Q, _ = np.linalg.qr(K)
-    y, *_ = np.linalg.lstsq(A @ P @ Q, b, rcond=None)
-    best = np.linalg.norm(b - A @ P @ Q @ y)
-    got = np.linalg.norm(b - A @ out.x)
+    out = sv.gmres(lambda v: A @ v, b, lambda v: P @ v, 50, 0.0, k, side=side)
+    if side == "right":
+        K = np.stack([np.linalg.matrix_power(A @ P, i) @ b for i in range(k)], axis=1)
+        Q, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(A @ P @ Q, b, rcond=None)
+        best = np.linalg.norm(b - A @ P @ Q @ y)
+        got = np.linalg.norm(b - A @ out.x)
+    else:
+        K = np.stack([np.linalg.matrix_power(P @ A, i) @ (P @ b) for i in range(k)], axis=1)
+        Q, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(P @ A @ Q, P @ b, rcond=None)
+        best = np.linalg.norm(P @ b - P @ A @ Q @ y)
+        got = np.linalg.norm(P @ (b - A @ out.x))
     assert out.iterations == k
     assert abs(got - best) <= 1e-10 * np.linalg.norm(b)
 
