@@ -1,0 +1,470 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 preconditioned FR/CPR implicit hot path.
+
+One step = one physical BDF2 step (Eq. unsteady_pre_discretized_3) of the isentropic
+vortex on the periodic [0,10]^2 box, 64x64 quads, p = 3 (262,144 DOF), M = 0.05,
+Re = 100 on the box length, dt = 0.01, driven to Res_m/Res_0 <= 1e-8 by the pseudo-time
+Newton loop: residual, exact forward-mode JVP, element block-Jacobi blocks (built,
+factored, applied), restarted GMRES with CGS2, Newton update.  Every step runs in the
+library's CUDA kernels behind the C ABI; inputs are resident in HBM when the timed
+region starts.
+
+value  = DOF advanced per second by BDF2 steps (GDOF/s) = N_dof * steps / time, summed
+         over ranks (replicas, weak scaling); sec_per_bdf2_step is its inverse per rank.
+e2e    = the same metric with host buffers: every step copies q^n, q^c,n, q^c,n-1 from
+         pinned host memory and q^n+1 back inside the timed region.
+roofline: the dominant kernel class (largest share of device time over a profiled
+         repetition of the timed steps): algorithmic flops (ALU-bound kernels, against the
+         FP64 or FP32 pipe peak) or algorithmic DRAM bytes (streaming kernels, against the
+         measured HBM copy bandwidth) over its CUDA-event duration.
+
+--impl reference times the CPU oracle (numpy, FP64) on a bounded sample of the same
+workload (the 16x16 sub-box at the same p, M, Re, dt: one BDF2 step per bench step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FR/CPR residual+JVP GDOF/s; sec per BDF2 step to 1e-8 (mixed vs FP64)"
+UNIT = "GDOF/s"
+
+
+# ------------------------------------------------------------------ roofline peaks
+# FP64 pipe of one GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26 TFLOP/s nominal;
+# 1.20 TFLOP/s measured with a dependent-FMA probe at 2.0 GHz on this machine.  FP32 SIMT:
+# 152 x 128 x 2 x 2.07 GHz = 80.5 TFLOP/s nominal, 70.3 measured by the same probe.
+FP64_PEAK_TFLOPS = 1.20
+FP32_PEAK_TFLOPS = 70.3
+ALU_PEAK_SOURCE = "FMA-throughput probe on this pool's GB300 (nominal from unit counts x clock: 1.26 FP64, 80.5 FP32)"
+ALU_KINDS = {"trace", "face", "elem", "trace_jvp", "face_jvp", "elem_jvp", "block_jacobian",
+             "block_factor", "geometry"}
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(steps: int, warmup: int):
+    """The oracle as it stands on a bounded sample: BDF2 steps on the 16x16 sub-box."""
+    from oracle import physics as ph
+    from oracle import residual as rs
+    from oracle import solver as sv
+    from paper_1903_06304_gb300 import inputs as inp
+    w0 = inp.NS_VORTEX_64
+    w = inp.Workload("ns_vortex_16x16_p3_sample", 16, 16, w0.p, w0.mach, w0.re, w0.kappa,
+                     (0.0, 2.5, 0.0, 2.5), dt=w0.dt, restart=w0.restart)
+    c, v, q = inp.make_case(w)
+    prob = sv.Problem(rs.Mesh(w.nx, w.ny, c, v), w.p, ph.Gas(mach=w.mach, re=w.re, kappa=w.kappa))
+    qc_n = prob.qc(q)
+    qc_nm1 = qc_n
+    times = []
+    for k in range(warmup + steps):
+        t0 = time.perf_counter()
+        q1, st = sv.bdf2_step(prob, q, qc_n, qc_nm1, w.dt, coeffs=sv.BDF1 if k == 0 else sv.BDF2,
+                              restart=w.restart, tol_res=w.tol_res, maxit_lin=w.maxit_lin,
+                              tol_pseudo=w.tol_pseudo, maxit_newton=w.maxit_newton)
+        dt_s = time.perf_counter() - t0
+        qc_nm1, qc_n, q = qc_n, prob.qc(q1), q1
+        if k >= warmup:
+            times.append(dt_s)
+    dof = w.dof
+    sec = sum(times) / len(times)
+    return {"value": dof / sec / 1e9, "unit": UNIT, "sec_per_step": sec, "dof": dof,
+            "cores": 1, "kind": "oracle",
+            "sample": "oracle BDF2 steps (BDF1 first) on the 16x16 p=3 sub-box of the vortex "
+                      "box (same p, M, Re, dt; 1/16 of the DOF), numpy FP64, one thread"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = oracle_sample(args.steps, args.warmup)
+    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["sec_per_step"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "ns_vortex_64x64_p3",
+                       "sample": "ns_vortex_16x16_p3 sub-box (same element size, p, M, Re, dt)",
+                       "note": res["sample"]},
+            "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": res["cores"],
+                             "kind": "oracle", "sample": res["sample"]},
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_1903_06304_gb300 import fr
+    from paper_1903_06304_gb300 import inputs as inp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = inp.WORKLOADS[args.workload]
+    corners, vel, q0 = inp.make_case(w)
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    def make_solver(prec):
+        cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=prec,
+                        restart=args.restart, maxit_lin=args.maxit_lin, tol_res=w.tol_res,
+                        tol_pseudo=w.tol_pseudo, maxit_newton=args.maxit_newton, lag=2,
+                        line_search=args.line_search)
+        S = fr.Solver(cfg, w.nx, w.ny)
+        S.update_mesh(T(corners), T(vel))
+        return S
+
+    class Run:
+        """State of a BDF2 march: q^n, q^c,n, q^c,n-1 resident on the device."""
+
+        def __init__(self, S):
+            self.S = S
+            self.q = T(q0)
+            self.qc_n = torch.empty_like(self.q)
+            self.qc_nm1 = torch.empty_like(self.q)
+            S.conservative(self.q, self.qc_n)
+            self.qc_nm1.copy_(self.qc_n)
+            self.k = 0
+
+        def step(self):
+            coeffs = fr.BDF1 if self.k == 0 else fr.BDF2
+            st = self.S.bdf2_step(self.q, self.qc_n, self.qc_nm1, w.dt, coeffs=coeffs,
+                                  allow_unconverged=True)
+            self.qc_nm1.copy_(self.qc_n)
+            self.S.conservative(self.q, self.qc_n)
+            self.k += 1
+            return st.summary()
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def timed_steps(run, K):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        stats = []
+        launches0 = run.S.kernel_launches
+        barrier()
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record()
+            stats.append(run.step())
+            ev[k][1].record()
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, stats, run.S.kernel_launches - launches0
+
+    # ---- headline: configured precision.  The march first runs --startup untimed steps:
+    # the sampled vortex is not a discrete solution of the scheme, and the first BDF2 steps
+    # carry a stiff pressure transient that the element block-Jacobi Newton-Krylov loop
+    # does not converge (see the design notes); warm-up and timed steps follow it.
+    S = make_solver(args.prec)
+    run = Run(S)
+    for _ in range(args.startup + args.warmup):
+        run.step()
+    clocks = ClockSampler(local)
+    ms, stats, launches = timed_steps(run, args.steps)
+    clock_info = clocks.stop()
+    t_rank = sum(ms) / 1e3
+    if dist is not None:
+        tt = torch.tensor([t_rank], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    else:
+        t_max = t_rank
+    dof = S.ndof
+    value = dof * args.steps * world / t_max / 1e9
+    ms_per_step = t_max * 1e3 / args.steps
+
+    # ---- per-kernel device time over the same number of steps (profiling pass)
+    S.profile(True)
+    S.profile_read(reset=True)
+    _ms_p, _st_p, _ = timed_steps(run, args.steps)
+    prof = S.profile_read(reset=True)
+    S.profile(False)
+    hbm_gbs, hbm_src = hbm_peak()
+    tot_ms = sum(v["ms"] for v in prof.values())
+    kernels = {}
+    for name, v in prof.items():
+        if v["launches"] == 0:
+            continue
+        t_s = v["ms"] * 1e-3
+        e = {"ms_total": v["ms"], "launches": v["launches"],
+             "us_per_launch": 1e3 * v["ms"] / v["launches"],
+             "share": v["ms"] / tot_ms if tot_ms else None}
+        if name in ALU_KINDS:
+            fp32 = name == "block_factor" and args.prec != "fp64"
+            peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+            e.update(bound="alu", pipe="fp32" if fp32 else "fp64", unit="TFLOP/s",
+                     achieved=v["flops"] / t_s / 1e12, peak=peak,
+                     alg_per_launch=v["flops"] / v["launches"])
+        else:
+            e.update(bound="hbm", unit="GB/s", achieved=v["bytes"] / t_s / 1e9, peak=hbm_gbs,
+                     alg_per_launch=v["bytes"] / v["launches"])
+        e["frac"] = e["achieved"] / e["peak"]
+        kernels[name] = e
+    dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
+
+    # ---- kernel throughput: residual and JVP at the final state (CUDA events)
+    out = torch.empty_like(run.q)
+    vec = torch.randn_like(run.q)
+
+    def time_calls(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    t_res = time_calls(lambda: S.residual(run.q, out))
+    t_jvp = time_calls(lambda: S.jvp(run.q, vec, out, 1e-20, 1.5 / w.dt))
+
+    # ---- precision comparison: a few steps from the same state per block precision
+    compare = {}
+    if not args.no_compare:
+        for prec in ("fp64", "fp32", "bf16"):
+            S2 = make_solver(prec)
+            r2 = Run(S2)
+            r2.q.copy_(run.q)
+            r2.qc_n.copy_(run.qc_n)
+            r2.qc_nm1.copy_(run.qc_nm1)
+            r2.k = run.k
+            ms2, st2, _ = timed_steps(r2, max(2, min(args.steps, 3)))
+            compare[prec] = {"sec_per_step": statistics.mean(ms2) / 1e3,
+                             "newton": [s["newton_iterations"] for s in st2],
+                             "gmres_total": [sum(s["gmres_iterations"]) for s in st2],
+                             "converged": all(s["converged"] for s in st2),
+                             "state_diff_vs_headline": None}
+            S2.close()
+
+    # ---- end-to-end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        hq = torch.empty_like(run.q, device="cpu").pin_memory()
+        hqn = torch.empty_like(hq).pin_memory()
+        hqm = torch.empty_like(hq).pin_memory()
+        hq.copy_(run.q)
+        hqn.copy_(run.qc_n)
+        hqm.copy_(run.qc_nm1)
+        evs = []
+        barrier()
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            run.q.copy_(hq, non_blocking=True)
+            run.qc_n.copy_(hqn, non_blocking=True)
+            run.qc_nm1.copy_(hqm, non_blocking=True)
+            run.step()
+            hq.copy_(run.q, non_blocking=True)
+            hqn.copy_(run.qc_n, non_blocking=True)
+            hqm.copy_(run.qc_nm1, non_blocking=True)
+            b.record()
+            evs.append((a, b))
+        barrier()
+        t_e2e = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+        if dist is not None:
+            tt = torch.tensor([t_e2e], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+        nb = run.q.numel() * 8
+        e2e = {"value": dof * args.steps * world / t_e2e / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * nb, "d2h_bytes_per_step": 3 * nb}
+
+    # ---- CPU baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = oracle_sample(1, 0)
+        cpu = {"value": res["value"], "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+               "sample": res["sample"]}
+
+    dk = kernels[dominant]
+    roof = {"kernel": dominant, "bound": dk["bound"], "achieved": dk["achieved"],
+            "peak": dk["peak"], "unit": dk["unit"], "frac": dk["frac"],
+            "peak_source": hbm_src if dk["bound"] == "hbm" else ALU_PEAK_SOURCE,
+            "alg_per_launch": dk["alg_per_launch"], "us_per_launch": dk["us_per_launch"],
+            "share": dk["share"], "traffic": None}
+
+    last = stats[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "mesh": f"{w.nx}x{w.ny} periodic [0,10]^2",
+                   "p": w.p, "dof": dof, "mach": w.mach, "re_ref": w.re, "kappa": w.kappa,
+                   "dt": w.dt, "tol_pseudo": w.tol_pseudo, "tol_res": w.tol_res,
+                   "gmres": f"GMRES({args.restart}) left-preconditioned, maxit {args.maxit_lin}",
+                   "newton": f"max {args.maxit_newton} iterations, backtracking {args.line_search} halvings",
+                   "precond": f"element block-Jacobi, {args.prec} blocks",
+                   "l2": "256 MiB write between timed steps, outside the per-step events",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "startup_steps": args.startup,
+        "sec_per_bdf2_step": ms_per_step / 1e3,
+        "converged_all": all(s["converged"] for s in stats),
+        "newton_iterations": [s["newton_iterations"] for s in stats],
+        "gmres_iterations_per_step": [sum(s["gmres_iterations"]) for s in stats],
+        "res_drop_last": last["res_history"][-1] / last["res_history"][0],
+        "residual_gdofs": dof / (t_res * 1e-3) / 1e9,
+        "jvp_gdofs": dof / (t_jvp * 1e-3) / 1e9,
+        "precision_compare": compare,
+        "kernels": kernels,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clock_info,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    S.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def kernels_only(args):
+    """Short fixed sequence for profiler captures: geometry, one residual, one JVP, a
+    block build and one GMRES solve on the chosen workload (no timing, no JSON)."""
+    import numpy as np
+    import torch
+
+    from paper_1903_06304_gb300 import fr
+    from paper_1903_06304_gb300 import inputs as inp
+    w = inp.WORKLOADS[args.workload]
+    c, v, q = inp.make_case(w, t=0.13 if w.deforming else 0.0)
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda:0")
+    S = fr.Solver(fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
+                            restart=args.restart, maxit_lin=args.maxit_lin), w.nx, w.ny)
+    S.update_mesh(T(c), T(v))
+    qd = T(q)
+    out = torch.empty_like(qd)
+    qc = torch.empty_like(qd)
+    S.conservative(qd, qc)
+    S.bdf_rhs(qd, qc, qc, fr.BDF1, w.dt, out)
+    x = torch.empty_like(qd)
+    for _ in range(args.steps):
+        S.residual(qd, x)
+        S.jvp(qd, out, x, 1e-20, 1.0 / w.dt)
+    S.precond_build(qd, 1e-20, 1.0 / w.dt)
+    its = S.gmres(qd, out, x, 1e-20, 1.0 / w.dt)
+    torch.cuda.synchronize()
+    print(f"kernels-only {w.name}: gmres {its} iterations, {S.kernel_launches} launches")
+    S.close()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--startup", type=int, default=8,
+                    help="untimed BDF2 steps of the march before the warm-up steps")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ns_vortex_64x64_p3")
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--maxit-lin", dest="maxit_lin", type=int, default=100)
+    ap.add_argument("--maxit-newton", dest="maxit_newton", type=int, default=40)
+    ap.add_argument("--line-search", dest="line_search", type=int, default=4,
+                    help="backtracking halvings per Newton update (0: plain Newton)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="short fixed call sequence for profiler captures")
+    args = ap.parse_args()
+    if args.kernels_only:
+        kernels_only(args)
+        return
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -61,6 +61,12 @@ typedef struct fr_ctx fr_ctx;
  * lag: rebuild the blocks every `lag` pseudo-iterations (2 unsteady, 1 steady, Sec. 4);
  * dtau0, dtau_min, dtau_max, r_ser: SER law (Eq. SER) for steady PTC;
  * dtau_unsteady: the fixed pseudo step of BDF2 runs (1e20 in Sec. 3.2);
+ * ser_unsteady: if nonzero, BDF2 pseudo-loops start at dtau0_unsteady and adapt dtau by
+ * the SER law (Eq. SER, same dtau_min/dtau_max/r_ser) instead of the fixed step, with the
+ * blocks rebuilt at every pseudo-iteration (pseudo-transient continuation);
+ * line_search: 0 = plain Newton updates (the paper); k > 0 = backtracking: the update
+ * q + lambda dq is tried with lambda = 1, 1/2, ..., 2^-k and the first lambda that lowers
+ * the full 2-norm of the pseudo-step residual is kept (the last one otherwise);
  * gmres_side: FR_GMRES_LEFT (PETSc's default, the paper's solver: Krylov space of B^-1 A,
  * tol_res relative to ||B^-1 b||) or FR_GMRES_RIGHT (Krylov space of A B^-1, tol_res
  * relative to ||b||). */
@@ -75,6 +81,9 @@ typedef struct fr_config {
   double tol_res, tol_pseudo;
   double dtau0, dtau_min, dtau_max, r_ser, dtau_unsteady;
   int gmres_side;
+  int ser_unsteady;
+  double dtau0_unsteady;
+  int line_search;
 } fr_config;
 
 /* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).
@@ -84,6 +93,7 @@ typedef struct fr_config {
 typedef struct fr_stats {
   int newton_iterations;
   int converged;
+  int line_search_halvings;
   int gmres_iterations[FR_MAX_NEWTON];
   double res_history[FR_MAX_NEWTON + 1];
   double dtau_history[FR_MAX_NEWTON + 1];
@@ -171,6 +181,20 @@ int fr_ptc_solve(fr_ctx* ctx, double* qp_d, fr_stats* stats, void* stream);
  * written to host *res_mass, *res_all.  Synchronises. */
 int fr_residual_norms(fr_ctx* ctx, const double* r_d, double* res_mass, double* res_all,
                       void* stream);
+
+/* Instrumentation (no counterpart in the paper).  While enabled, every kernel launch
+ * is bracketed by a pair of CUDA events on its own stream; fr_profile_read
+ * synchronises on them and returns, per kernel class k < FR_PROF_KINDS, the summed
+ * device milliseconds ms[k], the timed launch counts counts[k], the total launches
+ * launches[k] since creation, and the algorithmic flops[k] and DRAM bytes[k] of the
+ * launches issued since the last reset (both counted whether or not timing is on);
+ * reset != 0 clears the timing and the algorithmic totals.  Any output pointer may be
+ * NULL.  fr_profile_name(k) names class k. */
+#define FR_PROF_KINDS 13
+int fr_profile(fr_ctx* ctx, int enable);
+int fr_profile_read(fr_ctx* ctx, double* ms, long long* counts, long long* launches, double* flops,
+                    double* bytes, int reset);
+const char* fr_profile_name(int kind);
 
 /* Sizes: number of FP64 entries of a solution vector, block size b. */
 size_t fr_num_dof(const fr_ctx* ctx);

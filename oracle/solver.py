@@ -251,8 +251,10 @@ class StepStats:
 
 def newton_solve(prob: Problem, q, rhs, a0_dt: float, dtau0: float, restart: int,
                  tol_res: float, maxit_lin: int, tol_pseudo: float, maxit_newton: int,
-                 lag: int, ser=None, side: str = "left"):
-    """Pseudo-time Newton loop shared by BDF2 and PTC; ``ser`` = (dtau_min, dtau_max, r)."""
+                 lag: int, ser=None, side: str = "left", line_search: int = 0):
+    """Pseudo-time Newton loop shared by BDF2 and PTC; ``ser`` = (dtau_min, dtau_max, r).
+    line_search = k > 0: backtracking on the full residual 2-norm, lambda = 1, 1/2, ...,
+    2^-k (the paper takes plain Newton updates, k = 0)."""
     q = q.copy()
     r = rhs(q)
     res = [float(np.linalg.norm(r[0]))]
@@ -272,8 +274,16 @@ def newton_solve(prob: Problem, q, rhs, a0_dt: float, dtau0: float, restart: int
         out = gmres(lambda v: apply_A(prob, qm, v, inv_dtau, a0_dt), r,
                     lambda v: block_apply(Binv, v), restart, tol_res, maxit_lin, side)
         its.append(out.iterations)
-        q = q + out.x
+        prev_all = np.linalg.norm(r)
+        lam = 1.0
+        q = qm + lam * out.x
         r = rhs(q)
+        for _ in range(line_search):
+            if np.linalg.norm(r) < prev_all:
+                break
+            lam *= 0.5
+            q = qm + lam * out.x
+            r = rhs(q)
         res.append(float(np.linalg.norm(r[0])))
         if ser is not None:
             dmin, dmax, rser = ser
@@ -287,11 +297,14 @@ def newton_solve(prob: Problem, q, rhs, a0_dt: float, dtau0: float, restart: int
 def bdf2_step(prob: Problem, q, qc_n, qc_nm1, dt: float, coeffs=BDF2, dtau: float = 1e20,
               restart: int = 30, tol_res: float = 1e-6, maxit_lin: int = 100,
               tol_pseudo: float = 1e-8, maxit_newton: int = 20, lag: int = 2,
-              side: str = "left"):
-    """One physical BDF2 step (Eq. unsteady_pre_discretized_3) from q^n = q (initial guess)."""
+              side: str = "left", ser=None, line_search: int = 0):
+    """One physical BDF2 step (Eq. unsteady_pre_discretized_3) from q^n = q (initial guess).
+    ser = (dtau_min, dtau_max, r_ser): adapt the pseudo step from dtau by the SER law
+    (pseudo-transient continuation, the steady strategy of Sec. 3.2) instead of the fixed
+    dtau of the paper's unsteady runs."""
     rhs = lambda s: time_rhs(prob, s, qc_n, qc_nm1, dt, coeffs)
     return newton_solve(prob, q, rhs, coeffs[0] / dt, dtau, restart, tol_res, maxit_lin,
-                        tol_pseudo, maxit_newton, lag, side=side)
+                        tol_pseudo, maxit_newton, lag, ser=ser, side=side, line_search=line_search)
 
 
 def ptc_solve(prob: Problem, q, dtau0: float = 0.01, dtau_min: float = 0.01,

@@ -124,6 +124,7 @@ void free_mesh(fr_ctx* c) {
   if (c->Dr) { cudaFree(c->Dr); c->Dr = nullptr; }
   if (c->Dc) { cudaFree(c->Dc); c->Dc = nullptr; }
   if (c->info) { cudaFree(c->info); c->info = nullptr; }
+  if (c->ticket) { cudaFree(c->ticket); c->ticket = nullptr; }
   c->blocks_ready = 0;
 }
 
@@ -295,14 +296,15 @@ int newton_loop(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, do
   FR_TRY(norms_host(c, r, &rm, &ra, s));
   const double res0 = rm;
   st->res_history[0] = rm;
-  double dtau = steady ? c->cfg.dtau0 : c->cfg.dtau_unsteady;
+  const bool ser = steady || c->cfg.ser_unsteady;
+  double dtau = steady ? c->cfg.dtau0 : (c->cfg.ser_unsteady ? c->cfg.dtau0_unsteady : c->cfg.dtau_unsteady);
   st->dtau_history[0] = dtau;
   int m = 0;
   bool conv = false;
   for (m = 0; m < maxit; ++m) {
     if (rm <= c->cfg.tol_pseudo * res0) { conv = true; break; }
     const double inv_dtau = 1.0 / dtau;
-    if (steady || m % std::max(1, c->cfg.lag) == 0) {
+    if (ser || m % std::max(1, c->cfg.lag) == 0) {
       FR_TRY(frk::block_build(c, q, inv_dtau, a0dt, s));
       c->blocks_ready = 1;
       st->block_builds++;
@@ -310,12 +312,21 @@ int newton_loop(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, do
     int its = 0;
     FR_TRY(gmres_solve(c, q, r, inv_dtau, a0dt, c->w_x, &its, s));
     st->gmres_iterations[m] = its;
+    const double prev = rm, prev_all = ra;
     FR_TRY(frk::axpby(c, 1.0, c->w_x, 1.0, q, s));
     FR_TRY(rhs(r));
-    const double prev = rm;
     FR_TRY(norms_host(c, r, &rm, &ra, s));
+    // backtracking: q = q_m + lambda dq while the full residual norm does not decrease
+    double lambda = 1.0;
+    for (int h = 0; h < c->cfg.line_search && !(ra < prev_all); ++h) {
+      FR_TRY(frk::axpby(c, -0.5 * lambda, c->w_x, 1.0, q, s));
+      lambda *= 0.5;
+      FR_TRY(rhs(r));
+      FR_TRY(norms_host(c, r, &rm, &ra, s));
+      st->line_search_halvings++;
+    }
     st->res_history[m + 1] = rm;
-    if (steady) {
+    if (ser) {
       dtau = std::max(c->cfg.dtau_min, std::min(c->cfg.dtau_max, dtau * std::pow(prev / rm, c->cfg.r_ser)));
     }
     st->dtau_history[m + 1] = dtau;
@@ -326,9 +337,78 @@ int newton_loop(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, do
   return conv ? FR_OK : FR_ERR_NOT_CONVERGED;
 }
 
+const char* kKernelNames[KK_COUNT] = {
+    "geometry", "trace", "face", "elem", "trace_jvp", "face_jvp", "elem_jvp", "block_jacobian",
+    "block_factor", "block_apply", "krylov_reduce", "vector", "conservative"};
+
+// Fold the recorded event pairs into the per-kind totals (synchronises on the events).
+int prof_collect(fr_ctx* c) {
+  for (const FrProfPair& p : c->prof.pairs) {
+    FR_CUDA_CHECK(c, cudaEventSynchronize(p.b));
+    float ms = 0.f;
+    FR_CUDA_CHECK(c, cudaEventElapsedTime(&ms, p.a, p.b));
+    c->prof.ms[p.kind] += ms;
+    c->prof.n[p.kind] += 1;
+  }
+  c->prof.pairs.clear();
+  c->prof.used = 0;
+  return FR_OK;
+}
+
 }  // namespace
 
+cudaEvent_t fr_prof_begin(fr_ctx* c, cudaStream_t s) {
+  if (c->prof.used + 2 > c->prof.pool.size()) {
+    if (c->prof.pool.size() >= (1u << 20)) prof_collect(c);  // bound the pool
+    for (int k = 0; k < 256; ++k) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      c->prof.pool.push_back(e);
+    }
+  }
+  cudaEvent_t e = c->prof.pool[c->prof.used++];
+  cudaEventRecord(e, s);
+  return e;
+}
+
+void fr_prof_end(fr_ctx* c, cudaStream_t s, cudaEvent_t begin, int kind) {
+  if (c->prof.used + 1 > c->prof.pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    c->prof.pool.push_back(e);
+  }
+  cudaEvent_t e = c->prof.pool[c->prof.used++];
+  cudaEventRecord(e, s);
+  c->prof.pairs.push_back({begin, e, kind});
+}
+
 extern "C" {
+
+int fr_profile(fr_ctx* c, int enable) {
+  if (!c) return FR_ERR_ARG;
+  FR_TRY(prof_collect(c));
+  c->prof.on = enable != 0;
+  return FR_OK;
+}
+
+int fr_profile_read(fr_ctx* c, double* ms, long long* counts, long long* launches, double* flops,
+                    double* bytes, int reset) {
+  if (!c) return FR_ERR_ARG;
+  FR_TRY(prof_collect(c));
+  for (int k = 0; k < KK_COUNT; ++k) {
+    if (ms) ms[k] = c->prof.ms[k];
+    if (counts) counts[k] = c->prof.n[k];
+    if (launches) launches[k] = c->launches_by_kind[k];
+    if (flops) flops[k] = c->alg_flops[k];
+    if (bytes) bytes[k] = c->alg_bytes[k];
+    if (reset) { c->prof.ms[k] = 0.0; c->prof.n[k] = 0; c->alg_flops[k] = 0.0; c->alg_bytes[k] = 0.0; }
+  }
+  return FR_OK;
+}
+
+const char* fr_profile_name(int kind) {
+  return (kind >= 0 && kind < KK_COUNT) ? kKernelNames[kind] : "";
+}
 
 const char* fr_version(void) { return "fr-gb300 0.1 (sm_103a)"; }
 
@@ -354,6 +434,9 @@ void fr_default_config(fr_config* c) {
   c->r_ser = 2.0;
   c->dtau_unsteady = 1e20;
   c->gmres_side = FR_GMRES_LEFT;
+  c->ser_unsteady = 0;
+  c->dtau0_unsteady = 0.01;
+  c->line_search = 0;
 }
 
 int fr_create(const fr_config* cfg, fr_ctx** out) {
@@ -384,6 +467,8 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
 
 void fr_destroy(fr_ctx* c) {
   if (!c) return;
+  prof_collect(c);
+  for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   free_mesh(c);
   if (c->dsc) cudaFree(c->dsc);
   if (c->hsc) cudaFreeHost(c->hsc);
@@ -428,6 +513,8 @@ int fr_set_mesh(fr_ctx* c, int nx, int ny, int px, int py) {
   FR_TRY(dev_alloc(c, &c->w_t, c->ndof));
   FR_TRY(dev_alloc(c, &c->w_u, c->ndof));
   FR_TRY(dev_alloc(c, &c->red, (size_t)32 * c->red_blocks));
+  FR_TRY(dev_alloc(c, &c->ticket, 1));
+  FR_CUDA_CHECK(c, cudaMemset(c->ticket, 0, sizeof(unsigned int)));
   return FR_OK;
 }
 

@@ -3,8 +3,28 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <vector>
 #include "fr_device.cuh"
 #include "../../include/fr.h"
+
+// Kernel classes for the optional per-kernel timing (fr_profile) and launch counts.
+enum FrKernel {
+  KK_GEOM, KK_TRACE, KK_FACE, KK_ELEM, KK_TRACE_JVP, KK_FACE_JVP, KK_ELEM_JVP, KK_BLOCK,
+  KK_FACTOR, KK_APPLY, KK_KRYLOV, KK_VECTOR, KK_CONS, KK_COUNT
+};
+
+struct FrProfPair {
+  cudaEvent_t a, b;
+  int kind;
+};
+struct FrProf {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;   // reusable events
+  size_t used = 0;                 // events handed out since the last read
+  std::vector<FrProfPair> pairs;   // recorded launches since the last read
+  double ms[KK_COUNT] = {};
+  long long n[KK_COUNT] = {};
+};
 
 struct fr_ctx {
   fr_config cfg;
@@ -31,12 +51,41 @@ struct fr_ctx {
   double* V = nullptr;       // [(m+1)][ndof]
   double *w_r = nullptr, *w_z = nullptr, *w_x = nullptr, *w_t = nullptr, *w_u = nullptr;
   double* red = nullptr;     // reduction partials
+  unsigned int* ticket = nullptr;  // last-block counter of the reductions (kept at 0)
   double* dsc = nullptr;     // small device scalars
   double* hsc = nullptr;     // pinned host mirror of dsc
   int red_blocks = 0;
   long long launches = 0;
+  long long launches_by_kind[KK_COUNT] = {};
+  double alg_flops[KK_COUNT] = {};   // algorithmic FP64/FP32 flops issued per class
+  double alg_bytes[KK_COUNT] = {};   // algorithmic DRAM bytes (streaming kernels)
+  FrProf prof;
   char err[512];
 };
+
+// Algorithmic FP flops per solution point of the point-parallel kernels (see the design
+// notes for the itemised count; +,-,*,/,sqrt = 1 flop, FMA = 2).
+double fr_flops_trace(int n, bool viscous);
+double fr_flops_face_point(bool viscous);   // per owned flux point
+double fr_flops_elem(int n, bool viscous);
+extern const double FR_JVP_FLOP_FACTOR;     // dual-number cost over the value cost
+
+#define FR_ACCOUNT(c, k, flops, bytes) \
+  do {                                 \
+    (c)->alg_flops[(k)] += (flops);    \
+    (c)->alg_bytes[(k)] += (bytes);    \
+  } while (0)
+
+// Timing of one launch when profiling is on: a pair of events around it on its stream.
+cudaEvent_t fr_prof_begin(fr_ctx* c, cudaStream_t s);
+void fr_prof_end(fr_ctx* c, cudaStream_t s, cudaEvent_t begin, int kind);
+
+#define FR_PROF_BEGIN(c, s) cudaEvent_t fr_ev_ = (c)->prof.on ? fr_prof_begin((c), (s)) : nullptr
+#define FR_PROF_END(c, s, k)                                           \
+  do {                                                                  \
+    (c)->launches_by_kind[(k)]++;                                       \
+    if (fr_ev_) fr_prof_end((c), (s), fr_ev_, (k));                     \
+  } while (0)
 
 namespace frk {
 int geometry(fr_ctx* c, const double* corners, const double* vel, cudaStream_t s);

@@ -1,6 +1,6 @@
 // fr_krylov.cu -- FP64 vector kernels of restarted GMRES with CGS2 (Sec. 3.2) and the
 // pseudo-step residual norms.  Reductions are deterministic: a fixed grid writes one
-// partial per block and a second launch sums the partials in a fixed order.
+// partial per block and the last block to finish sums the partials in a fixed order.
 #include <cstdio>
 #include "fr_internal.h"
 
@@ -15,9 +15,13 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
-// Sum nv per-thread values over the block; thread 0 writes partial[k * nblk + blockIdx.x].
-__device__ __forceinline__ void block_store(double (&acc)[MAXV], int nv, double* partial) {
+// Block sums of nv per-thread values: partial[k * gridDim.x + blockIdx.x].  The last
+// block to finish (atomic ticket, no waiting) then sums the partials of every k in a
+// fixed order and writes out[k]: one launch per reduction, deterministic result.
+__device__ __forceinline__ void block_reduce_store(double (&acc)[MAXV], int nv, double* partial,
+                                                   double* out, unsigned int* ticket) {
   __shared__ double sm[MAXV][RT / 32];
+  __shared__ bool last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < MAXV; ++k) {
@@ -33,15 +37,31 @@ __device__ __forceinline__ void block_store(double (&acc)[MAXV], int nv, double*
     for (int w = 0; w < RT / 32; ++w) s += sm[threadIdx.x][w];
     partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // final pass: warp w sums the partials of k = w, w + 8, ... in a fixed order
+  const int nb = gridDim.x;
+  for (int k = wid; k < nv; k += RT / 32) {
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += ((volatile double*)partial)[(size_t)k * nb + b];
+    s = warp_sum(s);
+    if (lane == 0) out[k] = s;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// MODE 0: dots  partial_k = <V_k, w>
-// MODE 1: w -= sum_k h_k V_k, then partial_k = <V_k, w>       (CGS2 second pass)
-// MODE 2: w -= sum_k h_k V_k, then partial_0 = <w, w>
+// MODE 0: dots  out_k = <V_k, w>
+// MODE 1: w -= sum_k h_k V_k, then out_k = <V_k, w>       (CGS2 second pass)
+// MODE 2: w -= sum_k h_k V_k, then out_0 = <w, w>
 template <int MODE>
 __global__ void __launch_bounds__(RT) k_krylov(const double* __restrict__ V, size_t ld, int nv,
                                                const double* __restrict__ h, double* w, size_t n,
-                                               double* __restrict__ partial) {
+                                               double* __restrict__ partial, double* out,
+                                               unsigned int* ticket) {
   double acc[MAXV];
 #pragma unroll
   for (int k = 0; k < MAXV; ++k) acc[k] = 0.0;
@@ -66,21 +86,13 @@ __global__ void __launch_bounds__(RT) k_krylov(const double* __restrict__ V, siz
         if (k < nv) acc[k] = fma(V[k * ld + i], x, acc[k]);
     }
   }
-  block_store(acc, MODE == 2 ? 1 : nv, partial);
+  block_reduce_store(acc, MODE == 2 ? 1 : nv, partial, out, ticket);
 }
 
-// out[k] = sum over blocks of partial[k][*] (one thread per k, fixed order)
-__global__ void k_finish(const double* __restrict__ partial, int nblk, int nv, double* out) {
-  const int k = threadIdx.x;
-  if (k >= nv) return;
-  double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partial[(size_t)k * nblk + b];
-  out[k] = s;
-}
-
-// partial_0 = ||r[continuity row]||^2, partial_1 = ||r||^2
+// out_0 = ||r[continuity row]||^2, out_1 = ||r||^2
 __global__ void __launch_bounds__(RT) k_norms(const double* __restrict__ r, size_t sn, size_t n,
-                                              double* __restrict__ partial) {
+                                              double* __restrict__ partial, double* out,
+                                              unsigned int* ticket) {
   double acc[MAXV];
   acc[0] = 0.0;
   acc[1] = 0.0;
@@ -89,7 +101,7 @@ __global__ void __launch_bounds__(RT) k_norms(const double* __restrict__ r, size
     if (i < sn) acc[0] = fma(x, x, acc[0]);
     acc[1] = fma(x, x, acc[1]);
   }
-  block_store(acc, 2, partial);
+  block_reduce_store(acc, 2, partial, out, ticket);
 }
 
 __global__ void k_scale(const double* __restrict__ x, double a, double* __restrict__ y, size_t n) {
@@ -137,10 +149,11 @@ static int krylov(fr_ctx* c, const double* V, int nv, const double* h, double* w
                   cudaStream_t s) {
   if (nv < 1 || nv > MAXV) { snprintf(c->err, sizeof(c->err), "krylov: nv=%d", nv); return FR_ERR_ARG; }
   const int g = grid_for(c);
-  k_krylov<MODE><<<g, RT, 0, s>>>(V, c->ndof, nv, h, w, c->ndof, c->red);
-  FR_LAUNCH_CHECK(c);
-  const int nk = MODE == 2 ? 1 : nv;
-  k_finish<<<1, 32, 0, s>>>(c->red, g, nk, out);
+  FR_ACCOUNT(c, KK_KRYLOV, (MODE == 0 ? 2.0 : 4.0) * nv * c->ndof,
+             8.0 * c->ndof * (nv + 1 + (MODE != 0 ? 1 : 0)));
+  FR_PROF_BEGIN(c, s);
+  k_krylov<MODE><<<g, RT, 0, s>>>(V, c->ndof, nv, h, w, c->ndof, c->red, out, c->ticket);
+  FR_PROF_END(c, s, KK_KRYLOV);
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }
@@ -156,30 +169,35 @@ int axpy_norm(fr_ctx* c, const double* V, int nv, const double* h, double* w, do
 }
 int norms(fr_ctx* c, const double* r, double* out, cudaStream_t s) {
   const int g = grid_for(c);
-  k_norms<<<g, RT, 0, s>>>(r, (size_t)c->ne * c->np2, c->ndof, c->red);
-  FR_LAUNCH_CHECK(c);
-  k_finish<<<1, 32, 0, s>>>(c->red, g, 2, out);
+  FR_ACCOUNT(c, KK_KRYLOV, 2.0 * c->ndof, 8.0 * c->ndof);
+  FR_PROF_BEGIN(c, s);
+  k_norms<<<g, RT, 0, s>>>(r, (size_t)c->ne * c->np2, c->ndof, c->red, out, c->ticket);
+  FR_PROF_END(c, s, KK_KRYLOV);
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }
 int scale(fr_ctx* c, const double* x, double a, double* y, cudaStream_t s) {
-  k_scale<<<grid_for(c), RT, 0, s>>>(x, a, y, c->ndof);
+  FR_ACCOUNT(c, KK_VECTOR, 1.0 * c->ndof, 16.0 * c->ndof);
+{ FR_PROF_BEGIN(c, s); k_scale<<<grid_for(c), RT, 0, s>>>(x, a, y, c->ndof); FR_PROF_END(c, s, KK_VECTOR); }
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }
 int axpby(fr_ctx* c, double a, const double* x, double b, double* y, cudaStream_t s) {
-  k_axpby<<<grid_for(c), RT, 0, s>>>(a, x, b, y, c->ndof);
+  FR_ACCOUNT(c, KK_VECTOR, 3.0 * c->ndof, 24.0 * c->ndof);
+{ FR_PROF_BEGIN(c, s); k_axpby<<<grid_for(c), RT, 0, s>>>(a, x, b, y, c->ndof); FR_PROF_END(c, s, KK_VECTOR); }
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }
 // w -= sum_k h_k V_k (nv <= 32), no reduction
 int axpy(fr_ctx* c, const double* V, int nv, const double* h, double* w, cudaStream_t s) {
-  k_axpy_multi<<<grid_for(c), RT, 0, s>>>(V, c->ndof, nv, h, w, c->ndof);
+  FR_ACCOUNT(c, KK_VECTOR, 2.0 * nv * c->ndof, 8.0 * c->ndof * (nv + 2));
+{ FR_PROF_BEGIN(c, s); k_axpy_multi<<<grid_for(c), RT, 0, s>>>(V, c->ndof, nv, h, w, c->ndof); FR_PROF_END(c, s, KK_VECTOR); }
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }
 int lincomb(fr_ctx* c, const double* V, int nv, const double* y, double* u, cudaStream_t s) {
-  k_lincomb<<<grid_for(c), RT, 0, s>>>(V, c->ndof, nv, y, u, c->ndof);
+  FR_ACCOUNT(c, KK_VECTOR, 2.0 * nv * c->ndof, 8.0 * c->ndof * (nv + 1));
+{ FR_PROF_BEGIN(c, s); k_lincomb<<<grid_for(c), RT, 0, s>>>(V, c->ndof, nv, y, u, c->ndof); FR_PROF_END(c, s, KK_VECTOR); }
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }

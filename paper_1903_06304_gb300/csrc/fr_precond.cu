@@ -352,14 +352,26 @@ static int block_build_n(fr_ctx* c, const double* q, double inv_dtau, double a0_
   // value traces of every element (neighbour data of the blocks)
   constexpr int EPB = Tile<N>::EPB, TH = Tile<N>::THREADS;
   const int nblk = (c->ne + EPB - 1) / EPB;
-  k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(q)}, c->ne, c->basis,
-                                         c->gas, c->gs, Buf<double>{c->gl}, Buf<double>{c->tq},
-                                         Buf<double>{c->tg});
-  FR_LAUNCH_CHECK(c);
+  const bool visc = c->gas.viscous;
+  FR_ACCOUNT(c, KK_TRACE, (double)c->ne * N * N * fr_flops_trace(N, visc), 0.0);
+  // per element and tangent direction: gradients + traces, 4n face points, n^2 element points
+  FR_ACCOUNT(c, KK_BLOCK, (double)c->ne * c->bsz * FR_JVP_FLOP_FACTOR *
+                              (N * N * (fr_flops_trace(N, visc) + fr_flops_elem(N, visc)) +
+                               4.0 * N * fr_flops_face_point(visc)), 0.0);
+  {
+    FR_PROF_BEGIN(c, s);
+    k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(q)}, c->ne, c->basis,
+                                           c->gas, c->gs, Buf<double>{c->gl}, Buf<double>{c->tq},
+                                           Buf<double>{c->tg});
+    FR_PROF_END(c, s, KK_TRACE);
+    FR_LAUNCH_CHECK(c);
+  }
   const size_t smem = (size_t)BG * BlkSmem<N>::SIZE * sizeof(Dual);
   FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_block<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  FR_PROF_BEGIN(c, s);
   k_block<N><<<c->ne, BG * N * N, smem, s>>>(q, c->mesh, c->basis, c->gas, c->gs, c->gf, c->tq,
                                              c->tg, inv_dtau, a0_dt, c->B64);
+  FR_PROF_END(c, s, KK_BLOCK);
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }
@@ -367,6 +379,9 @@ static int block_build_n(fr_ctx* c, const double* q, double inv_dtau, double a0_
 static int factor(fr_ctx* c, cudaStream_t s) {
   const int bs = c->bsz;
   const int nt = 256;
+  // in-place Gauss-Jordan: bs steps of a rank-1 update of bs^2 entries (2 flops each)
+  FR_ACCOUNT(c, KK_FACTOR, 2.0 * (double)bs * bs * bs * c->ne, 0.0);
+  FR_PROF_BEGIN(c, s);
   if (c->cfg.prec_dtype == FR_PREC_FP64) {
     const size_t smem = (size_t)bs * bs * 8 + bs * 8 + bs * 4 * 2 + bs * 4;
     FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -380,6 +395,7 @@ static int factor(fr_ctx* c, cudaStream_t s) {
     FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<float, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_factor<float, __nv_bfloat16><<<c->ne, nt, smem, s>>>(c->B64, bs, (__nv_bfloat16*)c->Binv, c->Dr, c->Dc, c->info);
   }
+  FR_PROF_END(c, s, KK_FACTOR);
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }
@@ -400,12 +416,17 @@ int block_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaS
 int block_apply(fr_ctx* c, const double* r, double* z, cudaStream_t s) {
   const int bs = c->bsz;
   const int nt = (bs + 31) / 32 * 32;
+  const double esz = c->cfg.prec_dtype == FR_PREC_FP64 ? 8.0 : c->cfg.prec_dtype == FR_PREC_FP32 ? 4.0 : 2.0;
+  FR_ACCOUNT(c, KK_APPLY, 2.0 * (double)bs * bs * c->ne,
+             c->ne * ((double)bs * bs * esz + 2.0 * bs * 4.0) + 2.0 * 8.0 * c->ndof);
+  FR_PROF_BEGIN(c, s);
   if (c->cfg.prec_dtype == FR_PREC_FP64)
     k_apply<double, double><<<c->ne, nt, bs * 8, s>>>((const double*)c->Binv, c->Dr, c->Dc, r, c->ne, c->np2, z);
   else if (c->cfg.prec_dtype == FR_PREC_FP32)
     k_apply<float, float><<<c->ne, nt, bs * 4, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->ne, c->np2, z);
   else
     k_apply<__nv_bfloat16, float><<<c->ne, nt, bs * 4, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->ne, c->np2, z);
+  FR_PROF_END(c, s, KK_APPLY);
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }

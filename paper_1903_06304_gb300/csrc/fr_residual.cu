@@ -128,15 +128,33 @@ template <class T, int N, int MODE>
 static int run_pipeline(fr_ctx* c, Buf<T> Q, Buf<T> GL, Buf<T> TQ, Buf<T> TG, Buf<T> FNb,
                         Buf<T> QCb, double* out, TimeTerms tt, JvpTerms jt, cudaStream_t s) {
   constexpr int EPB = Tile<N>::EPB, TH = Tile<N>::THREADS;
+  constexpr bool jvp = MODE == MODE_JVP;
   const int nblk = (c->ne + EPB - 1) / EPB;
-  k_trace<T, N><<<nblk, TH, 0, s>>>(Q, c->ne, c->basis, c->gas, c->gs, GL, TQ, TG);
-  FR_LAUNCH_CHECK(c);
-  const int nf = c->ne * 2 * N;
-  k_face<T, N><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->basis, c->gas, c->gf, TQ, TG, FNb, QCb);
-  FR_LAUNCH_CHECK(c);
-  k_elem<T, N, MODE><<<nblk, TH, 0, s>>>(Q, c->mesh, c->basis, c->gas, c->gs, c->gf, GL, TQ, FNb,
-                                         QCb, out, tt, jt);
-  FR_LAUNCH_CHECK(c);
+  const bool visc = c->gas.viscous;
+  const double pts = (double)c->ne * N * N, fac = jvp ? FR_JVP_FLOP_FACTOR : 1.0;
+  FR_ACCOUNT(c, jvp ? KK_TRACE_JVP : KK_TRACE, fac * pts * fr_flops_trace(N, visc), 0.0);
+  FR_ACCOUNT(c, jvp ? KK_FACE_JVP : KK_FACE, fac * 2.0 * c->ne * N * fr_flops_face_point(visc), 0.0);
+  FR_ACCOUNT(c, jvp ? KK_ELEM_JVP : KK_ELEM, fac * pts * fr_flops_elem(N, visc), 0.0);
+  {
+    FR_PROF_BEGIN(c, s);
+    k_trace<T, N><<<nblk, TH, 0, s>>>(Q, c->ne, c->basis, c->gas, c->gs, GL, TQ, TG);
+    FR_PROF_END(c, s, jvp ? KK_TRACE_JVP : KK_TRACE);
+    FR_LAUNCH_CHECK(c);
+  }
+  {
+    const int nf = c->ne * 2 * N;
+    FR_PROF_BEGIN(c, s);
+    k_face<T, N><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->basis, c->gas, c->gf, TQ, TG, FNb, QCb);
+    FR_PROF_END(c, s, jvp ? KK_FACE_JVP : KK_FACE);
+    FR_LAUNCH_CHECK(c);
+  }
+  {
+    FR_PROF_BEGIN(c, s);
+    k_elem<T, N, MODE><<<nblk, TH, 0, s>>>(Q, c->mesh, c->basis, c->gas, c->gs, c->gf, GL, TQ, FNb,
+                                           QCb, out, tt, jt);
+    FR_PROF_END(c, s, jvp ? KK_ELEM_JVP : KK_ELEM);
+    FR_LAUNCH_CHECK(c);
+  }
   return FR_OK;
 }
 
@@ -160,11 +178,30 @@ static int jvp_n(fr_ctx* c, const double* q, const double* v, double* out, JvpTe
 
 }  // namespace fr
 
+// ------------------------------------------------------------------ flop counts
+// Itemised in the design notes: thermo 19, viscous flux 18, face common flux 12 (jumps
+// and means) + 81 (two normal fluxes) + 80 (preconditioned dissipation) + 75 (BR2 and
+// viscous flux), element point 19 + 122 (corrected gradient, viscous flux) + 40 (F, G) +
+// 4 (4n + 10) (corrected divergence, GCL term, 1/|J|).
+double fr_flops_trace(int n, bool viscous) {
+  const double grad = viscous ? 16.0 * n + 24.0 : 0.0;
+  return grad + 4.0 * n * (viscous ? 12.0 : 4.0) * (2.0 * n - 1.0) / (n * n);
+}
+double fr_flops_face_point(bool viscous) { return 12.0 + 81.0 + 80.0 + (viscous ? 75.0 : 0.0); }
+double fr_flops_elem(int n, bool viscous) {
+  return 19.0 + (viscous ? 122.0 : 0.0) + 40.0 + 4.0 * (4.0 * n + 10.0);
+}
+// A dual product costs 4 flops (value product, tangent product, fused tangent sum), a
+// dual sum 2, a dual by a constant 2: over the kernels' mix of operations the JVP does
+// about 3x the flops of the residual.
+const double FR_JVP_FLOP_FACTOR = 3.0;
+
 namespace frk {
 using namespace fr;
 
 int geometry(fr_ctx* c, const double* corners, const double* vel, cudaStream_t s) {
   const int th = 64, nb = (c->ne + th - 1) / th;
+  FR_PROF_BEGIN(c, s);
   switch (c->n) {
     case 2: k_geometry<2><<<nb, th, 0, s>>>(corners, vel, c->ne, c->basis, c->gs, c->gf); break;
     case 3: k_geometry<3><<<nb, th, 0, s>>>(corners, vel, c->ne, c->basis, c->gs, c->gf); break;
@@ -172,6 +209,7 @@ int geometry(fr_ctx* c, const double* corners, const double* vel, cudaStream_t s
     case 5: k_geometry<5><<<nb, th, 0, s>>>(corners, vel, c->ne, c->basis, c->gs, c->gf); break;
     default: return FR_ERR_ARG;
   }
+  FR_PROF_END(c, s, KK_GEOM);
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }
@@ -202,7 +240,10 @@ int jvp(fr_ctx* c, const double* q, const double* v, double inv_dtau, double a0_
 
 int conservative(fr_ctx* c, const double* q, double* qc, cudaStream_t s) {
   const size_t SN = (size_t)c->ne * c->np2;
+  FR_ACCOUNT(c, KK_CONS, 0.0, 8.0 * 8.0 * SN);
+  FR_PROF_BEGIN(c, s);
   k_conservative<<<(unsigned)((SN + 255) / 256), 256, 0, s>>>(q, SN, c->gas, qc);
+  FR_PROF_END(c, s, KK_CONS);
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }

@@ -40,12 +40,15 @@ class _Config(ctypes.Structure):
                 ("tol_res", ctypes.c_double), ("tol_pseudo", ctypes.c_double),
                 ("dtau0", ctypes.c_double), ("dtau_min", ctypes.c_double),
                 ("dtau_max", ctypes.c_double), ("r_ser", ctypes.c_double),
-                ("dtau_unsteady", ctypes.c_double), ("gmres_side", ctypes.c_int)]
+                ("dtau_unsteady", ctypes.c_double), ("gmres_side", ctypes.c_int),
+                ("ser_unsteady", ctypes.c_int), ("dtau0_unsteady", ctypes.c_double),
+                ("line_search", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("newton_iterations", ctypes.c_int),
                 ("converged", ctypes.c_int),
+                ("line_search_halvings", ctypes.c_int),
                 ("gmres_iterations", ctypes.c_int * MAX_NEWTON),
                 ("res_history", ctypes.c_double * (MAX_NEWTON + 1)),
                 ("dtau_history", ctypes.c_double * (MAX_NEWTON + 1)),
@@ -57,7 +60,8 @@ class Stats(ctypes.Structure):
                 "gmres_iterations": list(self.gmres_iterations[:n]),
                 "res_history": list(self.res_history[: n + 1]),
                 "dtau_history": list(self.dtau_history[: n + 1]),
-                "block_builds": self.block_builds}
+                "block_builds": self.block_builds,
+                "line_search_halvings": self.line_search_halvings}
 
 
 _lib = None
@@ -87,7 +91,13 @@ _SIGS = {
     "fr_kernel_launches": (ctypes.c_longlong, [_P]),
     "fr_last_error": (ctypes.c_char_p, [_P]),
     "fr_version": (ctypes.c_char_p, []),
+    "fr_profile": (_I, [_P, _I]),
+    "fr_profile_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
+                             ctypes.POINTER(_D), _I]),
+    "fr_profile_name": (ctypes.c_char_p, [_I]),
 }
+PROF_KINDS = 13
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -146,6 +156,9 @@ class Config:
     r_ser: float = 2.0
     dtau_unsteady: float = 1e20
     gmres_side: str = "left"
+    ser_unsteady: int = 0
+    dtau0_unsteady: float = 0.01
+    line_search: int = 0
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -258,6 +271,23 @@ class Solver:
         if not (allow_unconverged and rc == -4):
             self._check(rc)
         return st
+
+    def profile(self, enable: bool):
+        self._check(self.lib.fr_profile(self.ctx, 1 if enable else 0))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        """{kernel class: dict(ms, launches, all_launches, flops, bytes)} since the last reset:
+        device milliseconds and timed launches (while profiling is on), launches since
+        creation, algorithmic flops and DRAM bytes issued."""
+        ms = (ctypes.c_double * PROF_KINDS)()
+        cnt = (ctypes.c_longlong * PROF_KINDS)()
+        tot = (ctypes.c_longlong * PROF_KINDS)()
+        fl = (ctypes.c_double * PROF_KINDS)()
+        by = (ctypes.c_double * PROF_KINDS)()
+        self._check(self.lib.fr_profile_read(self.ctx, ms, cnt, tot, fl, by, 1 if reset else 0))
+        return {self.lib.fr_profile_name(k).decode():
+                dict(ms=ms[k], launches=cnt[k], all_launches=tot[k], flops=fl[k], bytes=by[k])
+                for k in range(PROF_KINDS)}
 
     def residual_norms(self, r, stream=None):
         m, a = ctypes.c_double(), ctypes.c_double()
