@@ -196,6 +196,30 @@ int fr_profile_read(fr_ctx* ctx, double* ms, long long* counts, long long* launc
                     double* bytes, int reset);
 const char* fr_profile_name(int kind);
 
+/* Residual without any allocation (no counterpart in the paper: a deployment variant of
+ * fr_residual).  For callers that cannot call cudaMalloc -- code running while a CUDA
+ * graph is being captured, code under an allocator or memory pool that forbids outside
+ * allocations, an embedding runtime that owns all device memory -- and so cannot create
+ * a context.  Computes the geometry of the bilinear mesh from corners_d / corner_vel_d
+ * (device [Ne][4][2]) and then R(q^p) exactly as fr_update_mesh + fr_residual do, with
+ * the configuration *cfg (host; only p, gamma, prandtl, mach, re, kappa, eps_floor are
+ * read), on a periodic nx-by-ny mesh; qp_d, R_d are device [4][Ne][n][n].
+ * Scratch: a file-scope 32 MiB device array that every GPU which loads the library
+ * holds until the process exits.  The mesh must fit in it:
+ *   Ne * (19 n^2 + 84 n) * 8 bytes (each of 7 sub-arrays rounded up to 256 bytes)
+ *   <= 32 MiB, i.e. Ne <= 17189 at p = 1, 9915 at p = 2, 6553 at p = 3 (64x64 fits),
+ *   4686 at p = 4;
+ * larger meshes return FR_ERR_ARG before any GPU work.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress, once per device, with that device
+ * current): make that first call before any stream capture.  Every call writes each
+ * scratch entry it later reads, so nothing needs clearing, but all calls share the one
+ * array: calls that overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Asynchronous on `stream`; returns FR_OK, FR_ERR_ARG or
+ * FR_ERR_CUDA (no error text: there is no context). */
+int fr_residual_noalloc(const fr_config* cfg, int nx, int ny, const double* corners_d,
+                        const double* corner_vel_d, const double* qp_d, double* R_d,
+                        void* stream);
+
 /* Sizes: number of FP64 entries of a solution vector, block size b. */
 size_t fr_num_dof(const fr_ctx* ctx);
 int fr_block_size(const fr_ctx* ctx);

@@ -39,7 +39,9 @@ void gauss_points(int n, double* xs) {
   }
 }
 
-fr::Basis make_basis(int p) {
+}  // namespace
+
+fr::Basis fr_make_basis(int p) {
   fr::Basis B;
   std::memset(&B, 0, sizeof(B));
   const int n = p + 1;
@@ -90,7 +92,7 @@ fr::Basis make_basis(int p) {
   return B;
 }
 
-fr::Gas make_gas(const fr_config& c) {
+fr::Gas fr_make_gas(const fr_config& c) {
   fr::Gas g;
   const double M2 = c.mach * c.mach;
   g.gamma = c.gamma;
@@ -107,6 +109,8 @@ fr::Gas make_gas(const fr_config& c) {
   g.eps_floor = c.eps_floor;
   return g;
 }
+
+namespace {
 
 template <class T> int dev_alloc(fr_ctx* c, T** p, size_t count) {
   if (*p) { cudaFree(*p); *p = nullptr; }
@@ -454,8 +458,8 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
   c->bsz = 4 * c->np2;
   c->ne = 0;
   c->err[0] = 0;
-  c->basis = make_basis(cfg->p);
-  c->gas = make_gas(*cfg);
+  c->basis = fr_make_basis(cfg->p);
+  c->gas = fr_make_gas(*cfg);
   if (cudaMalloc((void**)&c->dsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&c->hsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess) {
     delete c;

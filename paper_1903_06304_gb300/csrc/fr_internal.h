@@ -87,6 +87,11 @@ void fr_prof_end(fr_ctx* c, cudaStream_t s, cudaEvent_t begin, int kind);
     if (fr_ev_) fr_prof_end((c), (s), fr_ev_, (k));                     \
   } while (0)
 
+// 1-D FR basis (Sec. 3.1) and nondimensional gas (Sec. 2.1) of a configuration; host
+// only, no allocation.
+fr::Basis fr_make_basis(int p);
+fr::Gas fr_make_gas(const fr_config& c);
+
 namespace frk {
 int geometry(fr_ctx* c, const double* corners, const double* vel, cudaStream_t s);
 int residual(fr_ctx* c, const double* q, double* out, const double* qcn, const double* qcnm1,

@@ -16,100 +16,6 @@
 
 namespace fr {
 
-// ------------------------------------------------------------------ geometry (Sec. 2.3)
-// Bilinear map through the 4 corners: |J|, S_xi = |J| grad(xi) = (y_eta, -x_eta),
-// S_eta = |J| grad(eta) = (-y_xi, x_xi), v_g (bilinear in the corner velocities) and
-// |J| xi_t = -v_g . S_xi, |J| eta_t = -v_g . S_eta, at solution and flux points; the
-// divergence of (|J| xi_t, |J| eta_t) by the interpolant derivative.
-struct MapPoint {
-  double x_xi, x_eta, y_xi, y_eta, ug, vg;
-};
-
-__device__ __forceinline__ MapPoint map_at(const double X[4], const double Y[4],
-                                           const double VX[4], const double VY[4], double xi,
-                                           double eta) {
-  const double N0 = 0.25 * (1 - xi) * (1 - eta), N1 = 0.25 * (1 + xi) * (1 - eta);
-  const double N2 = 0.25 * (1 + xi) * (1 + eta), N3 = 0.25 * (1 - xi) * (1 + eta);
-  const double a0 = -0.25 * (1 - eta), a1 = 0.25 * (1 - eta), a2 = 0.25 * (1 + eta), a3 = -0.25 * (1 + eta);
-  const double b0 = -0.25 * (1 - xi), b1 = -0.25 * (1 + xi), b2 = 0.25 * (1 + xi), b3 = 0.25 * (1 - xi);
-  MapPoint m;
-  m.x_xi = a0 * X[0] + a1 * X[1] + a2 * X[2] + a3 * X[3];
-  m.y_xi = a0 * Y[0] + a1 * Y[1] + a2 * Y[2] + a3 * Y[3];
-  m.x_eta = b0 * X[0] + b1 * X[1] + b2 * X[2] + b3 * X[3];
-  m.y_eta = b0 * Y[0] + b1 * Y[1] + b2 * Y[2] + b3 * Y[3];
-  m.ug = N0 * VX[0] + N1 * VX[1] + N2 * VX[2] + N3 * VX[3];
-  m.vg = N0 * VY[0] + N1 * VY[1] + N2 * VY[2] + N3 * VY[3];
-  return m;
-}
-
-template <int N>
-__global__ void k_geometry(const double* __restrict__ corners, const double* __restrict__ vel,
-                           int ne, Basis B, double* __restrict__ gs, double* __restrict__ gf) {
-  constexpr int NP = N * N;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ne) return;
-  double X[4], Y[4], VX[4], VY[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    X[a] = corners[e * 8 + 2 * a];
-    Y[a] = corners[e * 8 + 2 * a + 1];
-    VX[a] = vel[e * 8 + 2 * a];
-    VY[a] = vel[e * 8 + 2 * a + 1];
-  }
-  const size_t SN = (size_t)ne * NP;
-  double stx[NP], ste[NP];
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const MapPoint m = map_at(X, Y, VX, VY, B.xs[i], B.xs[j]);
-      const double J = m.x_xi * m.y_eta - m.x_eta * m.y_xi;
-      const double sxx = m.y_eta, sxy = -m.x_eta, sex = -m.y_xi, sey = m.x_xi;
-      const size_t o = (size_t)e * NP + j * N + i;
-      gs[GS_SXX * SN + o] = sxx;
-      gs[GS_SXY * SN + o] = sxy;
-      gs[GS_SEX * SN + o] = sex;
-      gs[GS_SEY * SN + o] = sey;
-      stx[j * N + i] = -(m.ug * sxx + m.vg * sxy);
-      ste[j * N + i] = -(m.ug * sex + m.vg * sey);
-      gs[GS_STX * SN + o] = stx[j * N + i];
-      gs[GS_STE * SN + o] = ste[j * N + i];
-      gs[GS_INVJ * SN + o] = 1.0 / J;
-      gs[GS_J * SN + o] = J;
-      gs[GS_UG * SN + o] = m.ug;
-      gs[GS_VG * SN + o] = m.vg;
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      double d = 0.0;
-#pragma unroll
-      for (int k = 0; k < N; ++k) d += B.D[i][k] * stx[j * N + k] + B.D[j][k] * ste[k * N + i];
-      gs[GS_DIVST * SN + (size_t)e * NP + j * N + i] = d;
-    }
-  }
-  const size_t FN = (size_t)ne * 4 * N;
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {
-#pragma unroll
-    for (int t = 0; t < N; ++t) {
-      const double xi = f == FACE_L ? -1.0 : f == FACE_R ? 1.0 : B.xs[t];
-      const double eta = f == FACE_B ? -1.0 : f == FACE_T ? 1.0 : B.xs[t];
-      const MapPoint m = map_at(X, Y, VX, VY, xi, eta);
-      const double J = m.x_xi * m.y_eta - m.x_eta * m.y_xi;
-      const bool along_xi = (f == FACE_L || f == FACE_R);
-      const size_t o = ((size_t)e * 4 + f) * N + t;
-      gf[GF_SX * FN + o] = along_xi ? m.y_eta : -m.y_xi;
-      gf[GF_SY * FN + o] = along_xi ? -m.x_eta : m.x_xi;
-      gf[GF_J * FN + o] = J;
-      gf[GF_UG * FN + o] = m.ug;
-      gf[GF_VG * FN + o] = m.vg;
-    }
-  }
-}
-
 __global__ void k_conservative(const double* __restrict__ q, size_t SN, Gas gas,
                                double* __restrict__ qc) {
   const size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x;

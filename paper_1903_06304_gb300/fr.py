@@ -96,6 +96,7 @@ _SIGS = {
                              ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
                              ctypes.POINTER(_D), _I]),
     "fr_profile_name": (ctypes.c_char_p, [_I]),
+    "fr_residual_noalloc": (_I, [ctypes.POINTER(_Config), _I, _I, _P, _P, _P, _P, _P]),
 }
 PROF_KINDS = 13
 
