@@ -46,8 +46,11 @@ UNIT = "GDOF/s"
 FP64_PEAK_TFLOPS = 1.20
 FP32_PEAK_TFLOPS = 70.3
 ALU_PEAK_SOURCE = "FMA-throughput probe on this pool's GB300 (nominal from unit counts x clock: 1.26 FP64, 80.5 FP32)"
+# Bound of each kernel class as ncu measured it: every FP64 kernel, the Gram-Schmidt
+# reductions and vector updates included, saturates the FP64 pipe (1 FMA per 8 bytes
+# needs 1.7 TFLOP/s at full HBM bandwidth); the FP32/BF16 block apply streams DRAM.
 ALU_KINDS = {"trace", "face", "elem", "trace_jvp", "face_jvp", "elem_jvp", "block_jacobian",
-             "block_factor", "geometry"}
+             "block_factor", "geometry", "krylov_reduce", "vector"}
 
 
 def hbm_peak():
@@ -270,7 +273,7 @@ def gpu_arm(args):
         e = {"ms_total": v["ms"], "launches": v["launches"],
              "us_per_launch": 1e3 * v["ms"] / v["launches"],
              "share": v["ms"] / tot_ms if tot_ms else None}
-        if name in ALU_KINDS:
+        if name in ALU_KINDS or (name == "block_apply" and args.prec == "fp64"):
             fp32 = name == "block_factor" and args.prec != "fp64"
             peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
             e.update(bound="alu", pipe="fp32" if fp32 else "fp64", unit="TFLOP/s",
