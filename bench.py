@@ -50,7 +50,8 @@ ALU_PEAK_SOURCE = "FMA-throughput probe on this machine's GB300 (nominal from unit 
 # reductions and vector updates included, saturates the FP64 pipe (1 FMA per 8 bytes
 # needs 1.7 TFLOP/s at full HBM bandwidth); the FP32/BF16 block apply streams DRAM.
 ALU_KINDS = {"trace", "face", "elem", "trace_jvp", "face_jvp", "elem_jvp", "block_jacobian",
-             "block_factor", "geometry", "krylov_reduce", "vector"}
+             "block_factor", "geometry", "krylov_reduce", "vector", "linearize", "linear_apply",
+             "linear_adjoint"}
 
 
 def hbm_peak():
@@ -304,6 +305,9 @@ def gpu_arm(args):
 
     t_res = time_calls(lambda: S.residual(run.q, out))
     t_jvp = time_calls(lambda: S.jvp(run.q, vec, out, 1e-20, 1.5 / w.dt))
+    t_lin = time_calls(lambda: S.linearize(run.q, 1e-20, 1.5 / w.dt), reps=5)
+    t_app = time_calls(lambda: S.apply_linear(vec, out))
+    t_vjp = time_calls(lambda: S.apply_linear(vec, out, transpose=True))
 
     # ---- precision comparison: a few steps from the same state per block precision
     compare = {}
@@ -392,6 +396,9 @@ def gpu_arm(args):
         "res_drop_last": last["res_history"][-1] / last["res_history"][0],
         "residual_gdofs": dof / (t_res * 1e-3) / 1e9,
         "jvp_gdofs": dof / (t_jvp * 1e-3) / 1e9,
+        "linearized_jvp_gdofs": dof / (t_app * 1e-3) / 1e9,
+        "vjp_gdofs": dof / (t_vjp * 1e-3) / 1e9,
+        "linearize_ms": t_lin,
         "precision_compare": compare,
         "kernels": kernels,
         "roofline": roof,

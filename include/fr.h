@@ -64,6 +64,10 @@ typedef struct fr_ctx fr_ctx;
  * ser_unsteady: if nonzero, BDF2 pseudo-loops start at dtau0_unsteady and adapt dtau by
  * the SER law (Eq. SER, same dtau_min/dtau_max/r_ser) instead of the fixed step, with the
  * blocks rebuilt at every pseudo-iteration (pseudo-transient continuation);
+ * jvp_mode: how GMRES applies the Newton operator: FR_JVP_LINEARIZED (default) stores
+ * the local Jacobians once per Newton iteration (fr_linearize) and applies them, or
+ * FR_JVP_DUAL re-evaluates the residual over dual numbers for every product (fr_jvp);
+ * both are exact and agree to rounding;
  * line_search: 0 = plain Newton updates (the paper); k > 0 = backtracking: the update
  * q + lambda dq is tried with lambda = 1, 1/2, ..., 2^-k and the first lambda that lowers
  * the full 2-norm of the pseudo-step residual is kept (the last one otherwise);
@@ -71,6 +75,8 @@ typedef struct fr_ctx fr_ctx;
  * tol_res relative to ||B^-1 b||) or FR_GMRES_RIGHT (Krylov space of A B^-1, tol_res
  * relative to ||b||). */
 #define FR_MAX_RESTART 256
+#define FR_JVP_DUAL 0
+#define FR_JVP_LINEARIZED 1
 #define FR_GMRES_LEFT 0
 #define FR_GMRES_RIGHT 1
 typedef struct fr_config {
@@ -84,6 +90,7 @@ typedef struct fr_config {
   int ser_unsteady;
   double dtau0_unsteady;
   int line_search;
+  int jvp_mode;
 } fr_config;
 
 /* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).
@@ -148,6 +155,24 @@ int fr_conservative(fr_ctx* ctx, const double* qp_d, double* qc_d, void* stream)
 int fr_jvp(fr_ctx* ctx, const double* qp_d, const double* v_d, double inv_dtau, double a0_dt,
            double* Av_d, void* stream);
 
+/* Store the Newton operator's local Jacobians at q (forward mode, one dual direction per
+ * local input): the face map (q-, q+, grad q-, grad q+) -> F^num at every owned flux
+ * point, the point map (q, corrected grad q) -> (F, G) at every solution point, and the
+ * point matrix Gamma/dtau + a0_dt M - (1/|J|) div(|J| xi_t, |J| eta_t) M.  The linear maps
+ * (gradients, traces, liftings, corrected divergence) are fixed by basis and geometry.
+ * Overwrites the previous linearisation. */
+int fr_linearize(fr_ctx* ctx, const double* qp_d, double inv_dtau, double a0_dt, void* stream);
+/* out = A v (transpose = 0) or A^T v (transpose = 1) with the stored linearisation; A as
+ * in fr_jvp.  FR_ERR_ARG if fr_linearize has not been called. */
+int fr_apply_linear(fr_ctx* ctx, const double* v_d, double* out_d, int transpose, void* stream);
+/* Reverse-mode product (the adjoint of fr_jvp): out = A^T w at state q, i.e.
+ * (Gamma/dtau + a0_dt M)^T w - (dR/dq^p)^T w; inv_dtau = a0_dt = 0 gives -(dR/dq)^T w.
+ * Linearises at q (overwriting the stored linearisation) and applies the transposed
+ * factors in reverse order (elements, faces, traces); no face state is stored beyond
+ * the local Jacobians. */
+int fr_vjp(fr_ctx* ctx, const double* qp_d, const double* w_d, double inv_dtau, double a0_dt,
+           double* out_d, void* stream);
+
 /* Build the element block-Jacobi preconditioner at q (Sec. 4 parallel setting, element
  * blocks replacing per-process ILU(0)):
  * B_e = Gamma_e/dtau + a0_dt M_e - dR_e/dq_e (neighbours frozen), then factor it in the
@@ -190,7 +215,7 @@ int fr_residual_norms(fr_ctx* ctx, const double* r_d, double* res_mass, double* 
  * launches issued since the last reset (both counted whether or not timing is on);
  * reset != 0 clears the timing and the algorithmic totals.  Any output pointer may be
  * NULL.  fr_profile_name(k) names class k. */
-#define FR_PROF_KINDS 13
+#define FR_PROF_KINDS 16
 int fr_profile(fr_ctx* ctx, int enable);
 int fr_profile_read(fr_ctx* ctx, double* ms, long long* counts, long long* launches, double* flops,
                     double* bytes, int reset);

@@ -143,6 +143,24 @@ def block_jacobian(prob: Problem, q, inv_dtau: float, a0_dt: float):
     return B
 
 
+def dense_operator(prob: Problem, q, inv_dtau: float, a0_dt: float):
+    """The Newton operator A = Gamma/dtau + (a0/dt) M - dR/dq as a dense matrix, one column
+    per unknown (complex steps); small meshes only."""
+    nd = q.size
+    A = np.zeros((nd, nd))
+    for k in range(nd):
+        e = np.zeros(nd)
+        e[k] = 1.0
+        A[:, k] = apply_A(prob, q, e.reshape(q.shape), inv_dtau, a0_dt).ravel()
+    return A
+
+
+def vjp(prob: Problem, q, w, inv_dtau: float, a0_dt: float):
+    """A^T w by its definition: the transpose of the dense operator (small meshes)."""
+    A = dense_operator(prob, q, inv_dtau, a0_dt)
+    return (A.T @ w.ravel()).reshape(q.shape)
+
+
 def block_apply(Binv, r):
     """z_e = B_e^{-1} r_e for [4, Ne, n, n] vectors."""
     ne, bsz, _ = Binv.shape

@@ -122,7 +122,8 @@ template <class T> int dev_alloc(fr_ctx* c, T** p, size_t count) {
 void free_mesh(fr_ctx* c) {
   double** ds[] = {&c->gs, &c->gf, &c->tq, &c->tg, &c->gl, &c->fn, &c->qcm, &c->tq_d, &c->tg_d,
                    &c->gl_d, &c->fn_d, &c->qcm_d, &c->B64, &c->V, &c->w_r, &c->w_z, &c->w_x,
-                   &c->w_t, &c->w_u, &c->red};
+                   &c->w_t, &c->w_u, &c->red, &c->JFQ, &c->JFG, &c->JP, &c->JG, &c->PP,
+                   &c->adj_q, &c->adj_fn, &c->adj_qc};
   for (double** p : ds) if (*p) { cudaFree(*p); *p = nullptr; }
   if (c->Binv) { cudaFree(c->Binv); c->Binv = nullptr; }
   if (c->Dr) { cudaFree(c->Dr); c->Dr = nullptr; }
@@ -130,6 +131,7 @@ void free_mesh(fr_ctx* c) {
   if (c->info) { cudaFree(c->info); c->info = nullptr; }
   if (c->ticket) { cudaFree(c->ticket); c->ticket = nullptr; }
   c->blocks_ready = 0;
+  c->lin_ready = 0;
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -194,6 +196,14 @@ int cgs2(fr_ctx* c, int nv, double* w, cudaStream_t s) {
 // Layout of the device scalar area dsc (M = FR_MAX_RESTART): [0,M) first projections,
 // [M,2M) second projections, [2M] squared norm, [3M,4M) Krylov coefficients y,
 // [4M, 4M+2) norms.
+// The Newton operator applied inside GMRES: the stored linearisation (default) or the
+// dual-number JVP at q.
+int op_apply(fr_ctx* c, const double* q, const double* x, double inv_dtau, double a0_dt,
+             double* out, cudaStream_t s) {
+  if (c->cfg.jvp_mode == FR_JVP_LINEARIZED) return frk::apply_linear(c, x, out, false, s);
+  return frk::jvp(c, q, x, inv_dtau, a0_dt, out, s);
+}
+
 int gmres_solve(fr_ctx* c, const double* q, const double* b, double inv_dtau, double a0_dt,
                 double* x, int* iters, cudaStream_t s) {
   const size_t N = c->ndof;
@@ -223,11 +233,11 @@ int gmres_solve(fr_ctx* c, const double* q, const double* b, double inv_dtau, do
       double* Vj = c->V + (size_t)j * N;
       double* w = c->V + (size_t)(j + 1) * N;
       if (left) {
-        FR_TRY(frk::jvp(c, q, Vj, inv_dtau, a0_dt, c->w_z, s));
+        FR_TRY(op_apply(c, q, Vj, inv_dtau, a0_dt, c->w_z, s));
         FR_TRY(frk::block_apply(c, c->w_z, w, s));
       } else {
         FR_TRY(frk::block_apply(c, Vj, c->w_z, s));
-        FR_TRY(frk::jvp(c, q, c->w_z, inv_dtau, a0_dt, w, s));
+        FR_TRY(op_apply(c, q, c->w_z, inv_dtau, a0_dt, w, s));
       }
       FR_TRY(cgs2(c, j + 1, w, s));
       FR_CUDA_CHECK(c, cudaMemcpyAsync(c->hsc, c->dsc, (2 * FR_MAX_RESTART + 1) * sizeof(double),
@@ -270,7 +280,7 @@ int gmres_solve(fr_ctx* c, const double* q, const double* b, double inv_dtau, do
       FR_TRY(frk::axpby(c, 1.0, c->w_z, 1.0, x, s));
     }
     // residual of the restart: b - A x (left: preconditioned)
-    FR_TRY(frk::jvp(c, q, x, inv_dtau, a0_dt, c->w_t, s));
+    FR_TRY(op_apply(c, q, x, inv_dtau, a0_dt, c->w_t, s));
     FR_TRY(frk::axpby(c, 1.0, b, -1.0, c->w_t, s));
     if (left) FR_TRY(frk::block_apply(c, c->w_t, r, s));
     else FR_CUDA_CHECK(c, cudaMemcpyAsync(r, c->w_t, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -314,6 +324,7 @@ int newton_loop(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, do
       st->block_builds++;
     }
     int its = 0;
+    if (c->cfg.jvp_mode == FR_JVP_LINEARIZED) FR_TRY(frk::linearize(c, q, inv_dtau, a0dt, s));
     FR_TRY(gmres_solve(c, q, r, inv_dtau, a0dt, c->w_x, &its, s));
     st->gmres_iterations[m] = its;
     const double prev = rm, prev_all = ra;
@@ -343,7 +354,8 @@ int newton_loop(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, do
 
 const char* kKernelNames[KK_COUNT] = {
     "geometry", "trace", "face", "elem", "trace_jvp", "face_jvp", "elem_jvp", "block_jacobian",
-    "block_factor", "block_apply", "krylov_reduce", "vector", "conservative"};
+    "block_factor", "block_apply", "krylov_reduce", "vector", "conservative", "linearize",
+    "linear_apply", "linear_adjoint"};
 
 // Fold the recorded event pairs into the per-kind totals (synchronises on the events).
 int prof_collect(fr_ctx* c) {
@@ -441,6 +453,7 @@ void fr_default_config(fr_config* c) {
   c->ser_unsteady = 0;
   c->dtau0_unsteady = 0.01;
   c->line_search = 0;
+  c->jvp_mode = FR_JVP_LINEARIZED;
 }
 
 int fr_create(const fr_config* cfg, fr_ctx** out) {
@@ -448,7 +461,8 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
   *out = nullptr;
   if (cfg->p < 1 || cfg->p > 4 || cfg->mach <= 0 || cfg->gamma <= 1.0 || cfg->restart < 1 ||
       cfg->restart > FR_MAX_RESTART || cfg->prec_dtype < 0 || cfg->prec_dtype > 2 ||
-      (cfg->gmres_side != FR_GMRES_LEFT && cfg->gmres_side != FR_GMRES_RIGHT))
+      (cfg->gmres_side != FR_GMRES_LEFT && cfg->gmres_side != FR_GMRES_RIGHT) ||
+      (cfg->jvp_mode != FR_JVP_DUAL && cfg->jvp_mode != FR_JVP_LINEARIZED))
     return FR_ERR_ARG;
   fr_ctx* c = new fr_ctx();
   c->cfg = *cfg;
@@ -517,6 +531,15 @@ int fr_set_mesh(fr_ctx* c, int nx, int ny, int px, int py) {
   FR_TRY(dev_alloc(c, &c->w_t, c->ndof));
   FR_TRY(dev_alloc(c, &c->w_u, c->ndof));
   FR_TRY(dev_alloc(c, &c->red, (size_t)32 * c->red_blocks));
+  const size_t nfp = ne * 2 * n;
+  FR_TRY(dev_alloc(c, &c->JFQ, 32 * nfp));
+  FR_TRY(dev_alloc(c, &c->JFG, 64 * nfp));
+  FR_TRY(dev_alloc(c, &c->JP, 32 * ne * np2));
+  FR_TRY(dev_alloc(c, &c->JG, 64 * ne * np2));
+  FR_TRY(dev_alloc(c, &c->PP, 16 * ne * np2));
+  FR_TRY(dev_alloc(c, &c->adj_q, c->ndof));
+  FR_TRY(dev_alloc(c, &c->adj_fn, ne * 16 * n));
+  FR_TRY(dev_alloc(c, &c->adj_qc, ne * 16 * n));
   FR_TRY(dev_alloc(c, &c->ticket, 1));
   FR_CUDA_CHECK(c, cudaMemset(c->ticket, 0, sizeof(unsigned int)));
   return FR_OK;
@@ -551,6 +574,26 @@ int fr_jvp(fr_ctx* c, const double* q, const double* v, double inv_dtau, double 
   return frk::jvp(c, q, v, inv_dtau, a0_dt, Av, S(s));
 }
 
+int fr_linearize(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, void* s) {
+  FR_TRY(check_ready(c));
+  if (!q) return FR_ERR_ARG;
+  return frk::linearize(c, q, inv_dtau, a0_dt, S(s));
+}
+
+int fr_apply_linear(fr_ctx* c, const double* v, double* out, int transpose, void* s) {
+  FR_TRY(check_ready(c));
+  if (!v || !out) return FR_ERR_ARG;
+  return frk::apply_linear(c, v, out, transpose != 0, S(s));
+}
+
+int fr_vjp(fr_ctx* c, const double* q, const double* w, double inv_dtau, double a0_dt, double* out,
+           void* s) {
+  FR_TRY(check_ready(c));
+  if (!q || !w || !out) return FR_ERR_ARG;
+  FR_TRY(frk::linearize(c, q, inv_dtau, a0_dt, S(s)));
+  return frk::apply_linear(c, w, out, true, S(s));
+}
+
 int fr_precond_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, void* s) {
   FR_TRY(check_ready(c));
   FR_TRY(frk::block_build(c, q, inv_dtau, a0_dt, S(s)));
@@ -576,6 +619,7 @@ int fr_gmres(fr_ctx* c, const double* q, const double* b, double inv_dtau, doubl
              int* iters, void* s) {
   FR_TRY(check_ready(c));
   if (!c->blocks_ready) { snprintf(c->err, sizeof(c->err), "no preconditioner built"); return FR_ERR_ARG; }
+  if (c->cfg.jvp_mode == FR_JVP_LINEARIZED) FR_TRY(frk::linearize(c, q, inv_dtau, a0_dt, S(s)));
   int its = 0;
   FR_TRY(gmres_solve(c, q, b, inv_dtau, a0_dt, x, &its, S(s)));
   if (iters) *iters = its;

@@ -10,7 +10,8 @@
 // Kernel classes for the optional per-kernel timing (fr_profile) and launch counts.
 enum FrKernel {
   KK_GEOM, KK_TRACE, KK_FACE, KK_ELEM, KK_TRACE_JVP, KK_FACE_JVP, KK_ELEM_JVP, KK_BLOCK,
-  KK_FACTOR, KK_APPLY, KK_KRYLOV, KK_VECTOR, KK_CONS, KK_COUNT
+  KK_FACTOR, KK_APPLY, KK_KRYLOV, KK_VECTOR, KK_CONS, KK_LINEARIZE, KK_LIN_APPLY,
+  KK_LIN_ADJOINT, KK_COUNT
 };
 
 struct FrProfPair {
@@ -47,6 +48,11 @@ struct fr_ctx {
   float* Dc = nullptr;       // [Ne][b] column scales
   int* info = nullptr;       // [Ne] singular flags
   int blocks_ready = 0;
+  // stored local Jacobians of the Newton operator (fr_linear.cu)
+  double *JFQ = nullptr, *JFG = nullptr;           // face map: [32|64][Ne*2n]
+  double *JP = nullptr, *JG = nullptr, *PP = nullptr;  // point map: [32|64|16][Ne*n^2]
+  double *adj_q = nullptr, *adj_fn = nullptr, *adj_qc = nullptr;  // transpose work
+  int lin_ready = 0;
   // Krylov workspace
   double* V = nullptr;       // [(m+1)][ndof]
   double *w_r = nullptr, *w_z = nullptr, *w_x = nullptr, *w_t = nullptr, *w_u = nullptr;
@@ -101,6 +107,8 @@ int jvp(fr_ctx* c, const double* q, const double* v, double inv_dtau, double a0_
 int conservative(fr_ctx* c, const double* q, double* qc, cudaStream_t s);
 int block_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s);
 int block_apply(fr_ctx* c, const double* r, double* z, cudaStream_t s);
+int linearize(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s);
+int apply_linear(fr_ctx* c, const double* v, double* out, bool transpose, cudaStream_t s);
 // Krylov primitives (deterministic reductions over a fixed grid)
 int dots(fr_ctx* c, const double* V, int nv, const double* w, double* out_dev, cudaStream_t s);
 int axpy_dots(fr_ctx* c, const double* V, int nv, const double* h_dev, double* w, double* out_dev,

@@ -42,7 +42,7 @@ class _Config(ctypes.Structure):
                 ("dtau_max", ctypes.c_double), ("r_ser", ctypes.c_double),
                 ("dtau_unsteady", ctypes.c_double), ("gmres_side", ctypes.c_int),
                 ("ser_unsteady", ctypes.c_int), ("dtau0_unsteady", ctypes.c_double),
-                ("line_search", ctypes.c_int)]
+                ("line_search", ctypes.c_int), ("jvp_mode", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -97,8 +97,11 @@ _SIGS = {
                              ctypes.POINTER(_D), _I]),
     "fr_profile_name": (ctypes.c_char_p, [_I]),
     "fr_residual_noalloc": (_I, [ctypes.POINTER(_Config), _I, _I, _P, _P, _P, _P, _P]),
+    "fr_linearize": (_I, [_P, _P, _D, _D, _P]),
+    "fr_apply_linear": (_I, [_P, _P, _P, _I, _P]),
+    "fr_vjp": (_I, [_P, _P, _P, _D, _D, _P, _P]),
 }
-PROF_KINDS = 13
+PROF_KINDS = 16
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -160,6 +163,7 @@ class Config:
     ser_unsteady: int = 0
     dtau0_unsteady: float = 0.01
     line_search: int = 0
+    jvp_mode: str = "linearized"
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -169,6 +173,8 @@ class Config:
                 c.prec_dtype = PREC[self.prec]
             elif f.name == "gmres_side":
                 c.gmres_side = {"left": 0, "right": 1}[self.gmres_side]
+            elif f.name == "jvp_mode":
+                c.jvp_mode = {"dual": 0, "linearized": 1}[self.jvp_mode]
             else:
                 setattr(c, f.name, getattr(self, f.name))
         return c
@@ -239,6 +245,19 @@ class Solver:
                                     _stream(stream)))
         return out
 
+    def linearize(self, q, inv_dtau=0.0, a0_dt=0.0, stream=None):
+        self._check(self.lib.fr_linearize(self.ctx, _ptr(q), inv_dtau, a0_dt, _stream(stream)))
+
+    def apply_linear(self, v, out, transpose=False, stream=None):
+        self._check(self.lib.fr_apply_linear(self.ctx, _ptr(v), _ptr(out), 1 if transpose else 0,
+                                             _stream(stream)))
+        return out
+
+    def vjp(self, q, w, out, inv_dtau=0.0, a0_dt=0.0, stream=None):
+        self._check(self.lib.fr_vjp(self.ctx, _ptr(q), _ptr(w), inv_dtau, a0_dt, _ptr(out),
+                                    _stream(stream)))
+        return out
+
     def precond_build(self, q, inv_dtau=0.0, a0_dt=0.0, stream=None):
         self._check(self.lib.fr_precond_build(self.ctx, _ptr(q), inv_dtau, a0_dt, _stream(stream)))
 
@@ -295,3 +314,27 @@ class Solver:
         self._check(self.lib.fr_residual_norms(self.ctx, _ptr(r), ctypes.byref(m), ctypes.byref(a),
                                                _stream(stream)))
         return m.value, a.value
+
+
+def residual_function():
+    """A torch.autograd.Function computing R(q^p) with a Solver; its backward is the
+    library's reverse-mode product (fr_vjp), dR/dq^T g = -(A^T g) at inv_dtau = a0_dt = 0."""
+    import torch
+
+    class Residual(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, q, solver):
+            out = torch.empty_like(q)
+            solver.residual(q.contiguous(), out)
+            ctx.save_for_backward(q)
+            ctx.solver = solver
+            return out
+
+        @staticmethod
+        def backward(ctx, grad):
+            (q,) = ctx.saved_tensors
+            out = torch.empty_like(q)
+            ctx.solver.vjp(q.contiguous(), grad.contiguous(), out, 0.0, 0.0)
+            return -out, None
+
+    return Residual

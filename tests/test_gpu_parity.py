@@ -87,6 +87,89 @@ def test_jvp_parity(torch, cfg):
         assert np.all(err <= JVP_TOL), (inv_dtau, a0_dt, err)
 
 
+@pytest.mark.parametrize("cfg", CASES)
+def test_linearized_operator_matches_dual_jvp_and_oracle(torch, cfg):
+    """fr_linearize + fr_apply_linear (stored local Jacobians) equals the dual-number JVP
+    and the oracle's complex-step operator."""
+    nx, ny, p, mach, re, kappa, deforming = cfg
+    c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
+    prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
+    w = inp.random_vector(q.shape, 9)
+    w[0] *= prob.gas.R * 1e-2
+    S = solver_for(c, v, nx, ny, p, mach, re, kappa)
+    qd, wd = to_dev(q), to_dev(w)
+    lin = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+    dual = torch.empty_like(lin)
+    for inv_dtau, a0_dt in ((0.0, 0.0), (0.5, 150.0)):
+        S.linearize(qd, inv_dtau, a0_dt)
+        S.apply_linear(wd, lin)
+        S.jvp(qd, wd, dual, inv_dtau, a0_dt)
+        want = sv.apply_A(prob, q, w, inv_dtau, a0_dt)
+        assert np.all(jvp_errors(to_host(lin), want) <= JVP_TOL)
+        assert np.all(jvp_errors(to_host(lin), to_host(dual)) <= JVP_TOL)
+
+
+@pytest.mark.parametrize("cfg", CASES)
+def test_vjp_dot_product_identity(torch, cfg):
+    """<w, A v> = <A^T w, v> for the GPU forward and reverse products at the same state."""
+    nx, ny, p, mach, re, kappa, deforming = cfg
+    c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
+    S = solver_for(c, v, nx, ny, p, mach, re, kappa)
+    qd = to_dev(q)
+    rng = np.random.default_rng(31)
+    for inv_dtau, a0_dt in ((0.0, 0.0), (0.5, 150.0)):
+        S.linearize(qd, inv_dtau, a0_dt)
+        for _ in range(3):
+            x = to_dev(rng.standard_normal(q.shape))
+            y = to_dev(rng.standard_normal(q.shape))
+            Ax = torch.empty_like(x)
+            ATy = torch.empty_like(x)
+            S.apply_linear(x, Ax)
+            S.apply_linear(y, ATy, transpose=True)
+            lhs = float((y * Ax).sum())
+            rhs = float((ATy * x).sum())
+            scale = float(y.norm() * Ax.norm())
+            assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
+
+
+@pytest.mark.parametrize("cfg", [CASES[i] for i in (0, 1, 3, 6)])
+def test_vjp_parity_dense_oracle(torch, cfg):
+    """fr_vjp against the transpose of the oracle's dense operator (small meshes)."""
+    nx, ny, p, mach, re, kappa, deforming = cfg
+    if nx * ny * (p + 1) ** 2 > 200:
+        nx, ny = 2, 2
+    c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
+    prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
+    w = inp.random_vector(q.shape, 12)
+    S = solver_for(c, v, nx, ny, p, mach, re, kappa)
+    out = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+    for inv_dtau, a0_dt in ((0.0, 0.0), (0.5, 150.0)):
+        S.vjp(to_dev(q), to_dev(w), out, inv_dtau, a0_dt)
+        want = sv.vjp(prob, q, w, inv_dtau, a0_dt)
+        err = np.abs(to_host(out) - want).max(axis=(1, 2, 3)) / np.abs(want).max(axis=(1, 2, 3))
+        assert np.all(err <= 1e-11), err
+
+
+def test_autograd_residual_gradient(torch):
+    """torch.autograd through the library: d<c, R(q)>/dq equals the oracle's transpose
+    product, and matches the forward-mode directional derivative."""
+    from paper_1903_06304_gb300 import fr
+    nx, ny, p, mach, re, kappa, deforming = 3, 2, 2, 0.05, 10.0, 1.0, True
+    c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
+    prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
+    S = solver_for(c, v, nx, ny, p, mach, re, kappa)
+    cvec = inp.random_vector(q.shape, 41)
+    qd = to_dev(q).requires_grad_(True)
+    R = fr.residual_function().apply(qd, S)
+    (R * to_dev(cvec)).sum().backward()
+    got = to_host(qd.grad)
+    want = -sv.vjp(prob, q, cvec, 0.0, 0.0)
+    assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+    d = inp.random_vector(q.shape, 42)
+    jv = -sv.apply_A(prob, q, d, 0.0, 0.0)
+    assert abs(float((got * d).sum()) - float((cvec * jv).sum())) <= 1e-11 * np.linalg.norm(got) * np.linalg.norm(d)
+
+
 def test_jvp_of_zero_vector_is_zero(torch):
     c, v, q = case(5, 4, 3, 0.05, 10.0, 1.0, True)
     S = solver_for(c, v, 5, 4, 3, 0.05, 10.0, 1.0)

@@ -216,3 +216,21 @@ def test_ptc_ser_on_gaussian_bump():
     for m in range(1, len(st.dtau_history)):
         want = min(1e20, max(0.01, st.dtau_history[m - 1] * (res[m - 1] / res[m]) ** 2))
         assert abs(st.dtau_history[m] - want) <= 1e-12 * want
+
+
+def test_dense_operator_columns_match_jvp_and_fd():
+    """The dense operator used for the transpose product agrees with the JVP on random
+    vectors and with central differences of the residual (independent of complex steps)."""
+    prob, q = _small_problem(p=1, nx=2, ny=2)
+    A = sv.dense_operator(prob, q, 0.3, 150.0)
+    v = inp.random_vector(q.shape, 3)
+    np.testing.assert_allclose(A @ v.ravel(), sv.apply_A(prob, q, v, 0.3, 150.0).ravel(),
+                               rtol=1e-12, atol=1e-12 * np.abs(A).max())
+    G, M = prob.point_matrices(q)
+    h = 1e-5
+    fd = -(prob.R(q + h * v) - prob.R(q - h * v)) / (2 * h)
+    fd = fd + np.einsum("ab...,b...->a...", 0.3 * G + 150.0 * M, v)
+    assert np.abs(fd.ravel() - A @ v.ravel()).max() <= 1e-6 * np.abs(A @ v.ravel()).max()
+    w = inp.random_vector(q.shape, 4)
+    assert abs(w.ravel() @ (A @ v.ravel()) - sv.vjp(prob, q, w, 0.3, 150.0).ravel() @ v.ravel()) \
+        <= 1e-12 * np.linalg.norm(w) * np.linalg.norm(A @ v.ravel())
