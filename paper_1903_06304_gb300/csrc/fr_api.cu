@@ -219,9 +219,66 @@ int gmres_solve(fr_ctx* c, const double* q, const double* b, double inv_dtau, do
   FR_CUDA_CHECK(c, cudaMemsetAsync(x, 0, N * sizeof(double), s));
   *iters = 0;
   if (bnorm == 0.0) return FR_OK;
-  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   double beta = bnorm;
   int total = 0;
+  if (m <= GmresState::LD) {
+    // Device-resident Arnoldi: iterations are queued in chunks; one synchronisation per
+    // chunk reads the cycle's iteration count and stopping flag.  Iterations queued
+    // after the stopping test fired leave the cycle's state untouched.
+    constexpr int kChunk = 10;
+    double* tmp = c->w_u;
+    double* w = c->w_t;
+    while (true) {
+      if (beta <= tol * bnorm) break;
+      if (total >= maxit) break;
+      FR_TRY(frk::scale(c, r, 1.0 / beta, c->V, s));
+      GmresState* h = c->gst_h;
+      std::memset(h, 0, sizeof(GmresState));
+      h->g[0] = beta;
+      h->tol = tol * bnorm;
+      h->jmax = std::min(m, maxit - total);
+      FR_CUDA_CHECK(c, cudaMemcpyAsync(c->gst, h, sizeof(GmresState), cudaMemcpyHostToDevice, s));
+      int jh = 0;
+      FR_TRY(frk::gm_copy_in(c, tmp, s));
+      while (true) {
+        const int nchunk = std::min(kChunk, h->jmax - jh);
+        for (int it = 0; it < nchunk; ++it) {
+          if (left) {
+            FR_TRY(op_apply(c, q, tmp, inv_dtau, a0_dt, c->w_z, s));
+            FR_TRY(frk::block_apply(c, c->w_z, w, s));
+          } else {
+            FR_TRY(frk::block_apply(c, tmp, c->w_z, s));
+            FR_TRY(op_apply(c, q, c->w_z, inv_dtau, a0_dt, w, s));
+          }
+          FR_TRY(frk::gm_orthogonalize(c, w, tmp, jh + it + 1, s));
+        }
+        FR_CUDA_CHECK(c, cudaMemcpyAsync(&h->j, &c->gst->j, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        FR_CUDA_CHECK(c, cudaStreamSynchronize(s));
+        if (h->nonfinite) { snprintf(c->err, sizeof(c->err), "GMRES: non-finite Krylov vector"); return FR_ERR_NONFINITE; }
+        jh = h->j;
+        if (h->done || jh >= h->jmax) break;
+      }
+      const int k = jh;
+      total += k;
+      FR_TRY(frk::gm_trisolve(c, s));
+      FR_TRY(frk::lincomb(c, c->V, k, c->gst->y, c->w_u, s));
+      if (left) {
+        FR_TRY(frk::axpby(c, 1.0, c->w_u, 1.0, x, s));
+      } else {
+        FR_TRY(frk::block_apply(c, c->w_u, c->w_z, s));
+        FR_TRY(frk::axpby(c, 1.0, c->w_z, 1.0, x, s));
+      }
+      FR_TRY(op_apply(c, q, x, inv_dtau, a0_dt, c->w_t, s));
+      FR_TRY(frk::axpby(c, 1.0, b, -1.0, c->w_t, s));
+      if (left) FR_TRY(frk::block_apply(c, c->w_t, r, s));
+      else FR_CUDA_CHECK(c, cudaMemcpyAsync(r, c->w_t, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      double rm;
+      FR_TRY(norms_host(c, r, &rm, &beta, s));
+    }
+    *iters = total;
+    return FR_OK;
+  }
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   while (true) {
     if (beta <= tol * bnorm) break;
     if (total >= maxit) break;
@@ -475,7 +532,9 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
   c->basis = fr_make_basis(cfg->p);
   c->gas = fr_make_gas(*cfg);
   if (cudaMalloc((void**)&c->dsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost((void**)&c->hsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess) {
+      cudaMallocHost((void**)&c->hsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&c->gst, sizeof(GmresState)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->gst_h, sizeof(GmresState)) != cudaSuccess) {
     delete c;
     return FR_ERR_CUDA;
   }
@@ -490,6 +549,8 @@ void fr_destroy(fr_ctx* c) {
   free_mesh(c);
   if (c->dsc) cudaFree(c->dsc);
   if (c->hsc) cudaFreeHost(c->hsc);
+  if (c->gst) cudaFree(c->gst);
+  if (c->gst_h) cudaFreeHost(c->gst_h);
   delete c;
 }
 
@@ -504,7 +565,7 @@ int fr_set_mesh(fr_ctx* c, int nx, int ny, int px, int py) {
   c->mesh.nx = nx; c->mesh.ny = ny; c->mesh.ne = c->ne;
   const size_t ne = c->ne, n = c->n, np2 = c->np2, bs = c->bsz;
   c->ndof = 4 * ne * np2;
-  c->red_blocks = 2 * 152;
+  c->red_blocks = 152;
   FR_TRY(dev_alloc(c, &c->gs, (size_t)fr::GS_COUNT * ne * np2));
   FR_TRY(dev_alloc(c, &c->gf, (size_t)fr::GF_COUNT * ne * 4 * n));
   FR_TRY(dev_alloc(c, &c->tq, ne * 16 * n));

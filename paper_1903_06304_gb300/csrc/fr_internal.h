@@ -7,6 +7,19 @@
 #include "fr_device.cuh"
 #include "../../include/fr.h"
 
+// Device-resident state of one GMRES restart cycle (restart <= 32).
+struct GmresState {
+  static constexpr int LD = 32;
+  double H[(LD + 1) * LD];
+  double cs[LD], sn[LD], g[LD + 1], y[LD];
+  double tol;      // absolute tolerance tol_res * ||b||
+  double inv_hn;   // 1/||w|| of the newest vector
+  int j;           // newest basis index = iterations done in this cycle
+  int jmax;        // iteration limit of this cycle
+  int done;
+  int nonfinite;
+};
+
 // Kernel classes for the optional per-kernel timing (fr_profile) and launch counts.
 enum FrKernel {
   KK_GEOM, KK_TRACE, KK_FACE, KK_ELEM, KK_TRACE_JVP, KK_FACE_JVP, KK_ELEM_JVP, KK_BLOCK,
@@ -53,6 +66,8 @@ struct fr_ctx {
   double *JP = nullptr, *JG = nullptr, *PP = nullptr;  // point map: [32|64|16][Ne*n^2]
   double *adj_q = nullptr, *adj_fn = nullptr, *adj_qc = nullptr;  // transpose work
   int lin_ready = 0;
+  GmresState* gst = nullptr;      // device
+  GmresState* gst_h = nullptr;    // pinned host mirror
   // Krylov workspace
   double* V = nullptr;       // [(m+1)][ndof]
   double *w_r = nullptr, *w_z = nullptr, *w_x = nullptr, *w_t = nullptr, *w_u = nullptr;
@@ -119,6 +134,9 @@ int norms(fr_ctx* c, const double* r, double* out_dev, cudaStream_t s);
 int scale(fr_ctx* c, const double* x, double a, double* y, cudaStream_t s);
 int lincomb(fr_ctx* c, const double* V, int nv, const double* y_dev, double* u, cudaStream_t s);
 int axpy(fr_ctx* c, const double* V, int nv, const double* h_dev, double* w, cudaStream_t s);
+int gm_copy_in(fr_ctx* c, double* dst, cudaStream_t s);
+int gm_orthogonalize(fr_ctx* c, double* w, double* next, int nv_bound, cudaStream_t s);
+int gm_trisolve(fr_ctx* c, cudaStream_t s);
 int axpby(fr_ctx* c, double a, const double* x, double b, double* y, cudaStream_t s);
 }  // namespace frk
 
