@@ -309,6 +309,26 @@ def gpu_arm(args):
     t_app = time_calls(lambda: S.apply_linear(vec, out))
     t_vjp = time_calls(lambda: S.apply_linear(vec, out, transpose=True))
 
+    # ---- GMRES iteration cost at the final state: a fixed count (tol_res 1e-30), so the
+    # per-iteration time does not depend on the Newton history
+    gm_cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
+                       restart=args.restart, maxit_lin=120, tol_res=1e-30)
+    Sg = fr.Solver(gm_cfg, w.nx, w.ny)
+    Sg.update_mesh(T(corners), T(vel))
+    Sg.precond_build(run.q, 1e-20, 1.5 / w.dt)
+    rhs = torch.empty_like(run.q)
+    Sg.bdf_rhs(run.q, run.qc_n, run.qc_nm1, fr.BDF2, w.dt, rhs)
+    xg = torch.empty_like(run.q)
+    Sg.gmres(run.q, rhs, xg, 1e-20, 1.5 / w.dt)
+    torch.cuda.synchronize()
+    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ga.record()
+    its_g = Sg.gmres(run.q, rhs, xg, 1e-20, 1.5 / w.dt)
+    gb.record()
+    torch.cuda.synchronize()
+    us_per_gmres_it = 1e3 * ga.elapsed_time(gb) / its_g
+    Sg.close()
+
     # ---- precision comparison: a few steps from the same state per block precision
     compare = {}
     if not args.no_compare:
@@ -399,6 +419,7 @@ def gpu_arm(args):
         "linearized_jvp_gdofs": dof / (t_app * 1e-3) / 1e9,
         "vjp_gdofs": dof / (t_vjp * 1e-3) / 1e9,
         "linearize_ms": t_lin,
+        "us_per_gmres_iteration": us_per_gmres_it,
         "precision_compare": compare,
         "kernels": kernels,
         "roofline": roof,

@@ -1,6 +1,7 @@
 // fr_api.cu -- C ABI of the GB300 preconditioned FR/CPR implicit hot path: context and
 // workspace, the 1-D FR basis (Sec. 3.1), restarted right-preconditioned GMRES with CGS2
 // and the pseudo-time Newton loops of Sec. 3.2 (BDF2 dual time, steady PTC with SER).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -565,7 +566,9 @@ int fr_set_mesh(fr_ctx* c, int nx, int ny, int px, int py) {
   c->mesh.nx = nx; c->mesh.ny = ny; c->mesh.ne = c->ne;
   const size_t ne = c->ne, n = c->n, np2 = c->np2, bs = c->bsz;
   c->ndof = 4 * ne * np2;
-  c->red_blocks = 152;
+  // reduction grid: at least 4 pairs of entries per thread (256 threads), one to four
+  // blocks per SM, so that the per-block reduction stays small against the streaming
+  c->red_blocks = (int)std::max<size_t>(152, std::min<size_t>(4 * 152, c->ndof / 2 / (256 * 4)));
   FR_TRY(dev_alloc(c, &c->gs, (size_t)fr::GS_COUNT * ne * np2));
   FR_TRY(dev_alloc(c, &c->gf, (size_t)fr::GF_COUNT * ne * 4 * n));
   FR_TRY(dev_alloc(c, &c->tq, ne * 16 * n));

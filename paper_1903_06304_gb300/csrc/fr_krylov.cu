@@ -113,20 +113,47 @@ __global__ void __launch_bounds__(RT) k_krylov(const double* __restrict__ V, siz
 #pragma unroll
     for (int k = 0; k < NV; ++k) hk[k] = k < nv ? h[k] : 0.0;
   }
-  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n; i += (size_t)gridDim.x * RT) {
-    double x = w[i];
+  // pairs of entries through 16-byte loads, two pairs in flight per thread (n and ld
+  // are even: 4 variables per point)
+  const size_t n2 = n / 2, ld2 = ld / 2;
+  const double2* V2 = reinterpret_cast<const double2*>(V);
+  double2* w2 = reinterpret_cast<double2*>(w);
+  const size_t stride = (size_t)gridDim.x * RT;
+  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n2; i += 2 * stride) {
+    const bool two = i + stride < n2;
+    double2 xa = w2[i], xb = two ? w2[i + stride] : make_double2(0.0, 0.0);
     if (MODE != 0) {
 #pragma unroll
-      for (int k = 0; k < NV; ++k)
-        if (k < nv) x = fma(-hk[k], V[k * ld + i], x);
-      w[i] = x;
+      for (int k = 0; k < NV; ++k) {
+        if (k < nv) {
+          const double2 va = V2[k * ld2 + i];
+          const double2 vb = two ? V2[k * ld2 + i + stride] : make_double2(0.0, 0.0);
+          xa.x = fma(-hk[k], va.x, xa.x);
+          xa.y = fma(-hk[k], va.y, xa.y);
+          xb.x = fma(-hk[k], vb.x, xb.x);
+          xb.y = fma(-hk[k], vb.y, xb.y);
+        }
+      }
+      w2[i] = xa;
+      if (two) w2[i + stride] = xb;
     }
     if (MODE == 2) {
-      acc[0] = fma(x, x, acc[0]);
+      acc[0] = fma(xa.x, xa.x, acc[0]);
+      acc[0] = fma(xa.y, xa.y, acc[0]);
+      acc[0] = fma(xb.x, xb.x, acc[0]);
+      acc[0] = fma(xb.y, xb.y, acc[0]);
     } else {
 #pragma unroll
-      for (int k = 0; k < NV; ++k)
-        if (k < nv) acc[k] = fma(V[k * ld + i], x, acc[k]);
+      for (int k = 0; k < NV; ++k) {
+        if (k < nv) {
+          const double2 va = V2[k * ld2 + i];
+          const double2 vb = two ? V2[k * ld2 + i + stride] : make_double2(0.0, 0.0);
+          acc[k] = fma(va.x, xa.x, acc[k]);
+          acc[k] = fma(va.y, xa.y, acc[k]);
+          acc[k] = fma(vb.x, xb.x, acc[k]);
+          acc[k] = fma(vb.y, xb.y, acc[k]);
+        }
+      }
     }
   }
   const bool last = block_reduce_store(acc, MODE == 2 ? 1 : nv, partial, out, ticket);
