@@ -231,9 +231,9 @@ const char* fr_profile_name(int kind);
  * read), on a periodic nx-by-ny mesh; qp_d, R_d are device [4][Ne][n][n].
  * Scratch: a file-scope 32 MiB device array that every GPU which loads the library
  * holds until the process exits.  The mesh must fit in it:
- *   Ne * (19 n^2 + 84 n) * 8 bytes (each of 7 sub-arrays rounded up to 256 bytes)
- *   <= 32 MiB, i.e. Ne <= 17189 at p = 1, 9915 at p = 2, 6553 at p = 3 (64x64 fits),
- *   4686 at p = 4;
+ *   Ne * ((19 n^2 + 84 n) * 8 + 20) bytes plus the case parameters (each of 9
+ *   sub-arrays rounded up to 256 bytes) <= 32 MiB, i.e. Ne <= 17015 at p = 1, 9857 at
+ *   p = 2, 6528 at p = 3 (64x64 fits), 4673 at p = 4;
  * larger meshes return FR_ERR_ARG before any GPU work.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress, once per device, with that device
  * current): make that first call before any stream capture.  Every call writes each

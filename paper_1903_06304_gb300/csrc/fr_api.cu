@@ -131,6 +131,8 @@ void free_mesh(fr_ctx* c) {
   if (c->Dc) { cudaFree(c->Dc); c->Dc = nullptr; }
   if (c->info) { cudaFree(c->info); c->info = nullptr; }
   if (c->ticket) { cudaFree(c->ticket); c->ticket = nullptr; }
+  if (c->nbr) { cudaFree(c->nbr); c->nbr = nullptr; }
+  if (c->ecase) { cudaFree(c->ecase); c->ecase = nullptr; }
   c->blocks_ready = 0;
   c->lin_ready = 0;
 }
@@ -532,9 +534,13 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
   c->err[0] = 0;
   c->basis = fr_make_basis(cfg->p);
   c->gas = fr_make_gas(*cfg);
+  c->cp_h.gas = c->gas;
+  c->cp_h.a0dt = c->cp_h.a1dt = c->cp_h.a2dt = 0.0;
+  c->cp_h.inv_dtau = c->cp_h.a0_dt = 0.0;
   if (cudaMalloc((void**)&c->dsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&c->hsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&c->gst, sizeof(GmresState)) != cudaSuccess ||
+      cudaMalloc((void**)&c->cp, sizeof(fr::CaseParams)) != cudaSuccess ||
       cudaMallocHost((void**)&c->gst_h, sizeof(GmresState)) != cudaSuccess) {
     delete c;
     return FR_ERR_CUDA;
@@ -551,6 +557,7 @@ void fr_destroy(fr_ctx* c) {
   if (c->dsc) cudaFree(c->dsc);
   if (c->hsc) cudaFreeHost(c->hsc);
   if (c->gst) cudaFree(c->gst);
+  if (c->cp) cudaFree(c->cp);
   if (c->gst_h) cudaFreeHost(c->gst_h);
   delete c;
 }
@@ -563,7 +570,16 @@ int fr_set_mesh(fr_ctx* c, int nx, int ny, int px, int py) {
   }
   free_mesh(c);
   c->nx = nx; c->ny = ny; c->ne = nx * ny;
-  c->mesh.nx = nx; c->mesh.ny = ny; c->mesh.ne = c->ne;
+  FR_TRY(dev_alloc(c, &c->nbr, (size_t)4 * c->ne));
+  FR_TRY(dev_alloc(c, &c->ecase, (size_t)c->ne));
+  c->mesh.nbr = c->nbr;
+  c->mesh.ecase = c->ecase;
+  c->mesh.cp = c->cp;
+  c->mesh.ne = c->ne;
+  c->mesh.viscous = c->gas.viscous;
+  FR_TRY(frk::fill_topology(c, nx, ny, 0, 0, 0));
+  FR_TRY(frk::set_case_params(c, 0, c->cp_h, 0));
+  FR_CUDA_CHECK(c, cudaStreamSynchronize(0));
   const size_t ne = c->ne, n = c->n, np2 = c->np2, bs = c->bsz;
   c->ndof = 4 * ne * np2;
   // reduction grid: at least 4 pairs of entries per thread (256 threads), one to four

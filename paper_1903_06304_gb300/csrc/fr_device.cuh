@@ -42,20 +42,29 @@ enum { GS_SXX, GS_SXY, GS_SEX, GS_SEY, GS_STX, GS_STE, GS_INVJ, GS_DIVST, GS_UG,
 enum { GF_SX, GF_SY, GF_J, GF_UG, GF_VG, GF_COUNT };
 enum { FACE_L = 0, FACE_R = 1, FACE_B = 2, FACE_T = 3 };
 
+// Parameters of one independent case (a batch holds several): its gas, the time terms of
+// the pseudo-step right-hand side r = R - (a0 q^c + a1 qc_n + a2 qc_nm1)/dt (per dt) and
+// the coefficients of the Newton operator A = inv_dtau Gamma + a0_dt M - dR/dq.
+struct CaseParams {
+  Gas gas;
+  double a0dt, a1dt, a2dt;
+  double inv_dtau, a0_dt;
+};
+
+// Element topology of one launch: face neighbours (L, R, B, T) by global element index,
+// the case of each element and the case parameters.  All cases of a launch share the
+// polynomial degree (a template parameter of the kernels) and the viscous switch.
 struct Mesh {
-  int nx, ny, ne;
-  __device__ __forceinline__ int left(int e) const {
-    int i = e % nx, j = e / nx; return j * nx + (i == 0 ? nx - 1 : i - 1);
-  }
-  __device__ __forceinline__ int right(int e) const {
-    int i = e % nx, j = e / nx; return j * nx + (i == nx - 1 ? 0 : i + 1);
-  }
-  __device__ __forceinline__ int bottom(int e) const {
-    int i = e % nx, j = e / nx; return (j == 0 ? ny - 1 : j - 1) * nx + i;
-  }
-  __device__ __forceinline__ int top(int e) const {
-    int i = e % nx, j = e / nx; return (j == ny - 1 ? 0 : j + 1) * nx + i;
-  }
+  const int* nbr;          // [ne][4]
+  const int* ecase;        // [ne]
+  const CaseParams* cp;    // [ncases]
+  int ne;
+  int viscous;
+  __device__ __forceinline__ int left(int e) const { return nbr[4 * e + FACE_L]; }
+  __device__ __forceinline__ int right(int e) const { return nbr[4 * e + FACE_R]; }
+  __device__ __forceinline__ int bottom(int e) const { return nbr[4 * e + FACE_B]; }
+  __device__ __forceinline__ int top(int e) const { return nbr[4 * e + FACE_T]; }
+  __device__ __forceinline__ const CaseParams& par(int e) const { return cp[ecase[e]]; }
 };
 
 // ---------------------------------------------------------------- dual numbers

@@ -46,8 +46,13 @@ struct fr_ctx {
   int nx, ny, ne;
   size_t ndof;
   fr::Basis basis;
-  fr::Gas gas;
-  fr::Mesh mesh;
+  fr::Gas gas;                 // host copy of case 0's gas
+  fr::Mesh mesh;               // device topology and case table of the launches
+  int* nbr = nullptr;          // [Ne][4] face neighbours
+  int* ecase = nullptr;        // [Ne] case of each element
+  fr::CaseParams* cp = nullptr;  // [ncases] device
+  fr::CaseParams cp_h;         // host copy of case 0's parameters
+  int ncases = 1;
   // geometry (Sec. 2.3)
   double* gs = nullptr;   // [GS_COUNT][Ne*np2]
   double* gf = nullptr;   // [GF_COUNT][Ne*4*n]
@@ -114,6 +119,10 @@ fr::Basis fr_make_basis(int p);
 fr::Gas fr_make_gas(const fr_config& c);
 
 namespace frk {
+int set_case_params(fr_ctx* c, int cid, const fr::CaseParams& p, cudaStream_t s);
+int set_time_terms(fr_ctx* c, double a0dt, double a1dt, double a2dt, cudaStream_t s);
+int set_operator_terms(fr_ctx* c, double inv_dtau, double a0_dt, cudaStream_t s);
+int fill_topology(fr_ctx* c, int nx, int ny, int e0, int cid, cudaStream_t s);
 int geometry(fr_ctx* c, const double* corners, const double* vel, cudaStream_t s);
 int residual(fr_ctx* c, const double* q, double* out, const double* qcn, const double* qcnm1,
              double a0dt, double a1dt, double a2dt, cudaStream_t s);

@@ -101,14 +101,32 @@ __global__ void k_geometry(const double* __restrict__ corners, const double* __r
 }
 
 
+// ------------------------------------------------------------------ topology and parameters
+// Periodic structured nx-by-ny block starting at element e0 of a launch, case id cid.
+static __global__ void k_fill_topo(int nx, int ny, int e0, int cid, int* __restrict__ nbr,
+                            int* __restrict__ ecase) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nx * ny) return;
+  const int i = l % nx, j = l / nx;
+  const int g = e0 + l;
+  nbr[4 * g + FACE_L] = e0 + j * nx + (i == 0 ? nx - 1 : i - 1);
+  nbr[4 * g + FACE_R] = e0 + j * nx + (i == nx - 1 ? 0 : i + 1);
+  nbr[4 * g + FACE_B] = e0 + (j == 0 ? ny - 1 : j - 1) * nx + i;
+  nbr[4 * g + FACE_T] = e0 + (j == ny - 1 ? 0 : j + 1) * nx + i;
+  ecase[g] = cid;
+}
+
+static __global__ void k_set_case(CaseParams* cp, int cid, CaseParams value) { cp[cid] = value; }
+
 // ------------------------------------------------------------------ trace kernel
 // q^p (and the tangent) of EPB elements staged in shared memory; each thread owns one
 // solution point.  Outputs: gl[8][Ne*NP] local gradients (x comps then y comps),
 // tq[Ne][4][4][N] state traces, tg[Ne][4][8][N] gradient traces.
 template <class T, int N>
 __global__ void __launch_bounds__(Tile<N>::THREADS)
-k_trace(Buf<T> Q, int ne, Basis B, Gas gas, const double* __restrict__ gs, Buf<T> GL, Buf<T> TQ,
+k_trace(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs, Buf<T> GL, Buf<T> TQ,
         Buf<T> TG) {
+  const int ne = M.ne;
   constexpr int NP = N * N, EPB = Tile<N>::EPB;
   __shared__ T sq[EPB][4][NP];
   __shared__ T sg[EPB][8][NP];
@@ -123,7 +141,7 @@ k_trace(Buf<T> Q, int ne, Basis B, Gas gas, const double* __restrict__ gs, Buf<T
     for (int v = 0; v < 4; ++v) sq[le][v][pt] = Q.ld(v * SN + o);
   }
   __syncthreads();
-  if (gas.viscous) {
+  if (M.viscous) {
     if (live) {
       const double sxx = gs[GS_SXX * SN + o], sxy = gs[GS_SXY * SN + o];
       const double sex = gs[GS_SEX * SN + o], sey = gs[GS_SEY * SN + o];
@@ -159,7 +177,7 @@ k_trace(Buf<T> Q, int ne, Basis B, Gas gas, const double* __restrict__ gs, Buf<T
       for (int k = 1; k < N; ++k) acc = acc + w[k] * sq[le][c][row ? s * N + k : k * N + s];
       TQ.st((((size_t)e * 4 + f) * 4 + c) * N + s, acc);
     }
-    if (gas.viscous) {
+    if (M.viscous) {
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         T acc = w[0] * sg[le][c][row ? s * N : s];
@@ -175,20 +193,21 @@ k_trace(Buf<T> Q, int ne, Basis B, Gas gas, const double* __restrict__ gs, Buf<T
 // One thread per owned flux point: xi-faces are owned by their '-' (left) element (its R
 // face), eta-faces by their bottom element (its T face).  Outputs fn, qcm [Ne][2][4][N].
 template <class T, int N>
-__global__ void k_face(Mesh M, Basis B, Gas gas, const double* __restrict__ gf, Buf<T> TQ,
+__global__ void k_face(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ,
                        Buf<T> TG, Buf<T> FN, Buf<T> QC) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= M.ne * 2 * N) return;
   const int e = idx / (2 * N), rem = idx % (2 * N), dir = rem / N, t = rem % N;
   const int plus = dir == 0 ? M.right(e) : M.top(e);
   const int fm = dir == 0 ? FACE_R : FACE_T, fp = dir == 0 ? FACE_L : FACE_B;
+  const Gas& gas = M.par(e).gas;
   T qm[4], qp[4], gm[8], gp[8];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     qm[v] = TQ.ld((((size_t)e * 4 + fm) * 4 + v) * N + t);
     qp[v] = TQ.ld((((size_t)plus * 4 + fp) * 4 + v) * N + t);
   }
-  if (gas.viscous) {
+  if (M.viscous) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       gm[c] = TG.ld((((size_t)e * 4 + fm) * 8 + c) * N + t);
@@ -212,13 +231,9 @@ __global__ void k_face(Mesh M, Basis B, Gas gas, const double* __restrict__ gf, 
 // ------------------------------------------------------------------ element kernel
 enum { MODE_RESID = 0, MODE_JVP = 1 };
 
-struct TimeTerms {           // r = R - (a0 q^c + a1 qc_n + a2 qc_nm1)/dt
+struct TimeTerms {           // r = R - (a0 q^c + a1 qc_n + a2 qc_nm1)/dt, coefficients per case
   const double* qcn;
   const double* qcnm1;
-  double a0dt, a1dt, a2dt;
-};
-struct JvpTerms {            // A v = inv_dtau Gamma v + a0_dt M v - dR/dq v
-  double inv_dtau, a0_dt;
 };
 
 // (inv_dtau Gamma + a0_dt M) w at one point (Eqs. jacobian, preconditioning, theta),
@@ -251,9 +266,9 @@ __device__ __forceinline__ void gamma_m_apply(const double q[4], const double w[
 
 template <class T, int N, int MODE>
 __global__ void __launch_bounds__(Tile<N>::THREADS)
-k_elem(Buf<T> Q, Mesh M, Basis B, Gas gas, const double* __restrict__ gs,
+k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
        const double* __restrict__ gf, Buf<T> GL, Buf<T> TQ, Buf<T> FN, Buf<T> QC,
-       double* __restrict__ out, TimeTerms tt, JvpTerms jt) {
+       double* __restrict__ out, TimeTerms tt) {
   constexpr int NP = N * N, EPB = Tile<N>::EPB;
   __shared__ T sF[EPB][4][NP];
   __shared__ T sG[EPB][4][NP];
@@ -267,6 +282,8 @@ k_elem(Buf<T> Q, Mesh M, Basis B, Gas gas, const double* __restrict__ gs,
   T q[4];
   Thermo<T> th;
   double ij = 0.0;
+  const CaseParams& cpar = M.par(live ? e : 0);
+  const Gas& gas = cpar.gas;
   if (live) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) q[v] = Q.ld(v * SN + o);
@@ -275,7 +292,7 @@ k_elem(Buf<T> Q, Mesh M, Basis B, Gas gas, const double* __restrict__ gs,
     T fx[4], gy[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) { fx[v] = th.f[v]; gy[v] = th.g[v]; }
-    if (gas.viscous) {
+    if (M.viscous) {
       T qx[4], qy[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) { qx[v] = GL.ld(v * SN + o); qy[v] = GL.ld((4 + v) * SN + o); }
@@ -336,8 +353,8 @@ k_elem(Buf<T> Q, Mesh M, Basis B, Gas gas, const double* __restrict__ gs,
     for (int v = 0; v < 4; ++v) {
       double r = val(R[v]);
       if (tt.qcn) {
-        double acc = tt.a0dt * val(th.qc[v]) + tt.a1dt * tt.qcn[v * SN + o];
-        if (tt.qcnm1) acc += tt.a2dt * tt.qcnm1[v * SN + o];
+        double acc = cpar.a0dt * val(th.qc[v]) + cpar.a1dt * tt.qcn[v * SN + o];
+        if (tt.qcnm1) acc += cpar.a2dt * tt.qcnm1[v * SN + o];
         r -= acc;
       }
       out[v * SN + o] = r;
@@ -346,7 +363,7 @@ k_elem(Buf<T> Q, Mesh M, Basis B, Gas gas, const double* __restrict__ gs,
     double qv[4], wv[4], gm[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) { qv[v] = val(q[v]); wv[v] = tan_(q[v]); }
-    gamma_m_apply(qv, wv, gs[GS_UG * SN + o], gs[GS_VG * SN + o], gas, jt.inv_dtau, jt.a0_dt, gm);
+    gamma_m_apply(qv, wv, gs[GS_UG * SN + o], gs[GS_VG * SN + o], gas, cpar.inv_dtau, cpar.a0_dt, gm);
 #pragma unroll
     for (int v = 0; v < 4; ++v) out[v * SN + o] = gm[v] - tan_(R[v]);
   }

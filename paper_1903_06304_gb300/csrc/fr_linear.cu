@@ -23,7 +23,7 @@ namespace fr {
 //   JFQ[r*8 + c][o] = d fnum_r / d (q-_c (c<4) | q+_{c-4}),
 //   JFG[r*16 + c][o] = d fnum_r / d (g-_c (c<8) | g+_{c-8}).
 template <int N>
-__global__ void k_lin_face(Mesh M, Basis B, Gas gas, const double* __restrict__ gf,
+__global__ void k_lin_face(Mesh M, Basis B, const double* __restrict__ gf,
                            const double* __restrict__ tq, const double* __restrict__ tg,
                            double* __restrict__ JFQ, double* __restrict__ JFG) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -32,6 +32,7 @@ __global__ void k_lin_face(Mesh M, Basis B, Gas gas, const double* __restrict__ 
   const int e = idx / (2 * N), rem = idx % (2 * N), dir = rem / N, t = rem % N;
   const int plus = dir == 0 ? M.right(e) : M.top(e);
   const int fm = dir == 0 ? FACE_R : FACE_T, fp = dir == 0 ? FACE_L : FACE_B;
+  const Gas& gas = M.par(e).gas;
   double qm[4], qp[4], gm[8], gp[8];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -40,15 +41,15 @@ __global__ void k_lin_face(Mesh M, Basis B, Gas gas, const double* __restrict__ 
   }
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    gm[c] = gas.viscous ? tg[(((size_t)e * 4 + fm) * 8 + c) * N + t] : 0.0;
-    gp[c] = gas.viscous ? tg[(((size_t)plus * 4 + fp) * 8 + c) * N + t] : 0.0;
+    gm[c] = M.viscous ? tg[(((size_t)e * 4 + fm) * 8 + c) * N + t] : 0.0;
+    gp[c] = M.viscous ? tg[(((size_t)plus * 4 + fp) * 8 + c) * N + t] : 0.0;
   }
   const size_t FNs = (size_t)M.ne * 4 * N;
   const size_t om = ((size_t)e * 4 + fm) * N + t, op = ((size_t)plus * 4 + fp) * N + t;
   const double Sx = gf[GF_SX * FNs + om], Sy = gf[GF_SY * FNs + om];
   const double ug = gf[GF_UG * FNs + om], vg = gf[GF_VG * FNs + om];
   const double Jm = gf[GF_J * FNs + om], Jp = gf[GF_J * FNs + op];
-  const int ndir = gas.viscous ? 24 : 8;
+  const int ndir = M.viscous ? 24 : 8;
 #pragma unroll 1
   for (int dd = 0; dd < ndir; ++dd) {
     Dual dqm[4], dqp[4], dgm[8], dgp[8], fnum[4], qcom[4];
@@ -77,11 +78,10 @@ __global__ void k_lin_face(Mesh M, Basis B, Gas gas, const double* __restrict__ 
 //   PP[r*4 + c][o] = (Gamma/dtau + a0_dt M - (1/|J|) divst M)_rc.
 template <int N>
 __global__ void __launch_bounds__(Tile<N>::THREADS)
-k_lin_point(const double* __restrict__ q, Mesh M, Basis B, Gas gas, const double* __restrict__ gs,
+k_lin_point(const double* __restrict__ q, Mesh M, Basis B, const double* __restrict__ gs,
             const double* __restrict__ gf, const double* __restrict__ gl,
-            const double* __restrict__ tq, const double* __restrict__ qcm, double inv_dtau,
-            double a0_dt, double* __restrict__ JP, double* __restrict__ JG,
-            double* __restrict__ PP) {
+            const double* __restrict__ tq, const double* __restrict__ qcm,
+            double* __restrict__ JP, double* __restrict__ JG, double* __restrict__ PP) {
   constexpr int NP = N * N, EPB = Tile<N>::EPB;
   const int le = threadIdx.x / NP, pt = threadIdx.x % NP;
   const int e = blockIdx.x * EPB + le;
@@ -90,11 +90,14 @@ k_lin_point(const double* __restrict__ q, Mesh M, Basis B, Gas gas, const double
   const size_t SN = (size_t)M.ne * NP;
   const size_t FNs = (size_t)M.ne * 4 * N;
   const size_t o = (size_t)e * NP + pt;
+  const CaseParams& cpar = M.par(e);
+  const Gas& gas = cpar.gas;
+  const double inv_dtau = cpar.inv_dtau, a0_dt = cpar.a0_dt;
   double qv[4], gc[8];
 #pragma unroll
   for (int v = 0; v < 4; ++v) qv[v] = q[v * SN + o];
   const double ij = gs[GS_INVJ * SN + o];
-  if (gas.viscous) {
+  if (M.viscous) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) gc[c] = gl[c * SN + o];
     const int qsrc[4] = {M.left(e), e, M.bottom(e), e};
@@ -121,7 +124,7 @@ k_lin_point(const double* __restrict__ q, Mesh M, Basis B, Gas gas, const double
   const double sxx = gs[GS_SXX * SN + o], sxy = gs[GS_SXY * SN + o];
   const double sex = gs[GS_SEX * SN + o], sey = gs[GS_SEY * SN + o];
   const double stx = gs[GS_STX * SN + o], ste = gs[GS_STE * SN + o];
-  const int ndir = gas.viscous ? 12 : 4;
+  const int ndir = M.viscous ? 12 : 4;
 #pragma unroll 1
   for (int dd = 0; dd < ndir; ++dd) {
     Dual dq[4], dx[4], dy[4];
@@ -136,7 +139,7 @@ k_lin_point(const double* __restrict__ q, Mesh M, Basis B, Gas gas, const double
     Dual fx[4], gy[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) { fx[v] = th.f[v]; gy[v] = th.g[v]; }
-    if (gas.viscous) {
+    if (M.viscous) {
       Dual fv[4], gv[4];
       neg_viscous_flux(dq, dx, dy, gas, fv, gv);
 #pragma unroll
@@ -170,7 +173,7 @@ k_lin_point(const double* __restrict__ q, Mesh M, Basis B, Gas gas, const double
 // ------------------------------------------------------------------ forward (A v)
 // Owned flux point: dfnum = JFQ [dq-; dq+] + JFG [dg-; dg+],  dqcom = (dq- + dq+)/2.
 template <int N>
-__global__ void k_lin_face_apply(Mesh M, Gas gas, const double* __restrict__ tqv,
+__global__ void k_lin_face_apply(Mesh M, const double* __restrict__ tqv,
                                  const double* __restrict__ tgv, const double* __restrict__ JFQ,
                                  const double* __restrict__ JFG, double* __restrict__ fnv,
                                  double* __restrict__ qcv) {
@@ -194,7 +197,7 @@ __global__ void k_lin_face_apply(Mesh M, Gas gas, const double* __restrict__ tqv
     for (int c = 0; c < 8; ++c) s = fma(JFQ[(size_t)(r * 8 + c) * nf + idx], x[c], s);
     out[r] = s;
   }
-  if (gas.viscous) {
+  if (M.viscous) {
     double g[16];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -221,7 +224,7 @@ __global__ void k_lin_face_apply(Mesh M, Gas gas, const double* __restrict__ tqv
 // A v = P' dq + (1/|J|)(Dc dF + Dc dG + sum_f g_f' dfnum_f).
 template <int N>
 __global__ void __launch_bounds__(Tile<N>::THREADS)
-k_lin_elem_apply(const double* __restrict__ v, Mesh M, Basis B, Gas gas,
+k_lin_elem_apply(const double* __restrict__ v, Mesh M, Basis B,
                  const double* __restrict__ gs, const double* __restrict__ gf,
                  const double* __restrict__ glv, const double* __restrict__ tqv,
                  const double* __restrict__ fnv, const double* __restrict__ qcv,
@@ -250,7 +253,7 @@ k_lin_elem_apply(const double* __restrict__ v, Mesh M, Basis B, Gas gas,
       for (int c = 0; c < 4; ++c) s = fma(JP[(size_t)(r * 4 + c) * SN + o], dq[c], s);
       fg[r] = s;
     }
-    if (gas.viscous) {
+    if (M.viscous) {
       double g[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) g[c] = glv[c * SN + o];
@@ -311,7 +314,7 @@ k_lin_elem_apply(const double* __restrict__ v, Mesh M, Basis B, Gas gas,
 //   the common flux / common solution on its face f (the owning face sums two of them).
 template <int N>
 __global__ void __launch_bounds__(Tile<N>::THREADS)
-k_lin_elem_adjoint(const double* __restrict__ w, Mesh M, Basis B, Gas gas,
+k_lin_elem_adjoint(const double* __restrict__ w, Mesh M, Basis B,
                    const double* __restrict__ gs, const double* __restrict__ gf,
                    const double* __restrict__ JP, const double* __restrict__ JG,
                    const double* __restrict__ PP, double* __restrict__ aq,
@@ -358,7 +361,7 @@ k_lin_elem_adjoint(const double* __restrict__ w, Mesh M, Basis B, Gas gas,
       for (int r = 0; r < 8; ++r) s = fma(JP[(size_t)(r * 4 + c) * SN + o], aFG[r], s);
       aq[c * SN + o] = s;
     }
-    if (gas.viscous) {
+    if (M.viscous) {
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         double s = 0.0;
@@ -385,7 +388,7 @@ k_lin_elem_adjoint(const double* __restrict__ w, Mesh M, Basis B, Gas gas,
       for (int k = 0; k < N; ++k) {
         const int p2 = row ? s * N + k : k * N + s;   // points on the line of face point s
         a_fn = fma(dg[k], ss[le][r][p2], a_fn);
-        if (gas.viscous) a_qc = fma(dg[k], Sx * sgx[le][r][p2] + Sy * sgy[le][r][p2], a_qc);
+        if (M.viscous) a_qc = fma(dg[k], Sx * sgx[le][r][p2] + Sy * sgy[le][r][p2], a_qc);
       }
       afn[(((size_t)e * 4 + f) * 4 + r) * N + s] = a_fn;
       aqc[(((size_t)e * 4 + f) * 4 + r) * N + s] = a_qc;
@@ -397,7 +400,7 @@ k_lin_elem_adjoint(const double* __restrict__ w, Mesh M, Basis B, Gas gas,
 // transposed Jacobian, write the adjoints of both sides' traces.  The own-trace term of
 // the lifted jump (-a_qc) is added here as well.
 template <int N>
-__global__ void k_lin_face_adjoint(Mesh M, Gas gas, const double* __restrict__ JFQ,
+__global__ void k_lin_face_adjoint(Mesh M, const double* __restrict__ JFQ,
                                    const double* __restrict__ JFG, const double* __restrict__ afn,
                                    const double* __restrict__ aqc, double* __restrict__ atq,
                                    double* __restrict__ atg) {
@@ -429,7 +432,7 @@ __global__ void k_lin_face_adjoint(Mesh M, Gas gas, const double* __restrict__ J
     atq[(((size_t)e * 4 + fm) * 4 + c) * N + t] = sm;
     atq[(((size_t)plus * 4 + fp) * 4 + c) * N + t] = sp;
   }
-  if (gas.viscous) {
+  if (M.viscous) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       double sm = 0.0, sp = 0.0;
@@ -447,7 +450,7 @@ __global__ void k_lin_face_adjoint(Mesh M, Gas gas, const double* __restrict__ J
 // Trace pass (solution point): out = aq + l^T atq + (grad^T)(agl + l^T atg).
 template <int N>
 __global__ void __launch_bounds__(Tile<N>::THREADS)
-k_lin_trace_adjoint(Mesh M, Basis B, Gas gas, const double* __restrict__ gs,
+k_lin_trace_adjoint(Mesh M, Basis B, const double* __restrict__ gs,
                     const double* __restrict__ aq, const double* __restrict__ agl,
                     const double* __restrict__ atq, const double* __restrict__ atg,
                     double* __restrict__ out) {
@@ -472,7 +475,7 @@ k_lin_trace_adjoint(Mesh M, Basis B, Gas gas, const double* __restrict__ gs,
       for (int f = 0; f < 4; ++f) s = fma(wts[f], atq[(((size_t)e * 4 + f) * 4 + c) * N + lines[f]], s);
       acc[c] = s;
     }
-    if (gas.viscous) {
+    if (M.viscous) {
       const double sxx = gs[GS_SXX * SN + o], sxy = gs[GS_SXY * SN + o];
       const double sex = gs[GS_SEX * SN + o], sey = gs[GS_SEY * SN + o];
       const double ij = gs[GS_INVJ * SN + o];
@@ -492,7 +495,7 @@ k_lin_trace_adjoint(Mesh M, Basis B, Gas gas, const double* __restrict__ gs,
   }
   __syncthreads();
   if (!live) return;
-  if (gas.viscous) {
+  if (M.viscous) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       double s = acc[c];
@@ -514,16 +517,16 @@ namespace frk {
 using namespace fr;
 
 template <int N>
-static int linearize_n(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s) {
+static int linearize_n(fr_ctx* c, const double* q, cudaStream_t s) {
   constexpr int EPB = Tile<N>::EPB, TH = Tile<N>::THREADS;
   const int nblk = (c->ne + EPB - 1) / EPB;
-  const bool visc = c->gas.viscous;
+  const bool visc = c->mesh.viscous;
   const int nf = c->ne * 2 * N;
   {
     FR_ACCOUNT(c, KK_TRACE, (double)c->ne * N * N * fr_flops_trace(N, visc), 0.0);
     FR_PROF_BEGIN(c, s);
-    k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(q)}, c->ne, c->basis,
-                                           c->gas, c->gs, Buf<double>{c->gl}, Buf<double>{c->tq},
+    k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(q)}, c->mesh, c->basis,
+                                           c->gs, Buf<double>{c->gl}, Buf<double>{c->tq},
                                            Buf<double>{c->tg});
     FR_PROF_END(c, s, KK_TRACE);
     FR_LAUNCH_CHECK(c);
@@ -531,7 +534,7 @@ static int linearize_n(fr_ctx* c, const double* q, double inv_dtau, double a0_dt
   {
     FR_ACCOUNT(c, KK_FACE, (double)nf * fr_flops_face_point(visc), 0.0);
     FR_PROF_BEGIN(c, s);
-    k_face<double, N><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->basis, c->gas, c->gf,
+    k_face<double, N><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->basis, c->gf,
                                                       Buf<double>{c->tq}, Buf<double>{c->tg},
                                                       Buf<double>{c->fn}, Buf<double>{c->qcm});
     FR_PROF_END(c, s, KK_FACE);
@@ -540,7 +543,7 @@ static int linearize_n(fr_ctx* c, const double* q, double inv_dtau, double a0_dt
   {
     FR_ACCOUNT(c, KK_LINEARIZE, (visc ? 24.0 : 8.0) * nf * FR_JVP_FLOP_FACTOR * fr_flops_face_point(visc), 0.0);
     FR_PROF_BEGIN(c, s);
-    k_lin_face<N><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->basis, c->gas, c->gf, c->tq, c->tg,
+    k_lin_face<N><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->basis, c->gf, c->tq, c->tg,
                                                    c->JFQ, c->JFG);
     FR_PROF_END(c, s, KK_LINEARIZE);
     FR_LAUNCH_CHECK(c);
@@ -548,8 +551,8 @@ static int linearize_n(fr_ctx* c, const double* q, double inv_dtau, double a0_dt
   {
     FR_ACCOUNT(c, KK_LINEARIZE, (double)c->ne * N * N * (visc ? 12.0 : 4.0) * FR_JVP_FLOP_FACTOR * 95.0, 0.0);
     FR_PROF_BEGIN(c, s);
-    k_lin_point<N><<<nblk, TH, 0, s>>>(q, c->mesh, c->basis, c->gas, c->gs, c->gf, c->gl, c->tq,
-                                       c->qcm, inv_dtau, a0_dt, c->JP, c->JG, c->PP);
+    k_lin_point<N><<<nblk, TH, 0, s>>>(q, c->mesh, c->basis, c->gs, c->gf, c->gl, c->tq,
+                                       c->qcm, c->JP, c->JG, c->PP);
     FR_PROF_END(c, s, KK_LINEARIZE);
     FR_LAUNCH_CHECK(c);
   }
@@ -562,7 +565,7 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
   constexpr int EPB = Tile<N>::EPB, TH = Tile<N>::THREADS;
   const int nblk = (c->ne + EPB - 1) / EPB;
   const int nf = c->ne * 2 * N;
-  const bool visc = c->gas.viscous;
+  const bool visc = c->mesh.viscous;
   const double np = (double)c->ne * N * N;
   // algorithmic flops of the linear operator per solution point and per owned flux point
   const double fl_trace = fr_flops_trace(N, visc);
@@ -573,8 +576,8 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
     {
       FR_ACCOUNT(c, KK_LIN_APPLY, np * fl_trace, 0.0);
       FR_PROF_BEGIN(c, s);
-      k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(v)}, c->ne, c->basis,
-                                             c->gas, c->gs, Buf<double>{c->gl_d}, Buf<double>{c->tq_d},
+      k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(v)}, c->mesh, c->basis,
+                                             c->gs, Buf<double>{c->gl_d}, Buf<double>{c->tq_d},
                                              Buf<double>{c->tg_d});
       FR_PROF_END(c, s, KK_LIN_APPLY);
       FR_LAUNCH_CHECK(c);
@@ -582,7 +585,7 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
     {
       FR_ACCOUNT(c, KK_LIN_APPLY, nf * fl_face, 0.0);
       FR_PROF_BEGIN(c, s);
-      k_lin_face_apply<N><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->gas, c->tq_d, c->tg_d, c->JFQ,
+      k_lin_face_apply<N><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->tq_d, c->tg_d, c->JFQ,
                                                            c->JFG, c->fn_d, c->qcm_d);
       FR_PROF_END(c, s, KK_LIN_APPLY);
       FR_LAUNCH_CHECK(c);
@@ -590,7 +593,7 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
     {
       FR_ACCOUNT(c, KK_LIN_APPLY, np * fl_elem, 0.0);
       FR_PROF_BEGIN(c, s);
-      k_lin_elem_apply<N><<<nblk, TH, 0, s>>>(v, c->mesh, c->basis, c->gas, c->gs, c->gf, c->gl_d,
+      k_lin_elem_apply<N><<<nblk, TH, 0, s>>>(v, c->mesh, c->basis, c->gs, c->gf, c->gl_d,
                                               c->tq_d, c->fn_d, c->qcm_d, c->JP, c->JG, c->PP, out);
       FR_PROF_END(c, s, KK_LIN_APPLY);
       FR_LAUNCH_CHECK(c);
@@ -599,7 +602,7 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
     {
       FR_ACCOUNT(c, KK_LIN_ADJOINT, np * fl_elem, 0.0);
       FR_PROF_BEGIN(c, s);
-      k_lin_elem_adjoint<N><<<nblk, TH, 0, s>>>(v, c->mesh, c->basis, c->gas, c->gs, c->gf, c->JP,
+      k_lin_elem_adjoint<N><<<nblk, TH, 0, s>>>(v, c->mesh, c->basis, c->gs, c->gf, c->JP,
                                                 c->JG, c->PP, c->adj_q, c->gl_d, c->adj_fn, c->adj_qc);
       FR_PROF_END(c, s, KK_LIN_ADJOINT);
       FR_LAUNCH_CHECK(c);
@@ -607,7 +610,7 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
     {
       FR_ACCOUNT(c, KK_LIN_ADJOINT, nf * fl_face, 0.0);
       FR_PROF_BEGIN(c, s);
-      k_lin_face_adjoint<N><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->gas, c->JFQ, c->JFG, c->adj_fn,
+      k_lin_face_adjoint<N><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->JFQ, c->JFG, c->adj_fn,
                                                              c->adj_qc, c->tq_d, c->tg_d);
       FR_PROF_END(c, s, KK_LIN_ADJOINT);
       FR_LAUNCH_CHECK(c);
@@ -615,7 +618,7 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
     {
       FR_ACCOUNT(c, KK_LIN_ADJOINT, np * fl_trace, 0.0);
       FR_PROF_BEGIN(c, s);
-      k_lin_trace_adjoint<N><<<nblk, TH, 0, s>>>(c->mesh, c->basis, c->gas, c->gs, c->adj_q, c->gl_d,
+      k_lin_trace_adjoint<N><<<nblk, TH, 0, s>>>(c->mesh, c->basis, c->gs, c->adj_q, c->gl_d,
                                                  c->tq_d, c->tg_d, out);
       FR_PROF_END(c, s, KK_LIN_ADJOINT);
       FR_LAUNCH_CHECK(c);
@@ -625,11 +628,14 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
 }
 
 int linearize(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s) {
+  // the point-local block P' reads Gamma/dtau and a0/dt from the case parameters
+  const int rc = set_operator_terms(c, inv_dtau, a0_dt, s);
+  if (rc != FR_OK) return rc;
   switch (c->n) {
-    case 2: return linearize_n<2>(c, q, inv_dtau, a0_dt, s);
-    case 3: return linearize_n<3>(c, q, inv_dtau, a0_dt, s);
-    case 4: return linearize_n<4>(c, q, inv_dtau, a0_dt, s);
-    case 5: return linearize_n<5>(c, q, inv_dtau, a0_dt, s);
+    case 2: return linearize_n<2>(c, q, s);
+    case 3: return linearize_n<3>(c, q, s);
+    case 4: return linearize_n<4>(c, q, s);
+    case 5: return linearize_n<5>(c, q, s);
   }
   return FR_ERR_ARG;
 }

@@ -52,7 +52,9 @@ int run(const fr_config* cfg, int nx, int ny, const double* corners, const doubl
   const size_t b_tg = round256(sizeof(double) * ne * 32 * N);
   const size_t b_gl = round256(sizeof(double) * 8 * ne * NP);
   const size_t b_fn = round256(sizeof(double) * ne * 8 * N);
-  const size_t need = b_gs + b_gf + b_tq + b_tg + b_gl + 2 * b_fn;
+  const size_t b_nb = round256(sizeof(int) * ne * 5);
+  const size_t b_cp = round256(sizeof(CaseParams));
+  const size_t need = b_gs + b_gf + b_tq + b_tg + b_gl + 2 * b_fn + b_nb + b_cp;
   if (need > kScratchBytes) return FR_ERR_ARG;
   void* base = nullptr;
   int rc = scratch_address(&base);
@@ -64,23 +66,30 @@ int run(const fr_config* cfg, int nx, int ny, const double* corners, const doubl
   double* tg = reinterpret_cast<double*>(p); p += b_tg;
   double* gl = reinterpret_cast<double*>(p); p += b_gl;
   double* fn = reinterpret_cast<double*>(p); p += b_fn;
-  double* qc = reinterpret_cast<double*>(p);
+  double* qc = reinterpret_cast<double*>(p); p += b_fn;
+  int* nbr = reinterpret_cast<int*>(p);
+  int* ecase = nbr + 4 * ne;
+  p += b_nb;
+  CaseParams* cpd = reinterpret_cast<CaseParams*>(p);
   const Basis B = fr_make_basis(N - 1);
-  const Gas G = fr_make_gas(*cfg);
+  CaseParams cp;
+  cp.gas = fr_make_gas(*cfg);
+  cp.a0dt = cp.a1dt = cp.a2dt = cp.inv_dtau = cp.a0_dt = 0.0;
   Mesh M;
-  M.nx = nx; M.ny = ny; M.ne = (int)ne;
+  M.nbr = nbr; M.ecase = ecase; M.cp = cpd; M.ne = (int)ne; M.viscous = cp.gas.viscous;
+  k_fill_topo<<<(unsigned)((ne + 127) / 128), 128, 0, s>>>(nx, ny, 0, 0, nbr, ecase);
+  k_set_case<<<1, 1, 0, s>>>(cpd, 0, cp);
   k_geometry<N><<<(unsigned)((ne + 63) / 64), 64, 0, s>>>(corners, vel, (int)ne, B, gs, gf);
   const int nblk = (int)((ne + EPB - 1) / EPB);
-  k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(q)}, (int)ne, B, G, gs,
+  k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(q)}, M, B, gs,
                                          Buf<double>{gl}, Buf<double>{tq}, Buf<double>{tg});
   const int nf = (int)(ne * 2 * N);
-  k_face<double, N><<<(nf + 127) / 128, 128, 0, s>>>(M, B, G, gf, Buf<double>{tq}, Buf<double>{tg},
+  k_face<double, N><<<(nf + 127) / 128, 128, 0, s>>>(M, B, gf, Buf<double>{tq}, Buf<double>{tg},
                                                     Buf<double>{fn}, Buf<double>{qc});
-  TimeTerms tt{nullptr, nullptr, 0, 0, 0};
-  k_elem<double, N, MODE_RESID><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(q)}, M, B, G,
+  TimeTerms tt{nullptr, nullptr};
+  k_elem<double, N, MODE_RESID><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(q)}, M, B,
                                                     gs, gf, Buf<double>{gl}, Buf<double>{tq},
-                                                    Buf<double>{fn}, Buf<double>{qc}, R, tt,
-                                                    JvpTerms{0, 0});
+                                                    Buf<double>{fn}, Buf<double>{qc}, R, tt);
   return cudaGetLastError() == cudaSuccess ? FR_OK : FR_ERR_CUDA;
 }
 

@@ -25,10 +25,9 @@ template <int N> struct BlkSmem {
 
 template <int N>
 __global__ void __launch_bounds__(BG * N * N)
-k_block(const double* __restrict__ q, Mesh M, Basis B, Gas gas, const double* __restrict__ gs,
+k_block(const double* __restrict__ q, Mesh M, Basis B, const double* __restrict__ gs,
         const double* __restrict__ gf, const double* __restrict__ tqv,
-        const double* __restrict__ tgv, double inv_dtau, double a0_dt,
-        double* __restrict__ Bout) {
+        const double* __restrict__ tgv, double* __restrict__ Bout) {
   constexpr int NP = N * N, BS = 4 * NP;
   using L = BlkSmem<N>;
   extern __shared__ Dual smem_dual[];
@@ -48,6 +47,9 @@ k_block(const double* __restrict__ q, Mesh M, Basis B, Gas gas, const double* __
   const size_t FNs = (size_t)M.ne * 4 * N;
   const size_t o = (size_t)e * NP + pt;
   const int nbL = M.left(e), nbR = M.right(e), nbB = M.bottom(e), nbT = M.top(e);
+  const CaseParams& cpar = M.par(e);
+  const Gas& gas = cpar.gas;
+  const double inv_dtau = cpar.inv_dtau, a0_dt = cpar.a0_dt;
   double qv[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) qv[v] = q[v * SN + o];
@@ -65,7 +67,7 @@ k_block(const double* __restrict__ q, Mesh M, Basis B, Gas gas, const double* __
     for (int v = 0; v < 4; ++v) sq[v * NP + pt] = mk(qv[v], (v * NP + pt == d) ? 1.0 : 0.0);
     __syncthreads();
     // B: local gradients
-    if (gas.viscous) {
+    if (M.viscous) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         Dual dxi = B.D[i][0] * sq[v * NP + j * N];
@@ -92,7 +94,7 @@ k_block(const double* __restrict__ q, Mesh M, Basis B, Gas gas, const double* __
         for (int k = 1; k < N; ++k) acc = acc + w[k] * sq[c * NP + (row ? s * N + k : k * N + s)];
         stq[(f * 4 + c) * N + s] = acc;
       }
-      if (gas.viscous) {
+      if (M.viscous) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           Dual acc = w[0] * sg[c * NP + (row ? s * N : s)];
@@ -121,7 +123,7 @@ k_block(const double* __restrict__ q, Mesh M, Basis B, Gas gas, const double* __
         qm[v] = e_minus ? mine : theirs;
         qp[v] = e_minus ? theirs : mine;
       }
-      if (gas.viscous) {
+      if (M.viscous) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const Dual mine = stg[(f * 8 + c) * N + s];
@@ -150,7 +152,7 @@ k_block(const double* __restrict__ q, Mesh M, Basis B, Gas gas, const double* __
     Dual fx[4], gy[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) { fx[v] = th.f[v]; gy[v] = th.g[v]; }
-    if (gas.viscous) {
+    if (M.viscous) {
       Dual qx[4], qy[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) { qx[v] = sg[v * NP + pt]; qy[v] = sg[(4 + v) * NP + pt]; }
@@ -352,7 +354,11 @@ static int block_build_n(fr_ctx* c, const double* q, double inv_dtau, double a0_
   // value traces of every element (neighbour data of the blocks)
   constexpr int EPB = Tile<N>::EPB, TH = Tile<N>::THREADS;
   const int nblk = (c->ne + EPB - 1) / EPB;
-  const bool visc = c->gas.viscous;
+  const bool visc = c->mesh.viscous;
+  {
+    const int rc = set_operator_terms(c, inv_dtau, a0_dt, s);
+    if (rc != FR_OK) return rc;
+  }
   FR_ACCOUNT(c, KK_TRACE, (double)c->ne * N * N * fr_flops_trace(N, visc), 0.0);
   // per element and tangent direction: gradients + traces, 4n face points, n^2 element points
   FR_ACCOUNT(c, KK_BLOCK, (double)c->ne * c->bsz * FR_JVP_FLOP_FACTOR *
@@ -360,8 +366,8 @@ static int block_build_n(fr_ctx* c, const double* q, double inv_dtau, double a0_
                                4.0 * N * fr_flops_face_point(visc)), 0.0);
   {
     FR_PROF_BEGIN(c, s);
-    k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(q)}, c->ne, c->basis,
-                                           c->gas, c->gs, Buf<double>{c->gl}, Buf<double>{c->tq},
+    k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(q)}, c->mesh, c->basis,
+                                           c->gs, Buf<double>{c->gl}, Buf<double>{c->tq},
                                            Buf<double>{c->tg});
     FR_PROF_END(c, s, KK_TRACE);
     FR_LAUNCH_CHECK(c);
@@ -369,8 +375,8 @@ static int block_build_n(fr_ctx* c, const double* q, double inv_dtau, double a0_
   const size_t smem = (size_t)BG * BlkSmem<N>::SIZE * sizeof(Dual);
   FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_block<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FR_PROF_BEGIN(c, s);
-  k_block<N><<<c->ne, BG * N * N, smem, s>>>(q, c->mesh, c->basis, c->gas, c->gs, c->gf, c->tq,
-                                             c->tg, inv_dtau, a0_dt, c->B64);
+  k_block<N><<<c->ne, BG * N * N, smem, s>>>(q, c->mesh, c->basis, c->gs, c->gf, c->tq,
+                                             c->tg, c->B64);
   FR_PROF_END(c, s, KK_BLOCK);
   FR_LAUNCH_CHECK(c);
   return FR_OK;

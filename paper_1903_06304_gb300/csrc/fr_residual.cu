@@ -16,7 +16,7 @@
 
 namespace fr {
 
-__global__ void k_conservative(const double* __restrict__ q, size_t SN, Gas gas,
+__global__ void k_conservative(const double* __restrict__ q, size_t SN, int np2, Mesh M,
                                double* __restrict__ qc) {
   const size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (o >= SN) return;
@@ -24,7 +24,7 @@ __global__ void k_conservative(const double* __restrict__ q, size_t SN, Gas gas,
 #pragma unroll
   for (int v = 0; v < 4; ++v) qq[v] = q[v * SN + o];
   Thermo<double> th;
-  thermo(qq, gas, th);
+  thermo(qq, M.par((int)(o / np2)).gas, th);
 #pragma unroll
   for (int v = 0; v < 4; ++v) qc[v * SN + o] = th.qc[v];
 }
@@ -32,32 +32,32 @@ __global__ void k_conservative(const double* __restrict__ q, size_t SN, Gas gas,
 // ------------------------------------------------------------------ launchers
 template <class T, int N, int MODE>
 static int run_pipeline(fr_ctx* c, Buf<T> Q, Buf<T> GL, Buf<T> TQ, Buf<T> TG, Buf<T> FNb,
-                        Buf<T> QCb, double* out, TimeTerms tt, JvpTerms jt, cudaStream_t s) {
+                        Buf<T> QCb, double* out, TimeTerms tt, cudaStream_t s) {
   constexpr int EPB = Tile<N>::EPB, TH = Tile<N>::THREADS;
   constexpr bool jvp = MODE == MODE_JVP;
   const int nblk = (c->ne + EPB - 1) / EPB;
-  const bool visc = c->gas.viscous;
+  const bool visc = c->mesh.viscous;
   const double pts = (double)c->ne * N * N, fac = jvp ? FR_JVP_FLOP_FACTOR : 1.0;
   FR_ACCOUNT(c, jvp ? KK_TRACE_JVP : KK_TRACE, fac * pts * fr_flops_trace(N, visc), 0.0);
   FR_ACCOUNT(c, jvp ? KK_FACE_JVP : KK_FACE, fac * 2.0 * c->ne * N * fr_flops_face_point(visc), 0.0);
   FR_ACCOUNT(c, jvp ? KK_ELEM_JVP : KK_ELEM, fac * pts * fr_flops_elem(N, visc), 0.0);
   {
     FR_PROF_BEGIN(c, s);
-    k_trace<T, N><<<nblk, TH, 0, s>>>(Q, c->ne, c->basis, c->gas, c->gs, GL, TQ, TG);
+    k_trace<T, N><<<nblk, TH, 0, s>>>(Q, c->mesh, c->basis, c->gs, GL, TQ, TG);
     FR_PROF_END(c, s, jvp ? KK_TRACE_JVP : KK_TRACE);
     FR_LAUNCH_CHECK(c);
   }
   {
     const int nf = c->ne * 2 * N;
     FR_PROF_BEGIN(c, s);
-    k_face<T, N><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->basis, c->gas, c->gf, TQ, TG, FNb, QCb);
+    k_face<T, N><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->basis, c->gf, TQ, TG, FNb, QCb);
     FR_PROF_END(c, s, jvp ? KK_FACE_JVP : KK_FACE);
     FR_LAUNCH_CHECK(c);
   }
   {
     FR_PROF_BEGIN(c, s);
-    k_elem<T, N, MODE><<<nblk, TH, 0, s>>>(Q, c->mesh, c->basis, c->gas, c->gs, c->gf, GL, TQ, FNb,
-                                           QCb, out, tt, jt);
+    k_elem<T, N, MODE><<<nblk, TH, 0, s>>>(Q, c->mesh, c->basis, c->gs, c->gf, GL, TQ, FNb,
+                                           QCb, out, tt);
     FR_PROF_END(c, s, jvp ? KK_ELEM_JVP : KK_ELEM);
     FR_LAUNCH_CHECK(c);
   }
@@ -69,17 +69,16 @@ static int residual_n(fr_ctx* c, const double* q, double* out, TimeTerms tt, cud
   Buf<double> Q{const_cast<double*>(q)};
   return run_pipeline<double, N, MODE_RESID>(c, Q, Buf<double>{c->gl}, Buf<double>{c->tq},
                                              Buf<double>{c->tg}, Buf<double>{c->fn},
-                                             Buf<double>{c->qcm}, out, tt, JvpTerms{0, 0}, s);
+                                             Buf<double>{c->qcm}, out, tt, s);
 }
 
 template <int N>
-static int jvp_n(fr_ctx* c, const double* q, const double* v, double* out, JvpTerms jt,
-                 cudaStream_t s) {
+static int jvp_n(fr_ctx* c, const double* q, const double* v, double* out, cudaStream_t s) {
   Buf<Dual> Q{const_cast<double*>(q), const_cast<double*>(v)};
-  TimeTerms tt{nullptr, nullptr, 0, 0, 0};
+  TimeTerms tt{nullptr, nullptr};
   return run_pipeline<Dual, N, MODE_JVP>(c, Q, Buf<Dual>{c->gl, c->gl_d}, Buf<Dual>{c->tq, c->tq_d},
                                          Buf<Dual>{c->tg, c->tg_d}, Buf<Dual>{c->fn, c->fn_d},
-                                         Buf<Dual>{c->qcm, c->qcm_d}, out, tt, jt, s);
+                                         Buf<Dual>{c->qcm, c->qcm_d}, out, tt, s);
 }
 
 }  // namespace fr
@@ -105,6 +104,34 @@ const double FR_JVP_FLOP_FACTOR = 3.0;
 namespace frk {
 using namespace fr;
 
+int set_case_params(fr_ctx* c, int cid, const CaseParams& p, cudaStream_t s) {
+  k_set_case<<<1, 1, 0, s>>>(c->cp, cid, p);
+  FR_LAUNCH_CHECK(c);
+  return FR_OK;
+}
+
+// The single-case context keeps a host copy of case 0's parameters and rewrites the
+// device copy only when a call changes them (stream-ordered, by a one-thread kernel).
+int set_time_terms(fr_ctx* c, double a0dt, double a1dt, double a2dt, cudaStream_t s) {
+  CaseParams& h = c->cp_h;
+  if (h.a0dt == a0dt && h.a1dt == a1dt && h.a2dt == a2dt) return FR_OK;
+  h.a0dt = a0dt; h.a1dt = a1dt; h.a2dt = a2dt;
+  return set_case_params(c, 0, h, s);
+}
+
+int set_operator_terms(fr_ctx* c, double inv_dtau, double a0_dt, cudaStream_t s) {
+  CaseParams& h = c->cp_h;
+  if (h.inv_dtau == inv_dtau && h.a0_dt == a0_dt) return FR_OK;
+  h.inv_dtau = inv_dtau; h.a0_dt = a0_dt;
+  return set_case_params(c, 0, h, s);
+}
+
+int fill_topology(fr_ctx* c, int nx, int ny, int e0, int cid, cudaStream_t s) {
+  k_fill_topo<<<(nx * ny + 127) / 128, 128, 0, s>>>(nx, ny, e0, cid, c->nbr, c->ecase);
+  FR_LAUNCH_CHECK(c);
+  return FR_OK;
+}
+
 int geometry(fr_ctx* c, const double* corners, const double* vel, cudaStream_t s) {
   const int th = 64, nb = (c->ne + th - 1) / th;
   FR_PROF_BEGIN(c, s);
@@ -122,7 +149,11 @@ int geometry(fr_ctx* c, const double* corners, const double* vel, cudaStream_t s
 
 int residual(fr_ctx* c, const double* q, double* out, const double* qcn, const double* qcnm1,
              double a0dt, double a1dt, double a2dt, cudaStream_t s) {
-  TimeTerms tt{qcn, qcnm1, a0dt, a1dt, a2dt};
+  if (qcn) {
+    const int rc = set_time_terms(c, a0dt, a1dt, a2dt, s);
+    if (rc != FR_OK) return rc;
+  }
+  TimeTerms tt{qcn, qcnm1};
   switch (c->n) {
     case 2: return residual_n<2>(c, q, out, tt, s);
     case 3: return residual_n<3>(c, q, out, tt, s);
@@ -134,12 +165,13 @@ int residual(fr_ctx* c, const double* q, double* out, const double* qcn, const d
 
 int jvp(fr_ctx* c, const double* q, const double* v, double inv_dtau, double a0_dt, double* out,
         cudaStream_t s) {
-  JvpTerms jt{inv_dtau, a0_dt};
+  const int rc = set_operator_terms(c, inv_dtau, a0_dt, s);
+  if (rc != FR_OK) return rc;
   switch (c->n) {
-    case 2: return jvp_n<2>(c, q, v, out, jt, s);
-    case 3: return jvp_n<3>(c, q, v, out, jt, s);
-    case 4: return jvp_n<4>(c, q, v, out, jt, s);
-    case 5: return jvp_n<5>(c, q, v, out, jt, s);
+    case 2: return jvp_n<2>(c, q, v, out, s);
+    case 3: return jvp_n<3>(c, q, v, out, s);
+    case 4: return jvp_n<4>(c, q, v, out, s);
+    case 5: return jvp_n<5>(c, q, v, out, s);
   }
   return FR_ERR_ARG;
 }
@@ -148,7 +180,7 @@ int conservative(fr_ctx* c, const double* q, double* qc, cudaStream_t s) {
   const size_t SN = (size_t)c->ne * c->np2;
   FR_ACCOUNT(c, KK_CONS, 0.0, 8.0 * 8.0 * SN);
   FR_PROF_BEGIN(c, s);
-  k_conservative<<<(unsigned)((SN + 255) / 256), 256, 0, s>>>(q, SN, c->gas, qc);
+  k_conservative<<<(unsigned)((SN + 255) / 256), 256, 0, s>>>(q, SN, c->np2, c->mesh, qc);
   FR_PROF_END(c, s, KK_CONS);
   FR_LAUNCH_CHECK(c);
   return FR_OK;

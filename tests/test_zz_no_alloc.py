@@ -57,5 +57,5 @@ def test_noalloc_rejects_meshes_beyond_the_scratch(torch):
     cc = fr.Config(p=3).to_c()
     dummy = torch.zeros(8, dtype=torch.float64, device="cuda:0")
     stream = torch.cuda.current_stream().cuda_stream
-    # 81 x 81 = 6561 elements > 6553 at p = 3: refused before the pointers are touched
+    # 81 x 81 = 6561 elements > 6528 at p = 3: refused before the pointers are touched
     assert _noalloc(lib, cc, 81, 81, dummy, dummy, dummy, dummy, stream) == -1
