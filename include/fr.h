@@ -245,6 +245,62 @@ int fr_residual_noalloc(const fr_config* cfg, int nx, int ny, const double* corn
                         const double* corner_vel_d, const double* qp_d, double* R_d,
                         void* stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent problems solved together (the paper solves one at a time; Sec. 3.2's
+ * loop is applied to each case).  Cases may differ in polynomial degree, mesh size and
+ * gas (Mach, Reynolds, kappa); gamma, Pr, eps_floor and every solver setting come from
+ * the batch's fr_config.  Cases of equal degree and equal viscous switch form a group;
+ * every kernel of a group runs over all of the group's elements in one launch, with
+ * per-case parameters, per-case reductions, per-case GMRES state and a per-case Newton
+ * loop (a case stops iterating when it converges; the group stops when all have).
+ * Groups run concurrently, each on its own stream and host thread.
+ *
+ * Layout: a batch state vector (device, FP64) is the concatenation of the cases' states,
+ * each in the single-case layout [4][Ne_k][n_k][n_k]; fr_batch_case_info gives case k's
+ * offset and length (the cases of one group are adjacent, so offsets follow the group
+ * order, not the case order).  Corner arrays concatenate [Ne_k][4][2] blocks at the
+ * element offsets.  The restart length must be <= 32 (device-resident Arnoldi). */
+typedef struct fr_case {
+  int p;                    /* polynomial degree 1..4 */
+  int nx, ny;               /* doubly periodic box of nx x ny elements (>= 2 each) */
+  double mach, re, kappa;   /* free-stream Mach, Reynolds (<= 0: Euler), eps factor */
+} fr_case;
+typedef struct fr_batch fr_batch;
+
+/* Create a batch of ncases cases on the current device (host arrays; copied).
+ * FR_ERR_ARG on a bad case or config (*out stays NULL), FR_ERR_CUDA on allocation. */
+int fr_batch_create(const fr_config* cfg, const fr_case* cases, int ncases, fr_batch** out);
+void fr_batch_destroy(fr_batch* b);
+/* Case k's DOF offset and length in batch vectors, element offset and count. */
+int fr_batch_case_info(const fr_batch* b, int k, size_t* dof_offset, size_t* ndof,
+                       size_t* elem_offset, size_t* nelem);
+size_t fr_batch_num_dof(const fr_batch* b);
+size_t fr_batch_num_elements(const fr_batch* b);
+int fr_batch_num_groups(const fr_batch* b);
+/* Geometry of every case from concatenated corners / corner velocities (device). */
+int fr_batch_update_mesh(fr_batch* b, const double* corners_d, const double* corner_vel_d,
+                         void* stream);
+/* R(q^p) of every case (as fr_residual), and the conservative variables (as
+ * fr_conservative).  Asynchronous on stream. */
+int fr_batch_residual(fr_batch* b, const double* qp_d, double* R_d, void* stream);
+int fr_batch_conservative(fr_batch* b, const double* qp_d, double* qc_d, void* stream);
+/* One BDF2 step of every case (as fr_bdf2_step): coef (host [ncases][4]) holds case k's
+ * a0, a1, a2, dt; a2 = 0 makes it a BDF1 step and qc_nm1_d is then not read for it
+ * (qc_nm1_d may be NULL if every a2 is 0).  stats (host [ncases], may be NULL) is filled
+ * per case.  Synchronises.  FR_ERR_NOT_CONVERGED if some case reached maxit_newton,
+ * FR_ERR_NONFINITE if some case produced a non-finite value (other cases are still
+ * advanced: cases never interact). */
+int fr_batch_bdf2_step(fr_batch* b, double* qp_d, const double* qc_n_d, const double* qc_nm1_d,
+                       const double* coef, fr_stats* stats, void* stream);
+/* Steady PTC with SER for every case (as fr_ptc_solve). */
+int fr_batch_ptc_solve(fr_batch* b, double* qp_d, fr_stats* stats, void* stream);
+/* Instrumentation summed over the groups (as fr_profile / fr_profile_read). */
+int fr_batch_profile(fr_batch* b, int enable);
+int fr_batch_profile_read(fr_batch* b, double* ms, long long* counts, long long* launches,
+                          double* flops, double* bytes, int reset);
+long long fr_batch_kernel_launches(const fr_batch* b);
+const char* fr_batch_last_error(const fr_batch* b);
+
 /* Sizes: number of FP64 entries of a solution vector, block size b. */
 size_t fr_num_dof(const fr_ctx* ctx);
 int fr_block_size(const fr_ctx* ctx);

@@ -135,15 +135,11 @@ void free_mesh(fr_ctx* c) {
   if (c->ecase) { cudaFree(c->ecase); c->ecase = nullptr; }
   c->blocks_ready = 0;
   c->lin_ready = 0;
+  frk::batch_free(c);
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-#define FR_TRY(expr)                 \
-  do {                               \
-    int rc_ = (expr);                \
-    if (rc_ != FR_OK) return rc_;    \
-  } while (0)
 
 int check_ready(fr_ctx* c) {
   if (!c) return FR_ERR_ARG;
@@ -537,6 +533,9 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
   c->cp_h.gas = c->gas;
   c->cp_h.a0dt = c->cp_h.a1dt = c->cp_h.a2dt = 0.0;
   c->cp_h.inv_dtau = c->cp_h.a0_dt = 0.0;
+  c->cp_h.off = 0;
+  c->cp_h.e0 = 0;
+  c->cp_h.sn = 0;
   if (cudaMalloc((void**)&c->dsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&c->hsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&c->gst, sizeof(GmresState)) != cudaSuccess ||
@@ -568,17 +567,44 @@ int fr_set_mesh(fr_ctx* c, int nx, int ny, int px, int py) {
     snprintf(c->err, sizeof(c->err), "fr_set_mesh: need nx, ny >= 2 and periodic_x = periodic_y = 1");
     return FR_ERR_ARG;
   }
+  return fr_setup_cases(c, 1, &nx, &ny, &c->cp_h);
+}
+
+}  // extern "C"
+
+int fr_setup_cases(fr_ctx* c, int ncases, const int* nxs, const int* nys,
+                   const fr::CaseParams* params) {
   free_mesh(c);
-  c->nx = nx; c->ny = ny; c->ne = nx * ny;
+  long long ne_total = 0;
+  for (int k = 0; k < ncases; ++k) ne_total += (long long)nxs[k] * nys[k];
+  if (ncases < 1 || ne_total * c->np2 * 4 > (1LL << 31) - 1) {
+    snprintf(c->err, sizeof(c->err), "setup: %d cases, %lld elements", ncases, ne_total);
+    return FR_ERR_ARG;
+  }
+  c->nx = nxs[0]; c->ny = nys[0]; c->ne = (int)ne_total;
+  c->ncases = ncases;
+  c->cps.assign(params, params + ncases);
   FR_TRY(dev_alloc(c, &c->nbr, (size_t)4 * c->ne));
   FR_TRY(dev_alloc(c, &c->ecase, (size_t)c->ne));
+  FR_TRY(dev_alloc(c, &c->cp, (size_t)ncases));
   c->mesh.nbr = c->nbr;
   c->mesh.ecase = c->ecase;
   c->mesh.cp = c->cp;
   c->mesh.ne = c->ne;
   c->mesh.viscous = c->gas.viscous;
-  FR_TRY(frk::fill_topology(c, nx, ny, 0, 0, 0));
-  FR_TRY(frk::set_case_params(c, 0, c->cp_h, 0));
+  // cases in order: elements [e0, e0 + nx ny), states contiguous from off
+  long long e0 = 0;
+  for (int k = 0; k < ncases; ++k) {
+    fr::CaseParams& p = c->cps[k];
+    p.e0 = (int)e0;
+    p.off = 4 * e0 * c->np2;
+    p.sn = nxs[k] * nys[k] * c->np2;
+    FR_TRY(frk::fill_topology(c, nxs[k], nys[k], (int)e0, k, 0));
+    e0 += (long long)nxs[k] * nys[k];
+  }
+  c->cp_h = c->cps[0];
+  FR_CUDA_CHECK(c, cudaMemcpy(c->cp, c->cps.data(), ncases * sizeof(fr::CaseParams),
+                              cudaMemcpyHostToDevice));
   FR_CUDA_CHECK(c, cudaStreamSynchronize(0));
   const size_t ne = c->ne, n = c->n, np2 = c->np2, bs = c->bsz;
   c->ndof = 4 * ne * np2;
@@ -624,6 +650,8 @@ int fr_set_mesh(fr_ctx* c, int nx, int ny, int px, int py) {
   FR_CUDA_CHECK(c, cudaMemset(c->ticket, 0, sizeof(unsigned int)));
   return FR_OK;
 }
+
+extern "C" {
 
 int fr_update_mesh(fr_ctx* c, const double* corners, const double* vel, void* s) {
   FR_TRY(check_ready(c));

@@ -49,6 +49,11 @@ struct CaseParams {
   Gas gas;
   double a0dt, a1dt, a2dt;
   double inv_dtau, a0_dt;
+  // layout of the case in the state vectors the kernels read and write: the case's
+  // values are contiguous, [variable][element of the case][point], from DOF offset off;
+  // e0 is its first element in the launch's element numbering, sn = elements x points.
+  long long off;
+  int e0, sn;
 };
 
 // Element topology of one launch: face neighbours (L, R, B, T) by global element index,
@@ -65,6 +70,13 @@ struct Mesh {
   __device__ __forceinline__ int bottom(int e) const { return nbr[4 * e + FACE_B]; }
   __device__ __forceinline__ int top(int e) const { return nbr[4 * e + FACE_T]; }
   __device__ __forceinline__ const CaseParams& par(int e) const { return cp[ecase[e]]; }
+  // index of variable 0 at point 0 of element e in a state vector, and the stride
+  // between the variables of e's case
+  __device__ __forceinline__ size_t qbase(int e, int np) const {
+    const CaseParams& c = par(e);
+    return (size_t)c.off + (size_t)(e - c.e0) * np;
+  }
+  __device__ __forceinline__ size_t qstride(int e) const { return (size_t)par(e).sn; }
 };
 
 // ---------------------------------------------------------------- dual numbers

@@ -20,6 +20,37 @@ struct GmresState {
   int nonfinite;
 };
 
+// Per-case partition of a batch's vectors for the batched vector kernels: block b works
+// on the pair range [blo[b], bhi[b]) of case bcase[b]; case k owns blocks cb0[k] ..
+// cb0[k] + cnb[k] - 1 (device arrays).
+struct BatchSegs {
+  const int* bcase;
+  const long long* blo;
+  const long long* bhi;
+  const int* cb0;
+  const int* cnb;
+};
+
+// Workspace of the batched Krylov and Newton loops (allocated by frk::batch_setup).
+struct BatchWork {
+  int nblk = 0;                    // blocks of one batched vector launch
+  BatchSegs sg{};
+  int *bcase = nullptr, *cb0 = nullptr, *cnb = nullptr;
+  long long *blo = nullptr, *bhi = nullptr, *mend = nullptr;
+  double* partial = nullptr;       // [32][nblk]
+  unsigned int* tickets = nullptr; // [ncases], kept at 0
+  double* dsc = nullptr;           // [ncases][128] per-case scalars
+  double* hsc = nullptr;           // pinned mirror
+  GmresState* gst = nullptr;       // [ncases]
+  GmresState* gst_h = nullptr;     // pinned mirror
+  int4* status = nullptr;          // [ncases] (j, jmax, done, nonfinite)
+  int4* status_h = nullptr;
+  double* coef = nullptr;          // [ncases] per-case coefficients
+  double* coef_h = nullptr;        // pinned staging
+  fr::CaseParams* cp_stage = nullptr;   // pinned staging of the case table
+  cudaEvent_t staged = nullptr;    // the last upload from pinned staging has completed
+};
+
 // Kernel classes for the optional per-kernel timing (fr_profile) and launch counts.
 enum FrKernel {
   KK_GEOM, KK_TRACE, KK_FACE, KK_ELEM, KK_TRACE_JVP, KK_FACE_JVP, KK_ELEM_JVP, KK_BLOCK,
@@ -52,7 +83,10 @@ struct fr_ctx {
   int* ecase = nullptr;        // [Ne] case of each element
   fr::CaseParams* cp = nullptr;  // [ncases] device
   fr::CaseParams cp_h;         // host copy of case 0's parameters
+  std::vector<fr::CaseParams> cps;   // host copies of every case's parameters
   int ncases = 1;
+  bool external_terms = false;  // time and operator terms are set per case by the caller
+  BatchWork bw;                 // batched loops (cases of one degree and viscous switch)
   // geometry (Sec. 2.3)
   double* gs = nullptr;   // [GS_COUNT][Ne*np2]
   double* gf = nullptr;   // [GF_COUNT][Ne*4*n]
@@ -118,6 +152,12 @@ void fr_prof_end(fr_ctx* c, cudaStream_t s, cudaEvent_t begin, int kind);
 fr::Basis fr_make_basis(int p);
 fr::Gas fr_make_gas(const fr_config& c);
 
+// Topology, case table and workspace of ncases doubly periodic boxes of nxs[k] x nys[k]
+// elements, numbered case after case; params supplies each case's gas and terms (its
+// layout fields are filled here).  Synchronous.
+int fr_setup_cases(fr_ctx* c, int ncases, const int* nxs, const int* nys,
+                   const fr::CaseParams* params);
+
 namespace frk {
 int set_case_params(fr_ctx* c, int cid, const fr::CaseParams& p, cudaStream_t s);
 int set_time_terms(fr_ctx* c, double a0dt, double a1dt, double a2dt, cudaStream_t s);
@@ -147,6 +187,16 @@ int gm_copy_in(fr_ctx* c, double* dst, cudaStream_t s);
 int gm_orthogonalize(fr_ctx* c, double* w, double* next, int nv_bound, cudaStream_t s);
 int gm_trisolve(fr_ctx* c, cudaStream_t s);
 int axpby(fr_ctx* c, double a, const double* x, double b, double* y, cudaStream_t s);
+// Batched (per-case) forms; scalars of case k at bw.dsc + k * 128.
+int batch_setup(fr_ctx* c);
+void batch_free(fr_ctx* c);
+int bk_norms(fr_ctx* c, const double* r, cudaStream_t s);         // -> [k][96..97]
+int bk_init(fr_ctx* c, const double* r, double* next, cudaStream_t s);
+int bk_orthogonalize(fr_ctx* c, double* w, double* next, int nv_bound, cudaStream_t s);
+int bk_finish(fr_ctx* c, double* u, cudaStream_t s);              // trisolve + combination
+int bk_status(fr_ctx* c, cudaStream_t s);                         // -> bw.status_h (async)
+int bk_axpy_case(fr_ctx* c, const double* coef_dev, const double* x, double* y, cudaStream_t s);
+int upload_cases(fr_ctx* c, cudaStream_t s);                      // c->cps -> device
 }  // namespace frk
 
 #define FR_CUDA_CHECK(c, expr)                                                       \
@@ -157,6 +207,12 @@ int axpby(fr_ctx* c, double a, const double* x, double b, double* y, cudaStream_
                cudaGetErrorString(e_), __FILE__, __LINE__);                          \
       return FR_ERR_CUDA;                                                            \
     }                                                                                \
+  } while (0)
+
+#define FR_TRY(expr)                 \
+  do {                               \
+    int rc_ = (expr);                \
+    if (rc_ != FR_OK) return rc_;    \
   } while (0)
 
 #define FR_LAUNCH_CHECK(c)                                                           \

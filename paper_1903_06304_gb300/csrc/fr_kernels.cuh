@@ -137,8 +137,9 @@ k_trace(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs, Buf<T> GL, Buf
   const size_t SN = (size_t)ne * NP;
   const size_t o = (size_t)e * NP + pt;
   if (live) {
+    const size_t qo = M.qbase(e, NP) + pt, qs = M.qstride(e);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) sq[le][v][pt] = Q.ld(v * SN + o);
+    for (int v = 0; v < 4; ++v) sq[le][v][pt] = Q.ld(v * qs + qo);
   }
   __syncthreads();
   if (M.viscous) {
@@ -284,9 +285,10 @@ k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
   double ij = 0.0;
   const CaseParams& cpar = M.par(live ? e : 0);
   const Gas& gas = cpar.gas;
+  const size_t qo = live ? M.qbase(e, NP) + pt : 0, qs = cpar.sn;
   if (live) {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) q[v] = Q.ld(v * SN + o);
+    for (int v = 0; v < 4; ++v) q[v] = Q.ld(v * qs + qo);
     thermo(q, gas, th);
     ij = gs[GS_INVJ * SN + o];
     T fx[4], gy[4];
@@ -353,11 +355,11 @@ k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
     for (int v = 0; v < 4; ++v) {
       double r = val(R[v]);
       if (tt.qcn) {
-        double acc = cpar.a0dt * val(th.qc[v]) + cpar.a1dt * tt.qcn[v * SN + o];
-        if (tt.qcnm1) acc += cpar.a2dt * tt.qcnm1[v * SN + o];
+        double acc = cpar.a0dt * val(th.qc[v]) + cpar.a1dt * tt.qcn[v * qs + qo];
+        if (tt.qcnm1 && cpar.a2dt != 0.0) acc += cpar.a2dt * tt.qcnm1[v * qs + qo];
         r -= acc;
       }
-      out[v * SN + o] = r;
+      out[v * qs + qo] = r;
     }
   } else {
     double qv[4], wv[4], gm[4];
@@ -365,7 +367,7 @@ k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
     for (int v = 0; v < 4; ++v) { qv[v] = val(q[v]); wv[v] = tan_(q[v]); }
     gamma_m_apply(qv, wv, gs[GS_UG * SN + o], gs[GS_VG * SN + o], gas, cpar.inv_dtau, cpar.a0_dt, gm);
 #pragma unroll
-    for (int v = 0; v < 4; ++v) out[v * SN + o] = gm[v] - tan_(R[v]);
+    for (int v = 0; v < 4; ++v) out[v * qs + qo] = gm[v] - tan_(R[v]);
   }
 }
 

@@ -1,6 +1,7 @@
 // fr_krylov.cu -- FP64 vector kernels of restarted GMRES with CGS2 (Sec. 3.2) and the
 // pseudo-step residual norms.  Reductions are deterministic: a fixed grid writes one
 // partial per block and the last block to finish sums the partials in a fixed order.
+#include <algorithm>
 #include <cstdio>
 #include "fr_internal.h"
 
@@ -42,12 +43,15 @@ __device__ __forceinline__ double warp_transpose_sum(double (&acc)[NA]) {
 }
 
 // Block sums of nv per-thread values: partial[k * gridDim.x + blockIdx.x].  The last
-// block to finish (atomic ticket, no waiting) then sums the partials of every k in a
-// fixed order and writes out[k]: one launch per reduction, deterministic result.
-// Returns true in the last block (after out[] is written and visible to the block).
+// of the nb blocks b0 .. b0 + nb - 1 that share the ticket to finish (atomic ticket, no
+// waiting) then sums their partials of every k in a fixed order and writes out[k]: one
+// launch per reduction, deterministic result.  A whole-grid reduction passes b0 = 0,
+// nb = gridDim.x; a batched one passes the block range of one case.  Returns true in the
+// last block (after out[] is written and visible to the block).
 template <int NA>
 __device__ __forceinline__ bool block_reduce_store(double (&acc)[NA], int nv, double* partial,
-                                                   double* out, unsigned int* ticket) {
+                                                   double* out, unsigned int* ticket, int b0,
+                                                   int nb) {
   __shared__ double sm[NA][RT / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -72,15 +76,15 @@ __device__ __forceinline__ bool block_reduce_store(double (&acc)[NA], int nv, do
   }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == (unsigned)nb - 1;
   __syncthreads();
   if (!last) return false;
   __threadfence();
   // final pass: warp w sums the partials of k = w, w + 8, ... in a fixed order
-  const int nb = gridDim.x;
+  const size_t ld = gridDim.x;
   for (int k = wid; k < nv; k += RT / 32) {
     double s = 0.0;
-    for (int b = lane; b < nb; b += 32) s += ((volatile double*)partial)[(size_t)k * nb + b];
+    for (int b = lane; b < nb; b += 32) s += ((volatile double*)partial)[(size_t)k * ld + b0 + b];
     s = warp_sum(s);
     if (lane == 0) out[k] = s;
   }
@@ -92,35 +96,18 @@ __device__ __forceinline__ bool block_reduce_store(double (&acc)[NA], int nv, do
 
 __device__ void gm_givens(GmresState* st, const double* h1, const double* h2, const double* nrm2);
 
-// MODE 0: dots  out_k = <V_k, w>
-// MODE 1: w -= sum_k h_k V_k, then out_k = <V_k, w>       (CGS2 second pass)
-// MODE 2: w -= sum_k h_k V_k, then out_0 = <w, w>
-// NV (a multiple of 4, >= nv) sizes the unrolled loops, so that a launch issues FP64
-// work for at most 3 vectors beyond the nv it is given.
-template <int MODE, int NV>
-__global__ void __launch_bounds__(RT) k_krylov(const double* __restrict__ V, size_t ld, int nv,
-                                               const double* __restrict__ h, double* w, size_t n,
-                                               double* __restrict__ partial, double* out,
-                                               unsigned int* ticket, GmresState* gst) {
-  if (gst) nv = gst->j + 1;   // device-resident Arnoldi: nv = newest basis index + 1
-  if (nv > NV) nv = NV;
-  constexpr int NA = MODE == 2 ? 1 : NV;
-  double acc[NA];
-#pragma unroll
-  for (int k = 0; k < NA; ++k) acc[k] = 0.0;
-  double hk[NV];
-  if (MODE != 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) hk[k] = k < nv ? h[k] : 0.0;
-  }
-  // pairs of entries through 16-byte loads, two pairs in flight per thread (n and ld
-  // are even: 4 variables per point)
-  const size_t n2 = n / 2, ld2 = ld / 2;
-  const double2* V2 = reinterpret_cast<const double2*>(V);
-  double2* w2 = reinterpret_cast<double2*>(w);
-  const size_t stride = (size_t)gridDim.x * RT;
-  for (size_t i = blockIdx.x * (size_t)RT + threadIdx.x; i < n2; i += 2 * stride) {
-    const bool two = i + stride < n2;
+// The streaming part of one reduction pass over pairs i = start, start + stride, ...
+// below end, two pairs in flight per thread (16-byte loads; vector lengths and offsets
+// are even: 4 variables per point).
+// MODE 0: acc_k += <V_k, w>
+// MODE 1: w -= sum_k h_k V_k, then acc_k += <V_k, w>       (CGS2 second pass)
+// MODE 2: w -= sum_k h_k V_k, then acc_0 += <w, w>
+template <int MODE, int NV, int NA>
+__device__ __forceinline__ void krylov_pairs(const double2* __restrict__ V2, size_t ld2, double2* w2,
+                                             int nv, const double (&hk)[NV], double (&acc)[NA],
+                                             size_t start, size_t end, size_t stride) {
+  for (size_t i = start; i < end; i += 2 * stride) {
+    const bool two = i + stride < end;
     double2 xa = w2[i], xb = two ? w2[i + stride] : make_double2(0.0, 0.0);
     if (MODE != 0) {
 #pragma unroll
@@ -156,7 +143,29 @@ __global__ void __launch_bounds__(RT) k_krylov(const double* __restrict__ V, siz
       }
     }
   }
-  const bool last = block_reduce_store(acc, MODE == 2 ? 1 : nv, partial, out, ticket);
+}
+
+// One reduction pass over the whole vector (modes as above; out_k the reduced sums).
+// NV (a multiple of 4, >= nv) sizes the unrolled loops, so that a launch issues FP64
+// work for at most 3 vectors beyond the nv it is given.
+template <int MODE, int NV>
+__global__ void __launch_bounds__(RT) k_krylov(const double* __restrict__ V, size_t ld, int nv,
+                                               const double* __restrict__ h, double* w, size_t n,
+                                               double* __restrict__ partial, double* out,
+                                               unsigned int* ticket, GmresState* gst) {
+  if (gst) nv = gst->j + 1;   // device-resident Arnoldi: nv = newest basis index + 1
+  if (nv > NV) nv = NV;
+  constexpr int NA = MODE == 2 ? 1 : NV;
+  double acc[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) acc[k] = 0.0;
+  double hk[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) hk[k] = (MODE != 0 && k < nv) ? h[k] : 0.0;
+  const size_t stride = (size_t)gridDim.x * RT;
+  krylov_pairs<MODE, NV>(reinterpret_cast<const double2*>(V), ld / 2, reinterpret_cast<double2*>(w),
+                         nv, hk, acc, blockIdx.x * (size_t)RT + threadIdx.x, n / 2, stride);
+  const bool last = block_reduce_store(acc, MODE == 2 ? 1 : nv, partial, out, ticket, 0, gridDim.x);
   // the norm pass of a device-resident Arnoldi step closes it with the Givens update
   if (MODE == 2 && gst && last && threadIdx.x == 0) gm_givens(gst, h - FR_MAX_RESTART, h, out);
 }
@@ -173,7 +182,7 @@ __global__ void __launch_bounds__(RT) k_norms(const double* __restrict__ r, size
     if (i < sn) acc[0] = fma(x, x, acc[0]);
     acc[1] = fma(x, x, acc[1]);
   }
-  block_reduce_store(acc, 2, partial, out, ticket);
+  block_reduce_store(acc, 2, partial, out, ticket, 0, gridDim.x);
 }
 
 __global__ void k_scale(const double* __restrict__ x, double a, double* __restrict__ y, size_t n) {
@@ -260,14 +269,139 @@ __global__ void k_gm_store(const double* __restrict__ w, const GmresState* st,
 }
 
 // Back substitution H[0:k,0:k] y = g[0:k], k = j (one thread).
-__global__ void k_gm_trisolve(GmresState* st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void gm_trisolve(GmresState* st) {
   constexpr int L = GmresState::LD;
   const int k = st->j;
   for (int i = k - 1; i >= 0; --i) {
     double acc = st->g[i];
     for (int l = i + 1; l < k; ++l) acc -= st->H[i * L + l] * st->y[l];
     st->y[i] = acc / st->H[i * L + i];
+  }
+}
+__global__ void k_gm_trisolve(GmresState* st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) gm_trisolve(st);
+}
+
+// ------------------------------------------------------------------ batched (per-case) forms
+// The vectors of a batch hold its cases one after another.  Block b of a launch works on
+// the pair range [blo[b], bhi[b]) of case bcase[b]; case k owns blocks cb0[k] ..
+// cb0[k] + cnb[k] - 1.  Reductions are per case: the last of a case's blocks to finish
+// sums that case's partials.  Each case has its own GMRES state; the Arnoldi passes skip
+// a case whose cycle has stopped.  Per-case scalars: dsc[k * BDS + ...] with the first
+// projections at [0, BM), the second at [BM, 2BM), ||w||^2 at 2BM, norms at 3BM.
+constexpr int BM = GmresState::LD;
+constexpr int BDS = 4 * BM;
+
+template <int MODE, int NV>
+__global__ void __launch_bounds__(RT) k_bkrylov(const double* __restrict__ V, size_t ld, double* w,
+                                                BatchSegs sg, double* __restrict__ partial,
+                                                double* dsc, unsigned int* tickets, GmresState* gst) {
+  const int k = sg.bcase[blockIdx.x];
+  GmresState* st = gst + k;
+  if (st->done) return;   // uniform over the case's blocks: set by an earlier launch
+  int nv = st->j + 1;
+  if (nv > NV) nv = NV;
+  double* ds = dsc + (size_t)k * BDS;
+  constexpr int NA = MODE == 2 ? 1 : NV;
+  double acc[NA];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) acc[q] = 0.0;
+  double hk[NV];
+  const double* h = MODE == 1 ? ds : ds + BM;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) hk[q] = (MODE != 0 && q < nv) ? h[q] : 0.0;
+  krylov_pairs<MODE, NV>(reinterpret_cast<const double2*>(V), ld / 2, reinterpret_cast<double2*>(w),
+                         nv, hk, acc, (size_t)sg.blo[blockIdx.x] + threadIdx.x,
+                         (size_t)sg.bhi[blockIdx.x], RT);
+  double* out = MODE == 0 ? ds : MODE == 1 ? ds + BM : ds + 2 * BM;
+  const bool last = block_reduce_store(acc, MODE == 2 ? 1 : nv, partial, out, tickets + k,
+                                       sg.cb0[k], sg.cnb[k]);
+  if (MODE == 2 && last && threadIdx.x == 0) gm_givens(st, ds, ds + BM, ds + 2 * BM);
+}
+
+// Per case: ||r[continuity row]||^2 and ||r||^2 at dsc[k * BDS + 3BM + 0..1]; the
+// continuity row of case k ends at entry mend[k].
+__global__ void __launch_bounds__(RT) k_bnorms(const double* __restrict__ r, BatchSegs sg,
+                                               const long long* __restrict__ mend,
+                                               double* __restrict__ partial, double* dsc,
+                                               unsigned int* tickets) {
+  const int k = sg.bcase[blockIdx.x];
+  const size_t me = (size_t)mend[k];
+  double acc[2] = {0.0, 0.0};
+  const double2* r2 = reinterpret_cast<const double2*>(r);
+  for (size_t i = (size_t)sg.blo[blockIdx.x] + threadIdx.x; i < (size_t)sg.bhi[blockIdx.x]; i += RT) {
+    const double2 x = r2[i];
+    const double xx = x.x * x.x, yy = x.y * x.y;
+    if (2 * i < me) acc[0] += xx;
+    if (2 * i + 1 < me) acc[0] += yy;
+    acc[1] += xx + yy;
+  }
+  block_reduce_store(acc, 2, partial, dsc + (size_t)k * BDS + 3 * BM, tickets + k, sg.cb0[k], sg.cnb[k]);
+}
+
+// V[j] = next = w * inv_hn per case, j the case's newest basis index.  With init set the
+// cycle's first vector is written for every case (inv_hn = 0 gives zeros for a case that
+// does not iterate); otherwise stopped cases are skipped.
+__global__ void k_bgm_store(const double* __restrict__ w, const GmresState* gst, double* __restrict__ V,
+                            size_t ld, double* __restrict__ next, BatchSegs sg, int init) {
+  const GmresState* st = gst + sg.bcase[blockIdx.x];
+  if (!init && st->done) return;
+  const double s = st->inv_hn;
+  const size_t base = (size_t)st->j * (ld / 2);
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  double2* V2 = reinterpret_cast<double2*>(V);
+  double2* n2 = reinterpret_cast<double2*>(next);
+  for (size_t i = (size_t)sg.blo[blockIdx.x] + threadIdx.x; i < (size_t)sg.bhi[blockIdx.x]; i += RT) {
+    const double2 x = w2[i];
+    const double2 y = make_double2(x.x * s, x.y * s);
+    V2[base + i] = y;
+    n2[i] = y;
+  }
+}
+
+// u = sum_{i < j} y_i V_i per case (zero for a case with no iteration in the cycle).
+__global__ void k_blincomb(const double* __restrict__ V, size_t ld, const GmresState* gst,
+                           double* __restrict__ u, BatchSegs sg) {
+  const GmresState* st = gst + sg.bcase[blockIdx.x];
+  const int nk = st->j;
+  const double2* V2 = reinterpret_cast<const double2*>(V);
+  double2* u2 = reinterpret_cast<double2*>(u);
+  const size_t ld2 = ld / 2;
+  for (size_t i = (size_t)sg.blo[blockIdx.x] + threadIdx.x; i < (size_t)sg.bhi[blockIdx.x]; i += RT) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int q = 0; q < nk; ++q) {
+      const double2 v = V2[q * ld2 + i];
+      acc.x = fma(st->y[q], v.x, acc.x);
+      acc.y = fma(st->y[q], v.y, acc.y);
+    }
+    u2[i] = acc;
+  }
+}
+
+// y += coef[k] x over case k's entries.
+__global__ void k_baxpy_case(const double* __restrict__ coef, const double* __restrict__ x,
+                             double* __restrict__ y, BatchSegs sg) {
+  const double a = coef[sg.bcase[blockIdx.x]];
+  if (a == 0.0) return;
+  const double2* x2 = reinterpret_cast<const double2*>(x);
+  double2* y2 = reinterpret_cast<double2*>(y);
+  for (size_t i = (size_t)sg.blo[blockIdx.x] + threadIdx.x; i < (size_t)sg.bhi[blockIdx.x]; i += RT) {
+    const double2 a2 = x2[i];
+    double2 b2 = y2[i];
+    b2.x = fma(a, a2.x, b2.x);
+    b2.y = fma(a, a2.y, b2.y);
+    y2[i] = b2;
+  }
+}
+
+// Block k: back substitution of case k; thread k of block 0 gathers the stop state.
+__global__ void k_bgm_trisolve(GmresState* gst) {
+  if (threadIdx.x == 0) gm_trisolve(gst + blockIdx.x);
+}
+__global__ void k_bgm_status(const GmresState* gst, int ncases, int4* out) {
+  for (int k = threadIdx.x; k < ncases; k += blockDim.x) {
+    const GmresState* st = gst + k;
+    out[k] = make_int4(st->j, st->jmax, st->done, st->nonfinite);
   }
 }
 
@@ -395,6 +529,176 @@ int gm_trisolve(fr_ctx* c, cudaStream_t s) {
 int lincomb(fr_ctx* c, const double* V, int nv, const double* y, double* u, cudaStream_t s) {
   FR_ACCOUNT(c, KK_VECTOR, 2.0 * nv * c->ndof, 8.0 * c->ndof * (nv + 1));
 { FR_PROF_BEGIN(c, s); k_lincomb<<<grid_for(c), RT, 0, s>>>(V, c->ndof, nv, y, u, c->ndof); FR_PROF_END(c, s, KK_VECTOR); }
+  FR_LAUNCH_CHECK(c);
+  return FR_OK;
+}
+
+}  // namespace frk
+
+// ------------------------------------------------------------------ batched launchers
+namespace frk {
+using namespace fr;
+
+template <class T> static int bw_alloc(fr_ctx* c, T** p, size_t n) {
+  FR_CUDA_CHECK(c, cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T)));
+  return FR_OK;
+}
+template <class T> static int bw_alloc_host(fr_ctx* c, T** p, size_t n) {
+  FR_CUDA_CHECK(c, cudaMallocHost((void**)p, std::max<size_t>(n, 1) * sizeof(T)));
+  return FR_OK;
+}
+
+void batch_free(fr_ctx* c) {
+  BatchWork& b = c->bw;
+  void* dev[] = {b.bcase, b.cb0, b.cnb, b.blo, b.bhi, b.mend, b.partial, b.tickets, b.dsc, b.gst,
+                 b.status, b.coef};
+  for (void* p : dev) if (p) cudaFree(p);
+  void* host[] = {b.hsc, b.gst_h, b.status_h, b.coef_h, b.cp_stage};
+  for (void* p : host) if (p) cudaFreeHost(p);
+  if (b.staged) cudaEventDestroy(b.staged);
+  b = BatchWork();
+}
+
+// Blocks of each case in proportion to its length: about 4 pairs per thread, 1 to 1024
+// blocks per case.
+int batch_setup(fr_ctx* c) {
+  batch_free(c);
+  BatchWork& b = c->bw;
+  const int nc = c->ncases;
+  std::vector<int> bcase, cb0(nc), cnb(nc);
+  std::vector<long long> blo, bhi, mend(nc);
+  for (int k = 0; k < nc; ++k) {
+    const long long p0 = c->cps[k].off / 2, np = 2LL * c->cps[k].sn;
+    const int nb = (int)std::min<long long>(1024, std::max<long long>(1, (np + 4 * RT - 1) / (4 * RT)));
+    cb0[k] = (int)bcase.size();
+    cnb[k] = nb;
+    mend[k] = c->cps[k].off + c->cps[k].sn;
+    for (int q = 0; q < nb; ++q) {
+      bcase.push_back(k);
+      blo.push_back(p0 + np * q / nb);
+      bhi.push_back(p0 + np * (q + 1) / nb);
+    }
+  }
+  b.nblk = (int)bcase.size();
+  if (bw_alloc(c, &b.bcase, b.nblk) || bw_alloc(c, &b.blo, b.nblk) || bw_alloc(c, &b.bhi, b.nblk) ||
+      bw_alloc(c, &b.cb0, nc) || bw_alloc(c, &b.cnb, nc) || bw_alloc(c, &b.mend, nc) ||
+      bw_alloc(c, &b.partial, (size_t)32 * b.nblk) || bw_alloc(c, &b.tickets, nc) ||
+      bw_alloc(c, &b.dsc, (size_t)BDS * nc) || bw_alloc(c, &b.gst, nc) ||
+      bw_alloc(c, &b.status, nc) || bw_alloc(c, &b.coef, nc) ||
+      bw_alloc_host(c, &b.hsc, (size_t)BDS * nc) || bw_alloc_host(c, &b.gst_h, nc) ||
+      bw_alloc_host(c, &b.status_h, nc) || bw_alloc_host(c, &b.coef_h, nc) ||
+      bw_alloc_host(c, &b.cp_stage, nc))
+    return FR_ERR_CUDA;
+  FR_CUDA_CHECK(c, cudaEventCreateWithFlags(&b.staged, cudaEventDisableTiming));
+  FR_CUDA_CHECK(c, cudaMemcpy(b.bcase, bcase.data(), b.nblk * sizeof(int), cudaMemcpyHostToDevice));
+  FR_CUDA_CHECK(c, cudaMemcpy(b.blo, blo.data(), b.nblk * sizeof(long long), cudaMemcpyHostToDevice));
+  FR_CUDA_CHECK(c, cudaMemcpy(b.bhi, bhi.data(), b.nblk * sizeof(long long), cudaMemcpyHostToDevice));
+  FR_CUDA_CHECK(c, cudaMemcpy(b.cb0, cb0.data(), nc * sizeof(int), cudaMemcpyHostToDevice));
+  FR_CUDA_CHECK(c, cudaMemcpy(b.cnb, cnb.data(), nc * sizeof(int), cudaMemcpyHostToDevice));
+  FR_CUDA_CHECK(c, cudaMemcpy(b.mend, mend.data(), nc * sizeof(long long), cudaMemcpyHostToDevice));
+  FR_CUDA_CHECK(c, cudaMemset(b.tickets, 0, nc * sizeof(unsigned int)));
+  FR_CUDA_CHECK(c, cudaMemset(b.gst, 0, nc * sizeof(GmresState)));
+  b.sg = BatchSegs{b.bcase, b.blo, b.bhi, b.cb0, b.cnb};
+  return FR_OK;
+}
+
+template <int MODE>
+static void launch_bkrylov(fr_ctx* c, int nv_bound, double* w, cudaStream_t s) {
+  BatchWork& b = c->bw;
+  switch ((nv_bound + 3) / 4) {
+#define FR_BKRYLOV_CASE(q)                                                                       \
+    case q: k_bkrylov<MODE, 4 * q><<<b.nblk, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, \
+                                                         b.tickets, b.gst); break;
+    FR_BKRYLOV_CASE(1) FR_BKRYLOV_CASE(2) FR_BKRYLOV_CASE(3) FR_BKRYLOV_CASE(4)
+    FR_BKRYLOV_CASE(5) FR_BKRYLOV_CASE(6) FR_BKRYLOV_CASE(7)
+    default: k_bkrylov<MODE, 32><<<b.nblk, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc,
+                                                       b.tickets, b.gst); break;
+#undef FR_BKRYLOV_CASE
+  }
+}
+
+int bk_norms(fr_ctx* c, const double* r, cudaStream_t s) {
+  FR_ACCOUNT(c, KK_KRYLOV, 2.0 * c->ndof, 8.0 * c->ndof);
+  FR_PROF_BEGIN(c, s);
+  k_bnorms<<<c->bw.nblk, RT, 0, s>>>(r, c->bw.sg, c->bw.mend, c->bw.partial, c->bw.dsc, c->bw.tickets);
+  FR_PROF_END(c, s, KK_KRYLOV);
+  FR_LAUNCH_CHECK(c);
+  return FR_OK;
+}
+
+int bk_init(fr_ctx* c, const double* r, double* next, cudaStream_t s) {
+  FR_ACCOUNT(c, KK_VECTOR, 1.0 * c->ndof, 24.0 * c->ndof);
+  FR_PROF_BEGIN(c, s);
+  k_bgm_store<<<c->bw.nblk, RT, 0, s>>>(r, c->bw.gst, c->V, c->ndof, next, c->bw.sg, 1);
+  FR_PROF_END(c, s, KK_VECTOR);
+  FR_LAUNCH_CHECK(c);
+  return FR_OK;
+}
+
+int bk_orthogonalize(fr_ctx* c, double* w, double* next, int nv_bound, cudaStream_t s) {
+  FR_ACCOUNT(c, KK_KRYLOV, 8.0 * nv_bound * c->ndof + 2.0 * c->ndof, 8.0 * c->ndof * (3.0 * nv_bound + 5.0));
+  {
+    FR_PROF_BEGIN(c, s);
+    launch_bkrylov<0>(c, nv_bound, w, s);
+    FR_PROF_END(c, s, KK_KRYLOV);
+    FR_LAUNCH_CHECK(c);
+  }
+  {
+    FR_PROF_BEGIN(c, s);
+    launch_bkrylov<1>(c, nv_bound, w, s);
+    FR_PROF_END(c, s, KK_KRYLOV);
+    FR_LAUNCH_CHECK(c);
+  }
+  {
+    FR_PROF_BEGIN(c, s);
+    launch_bkrylov<2>(c, nv_bound, w, s);
+    FR_PROF_END(c, s, KK_KRYLOV);
+    FR_LAUNCH_CHECK(c);
+  }
+  {
+    FR_ACCOUNT(c, KK_VECTOR, 1.0 * c->ndof, 24.0 * c->ndof);
+    FR_PROF_BEGIN(c, s);
+    k_bgm_store<<<c->bw.nblk, RT, 0, s>>>(w, c->bw.gst, c->V, c->ndof, next, c->bw.sg, 0);
+    FR_PROF_END(c, s, KK_VECTOR);
+    FR_LAUNCH_CHECK(c);
+  }
+  return FR_OK;
+}
+
+int bk_finish(fr_ctx* c, double* u, cudaStream_t s) {
+  {
+    FR_PROF_BEGIN(c, s);
+    k_bgm_trisolve<<<c->ncases, 32, 0, s>>>(c->bw.gst);
+    FR_PROF_END(c, s, KK_KRYLOV);
+    FR_LAUNCH_CHECK(c);
+  }
+  {
+    FR_ACCOUNT(c, KK_VECTOR, 2.0 * GmresState::LD * c->ndof, 8.0 * c->ndof * (GmresState::LD + 1));
+    FR_PROF_BEGIN(c, s);
+    k_blincomb<<<c->bw.nblk, RT, 0, s>>>(c->V, c->ndof, c->bw.gst, u, c->bw.sg);
+    FR_PROF_END(c, s, KK_VECTOR);
+    FR_LAUNCH_CHECK(c);
+  }
+  return FR_OK;
+}
+
+int bk_status(fr_ctx* c, cudaStream_t s) {
+  {
+    FR_PROF_BEGIN(c, s);
+    k_bgm_status<<<1, 256, 0, s>>>(c->bw.gst, c->ncases, c->bw.status);
+    FR_PROF_END(c, s, KK_KRYLOV);
+    FR_LAUNCH_CHECK(c);
+  }
+  FR_CUDA_CHECK(c, cudaMemcpyAsync(c->bw.status_h, c->bw.status, c->ncases * sizeof(int4),
+                                   cudaMemcpyDeviceToHost, s));
+  return FR_OK;
+}
+
+int bk_axpy_case(fr_ctx* c, const double* coef, const double* x, double* y, cudaStream_t s) {
+  FR_ACCOUNT(c, KK_VECTOR, 2.0 * c->ndof, 24.0 * c->ndof);
+  FR_PROF_BEGIN(c, s);
+  k_baxpy_case<<<c->bw.nblk, RT, 0, s>>>(coef, x, y, c->bw.sg);
+  FR_PROF_END(c, s, KK_VECTOR);
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }

@@ -94,8 +94,9 @@ k_lin_point(const double* __restrict__ q, Mesh M, Basis B, const double* __restr
   const Gas& gas = cpar.gas;
   const double inv_dtau = cpar.inv_dtau, a0_dt = cpar.a0_dt;
   double qv[4], gc[8];
+  const size_t qo = M.qbase(e, NP) + pt, qs = cpar.sn;
 #pragma unroll
-  for (int v = 0; v < 4; ++v) qv[v] = q[v * SN + o];
+  for (int v = 0; v < 4; ++v) qv[v] = q[v * qs + qo];
   const double ij = gs[GS_INVJ * SN + o];
   if (M.viscous) {
 #pragma unroll
@@ -241,9 +242,10 @@ k_lin_elem_apply(const double* __restrict__ v, Mesh M, Basis B,
   const size_t FNs = (size_t)M.ne * 4 * N;
   const size_t o = (size_t)e * NP + pt;
   double dq[4] = {0, 0, 0, 0}, ij = 0.0;
+  const size_t qo = live ? M.qbase(e, NP) + pt : 0, qs = live ? M.qstride(e) : 0;
   if (live) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) dq[c] = v[c * SN + o];
+    for (int c = 0; c < 4; ++c) dq[c] = v[c * qs + qo];
     ij = gs[GS_INVJ * SN + o];
     double fg[8];
 #pragma unroll
@@ -302,7 +304,7 @@ k_lin_elem_apply(const double* __restrict__ v, Mesh M, Basis B,
     double p = 0.0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) p = fma(PP[(size_t)(r * 4 + c) * SN + o], dq[c], p);
-    out[r * SN + o] = fma(ij, d, p);
+    out[r * qs + qo] = fma(ij, d, p);
   }
 }
 
@@ -333,8 +335,9 @@ k_lin_elem_adjoint(const double* __restrict__ w, Mesh M, Basis B,
   double wv[4] = {0, 0, 0, 0}, ij = 0.0;
   if (live) {
     ij = gs[GS_INVJ * SN + o];
+    const size_t qo = M.qbase(e, NP) + pt, qs = M.qstride(e);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) { wv[r] = w[r * SN + o]; ss[le][r][pt] = wv[r] * ij; }
+    for (int r = 0; r < 4; ++r) { wv[r] = w[r * qs + qo]; ss[le][r][pt] = wv[r] * ij; }
   }
   __syncthreads();
   if (live) {
@@ -507,8 +510,9 @@ k_lin_trace_adjoint(Mesh M, Basis B, const double* __restrict__ gs,
       acc[c] = s;
     }
   }
+  const size_t qo = M.qbase(e, NP) + pt, qs = M.qstride(e);
 #pragma unroll
-  for (int c = 0; c < 4; ++c) out[c * SN + o] = acc[c];
+  for (int c = 0; c < 4; ++c) out[c * qs + qo] = acc[c];
 }
 
 }  // namespace fr

@@ -75,6 +75,9 @@ int run(const fr_config* cfg, int nx, int ny, const double* corners, const doubl
   CaseParams cp;
   cp.gas = fr_make_gas(*cfg);
   cp.a0dt = cp.a1dt = cp.a2dt = cp.inv_dtau = cp.a0_dt = 0.0;
+  cp.off = 0;
+  cp.e0 = 0;
+  cp.sn = (int)(ne * NP);
   Mesh M;
   M.nbr = nbr; M.ecase = ecase; M.cp = cpd; M.ne = (int)ne; M.viscous = cp.gas.viscous;
   k_fill_topo<<<(unsigned)((ne + 127) / 128), 128, 0, s>>>(nx, ny, 0, 0, nbr, ecase);

@@ -51,8 +51,9 @@ k_block(const double* __restrict__ q, Mesh M, Basis B, const double* __restrict_
   const Gas& gas = cpar.gas;
   const double inv_dtau = cpar.inv_dtau, a0_dt = cpar.a0_dt;
   double qv[4];
+  const size_t qo = M.qbase(e, NP) + pt, qs = cpar.sn;
 #pragma unroll
-  for (int v = 0; v < 4; ++v) qv[v] = q[v * SN + o];
+  for (int v = 0; v < 4; ++v) qv[v] = q[v * qs + qo];
   const double sxx = gs[GS_SXX * SN + o], sxy = gs[GS_SXY * SN + o];
   const double sex = gs[GS_SEX * SN + o], sey = gs[GS_SEY * SN + o];
   const double stx = gs[GS_STX * SN + o], ste = gs[GS_STE * SN + o];
@@ -305,15 +306,15 @@ template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x
 // z_e = Dc (A^T_stored (Dr r_e)); one CTA per element, thread per row.
 template <class S, class Acc>
 __global__ void k_apply(const S* __restrict__ AT, const float* __restrict__ Dr,
-                        const float* __restrict__ Dc, const double* __restrict__ r, int ne,
+                        const float* __restrict__ Dc, const double* __restrict__ r, Mesh M,
                         int np2, double* __restrict__ z) {
   extern __shared__ unsigned char smraw[];
   Acc* x = reinterpret_cast<Acc*>(smraw);
   const int e = blockIdx.x, bs = 4 * np2, row = threadIdx.x;
-  const size_t SN = (size_t)ne * np2;
+  const size_t qo = M.qbase(e, np2), qs = M.qstride(e);
   if (row < bs) {
     const int v = row / np2, pt = row % np2;
-    x[row] = (Acc)(r[v * SN + (size_t)e * np2 + pt] * (double)Dr[(size_t)e * bs + row]);
+    x[row] = (Acc)(r[v * qs + qo + pt] * (double)Dr[(size_t)e * bs + row]);
   }
   __syncthreads();
   if (row >= bs) return;
@@ -321,19 +322,19 @@ __global__ void k_apply(const S* __restrict__ AT, const float* __restrict__ Dr,
   Acc acc = 0;
   for (int c2 = 0; c2 < bs; ++c2) acc += (Acc)to_f(A[(size_t)c2 * bs + row]) * x[c2];
   const int v = row / np2, pt = row % np2;
-  z[v * SN + (size_t)e * np2 + pt] = (double)acc * (double)Dc[(size_t)e * bs + row];
+  z[v * qs + qo + pt] = (double)acc * (double)Dc[(size_t)e * bs + row];
 }
 template <>
 __global__ void k_apply<double, double>(const double* __restrict__ AT, const float* __restrict__ Dr,
                                         const float* __restrict__ Dc, const double* __restrict__ r,
-                                        int ne, int np2, double* __restrict__ z) {
+                                        Mesh M, int np2, double* __restrict__ z) {
   extern __shared__ unsigned char smraw[];
   double* x = reinterpret_cast<double*>(smraw);
   const int e = blockIdx.x, bs = 4 * np2, row = threadIdx.x;
-  const size_t SN = (size_t)ne * np2;
+  const size_t qo = M.qbase(e, np2), qs = M.qstride(e);
   if (row < bs) {
     const int v = row / np2, pt = row % np2;
-    x[row] = r[v * SN + (size_t)e * np2 + pt] * (double)Dr[(size_t)e * bs + row];
+    x[row] = r[v * qs + qo + pt] * (double)Dr[(size_t)e * bs + row];
   }
   __syncthreads();
   if (row >= bs) return;
@@ -341,7 +342,7 @@ __global__ void k_apply<double, double>(const double* __restrict__ AT, const flo
   double acc = 0;
   for (int c2 = 0; c2 < bs; ++c2) acc = fma(A[(size_t)c2 * bs + row], x[c2], acc);
   const int v = row / np2, pt = row % np2;
-  z[v * SN + (size_t)e * np2 + pt] = acc * (double)Dc[(size_t)e * bs + row];
+  z[v * qs + qo + pt] = acc * (double)Dc[(size_t)e * bs + row];
 }
 
 }  // namespace fr
@@ -427,11 +428,11 @@ int block_apply(fr_ctx* c, const double* r, double* z, cudaStream_t s) {
              c->ne * ((double)bs * bs * esz + 2.0 * bs * 4.0) + 2.0 * 8.0 * c->ndof);
   FR_PROF_BEGIN(c, s);
   if (c->cfg.prec_dtype == FR_PREC_FP64)
-    k_apply<double, double><<<c->ne, nt, bs * 8, s>>>((const double*)c->Binv, c->Dr, c->Dc, r, c->ne, c->np2, z);
+    k_apply<double, double><<<c->ne, nt, bs * 8, s>>>((const double*)c->Binv, c->Dr, c->Dc, r, c->mesh, c->np2, z);
   else if (c->cfg.prec_dtype == FR_PREC_FP32)
-    k_apply<float, float><<<c->ne, nt, bs * 4, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->ne, c->np2, z);
+    k_apply<float, float><<<c->ne, nt, bs * 4, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, c->np2, z);
   else
-    k_apply<__nv_bfloat16, float><<<c->ne, nt, bs * 4, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->ne, c->np2, z);
+    k_apply<__nv_bfloat16, float><<<c->ne, nt, bs * 4, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, c->np2, z);
   FR_PROF_END(c, s, KK_APPLY);
   FR_LAUNCH_CHECK(c);
   return FR_OK;

@@ -11,6 +11,7 @@
 //          BDF pseudo-step right-hand side, or the Newton operator A v).
 // The JVP runs the same kernels with T = Dual (value + tangent).
 #include <cstdio>
+#include <cstring>
 #include "fr_internal.h"
 #include "fr_kernels.cuh"
 
@@ -20,13 +21,15 @@ __global__ void k_conservative(const double* __restrict__ q, size_t SN, int np2,
                                double* __restrict__ qc) {
   const size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (o >= SN) return;
+  const int e = (int)(o / np2);
+  const size_t qo = M.qbase(e, np2) + o % np2, qs = M.qstride(e);
   double qq[4];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) qq[v] = q[v * SN + o];
+  for (int v = 0; v < 4; ++v) qq[v] = q[v * qs + qo];
   Thermo<double> th;
-  thermo(qq, M.par((int)(o / np2)).gas, th);
+  thermo(qq, M.par(e).gas, th);
 #pragma unroll
-  for (int v = 0; v < 4; ++v) qc[v * SN + o] = th.qc[v];
+  for (int v = 0; v < 4; ++v) qc[v * qs + qo] = th.qc[v];
 }
 
 // ------------------------------------------------------------------ launchers
@@ -113,6 +116,7 @@ int set_case_params(fr_ctx* c, int cid, const CaseParams& p, cudaStream_t s) {
 // The single-case context keeps a host copy of case 0's parameters and rewrites the
 // device copy only when a call changes them (stream-ordered, by a one-thread kernel).
 int set_time_terms(fr_ctx* c, double a0dt, double a1dt, double a2dt, cudaStream_t s) {
+  if (c->external_terms) return FR_OK;
   CaseParams& h = c->cp_h;
   if (h.a0dt == a0dt && h.a1dt == a1dt && h.a2dt == a2dt) return FR_OK;
   h.a0dt = a0dt; h.a1dt = a1dt; h.a2dt = a2dt;
@@ -120,10 +124,25 @@ int set_time_terms(fr_ctx* c, double a0dt, double a1dt, double a2dt, cudaStream_
 }
 
 int set_operator_terms(fr_ctx* c, double inv_dtau, double a0_dt, cudaStream_t s) {
+  if (c->external_terms) return FR_OK;
   CaseParams& h = c->cp_h;
   if (h.inv_dtau == inv_dtau && h.a0_dt == a0_dt) return FR_OK;
   h.inv_dtau = inv_dtau; h.a0_dt = a0_dt;
   return set_case_params(c, 0, h, s);
+}
+
+// The whole case table from the host copies c->cps, staged through pinned memory.  The
+// host waits for the previous staged upload to complete before it rewrites the staging
+// area, so a caller may change c->cps again right after this returns.
+int upload_cases(fr_ctx* c, cudaStream_t s) {
+  BatchWork& b = c->bw;
+  if (!b.cp_stage || !b.staged) { snprintf(c->err, sizeof(c->err), "no batch workspace"); return FR_ERR_ARG; }
+  FR_CUDA_CHECK(c, cudaEventSynchronize(b.staged));
+  std::memcpy(b.cp_stage, c->cps.data(), c->ncases * sizeof(CaseParams));
+  FR_CUDA_CHECK(c, cudaMemcpyAsync(c->cp, b.cp_stage, c->ncases * sizeof(CaseParams),
+                                   cudaMemcpyHostToDevice, s));
+  FR_CUDA_CHECK(c, cudaEventRecord(b.staged, s));
+  return FR_OK;
 }
 
 int fill_topology(fr_ctx* c, int nx, int ny, int e0, int cid, cudaStream_t s) {

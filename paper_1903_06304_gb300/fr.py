@@ -100,6 +100,24 @@ _SIGS = {
     "fr_linearize": (_I, [_P, _P, _D, _D, _P]),
     "fr_apply_linear": (_I, [_P, _P, _P, _I, _P]),
     "fr_vjp": (_I, [_P, _P, _P, _D, _D, _P, _P]),
+    "fr_batch_create": (_I, [ctypes.POINTER(_Config), _P, _I, ctypes.POINTER(_P)]),
+    "fr_batch_destroy": (None, [_P]),
+    "fr_batch_case_info": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                                ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "fr_batch_num_dof": (ctypes.c_size_t, [_P]),
+    "fr_batch_num_elements": (ctypes.c_size_t, [_P]),
+    "fr_batch_num_groups": (_I, [_P]),
+    "fr_batch_update_mesh": (_I, [_P, _P, _P, _P]),
+    "fr_batch_residual": (_I, [_P, _P, _P, _P]),
+    "fr_batch_conservative": (_I, [_P, _P, _P, _P]),
+    "fr_batch_bdf2_step": (_I, [_P, _P, _P, _P, ctypes.POINTER(_D), _P, _P]),
+    "fr_batch_ptc_solve": (_I, [_P, _P, _P, _P]),
+    "fr_batch_profile": (_I, [_P, _I]),
+    "fr_batch_profile_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
+                                   ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D),
+                                   ctypes.POINTER(_D), _I]),
+    "fr_batch_kernel_launches": (ctypes.c_longlong, [_P]),
+    "fr_batch_last_error": (ctypes.c_char_p, [_P]),
 }
 PROF_KINDS = 16
 
@@ -178,6 +196,123 @@ class Config:
             else:
                 setattr(c, f.name, getattr(self, f.name))
         return c
+
+
+class _Case(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("mach", ctypes.c_double), ("re", ctypes.c_double), ("kappa", ctypes.c_double)]
+
+
+@dataclasses.dataclass
+class Case:
+    """One case of a batch: degree, periodic box size and gas (fr_case)."""
+    p: int
+    nx: int
+    ny: int
+    mach: float
+    re: float
+    kappa: float = 1.0
+
+
+class Batch:
+    """Independent cases advanced together (fr_batch_*): state vectors concatenate the
+    cases' single-case layouts at the offsets of ``case_slice``."""
+
+    def __init__(self, cfg: Config, cases):
+        self.lib = load()
+        self.cfg = cfg
+        self.cases = list(cases)
+        self._cc = cfg.to_c()
+        arr = (_Case * len(self.cases))(*[_Case(c.p, c.nx, c.ny, c.mach, c.re, c.kappa)
+                                          for c in self.cases])
+        h = ctypes.c_void_p()
+        rc = self.lib.fr_batch_create(ctypes.byref(self._cc), ctypes.cast(arr, _P), len(self.cases),
+                                      ctypes.byref(h))
+        if rc != FR_OK:
+            raise FrError(rc, "fr_batch_create failed")
+        self.b = h
+        self.ndof = int(self.lib.fr_batch_num_dof(self.b))
+        self.ne = int(self.lib.fr_batch_num_elements(self.b))
+        self.num_groups = int(self.lib.fr_batch_num_groups(self.b))
+        self.dof_off, self.case_ndof, self.elem_off, self.case_ne = [], [], [], []
+        for k in range(len(self.cases)):
+            v = [ctypes.c_size_t() for _ in range(4)]
+            self._check(self.lib.fr_batch_case_info(self.b, k, *[ctypes.byref(x) for x in v]))
+            self.dof_off.append(v[0].value)
+            self.case_ndof.append(v[1].value)
+            self.elem_off.append(v[2].value)
+            self.case_ne.append(v[3].value)
+
+    def _check(self, rc):
+        if rc != FR_OK:
+            msg = self.lib.fr_batch_last_error(self.b)
+            raise FrError(rc, (msg or b"").decode())
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.fr_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def case_slice(self, k) -> slice:
+        return slice(self.dof_off[k], self.dof_off[k] + self.case_ndof[k])
+
+    def elem_slice(self, k) -> slice:
+        return slice(self.elem_off[k], self.elem_off[k] + self.case_ne[k])
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.lib.fr_batch_kernel_launches(self.b))
+
+    def update_mesh(self, corners, vel, stream=None):
+        self._check(self.lib.fr_batch_update_mesh(self.b, _ptr(corners), _ptr(vel), _stream(stream)))
+
+    def residual(self, q, out, stream=None):
+        self._check(self.lib.fr_batch_residual(self.b, _ptr(q), _ptr(out), _stream(stream)))
+        return out
+
+    def conservative(self, q, out, stream=None):
+        self._check(self.lib.fr_batch_conservative(self.b, _ptr(q), _ptr(out), _stream(stream)))
+        return out
+
+    def bdf2_step(self, q, qc_n, qc_nm1, coef, stream=None, allow_unconverged=False):
+        """coef: per case (a0, a1, a2, dt).  Returns the per-case Stats list."""
+        nc = len(self.cases)
+        flat = (ctypes.c_double * (4 * nc))(*[float(x) for row in coef for x in row])
+        st = (Stats * nc)()
+        pnm1 = _ptr(qc_nm1) if qc_nm1 is not None else None
+        rc = self.lib.fr_batch_bdf2_step(self.b, _ptr(q), _ptr(qc_n), pnm1, flat,
+                                         ctypes.cast(st, _P), _stream(stream))
+        if not (allow_unconverged and rc == -4):
+            self._check(rc)
+        return list(st)
+
+    def ptc_solve(self, q, stream=None, allow_unconverged=False):
+        nc = len(self.cases)
+        st = (Stats * nc)()
+        rc = self.lib.fr_batch_ptc_solve(self.b, _ptr(q), ctypes.cast(st, _P), _stream(stream))
+        if not (allow_unconverged and rc == -4):
+            self._check(rc)
+        return list(st)
+
+    def profile(self, enable: bool):
+        self._check(self.lib.fr_batch_profile(self.b, 1 if enable else 0))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        ms = (ctypes.c_double * PROF_KINDS)()
+        cnt = (ctypes.c_longlong * PROF_KINDS)()
+        tot = (ctypes.c_longlong * PROF_KINDS)()
+        fl = (ctypes.c_double * PROF_KINDS)()
+        by = (ctypes.c_double * PROF_KINDS)()
+        self._check(self.lib.fr_batch_profile_read(self.b, ms, cnt, tot, fl, by, 1 if reset else 0))
+        return {self.lib.fr_profile_name(k).decode():
+                dict(ms=ms[k], launches=cnt[k], all_launches=tot[k], flops=fl[k], bytes=by[k])
+                for k in range(PROF_KINDS)}
 
 
 class Solver:

@@ -95,10 +95,16 @@ def uniform_state(ne: int, p: int, mach: float, u: float = 1.0, v: float = 0.0) 
 
 
 def gaussian_bump(x: np.ndarray, y: np.ndarray, mach: float, amp: float = 1e-3,
-                  width: float = 0.1, xc: float = 0.5, yc: float = 0.5) -> np.ndarray:
+                  width: float = 0.1, xc: float = 0.5, yc: float = 0.5,
+                  period: float = 0.0) -> np.ndarray:
     """Uniform flow u=1, v=0, T=1 plus a Gaussian pressure bump
-    p = p_inf (1 + amp exp(-|x - x_c|^2 / width^2))."""
-    r2 = (x - xc) ** 2 + (y - yc) ** 2
+    p = p_inf (1 + amp exp(-|x - x_c|^2 / width^2)); period > 0 measures the distance
+    to the nearest periodic image of the centre."""
+    dx, dy = x - xc, y - yc
+    if period > 0:
+        dx = dx - period * np.round(dx / period)
+        dy = dy - period * np.round(dy / period)
+    r2 = dx ** 2 + dy ** 2
     q = np.empty((4,) + x.shape)
     q[0] = p_inf(mach) * (1.0 + amp * np.exp(-r2 / width ** 2))
     q[1], q[2], q[3] = 1.0, 0.0, 1.0
@@ -227,4 +233,54 @@ def make_case(w: Workload, t: float = 0.0):
         q = vortex_state(x, y, t, vx)
     else:
         q = uniform_state(w.ne, w.p, w.mach)
+    return corners, vel, q
+
+
+# ------------------------------------------------------------------ batches of cases
+@dataclasses.dataclass(frozen=True)
+class BatchCase:
+    """One case of a batch workload: a periodic n x n box [0, box]^2 at degree p."""
+    p: int
+    n: int
+    mach: float
+    ic: str              # "vortex" | "bump"
+    xc: float
+    yc: float
+    alpha: float         # vortex strength, or bump amplitude in units of 1e-3 p_inf
+    re: float = 10.0     # Re = 100 on the box length 10
+    kappa: float = 1.0
+    box: float = 10.0
+
+
+def batch_cases(seed: int = 0, ncases: int = 64, side=(32, 128), degrees=(2, 3, 4),
+                mach=(0.01, 0.3)) -> list:
+    """Seeded batch recipe: mesh side uniform in [side[0], side[1]], degree uniform over
+    ``degrees``, Mach uniform in ``mach``, vortex or bump with probability 1/2, centre
+    uniform in the box, strength alpha uniform in [1, 5]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(ncases):
+        n = int(rng.integers(side[0], side[1] + 1))
+        p = int(rng.choice(degrees))
+        m = float(rng.uniform(mach[0], mach[1]))
+        ic = "vortex" if rng.uniform() < 0.5 else "bump"
+        xc, yc = (float(v) for v in rng.uniform(0.0, 10.0, size=2))
+        alpha = float(rng.uniform(1.0, 5.0))
+        out.append(BatchCase(p, n, m, ic, xc, yc, alpha))
+    return out
+
+
+def make_batch_case(bc: BatchCase):
+    """Corners, corner velocities (static mesh) and initial state of one batch case.  The
+    bump has width box/10 (C1's width relative to its box) and amplitude alpha 1e-3 p_inf."""
+    corners = box_mesh(bc.n, bc.n, 0.0, bc.box, 0.0, bc.box)
+    vel = np.zeros_like(corners)
+    x, y = sample_points(corners, bc.p)
+    if bc.ic == "vortex":
+        vx = Vortex(mach=bc.mach, alpha=bc.alpha, x0=bc.xc, y0=bc.yc,
+                    period_x=bc.box, period_y=bc.box)
+        q = vortex_state(x, y, 0.0, vx)
+    else:
+        q = gaussian_bump(x, y, bc.mach, amp=1e-3 * bc.alpha, width=0.1 * bc.box, xc=bc.xc,
+                          yc=bc.yc, period=bc.box)
     return corners, vel, q

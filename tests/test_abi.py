@@ -67,3 +67,24 @@ def test_oracle_and_library_share_no_code():
         if f.endswith((".py", ".cu", ".cuh", ".h")):
             src = open(f).read()
             assert "import oracle" not in src and "from oracle" not in src
+
+
+def test_bad_batch_rejected_without_gpu():
+    """fr_batch_create validates the cases and the restart length before any GPU work."""
+    from paper_1903_06304_gb300 import fr
+    lib = fr.load()
+    c = fr._Config()
+    lib.fr_default_config(ctypes.byref(c))
+    h = ctypes.c_void_p()
+    good = fr._Case(2, 4, 4, 0.1, 0.0, 1.0)
+    bad = [fr._Case(0, 4, 4, 0.1, 0.0, 1.0), fr._Case(2, 1, 4, 0.1, 0.0, 1.0),
+           fr._Case(2, 4, 4, 0.0, 0.0, 1.0), fr._Case(5, 4, 4, 0.1, 10.0, 1.0)]
+    for b in bad:
+        arr = (fr._Case * 2)(good, b)
+        assert lib.fr_batch_create(ctypes.byref(c), ctypes.cast(arr, ctypes.c_void_p), 2,
+                                   ctypes.byref(h)) == -1
+        assert not h.value
+    c.restart = 40   # the batched Arnoldi keeps at most 32 vectors on the device
+    arr = (fr._Case * 1)(good)
+    assert lib.fr_batch_create(ctypes.byref(c), ctypes.cast(arr, ctypes.c_void_p), 1,
+                               ctypes.byref(h)) == -1
