@@ -193,7 +193,7 @@ def gpu_arm(args):
         cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=prec,
                         restart=args.restart, maxit_lin=args.maxit_lin, tol_res=w.tol_res,
                         tol_pseudo=w.tol_pseudo, maxit_newton=args.maxit_newton, lag=2,
-                        line_search=args.line_search)
+                        line_search=args.line_search, graphs=args.graphs)
         S = fr.Solver(cfg, w.nx, w.ny)
         S.update_mesh(T(corners), T(vel))
         return S
@@ -312,7 +312,7 @@ def gpu_arm(args):
     # ---- GMRES iteration cost at the final state: a fixed count (tol_res 1e-30), so the
     # per-iteration time does not depend on the Newton history
     gm_cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
-                       restart=args.restart, maxit_lin=120, tol_res=1e-30)
+                       restart=args.restart, maxit_lin=120, tol_res=1e-30, graphs=args.graphs)
     Sg = fr.Solver(gm_cfg, w.nx, w.ny)
     Sg.update_mesh(T(corners), T(vel))
     Sg.precond_build(run.q, 1e-20, 1.5 / w.dt)
@@ -465,6 +465,83 @@ def kernels_only(args):
     S.close()
 
 
+# ------------------------------------------------------------------ batched cases
+def batch_arm(args):
+    """Independent cases advanced together (fr_batch_*): the seeded batch recipe (mesh
+    side 32..128, p in {2,3,4}, M in [0.01, 0.3], vortex or bump, Re = 100 on the box),
+    one BDF2 step of every case per bench step; value = DOF of all cases x steps / time."""
+    import numpy as np
+    import torch
+    from paper_1903_06304_gb300 import fr
+    from paper_1903_06304_gb300 import inputs as inp
+    dev = "cuda:0"
+    cs = inp.batch_cases(seed=0, ncases=args.batch_cases)
+    cases = [fr.Case(c.p, c.n, c.n, c.mach, c.re, c.kappa) for c in cs]
+    cfg = fr.Config(prec=args.prec, restart=args.restart, maxit_lin=args.maxit_lin,
+                    maxit_newton=args.maxit_newton, lag=2, line_search=args.line_search,
+                    graphs=args.graphs)
+    B = fr.Batch(cfg, cases)
+    corners = np.zeros((B.ne, 4, 2))
+    q = np.zeros(B.ndof)
+    for k, bc in enumerate(cs):
+        c, _v, qk = inp.make_batch_case(bc)
+        corners[B.elem_slice(k)] = c
+        q[B.case_slice(k)] = qk.ravel()
+    T = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    B.update_mesh(T(corners), T(np.zeros_like(corners)))
+    qd = T(q)
+    qc_n, qc_nm1 = torch.empty_like(qd), torch.empty_like(qd)
+    B.conservative(qd, qc_n)
+    qc_nm1.copy_(qc_n)
+    dt = 0.01
+    state = {"k": 0}
+
+    def step():
+        a = (1.0, -1.0, 0.0) if state["k"] == 0 else (1.5, -2.0, 0.5)
+        st = B.bdf2_step(qd, qc_n, qc_nm1, [a + (dt,)] * len(cs), allow_unconverged=True)
+        qc_nm1.copy_(qc_n)
+        B.conservative(qd, qc_n)
+        state["k"] += 1
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    launches0 = B.kernel_launches
+    clocks = ClockSampler(0)
+    ms, stats = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        stats.append(step())
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    clock_info = clocks.stop()
+    launches = B.kernel_launches - launches0
+    t = sum(ms) / 1e3
+    newton = [s.newton_iterations for st in stats for s in st]
+    gmres = [sum(s.gmres_iterations[:s.newton_iterations]) for st in stats for s in st]
+    conv = [s.converged for st in stats for s in st]
+    out = {"metric": "batched BDF2 steps of independent cases (GDOF/s)", "impl": "ours",
+           "value": B.ndof * args.steps / t / 1e9, "unit": "GDOF/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "dtype": "f64 (blocks %s)" % args.prec,
+           "data": "synthetic",
+           "config": {"workload": f"batch of {len(cs)} cases (seed 0)", "cases": len(cs),
+                      "groups": B.num_groups, "dof": B.ndof, "elements": B.ne,
+                      "prec": args.prec, "restart": args.restart, "maxit_lin": args.maxit_lin,
+                      "maxit_newton": args.maxit_newton, "line_search": args.line_search,
+                      "graphs": args.graphs, "l2": "256 MiB flush between steps"},
+           "cases_converged_per_step": sum(conv) / args.steps,
+           "newton_iterations": {"mean": statistics.mean(newton), "max": max(newton)},
+           "gmres_iterations": {"mean": statistics.mean(gmres), "max": max(gmres)},
+           "gpu_launches": launches, "clocks": clock_info}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -480,9 +557,13 @@ def main():
     ap.add_argument("--maxit-newton", dest="maxit_newton", type=int, default=40)
     ap.add_argument("--line-search", dest="line_search", type=int, default=4,
                     help="backtracking halvings per Newton update (0: plain Newton)")
+    ap.add_argument("--graphs", type=int, default=1,
+                    help="replay GMRES chunks from captured CUDA graphs (1) or launch each kernel (0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--batch-cases", dest="batch_cases", type=int, default=0,
+                    help="run the batched-cases workload with this many cases instead")
     ap.add_argument("--kernels-only", action="store_true",
                     help="short fixed call sequence for profiler captures")
     args = ap.parse_args()
@@ -493,6 +574,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         reference_arm(args)
+    elif args.batch_cases > 0:
+        batch_arm(args)
     else:
         gpu_arm(args)
 

@@ -73,7 +73,10 @@ typedef struct fr_ctx fr_ctx;
  * the full 2-norm of the pseudo-step residual is kept (the last one otherwise);
  * gmres_side: FR_GMRES_LEFT (PETSc's default, the paper's solver: Krylov space of B^-1 A,
  * tol_res relative to ||B^-1 b||) or FR_GMRES_RIGHT (Krylov space of A B^-1, tol_res
- * relative to ||b||). */
+ * relative to ||b||);
+ * graphs: if nonzero (default) and restart <= 32, GMRES iterations are issued in chunks of
+ * up to 10 whose kernel launches are captured once into a CUDA graph and replayed (same
+ * results; fewer launch overheads); ignored while fr_profile timing is on. */
 #define FR_MAX_RESTART 256
 #define FR_JVP_DUAL 0
 #define FR_JVP_LINEARIZED 1
@@ -91,6 +94,7 @@ typedef struct fr_config {
   double dtau0_unsteady;
   int line_search;
   int jvp_mode;
+  int graphs;
 } fr_config;
 
 /* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).
@@ -244,6 +248,25 @@ const char* fr_profile_name(int kind);
 int fr_residual_noalloc(const fr_config* cfg, int nx, int ny, const double* corners_d,
                         const double* corner_vel_d, const double* qp_d, double* R_d,
                         void* stream);
+
+/* Parameter sensitivities of the residual contracted with a weight vector (the paper does
+ * not differentiate its solver; this is the parameter part of a discrete adjoint, e.g.
+ * for sensitivities of forces to the Mach number or to a prescribed mesh motion).  At
+ * state qp_d, for the mesh given again by corners_d / corner_vel_d (device [Ne][4][2], as
+ * passed to fr_update_mesh) and weights w_d (device, state layout):
+ *   *dmach (host)        = w . dR/dM_inf  (the gas constants R = 1/(gamma M^2),
+ *                           C_p = 1/((gamma-1) M^2), k = mu C_p/Pr and the cut-off kappa M_inf
+ *                           all move with M_inf, Sec. 2.1 and Eq. eps_move);
+ *   dcorners_d[e][a][c]  = w . dR/d(coordinate c of corner a of element e);
+ *   dvel_d[e][a][c]      = w . dR/d(velocity component c of corner a of element e).
+ * A node shared by several elements appears once per element: its sensitivity is the sum
+ * over its copies.  Any of dmach, dcorners_d, dvel_d may be NULL (skipped).  Exact
+ * forward mode over colour classes of elements (9 to 25 classes, 8 directions each for
+ * corners and again for velocities).  Single-case contexts.  Synchronises when dmach is
+ * requested; otherwise asynchronous on stream. */
+int fr_param_vjp(fr_ctx* ctx, const double* qp_d, const double* w_d, const double* corners_d,
+                 const double* corner_vel_d, double* dmach, double* dcorners_d, double* dvel_d,
+                 void* stream);
 
 /* ---------------------------------------------------------------- batches
  * Many independent problems solved together (the paper solves one at a time; Sec. 3.2's

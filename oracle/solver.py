@@ -353,3 +353,34 @@ def entropy_error(prob: Problem, q):
     s_inf = g.R  # p_inf / rho_inf^gamma with rho_inf = T_inf = 1
     s = q[0] / rho ** g.gamma
     return float(np.sqrt(np.sum(w * (s - s_inf) ** 2) / np.sum(w * s_inf ** 2)))
+
+
+# ------------------------------------------------------------------ parameter sensitivities
+
+def param_vjp(prob: Problem, q, w):
+    """Sensitivities of w . R to the parameters, by the complex step (brute force: one
+    complex residual per parameter):
+
+        dmach          = w . dR/dM_inf     (R, C_p, k and kappa M_inf move with M_inf, Sec. 2.1)
+        dcorners[e,a,c] = w . dR/d(corner a of element e, coordinate c)
+        dvel[e,a,c]     = w . dR/d(velocity of corner a of element e, component c)
+    """
+    h = COMPLEX_STEP
+    gas_c = dataclasses.replace(prob.gas, mach=prob.gas.mach + 1j * h)
+    dmach = float(np.sum(w * np.imag(Problem(prob.mesh, prob.p, gas_c).R(q))) / h)
+    m = prob.mesh
+    out = []
+    for which in ("corners", "vel"):
+        base = getattr(m, which)
+        d = np.zeros(base.shape)
+        for e in range(base.shape[0]):
+            for a in range(4):
+                for c in range(2):
+                    pert = base.astype(complex)
+                    pert[e, a, c] += 1j * h
+                    corners = pert if which == "corners" else m.corners
+                    vel = pert if which == "vel" else m.vel
+                    Rc = Problem(Mesh(m.nx, m.ny, corners, vel), prob.p, prob.gas).R(q)
+                    d[e, a, c] = np.sum(w * np.imag(Rc)) / h
+        out.append(d)
+    return dmach, out[0], out[1]

@@ -111,6 +111,62 @@ fr::Gas fr_make_gas(const fr_config& c) {
   return g;
 }
 
+void graphs_free(fr_ctx* c) {
+  for (GraphEntry& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
+int gm_chunk(fr_ctx* c, int start, int count, int tag, const void* q,
+             const std::function<int(cudaStream_t)>& issue, cudaStream_t s) {
+  if (!c->cfg.graphs || c->prof.on) return issue(s);
+  for (GraphEntry& g : c->graphs) {
+    if (g.start == start && g.count == count && g.tag == tag && g.q == q) {
+      FR_CUDA_CHECK(c, cudaGraphLaunch(g.exec, s));
+      c->launches += g.launches;
+      for (int k = 0; k < KK_COUNT; ++k) {
+        c->launches_by_kind[k] += g.by_kind[k];
+        c->alg_flops[k] += g.flops[k];
+        c->alg_bytes[k] += g.bytes[k];
+      }
+      return FR_OK;
+    }
+  }
+  // capture on a private stream (capture executes nothing), replay on s; the counters
+  // advanced during capture stand for this first replay
+  if (!c->cap_stream) FR_CUDA_CHECK(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  GraphEntry e;
+  std::memset(&e, 0, sizeof(e));
+  e.start = start; e.count = count; e.tag = tag; e.q = q;
+  const long long l0 = c->launches;
+  long long k0[KK_COUNT];
+  double f0[KK_COUNT], b0[KK_COUNT];
+  for (int k = 0; k < KK_COUNT; ++k) { k0[k] = c->launches_by_kind[k]; f0[k] = c->alg_flops[k]; b0[k] = c->alg_bytes[k]; }
+  FR_CUDA_CHECK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = issue(c->cap_stream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
+  if (rc != FR_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+  if (ce != cudaSuccess || !graph) {
+    snprintf(c->err, sizeof(c->err), "graph capture: %s", cudaGetErrorString(ce));
+    return FR_ERR_CUDA;
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    snprintf(c->err, sizeof(c->err), "graph instantiate: %s", cudaGetErrorString(ie));
+    return FR_ERR_CUDA;
+  }
+  e.launches = c->launches - l0;
+  for (int k = 0; k < KK_COUNT; ++k) {
+    e.by_kind[k] = c->launches_by_kind[k] - k0[k];
+    e.flops[k] = c->alg_flops[k] - f0[k];
+    e.bytes[k] = c->alg_bytes[k] - b0[k];
+  }
+  c->graphs.push_back(e);
+  FR_CUDA_CHECK(c, cudaGraphLaunch(e.exec, s));
+  return FR_OK;
+}
+
 namespace {
 
 template <class T> int dev_alloc(fr_ctx* c, T** p, size_t count) {
@@ -124,7 +180,8 @@ void free_mesh(fr_ctx* c) {
   double** ds[] = {&c->gs, &c->gf, &c->tq, &c->tg, &c->gl, &c->fn, &c->qcm, &c->tq_d, &c->tg_d,
                    &c->gl_d, &c->fn_d, &c->qcm_d, &c->B64, &c->V, &c->w_r, &c->w_z, &c->w_x,
                    &c->w_t, &c->w_u, &c->red, &c->JFQ, &c->JFG, &c->JP, &c->JG, &c->PP,
-                   &c->adj_q, &c->adj_fn, &c->adj_qc};
+                   &c->adj_q, &c->adj_fn, &c->adj_qc, &c->sgs, &c->sdgs, &c->sgf, &c->sdgf,
+                   &c->seed, &c->edot, &c->zero, &c->rtan};
   for (double** p : ds) if (*p) { cudaFree(*p); *p = nullptr; }
   if (c->Binv) { cudaFree(c->Binv); c->Binv = nullptr; }
   if (c->Dr) { cudaFree(c->Dr); c->Dr = nullptr; }
@@ -136,6 +193,7 @@ void free_mesh(fr_ctx* c) {
   c->blocks_ready = 0;
   c->lin_ready = 0;
   frk::batch_free(c);
+  graphs_free(c);
 }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -211,6 +269,18 @@ int gmres_solve(fr_ctx* c, const double* q, const double* b, double inv_dtau, do
   const int maxit = c->cfg.maxit_lin;
   const bool left = c->cfg.gmres_side == FR_GMRES_LEFT;
   double* r = c->w_r;
+  // the operator's terms go to the case table here, outside any captured chunk
+  FR_TRY(frk::set_operator_terms(c, inv_dtau, a0_dt, s));
+  if (m <= GmresState::LD) {
+    // Device-resident Arnoldi (the per-case path with one case): iterations are queued in
+    // chunks, one synchronisation per chunk reads the iteration count and stopping flag.
+    std::vector<char> active(1, 1), failed(1, 0);
+    std::vector<int> its;
+    FR_TRY(frk::gmres_cases(c, q, b, x, inv_dtau, a0_dt, active, its, failed, s));
+    if (failed[0]) { snprintf(c->err, sizeof(c->err), "GMRES: non-finite Krylov vector"); return FR_ERR_NONFINITE; }
+    *iters = its[0];
+    return FR_OK;
+  }
   if (left) FR_TRY(frk::block_apply(c, b, r, s));
   else FR_CUDA_CHECK(c, cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   double bm, bnorm;
@@ -220,63 +290,6 @@ int gmres_solve(fr_ctx* c, const double* q, const double* b, double inv_dtau, do
   if (bnorm == 0.0) return FR_OK;
   double beta = bnorm;
   int total = 0;
-  if (m <= GmresState::LD) {
-    // Device-resident Arnoldi: iterations are queued in chunks; one synchronisation per
-    // chunk reads the cycle's iteration count and stopping flag.  Iterations queued
-    // after the stopping test fired leave the cycle's state untouched.
-    constexpr int kChunk = 10;
-    double* tmp = c->w_u;
-    double* w = c->w_t;
-    while (true) {
-      if (beta <= tol * bnorm) break;
-      if (total >= maxit) break;
-      FR_TRY(frk::scale(c, r, 1.0 / beta, c->V, s));
-      GmresState* h = c->gst_h;
-      std::memset(h, 0, sizeof(GmresState));
-      h->g[0] = beta;
-      h->tol = tol * bnorm;
-      h->jmax = std::min(m, maxit - total);
-      FR_CUDA_CHECK(c, cudaMemcpyAsync(c->gst, h, sizeof(GmresState), cudaMemcpyHostToDevice, s));
-      int jh = 0;
-      FR_TRY(frk::gm_copy_in(c, tmp, s));
-      while (true) {
-        const int nchunk = std::min(kChunk, h->jmax - jh);
-        for (int it = 0; it < nchunk; ++it) {
-          if (left) {
-            FR_TRY(op_apply(c, q, tmp, inv_dtau, a0_dt, c->w_z, s));
-            FR_TRY(frk::block_apply(c, c->w_z, w, s));
-          } else {
-            FR_TRY(frk::block_apply(c, tmp, c->w_z, s));
-            FR_TRY(op_apply(c, q, c->w_z, inv_dtau, a0_dt, w, s));
-          }
-          FR_TRY(frk::gm_orthogonalize(c, w, tmp, jh + it + 1, s));
-        }
-        FR_CUDA_CHECK(c, cudaMemcpyAsync(&h->j, &c->gst->j, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        FR_CUDA_CHECK(c, cudaStreamSynchronize(s));
-        if (h->nonfinite) { snprintf(c->err, sizeof(c->err), "GMRES: non-finite Krylov vector"); return FR_ERR_NONFINITE; }
-        jh = h->j;
-        if (h->done || jh >= h->jmax) break;
-      }
-      const int k = jh;
-      total += k;
-      FR_TRY(frk::gm_trisolve(c, s));
-      FR_TRY(frk::lincomb(c, c->V, k, c->gst->y, c->w_u, s));
-      if (left) {
-        FR_TRY(frk::axpby(c, 1.0, c->w_u, 1.0, x, s));
-      } else {
-        FR_TRY(frk::block_apply(c, c->w_u, c->w_z, s));
-        FR_TRY(frk::axpby(c, 1.0, c->w_z, 1.0, x, s));
-      }
-      FR_TRY(op_apply(c, q, x, inv_dtau, a0_dt, c->w_t, s));
-      FR_TRY(frk::axpby(c, 1.0, b, -1.0, c->w_t, s));
-      if (left) FR_TRY(frk::block_apply(c, c->w_t, r, s));
-      else FR_CUDA_CHECK(c, cudaMemcpyAsync(r, c->w_t, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      double rm;
-      FR_TRY(norms_host(c, r, &rm, &beta, s));
-    }
-    *iters = total;
-    return FR_OK;
-  }
   std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   while (true) {
     if (beta <= tol * bnorm) break;
@@ -510,6 +523,7 @@ void fr_default_config(fr_config* c) {
   c->dtau0_unsteady = 0.01;
   c->line_search = 0;
   c->jvp_mode = FR_JVP_LINEARIZED;
+  c->graphs = 1;
 }
 
 int fr_create(const fr_config* cfg, fr_ctx** out) {
@@ -538,9 +552,7 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
   c->cp_h.sn = 0;
   if (cudaMalloc((void**)&c->dsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&c->hsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&c->gst, sizeof(GmresState)) != cudaSuccess ||
-      cudaMalloc((void**)&c->cp, sizeof(fr::CaseParams)) != cudaSuccess ||
-      cudaMallocHost((void**)&c->gst_h, sizeof(GmresState)) != cudaSuccess) {
+      cudaMalloc((void**)&c->cp, sizeof(fr::CaseParams)) != cudaSuccess) {
     delete c;
     return FR_ERR_CUDA;
   }
@@ -553,11 +565,10 @@ void fr_destroy(fr_ctx* c) {
   prof_collect(c);
   for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
   free_mesh(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->dsc) cudaFree(c->dsc);
   if (c->hsc) cudaFreeHost(c->hsc);
-  if (c->gst) cudaFree(c->gst);
   if (c->cp) cudaFree(c->cp);
-  if (c->gst_h) cudaFreeHost(c->gst_h);
   delete c;
 }
 
@@ -599,6 +610,8 @@ int fr_setup_cases(fr_ctx* c, int ncases, const int* nxs, const int* nys,
     p.e0 = (int)e0;
     p.off = 4 * e0 * c->np2;
     p.sn = nxs[k] * nys[k] * c->np2;
+    p.nx = nxs[k];
+    p.ny = nys[k];
     FR_TRY(frk::fill_topology(c, nxs[k], nys[k], (int)e0, k, 0));
     e0 += (long long)nxs[k] * nys[k];
   }
@@ -648,7 +661,8 @@ int fr_setup_cases(fr_ctx* c, int ncases, const int* nxs, const int* nys,
   FR_TRY(dev_alloc(c, &c->adj_qc, ne * 16 * n));
   FR_TRY(dev_alloc(c, &c->ticket, 1));
   FR_CUDA_CHECK(c, cudaMemset(c->ticket, 0, sizeof(unsigned int)));
-  return FR_OK;
+  // per-case vector partition, GMRES states and staging (used by every context)
+  return frk::batch_setup(c);
 }
 
 extern "C" {

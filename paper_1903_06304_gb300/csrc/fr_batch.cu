@@ -42,7 +42,7 @@ struct fr_batch {
   char err[512];
 };
 
-namespace {
+namespace frk {
 
 // Per-case continuity-row and full 2-norms of r (synchronises).  A case with a
 // non-finite norm is reported in bad[] (norms set to +inf).
@@ -69,7 +69,7 @@ int case_norms(fr_ctx* c, const double* r, std::vector<double>& mass, std::vecto
 }
 
 // Per-case coefficients to the device (pinned staging, guarded like the case table).
-int upload_coef(fr_ctx* c, const std::vector<double>& a, cudaStream_t s) {
+static int upload_coef(fr_ctx* c, const std::vector<double>& a, cudaStream_t s) {
   BatchWork& b = c->bw;
   FR_CUDA_CHECK(c, cudaEventSynchronize(b.staged));
   std::memcpy(b.coef_h, a.data(), c->ncases * sizeof(double));
@@ -79,7 +79,7 @@ int upload_coef(fr_ctx* c, const std::vector<double>& a, cudaStream_t s) {
   return FR_OK;
 }
 
-int upload_gmres(fr_ctx* c, cudaStream_t s) {
+static int upload_gmres(fr_ctx* c, cudaStream_t s) {
   BatchWork& b = c->bw;
   FR_CUDA_CHECK(c, cudaMemcpyAsync(b.gst, b.gst_h, c->ncases * sizeof(GmresState),
                                    cudaMemcpyHostToDevice, s));
@@ -87,15 +87,16 @@ int upload_gmres(fr_ctx* c, cudaStream_t s) {
   return FR_OK;
 }
 
-int op_apply(fr_ctx* c, const double* q, const double* x, double* out, cudaStream_t s) {
+static int op_apply(fr_ctx* c, const double* q, const double* x, double inv_dtau, double a0_dt,
+                    double* out, cudaStream_t s) {
   if (c->cfg.jvp_mode == FR_JVP_LINEARIZED) return frk::apply_linear(c, x, out, false, s);
-  return frk::jvp(c, q, x, 0.0, 0.0, out, s);   // terms come from the case table
+  return frk::jvp(c, q, x, inv_dtau, a0_dt, out, s);
 }
 
 // Batched restarted GMRES(m <= 32): every active case solves its own A_k x_k = b_k with
 // its own Krylov space, tolerance and iteration limit; x is zero for inactive cases.
-int batch_gmres(fr_ctx* c, const double* q, const double* b, double* x,
-                const std::vector<char>& active, std::vector<int>& iters,
+int gmres_cases(fr_ctx* c, const double* q, const double* b, double* x, double inv_dtau,
+                double a0_dt, const std::vector<char>& active, std::vector<int>& iters,
                 std::vector<char>& failed, cudaStream_t s) {
   const int nc = c->ncases;
   const size_t N = c->ndof;
@@ -143,16 +144,23 @@ int batch_gmres(fr_ctx* c, const double* q, const double* b, double* x,
     int issued = 0;
     while (true) {
       const int nchunk = std::min(kChunk, jmax_all - issued);
-      for (int it = 0; it < nchunk; ++it) {
-        if (left) {
-          FR_TRY(op_apply(c, q, tmp, c->w_z, s));
-          FR_TRY(frk::block_apply(c, c->w_z, w, s));
-        } else {
-          FR_TRY(frk::block_apply(c, tmp, c->w_z, s));
-          FR_TRY(op_apply(c, q, c->w_z, w, s));
+      const int j0 = issued;
+      auto issue = [&](cudaStream_t cs) -> int {
+        for (int it = 0; it < nchunk; ++it) {
+          if (left) {
+            FR_TRY(op_apply(c, q, tmp, inv_dtau, a0_dt, c->w_z, cs));
+            FR_TRY(frk::block_apply(c, c->w_z, w, cs));
+          } else {
+            FR_TRY(frk::block_apply(c, tmp, c->w_z, cs));
+            FR_TRY(op_apply(c, q, c->w_z, inv_dtau, a0_dt, w, cs));
+          }
+          FR_TRY(frk::bk_orthogonalize(c, w, tmp, j0 + it + 1, cs));
         }
-        FR_TRY(frk::bk_orthogonalize(c, w, tmp, issued + it + 1, s));
-      }
+        return FR_OK;
+      };
+      const bool dual = c->cfg.jvp_mode == FR_JVP_DUAL;
+      FR_TRY(gm_chunk(c, j0, nchunk, 4 + (left ? 2 : 0) + (dual ? 1 : 0), dual ? q : nullptr,
+                      issue, s));
       issued += nchunk;
       FR_TRY(frk::bk_status(c, s));
       FR_CUDA_CHECK(c, cudaStreamSynchronize(s));
@@ -173,7 +181,7 @@ int batch_gmres(fr_ctx* c, const double* q, const double* b, double* x,
       FR_TRY(frk::block_apply(c, c->w_u, c->w_z, s));
       FR_TRY(frk::axpby(c, 1.0, c->w_z, 1.0, x, s));
     }
-    FR_TRY(op_apply(c, q, x, c->w_t, s));
+    FR_TRY(op_apply(c, q, x, inv_dtau, a0_dt, c->w_t, s));
     FR_TRY(frk::axpby(c, 1.0, b, -1.0, c->w_t, s));
     if (left) FR_TRY(frk::block_apply(c, c->w_t, r, s));
     else FR_CUDA_CHECK(c, cudaMemcpyAsync(r, c->w_t, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -184,6 +192,13 @@ int batch_gmres(fr_ctx* c, const double* q, const double* b, double* x,
   iters = total;
   return FR_OK;
 }
+
+}  // namespace frk
+
+namespace {
+
+using frk::case_norms;
+using frk::upload_coef;
 
 // The pseudo-time Newton loop of Sec. 3.2 for every case of a group, in lock step.
 // a[k] = {a0, a1, a2, dt} of case k (unsteady) or unused (steady).
@@ -256,7 +271,7 @@ int batch_newton(fr_ctx* c, double* q, const double* qcn, const double* qcnm1,
       for (int k = 0; k < nc; ++k) S[k]->block_builds += active[k];
     }
     if (cfg.jvp_mode == FR_JVP_LINEARIZED) FR_TRY(frk::linearize(c, q, 0.0, 0.0, s));
-    FR_TRY(batch_gmres(c, q, r, c->w_x, active, its, failed, s));
+    FR_TRY(frk::gmres_cases(c, q, r, c->w_x, 0.0, 0.0, active, its, failed, s));
     for (int k = 0; k < nc; ++k) {
       if (active[k]) S[k]->gmres_iterations[mk[k]] = its[k];
       prev[k] = rm[k];
@@ -429,7 +444,6 @@ int fr_batch_create(const fr_config* cfg, const fr_case* cases, int ncases, fr_b
     if (rc != FR_OK) break;
     G.c->external_terms = true;
     rc = fr_setup_cases(G.c, (int)G.cases.size(), nxs.data(), nys.data(), params.data());
-    if (rc == FR_OK) rc = frk::batch_setup(G.c);
     if (rc == FR_OK && (cudaStreamCreateWithFlags(&G.s, cudaStreamNonBlocking) != cudaSuccess ||
                         cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming) != cudaSuccess))
       rc = FR_ERR_CUDA;

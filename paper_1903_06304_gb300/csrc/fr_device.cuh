@@ -54,6 +54,7 @@ struct CaseParams {
   // e0 is its first element in the launch's element numbering, sn = elements x points.
   long long off;
   int e0, sn;
+  int nx, ny;   // the case's periodic box: element e0 + j nx + i is at column i, row j
 };
 
 // Element topology of one launch: face neighbours (L, R, B, T) by global element index,
@@ -119,6 +120,49 @@ template <class T> __device__ __forceinline__ T from_parts(double v, double d);
 template <> __device__ __forceinline__ double from_parts<double>(double v, double) { return v; }
 template <> __device__ __forceinline__ Dual from_parts<Dual>(double v, double d) { return mk(v, d); }
 
+// A constant (double) or a parameter-dependent value (Dual) as a T.
+template <class T> __device__ __forceinline__ T as_T(double x) { return from_parts<T>(x, 0.0); }
+template <class T> __device__ __forceinline__ T as_T(Dual x);
+template <> __device__ __forceinline__ Dual as_T<Dual>(Dual x) { return x; }
+
+// Gas with the tangent of its Mach-dependent constants (R = 1/(gamma M^2), C_p =
+// 1/((gamma-1) M^2), k = mu C_p / Pr, kappa M_inf) for a Mach tangent dM; the others have
+// zero tangent.
+struct GasD {
+  Dual gamma, R, inv_R, cp, inv_cp, inv_gm1, mu, inv_re, k_cond, kappa_minf, eps_floor;
+  int viscous;
+};
+__device__ __forceinline__ GasD gas_tangent(const Gas& g, double dM) {
+  const double M = sqrt(g.inv_R / g.gamma);   // inv_R = gamma M^2
+  const double s = dM / M;                    // d(M^k)/M^k = k dM / M
+  GasD o;
+  o.gamma = mk(g.gamma, 0.0);
+  o.R = mk(g.R, -2.0 * g.R * s);
+  o.inv_R = mk(g.inv_R, 2.0 * g.inv_R * s);
+  o.cp = mk(g.cp, -2.0 * g.cp * s);
+  o.inv_cp = mk(g.inv_cp, 2.0 * g.inv_cp * s);
+  o.inv_gm1 = mk(g.inv_gm1, 0.0);
+  o.mu = mk(g.mu, 0.0);
+  o.inv_re = mk(g.inv_re, 0.0);
+  o.k_cond = mk(g.k_cond, -2.0 * g.k_cond * s);
+  o.kappa_minf = mk(g.kappa_minf, g.kappa_minf * s);
+  o.eps_floor = mk(g.eps_floor, 0.0);
+  o.viscous = g.viscous;
+  return o;
+}
+// The gas a kernel instantiation computes with: plain for G = double, with the Mach
+// tangent for G = Dual (the parameter-sensitivity path).
+template <class G> struct GasOf { using type = const Gas&; };
+template <> struct GasOf<Dual> { using type = GasD; };
+template <class G> __device__ __forceinline__ typename GasOf<G>::type gas_for(const Gas& g, double dM);
+template <> __device__ __forceinline__ const Gas& gas_for<double>(const Gas& g, double) { return g; }
+template <> __device__ __forceinline__ GasD gas_for<Dual>(const Gas& g, double dM) { return gas_tangent(g, dM); }
+
+// Geometry read as G: plain values, or values with tangents from a second array.
+template <class G> __device__ __forceinline__ G geo(const double* v, const double* d, size_t i);
+template <> __device__ __forceinline__ double geo<double>(const double* v, const double*, size_t i) { return v[i]; }
+template <> __device__ __forceinline__ Dual geo<Dual>(const double* v, const double* d, size_t i) { return mk(v[i], d[i]); }
+
 // A device buffer of T stored as separate value / tangent FP64 arrays.
 template <class T> struct Buf;
 template <> struct Buf<double> {
@@ -140,8 +184,8 @@ struct Thermo {
   T rho, qc[4], f[4], g[4];
 };
 
-template <class T>
-__device__ __forceinline__ void thermo(const T q[4], const Gas& gs, Thermo<T>& o) {
+template <class T, class GS>
+__device__ __forceinline__ void thermo(const T q[4], const GS& gs, Thermo<T>& o) {
   const T invT = inv(q[3]);
   o.rho = q[0] * invT * gs.inv_R;
   const T ru = o.rho * q[1], rv = o.rho * q[2];
@@ -155,11 +199,11 @@ __device__ __forceinline__ void thermo(const T q[4], const Gas& gs, Thermo<T>& o
 
 // Viscous fluxes (Eqs. diffusion, shear_stress), added with the FR sign: the total
 // flux is f_inv - f_vis, so fv/gv here are returned as -f_vis, -g_vis.
-template <class T>
+template <class T, class GS>
 __device__ __forceinline__ void neg_viscous_flux(const T q[4], const T qx[4], const T qy[4],
-                                                 const Gas& gs, T fv[4], T gv[4]) {
-  const double m43 = 4.0 / 3.0 * gs.mu * gs.inv_re, m23 = 2.0 / 3.0 * gs.mu * gs.inv_re;
-  const double m1 = gs.mu * gs.inv_re, kr = gs.k_cond * gs.inv_re;
+                                                 const GS& gs, T fv[4], T gv[4]) {
+  const auto m43 = 4.0 / 3.0 * gs.mu * gs.inv_re, m23 = 2.0 / 3.0 * gs.mu * gs.inv_re;
+  const auto m1 = gs.mu * gs.inv_re, kr = gs.k_cond * gs.inv_re;
   const T txx = m43 * qx[1] - m23 * qy[2];
   const T tyy = m43 * qy[2] - m23 * qx[1];
   const T txy = m1 * (qy[1] + qx[2]);
@@ -183,11 +227,10 @@ __device__ __forceinline__ void neg_viscous_flux(const T q[4], const T qx[4], co
 //   viscous (BR2, Sec. 3.1): q^com = (q+ + q-)/2, grad q^com = (grad q+ + r+ + grad q-
 //     + r-)/2 with r-+ = (q^com - q-+) S g'(end) / |J|-+, which sum to
 //     (q+ - q-) S g_R'(1) (1/|J|- + 1/|J|+) / 2;  |S| f_vis . n = f_vis . S.
-template <class T>
+template <class T, class G, class GS>
 __device__ __forceinline__ void face_common(const T qm[4], const T qp[4], const T gm[8],
-                                            const T gp[8], double Sx, double Sy, double ug,
-                                            double vg, double Jm, double Jp, const Gas& gs,
-                                            double dgR_end, T fnum[4], T qcom[4]) {
+                                            const T gp[8], G Sx, G Sy, G ug, G vg, G Jm, G Jp,
+                                            const GS& gs, double dgR_end, T fnum[4], T qcom[4]) {
   T dq[4], qa[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) { dq[k] = qp[k] - qm[k]; qa[k] = 0.5 * (qp[k] + qm[k]); qcom[k] = qa[k]; }
@@ -196,7 +239,7 @@ __device__ __forceinline__ void face_common(const T qm[4], const T qp[4], const 
   {
     Thermo<T> t;
     thermo(qm, gs, t);
-    const double vgS = ug * Sx + vg * Sy;
+    const G vgS = ug * Sx + vg * Sy;
 #pragma unroll
     for (int k = 0; k < 4; ++k) fm[k] = t.f[k] * Sx + t.g[k] * Sy - vgS * t.qc[k];
     thermo(qp, gs, t);
@@ -212,13 +255,13 @@ __device__ __forceinline__ void face_common(const T qm[4], const T qp[4], const 
   const T w2 = wx * wx + wy * wy;
   // M_mov^2 = |v - v_g|^2 / c^2; eps = min(1, max(kappa M_inf, M_mov)), floored.
   T eps = sqrt_(w2 * inv(c2));
-  eps = vmax(from_parts<T>(gs.kappa_minf, 0.0), eps);
+  eps = vmax(as_T<T>(gs.kappa_minf), eps);
   eps = vmin(from_parts<T>(1.0, 0.0), eps);
-  eps = vmax(eps, from_parts<T>(gs.eps_floor, 0.0));
+  eps = vmax(eps, as_T<T>(gs.eps_floor));
   const T ur2 = eps * eps * c2;
   const T beta = (gs.inv_R - gs.inv_cp) * invTa;     // rho_p + rho_T/(rho C_p)
   const T alpha = 0.5 * (1.0 - beta * ur2);
-  const double S2 = Sx * Sx + Sy * Sy;
+  const G S2 = Sx * Sx + Sy * Sy;
   const T un = wx * Sx + wy * Sy;                     // |S| u_n
   const T unp = un * (1.0 - alpha);
   const T cpr = sqrt_(alpha * alpha * un * un + ur2 * S2);
@@ -242,7 +285,7 @@ __device__ __forceinline__ void face_common(const T qm[4], const T qp[4], const 
   for (int k = 0; k < 4; ++k) fnum[k] = 0.5 * (fm[k] + fp[k]) - hl * diss[k];
   if (gs.viscous) {
     // (r- + r+)/2 = (q+ - q-) S g_R'(1) (1/|J|- + 1/|J|+) / 4
-    const double lift = 0.25 * dgR_end * (1.0 / Jm + 1.0 / Jp);
+    const G lift = 0.25 * dgR_end * (inv(Jm) + inv(Jp));
     T qx[4], qy[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {

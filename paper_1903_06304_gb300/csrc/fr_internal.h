@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <functional>
 #include <vector>
 #include "fr_device.cuh"
 #include "../../include/fr.h"
@@ -71,6 +72,17 @@ struct FrProf {
   long long n[KK_COUNT] = {};
 };
 
+// A captured chunk of GMRES iterations (CUDA graph) and the launch / algorithmic counts
+// one replay adds.
+struct GraphEntry {
+  int start, count, tag;
+  const void* q;
+  cudaGraphExec_t exec;
+  long long launches;
+  long long by_kind[KK_COUNT];
+  double flops[KK_COUNT], bytes[KK_COUNT];
+};
+
 struct fr_ctx {
   fr_config cfg;
   int p, n, np2, bsz;
@@ -87,6 +99,12 @@ struct fr_ctx {
   int ncases = 1;
   bool external_terms = false;  // time and operator terms are set per case by the caller
   BatchWork bw;                 // batched loops (cases of one degree and viscous switch)
+  std::vector<GraphEntry> graphs;   // captured GMRES chunks (fr_api.cu)
+  // parameter sensitivities (fr_sens.cu): geometry values and tangents, seeds, per-element
+  // dot products, a zero state tangent and the residual tangent
+  double *sgs = nullptr, *sdgs = nullptr, *sgf = nullptr, *sdgf = nullptr;
+  double *seed = nullptr, *edot = nullptr, *zero = nullptr, *rtan = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only for capturing
   // geometry (Sec. 2.3)
   double* gs = nullptr;   // [GS_COUNT][Ne*np2]
   double* gf = nullptr;   // [GF_COUNT][Ne*4*n]
@@ -105,8 +123,6 @@ struct fr_ctx {
   double *JP = nullptr, *JG = nullptr, *PP = nullptr;  // point map: [32|64|16][Ne*n^2]
   double *adj_q = nullptr, *adj_fn = nullptr, *adj_qc = nullptr;  // transpose work
   int lin_ready = 0;
-  GmresState* gst = nullptr;      // device
-  GmresState* gst_h = nullptr;    // pinned host mirror
   // Krylov workspace
   double* V = nullptr;       // [(m+1)][ndof]
   double *w_r = nullptr, *w_z = nullptr, *w_x = nullptr, *w_t = nullptr, *w_u = nullptr;
@@ -152,6 +168,14 @@ void fr_prof_end(fr_ctx* c, cudaStream_t s, cudaEvent_t begin, int kind);
 fr::Basis fr_make_basis(int p);
 fr::Gas fr_make_gas(const fr_config& c);
 
+// Issue `count` GMRES iterations starting at basis index `start` through issue(stream):
+// directly while profiling or with cfg.graphs off, otherwise by replaying a CUDA graph
+// captured on first use (keyed by start, count, tag and q).  Every launch inside a chunk
+// must take fixed arguments for a given key.
+int gm_chunk(fr_ctx* c, int start, int count, int tag, const void* q,
+             const std::function<int(cudaStream_t)>& issue, cudaStream_t s);
+void graphs_free(fr_ctx* c);
+
 // Topology, case table and workspace of ncases doubly periodic boxes of nxs[k] x nys[k]
 // elements, numbered case after case; params supplies each case's gas and terms (its
 // layout fields are filled here).  Synchronous.
@@ -183,9 +207,6 @@ int norms(fr_ctx* c, const double* r, double* out_dev, cudaStream_t s);
 int scale(fr_ctx* c, const double* x, double a, double* y, cudaStream_t s);
 int lincomb(fr_ctx* c, const double* V, int nv, const double* y_dev, double* u, cudaStream_t s);
 int axpy(fr_ctx* c, const double* V, int nv, const double* h_dev, double* w, cudaStream_t s);
-int gm_copy_in(fr_ctx* c, double* dst, cudaStream_t s);
-int gm_orthogonalize(fr_ctx* c, double* w, double* next, int nv_bound, cudaStream_t s);
-int gm_trisolve(fr_ctx* c, cudaStream_t s);
 int axpby(fr_ctx* c, double a, const double* x, double b, double* y, cudaStream_t s);
 // Batched (per-case) forms; scalars of case k at bw.dsc + k * 128.
 int batch_setup(fr_ctx* c);
@@ -197,6 +218,15 @@ int bk_finish(fr_ctx* c, double* u, cudaStream_t s);              // trisolve + 
 int bk_status(fr_ctx* c, cudaStream_t s);                         // -> bw.status_h (async)
 int bk_axpy_case(fr_ctx* c, const double* coef_dev, const double* x, double* y, cudaStream_t s);
 int upload_cases(fr_ctx* c, cudaStream_t s);                      // c->cps -> device
+// Per-case continuity-row and full norms of r (synchronises; bad[k] set for non-finite).
+int case_norms(fr_ctx* c, const double* r, std::vector<double>& mass, std::vector<double>& all,
+               std::vector<char>& bad, cudaStream_t s);
+// Restarted GMRES(m <= 32) of every active case with device-resident Arnoldi (fr_batch.cu);
+// inv_dtau, a0_dt feed the dual-number operator of a single-case context (a batch reads
+// its terms from the case table).
+int gmres_cases(fr_ctx* c, const double* q, const double* b, double* x, double inv_dtau,
+                double a0_dt, const std::vector<char>& active, std::vector<int>& iters,
+                std::vector<char>& failed, cudaStream_t s);
 }  // namespace frk
 
 #define FR_CUDA_CHECK(c, expr)                                                       \

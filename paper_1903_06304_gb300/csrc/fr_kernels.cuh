@@ -11,18 +11,19 @@ namespace fr {
 // S_eta = |J| grad(eta) = (-y_xi, x_xi), v_g (bilinear in the corner velocities) and
 // |J| xi_t = -v_g . S_xi, |J| eta_t = -v_g . S_eta, at solution and flux points; the
 // divergence of (|J| xi_t, |J| eta_t) by the interpolant derivative.
+template <class T>
 struct MapPoint {
-  double x_xi, x_eta, y_xi, y_eta, ug, vg;
+  T x_xi, x_eta, y_xi, y_eta, ug, vg;
 };
 
-__device__ __forceinline__ MapPoint map_at(const double X[4], const double Y[4],
-                                           const double VX[4], const double VY[4], double xi,
-                                           double eta) {
+template <class T>
+__device__ __forceinline__ MapPoint<T> map_at(const T X[4], const T Y[4], const T VX[4],
+                                              const T VY[4], double xi, double eta) {
   const double N0 = 0.25 * (1 - xi) * (1 - eta), N1 = 0.25 * (1 + xi) * (1 - eta);
   const double N2 = 0.25 * (1 + xi) * (1 + eta), N3 = 0.25 * (1 - xi) * (1 + eta);
   const double a0 = -0.25 * (1 - eta), a1 = 0.25 * (1 - eta), a2 = 0.25 * (1 + eta), a3 = -0.25 * (1 + eta);
   const double b0 = -0.25 * (1 - xi), b1 = -0.25 * (1 + xi), b2 = 0.25 * (1 + xi), b3 = 0.25 * (1 - xi);
-  MapPoint m;
+  MapPoint<T> m;
   m.x_xi = a0 * X[0] + a1 * X[1] + a2 * X[2] + a3 * X[3];
   m.y_xi = a0 * Y[0] + a1 * Y[1] + a2 * Y[2] + a3 * Y[3];
   m.x_eta = b0 * X[0] + b1 * X[1] + b2 * X[2] + b3 * X[3];
@@ -32,52 +33,57 @@ __device__ __forceinline__ MapPoint map_at(const double X[4], const double Y[4],
   return m;
 }
 
-template <int N>
+// T = double: the geometry.  T = Dual: the geometry and its tangent for the corner and
+// corner-velocity tangents dcorners, dvel (the parameter-sensitivity path).
+template <int N, class T = double>
 __global__ void k_geometry(const double* __restrict__ corners, const double* __restrict__ vel,
-                           int ne, Basis B, double* __restrict__ gs, double* __restrict__ gf) {
+                           int ne, Basis B, Buf<T> GS, Buf<T> GF,
+                           const double* __restrict__ dcorners = nullptr,
+                           const double* __restrict__ dvel = nullptr) {
   constexpr int NP = N * N;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
-  double X[4], Y[4], VX[4], VY[4];
+  T X[4], Y[4], VX[4], VY[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    X[a] = corners[e * 8 + 2 * a];
-    Y[a] = corners[e * 8 + 2 * a + 1];
-    VX[a] = vel[e * 8 + 2 * a];
-    VY[a] = vel[e * 8 + 2 * a + 1];
+    const size_t i = (size_t)e * 8 + 2 * a;
+    X[a] = from_parts<T>(corners[i], dcorners ? dcorners[i] : 0.0);
+    Y[a] = from_parts<T>(corners[i + 1], dcorners ? dcorners[i + 1] : 0.0);
+    VX[a] = from_parts<T>(vel[i], dvel ? dvel[i] : 0.0);
+    VY[a] = from_parts<T>(vel[i + 1], dvel ? dvel[i + 1] : 0.0);
   }
   const size_t SN = (size_t)ne * NP;
-  double stx[NP], ste[NP];
+  T stx[NP], ste[NP];
 #pragma unroll
   for (int j = 0; j < N; ++j) {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const MapPoint m = map_at(X, Y, VX, VY, B.xs[i], B.xs[j]);
-      const double J = m.x_xi * m.y_eta - m.x_eta * m.y_xi;
-      const double sxx = m.y_eta, sxy = -m.x_eta, sex = -m.y_xi, sey = m.x_xi;
+      const MapPoint<T> m = map_at(X, Y, VX, VY, B.xs[i], B.xs[j]);
+      const T J = m.x_xi * m.y_eta - m.x_eta * m.y_xi;
+      const T sxx = m.y_eta, sxy = -m.x_eta, sex = -m.y_xi, sey = m.x_xi;
       const size_t o = (size_t)e * NP + j * N + i;
-      gs[GS_SXX * SN + o] = sxx;
-      gs[GS_SXY * SN + o] = sxy;
-      gs[GS_SEX * SN + o] = sex;
-      gs[GS_SEY * SN + o] = sey;
+      GS.st(GS_SXX * SN + o, sxx);
+      GS.st(GS_SXY * SN + o, sxy);
+      GS.st(GS_SEX * SN + o, sex);
+      GS.st(GS_SEY * SN + o, sey);
       stx[j * N + i] = -(m.ug * sxx + m.vg * sxy);
       ste[j * N + i] = -(m.ug * sex + m.vg * sey);
-      gs[GS_STX * SN + o] = stx[j * N + i];
-      gs[GS_STE * SN + o] = ste[j * N + i];
-      gs[GS_INVJ * SN + o] = 1.0 / J;
-      gs[GS_J * SN + o] = J;
-      gs[GS_UG * SN + o] = m.ug;
-      gs[GS_VG * SN + o] = m.vg;
+      GS.st(GS_STX * SN + o, stx[j * N + i]);
+      GS.st(GS_STE * SN + o, ste[j * N + i]);
+      GS.st(GS_INVJ * SN + o, inv(J));
+      GS.st(GS_J * SN + o, J);
+      GS.st(GS_UG * SN + o, m.ug);
+      GS.st(GS_VG * SN + o, m.vg);
     }
   }
 #pragma unroll
   for (int j = 0; j < N; ++j) {
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      double d = 0.0;
+      T d = from_parts<T>(0.0, 0.0);
 #pragma unroll
-      for (int k = 0; k < N; ++k) d += B.D[i][k] * stx[j * N + k] + B.D[j][k] * ste[k * N + i];
-      gs[GS_DIVST * SN + (size_t)e * NP + j * N + i] = d;
+      for (int k = 0; k < N; ++k) d = d + (B.D[i][k] * stx[j * N + k] + B.D[j][k] * ste[k * N + i]);
+      GS.st(GS_DIVST * SN + (size_t)e * NP + j * N + i, d);
     }
   }
   const size_t FN = (size_t)ne * 4 * N;
@@ -87,15 +93,15 @@ __global__ void k_geometry(const double* __restrict__ corners, const double* __r
     for (int t = 0; t < N; ++t) {
       const double xi = f == FACE_L ? -1.0 : f == FACE_R ? 1.0 : B.xs[t];
       const double eta = f == FACE_B ? -1.0 : f == FACE_T ? 1.0 : B.xs[t];
-      const MapPoint m = map_at(X, Y, VX, VY, xi, eta);
-      const double J = m.x_xi * m.y_eta - m.x_eta * m.y_xi;
+      const MapPoint<T> m = map_at(X, Y, VX, VY, xi, eta);
+      const T J = m.x_xi * m.y_eta - m.x_eta * m.y_xi;
       const bool along_xi = (f == FACE_L || f == FACE_R);
       const size_t o = ((size_t)e * 4 + f) * N + t;
-      gf[GF_SX * FN + o] = along_xi ? m.y_eta : -m.y_xi;
-      gf[GF_SY * FN + o] = along_xi ? -m.x_eta : m.x_xi;
-      gf[GF_J * FN + o] = J;
-      gf[GF_UG * FN + o] = m.ug;
-      gf[GF_VG * FN + o] = m.vg;
+      GF.st(GF_SX * FN + o, along_xi ? m.y_eta : -m.y_xi);
+      GF.st(GF_SY * FN + o, along_xi ? -m.x_eta : m.x_xi);
+      GF.st(GF_J * FN + o, J);
+      GF.st(GF_UG * FN + o, m.ug);
+      GF.st(GF_VG * FN + o, m.vg);
     }
   }
 }
@@ -122,10 +128,10 @@ static __global__ void k_set_case(CaseParams* cp, int cid, CaseParams value) { c
 // q^p (and the tangent) of EPB elements staged in shared memory; each thread owns one
 // solution point.  Outputs: gl[8][Ne*NP] local gradients (x comps then y comps),
 // tq[Ne][4][4][N] state traces, tg[Ne][4][8][N] gradient traces.
-template <class T, int N>
+template <class T, int N, class G = double>
 __global__ void __launch_bounds__(Tile<N>::THREADS)
 k_trace(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs, Buf<T> GL, Buf<T> TQ,
-        Buf<T> TG) {
+        Buf<T> TG, const double* __restrict__ dgs = nullptr) {
   const int ne = M.ne;
   constexpr int NP = N * N, EPB = Tile<N>::EPB;
   __shared__ T sq[EPB][4][NP];
@@ -144,9 +150,9 @@ k_trace(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs, Buf<T> GL, Buf
   __syncthreads();
   if (M.viscous) {
     if (live) {
-      const double sxx = gs[GS_SXX * SN + o], sxy = gs[GS_SXY * SN + o];
-      const double sex = gs[GS_SEX * SN + o], sey = gs[GS_SEY * SN + o];
-      const double ij = gs[GS_INVJ * SN + o];
+      const G sxx = geo<G>(gs, dgs, GS_SXX * SN + o), sxy = geo<G>(gs, dgs, GS_SXY * SN + o);
+      const G sex = geo<G>(gs, dgs, GS_SEX * SN + o), sey = geo<G>(gs, dgs, GS_SEY * SN + o);
+      const G ij = geo<G>(gs, dgs, GS_INVJ * SN + o);
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         T dxi = B.D[i][0] * sq[le][v][j * N + 0];
@@ -193,15 +199,16 @@ k_trace(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs, Buf<T> GL, Buf
 // ------------------------------------------------------------------ face kernel
 // One thread per owned flux point: xi-faces are owned by their '-' (left) element (its R
 // face), eta-faces by their bottom element (its T face).  Outputs fn, qcm [Ne][2][4][N].
-template <class T, int N>
+template <class T, int N, class G = double>
 __global__ void k_face(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ,
-                       Buf<T> TG, Buf<T> FN, Buf<T> QC) {
+                       Buf<T> TG, Buf<T> FN, Buf<T> QC, const double* __restrict__ dgf = nullptr,
+                       double dmach = 0.0) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= M.ne * 2 * N) return;
   const int e = idx / (2 * N), rem = idx % (2 * N), dir = rem / N, t = rem % N;
   const int plus = dir == 0 ? M.right(e) : M.top(e);
   const int fm = dir == 0 ? FACE_R : FACE_T, fp = dir == 0 ? FACE_L : FACE_B;
-  const Gas& gas = M.par(e).gas;
+  typename GasOf<G>::type gas = gas_for<G>(M.par(e).gas, dmach);
   T qm[4], qp[4], gm[8], gp[8];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -218,8 +225,9 @@ __global__ void k_face(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ
   const size_t FNs = (size_t)M.ne * 4 * N;
   const size_t om = ((size_t)e * 4 + fm) * N + t, op = ((size_t)plus * 4 + fp) * N + t;
   T fnum[4], qcom[4];
-  face_common(qm, qp, gm, gp, gf[GF_SX * FNs + om], gf[GF_SY * FNs + om], gf[GF_UG * FNs + om],
-              gf[GF_VG * FNs + om], gf[GF_J * FNs + om], gf[GF_J * FNs + op], gas, B.dgR_end,
+  face_common(qm, qp, gm, gp, geo<G>(gf, dgf, GF_SX * FNs + om), geo<G>(gf, dgf, GF_SY * FNs + om),
+              geo<G>(gf, dgf, GF_UG * FNs + om), geo<G>(gf, dgf, GF_VG * FNs + om),
+              geo<G>(gf, dgf, GF_J * FNs + om), geo<G>(gf, dgf, GF_J * FNs + op), gas, B.dgR_end,
               fnum, qcom);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -230,7 +238,8 @@ __global__ void k_face(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ
 }
 
 // ------------------------------------------------------------------ element kernel
-enum { MODE_RESID = 0, MODE_JVP = 1 };
+// MODE_TAN writes only the tangent of R (the parameter-sensitivity path).
+enum { MODE_RESID = 0, MODE_JVP = 1, MODE_TAN = 2 };
 
 struct TimeTerms {           // r = R - (a0 q^c + a1 qc_n + a2 qc_nm1)/dt, coefficients per case
   const double* qcn;
@@ -265,11 +274,12 @@ __device__ __forceinline__ void gamma_m_apply(const double q[4], const double w[
   out[3] = h * d0 - s * w[0] + sr * (q[1] * w[1] + q[2] * w[2]) + sr * gs.cp * w[3];
 }
 
-template <class T, int N, int MODE>
+template <class T, int N, int MODE, class G = double>
 __global__ void __launch_bounds__(Tile<N>::THREADS)
 k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
        const double* __restrict__ gf, Buf<T> GL, Buf<T> TQ, Buf<T> FN, Buf<T> QC,
-       double* __restrict__ out, TimeTerms tt) {
+       double* __restrict__ out, TimeTerms tt, const double* __restrict__ dgs = nullptr,
+       const double* __restrict__ dgf = nullptr, double dmach = 0.0) {
   constexpr int NP = N * N, EPB = Tile<N>::EPB;
   __shared__ T sF[EPB][4][NP];
   __shared__ T sG[EPB][4][NP];
@@ -282,15 +292,15 @@ k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
   const size_t o = (size_t)e * NP + pt;
   T q[4];
   Thermo<T> th;
-  double ij = 0.0;
+  G ij = from_parts<G>(0.0, 0.0);
   const CaseParams& cpar = M.par(live ? e : 0);
-  const Gas& gas = cpar.gas;
+  typename GasOf<G>::type gas = gas_for<G>(cpar.gas, dmach);
   const size_t qo = live ? M.qbase(e, NP) + pt : 0, qs = cpar.sn;
   if (live) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) q[v] = Q.ld(v * qs + qo);
     thermo(q, gas, th);
-    ij = gs[GS_INVJ * SN + o];
+    ij = geo<G>(gs, dgs, GS_INVJ * SN + o);
     T fx[4], gy[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) { fx[v] = th.f[v]; gy[v] = th.g[v]; }
@@ -308,7 +318,7 @@ k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
         const double w = (f == FACE_L) ? B.dgL[i] : (f == FACE_R) ? B.dgR[i]
                        : (f == FACE_B) ? B.dgL[j] : B.dgR[j];
         const size_t of = ((size_t)e * 4 + f) * N + s;
-        const double sx = gf[GF_SX * FNs + of] * w * ij, sy = gf[GF_SY * FNs + of] * w * ij;
+        const G sx = geo<G>(gf, dgf, GF_SX * FNs + of) * w * ij, sy = geo<G>(gf, dgf, GF_SY * FNs + of) * w * ij;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const T jump = QC.ld((((size_t)qsrc[f] * 2 + qdir[f]) * 4 + v) * N + s) -
@@ -322,9 +332,9 @@ k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
 #pragma unroll
       for (int v = 0; v < 4; ++v) { fx[v] = fx[v] + fv[v]; gy[v] = gy[v] + gv[v]; }
     }
-    const double sxx = gs[GS_SXX * SN + o], sxy = gs[GS_SXY * SN + o];
-    const double sex = gs[GS_SEX * SN + o], sey = gs[GS_SEY * SN + o];
-    const double stx = gs[GS_STX * SN + o], ste = gs[GS_STE * SN + o];
+    const G sxx = geo<G>(gs, dgs, GS_SXX * SN + o), sxy = geo<G>(gs, dgs, GS_SXY * SN + o);
+    const G sex = geo<G>(gs, dgs, GS_SEX * SN + o), sey = geo<G>(gs, dgs, GS_SEY * SN + o);
+    const G stx = geo<G>(gs, dgs, GS_STX * SN + o), ste = geo<G>(gs, dgs, GS_STE * SN + o);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       sF[le][v][pt] = sxx * fx[v] + sxy * gy[v] + stx * th.qc[v];
@@ -334,7 +344,7 @@ k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
   __syncthreads();
   if (!live) return;
   const int nbL = M.left(e), nbB = M.bottom(e);
-  const double divst = gs[GS_DIVST * SN + o];
+  const G divst = geo<G>(gs, dgs, GS_DIVST * SN + o);
   T R[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -350,7 +360,7 @@ k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
     d = d - th.qc[v] * divst;
     R[v] = -(d * ij);
   }
-  if (MODE == MODE_RESID) {
+  if constexpr (MODE == MODE_RESID) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       double r = val(R[v]);
@@ -361,6 +371,9 @@ k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
       }
       out[v * qs + qo] = r;
     }
+  } else if constexpr (MODE == MODE_TAN) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[v * qs + qo] = tan_(R[v]);
   } else {
     double qv[4], wv[4], gm[4];
 #pragma unroll

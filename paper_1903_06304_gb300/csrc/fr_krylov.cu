@@ -220,13 +220,8 @@ __global__ void k_lincomb(const double* __restrict__ V, size_t ld, int nv, const
 
 // ------------------------------------------------------------------ device-resident Arnoldi
 // One restart cycle's Hessenberg matrix, Givens rotations and residual estimates live on
-// the device so that iterations are queued without a host round trip.
-__global__ void k_gm_copy_in(const double* __restrict__ V, size_t ld, const GmresState* st,
-                             double* __restrict__ dst, size_t n) {
-  const size_t base = (size_t)st->j * ld;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = V[base + i];
-}
+// the device (one GmresState per case) so that iterations are queued without a host
+// round trip.
 
 // Column j of H from the CGS2 projections h1 + h2 and ||w||, the previous rotations, a
 // new rotation, the residual estimate |g_{j+1}| and the stopping test (one thread).
@@ -255,19 +250,6 @@ __device__ void gm_givens(GmresState* st, const double* h1, const double* h2, co
   if (fabs(st->g[j + 1]) <= st->tol || hn == 0.0 || j + 1 >= st->jmax) st->done = 1;
 }
 
-// V[j] = w / ||w|| with j the index the Givens update wrote; the same values go to next,
-// the input of the following iteration's operator.
-__global__ void k_gm_store(const double* __restrict__ w, const GmresState* st,
-                           double* __restrict__ V, size_t ld, double* __restrict__ next, size_t n) {
-  const size_t base = (size_t)st->j * ld;
-  const double s = st->inv_hn;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double x = w[i] * s;
-    V[base + i] = x;
-    next[i] = x;
-  }
-}
-
 // Back substitution H[0:k,0:k] y = g[0:k], k = j (one thread).
 __device__ void gm_trisolve(GmresState* st) {
   constexpr int L = GmresState::LD;
@@ -277,9 +259,6 @@ __device__ void gm_trisolve(GmresState* st) {
     for (int l = i + 1; l < k; ++l) acc -= st->H[i * L + l] * st->y[l];
     st->y[i] = acc / st->H[i * L + i];
   }
-}
-__global__ void k_gm_trisolve(GmresState* st) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) gm_trisolve(st);
 }
 
 // ------------------------------------------------------------------ batched (per-case) forms
@@ -291,33 +270,6 @@ __global__ void k_gm_trisolve(GmresState* st) {
 // projections at [0, BM), the second at [BM, 2BM), ||w||^2 at 2BM, norms at 3BM.
 constexpr int BM = GmresState::LD;
 constexpr int BDS = 4 * BM;
-
-template <int MODE, int NV>
-__global__ void __launch_bounds__(RT) k_bkrylov(const double* __restrict__ V, size_t ld, double* w,
-                                                BatchSegs sg, double* __restrict__ partial,
-                                                double* dsc, unsigned int* tickets, GmresState* gst) {
-  const int k = sg.bcase[blockIdx.x];
-  GmresState* st = gst + k;
-  if (st->done) return;   // uniform over the case's blocks: set by an earlier launch
-  int nv = st->j + 1;
-  if (nv > NV) nv = NV;
-  double* ds = dsc + (size_t)k * BDS;
-  constexpr int NA = MODE == 2 ? 1 : NV;
-  double acc[NA];
-#pragma unroll
-  for (int q = 0; q < NA; ++q) acc[q] = 0.0;
-  double hk[NV];
-  const double* h = MODE == 1 ? ds : ds + BM;
-#pragma unroll
-  for (int q = 0; q < NV; ++q) hk[q] = (MODE != 0 && q < nv) ? h[q] : 0.0;
-  krylov_pairs<MODE, NV>(reinterpret_cast<const double2*>(V), ld / 2, reinterpret_cast<double2*>(w),
-                         nv, hk, acc, (size_t)sg.blo[blockIdx.x] + threadIdx.x,
-                         (size_t)sg.bhi[blockIdx.x], RT);
-  double* out = MODE == 0 ? ds : MODE == 1 ? ds + BM : ds + 2 * BM;
-  const bool last = block_reduce_store(acc, MODE == 2 ? 1 : nv, partial, out, tickets + k,
-                                       sg.cb0[k], sg.cnb[k]);
-  if (MODE == 2 && last && threadIdx.x == 0) gm_givens(st, ds, ds + BM, ds + 2 * BM);
-}
 
 // Per case: ||r[continuity row]||^2 and ||r||^2 at dsc[k * BDS + 3BM + 0..1]; the
 // continuity row of case k ends at entry mend[k].
@@ -337,6 +289,146 @@ __global__ void __launch_bounds__(RT) k_bnorms(const double* __restrict__ r, Bat
     acc[1] += xx + yy;
   }
   block_reduce_store(acc, 2, partial, dsc + (size_t)k * BDS + 3 * BM, tickets + k, sg.cb0[k], sg.cnb[k]);
+}
+
+// ---- Arnoldi passes of high occupancy.  The reductions above hold one accumulator per
+// basis vector in every thread, which limits them to one 256-thread block per SM and
+// leaves them waiting on loads.  Here the dot products run on a 2-D grid (pair range x
+// group of KG vectors, a few accumulators per thread) and the updates w -= V h on a grid
+// of SPLIT blocks per pair range (one accumulator per thread, coefficients in shared
+// memory): the same FP64 operations with four to eight times the warps in flight.
+constexpr int KG = 4;       // vectors per block of the dot-product pass
+constexpr int SPLIT = 4;    // blocks per pair range of the update passes
+
+// This block's nw sums acc[0..nw) go to partial[(k0 + q) * ld + pidx]; the last of the
+// `target` blocks sharing the ticket writes out[q] = sum of partial[q * ld + p] over p in
+// [first, first + count), q < nout, in a fixed order.  True in the last block.
+template <int NA>
+__device__ __forceinline__ bool seg_reduce(double (&acc)[NA], int nw, int k0, double* partial,
+                                           size_t ld, size_t pidx, double* out, int nout,
+                                           unsigned int* ticket, unsigned int target,
+                                           size_t first, int count) {
+  __shared__ double sm[NA][RT / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    const double t = warp_sum(acc[q]);
+    if (lane == 0) sm[q][wid] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < nw) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < RT / 32; ++w) t += sm[threadIdx.x][w];
+    partial[(size_t)(k0 + threadIdx.x) * ld + pidx] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == target - 1;
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  for (int q = wid; q < nout; q += RT / 32) {
+    double t = 0.0;
+    for (int p = lane; p < count; p += 32) t += ((volatile double*)partial)[(size_t)q * ld + first + p];
+    t = warp_sum(t);
+    if (lane == 0) out[q] = t;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  __threadfence_block();
+  __syncthreads();
+  return true;
+}
+
+// ds[out_off + k] = <V_k, w>, k < nv, per case (block (b, g): range b, vectors g KG ..).
+__global__ void __launch_bounds__(RT) k_vdots(const double* __restrict__ V, size_t ld,
+                                              const double* __restrict__ w, BatchSegs sg,
+                                              double* __restrict__ partial, double* dsc,
+                                              int out_off, unsigned int* tickets,
+                                              const GmresState* gst) {
+  const int b = blockIdx.x, g = blockIdx.y;
+  const int k = sg.bcase[b];
+  const GmresState* st = gst + k;
+  if (st->done) return;
+  const int nv = st->j + 1;
+  const int ng = (nv + KG - 1) / KG;
+  if (g >= ng) return;
+  const int k0 = g * KG, nw = min(KG, nv - k0);
+  double acc[KG] = {0.0, 0.0, 0.0, 0.0};
+  const double2* V2 = reinterpret_cast<const double2*>(V);
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  const size_t ld2 = ld / 2;
+  const size_t lo = (size_t)sg.blo[b], hi = (size_t)sg.bhi[b];
+  for (size_t i = lo + threadIdx.x; i < hi; i += 2 * RT) {
+    const bool two = i + RT < hi;
+    const double2 xa = w2[i], xb = two ? w2[i + RT] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int q = 0; q < KG; ++q) {
+      if (q < nw) {
+        const double2 va = V2[(k0 + q) * ld2 + i];
+        const double2 vb = two ? V2[(k0 + q) * ld2 + i + RT] : make_double2(0.0, 0.0);
+        acc[q] = fma(va.x, xa.x, acc[q]);
+        acc[q] = fma(va.y, xa.y, acc[q]);
+        acc[q] = fma(vb.x, xb.x, acc[q]);
+        acc[q] = fma(vb.y, xb.y, acc[q]);
+      }
+    }
+  }
+  seg_reduce(acc, nw, k0, partial, gridDim.x, b, dsc + (size_t)k * BDS + out_off, nv,
+             tickets + k, (unsigned)(sg.cnb[k] * ng), (size_t)sg.cb0[k], sg.cnb[k]);
+}
+
+// w -= sum_{k < nv} h_k V_k with h = ds[h_off ..], per case; with NORM also ||w||^2 per
+// case into ds[2BM] and, in the case's last block, the Givens update of the cycle.
+template <bool NORM>
+__global__ void __launch_bounds__(RT) k_vaxpy(const double* __restrict__ V, size_t ld, double* w,
+                                              BatchSegs sg, double* __restrict__ partial,
+                                              double* dsc, int h_off, unsigned int* tickets,
+                                              GmresState* gst) {
+  __shared__ double hs[GmresState::LD + 1];
+  const int b = blockIdx.x, part = blockIdx.y;
+  const int k = sg.bcase[b];
+  GmresState* st = gst + k;
+  if (st->done) return;
+  const int nv = st->j + 1;
+  double* ds = dsc + (size_t)k * BDS;
+  for (int q = threadIdx.x; q < nv; q += RT) hs[q] = ds[h_off + q];
+  __syncthreads();
+  const size_t lo0 = (size_t)sg.blo[b], hi0 = (size_t)sg.bhi[b], len = hi0 - lo0;
+  const size_t lo = lo0 + len * part / SPLIT, hi = lo0 + len * (part + 1) / SPLIT;
+  const double2* V2 = reinterpret_cast<const double2*>(V);
+  double2* w2 = reinterpret_cast<double2*>(w);
+  const size_t ld2 = ld / 2;
+  double acc[1] = {0.0};
+  for (size_t i = lo + threadIdx.x; i < hi; i += RT) {
+    double2 x = w2[i];
+    int q = 0;
+    for (; q + 4 <= nv; q += 4) {   // four independent loads in flight
+      const double2 v0 = V2[(q + 0) * ld2 + i], v1 = V2[(q + 1) * ld2 + i];
+      const double2 v2 = V2[(q + 2) * ld2 + i], v3 = V2[(q + 3) * ld2 + i];
+      x.x = fma(-hs[q], v0.x, x.x); x.y = fma(-hs[q], v0.y, x.y);
+      x.x = fma(-hs[q + 1], v1.x, x.x); x.y = fma(-hs[q + 1], v1.y, x.y);
+      x.x = fma(-hs[q + 2], v2.x, x.x); x.y = fma(-hs[q + 2], v2.y, x.y);
+      x.x = fma(-hs[q + 3], v3.x, x.x); x.y = fma(-hs[q + 3], v3.y, x.y);
+    }
+    for (; q < nv; ++q) {
+      const double2 v = V2[q * ld2 + i];
+      x.x = fma(-hs[q], v.x, x.x);
+      x.y = fma(-hs[q], v.y, x.y);
+    }
+    w2[i] = x;
+    if (NORM) {
+      acc[0] = fma(x.x, x.x, acc[0]);
+      acc[0] = fma(x.y, x.y, acc[0]);
+    }
+  }
+  if (!NORM) return;
+  const size_t pb = (size_t)b * SPLIT + part;
+  const bool last = seg_reduce(acc, 1, 0, partial, (size_t)gridDim.x * SPLIT, pb, ds + 2 * BM, 1,
+                               tickets + k, (unsigned)(sg.cnb[k] * SPLIT),
+                               (size_t)sg.cb0[k] * SPLIT, sg.cnb[k] * SPLIT);
+  if (last && threadIdx.x == 0) gm_givens(st, ds, ds + BM, ds + 2 * BM);
 }
 
 // V[j] = next = w * inv_hn per case, j the case's newest basis index.  With init set the
@@ -478,54 +570,6 @@ int axpy(fr_ctx* c, const double* V, int nv, const double* h, double* w, cudaStr
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }
-// One Arnoldi iteration's reductions and Givens update with the basis index on the device.
-int gm_copy_in(fr_ctx* c, double* dst, cudaStream_t s) {
-  FR_ACCOUNT(c, KK_VECTOR, 0.0, 16.0 * c->ndof);
-  FR_PROF_BEGIN(c, s);
-  k_gm_copy_in<<<grid_for(c), RT, 0, s>>>(c->V, c->ndof, c->gst, dst, c->ndof);
-  FR_PROF_END(c, s, KK_VECTOR);
-  FR_LAUNCH_CHECK(c);
-  return FR_OK;
-}
-int gm_orthogonalize(fr_ctx* c, double* w, double* next, int nv_bound, cudaStream_t s) {
-  const int g = grid_for(c);
-  GmresState* jd = c->gst;
-  constexpr int M = FR_MAX_RESTART;
-  FR_ACCOUNT(c, KK_KRYLOV, 8.0 * nv_bound * c->ndof + 2.0 * c->ndof, 8.0 * c->ndof * (3.0 * nv_bound + 5.0));
-  {
-    FR_PROF_BEGIN(c, s);
-    launch_krylov<0>(nv_bound, g, s, c->V, c->ndof, 0, nullptr, w, c->ndof, c->red, c->dsc, c->ticket, jd);
-    FR_PROF_END(c, s, KK_KRYLOV);
-    FR_LAUNCH_CHECK(c);
-  }
-  {
-    FR_PROF_BEGIN(c, s);
-    launch_krylov<1>(nv_bound, g, s, c->V, c->ndof, 0, c->dsc, w, c->ndof, c->red, c->dsc + M, c->ticket, jd);
-    FR_PROF_END(c, s, KK_KRYLOV);
-    FR_LAUNCH_CHECK(c);
-  }
-  {
-    FR_PROF_BEGIN(c, s);
-    launch_krylov<2>(nv_bound, g, s, c->V, c->ndof, 0, c->dsc + M, w, c->ndof, c->red, c->dsc + 2 * M, c->ticket, jd);
-    FR_PROF_END(c, s, KK_KRYLOV);
-    FR_LAUNCH_CHECK(c);
-  }
-  {
-    FR_ACCOUNT(c, KK_VECTOR, 1.0 * c->ndof, 24.0 * c->ndof);
-    FR_PROF_BEGIN(c, s);
-    k_gm_store<<<grid_for(c), RT, 0, s>>>(w, c->gst, c->V, c->ndof, next, c->ndof);
-    FR_PROF_END(c, s, KK_VECTOR);
-    FR_LAUNCH_CHECK(c);
-  }
-  return FR_OK;
-}
-int gm_trisolve(fr_ctx* c, cudaStream_t s) {
-  FR_PROF_BEGIN(c, s);
-  k_gm_trisolve<<<1, 32, 0, s>>>(c->gst);
-  FR_PROF_END(c, s, KK_KRYLOV);
-  FR_LAUNCH_CHECK(c);
-  return FR_OK;
-}
 int lincomb(fr_ctx* c, const double* V, int nv, const double* y, double* u, cudaStream_t s) {
   FR_ACCOUNT(c, KK_VECTOR, 2.0 * nv * c->ndof, 8.0 * c->ndof * (nv + 1));
 { FR_PROF_BEGIN(c, s); k_lincomb<<<grid_for(c), RT, 0, s>>>(V, c->ndof, nv, y, u, c->ndof); FR_PROF_END(c, s, KK_VECTOR); }
@@ -602,21 +646,6 @@ int batch_setup(fr_ctx* c) {
   return FR_OK;
 }
 
-template <int MODE>
-static void launch_bkrylov(fr_ctx* c, int nv_bound, double* w, cudaStream_t s) {
-  BatchWork& b = c->bw;
-  switch ((nv_bound + 3) / 4) {
-#define FR_BKRYLOV_CASE(q)                                                                       \
-    case q: k_bkrylov<MODE, 4 * q><<<b.nblk, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, \
-                                                         b.tickets, b.gst); break;
-    FR_BKRYLOV_CASE(1) FR_BKRYLOV_CASE(2) FR_BKRYLOV_CASE(3) FR_BKRYLOV_CASE(4)
-    FR_BKRYLOV_CASE(5) FR_BKRYLOV_CASE(6) FR_BKRYLOV_CASE(7)
-    default: k_bkrylov<MODE, 32><<<b.nblk, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc,
-                                                       b.tickets, b.gst); break;
-#undef FR_BKRYLOV_CASE
-  }
-}
-
 int bk_norms(fr_ctx* c, const double* r, cudaStream_t s) {
   FR_ACCOUNT(c, KK_KRYLOV, 2.0 * c->ndof, 8.0 * c->ndof);
   FR_PROF_BEGIN(c, s);
@@ -636,29 +665,38 @@ int bk_init(fr_ctx* c, const double* r, double* next, cudaStream_t s) {
 }
 
 int bk_orthogonalize(fr_ctx* c, double* w, double* next, int nv_bound, cudaStream_t s) {
-  FR_ACCOUNT(c, KK_KRYLOV, 8.0 * nv_bound * c->ndof + 2.0 * c->ndof, 8.0 * c->ndof * (3.0 * nv_bound + 5.0));
+  BatchWork& b = c->bw;
+  const dim3 gdots(b.nblk, (nv_bound + KG - 1) / KG), gaxpy(b.nblk, SPLIT);
+  // CGS2: h1 = V^T w; w -= V h1; h2 = V^T w; w -= V h2, ||w||, Givens; V[j+1] = w/||w||
+  FR_ACCOUNT(c, KK_KRYLOV, 8.0 * nv_bound * c->ndof + 2.0 * c->ndof, 8.0 * c->ndof * (4.0 * nv_bound + 6.0));
   {
     FR_PROF_BEGIN(c, s);
-    launch_bkrylov<0>(c, nv_bound, w, s);
+    k_vdots<<<gdots, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, 0, b.tickets, b.gst);
     FR_PROF_END(c, s, KK_KRYLOV);
     FR_LAUNCH_CHECK(c);
   }
   {
     FR_PROF_BEGIN(c, s);
-    launch_bkrylov<1>(c, nv_bound, w, s);
+    k_vaxpy<false><<<gaxpy, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, 0, b.tickets, b.gst);
     FR_PROF_END(c, s, KK_KRYLOV);
     FR_LAUNCH_CHECK(c);
   }
   {
     FR_PROF_BEGIN(c, s);
-    launch_bkrylov<2>(c, nv_bound, w, s);
+    k_vdots<<<gdots, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, BM, b.tickets, b.gst);
+    FR_PROF_END(c, s, KK_KRYLOV);
+    FR_LAUNCH_CHECK(c);
+  }
+  {
+    FR_PROF_BEGIN(c, s);
+    k_vaxpy<true><<<gaxpy, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, BM, b.tickets, b.gst);
     FR_PROF_END(c, s, KK_KRYLOV);
     FR_LAUNCH_CHECK(c);
   }
   {
     FR_ACCOUNT(c, KK_VECTOR, 1.0 * c->ndof, 24.0 * c->ndof);
     FR_PROF_BEGIN(c, s);
-    k_bgm_store<<<c->bw.nblk, RT, 0, s>>>(w, c->bw.gst, c->V, c->ndof, next, c->bw.sg, 0);
+    k_bgm_store<<<b.nblk, RT, 0, s>>>(w, b.gst, c->V, c->ndof, next, b.sg, 0);
     FR_PROF_END(c, s, KK_VECTOR);
     FR_LAUNCH_CHECK(c);
   }

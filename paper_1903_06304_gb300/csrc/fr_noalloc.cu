@@ -78,11 +78,14 @@ int run(const fr_config* cfg, int nx, int ny, const double* corners, const doubl
   cp.off = 0;
   cp.e0 = 0;
   cp.sn = (int)(ne * NP);
+  cp.nx = nx;
+  cp.ny = ny;
   Mesh M;
   M.nbr = nbr; M.ecase = ecase; M.cp = cpd; M.ne = (int)ne; M.viscous = cp.gas.viscous;
   k_fill_topo<<<(unsigned)((ne + 127) / 128), 128, 0, s>>>(nx, ny, 0, 0, nbr, ecase);
   k_set_case<<<1, 1, 0, s>>>(cpd, 0, cp);
-  k_geometry<N><<<(unsigned)((ne + 63) / 64), 64, 0, s>>>(corners, vel, (int)ne, B, gs, gf);
+  k_geometry<N><<<(unsigned)((ne + 63) / 64), 64, 0, s>>>(corners, vel, (int)ne, B, Buf<double>{gs},
+                                                           Buf<double>{gf});
   const int nblk = (int)((ne + EPB - 1) / EPB);
   k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(q)}, M, B, gs,
                                          Buf<double>{gl}, Buf<double>{tq}, Buf<double>{tg});

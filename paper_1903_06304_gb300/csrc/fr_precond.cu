@@ -383,6 +383,13 @@ static int block_build_n(fr_ctx* c, const double* q, double inv_dtau, double a0_
   return FR_OK;
 }
 
+// Dynamic shared memory of k_factor<W, S> for block size bs.  The function attribute is
+// set to the largest block (p = 4, bs = 100): contexts of several degrees may build
+// blocks concurrently from different threads, and a per-call value would race.
+template <class W>
+static size_t factor_smem(int bs) { return (size_t)bs * bs * sizeof(W) + bs * sizeof(W) + bs * 4 * 2 + bs * 4; }
+constexpr int kMaxBlock = 4 * 5 * 5;
+
 static int factor(fr_ctx* c, cudaStream_t s) {
   const int bs = c->bsz;
   const int nt = 256;
@@ -390,16 +397,19 @@ static int factor(fr_ctx* c, cudaStream_t s) {
   FR_ACCOUNT(c, KK_FACTOR, 2.0 * (double)bs * bs * bs * c->ne, 0.0);
   FR_PROF_BEGIN(c, s);
   if (c->cfg.prec_dtype == FR_PREC_FP64) {
-    const size_t smem = (size_t)bs * bs * 8 + bs * 8 + bs * 4 * 2 + bs * 4;
-    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = factor_smem<double>(bs);
+    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)factor_smem<double>(kMaxBlock)));
     k_factor<double, double><<<c->ne, nt, smem, s>>>(c->B64, bs, (double*)c->Binv, c->Dr, c->Dc, c->info);
   } else if (c->cfg.prec_dtype == FR_PREC_FP32) {
-    const size_t smem = (size_t)bs * bs * 4 + bs * 4 + bs * 4 * 2 + bs * 4;
-    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = factor_smem<float>(bs);
+    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)factor_smem<float>(kMaxBlock)));
     k_factor<float, float><<<c->ne, nt, smem, s>>>(c->B64, bs, (float*)c->Binv, c->Dr, c->Dc, c->info);
   } else {
-    const size_t smem = (size_t)bs * bs * 4 + bs * 4 + bs * 4 * 2 + bs * 4;
-    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<float, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = factor_smem<float>(bs);
+    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<float, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)factor_smem<float>(kMaxBlock)));
     k_factor<float, __nv_bfloat16><<<c->ne, nt, smem, s>>>(c->B64, bs, (__nv_bfloat16*)c->Binv, c->Dr, c->Dc, c->info);
   }
   FR_PROF_END(c, s, KK_FACTOR);

@@ -155,10 +155,10 @@ int geometry(fr_ctx* c, const double* corners, const double* vel, cudaStream_t s
   const int th = 64, nb = (c->ne + th - 1) / th;
   FR_PROF_BEGIN(c, s);
   switch (c->n) {
-    case 2: k_geometry<2><<<nb, th, 0, s>>>(corners, vel, c->ne, c->basis, c->gs, c->gf); break;
-    case 3: k_geometry<3><<<nb, th, 0, s>>>(corners, vel, c->ne, c->basis, c->gs, c->gf); break;
-    case 4: k_geometry<4><<<nb, th, 0, s>>>(corners, vel, c->ne, c->basis, c->gs, c->gf); break;
-    case 5: k_geometry<5><<<nb, th, 0, s>>>(corners, vel, c->ne, c->basis, c->gs, c->gf); break;
+    case 2: k_geometry<2><<<nb, th, 0, s>>>(corners, vel, c->ne, c->basis, Buf<double>{c->gs}, Buf<double>{c->gf}); break;
+    case 3: k_geometry<3><<<nb, th, 0, s>>>(corners, vel, c->ne, c->basis, Buf<double>{c->gs}, Buf<double>{c->gf}); break;
+    case 4: k_geometry<4><<<nb, th, 0, s>>>(corners, vel, c->ne, c->basis, Buf<double>{c->gs}, Buf<double>{c->gf}); break;
+    case 5: k_geometry<5><<<nb, th, 0, s>>>(corners, vel, c->ne, c->basis, Buf<double>{c->gs}, Buf<double>{c->gf}); break;
     default: return FR_ERR_ARG;
   }
   FR_PROF_END(c, s, KK_GEOM);

@@ -42,7 +42,8 @@ class _Config(ctypes.Structure):
                 ("dtau_max", ctypes.c_double), ("r_ser", ctypes.c_double),
                 ("dtau_unsteady", ctypes.c_double), ("gmres_side", ctypes.c_int),
                 ("ser_unsteady", ctypes.c_int), ("dtau0_unsteady", ctypes.c_double),
-                ("line_search", ctypes.c_int), ("jvp_mode", ctypes.c_int)]
+                ("line_search", ctypes.c_int), ("jvp_mode", ctypes.c_int),
+                ("graphs", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -100,6 +101,7 @@ _SIGS = {
     "fr_linearize": (_I, [_P, _P, _D, _D, _P]),
     "fr_apply_linear": (_I, [_P, _P, _P, _I, _P]),
     "fr_vjp": (_I, [_P, _P, _P, _D, _D, _P, _P]),
+    "fr_param_vjp": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_D), _P, _P, _P]),
     "fr_batch_create": (_I, [ctypes.POINTER(_Config), _P, _I, ctypes.POINTER(_P)]),
     "fr_batch_destroy": (None, [_P]),
     "fr_batch_case_info": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
@@ -182,6 +184,7 @@ class Config:
     dtau0_unsteady: float = 0.01
     line_search: int = 0
     jvp_mode: str = "linearized"
+    graphs: int = 1
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -393,6 +396,17 @@ class Solver:
                                     _stream(stream)))
         return out
 
+    def param_vjp(self, q, w, corners, vel, dcorners=None, dvel=None, mach=True, stream=None):
+        """w . dR/dM_inf (returned; None if mach is False), and w . dR/d(corners),
+        w . dR/d(corner velocities) into dcorners / dvel ([Ne, 4, 2] tensors) if given."""
+        dm = ctypes.c_double(0.0)
+        self._check(self.lib.fr_param_vjp(
+            self.ctx, _ptr(q), _ptr(w), _ptr(corners), _ptr(vel),
+            ctypes.byref(dm) if mach else None,
+            _ptr(dcorners) if dcorners is not None else None,
+            _ptr(dvel) if dvel is not None else None, _stream(stream)))
+        return dm.value if mach else None
+
     def precond_build(self, q, inv_dtau=0.0, a0_dt=0.0, stream=None):
         self._check(self.lib.fr_precond_build(self.ctx, _ptr(q), inv_dtau, a0_dt, _stream(stream)))
 
@@ -452,24 +466,46 @@ class Solver:
 
 
 def residual_function():
-    """A torch.autograd.Function computing R(q^p) with a Solver; its backward is the
-    library's reverse-mode product (fr_vjp), dR/dq^T g = -(A^T g) at inv_dtau = a0_dt = 0."""
+    """A torch.autograd.Function computing R(q^p) with a Solver.
+
+    ``Residual.apply(q, solver)``: backward is the library's reverse-mode product
+    (fr_vjp), dR/dq^T g = -(A^T g) at inv_dtau = a0_dt = 0.
+    ``Residual.apply(q, solver, corners, vel, mach)``: the mesh is first set from
+    ``corners``, ``vel`` ([Ne, 4, 2] tensors) and the gradients also flow to them and to
+    ``mach`` (a 0-d tensor equal to the solver's Mach number) through fr_param_vjp."""
     import torch
 
     class Residual(torch.autograd.Function):
         @staticmethod
-        def forward(ctx, q, solver):
+        def forward(ctx, q, solver, corners=None, vel=None, mach=None):
+            if corners is not None:
+                solver.update_mesh(corners.contiguous(), vel.contiguous())
+            if mach is not None and abs(float(mach) - solver.cfg.mach) > 1e-15 * solver.cfg.mach:
+                raise ValueError("mach must equal the solver's Mach number")
             out = torch.empty_like(q)
             solver.residual(q.contiguous(), out)
-            ctx.save_for_backward(q)
+            ctx.save_for_backward(q, corners, vel)
             ctx.solver = solver
+            ctx.has_mach = mach is not None
             return out
 
         @staticmethod
         def backward(ctx, grad):
-            (q,) = ctx.saved_tensors
+            q, corners, vel = ctx.saved_tensors
+            g = grad.contiguous()
             out = torch.empty_like(q)
-            ctx.solver.vjp(q.contiguous(), grad.contiguous(), out, 0.0, 0.0)
-            return -out, None
+            ctx.solver.vjp(q.contiguous(), g, out, 0.0, 0.0)
+            gc = gv = gm = None
+            if corners is not None:
+                need_c, need_v = ctx.needs_input_grad[2], ctx.needs_input_grad[3]
+                gc = torch.empty_like(corners) if need_c else None
+                gv = torch.empty_like(vel) if need_v else None
+                want_m = ctx.has_mach and ctx.needs_input_grad[4]
+                if need_c or need_v or want_m:
+                    dm = ctx.solver.param_vjp(q.contiguous(), g, corners.contiguous(),
+                                              vel.contiguous(), gc, gv, mach=want_m)
+                    if want_m:
+                        gm = torch.tensor(dm, dtype=q.dtype, device=q.device)
+            return -out, None, gc, gv, gm
 
     return Residual
