@@ -163,6 +163,53 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def large_n_sweep(sizes, torch, fr, inp, flush):
+    """Residual, dual and linearized JVP and VJP throughput on the benchmark geometry
+    scaled to n x n elements (inputs far beyond L2): median of 10 calls each, with the
+    FP64 rate from the library's algorithmic flop counts."""
+    import numpy as np
+    out = {}
+    base = inp.NS_VORTEX_64
+    for n in sizes:
+        w = inp.Workload(f"vortex_{n}", n, n, base.p, base.mach, base.re, base.kappa, base.box,
+                         ic="vortex", dt=base.dt)
+        c, v, q = inp.make_case(w)
+        T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda:0")
+        S = fr.Solver(fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa), n, n)
+        S.update_mesh(T(c), T(v))
+        qd = T(q)
+        del c, v, q
+        vec = torch.randn_like(qd)
+        o = torch.empty_like(qd)
+        S.linearize(qd, 1e-20, 1.5 / w.dt)
+        res = {"dof": S.ndof}
+        for name, fn in (("residual", lambda: S.residual(qd, o)),
+                         ("jvp_dual", lambda: S.jvp(qd, vec, o, 1e-20, 1.5 / w.dt)),
+                         ("jvp_linearized", lambda: S.apply_linear(vec, o)),
+                         ("vjp", lambda: S.apply_linear(vec, o, transpose=True))):
+            fn()
+            torch.cuda.synchronize()
+            S.profile_read(reset=True)
+            ts = []
+            for _ in range(10):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                ts.append((a, b))
+            torch.cuda.synchronize()
+            flops = sum(x["flops"] for x in S.profile_read(reset=True).values()) / 10
+            t = statistics.median(a.elapsed_time(b) for a, b in ts) * 1e-3
+            res[name] = {"gdofs": S.ndof / t / 1e9, "ms": t * 1e3,
+                         "fp64_tflops": flops / t / 1e12, "fp64_frac": flops / t / 1e12 / FP64_PEAK_TFLOPS}
+        out[f"{n}x{n}"] = res
+        S.close()
+        del qd, vec, o
+        torch.cuda.empty_cache()
+    return out
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -193,7 +240,8 @@ def gpu_arm(args):
         cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=prec,
                         restart=args.restart, maxit_lin=args.maxit_lin, tol_res=w.tol_res,
                         tol_pseudo=w.tol_pseudo, maxit_newton=args.maxit_newton, lag=2,
-                        line_search=args.line_search, graphs=args.graphs)
+                        line_search=args.line_search, graphs=args.graphs,
+                        apply_accum=args.apply_accum)
         S = fr.Solver(cfg, w.nx, w.ny)
         S.update_mesh(T(corners), T(vel))
         return S
@@ -291,28 +339,48 @@ def gpu_arm(args):
     out = torch.empty_like(run.q)
     vec = torch.randn_like(run.q)
 
-    def time_calls(fn, reps=20):
+    def time_calls(fn, reps=50, flush_between=False):
+        """Median device time of one call (CUDA events around each call), after 3 calls
+        of warm-up; with flush_between the 256 MiB buffer is rewritten before each call."""
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
+        evs = []
         for _ in range(reps):
+            if flush_between:
+                flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
             fn()
-        b.record()
+            b.record()
+            evs.append((a, b))
         torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
+        return statistics.median(a.elapsed_time(b) for a, b in evs)
 
-    t_res = time_calls(lambda: S.residual(run.q, out))
-    t_jvp = time_calls(lambda: S.jvp(run.q, vec, out, 1e-20, 1.5 / w.dt))
+    calls = {
+        "residual": lambda: S.residual(run.q, out),
+        "jvp_dual": lambda: S.jvp(run.q, vec, out, 1e-20, 1.5 / w.dt),
+        "jvp_linearized": lambda: S.apply_linear(vec, out),
+        "vjp": lambda: S.apply_linear(vec, out, transpose=True),
+    }
+    S.linearize(run.q, 1e-20, 1.5 / w.dt)
+    call_gdofs = {}
+    for name, fn in calls.items():
+        warm = time_calls(fn)
+        cold = time_calls(fn, flush_between=True)
+        call_gdofs[name] = {"warm_l2": dof / (warm * 1e-3) / 1e9,
+                            "flushed_l2": dof / (cold * 1e-3) / 1e9, "median_of": 50}
     t_lin = time_calls(lambda: S.linearize(run.q, 1e-20, 1.5 / w.dt), reps=5)
-    t_app = time_calls(lambda: S.apply_linear(vec, out))
-    t_vjp = time_calls(lambda: S.apply_linear(vec, out, transpose=True))
+
+    sweep = None
+    if rank == 0 and not args.no_sweep:
+        sweep = large_n_sweep(args.sweep, torch, fr, inp, flush)
 
     # ---- GMRES iteration cost at the final state: a fixed count (tol_res 1e-30), so the
     # per-iteration time does not depend on the Newton history
     gm_cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
-                       restart=args.restart, maxit_lin=120, tol_res=1e-30, graphs=args.graphs)
+                       restart=args.restart, maxit_lin=120, tol_res=1e-30, graphs=args.graphs,
+                       apply_accum=args.apply_accum)
     Sg = fr.Solver(gm_cfg, w.nx, w.ny)
     Sg.update_mesh(T(corners), T(vel))
     Sg.precond_build(run.q, 1e-20, 1.5 / w.dt)
@@ -329,9 +397,13 @@ def gpu_arm(args):
     us_per_gmres_it = 1e3 * ga.elapsed_time(gb) / its_g
     Sg.close()
 
-    # ---- precision comparison: a few steps from the same state per block precision
+    # ---- precision comparison: the same steps from the same state per block precision;
+    # the final state of each against the FP64-block run (max over entries, relative to
+    # the per-variable magnitude of the state change)
     compare = {}
     if not args.no_compare:
+        finals = {}
+        q_start = run.q.clone()
         for prec in ("fp64", "fp32", "bf16"):
             S2 = make_solver(prec)
             r2 = Run(S2)
@@ -340,12 +412,17 @@ def gpu_arm(args):
             r2.qc_nm1.copy_(run.qc_nm1)
             r2.k = run.k
             ms2, st2, _ = timed_steps(r2, max(2, min(args.steps, 3)))
+            finals[prec] = r2.q.clone()
             compare[prec] = {"sec_per_step": statistics.mean(ms2) / 1e3,
                              "newton": [s["newton_iterations"] for s in st2],
                              "gmres_total": [sum(s["gmres_iterations"]) for s in st2],
-                             "converged": all(s["converged"] for s in st2),
-                             "state_diff_vs_headline": None}
+                             "converged": all(s["converged"] for s in st2)}
             S2.close()
+        nvar = 4
+        dq = (finals["fp64"] - q_start).view(nvar, -1).abs().amax(dim=1)
+        for prec in compare:
+            diff = (finals[prec] - finals["fp64"]).view(nvar, -1).abs().amax(dim=1)
+            compare[prec]["state_diff_vs_fp64"] = float((diff / dq).max())
 
     # ---- end-to-end through host buffers
     e2e = None
@@ -405,7 +482,7 @@ def gpu_arm(args):
                    "dt": w.dt, "tol_pseudo": w.tol_pseudo, "tol_res": w.tol_res,
                    "gmres": f"GMRES({args.restart}) left-preconditioned, maxit {args.maxit_lin}",
                    "newton": f"max {args.maxit_newton} iterations, backtracking {args.line_search} halvings",
-                   "precond": f"element block-Jacobi, {args.prec} blocks",
+                   "precond": f"element block-Jacobi, {args.prec} blocks, {args.apply_accum} apply accumulation",
                    "l2": "256 MiB write between timed steps, outside the per-step events",
                    "parallelism": "replicas" if world > 1 else "single"},
         "startup_steps": args.startup,
@@ -414,10 +491,12 @@ def gpu_arm(args):
         "newton_iterations": [s["newton_iterations"] for s in stats],
         "gmres_iterations_per_step": [sum(s["gmres_iterations"]) for s in stats],
         "res_drop_last": last["res_history"][-1] / last["res_history"][0],
-        "residual_gdofs": dof / (t_res * 1e-3) / 1e9,
-        "jvp_gdofs": dof / (t_jvp * 1e-3) / 1e9,
-        "linearized_jvp_gdofs": dof / (t_app * 1e-3) / 1e9,
-        "vjp_gdofs": dof / (t_vjp * 1e-3) / 1e9,
+        "residual_gdofs": call_gdofs["residual"]["warm_l2"],
+        "jvp_gdofs": call_gdofs["jvp_dual"]["warm_l2"],
+        "linearized_jvp_gdofs": call_gdofs["jvp_linearized"]["warm_l2"],
+        "vjp_gdofs": call_gdofs["vjp"]["warm_l2"],
+        "call_gdofs": call_gdofs,
+        "large_n_sweep": sweep,
         "linearize_ms": t_lin,
         "us_per_gmres_iteration": us_per_gmres_it,
         "precision_compare": compare,
@@ -479,7 +558,7 @@ def batch_arm(args):
     cases = [fr.Case(c.p, c.n, c.n, c.mach, c.re, c.kappa) for c in cs]
     cfg = fr.Config(prec=args.prec, restart=args.restart, maxit_lin=args.maxit_lin,
                     maxit_newton=args.maxit_newton, lag=2, line_search=args.line_search,
-                    graphs=args.graphs)
+                    graphs=args.graphs, apply_accum=args.apply_accum)
     B = fr.Batch(cfg, cases)
     corners = np.zeros((B.ne, 4, 2))
     q = np.zeros(B.ndof)
@@ -557,9 +636,14 @@ def main():
     ap.add_argument("--maxit-newton", dest="maxit_newton", type=int, default=40)
     ap.add_argument("--line-search", dest="line_search", type=int, default=4,
                     help="backtracking halvings per Newton update (0: plain Newton)")
+    ap.add_argument("--apply-accum", dest="apply_accum", default="df64", choices=["df64", "fp32"],
+                    help="block-apply arithmetic with FP32/BF16-stored inverses")
     ap.add_argument("--graphs", type=int, default=1,
                     help="replay GMRES chunks from captured CUDA graphs (1) or launch each kernel (0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep", type=lambda t: [int(x) for x in t.split(",")], default=[256, 512, 1024],
+                    help="mesh sides of the large-N kernel throughput sweep")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--batch-cases", dest="batch_cases", type=int, default=0,

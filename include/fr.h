@@ -74,6 +74,12 @@ typedef struct fr_ctx fr_ctx;
  * gmres_side: FR_GMRES_LEFT (PETSc's default, the paper's solver: Krylov space of B^-1 A,
  * tol_res relative to ||B^-1 b||) or FR_GMRES_RIGHT (Krylov space of A B^-1, tol_res
  * relative to ||b||);
+ * apply_accum: arithmetic of the block apply with FP32/BF16-stored inverses:
+ * FR_ACCUM_DF64 (default) carries the input and the sums as FP32 pairs with error-free
+ * transformations (about 2^-44 relative), so the preconditioner is linear to near FP64
+ * round-off while it runs on the FP32 pipe; FR_ACCUM_FP32 rounds the input and
+ * accumulates in plain FP32 (a state-dependent perturbation with which GMRES can stall
+ * on stiff cases);
  * graphs: if nonzero (default) and restart <= 32, GMRES iterations are issued in chunks of
  * up to 10 whose kernel launches are captured once into a CUDA graph and replayed (same
  * results; fewer launch overheads); ignored while fr_profile timing is on. */
@@ -82,6 +88,8 @@ typedef struct fr_ctx fr_ctx;
 #define FR_JVP_LINEARIZED 1
 #define FR_GMRES_LEFT 0
 #define FR_GMRES_RIGHT 1
+#define FR_ACCUM_FP32 0
+#define FR_ACCUM_DF64 1
 typedef struct fr_config {
   int p;
   double gamma, prandtl, mach, re, kappa, eps_floor;
@@ -95,6 +103,7 @@ typedef struct fr_config {
   int line_search;
   int jvp_mode;
   int graphs;
+  int apply_accum;
 } fr_config;
 
 /* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).

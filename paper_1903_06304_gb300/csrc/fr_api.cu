@@ -524,6 +524,7 @@ void fr_default_config(fr_config* c) {
   c->line_search = 0;
   c->jvp_mode = FR_JVP_LINEARIZED;
   c->graphs = 1;
+  c->apply_accum = FR_ACCUM_DF64;
 }
 
 int fr_create(const fr_config* cfg, fr_ctx** out) {
@@ -532,7 +533,8 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
   if (cfg->p < 1 || cfg->p > 4 || cfg->mach <= 0 || cfg->gamma <= 1.0 || cfg->restart < 1 ||
       cfg->restart > FR_MAX_RESTART || cfg->prec_dtype < 0 || cfg->prec_dtype > 2 ||
       (cfg->gmres_side != FR_GMRES_LEFT && cfg->gmres_side != FR_GMRES_RIGHT) ||
-      (cfg->jvp_mode != FR_JVP_DUAL && cfg->jvp_mode != FR_JVP_LINEARIZED))
+      (cfg->jvp_mode != FR_JVP_DUAL && cfg->jvp_mode != FR_JVP_LINEARIZED) ||
+      (cfg->apply_accum != FR_ACCUM_FP32 && cfg->apply_accum != FR_ACCUM_DF64))
     return FR_ERR_ARG;
   fr_ctx* c = new fr_ctx();
   c->cfg = *cfg;
@@ -550,6 +552,7 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
   c->cp_h.off = 0;
   c->cp_h.e0 = 0;
   c->cp_h.sn = 0;
+  c->cp_h.active = 1;
   if (cudaMalloc((void**)&c->dsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&c->hsc, (4 * FR_MAX_RESTART + 8) * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&c->cp, sizeof(fr::CaseParams)) != cudaSuccess) {

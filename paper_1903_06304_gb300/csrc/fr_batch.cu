@@ -176,10 +176,15 @@ int gmres_cases(fr_ctx* c, const double* q, const double* b, double* x, double i
       if (cyc[k]) total[k] += c->bw.status_h[k].x;
     FR_TRY(frk::bk_finish(c, c->w_u, s));
     if (left) {
-      FR_TRY(frk::axpby(c, 1.0, c->w_u, 1.0, x, s));
+      FR_TRY(frk::axpby(c, 1.0, c->w_u, 1.0, x, s));   // u = 0 for cases that did not iterate
     } else {
+      // B^-1 u, added only for the cases that iterated (the block apply skips the elements
+      // of stopped cases, whose entries of w_z are stale)
       FR_TRY(frk::block_apply(c, c->w_u, c->w_z, s));
-      FR_TRY(frk::axpby(c, 1.0, c->w_z, 1.0, x, s));
+      std::vector<double> one(nc);
+      for (int k = 0; k < nc; ++k) one[k] = cyc[k] ? 1.0 : 0.0;
+      FR_TRY(upload_coef(c, one, s));
+      FR_TRY(frk::bk_axpy_case(c, c->bw.coef, c->w_z, x, s));
     }
     FR_TRY(op_apply(c, q, x, inv_dtau, a0_dt, c->w_t, s));
     FR_TRY(frk::axpby(c, 1.0, b, -1.0, c->w_t, s));
@@ -230,8 +235,18 @@ int batch_newton(fr_ctx* c, double* q, const double* qcn, const double* qcnm1,
     }
     p.inv_dtau = 0.0;
     p.a0_dt = a0dt[k];
+    p.active = 1;
   }
   FR_TRY(frk::upload_cases(c, s));
+  // every case active again on return, whatever the exit path
+  struct Restore {
+    fr_ctx* c;
+    cudaStream_t s;
+    ~Restore() {
+      for (fr::CaseParams& p : c->cps) p.active = 1;
+      frk::upload_cases(c, s);
+    }
+  } restore{c, s};
   auto rhs = [&](double* out) -> int {
     if (steady) return frk::residual(c, q, out, nullptr, nullptr, 0, 0, 0, s);
     return frk::residual(c, q, out, qcn, any_bdf2 ? qcnm1 : nullptr, 0, 0, 0, s);
@@ -263,6 +278,7 @@ int batch_newton(fr_ctx* c, double* q, const double* qcn, const double* qcnm1,
     for (int k = 0; k < nc; ++k) {
       c->cps[k].inv_dtau = 1.0 / dtau[k];
       c->cps[k].a0_dt = a0dt[k];
+      c->cps[k].active = active[k];   // the kernels skip the elements of stopped cases
     }
     FR_TRY(frk::upload_cases(c, s));
     if (ser || m % std::max(1, cfg.lag) == 0) {
@@ -432,6 +448,7 @@ int fr_batch_create(const fr_config* cfg, const fr_case* cases, int ncases, fr_b
       fr::CaseParams cp;
       std::memset(&cp, 0, sizeof(cp));
       cp.gas = fr_make_gas(ck);
+      cp.active = 1;
       params.push_back(cp);
     }
     fr_config gc = *cfg;

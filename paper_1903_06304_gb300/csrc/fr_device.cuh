@@ -55,6 +55,7 @@ struct CaseParams {
   long long off;
   int e0, sn;
   int nx, ny;   // the case's periodic box: element e0 + j nx + i is at column i, row j
+  int active;   // 0: the Newton loop of this case has stopped; its elements are skipped
 };
 
 // Element topology of one launch: face neighbours (L, R, B, T) by global element index,
@@ -71,6 +72,7 @@ struct Mesh {
   __device__ __forceinline__ int bottom(int e) const { return nbr[4 * e + FACE_B]; }
   __device__ __forceinline__ int top(int e) const { return nbr[4 * e + FACE_T]; }
   __device__ __forceinline__ const CaseParams& par(int e) const { return cp[ecase[e]]; }
+  __device__ __forceinline__ bool on(int e) const { return cp[ecase[e]].active != 0; }
   // index of variable 0 at point 0 of element e in a state vector, and the stride
   // between the variables of e's case
   __device__ __forceinline__ size_t qbase(int e, int np) const {

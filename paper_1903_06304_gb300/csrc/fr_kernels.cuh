@@ -138,7 +138,7 @@ k_trace(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs, Buf<T> GL, Buf
   __shared__ T sg[EPB][8][NP];
   const int le = threadIdx.x / NP, pt = threadIdx.x % NP;
   const int e = blockIdx.x * EPB + le;
-  const bool live = (le < EPB) && (e < ne);
+  const bool live = (le < EPB) && (e < ne) && M.on(e);
   const int i = pt % N, j = pt / N;
   const size_t SN = (size_t)ne * NP;
   const size_t o = (size_t)e * NP + pt;
@@ -206,6 +206,7 @@ __global__ void k_face(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= M.ne * 2 * N) return;
   const int e = idx / (2 * N), rem = idx % (2 * N), dir = rem / N, t = rem % N;
+  if (!M.on(e)) return;
   const int plus = dir == 0 ? M.right(e) : M.top(e);
   const int fm = dir == 0 ? FACE_R : FACE_T, fp = dir == 0 ? FACE_L : FACE_B;
   typename GasOf<G>::type gas = gas_for<G>(M.par(e).gas, dmach);
@@ -285,7 +286,7 @@ k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
   __shared__ T sG[EPB][4][NP];
   const int le = threadIdx.x / NP, pt = threadIdx.x % NP;
   const int e = blockIdx.x * EPB + le;
-  const bool live = (le < EPB) && (e < M.ne);
+  const bool live = (le < EPB) && (e < M.ne) && M.on(e);
   const int i = pt % N, j = pt / N;
   const size_t SN = (size_t)M.ne * NP;
   const size_t FNs = (size_t)M.ne * 4 * N;

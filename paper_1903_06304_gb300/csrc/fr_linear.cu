@@ -30,6 +30,7 @@ __global__ void k_lin_face(Mesh M, Basis B, const double* __restrict__ gf,
   const int nf = M.ne * 2 * N;
   if (idx >= nf) return;
   const int e = idx / (2 * N), rem = idx % (2 * N), dir = rem / N, t = rem % N;
+  if (!M.on(e)) return;
   const int plus = dir == 0 ? M.right(e) : M.top(e);
   const int fm = dir == 0 ? FACE_R : FACE_T, fp = dir == 0 ? FACE_L : FACE_B;
   const Gas& gas = M.par(e).gas;
@@ -85,7 +86,7 @@ k_lin_point(const double* __restrict__ q, Mesh M, Basis B, const double* __restr
   constexpr int NP = N * N, EPB = Tile<N>::EPB;
   const int le = threadIdx.x / NP, pt = threadIdx.x % NP;
   const int e = blockIdx.x * EPB + le;
-  if (le >= EPB || e >= M.ne) return;
+  if (le >= EPB || e >= M.ne || !M.on(e)) return;
   const int i = pt % N, j = pt / N;
   const size_t SN = (size_t)M.ne * NP;
   const size_t FNs = (size_t)M.ne * 4 * N;
@@ -182,6 +183,7 @@ __global__ void k_lin_face_apply(Mesh M, const double* __restrict__ tqv,
   const int nf = M.ne * 2 * N;
   if (idx >= nf) return;
   const int e = idx / (2 * N), rem = idx % (2 * N), dir = rem / N, t = rem % N;
+  if (!M.on(e)) return;
   const int plus = dir == 0 ? M.right(e) : M.top(e);
   const int fm = dir == 0 ? FACE_R : FACE_T, fp = dir == 0 ? FACE_L : FACE_B;
   double x[8];
@@ -236,7 +238,7 @@ k_lin_elem_apply(const double* __restrict__ v, Mesh M, Basis B,
   __shared__ double sG[EPB][4][NP];
   const int le = threadIdx.x / NP, pt = threadIdx.x % NP;
   const int e = blockIdx.x * EPB + le;
-  const bool live = (le < EPB) && (e < M.ne);
+  const bool live = (le < EPB) && (e < M.ne) && M.on(e);
   const int i = pt % N, j = pt / N;
   const size_t SN = (size_t)M.ne * NP;
   const size_t FNs = (size_t)M.ne * 4 * N;

@@ -80,6 +80,7 @@ int run(const fr_config* cfg, int nx, int ny, const double* corners, const doubl
   cp.sn = (int)(ne * NP);
   cp.nx = nx;
   cp.ny = ny;
+  cp.active = 1;
   Mesh M;
   M.nbr = nbr; M.ecase = ecase; M.cp = cpd; M.ne = (int)ne; M.viscous = cp.gas.viscous;
   k_fill_topo<<<(unsigned)((ne + 127) / 128), 128, 0, s>>>(nx, ny, 0, 0, nbr, ecase);

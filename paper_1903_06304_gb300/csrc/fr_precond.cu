@@ -32,6 +32,7 @@ k_block(const double* __restrict__ q, Mesh M, Basis B, const double* __restrict_
   using L = BlkSmem<N>;
   extern __shared__ Dual smem_dual[];
   const int e = blockIdx.x;
+  if (!M.on(e)) return;
   const int grp = threadIdx.x / NP, pt = threadIdx.x % NP;
   const int i = pt % N, j = pt / N;
   Dual* S = smem_dual + grp * L::SIZE;
@@ -214,7 +215,8 @@ template <class W> __device__ __forceinline__ W wabs(W x) { return x < 0 ? -x : 
 // one CTA per element; writes the transposed scaled inverse and the scales.
 template <class W, class S>
 __global__ void k_factor(const double* __restrict__ Bin, int bs, S* __restrict__ Aout,
-                         float* __restrict__ Dr, float* __restrict__ Dc, int* __restrict__ info) {
+                         float* __restrict__ Dr, float* __restrict__ Dc, int* __restrict__ info,
+                         Mesh M) {
   extern __shared__ unsigned char smraw[];
   W* A = reinterpret_cast<W*>(smraw);               // [bs][bs] row-major
   W* col = A + bs * bs;                             // [bs]
@@ -224,6 +226,7 @@ __global__ void k_factor(const double* __restrict__ Bin, int bs, S* __restrict__
   __shared__ int s_piv;
   __shared__ int s_bad;
   const int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  if (!M.on(e)) return;
   const double* Be = Bin + (size_t)e * bs * bs;
   if (tid == 0) s_bad = 0;
   // row scales: 2^-round(log2(max |B_ij|)) over the row
@@ -303,46 +306,109 @@ __global__ void k_factor(const double* __restrict__ Bin, int bs, S* __restrict__
 template <class S> __device__ __forceinline__ float to_f(S x) { return (float)x; }
 template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
 
-// z_e = Dc (A^T_stored (Dr r_e)); one CTA per element, thread per row.
-template <class S, class Acc>
-__global__ void k_apply(const S* __restrict__ AT, const float* __restrict__ Dr,
-                        const float* __restrict__ Dc, const double* __restrict__ r, Mesh M,
-                        int np2, double* __restrict__ z) {
-  extern __shared__ unsigned char smraw[];
-  Acc* x = reinterpret_cast<Acc*>(smraw);
-  const int e = blockIdx.x, bs = 4 * np2, row = threadIdx.x;
-  const size_t qo = M.qbase(e, np2), qs = M.qstride(e);
-  if (row < bs) {
-    const int v = row / np2, pt = row % np2;
-    x[row] = (Acc)(r[v * qs + qo + pt] * (double)Dr[(size_t)e * bs + row]);
-  }
-  __syncthreads();
-  if (row >= bs) return;
-  const S* A = AT + (size_t)e * bs * bs;
-  Acc acc = 0;
-  for (int c2 = 0; c2 < bs; ++c2) acc += (Acc)to_f(A[(size_t)c2 * bs + row]) * x[c2];
-  const int v = row / np2, pt = row % np2;
-  z[v * qs + qo + pt] = (double)acc * (double)Dc[(size_t)e * bs + row];
+// z_e = Dc (A^T_stored (Dr r_e)) with four threads per row: thread (part, row) sums the
+// columns c = part, part + 4, ... (consecutive rows of one column are adjacent in the
+// transposed store: coalesced), two partial sums each; the four parts meet in shared
+// memory.  ACC: 0 FP64, 1 FP32, 2 double-float (FP32 pairs with error-free
+// transformations, linear to about 2^-44 of the summed magnitudes).
+constexpr int APPLY_PARTS = 4;
+
+__device__ __forceinline__ void df_add(float& sh, float& sl, float a, float2 xv) {
+  const float ph = a * xv.x;
+  float pl = fmaf(a, xv.x, -ph);   // exact low part of a x_hi
+  pl = fmaf(a, xv.y, pl);           // + a x_lo
+  const float sn = sh + ph;         // two-sum
+  const float bv = sn - sh;
+  const float er = (sh - (sn - bv)) + (ph - bv);
+  sh = sn;
+  sl += er + pl;
 }
-template <>
-__global__ void k_apply<double, double>(const double* __restrict__ AT, const float* __restrict__ Dr,
-                                        const float* __restrict__ Dc, const double* __restrict__ r,
-                                        Mesh M, int np2, double* __restrict__ z) {
-  extern __shared__ unsigned char smraw[];
-  double* x = reinterpret_cast<double*>(smraw);
-  const int e = blockIdx.x, bs = 4 * np2, row = threadIdx.x;
-  const size_t qo = M.qbase(e, np2), qs = M.qstride(e);
-  if (row < bs) {
-    const int v = row / np2, pt = row % np2;
-    x[row] = r[v * qs + qo + pt] * (double)Dr[(size_t)e * bs + row];
+
+template <class S, int ACC, int N>
+__global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
+                         const float* __restrict__ Dc, const double* __restrict__ r, Mesh M,
+                         double* __restrict__ z) {
+  constexpr int NP = N * N, BS = 4 * NP, BSR = (BS + 31) / 32 * 32;
+  constexpr int COLS = (BS + APPLY_PARTS - 1) / APPLY_PARTS;   // columns per thread
+  __shared__ double xd[ACC == 0 ? BS : 1];
+  __shared__ float xf[ACC == 1 ? BS : 1];
+  __shared__ float2 x2[ACC == 2 ? BS : 1];
+  __shared__ double pd[APPLY_PARTS][BSR];
+  __shared__ float pf[ACC == 1 ? APPLY_PARTS : 1][BSR];
+  const int e = blockIdx.x;
+  if (!M.on(e)) return;
+  const int part = threadIdx.x / BSR, row = threadIdx.x % BSR;
+  const S* A = AT + (size_t)e * BS * BS;
+  // every load of this thread's columns issued before any arithmetic
+  S av[COLS];
+#pragma unroll
+  for (int k = 0; k < COLS; ++k) {
+    const int c2 = part + APPLY_PARTS * k;
+    av[k] = (row < BS && c2 < BS) ? A[(size_t)c2 * BS + row] : S(0.0f);
+  }
+  const size_t qo = M.qbase(e, NP), qs = M.qstride(e);
+  for (int t = threadIdx.x; t < BS; t += blockDim.x) {
+    const int v = t / NP, pt = t % NP;
+    const double u = r[v * qs + qo + pt] * (double)Dr[(size_t)e * BS + t];
+    if (ACC == 0) xd[t] = u;
+    else if (ACC == 1) xf[t] = (float)u;
+    else {
+      const float hi = __double2float_rn(u);
+      x2[t] = make_float2(hi, __double2float_rn(u - (double)hi));
+    }
   }
   __syncthreads();
-  if (row >= bs) return;
-  const double* A = AT + (size_t)e * bs * bs;
-  double acc = 0;
-  for (int c2 = 0; c2 < bs; ++c2) acc = fma(A[(size_t)c2 * bs + row], x[c2], acc);
-  const int v = row / np2, pt = row % np2;
-  z[v * qs + qo + pt] = acc * (double)Dc[(size_t)e * bs + row];
+  if (row < BS) {
+    if (ACC == 0) {
+      double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) {
+        const int c2 = part + APPLY_PARTS * k;
+        if (c2 < BS) {
+          if (k & 1) a1 = fma((double)av[k], xd[c2], a1);
+          else a0 = fma((double)av[k], xd[c2], a0);
+        }
+      }
+      pd[part][row] = a0 + a1;
+    } else if (ACC == 1) {
+      float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) {
+        const int c2 = part + APPLY_PARTS * k;
+        if (c2 < BS) {
+          if (k & 1) a1 = fmaf(to_f(av[k]), xf[c2], a1);
+          else a0 = fmaf(to_f(av[k]), xf[c2], a0);
+        }
+      }
+      pf[part][row] = a0 + a1;
+    } else {
+      float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+#pragma unroll
+      for (int k = 0; k < COLS; ++k) {
+        const int c2 = part + APPLY_PARTS * k;
+        if (c2 < BS) {
+          if (k & 1) df_add(h1, l1, to_f(av[k]), x2[c2]);
+          else df_add(h0, l0, to_f(av[k]), x2[c2]);
+        }
+      }
+      pd[part][row] = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
+    }
+  }
+  __syncthreads();
+  if (part != 0 || row >= BS) return;
+  double acc;
+  if (ACC == 1) {
+    float t = pf[0][row];
+#pragma unroll
+    for (int q = 1; q < APPLY_PARTS; ++q) t += pf[q][row];
+    acc = (double)t;
+  } else {
+    acc = pd[0][row];
+#pragma unroll
+    for (int q = 1; q < APPLY_PARTS; ++q) acc += pd[q][row];
+  }
+  const int v = row / NP, pt = row % NP;
+  z[v * qs + qo + pt] = acc * (double)Dc[(size_t)e * BS + row];
 }
 
 }  // namespace fr
@@ -400,17 +466,17 @@ static int factor(fr_ctx* c, cudaStream_t s) {
     const size_t smem = factor_smem<double>(bs);
     FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)factor_smem<double>(kMaxBlock)));
-    k_factor<double, double><<<c->ne, nt, smem, s>>>(c->B64, bs, (double*)c->Binv, c->Dr, c->Dc, c->info);
+    k_factor<double, double><<<c->ne, nt, smem, s>>>(c->B64, bs, (double*)c->Binv, c->Dr, c->Dc, c->info, c->mesh);
   } else if (c->cfg.prec_dtype == FR_PREC_FP32) {
     const size_t smem = factor_smem<float>(bs);
     FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)factor_smem<float>(kMaxBlock)));
-    k_factor<float, float><<<c->ne, nt, smem, s>>>(c->B64, bs, (float*)c->Binv, c->Dr, c->Dc, c->info);
+    k_factor<float, float><<<c->ne, nt, smem, s>>>(c->B64, bs, (float*)c->Binv, c->Dr, c->Dc, c->info, c->mesh);
   } else {
     const size_t smem = factor_smem<float>(bs);
     FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<float, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)factor_smem<float>(kMaxBlock)));
-    k_factor<float, __nv_bfloat16><<<c->ne, nt, smem, s>>>(c->B64, bs, (__nv_bfloat16*)c->Binv, c->Dr, c->Dc, c->info);
+    k_factor<float, __nv_bfloat16><<<c->ne, nt, smem, s>>>(c->B64, bs, (__nv_bfloat16*)c->Binv, c->Dr, c->Dc, c->info, c->mesh);
   }
   FR_PROF_END(c, s, KK_FACTOR);
   FR_LAUNCH_CHECK(c);
@@ -432,17 +498,32 @@ int block_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaS
 
 int block_apply(fr_ctx* c, const double* r, double* z, cudaStream_t s) {
   const int bs = c->bsz;
-  const int nt = (bs + 31) / 32 * 32;
   const double esz = c->cfg.prec_dtype == FR_PREC_FP64 ? 8.0 : c->cfg.prec_dtype == FR_PREC_FP32 ? 4.0 : 2.0;
   FR_ACCOUNT(c, KK_APPLY, 2.0 * (double)bs * bs * c->ne,
              c->ne * ((double)bs * bs * esz + 2.0 * bs * 4.0) + 2.0 * 8.0 * c->ndof);
   FR_PROF_BEGIN(c, s);
-  if (c->cfg.prec_dtype == FR_PREC_FP64)
-    k_apply<double, double><<<c->ne, nt, bs * 8, s>>>((const double*)c->Binv, c->Dr, c->Dc, r, c->mesh, c->np2, z);
-  else if (c->cfg.prec_dtype == FR_PREC_FP32)
-    k_apply<float, float><<<c->ne, nt, bs * 4, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, c->np2, z);
-  else
-    k_apply<__nv_bfloat16, float><<<c->ne, nt, bs * 4, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, c->np2, z);
+  // Double-float accumulation keeps the preconditioner linear to near FP64 round-off (the
+  // stored inverse rounded once); plain FP32 accumulation also rounds the input and every
+  // partial sum, a state-dependent perturbation that left-preconditioned GMRES cannot get
+  // below on stiff cases
+  const bool df = c->cfg.apply_accum == FR_ACCUM_DF64;
+  const int nt4 = APPLY_PARTS * ((bs + 31) / 32 * 32);
+  const int acc = c->cfg.prec_dtype == FR_PREC_FP64 ? 0 : df ? 2 : 1;
+  switch (c->n * 10 + acc) {
+#define FR_APPLY_CASE(NN)                                                                      \
+    case NN * 10 + 0: k_apply4<double, 0, NN><<<c->ne, nt4, 0, s>>>((const double*)c->Binv, c->Dr, c->Dc, r, c->mesh, z); break; \
+    case NN * 10 + 1: if (c->cfg.prec_dtype == FR_PREC_FP32)                                  \
+        k_apply4<float, 1, NN><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z); \
+      else k_apply4<__nv_bfloat16, 1, NN><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z); \
+      break;                                                                                   \
+    case NN * 10 + 2: if (c->cfg.prec_dtype == FR_PREC_FP32)                                  \
+        k_apply4<float, 2, NN><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z); \
+      else k_apply4<__nv_bfloat16, 2, NN><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z); \
+      break;
+    FR_APPLY_CASE(2) FR_APPLY_CASE(3) FR_APPLY_CASE(4) FR_APPLY_CASE(5)
+#undef FR_APPLY_CASE
+    default: return FR_ERR_ARG;
+  }
   FR_PROF_END(c, s, KK_APPLY);
   FR_LAUNCH_CHECK(c);
   return FR_OK;

@@ -43,7 +43,7 @@ class _Config(ctypes.Structure):
                 ("dtau_unsteady", ctypes.c_double), ("gmres_side", ctypes.c_int),
                 ("ser_unsteady", ctypes.c_int), ("dtau0_unsteady", ctypes.c_double),
                 ("line_search", ctypes.c_int), ("jvp_mode", ctypes.c_int),
-                ("graphs", ctypes.c_int)]
+                ("graphs", ctypes.c_int), ("apply_accum", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -185,6 +185,7 @@ class Config:
     line_search: int = 0
     jvp_mode: str = "linearized"
     graphs: int = 1
+    apply_accum: str = "df64"
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -196,6 +197,8 @@ class Config:
                 c.gmres_side = {"left": 0, "right": 1}[self.gmres_side]
             elif f.name == "jvp_mode":
                 c.jvp_mode = {"dual": 0, "linearized": 1}[self.jvp_mode]
+            elif f.name == "apply_accum":
+                c.apply_accum = {"fp32": 0, "df64": 1}[self.apply_accum]
             else:
                 setattr(c, f.name, getattr(self, f.name))
         return c

@@ -193,8 +193,10 @@ def test_block_parity(torch, cfg):
     assert np.all(err <= BLK_TOL), err
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-4), ("bf16", 1e-1)])
-def test_block_apply(torch, prec, tol):
+@pytest.mark.parametrize("prec,tol,accum", [("fp64", 1e-11, "df64"), ("fp32", 2e-4, "df64"),
+                                            ("bf16", 1e-1, "df64"), ("fp32", 2e-4, "fp32"),
+                                            ("bf16", 1e-1, "fp32")])
+def test_block_apply(torch, prec, tol, accum):
     """z_e = B_e^-1 r_e against numpy's inverse of the oracle blocks; FP32/BF16 storage
     within their unit round-off times the block condition (equilibrated)."""
     nx, ny, p, mach, re, kappa, deforming = 5, 3, 2, 0.05, 10.0, 1.0, True
@@ -203,7 +205,7 @@ def test_block_apply(torch, prec, tol):
     Bo = sv.block_jacobian(prob, q, 0.0, 150.0)
     r = inp.random_vector(q.shape, 11)
     want = sv.block_apply(np.linalg.inv(Bo), r)
-    S = solver_for(c, v, nx, ny, p, mach, re, kappa, prec=prec)
+    S = solver_for(c, v, nx, ny, p, mach, re, kappa, prec=prec, apply_accum=accum)
     S.precond_build(to_dev(q), 0.0, 150.0)
     z = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
     S.precond_apply(to_dev(r), z)
@@ -216,6 +218,29 @@ def test_block_apply(torch, prec, tol):
     assert rel.max() <= tol, rel.max()
     if prec == "fp64":
         assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_block_apply_double_float_is_linear(torch, prec):
+    """With FP32/BF16-stored inverses and double-float accumulation the preconditioner is a
+    linear map to near FP64 rounding: z(a r1 + b r2) = a z(r1) + b z(r2) within 1e-11;
+    plain FP32 accumulation is not (its deviation is of the order of FP32 round-off)."""
+    nx, ny, p, mach, re, kappa, deforming = 5, 3, 3, 0.05, 10.0, 1.0, True
+    c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
+    r1 = to_dev(inp.random_vector(q.shape, 21))
+    r2 = to_dev(inp.random_vector(q.shape, 22)) * 1e-3
+    dev = {}
+    for accum in ("df64", "fp32"):
+        S = solver_for(c, v, nx, ny, p, mach, re, kappa, prec=prec, apply_accum=accum)
+        S.precond_build(to_dev(q), 0.0, 150.0)
+        z1, z2, z12 = (torch.empty(S.shape, dtype=torch.float64, device="cuda:0") for _ in range(3))
+        S.precond_apply(r1, z1)
+        S.precond_apply(r2, z2)
+        S.precond_apply(0.7 * r1 + 1.3 * r2, z12)
+        lin = 0.7 * z1 + 1.3 * z2
+        dev[accum] = float((z12 - lin).abs().max() / lin.abs().max())
+    assert dev["df64"] <= 1e-11, dev
+    assert dev["fp32"] > 100 * dev["df64"], dev
 
 
 @pytest.mark.parametrize("side", ["left", "right"])
