@@ -54,6 +54,12 @@ ALU_KINDS = {"trace", "face", "elem", "trace_jvp", "face_jvp", "elem_jvp", "bloc
              "linear_adjoint"}
 
 
+# DRAM bytes per launch of a kernel class from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum averaged over the captured launches; the summary under profiles/
+# gives the command).  A class whose kernels changed since the capture is left out.
+NCU_TRAFFIC = {}
+
+
 def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -470,7 +476,7 @@ def gpu_arm(args):
             "peak": dk["peak"], "unit": dk["unit"], "frac": dk["frac"],
             "peak_source": hbm_src if dk["bound"] == "hbm" else ALU_PEAK_SOURCE,
             "alg_per_launch": dk["alg_per_launch"], "us_per_launch": dk["us_per_launch"],
-            "share": dk["share"], "traffic": None}
+            "share": dk["share"], "traffic": NCU_TRAFFIC.get(dominant)}
 
     last = stats[-1]
     line = {

@@ -16,6 +16,23 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+// Sum of pp[0 .. count) by one warp in a fixed order: lane l adds pp[l + 32 i], four
+// independent loads in flight (L2 reads: the partials come from other blocks after a
+// fence), then a warp sum.
+__device__ __forceinline__ double warp_sum_partials(const double* pp, int count) {
+  const int lane = threadIdx.x & 31;
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+  int p = lane;
+  for (; p + 96 < count; p += 128) {
+    t0 += __ldcg(pp + p);
+    t1 += __ldcg(pp + p + 32);
+    t2 += __ldcg(pp + p + 64);
+    t3 += __ldcg(pp + p + 96);
+  }
+  for (; p < count; p += 32) t0 += __ldcg(pp + p);
+  return warp_sum((t0 + t1) + (t2 + t3));
+}
+
 // Block sums of nv per-thread values: partial[k * gridDim.x + blockIdx.x].  The last
 // block to finish (atomic ticket, no waiting) then sums the partials of every k in a
 // fixed order and writes out[k]: one launch per reduction, deterministic result.
@@ -83,9 +100,7 @@ __device__ __forceinline__ bool block_reduce_store(double (&acc)[NA], int nv, do
   // final pass: warp w sums the partials of k = w, w + 8, ... in a fixed order
   const size_t ld = gridDim.x;
   for (int k = wid; k < nv; k += RT / 32) {
-    double s = 0.0;
-    for (int b = lane; b < nb; b += 32) s += ((volatile double*)partial)[(size_t)k * ld + b0 + b];
-    s = warp_sum(s);
+    const double s = warp_sum_partials(partial + (size_t)k * ld + b0, nb);
     if (lane == 0) out[k] = s;
   }
   if (threadIdx.x == 0) *ticket = 0u;
@@ -330,9 +345,7 @@ __device__ __forceinline__ bool seg_reduce(double (&acc)[NA], int nw, int k0, do
   if (!last) return false;
   __threadfence();
   for (int q = wid; q < nout; q += RT / 32) {
-    double t = 0.0;
-    for (int p = lane; p < count; p += 32) t += ((volatile double*)partial)[(size_t)q * ld + first + p];
-    t = warp_sum(t);
+    const double t = warp_sum_partials(partial + (size_t)q * ld + first, count);
     if (lane == 0) out[q] = t;
   }
   if (threadIdx.x == 0) *ticket = 0u;
@@ -429,6 +442,88 @@ __global__ void __launch_bounds__(RT) k_vaxpy(const double* __restrict__ V, size
                                tickets + k, (unsigned)(sg.cnb[k] * SPLIT),
                                (size_t)sg.cb0[k] * SPLIT, sg.cnb[k] * SPLIT);
   if (last && threadIdx.x == 0) gm_givens(st, ds, ds + BM, ds + 2 * BM);
+}
+
+// CGS2 middle step in one pass: w -= sum_k h1_k V_k over this block's part of a range
+// (one pair per thread, kept in shared memory), then <V_k, w> of the updated part for
+// every k < nv (warp q takes k = q, q + 8, ...), reduced per case into ds[BM ..].
+__global__ void __launch_bounds__(RT) k_vaxdots(const double* __restrict__ V, size_t ld, double* w,
+                                                BatchSegs sg, double* __restrict__ partial,
+                                                double* dsc, unsigned int* tickets,
+                                                GmresState* gst) {
+  __shared__ double hs[GmresState::LD + 1];
+  __shared__ double2 ws[RT];
+  __shared__ double sums[GmresState::LD + 1];
+  __shared__ bool last;
+  const int b = blockIdx.x, part = blockIdx.y;
+  const int k = sg.bcase[b];
+  GmresState* st = gst + k;
+  if (st->done) return;
+  const int nv = st->j + 1;
+  double* ds = dsc + (size_t)k * BDS;
+  for (int q = threadIdx.x; q < nv; q += RT) hs[q] = ds[q];
+  __syncthreads();
+  const size_t lo0 = (size_t)sg.blo[b], hi0 = (size_t)sg.bhi[b], len0 = hi0 - lo0;
+  const size_t lo = lo0 + len0 * part / SPLIT, hi = lo0 + len0 * (part + 1) / SPLIT;
+  const int len = (int)(hi - lo);   // <= RT: a range holds at most 4 RT pairs
+  const double2* V2 = reinterpret_cast<const double2*>(V);
+  double2* w2 = reinterpret_cast<double2*>(w);
+  const size_t ld2 = ld / 2;
+  if (threadIdx.x < len) {
+    const size_t i = lo + threadIdx.x;
+    double2 x = w2[i];
+    int q = 0;
+    for (; q + 4 <= nv; q += 4) {
+      const double2 v0 = V2[(q + 0) * ld2 + i], v1 = V2[(q + 1) * ld2 + i];
+      const double2 v2 = V2[(q + 2) * ld2 + i], v3 = V2[(q + 3) * ld2 + i];
+      x.x = fma(-hs[q], v0.x, x.x); x.y = fma(-hs[q], v0.y, x.y);
+      x.x = fma(-hs[q + 1], v1.x, x.x); x.y = fma(-hs[q + 1], v1.y, x.y);
+      x.x = fma(-hs[q + 2], v2.x, x.x); x.y = fma(-hs[q + 2], v2.y, x.y);
+      x.x = fma(-hs[q + 3], v3.x, x.x); x.y = fma(-hs[q + 3], v3.y, x.y);
+    }
+    for (; q < nv; ++q) {
+      const double2 v = V2[q * ld2 + i];
+      x.x = fma(-hs[q], v.x, x.x);
+      x.y = fma(-hs[q], v.y, x.y);
+    }
+    w2[i] = x;
+    ws[threadIdx.x] = x;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = wid; q < nv; q += RT / 32) {
+    const double2* vq = V2 + q * ld2 + lo;
+    double a0 = 0.0, a1 = 0.0;
+    int t = lane;
+    for (; t + 32 < len; t += 64) {
+      const double2 va = vq[t], vb = vq[t + 32];
+      const double2 xa = ws[t], xb = ws[t + 32];
+      a0 = fma(va.x, xa.x, a0); a0 = fma(va.y, xa.y, a0);
+      a1 = fma(vb.x, xb.x, a1); a1 = fma(vb.y, xb.y, a1);
+    }
+    if (t < len) {
+      const double2 va = vq[t], xa = ws[t];
+      a0 = fma(va.x, xa.x, a0); a0 = fma(va.y, xa.y, a0);
+    }
+    const double s = warp_sum(a0 + a1);
+    if (lane == 0) sums[q] = s;
+  }
+  __syncthreads();
+  const size_t ldp = (size_t)gridDim.x * SPLIT, pb = (size_t)b * SPLIT + part;
+  if (threadIdx.x < nv) partial[(size_t)threadIdx.x * ldp + pb] = sums[threadIdx.x];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(tickets + k, 1u) == (unsigned)(sg.cnb[k] * SPLIT) - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const size_t first = (size_t)sg.cb0[k] * SPLIT;
+  const int count = sg.cnb[k] * SPLIT;
+  for (int q = wid; q < nv; q += RT / 32) {
+    const double t = warp_sum_partials(partial + (size_t)q * ldp + first, count);
+    if (lane == 0) ds[BM + q] = t;
+  }
+  if (threadIdx.x == 0) tickets[k] = 0u;
 }
 
 // V[j] = next = w * inv_hn per case, j the case's newest basis index.  With init set the
@@ -603,8 +698,8 @@ void batch_free(fr_ctx* c) {
   b = BatchWork();
 }
 
-// Blocks of each case in proportion to its length: about 4 pairs per thread, 1 to 1024
-// blocks per case.
+// Blocks of each case in proportion to its length: at most 4 pairs per thread (a range
+// holds at most 4 RT pairs, one pair per thread of each of the SPLIT parts).
 int batch_setup(fr_ctx* c) {
   batch_free(c);
   BatchWork& b = c->bw;
@@ -613,7 +708,7 @@ int batch_setup(fr_ctx* c) {
   std::vector<long long> blo, bhi, mend(nc);
   for (int k = 0; k < nc; ++k) {
     const long long p0 = c->cps[k].off / 2, np = 2LL * c->cps[k].sn;
-    const int nb = (int)std::min<long long>(1024, std::max<long long>(1, (np + 4 * RT - 1) / (4 * RT)));
+    const int nb = (int)std::max<long long>(1, (np + 4 * RT - 1) / (4 * RT));
     cb0[k] = (int)bcase.size();
     cnb[k] = nb;
     mend[k] = c->cps[k].off + c->cps[k].sn;
@@ -667,7 +762,7 @@ int bk_init(fr_ctx* c, const double* r, double* next, cudaStream_t s) {
 int bk_orthogonalize(fr_ctx* c, double* w, double* next, int nv_bound, cudaStream_t s) {
   BatchWork& b = c->bw;
   const dim3 gdots(b.nblk, (nv_bound + KG - 1) / KG), gaxpy(b.nblk, SPLIT);
-  // CGS2: h1 = V^T w; w -= V h1; h2 = V^T w; w -= V h2, ||w||, Givens; V[j+1] = w/||w||
+  // CGS2: h1 = V^T w; (w -= V h1, h2 = V^T w); (w -= V h2, ||w||, Givens); V[j+1] = w/||w||
   FR_ACCOUNT(c, KK_KRYLOV, 8.0 * nv_bound * c->ndof + 2.0 * c->ndof, 8.0 * c->ndof * (4.0 * nv_bound + 6.0));
   {
     FR_PROF_BEGIN(c, s);
@@ -677,13 +772,7 @@ int bk_orthogonalize(fr_ctx* c, double* w, double* next, int nv_bound, cudaStrea
   }
   {
     FR_PROF_BEGIN(c, s);
-    k_vaxpy<false><<<gaxpy, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, 0, b.tickets, b.gst);
-    FR_PROF_END(c, s, KK_KRYLOV);
-    FR_LAUNCH_CHECK(c);
-  }
-  {
-    FR_PROF_BEGIN(c, s);
-    k_vdots<<<gdots, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, BM, b.tickets, b.gst);
+    k_vaxdots<<<gaxpy, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, b.tickets, b.gst);
     FR_PROF_END(c, s, KK_KRYLOV);
     FR_LAUNCH_CHECK(c);
   }
