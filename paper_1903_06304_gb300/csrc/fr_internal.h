@@ -38,7 +38,7 @@ struct BatchWork {
   BatchSegs sg{};
   int *bcase = nullptr, *cb0 = nullptr, *cnb = nullptr;
   long long *blo = nullptr, *bhi = nullptr, *mend = nullptr;
-  double* partial = nullptr;       // [32][nblk]
+  double* partial = nullptr;       // [32][nblk x 4]: up to 32 sums per block of a split pass
   unsigned int* tickets = nullptr; // [ncases], kept at 0
   double* dsc = nullptr;           // [ncases][128] per-case scalars
   double* hsc = nullptr;           // pinned mirror
