@@ -313,6 +313,15 @@ template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x
 // transformations, linear to about 2^-44 of the summed magnitudes).
 constexpr int APPLY_PARTS = 4;
 
+// (sh, sl) += (bh, bl), both unevaluated FP32 pairs (two-sum of the high parts).
+__device__ __forceinline__ void df_merge(float& sh, float& sl, float bh, float bl) {
+  const float sn = sh + bh;
+  const float bv = sn - sh;
+  const float er = (sh - (sn - bv)) + (bh - bv);
+  sh = sn;
+  sl += bl + er;
+}
+
 __device__ __forceinline__ void df_add(float& sh, float& sl, float a, float2 xv) {
   const float ph = a * xv.x;
   float pl = fmaf(a, xv.x, -ph);   // exact low part of a x_hi
@@ -333,8 +342,9 @@ __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
   __shared__ double xd[ACC == 0 ? BS : 1];
   __shared__ float xf[ACC == 1 ? BS : 1];
   __shared__ float2 x2[ACC == 2 ? BS : 1];
-  __shared__ double pd[APPLY_PARTS][BSR];
+  __shared__ double pd[ACC == 0 ? APPLY_PARTS : 1][BSR];
   __shared__ float pf[ACC == 1 ? APPLY_PARTS : 1][BSR];
+  __shared__ float2 p2[ACC == 2 ? APPLY_PARTS : 1][BSR];
   const int e = blockIdx.x;
   if (!M.on(e)) return;
   const int part = threadIdx.x / BSR, row = threadIdx.x % BSR;
@@ -391,7 +401,10 @@ __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
           else df_add(h0, l0, to_f(av[k]), x2[c2]);
         }
       }
-      pd[part][row] = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
+      // partial sums combined as FP32 pairs: conversions and FP64 additions run on the
+      // FP64 pipe, which is slower than all of the two-sum work above
+      df_merge(h0, l0, h1, l1);
+      p2[part][row] = make_float2(h0, l0);
     }
   }
   __syncthreads();
@@ -402,6 +415,11 @@ __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
 #pragma unroll
     for (int q = 1; q < APPLY_PARTS; ++q) t += pf[q][row];
     acc = (double)t;
+  } else if (ACC == 2) {
+    float sh = p2[0][row].x, sl = p2[0][row].y;
+#pragma unroll
+    for (int q = 1; q < APPLY_PARTS; ++q) df_merge(sh, sl, p2[q][row].x, p2[q][row].y);
+    acc = (double)sh + (double)sl;
   } else {
     acc = pd[0][row];
 #pragma unroll
