@@ -57,7 +57,11 @@ ALU_KINDS = {"trace", "face", "elem", "trace_jvp", "face_jvp", "elem_jvp", "bloc
 # DRAM bytes per launch of a kernel class from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum averaged over the captured launches; the summary under profiles/
 # gives the command).  A class whose kernels changed since the capture is left out.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # k_vdots / k_vaxdots / k_vaxpy<1>, one GMRES iteration of the 64x64 p=3 vortex at
+    # nv = 7 (16.8 + 16.8 + 15.2 MB): equal to the algorithmic bytes of those launches
+    "krylov_reduce": 16.28e6,
+}
 
 
 def hbm_peak():
