@@ -243,8 +243,9 @@ def test_block_apply_double_float_is_linear(torch, prec):
     assert dev["fp32"] > 100 * dev["df64"], dev
 
 
-@pytest.mark.parametrize("side", ["left", "right"])
-def test_gmres_parity(torch, side):
+# restart <= 32: device-resident Arnoldi; restart 40: the host-Givens path
+@pytest.mark.parametrize("side,restart", [("left", 10), ("right", 10), ("left", 40), ("right", 40)])
+def test_gmres_parity(torch, side, restart):
     nx, ny, p, mach, re, kappa, deforming = 4, 4, 2, 0.05, 10.0, 1.0, True
     c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
     prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
@@ -252,10 +253,10 @@ def test_gmres_parity(torch, side):
     b = inp.random_vector(q.shape, 13)
     Binv = np.linalg.inv(sv.block_jacobian(prob, q, inv_dtau, a0_dt))
     P = lambda x: sv.block_apply(Binv, x)
-    want = sv.gmres(lambda x: sv.apply_A(prob, q, x, inv_dtau, a0_dt), b, P, 10, 1e-8, 200,
+    want = sv.gmres(lambda x: sv.apply_A(prob, q, x, inv_dtau, a0_dt), b, P, restart, 1e-8, 200,
                     side=side)
-    S = solver_for(c, v, nx, ny, p, mach, re, kappa, restart=10, maxit_lin=200, tol_res=1e-8,
-                   gmres_side=side)
+    S = solver_for(c, v, nx, ny, p, mach, re, kappa, restart=restart, maxit_lin=200,
+                   tol_res=1e-8, gmres_side=side)
     qd = to_dev(q)
     S.precond_build(qd, inv_dtau, a0_dt)
     x = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
