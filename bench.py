@@ -251,7 +251,7 @@ def gpu_arm(args):
                         restart=args.restart, maxit_lin=args.maxit_lin, tol_res=w.tol_res,
                         tol_pseudo=w.tol_pseudo, maxit_newton=args.maxit_newton, lag=2,
                         line_search=args.line_search, graphs=args.graphs,
-                        apply_accum=args.apply_accum)
+                        apply_accum=args.apply_accum, tiles=args.tiles)
         S = fr.Solver(cfg, w.nx, w.ny)
         S.update_mesh(T(corners), T(vel))
         return S
@@ -494,6 +494,7 @@ def gpu_arm(args):
                    "newton": f"max {args.maxit_newton} iterations, backtracking {args.line_search} halvings",
                    "precond": f"element block-Jacobi, {args.prec} blocks, {args.apply_accum} apply accumulation",
                    "l2": "256 MiB write between timed steps, outside the per-step events",
+                   "tiles": S.tiles,
                    "parallelism": "replicas" if world > 1 else "single"},
         "startup_steps": args.startup,
         "sec_per_bdf2_step": ms_per_step / 1e3,
@@ -648,6 +649,8 @@ def main():
                     help="backtracking halvings per Newton update (0: plain Newton)")
     ap.add_argument("--apply-accum", dest="apply_accum", default="df64", choices=["df64", "fp32"],
                     help="block-apply arithmetic with FP32/BF16-stored inverses")
+    ap.add_argument("--tiles", type=int, default=0, choices=[0, 1, 2],
+                    help="elements per CTA of the point kernels: 0 autotuned at set-up, 1 or 2 fixed")
     ap.add_argument("--graphs", type=int, default=1,
                     help="replay GMRES chunks from captured CUDA graphs (1) or launch each kernel (0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -80,6 +80,11 @@ typedef struct fr_ctx fr_ctx;
  * round-off while it runs on the FP32 pipe; FR_ACCUM_FP32 rounds the input and
  * accumulates in plain FP32 (a state-dependent perturbation with which GMRES can stall
  * on stiff cases);
+ * tiles: elements per CTA of the point-parallel kernels, K x floor(128 / (p+1)^2) with
+ * K = 1 (default) or 2; 0 lets fr_set_mesh time both for each kernel on the context's
+ * own sizes and keep the faster.  The two shapes compute the same operations per point
+ * but are compiled separately, and their results agree to rounding (about 1e-14
+ * relative), not bit for bit; a timed choice can therefore differ between runs;
  * graphs: if nonzero (default) and restart <= 32, GMRES iterations are issued in chunks of
  * up to 10 whose kernel launches are captured once into a CUDA graph and replayed (same
  * results; fewer launch overheads); ignored while fr_profile timing is on. */
@@ -104,6 +109,7 @@ typedef struct fr_config {
   int jvp_mode;
   int graphs;
   int apply_accum;
+  int tiles;
 } fr_config;
 
 /* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).
@@ -336,6 +342,10 @@ const char* fr_batch_last_error(const fr_batch* b);
 /* Sizes: number of FP64 entries of a solution vector, block size b. */
 size_t fr_num_dof(const fr_ctx* ctx);
 int fr_block_size(const fr_ctx* ctx);
+/* The tile shapes in use (K of each point-parallel kernel: residual trace, residual
+ * element pass, JVP trace, JVP element pass, linearised-operator element pass) into
+ * k[0..4] (host). */
+int fr_tiles(const fr_ctx* ctx, int* k);
 /* Number of kernels this context has launched since creation (device work items). */
 long long fr_kernel_launches(const fr_ctx* ctx);
 

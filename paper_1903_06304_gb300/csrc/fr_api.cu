@@ -525,6 +525,7 @@ void fr_default_config(fr_config* c) {
   c->jvp_mode = FR_JVP_LINEARIZED;
   c->graphs = 1;
   c->apply_accum = FR_ACCUM_DF64;
+  c->tiles = 1;
 }
 
 int fr_create(const fr_config* cfg, fr_ctx** out) {
@@ -534,7 +535,8 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
       cfg->restart > FR_MAX_RESTART || cfg->prec_dtype < 0 || cfg->prec_dtype > 2 ||
       (cfg->gmres_side != FR_GMRES_LEFT && cfg->gmres_side != FR_GMRES_RIGHT) ||
       (cfg->jvp_mode != FR_JVP_DUAL && cfg->jvp_mode != FR_JVP_LINEARIZED) ||
-      (cfg->apply_accum != FR_ACCUM_FP32 && cfg->apply_accum != FR_ACCUM_DF64))
+      (cfg->apply_accum != FR_ACCUM_FP32 && cfg->apply_accum != FR_ACCUM_DF64) ||
+      cfg->tiles < 0 || cfg->tiles > 2)
     return FR_ERR_ARG;
   fr_ctx* c = new fr_ctx();
   c->cfg = *cfg;
@@ -665,7 +667,9 @@ int fr_setup_cases(fr_ctx* c, int ncases, const int* nxs, const int* nys,
   FR_TRY(dev_alloc(c, &c->ticket, 1));
   FR_CUDA_CHECK(c, cudaMemset(c->ticket, 0, sizeof(unsigned int)));
   // per-case vector partition, GMRES states and staging (used by every context)
-  return frk::batch_setup(c);
+  FR_TRY(frk::batch_setup(c));
+  // tile shapes of the point-parallel kernels (timed on these buffers unless forced)
+  return frk::autotune_tiles(c);
 }
 
 extern "C" {
@@ -774,6 +778,12 @@ int fr_residual_norms(fr_ctx* c, const double* r, double* mass, double* all, voi
 }
 
 size_t fr_num_dof(const fr_ctx* c) { return c ? c->ndof : 0; }
+int fr_tiles(const fr_ctx* c, int* k) {
+  if (!c || !k) return FR_ERR_ARG;
+  k[0] = c->tile.trace; k[1] = c->tile.elem; k[2] = c->tile.trace_d; k[3] = c->tile.elem_d;
+  k[4] = c->tile.lin_elem;
+  return FR_OK;
+}
 int fr_block_size(const fr_ctx* c) { return c ? c->bsz : 0; }
 long long fr_kernel_launches(const fr_ctx* c) { return c ? c->launches : 0; }
 const char* fr_last_error(const fr_ctx* c) { return c ? c->err : "null context"; }

@@ -303,10 +303,12 @@ __device__ __forceinline__ void face_common(const T qm[4], const T qp[4], const 
 }
 
 // ---------------------------------------------------------------- launch geometry
-// Elements per block for the point-parallel kernels (one thread per solution point).
-template <int N> struct Tile {
+// Elements per block for the point-parallel kernels (one thread per solution point):
+// K x floor(128 / n^2) elements, K = 1 or 2 (the tile shape, fixed or chosen per kernel
+// by the autotuner; a thread performs the same operations for either K).
+template <int N, int K = 1> struct Tile {
   static constexpr int NP = N * N;
-  static constexpr int EPB = 128 / NP;
+  static constexpr int EPB = K * (128 / NP);
   static constexpr int THREADS = EPB * NP;
 };
 

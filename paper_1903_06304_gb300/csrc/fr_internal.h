@@ -72,6 +72,12 @@ struct FrProf {
   long long n[KK_COUNT] = {};
 };
 
+// Tile shapes (K of Tile<N, K>) of the point-parallel kernels: residual and dual JVP
+// trace / element passes and the element pass of the linearised operator.
+struct TileChoice {
+  int trace = 1, elem = 1, trace_d = 1, elem_d = 1, lin_elem = 1;
+};
+
 // A captured chunk of GMRES iterations (CUDA graph) and the launch / algorithmic counts
 // one replay adds.
 struct GraphEntry {
@@ -100,6 +106,7 @@ struct fr_ctx {
   bool external_terms = false;  // time and operator terms are set per case by the caller
   BatchWork bw;                 // batched loops (cases of one degree and viscous switch)
   std::vector<GraphEntry> graphs;   // captured GMRES chunks (fr_api.cu)
+  TileChoice tile;                  // tile shapes (fr_linear.cu autotune_tiles)
   // parameter sensitivities (fr_sens.cu): geometry values and tangents, seeds, per-element
   // dot products, a zero state tangent and the residual tangent
   double *sgs = nullptr, *sdgs = nullptr, *sgf = nullptr, *sdgf = nullptr;
@@ -218,6 +225,9 @@ int bk_finish(fr_ctx* c, double* u, cudaStream_t s);              // trisolve + 
 int bk_status(fr_ctx* c, cudaStream_t s);                         // -> bw.status_h (async)
 int bk_axpy_case(fr_ctx* c, const double* coef_dev, const double* x, double* y, cudaStream_t s);
 int upload_cases(fr_ctx* c, cudaStream_t s);                      // c->cps -> device
+// Tile shapes: forced by cfg.tiles (1 or 2) or timed on the context's own buffers
+// (cfg.tiles = 0).  Synchronous; called once at mesh set-up.
+int autotune_tiles(fr_ctx* c);
 // Per-case continuity-row and full norms of r (synchronises; bad[k] set for non-finite).
 int case_norms(fr_ctx* c, const double* r, std::vector<double>& mass, std::vector<double>& all,
                std::vector<char>& bad, cudaStream_t s);

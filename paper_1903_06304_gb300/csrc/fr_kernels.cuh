@@ -128,12 +128,12 @@ static __global__ void k_set_case(CaseParams* cp, int cid, CaseParams value) { c
 // q^p (and the tangent) of EPB elements staged in shared memory; each thread owns one
 // solution point.  Outputs: gl[8][Ne*NP] local gradients (x comps then y comps),
 // tq[Ne][4][4][N] state traces, tg[Ne][4][8][N] gradient traces.
-template <class T, int N, class G = double>
-__global__ void __launch_bounds__(Tile<N>::THREADS)
+template <class T, int N, class G = double, int K = 1>
+__global__ void __launch_bounds__(Tile<N, K>::THREADS)
 k_trace(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs, Buf<T> GL, Buf<T> TQ,
         Buf<T> TG, const double* __restrict__ dgs = nullptr) {
   const int ne = M.ne;
-  constexpr int NP = N * N, EPB = Tile<N>::EPB;
+  constexpr int NP = N * N, EPB = Tile<N, K>::EPB;
   __shared__ T sq[EPB][4][NP];
   __shared__ T sg[EPB][8][NP];
   const int le = threadIdx.x / NP, pt = threadIdx.x % NP;
@@ -275,13 +275,13 @@ __device__ __forceinline__ void gamma_m_apply(const double q[4], const double w[
   out[3] = h * d0 - s * w[0] + sr * (q[1] * w[1] + q[2] * w[2]) + sr * gs.cp * w[3];
 }
 
-template <class T, int N, int MODE, class G = double>
-__global__ void __launch_bounds__(Tile<N>::THREADS)
+template <class T, int N, int MODE, class G = double, int K = 1>
+__global__ void __launch_bounds__(Tile<N, K>::THREADS)
 k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
        const double* __restrict__ gf, Buf<T> GL, Buf<T> TQ, Buf<T> FN, Buf<T> QC,
        double* __restrict__ out, TimeTerms tt, const double* __restrict__ dgs = nullptr,
        const double* __restrict__ dgf = nullptr, double dmach = 0.0) {
-  constexpr int NP = N * N, EPB = Tile<N>::EPB;
+  constexpr int NP = N * N, EPB = Tile<N, K>::EPB;
   __shared__ T sF[EPB][4][NP];
   __shared__ T sG[EPB][4][NP];
   const int le = threadIdx.x / NP, pt = threadIdx.x % NP;

@@ -12,6 +12,7 @@
 // state q is fixed during a GMRES solve, so the JVP then costs small mat-vecs instead
 // of a dual-number residual, and the VJP is the same factors transposed, applied in
 // reverse order.
+#include <algorithm>
 #include <cstdio>
 #include "fr_internal.h"
 #include "fr_kernels.cuh"
@@ -225,15 +226,15 @@ __global__ void k_lin_face_apply(Mesh M, const double* __restrict__ tqv,
 
 // Solution point: dgc = dg + lifted jumps, d(F,G) = JP dq + JG dgc, then
 // A v = P' dq + (1/|J|)(Dc dF + Dc dG + sum_f g_f' dfnum_f).
-template <int N>
-__global__ void __launch_bounds__(Tile<N>::THREADS)
+template <int N, int K = 1>
+__global__ void __launch_bounds__(Tile<N, K>::THREADS)
 k_lin_elem_apply(const double* __restrict__ v, Mesh M, Basis B,
                  const double* __restrict__ gs, const double* __restrict__ gf,
                  const double* __restrict__ glv, const double* __restrict__ tqv,
                  const double* __restrict__ fnv, const double* __restrict__ qcv,
                  const double* __restrict__ JP, const double* __restrict__ JG,
                  const double* __restrict__ PP, double* __restrict__ out) {
-  constexpr int NP = N * N, EPB = Tile<N>::EPB;
+  constexpr int NP = N * N, EPB = Tile<N, K>::EPB;
   __shared__ double sF[EPB][4][NP];
   __shared__ double sG[EPB][4][NP];
   const int le = threadIdx.x / NP, pt = threadIdx.x % NP;
@@ -582,9 +583,15 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
     {
       FR_ACCOUNT(c, KK_LIN_APPLY, np * fl_trace, 0.0);
       FR_PROF_BEGIN(c, s);
-      k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(v)}, c->mesh, c->basis,
-                                             c->gs, Buf<double>{c->gl_d}, Buf<double>{c->tq_d},
-                                             Buf<double>{c->tg_d});
+      if (c->tile.trace == 2)
+        k_trace<double, N, double, 2><<<(c->ne + Tile<N, 2>::EPB - 1) / Tile<N, 2>::EPB,
+                                        Tile<N, 2>::THREADS, 0, s>>>(
+            Buf<double>{const_cast<double*>(v)}, c->mesh, c->basis, c->gs, Buf<double>{c->gl_d},
+            Buf<double>{c->tq_d}, Buf<double>{c->tg_d});
+      else
+        k_trace<double, N><<<nblk, TH, 0, s>>>(Buf<double>{const_cast<double*>(v)}, c->mesh, c->basis,
+                                               c->gs, Buf<double>{c->gl_d}, Buf<double>{c->tq_d},
+                                               Buf<double>{c->tg_d});
       FR_PROF_END(c, s, KK_LIN_APPLY);
       FR_LAUNCH_CHECK(c);
     }
@@ -599,8 +606,13 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
     {
       FR_ACCOUNT(c, KK_LIN_APPLY, np * fl_elem, 0.0);
       FR_PROF_BEGIN(c, s);
-      k_lin_elem_apply<N><<<nblk, TH, 0, s>>>(v, c->mesh, c->basis, c->gs, c->gf, c->gl_d,
-                                              c->tq_d, c->fn_d, c->qcm_d, c->JP, c->JG, c->PP, out);
+      if (c->tile.lin_elem == 2)
+        k_lin_elem_apply<N, 2><<<(c->ne + Tile<N, 2>::EPB - 1) / Tile<N, 2>::EPB, Tile<N, 2>::THREADS,
+                                 0, s>>>(v, c->mesh, c->basis, c->gs, c->gf, c->gl_d, c->tq_d,
+                                         c->fn_d, c->qcm_d, c->JP, c->JG, c->PP, out);
+      else
+        k_lin_elem_apply<N><<<nblk, TH, 0, s>>>(v, c->mesh, c->basis, c->gs, c->gf, c->gl_d,
+                                                c->tq_d, c->fn_d, c->qcm_d, c->JP, c->JG, c->PP, out);
       FR_PROF_END(c, s, KK_LIN_APPLY);
       FR_LAUNCH_CHECK(c);
     }
@@ -653,6 +665,99 @@ int apply_linear(fr_ctx* c, const double* v, double* out, bool transpose, cudaSt
     case 3: return apply_n<3>(c, v, out, transpose, s);
     case 4: return apply_n<4>(c, v, out, transpose, s);
     case 5: return apply_n<5>(c, v, out, transpose, s);
+  }
+  return FR_ERR_ARG;
+}
+
+}  // namespace frk
+
+// ------------------------------------------------------------------ tile-shape autotuner
+namespace frk {
+using namespace fr;
+
+static __global__ void k_fill(double* __restrict__ p, size_t n, double v) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// Median device time of 5 launches of fn after one untimed launch (stream 0, set-up).
+template <class F>
+static int time_launches(fr_ctx* c, F fn, float* ms) {
+  cudaEvent_t ev[6];
+  for (auto& e : ev) FR_CUDA_CHECK(c, cudaEventCreate(&e));
+  fn();
+  FR_CUDA_CHECK(c, cudaGetLastError());
+  for (int k = 0; k < 5; ++k) {
+    FR_CUDA_CHECK(c, cudaEventRecord(ev[k], 0));
+    fn();
+  }
+  FR_CUDA_CHECK(c, cudaEventRecord(ev[5], 0));
+  FR_CUDA_CHECK(c, cudaGetLastError());
+  FR_CUDA_CHECK(c, cudaEventSynchronize(ev[5]));
+  float t[5];
+  for (int k = 0; k < 5; ++k) FR_CUDA_CHECK(c, cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]));
+  std::sort(t, t + 5);
+  *ms = t[2];
+  for (auto& e : ev) cudaEventDestroy(e);
+  return FR_OK;
+}
+
+// Picks K in {1, 2} for each point-parallel kernel by timing both on this context's own
+// sizes and buffers (filled with finite placeholder values; every one of them is
+// rewritten before its first real use).  The shapes agree to rounding.
+template <int N>
+static int autotune_n(fr_ctx* c) {
+  const int nb1 = (c->ne + Tile<N, 1>::EPB - 1) / Tile<N, 1>::EPB;
+  const int nb2 = (c->ne + Tile<N, 2>::EPB - 1) / Tile<N, 2>::EPB;
+  constexpr int T1 = Tile<N, 1>::THREADS, T2 = Tile<N, 2>::THREADS;
+  const size_t SN = (size_t)c->ne * c->np2, FNn = (size_t)c->ne * 4 * c->n;
+  struct Fill { double* p; size_t n; double v; };
+  const Fill fills[] = {{c->gs, GS_COUNT * SN, 1.0}, {c->gf, GF_COUNT * FNn, 1.0}, {c->w_r, c->ndof, 1.0},
+                        {c->w_z, c->ndof, 0.5}, {c->JP, 32 * SN, 0.1}, {c->JG, 64 * SN, 0.1},
+                        {c->PP, 16 * SN, 0.1}, {c->gl, 8 * SN, 0.1}, {c->gl_d, 8 * SN, 0.1},
+                        {c->tq, c->ne * 16 * (size_t)c->n, 1.0}, {c->tq_d, c->ne * 16 * (size_t)c->n, 0.1},
+                        {c->fn, c->ne * 8 * (size_t)c->n, 0.1}, {c->fn_d, c->ne * 8 * (size_t)c->n, 0.1},
+                        {c->qcm, c->ne * 8 * (size_t)c->n, 1.0}, {c->qcm_d, c->ne * 8 * (size_t)c->n, 0.1}};
+  for (const Fill& f : fills) k_fill<<<1024, 256>>>(f.p, f.n, f.v);
+  FR_CUDA_CHECK(c, cudaGetLastError());
+  const Basis& B = c->basis;
+  const Mesh& M = c->mesh;
+  const Buf<double> Q{c->w_r}, GL{c->gl}, TQ{c->tq}, TG{c->tg}, FN{c->fn}, QC{c->qcm};
+  const Buf<Dual> QD{c->w_r, c->w_z}, GLD{c->gl, c->gl_d}, TQD{c->tq, c->tq_d}, TGD{c->tg, c->tg_d};
+  const Buf<Dual> FND{c->fn, c->fn_d}, QCD{c->qcm, c->qcm_d};
+  const TimeTerms tt{nullptr, nullptr};
+  float a = 0.f, b = 0.f;
+  auto pick = [&](int* slot) { *slot = b < a ? 2 : 1; };
+  FR_TRY(time_launches(c, [&] { k_trace<double, N><<<nb1, T1>>>(Q, M, B, c->gs, GL, TQ, TG); }, &a));
+  FR_TRY(time_launches(c, [&] { k_trace<double, N, double, 2><<<nb2, T2>>>(Q, M, B, c->gs, GL, TQ, TG); }, &b));
+  pick(&c->tile.trace);
+  FR_TRY(time_launches(c, [&] { k_elem<double, N, MODE_RESID><<<nb1, T1>>>(Q, M, B, c->gs, c->gf, GL, TQ, FN, QC, c->w_t, tt); }, &a));
+  FR_TRY(time_launches(c, [&] { k_elem<double, N, MODE_RESID, double, 2><<<nb2, T2>>>(Q, M, B, c->gs, c->gf, GL, TQ, FN, QC, c->w_t, tt); }, &b));
+  pick(&c->tile.elem);
+  FR_TRY(time_launches(c, [&] { k_trace<Dual, N><<<nb1, T1>>>(QD, M, B, c->gs, GLD, TQD, TGD); }, &a));
+  FR_TRY(time_launches(c, [&] { k_trace<Dual, N, double, 2><<<nb2, T2>>>(QD, M, B, c->gs, GLD, TQD, TGD); }, &b));
+  pick(&c->tile.trace_d);
+  FR_TRY(time_launches(c, [&] { k_elem<Dual, N, MODE_JVP><<<nb1, T1>>>(QD, M, B, c->gs, c->gf, GLD, TQD, FND, QCD, c->w_t, tt); }, &a));
+  FR_TRY(time_launches(c, [&] { k_elem<Dual, N, MODE_JVP, double, 2><<<nb2, T2>>>(QD, M, B, c->gs, c->gf, GLD, TQD, FND, QCD, c->w_t, tt); }, &b));
+  pick(&c->tile.elem_d);
+  FR_TRY(time_launches(c, [&] { k_lin_elem_apply<N><<<nb1, T1>>>(c->w_r, M, B, c->gs, c->gf, c->gl_d, c->tq_d, c->fn_d, c->qcm_d, c->JP, c->JG, c->PP, c->w_t); }, &a));
+  FR_TRY(time_launches(c, [&] { k_lin_elem_apply<N, 2><<<nb2, T2>>>(c->w_r, M, B, c->gs, c->gf, c->gl_d, c->tq_d, c->fn_d, c->qcm_d, c->JP, c->JG, c->PP, c->w_t); }, &b));
+  pick(&c->tile.lin_elem);
+  FR_CUDA_CHECK(c, cudaDeviceSynchronize());
+  return FR_OK;
+}
+
+int autotune_tiles(fr_ctx* c) {
+  const int forced = c->cfg.tiles;
+  if (forced == 1 || forced == 2) {
+    c->tile.trace = c->tile.elem = c->tile.trace_d = c->tile.elem_d = c->tile.lin_elem = forced;
+    return FR_OK;
+  }
+  switch (c->n) {
+    case 2: return autotune_n<2>(c);
+    case 3: return autotune_n<3>(c);
+    case 4: return autotune_n<4>(c);
+    case 5: return autotune_n<5>(c);
   }
   return FR_ERR_ARG;
 }

@@ -36,9 +36,10 @@ __global__ void k_conservative(const double* __restrict__ q, size_t SN, int np2,
 template <class T, int N, int MODE>
 static int run_pipeline(fr_ctx* c, Buf<T> Q, Buf<T> GL, Buf<T> TQ, Buf<T> TG, Buf<T> FNb,
                         Buf<T> QCb, double* out, TimeTerms tt, cudaStream_t s) {
-  constexpr int EPB = Tile<N>::EPB, TH = Tile<N>::THREADS;
   constexpr bool jvp = MODE == MODE_JVP;
-  const int nblk = (c->ne + EPB - 1) / EPB;
+  const int kt = jvp ? c->tile.trace_d : c->tile.trace, ke = jvp ? c->tile.elem_d : c->tile.elem;
+  const int nb1 = (c->ne + Tile<N, 1>::EPB - 1) / Tile<N, 1>::EPB;
+  const int nb2 = (c->ne + Tile<N, 2>::EPB - 1) / Tile<N, 2>::EPB;
   const bool visc = c->mesh.viscous;
   const double pts = (double)c->ne * N * N, fac = jvp ? FR_JVP_FLOP_FACTOR : 1.0;
   FR_ACCOUNT(c, jvp ? KK_TRACE_JVP : KK_TRACE, fac * pts * fr_flops_trace(N, visc), 0.0);
@@ -46,7 +47,10 @@ static int run_pipeline(fr_ctx* c, Buf<T> Q, Buf<T> GL, Buf<T> TQ, Buf<T> TG, Bu
   FR_ACCOUNT(c, jvp ? KK_ELEM_JVP : KK_ELEM, fac * pts * fr_flops_elem(N, visc), 0.0);
   {
     FR_PROF_BEGIN(c, s);
-    k_trace<T, N><<<nblk, TH, 0, s>>>(Q, c->mesh, c->basis, c->gs, GL, TQ, TG);
+    if (kt == 2)
+      k_trace<T, N, double, 2><<<nb2, Tile<N, 2>::THREADS, 0, s>>>(Q, c->mesh, c->basis, c->gs, GL, TQ, TG);
+    else
+      k_trace<T, N><<<nb1, Tile<N, 1>::THREADS, 0, s>>>(Q, c->mesh, c->basis, c->gs, GL, TQ, TG);
     FR_PROF_END(c, s, jvp ? KK_TRACE_JVP : KK_TRACE);
     FR_LAUNCH_CHECK(c);
   }
@@ -59,8 +63,12 @@ static int run_pipeline(fr_ctx* c, Buf<T> Q, Buf<T> GL, Buf<T> TQ, Buf<T> TG, Bu
   }
   {
     FR_PROF_BEGIN(c, s);
-    k_elem<T, N, MODE><<<nblk, TH, 0, s>>>(Q, c->mesh, c->basis, c->gs, c->gf, GL, TQ, FNb,
-                                           QCb, out, tt);
+    if (ke == 2)
+      k_elem<T, N, MODE, double, 2><<<nb2, Tile<N, 2>::THREADS, 0, s>>>(
+          Q, c->mesh, c->basis, c->gs, c->gf, GL, TQ, FNb, QCb, out, tt);
+    else
+      k_elem<T, N, MODE><<<nb1, Tile<N, 1>::THREADS, 0, s>>>(Q, c->mesh, c->basis, c->gs, c->gf,
+                                                            GL, TQ, FNb, QCb, out, tt);
     FR_PROF_END(c, s, jvp ? KK_ELEM_JVP : KK_ELEM);
     FR_LAUNCH_CHECK(c);
   }

@@ -43,7 +43,7 @@ class _Config(ctypes.Structure):
                 ("dtau_unsteady", ctypes.c_double), ("gmres_side", ctypes.c_int),
                 ("ser_unsteady", ctypes.c_int), ("dtau0_unsteady", ctypes.c_double),
                 ("line_search", ctypes.c_int), ("jvp_mode", ctypes.c_int),
-                ("graphs", ctypes.c_int), ("apply_accum", ctypes.c_int)]
+                ("graphs", ctypes.c_int), ("apply_accum", ctypes.c_int), ("tiles", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -101,6 +101,7 @@ _SIGS = {
     "fr_linearize": (_I, [_P, _P, _D, _D, _P]),
     "fr_apply_linear": (_I, [_P, _P, _P, _I, _P]),
     "fr_vjp": (_I, [_P, _P, _P, _D, _D, _P, _P]),
+    "fr_tiles": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "fr_param_vjp": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_D), _P, _P, _P]),
     "fr_batch_create": (_I, [ctypes.POINTER(_Config), _P, _I, ctypes.POINTER(_P)]),
     "fr_batch_destroy": (None, [_P]),
@@ -186,6 +187,7 @@ class Config:
     jvp_mode: str = "linearized"
     graphs: int = 1
     apply_accum: str = "df64"
+    tiles: int = 1
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -361,6 +363,13 @@ class Solver:
     @property
     def kernel_launches(self) -> int:
         return int(self.lib.fr_kernel_launches(self.ctx))
+
+    @property
+    def tiles(self) -> dict:
+        """Tile shape K (elements per CTA = K x floor(128 / n^2)) of each point kernel."""
+        k = (ctypes.c_int * 5)()
+        self._check(self.lib.fr_tiles(self.ctx, k))
+        return dict(zip(("trace", "elem", "trace_jvp", "elem_jvp", "linear_elem"), list(k)))
 
     # -- calls of include/fr.h
     def update_mesh(self, corners, vel, stream=None):
