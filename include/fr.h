@@ -80,6 +80,9 @@ typedef struct fr_ctx fr_ctx;
  * round-off while it runs on the FP32 pipe; FR_ACCUM_FP32 rounds the input and
  * accumulates in plain FP32 (a state-dependent perturbation with which GMRES can stall
  * on stiff cases);
+ * block_mode: how the element blocks are formed, both exact: FR_BLOCK_LINEARIZED
+ * (default) composes them from the stored local Jacobians (fr_linearize, done by the
+ * build), FR_BLOCK_DUAL differentiates each element's residual by dual numbers;
  * tiles: elements per CTA of the point-parallel kernels, K x floor(128 / (p+1)^2) with
  * K = 1 (default) or 2; 0 lets fr_set_mesh time both for each kernel on the context's
  * own sizes and keep the faster.  The two shapes compute the same operations per point
@@ -95,6 +98,8 @@ typedef struct fr_ctx fr_ctx;
 #define FR_GMRES_RIGHT 1
 #define FR_ACCUM_FP32 0
 #define FR_ACCUM_DF64 1
+#define FR_BLOCK_LINEARIZED 0
+#define FR_BLOCK_DUAL 1
 typedef struct fr_config {
   int p;
   double gamma, prandtl, mach, re, kappa, eps_floor;
@@ -110,6 +115,7 @@ typedef struct fr_config {
   int graphs;
   int apply_accum;
   int tiles;
+  int block_mode;
 } fr_config;
 
 /* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).

@@ -387,13 +387,15 @@ int newton_loop(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, do
   for (m = 0; m < maxit; ++m) {
     if (rm <= c->cfg.tol_pseudo * res0) { conv = true; break; }
     const double inv_dtau = 1.0 / dtau;
+    bool lin_done = false;   // a build from the local Jacobians leaves them stored at q
     if (ser || m % std::max(1, c->cfg.lag) == 0) {
       FR_TRY(frk::block_build(c, q, inv_dtau, a0dt, s));
       c->blocks_ready = 1;
       st->block_builds++;
+      lin_done = c->cfg.block_mode == FR_BLOCK_LINEARIZED;
     }
     int its = 0;
-    if (c->cfg.jvp_mode == FR_JVP_LINEARIZED) FR_TRY(frk::linearize(c, q, inv_dtau, a0dt, s));
+    if (c->cfg.jvp_mode == FR_JVP_LINEARIZED && !lin_done) FR_TRY(frk::linearize(c, q, inv_dtau, a0dt, s));
     FR_TRY(gmres_solve(c, q, r, inv_dtau, a0dt, c->w_x, &its, s));
     st->gmres_iterations[m] = its;
     const double prev = rm, prev_all = ra;
@@ -526,6 +528,7 @@ void fr_default_config(fr_config* c) {
   c->graphs = 1;
   c->apply_accum = FR_ACCUM_DF64;
   c->tiles = 1;
+  c->block_mode = FR_BLOCK_LINEARIZED;
 }
 
 int fr_create(const fr_config* cfg, fr_ctx** out) {
@@ -536,7 +539,8 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
       (cfg->gmres_side != FR_GMRES_LEFT && cfg->gmres_side != FR_GMRES_RIGHT) ||
       (cfg->jvp_mode != FR_JVP_DUAL && cfg->jvp_mode != FR_JVP_LINEARIZED) ||
       (cfg->apply_accum != FR_ACCUM_FP32 && cfg->apply_accum != FR_ACCUM_DF64) ||
-      cfg->tiles < 0 || cfg->tiles > 2)
+      cfg->tiles < 0 || cfg->tiles > 2 ||
+      (cfg->block_mode != FR_BLOCK_LINEARIZED && cfg->block_mode != FR_BLOCK_DUAL))
     return FR_ERR_ARG;
   fr_ctx* c = new fr_ctx();
   c->cfg = *cfg;

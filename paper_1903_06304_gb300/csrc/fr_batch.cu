@@ -281,12 +281,14 @@ int batch_newton(fr_ctx* c, double* q, const double* qcn, const double* qcnm1,
       c->cps[k].active = active[k];   // the kernels skip the elements of stopped cases
     }
     FR_TRY(frk::upload_cases(c, s));
+    bool lin_done = false;   // a build from the local Jacobians leaves them stored at q
     if (ser || m % std::max(1, cfg.lag) == 0) {
       FR_TRY(frk::block_build(c, q, 0.0, 0.0, s));
       c->blocks_ready = 1;
       for (int k = 0; k < nc; ++k) S[k]->block_builds += active[k];
+      lin_done = cfg.block_mode == FR_BLOCK_LINEARIZED;
     }
-    if (cfg.jvp_mode == FR_JVP_LINEARIZED) FR_TRY(frk::linearize(c, q, 0.0, 0.0, s));
+    if (cfg.jvp_mode == FR_JVP_LINEARIZED && !lin_done) FR_TRY(frk::linearize(c, q, 0.0, 0.0, s));
     FR_TRY(frk::gmres_cases(c, q, r, c->w_x, 0.0, 0.0, active, its, failed, s));
     for (int k = 0; k < nc; ++k) {
       if (active[k]) S[k]->gmres_iterations[mk[k]] = its[k];

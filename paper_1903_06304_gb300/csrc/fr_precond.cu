@@ -1,7 +1,8 @@
 // fr_precond.cu -- element block-Jacobi preconditioner for the Newton operator
 //   A = Gamma/dtau + (a0/dt) M - dR/dq^p        (Eq. unsteady_pre_discretized_3)
-// Build:  B_e = Gamma_e/dtau + (a0/dt) M_e - dR_e/dq_e  (neighbour states frozen),
-//         exact by forward mode, one CTA per element, 8 tangent directions in flight.
+// Build:  B_e = Gamma_e/dtau + (a0/dt) M_e - dR_e/dq_e  (neighbour states frozen), exact:
+//         from the stored local Jacobians (default) or by dual-number forward mode; one
+//         CTA per element, 8 columns in flight.
 // Factor: power-of-two row/column equilibration, in-place Gauss-Jordan inversion with
 //         partial pivoting in FP64 or FP32; stored transposed, scaled, in FP64, FP32 or
 //         BF16 (the FP32 inverse rounded).
@@ -202,6 +203,211 @@ k_block(const double* __restrict__ q, Mesh M, Basis B, const double* __restrict_
         dv = dv - th.qc[v] * divst;
         const double dR = -(dv.d * ij);
         Bout[((size_t)e * BS + v * NP + pt) * BS + d] = gmv[v] - dR;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ blocks from the linearisation
+// B_e from the stored local Jacobians (fr_linearize): the linearised operator restricted
+// to element e with the neighbours' inputs zero, one unit column at a time:
+//   traces and local gradient of the unit vector -> face fluxes through e's side of the
+//   face Jacobians (columns of q-/g- on e's R, T faces, of q+/g+ on its L, B faces), half
+//   of e's trace in the common solution -> corrected gradient -> point Jacobians ->
+//   corrected divergence plus the point block P'.
+// The element's face and point Jacobians are staged once in shared memory; BG columns
+// are in flight, one group of n^2 threads each.
+template <int N> struct BlkLinSmem {
+  static constexpr int NP = N * N;
+  static constexpr int JF = 4 * N * 48;   // [face][s][16 q-entries (r,c) | 32 g-entries (r,c)]
+  static constexpr int JPT = 112 * NP;    // [JP 32 | JG 64 | PP 16][point]
+  static constexpr int Q = 0, GL = Q + 4 * NP, TQ = GL + 8 * NP, TG = TQ + 16 * N,
+                       FN = TG + 32 * N, F = FN + 16 * N, G = F + 4 * NP, SIZE = G + 4 * NP;
+  static constexpr size_t BYTES = sizeof(double) * (JF + JPT + (size_t)BG * SIZE);
+};
+
+template <int N>
+__global__ void __launch_bounds__(BG * N * N)
+k_block_lin(Mesh M, Basis B, const double* __restrict__ gs, const double* __restrict__ gf,
+            const double* __restrict__ JFQ, const double* __restrict__ JFG,
+            const double* __restrict__ JP, const double* __restrict__ JG,
+            const double* __restrict__ PP, double* __restrict__ Bout) {
+  constexpr int NP = N * N, BS = 4 * NP;
+  using L = BlkLinSmem<N>;
+  extern __shared__ double smd[];
+  const int e = blockIdx.x;
+  if (!M.on(e)) return;
+  const int grp = threadIdx.x / NP, pt = threadIdx.x % NP;
+  const int i = pt % N, j = pt / N;
+  double* sJF = smd;
+  double* sJP = smd + L::JF;
+  double* S = smd + L::JF + L::JPT + grp * L::SIZE;
+  double* sq = S + L::Q;
+  double* sg = S + L::GL;
+  double* stq = S + L::TQ;
+  double* stg = S + L::TG;
+  double* sfn = S + L::FN;
+  double* sF = S + L::F;
+  double* sG = S + L::G;
+  const int nf = M.ne * 2 * N;
+  const size_t SN = (size_t)M.ne * NP, FNs = (size_t)M.ne * 4 * N;
+  const size_t o = (size_t)e * NP + pt;
+  const bool visc = M.viscous;
+  // stage this element's side of its four faces' Jacobians and its point Jacobians
+  for (int t = threadIdx.x; t < L::JF; t += blockDim.x) {
+    const int f = t / (N * 48), rem = t % (N * 48), sp = rem / 48, k = rem % 48;
+    const bool minus = (f == FACE_R || f == FACE_T);     // e owns its R and T faces
+    const int owner = f == FACE_R || f == FACE_T ? e : f == FACE_L ? M.left(e) : M.bottom(e);
+    const int dir = (f == FACE_R || f == FACE_L) ? 0 : 1;
+    const size_t idx = ((size_t)owner * 2 + dir) * N + sp;
+    double val;
+    if (k < 16) {
+      const int r = k / 4, cc = k % 4;
+      val = JFQ[(size_t)(r * 8 + (minus ? cc : 4 + cc)) * nf + idx];
+    } else {
+      const int r = (k - 16) / 8, cc = (k - 16) % 8;
+      val = visc ? JFG[(size_t)(r * 16 + (minus ? cc : 8 + cc)) * nf + idx] : 0.0;
+    }
+    sJF[t] = val;
+  }
+  for (int t = threadIdx.x; t < L::JPT; t += blockDim.x) {
+    const int r = t / NP, pp = t % NP;
+    const size_t oo = (size_t)e * NP + pp;
+    sJP[t] = r < 32 ? JP[(size_t)r * SN + oo]
+           : r < 96 ? (visc ? JG[(size_t)(r - 32) * SN + oo] : 0.0)
+                    : PP[(size_t)(r - 96) * SN + oo];
+  }
+  const double sxx = gs[GS_SXX * SN + o], sxy = gs[GS_SXY * SN + o];
+  const double sex = gs[GS_SEX * SN + o], sey = gs[GS_SEY * SN + o];
+  const double ij = gs[GS_INVJ * SN + o];
+  // lifting weights of the four faces at this point: S_f g_f' / |J|
+  double lsx[4], lsy[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const int sp = (f < 2) ? j : i;
+    const double w = (f == FACE_L) ? B.dgL[i] : (f == FACE_R) ? B.dgR[i]
+                   : (f == FACE_B) ? B.dgL[j] : B.dgR[j];
+    const size_t of = ((size_t)e * 4 + f) * N + sp;
+    lsx[f] = gf[GF_SX * FNs + of] * w * ij;
+    lsy[f] = gf[GF_SY * FNs + of] * w * ij;
+  }
+  __syncthreads();
+  for (int d0 = 0; d0 < BS; d0 += BG) {
+    const int d = d0 + grp;
+    const bool act = d < BS;
+    // A: unit column
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sq[v * NP + pt] = (act && v * NP + pt == d) ? 1.0 : 0.0;
+    __syncthreads();
+    // B: local gradient
+    if (visc) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double dxi = 0.0, deta = 0.0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          dxi = fma(B.D[i][k], sq[v * NP + j * N + k], dxi);
+          deta = fma(B.D[j][k], sq[v * NP + k * N + i], deta);
+        }
+        sg[v * NP + pt] = (sxx * dxi + sex * deta) * ij;
+        sg[(4 + v) * NP + pt] = (sxy * dxi + sey * deta) * ij;
+      }
+    }
+    __syncthreads();
+    // C: traces of the column and of its gradient
+    for (int t = pt; t < 4 * N; t += NP) {
+      const int f = t / N, sp = t % N;
+      const double* w = (f == FACE_L || f == FACE_B) ? B.lL : B.lR;
+      const bool row = (f == FACE_L || f == FACE_R);
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) acc = fma(w[k], sq[cc * NP + (row ? sp * N + k : k * N + sp)], acc);
+        stq[(f * 4 + cc) * N + sp] = acc;
+      }
+      if (visc) {
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) {
+          double acc = 0.0;
+#pragma unroll
+          for (int k = 0; k < N; ++k) acc = fma(w[k], sg[cc * NP + (row ? sp * N + k : k * N + sp)], acc);
+          stg[(f * 8 + cc) * N + sp] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    // D: face fluxes through e's side of the face Jacobians
+    for (int t = pt; t < 4 * N; t += NP) {
+      const int f = t / N, sp = t % N;
+      const double* jf = sJF + (f * N + sp) * 48;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        double acc = 0.0;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) acc = fma(jf[r * 4 + cc], stq[(f * 4 + cc) * N + sp], acc);
+        if (visc) {
+#pragma unroll
+          for (int cc = 0; cc < 8; ++cc) acc = fma(jf[16 + r * 8 + cc], stg[(f * 8 + cc) * N + sp], acc);
+        }
+        sfn[(f * 4 + r) * N + sp] = acc;
+      }
+    }
+    __syncthreads();
+    // E: corrected gradient (the common solution holds half of e's trace), point fluxes
+    double dq[4], g[8];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) dq[v] = sq[v * NP + pt];
+    double fg[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      double acc = 0.0;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) acc = fma(sJP[(r * 4 + cc) * NP + pt], dq[cc], acc);
+      fg[r] = acc;
+    }
+    if (visc) {
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) g[cc] = sg[cc * NP + pt];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int sp = (f < 2) ? j : i;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const double jump = -0.5 * stq[(f * 4 + v) * N + sp];
+          g[v] = fma(jump, lsx[f], g[v]);
+          g[4 + v] = fma(jump, lsy[f], g[4 + v]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        double acc = fg[r];
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) acc = fma(sJP[(32 + r * 8 + cc) * NP + pt], g[cc], acc);
+        fg[r] = acc;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { sF[v * NP + pt] = fg[v]; sG[v * NP + pt] = fg[4 + v]; }
+    __syncthreads();
+    // F: corrected divergence, point block, one block entry per row
+    if (act) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double dv = 0.0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) dv = fma(B.Dc[i][k], sF[v * NP + j * N + k], dv);
+#pragma unroll
+        for (int k = 0; k < N; ++k) dv = fma(B.Dc[j][k], sG[v * NP + k * N + i], dv);
+        dv = fma(B.dgL[i], sfn[(FACE_L * 4 + v) * N + j], dv);
+        dv = fma(B.dgR[i], sfn[(FACE_R * 4 + v) * N + j], dv);
+        dv = fma(B.dgL[j], sfn[(FACE_B * 4 + v) * N + i], dv);
+        dv = fma(B.dgR[j], sfn[(FACE_T * 4 + v) * N + i], dv);
+        double pv = 0.0;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) pv = fma(sJP[(96 + v * 4 + cc) * NP + pt], dq[cc], pv);
+        Bout[((size_t)e * BS + v * NP + pt) * BS + d] = fma(ij, dv, pv);
       }
     }
     __syncthreads();
@@ -436,7 +642,23 @@ using namespace fr;
 
 template <int N>
 static int block_build_n(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s) {
-  // value traces of every element (neighbour data of the blocks)
+  if (c->cfg.block_mode == FR_BLOCK_LINEARIZED) {
+    // from the local Jacobians at q (also the operator GMRES applies next)
+    FR_TRY(linearize(c, q, inv_dtau, a0_dt, s));
+    const bool visc = c->mesh.viscous;
+    // per element and unit column: gradient, traces, face products, point products, divergence
+    const double per_col = (double)N * N * (16.0 * N + 112.0) + 4.0 * N * (12.0 * N + 48.0);
+    FR_ACCOUNT(c, KK_BLOCK, 2.0 * c->ne * c->bsz * (visc ? per_col : 0.5 * per_col), 0.0);
+    const size_t smem = BlkLinSmem<N>::BYTES;
+    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_block_lin<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FR_PROF_BEGIN(c, s);
+    k_block_lin<N><<<c->ne, BG * N * N, smem, s>>>(c->mesh, c->basis, c->gs, c->gf, c->JFQ, c->JFG,
+                                                   c->JP, c->JG, c->PP, c->B64);
+    FR_PROF_END(c, s, KK_BLOCK);
+    FR_LAUNCH_CHECK(c);
+    return FR_OK;
+  }
+  // dual-number forward mode: value traces of every element (neighbour data of the blocks)
   constexpr int EPB = Tile<N>::EPB, TH = Tile<N>::THREADS;
   const int nblk = (c->ne + EPB - 1) / EPB;
   const bool visc = c->mesh.viscous;

@@ -43,7 +43,8 @@ class _Config(ctypes.Structure):
                 ("dtau_unsteady", ctypes.c_double), ("gmres_side", ctypes.c_int),
                 ("ser_unsteady", ctypes.c_int), ("dtau0_unsteady", ctypes.c_double),
                 ("line_search", ctypes.c_int), ("jvp_mode", ctypes.c_int),
-                ("graphs", ctypes.c_int), ("apply_accum", ctypes.c_int), ("tiles", ctypes.c_int)]
+                ("graphs", ctypes.c_int), ("apply_accum", ctypes.c_int), ("tiles", ctypes.c_int),
+                ("block_mode", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -188,6 +189,7 @@ class Config:
     graphs: int = 1
     apply_accum: str = "df64"
     tiles: int = 1
+    block_mode: str = "linearized"
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -199,6 +201,8 @@ class Config:
                 c.gmres_side = {"left": 0, "right": 1}[self.gmres_side]
             elif f.name == "jvp_mode":
                 c.jvp_mode = {"dual": 0, "linearized": 1}[self.jvp_mode]
+            elif f.name == "block_mode":
+                c.block_mode = {"linearized": 0, "dual": 1}[self.block_mode]
             elif f.name == "apply_accum":
                 c.apply_accum = {"fp32": 0, "df64": 1}[self.apply_accum]
             else:

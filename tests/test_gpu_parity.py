@@ -180,17 +180,24 @@ def test_jvp_of_zero_vector_is_zero(torch):
 
 @pytest.mark.parametrize("cfg", [CASES[i] for i in (0, 1, 2, 3, 6)])
 def test_block_parity(torch, cfg):
+    """Element blocks from the stored local Jacobians (default) and by dual numbers, both
+    against the oracle's coloured complex-step blocks."""
     nx, ny, p, mach, re, kappa, deforming = cfg
     c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
     prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
     inv_dtau, a0_dt = 0.5, 150.0
     want = sv.block_jacobian(prob, q, inv_dtau, a0_dt)
-    S = solver_for(c, v, nx, ny, p, mach, re, kappa)
-    S.precond_build(to_dev(q), inv_dtau, a0_dt)
-    B = torch.empty((nx * ny, S.block_size, S.block_size), dtype=torch.float64, device="cuda:0")
-    S.precond_blocks(B)
-    err = block_errors(to_host(B), want, (p + 1) ** 2)
-    assert np.all(err <= BLK_TOL), err
+    got = {}
+    for mode in ("linearized", "dual"):
+        S = solver_for(c, v, nx, ny, p, mach, re, kappa, block_mode=mode)
+        S.precond_build(to_dev(q), inv_dtau, a0_dt)
+        B = torch.empty((nx * ny, S.block_size, S.block_size), dtype=torch.float64, device="cuda:0")
+        S.precond_blocks(B)
+        got[mode] = to_host(B)
+        err = block_errors(got[mode], want, (p + 1) ** 2)
+        assert np.all(err <= BLK_TOL), (mode, err)
+    # the two constructions agree to rounding
+    assert np.all(block_errors(got["linearized"], got["dual"], (p + 1) ** 2) <= 1e-12)
 
 
 @pytest.mark.parametrize("prec,tol,accum", [("fp64", 1e-11, "df64"), ("fp32", 2e-4, "df64"),
@@ -327,6 +334,25 @@ def test_ptc_parity(torch):
 
 
 # ------------------------------------------------------------------ full workload sizes
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_free_stream_preserved_on_deforming_mesh(torch, p):
+    """The GCL invariant at the deforming benchmark's size (128x128, M = 0.01): a uniform
+    state on the moving mesh has zero residual to rounding, on the GPU as in the oracle."""
+    w = inp.NS_DEFORM_128
+    ref = inp.box_mesh(w.nx, w.ny, *w.box)
+    c, v = inp.deform(ref, 0.13, w.motion)
+    q = inp.uniform_state(w.nx * w.ny, p, w.mach, 0.8, 0.3)
+    S = solver_for(c, v, w.nx, w.ny, p, w.mach, w.re, w.kappa)
+    out = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+    S.residual(to_dev(q), out)
+    prob = oracle_problem(c, v, w.nx, w.ny, p, w.mach, w.re, w.kappa)
+    from oracle import scale as sc
+    sigma = sc.residual_scale(q, prob.mesh, p, prob.gas)
+    err = np.abs(to_host(out)).max(axis=(1, 2, 3)) / sigma
+    # the residual tolerance (rounding of the summed terms); measured <= 1.2e-13 at p = 4
+    assert np.all(err <= RES_TOL), err
+
 
 @pytest.mark.parametrize("w", [inp.NS_VORTEX_64, inp.NS_DEFORM_128], ids=lambda w: w.name)
 def test_full_size_residual_and_jvp(torch, w):
