@@ -88,7 +88,7 @@ typedef struct fr_ctx fr_ctx;
  * own sizes and keep the faster.  The two shapes compute the same operations per point
  * but are compiled separately, and their results agree to rounding (about 1e-14
  * relative), not bit for bit; a timed choice can therefore differ between runs;
- * graphs: if nonzero (default) and restart <= 32, GMRES iterations are issued in chunks of
+ * graphs: if nonzero (default) and restart <= 128, GMRES iterations are issued in chunks of
  * up to 10 whose kernel launches are captured once into a CUDA graph and replayed (same
  * results; fewer launch overheads); ignored while fr_profile timing is on. */
 #define FR_MAX_RESTART 256
@@ -303,7 +303,7 @@ int fr_param_vjp(fr_ctx* ctx, const double* qp_d, const double* w_d, const doubl
  * each in the single-case layout [4][Ne_k][n_k][n_k]; fr_batch_case_info gives case k's
  * offset and length (the cases of one group are adjacent, so offsets follow the group
  * order, not the case order).  Corner arrays concatenate [Ne_k][4][2] blocks at the
- * element offsets.  The restart length must be <= 32 (device-resident Arnoldi). */
+ * element offsets.  The restart length must be <= 128 (device-resident Arnoldi). */
 typedef struct fr_case {
   int p;                    /* polynomial degree 1..4 */
   int nx, ny;               /* doubly periodic box of nx x ny elements (>= 2 each) */

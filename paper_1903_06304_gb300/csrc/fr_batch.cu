@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <thread>
@@ -79,10 +80,11 @@ static int upload_coef(fr_ctx* c, const std::vector<double>& a, cudaStream_t s) 
   return FR_OK;
 }
 
+// The header of every case's GMRES state (the Hessenberg matrix needs no initial value).
 static int upload_gmres(fr_ctx* c, cudaStream_t s) {
   BatchWork& b = c->bw;
-  FR_CUDA_CHECK(c, cudaMemcpyAsync(b.gst, b.gst_h, c->ncases * sizeof(GmresState),
-                                   cudaMemcpyHostToDevice, s));
+  FR_CUDA_CHECK(c, cudaMemcpy2DAsync(b.gst, sizeof(GmresState), b.gst_h, sizeof(GmresState),
+                                     offsetof(GmresState, H), c->ncases, cudaMemcpyHostToDevice, s));
   FR_CUDA_CHECK(c, cudaEventRecord(b.staged, s));
   return FR_OK;
 }
@@ -93,7 +95,7 @@ static int op_apply(fr_ctx* c, const double* q, const double* x, double inv_dtau
   return frk::jvp(c, q, x, inv_dtau, a0_dt, out, s);
 }
 
-// Batched restarted GMRES(m <= 32): every active case solves its own A_k x_k = b_k with
+// Batched restarted GMRES(m <= 128): every active case solves its own A_k x_k = b_k with
 // its own Krylov space, tolerance and iteration limit; x is zero for inactive cases.
 int gmres_cases(fr_ctx* c, const double* q, const double* b, double* x, double inv_dtau,
                 double a0_dt, const std::vector<char>& active, std::vector<int>& iters,
@@ -127,7 +129,7 @@ int gmres_cases(fr_ctx* c, const double* q, const double* b, double* x, double i
       cyc[k] = active[k] && !failed[k] && bnorm[k] > 0.0 && beta[k] > tol * bnorm[k] &&
                total[k] < maxit;
       GmresState& h = c->bw.gst_h[k];
-      std::memset(&h, 0, sizeof(GmresState));
+      std::memset(&h, 0, offsetof(GmresState, H));
       if (cyc[k]) {
         h.g[0] = beta[k];
         h.tol = tol * bnorm[k];

@@ -8,17 +8,19 @@
 #include "fr_device.cuh"
 #include "../../include/fr.h"
 
-// Device-resident state of one GMRES restart cycle (restart <= 32).
+// Device-resident state of one GMRES restart cycle (restart <= 128).
 struct GmresState {
-  static constexpr int LD = 32;
-  double H[(LD + 1) * LD];
-  double cs[LD], sn[LD], g[LD + 1], y[LD];
+  static constexpr int LD = 128;   // longest restart cycle kept on the device
+  // header: set by the host at the start of a cycle (everything before H)
   double tol;      // absolute tolerance tol_res * ||b||
   double inv_hn;   // 1/||w|| of the newest vector
   int j;           // newest basis index = iterations done in this cycle
   int jmax;        // iteration limit of this cycle
   int done;
   int nonfinite;
+  double g[LD + 1], cs[LD], sn[LD], y[LD];
+  // Hessenberg matrix: column j is written by the Givens update of iteration j
+  double H[(LD + 1) * LD];
 };
 
 // Per-case partition of a batch's vectors for the batched vector kernels: block b works
@@ -231,7 +233,7 @@ int autotune_tiles(fr_ctx* c);
 // Per-case continuity-row and full norms of r (synchronises; bad[k] set for non-finite).
 int case_norms(fr_ctx* c, const double* r, std::vector<double>& mass, std::vector<double>& all,
                std::vector<char>& bad, cudaStream_t s);
-// Restarted GMRES(m <= 32) of every active case with device-resident Arnoldi (fr_batch.cu);
+// Restarted GMRES(m <= 128) of every active case with device-resident Arnoldi (fr_batch.cu);
 // inv_dtau, a0_dt feed the dual-number operator of a single-case context (a batch reads
 // its terms from the case table).
 int gmres_cases(fr_ctx* c, const double* q, const double* b, double* x, double inv_dtau,

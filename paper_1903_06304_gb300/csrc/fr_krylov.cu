@@ -721,7 +721,7 @@ int batch_setup(fr_ctx* c) {
   b.nblk = (int)bcase.size();
   if (bw_alloc(c, &b.bcase, b.nblk) || bw_alloc(c, &b.blo, b.nblk) || bw_alloc(c, &b.bhi, b.nblk) ||
       bw_alloc(c, &b.cb0, nc) || bw_alloc(c, &b.cnb, nc) || bw_alloc(c, &b.mend, nc) ||
-      bw_alloc(c, &b.partial, (size_t)32 * SPLIT * b.nblk) || bw_alloc(c, &b.tickets, nc) ||
+      bw_alloc(c, &b.partial, (size_t)GmresState::LD * SPLIT * b.nblk) || bw_alloc(c, &b.tickets, nc) ||
       bw_alloc(c, &b.dsc, (size_t)BDS * nc) || bw_alloc(c, &b.gst, nc) ||
       bw_alloc(c, &b.status, nc) || bw_alloc(c, &b.coef, nc) ||
       bw_alloc_host(c, &b.hsc, (size_t)BDS * nc) || bw_alloc_host(c, &b.gst_h, nc) ||

@@ -84,7 +84,7 @@ def test_bad_batch_rejected_without_gpu():
         assert lib.fr_batch_create(ctypes.byref(c), ctypes.cast(arr, ctypes.c_void_p), 2,
                                    ctypes.byref(h)) == -1
         assert not h.value
-    c.restart = 40   # the batched Arnoldi keeps at most 32 vectors on the device
+    c.restart = 200   # the batched Arnoldi keeps at most 128 vectors on the device
     arr = (fr._Case * 1)(good)
     assert lib.fr_batch_create(ctypes.byref(c), ctypes.cast(arr, ctypes.c_void_p), 1,
                                ctypes.byref(h)) == -1

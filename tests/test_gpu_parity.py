@@ -250,8 +250,9 @@ def test_block_apply_double_float_is_linear(torch, prec):
     assert dev["fp32"] > 100 * dev["df64"], dev
 
 
-# restart <= 32: device-resident Arnoldi; restart 40: the host-Givens path
-@pytest.mark.parametrize("side,restart", [("left", 10), ("right", 10), ("left", 40), ("right", 40)])
+# restart <= 128: device-resident Arnoldi; restart 140: the host-Givens path
+@pytest.mark.parametrize("side,restart", [("left", 10), ("right", 10), ("left", 40), ("right", 40),
+                                          ("left", 140)])
 def test_gmres_parity(torch, side, restart):
     nx, ny, p, mach, re, kappa, deforming = 4, 4, 2, 0.05, 10.0, 1.0, True
     c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
