@@ -202,17 +202,20 @@ __global__ void k_lin_face_apply(Mesh M, const double* __restrict__ tqv,
     out[r] = s;
   }
   if (M.viscous) {
+    // the viscous flux has no mass component and does not depend on the pressure
+    // gradient: row 0 and the columns of p_x, p_y (c % 4 == 0) of JFG are exact zeros
     double g[16];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      g[c] = tgv[(((size_t)e * 4 + fm) * 8 + c) * N + t];
-      g[8 + c] = tgv[(((size_t)plus * 4 + fp) * 8 + c) * N + t];
+      g[c] = c % 4 ? tgv[(((size_t)e * 4 + fm) * 8 + c) * N + t] : 0.0;
+      g[8 + c] = c % 4 ? tgv[(((size_t)plus * 4 + fp) * 8 + c) * N + t] : 0.0;
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 1; r < 4; ++r) {
       double s = out[r];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) s = fma(JFG[(size_t)(r * 16 + c) * nf + idx], g[c], s);
+      for (int c = 0; c < 16; ++c)
+        if (c % 4) s = fma(JFG[(size_t)(r * 16 + c) * nf + idx], g[c], s);
       out[r] = s;
     }
   }
@@ -279,11 +282,15 @@ k_lin_elem_apply(const double* __restrict__ v, Mesh M, Basis B,
           g[4 + c] += jump * sy;
         }
       }
+      // rows of the mass fluxes (r = 0, 4) and columns of p_x, p_y (c = 0, 4) of JG are
+      // exact zeros (no viscous mass flux, no pressure-gradient dependence)
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
+        if (r % 4 == 0) continue;
         double s = fg[r];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) s = fma(JG[(size_t)(r * 8 + c) * SN + o], g[c], s);
+        for (int c = 0; c < 8; ++c)
+          if (c % 4) s = fma(JG[(size_t)(r * 8 + c) * SN + o], g[c], s);
         fg[r] = s;
       }
     }
@@ -576,8 +583,9 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
   const double np = (double)c->ne * N * N;
   // algorithmic flops of the linear operator per solution point and per owned flux point
   const double fl_trace = fr_flops_trace(N, visc);
-  const double fl_face = 2.0 * (4 * 8 + (visc ? 4 * 16 : 0)) + 8.0;
-  const double fl_elem = 2.0 * (8 * 4 + (visc ? 8 * 8 : 0)) + (visc ? 96.0 : 0.0) +
+  // (the gradient Jacobians' non-zero part: 3 x 12 at a face point, 6 x 6 at a point)
+  const double fl_face = 2.0 * (4 * 8 + (visc ? 3 * 12 : 0)) + 8.0;
+  const double fl_elem = 2.0 * (8 * 4 + (visc ? 6 * 6 : 0)) + (visc ? 96.0 : 0.0) +
                          4.0 * (4.0 * N + 8.0 + 8.0 + 2.0);
   if (!transpose) {
     {

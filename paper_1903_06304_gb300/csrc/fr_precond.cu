@@ -347,9 +347,10 @@ k_block_lin(Mesh M, Basis B, const double* __restrict__ gs, const double* __rest
         double acc = 0.0;
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) acc = fma(jf[r * 4 + cc], stq[(f * 4 + cc) * N + sp], acc);
-        if (visc) {
+        if (visc && r > 0) {   // exact zeros: mass row, pressure-gradient columns
 #pragma unroll
-          for (int cc = 0; cc < 8; ++cc) acc = fma(jf[16 + r * 8 + cc], stg[(f * 8 + cc) * N + sp], acc);
+          for (int cc = 0; cc < 8; ++cc)
+            if (cc % 4) acc = fma(jf[16 + r * 8 + cc], stg[(f * 8 + cc) * N + sp], acc);
         }
         sfn[(f * 4 + r) * N + sp] = acc;
       }
@@ -382,9 +383,11 @@ k_block_lin(Mesh M, Basis B, const double* __restrict__ gs, const double* __rest
       }
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
+        if (r % 4 == 0) continue;   // exact zeros: mass rows, pressure-gradient columns
         double acc = fg[r];
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) acc = fma(sJP[(32 + r * 8 + cc) * NP + pt], g[cc], acc);
+        for (int cc = 0; cc < 8; ++cc)
+          if (cc % 4) acc = fma(sJP[(32 + r * 8 + cc) * NP + pt], g[cc], acc);
         fg[r] = acc;
       }
     }
@@ -647,7 +650,7 @@ static int block_build_n(fr_ctx* c, const double* q, double inv_dtau, double a0_
     FR_TRY(linearize(c, q, inv_dtau, a0_dt, s));
     const bool visc = c->mesh.viscous;
     // per element and unit column: gradient, traces, face products, point products, divergence
-    const double per_col = (double)N * N * (16.0 * N + 112.0) + 4.0 * N * (12.0 * N + 48.0);
+    const double per_col = (double)N * N * (16.0 * N + 84.0) + 4.0 * N * (12.0 * N + 34.0);
     FR_ACCOUNT(c, KK_BLOCK, 2.0 * c->ne * c->bsz * (visc ? per_col : 0.5 * per_col), 0.0);
     const size_t smem = BlkLinSmem<N>::BYTES;
     FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_block_lin<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
