@@ -6,7 +6,8 @@
 // Factor: power-of-two row/column equilibration, in-place Gauss-Jordan inversion with
 //         partial pivoting in FP64 or FP32; stored transposed, scaled, in FP64, FP32 or
 //         BF16 (the FP32 inverse rounded).
-// Apply:  z_e = Dc (B~_e^-1 (Dr r_e)), FP64 in/out, FP32 accumulation for FP32/BF16.
+// Apply:  z_e = Dc (B~_e^-1 (Dr r_e)), FP64 in/out; FP32/BF16 inverses applied with
+//         double-float accumulation on the FP32 pipe (default) or in plain FP32.
 #include <cstdio>
 #include <cuda_bf16.h>
 #include "fr_internal.h"
