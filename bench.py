@@ -120,6 +120,20 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------------------ replicas
+def replica_throughput(t_rank: float, units_per_rank: float, world: int, dist, device):
+    """Whole-job throughput of `world` replicas: the slowest rank's time (all-reduce MAX
+    over the ranks, or the local time on one rank) and the units all ranks processed per
+    second over it, in billions.  Returns (t_max, value)."""
+    import torch
+    t_max = t_rank
+    if dist is not None and world > 1:
+        tt = torch.tensor([t_rank], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    return t_max, units_per_rank * world / t_max / 1e9
+
+
 # ------------------------------------------------------------------ CPU oracle sample
 def oracle_sample(steps: int, warmup: int):
     """The oracle as it stands on a bounded sample: BDF2 steps on the 16x16 sub-box."""
@@ -306,14 +320,8 @@ def gpu_arm(args):
     ms, stats, launches = timed_steps(run, args.steps)
     clock_info = clocks.stop()
     t_rank = sum(ms) / 1e3
-    if dist is not None:
-        tt = torch.tensor([t_rank], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    else:
-        t_max = t_rank
     dof = S.ndof
-    value = dof * args.steps * world / t_max / 1e9
+    t_max, value = replica_throughput(t_rank, dof * args.steps, world, dist, dev)
     ms_per_step = t_max * 1e3 / args.steps
 
     # ---- per-kernel device time over the same number of steps (profiling pass)
@@ -460,12 +468,9 @@ def gpu_arm(args):
             evs.append((a, b))
         barrier()
         t_e2e = sum(a.elapsed_time(b) for a, b in evs) / 1e3
-        if dist is not None:
-            tt = torch.tensor([t_e2e], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
+        t_e2e, e2e_value = replica_throughput(t_e2e, dof * args.steps, world, dist, dev)
         nb = run.q.numel() * 8
-        e2e = {"value": dof * args.steps * world / t_e2e / 1e9, "unit": UNIT,
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 3 * nb, "d2h_bytes_per_step": 3 * nb}
 
     # ---- CPU baseline (rank 0, N = 1 only)
