@@ -265,7 +265,7 @@ def gpu_arm(args):
                         restart=args.restart, maxit_lin=args.maxit_lin, tol_res=w.tol_res,
                         tol_pseudo=w.tol_pseudo, maxit_newton=args.maxit_newton, lag=2,
                         line_search=args.line_search, graphs=args.graphs,
-                        apply_accum=args.apply_accum, tiles=args.tiles)
+                        apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog)
         S = fr.Solver(cfg, w.nx, w.ny)
         S.update_mesh(T(corners), T(vel))
         return S
@@ -398,7 +398,7 @@ def gpu_arm(args):
     # per-iteration time does not depend on the Newton history
     gm_cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
                        restart=args.restart, maxit_lin=120, tol_res=1e-30, graphs=args.graphs,
-                       apply_accum=args.apply_accum)
+                       apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog)
     Sg = fr.Solver(gm_cfg, w.nx, w.ny)
     Sg.update_mesh(T(corners), T(vel))
     Sg.precond_build(run.q, 1e-20, 1.5 / w.dt)
@@ -495,7 +495,7 @@ def gpu_arm(args):
         "config": {"workload": w.name, "mesh": f"{w.nx}x{w.ny} periodic [0,10]^2",
                    "p": w.p, "dof": dof, "mach": w.mach, "re_ref": w.re, "kappa": w.kappa,
                    "dt": w.dt, "tol_pseudo": w.tol_pseudo, "tol_res": w.tol_res,
-                   "gmres": f"GMRES({args.restart}) left-preconditioned, maxit {args.maxit_lin}",
+                   "gmres": f"GMRES({args.restart}) left-preconditioned, {args.orthog}, maxit {args.maxit_lin}",
                    "newton": f"max {args.maxit_newton} iterations, backtracking {args.line_search} halvings",
                    "precond": f"element block-Jacobi, {args.prec} blocks, {args.apply_accum} apply accumulation",
                    "l2": "256 MiB write between timed steps, outside the per-step events",
@@ -654,6 +654,8 @@ def main():
                     help="backtracking halvings per Newton update (0: plain Newton)")
     ap.add_argument("--apply-accum", dest="apply_accum", default="df64", choices=["df64", "fp32"],
                     help="block-apply arithmetic with FP32/BF16-stored inverses")
+    ap.add_argument("--orthog", default="cgs2", choices=["cgs2", "cgs"],
+                    help="Arnoldi orthogonalisation: CGS2, or one classical pass (PETSc's default)")
     ap.add_argument("--tiles", type=int, default=0, choices=[0, 1, 2],
                     help="elements per CTA of the point kernels: 0 autotuned at set-up, 1 or 2 fixed")
     ap.add_argument("--graphs", type=int, default=1,

@@ -80,6 +80,9 @@ typedef struct fr_ctx fr_ctx;
  * round-off while it runs on the FP32 pipe; FR_ACCUM_FP32 rounds the input and
  * accumulates in plain FP32 (a state-dependent perturbation with which GMRES can stall
  * on stiff cases);
+ * orthog: Arnoldi orthogonalisation: FR_ORTHO_CGS2 (default) classical Gram-Schmidt with
+ * one re-orthogonalisation; FR_ORTHO_CGS a single classical pass (PETSc's default
+ * refinement setting, "never"), about half the Arnoldi work;
  * block_mode: how the element blocks are formed, both exact: FR_BLOCK_LINEARIZED
  * (default) composes them from the stored local Jacobians (fr_linearize, done by the
  * build), FR_BLOCK_DUAL differentiates each element's residual by dual numbers;
@@ -100,6 +103,8 @@ typedef struct fr_ctx fr_ctx;
 #define FR_ACCUM_DF64 1
 #define FR_BLOCK_LINEARIZED 0
 #define FR_BLOCK_DUAL 1
+#define FR_ORTHO_CGS2 0
+#define FR_ORTHO_CGS 1
 typedef struct fr_config {
   int p;
   double gamma, prandtl, mach, re, kappa, eps_floor;
@@ -116,6 +121,7 @@ typedef struct fr_config {
   int apply_accum;
   int tiles;
   int block_mode;
+  int orthog;
 } fr_config;
 
 /* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).

@@ -179,8 +179,11 @@ class GmresResult:
     res_history: list
 
 
-def gmres(Aop, b, Minv, restart: int, tol: float, maxit: int, side: str = "left") -> GmresResult:
-    """Restarted preconditioned GMRES(m) with CGS2 Arnoldi (see module notes).
+def gmres(Aop, b, Minv, restart: int, tol: float, maxit: int, side: str = "left",
+          passes: int = 2) -> GmresResult:
+    """Restarted preconditioned GMRES(m) with CGS2 Arnoldi (see module notes); passes=1
+    is classical Gram-Schmidt without re-orthogonalisation (PETSc's default refinement
+    setting, "never").
 
     side="left" (the default of PETSc, whose solver the paper uses): Krylov space of
     M^-1 A, the preconditioned residual M^-1 (b - A x) is minimised and tested against
@@ -220,9 +223,12 @@ def gmres(Aop, b, Minv, restart: int, tol: float, maxit: int, side: str = "left"
                 w = Aop(Minv(V[j].reshape(shape))).ravel()
             h1 = V[: j + 1] @ w
             w = w - V[: j + 1].T @ h1
-            h2 = V[: j + 1] @ w
-            w = w - V[: j + 1].T @ h2
-            H[: j + 1, j] = h1 + h2
+            if passes == 2:
+                h2 = V[: j + 1] @ w
+                w = w - V[: j + 1].T @ h2
+                H[: j + 1, j] = h1 + h2
+            else:
+                H[: j + 1, j] = h1
             hn = np.linalg.norm(w)
             H[j + 1, j] = hn
             if hn > 0:

@@ -229,6 +229,16 @@ int norms_host(fr_ctx* c, const double* r, double* mass, double* all, cudaStream
 int cgs2(fr_ctx* c, int nv, double* w, cudaStream_t s) {
   constexpr int CH = 32, M = FR_MAX_RESTART;
   const size_t N = c->ndof;
+  if (c->cfg.orthog == FR_ORTHO_CGS) {
+    // one classical pass: projections at dsc[0..nv), the second set zero
+    FR_CUDA_CHECK(c, cudaMemsetAsync(c->dsc + M, 0, nv * sizeof(double), s));
+    for (int k0 = 0; k0 < nv; k0 += CH)
+      FR_TRY(frk::dots(c, c->V + (size_t)k0 * N, std::min(CH, nv - k0), w, c->dsc + k0, s));
+    for (int k0 = 0; k0 + CH < nv; k0 += CH)
+      FR_TRY(frk::axpy(c, c->V + (size_t)k0 * N, CH, c->dsc + k0, w, s));
+    const int last = ((nv - 1) / CH) * CH;
+    return frk::axpy_norm(c, c->V + (size_t)last * N, nv - last, c->dsc + last, w, c->dsc + 2 * M, s);
+  }
   if (nv <= CH) {
     FR_TRY(frk::dots(c, c->V, nv, w, c->dsc, s));
     FR_TRY(frk::axpy_dots(c, c->V, nv, c->dsc, w, c->dsc + M, s));
@@ -529,6 +539,7 @@ void fr_default_config(fr_config* c) {
   c->apply_accum = FR_ACCUM_DF64;
   c->tiles = 1;
   c->block_mode = FR_BLOCK_LINEARIZED;
+  c->orthog = FR_ORTHO_CGS2;
 }
 
 int fr_create(const fr_config* cfg, fr_ctx** out) {
@@ -540,7 +551,8 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
       (cfg->jvp_mode != FR_JVP_DUAL && cfg->jvp_mode != FR_JVP_LINEARIZED) ||
       (cfg->apply_accum != FR_ACCUM_FP32 && cfg->apply_accum != FR_ACCUM_DF64) ||
       cfg->tiles < 0 || cfg->tiles > 2 ||
-      (cfg->block_mode != FR_BLOCK_LINEARIZED && cfg->block_mode != FR_BLOCK_DUAL))
+      (cfg->block_mode != FR_BLOCK_LINEARIZED && cfg->block_mode != FR_BLOCK_DUAL) ||
+      (cfg->orthog != FR_ORTHO_CGS2 && cfg->orthog != FR_ORTHO_CGS))
     return FR_ERR_ARG;
   fr_ctx* c = new fr_ctx();
   c->cfg = *cfg;

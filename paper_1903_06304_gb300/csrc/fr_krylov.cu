@@ -246,7 +246,7 @@ __device__ void gm_givens(GmresState* st, const double* h1, const double* h2, co
   constexpr int L = GmresState::LD;
   const double hn = sqrt(nrm2[0]);
   if (!isfinite(hn)) { st->nonfinite = 1; st->done = 1; return; }
-  for (int i = 0; i <= j; ++i) st->H[i * L + j] = h1[i] + h2[i];
+  for (int i = 0; i <= j; ++i) st->H[i * L + j] = h2 ? h1[i] + h2[i] : h1[i];
   st->H[(j + 1) * L + j] = hn;
   for (int i = 0; i < j; ++i) {
     const double a = st->H[i * L + j], b = st->H[(i + 1) * L + j];
@@ -398,7 +398,7 @@ template <bool NORM>
 __global__ void __launch_bounds__(RT) k_vaxpy(const double* __restrict__ V, size_t ld, double* w,
                                               BatchSegs sg, double* __restrict__ partial,
                                               double* dsc, int h_off, unsigned int* tickets,
-                                              GmresState* gst) {
+                                              GmresState* gst, int two_pass) {
   __shared__ double hs[GmresState::LD + 1];
   const int b = blockIdx.x, part = blockIdx.y;
   const int k = sg.bcase[b];
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(RT) k_vaxpy(const double* __restrict__ V, size
   const bool last = seg_reduce(acc, 1, 0, partial, (size_t)gridDim.x * SPLIT, pb, ds + 2 * BM, 1,
                                tickets + k, (unsigned)(sg.cnb[k] * SPLIT),
                                (size_t)sg.cb0[k] * SPLIT, sg.cnb[k] * SPLIT);
-  if (last && threadIdx.x == 0) gm_givens(st, ds, ds + BM, ds + 2 * BM);
+  if (last && threadIdx.x == 0) gm_givens(st, ds, two_pass ? ds + BM : nullptr, ds + 2 * BM);
 }
 
 // CGS2 middle step in one pass: w -= sum_k h1_k V_k over this block's part of a range
@@ -762,15 +762,18 @@ int bk_init(fr_ctx* c, const double* r, double* next, cudaStream_t s) {
 int bk_orthogonalize(fr_ctx* c, double* w, double* next, int nv_bound, cudaStream_t s) {
   BatchWork& b = c->bw;
   const dim3 gdots(b.nblk, (nv_bound + KG - 1) / KG), gaxpy(b.nblk, SPLIT);
+  const bool two = c->cfg.orthog == FR_ORTHO_CGS2;
   // CGS2: h1 = V^T w; (w -= V h1, h2 = V^T w); (w -= V h2, ||w||, Givens); V[j+1] = w/||w||
-  FR_ACCOUNT(c, KK_KRYLOV, 8.0 * nv_bound * c->ndof + 2.0 * c->ndof, 8.0 * c->ndof * (4.0 * nv_bound + 6.0));
+  // CGS:  h1 = V^T w; (w -= V h1, ||w||, Givens); V[j+1] = w/||w||
+  FR_ACCOUNT(c, KK_KRYLOV, (two ? 8.0 : 4.0) * nv_bound * c->ndof + 2.0 * c->ndof,
+             8.0 * c->ndof * ((two ? 4.0 : 2.0) * nv_bound + 6.0));
   {
     FR_PROF_BEGIN(c, s);
     k_vdots<<<gdots, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, 0, b.tickets, b.gst);
     FR_PROF_END(c, s, KK_KRYLOV);
     FR_LAUNCH_CHECK(c);
   }
-  {
+  if (two) {
     FR_PROF_BEGIN(c, s);
     k_vaxdots<<<gaxpy, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, b.tickets, b.gst);
     FR_PROF_END(c, s, KK_KRYLOV);
@@ -778,7 +781,8 @@ int bk_orthogonalize(fr_ctx* c, double* w, double* next, int nv_bound, cudaStrea
   }
   {
     FR_PROF_BEGIN(c, s);
-    k_vaxpy<true><<<gaxpy, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, BM, b.tickets, b.gst);
+    k_vaxpy<true><<<gaxpy, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, two ? BM : 0,
+                                       b.tickets, b.gst, two ? 1 : 0);
     FR_PROF_END(c, s, KK_KRYLOV);
     FR_LAUNCH_CHECK(c);
   }

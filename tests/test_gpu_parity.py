@@ -250,10 +250,13 @@ def test_block_apply_double_float_is_linear(torch, prec):
     assert dev["fp32"] > 100 * dev["df64"], dev
 
 
-# restart <= 128: device-resident Arnoldi; restart 140: the host-Givens path
-@pytest.mark.parametrize("side,restart", [("left", 10), ("right", 10), ("left", 40), ("right", 40),
-                                          ("left", 140)])
-def test_gmres_parity(torch, side, restart):
+# restart <= 128: device-resident Arnoldi; restart 140: the host-Givens path; CGS2 (the
+# default) and one classical pass
+@pytest.mark.parametrize("side,restart,orthog", [("left", 10, "cgs2"), ("right", 10, "cgs2"),
+                                                 ("left", 40, "cgs2"), ("right", 40, "cgs2"),
+                                                 ("left", 140, "cgs2"), ("left", 10, "cgs"),
+                                                 ("right", 40, "cgs"), ("left", 140, "cgs")])
+def test_gmres_parity(torch, side, restart, orthog):
     nx, ny, p, mach, re, kappa, deforming = 4, 4, 2, 0.05, 10.0, 1.0, True
     c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
     prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
@@ -262,9 +265,9 @@ def test_gmres_parity(torch, side, restart):
     Binv = np.linalg.inv(sv.block_jacobian(prob, q, inv_dtau, a0_dt))
     P = lambda x: sv.block_apply(Binv, x)
     want = sv.gmres(lambda x: sv.apply_A(prob, q, x, inv_dtau, a0_dt), b, P, restart, 1e-8, 200,
-                    side=side)
+                    side=side, passes=2 if orthog == "cgs2" else 1)
     S = solver_for(c, v, nx, ny, p, mach, re, kappa, restart=restart, maxit_lin=200,
-                   tol_res=1e-8, gmres_side=side)
+                   tol_res=1e-8, gmres_side=side, orthog=orthog)
     qd = to_dev(q)
     S.precond_build(qd, inv_dtau, a0_dt)
     x = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")

@@ -86,21 +86,24 @@ def test_residual_stencil_is_face_neighbours_only():
     assert touched == {12, 11, 13, 7, 17}
 
 
-def test_gmres_matches_direct_solve_with_restarts():
+@pytest.mark.parametrize("passes", [2, 1])
+def test_gmres_matches_direct_solve_with_restarts(passes):
     rng = np.random.default_rng(0)
     N = 60
     A = np.eye(N) * 4 + rng.standard_normal((N, N)) * 0.3
     b = rng.standard_normal(N)
     P = np.diag(1 / np.diag(A))
     for side in ("left", "right"):
-        out = sv.gmres(lambda v: A @ v, b, lambda v: P @ v, 10, 1e-12, 500, side=side)
+        out = sv.gmres(lambda v: A @ v, b, lambda v: P @ v, 10, 1e-12, 500, side=side,
+                       passes=passes)
         assert out.converged
         np.testing.assert_allclose(out.x, np.linalg.solve(A, b), atol=1e-10)
     np.testing.assert_allclose(out.x, np.linalg.solve(A, b), atol=1e-10)
 
 
+@pytest.mark.parametrize("passes", [2, 1])
 @pytest.mark.parametrize("side", ["left", "right"])
-def test_gmres_minimal_residual_property(side):
+def test_gmres_minimal_residual_property(side, passes):
     """Without restart, after k steps GMRES attains the least-squares minimum over its
     Krylov space (library lstsq on an explicit basis): right preconditioning minimises
     ||b - A x|| over x in P K_k(A P, b); left preconditioning minimises ||P (b - A x)||
@@ -110,7 +113,7 @@ def test_gmres_minimal_residual_property(side):
     A = np.eye(N) * 3 + rng.standard_normal((N, N)) * 0.5
     P = np.diag(1.0 + rng.uniform(0, 1, N))
     b = rng.standard_normal(N)
-    out = sv.gmres(lambda v: A @ v, b, lambda v: P @ v, 50, 0.0, k, side=side)
+    out = sv.gmres(lambda v: A @ v, b, lambda v: P @ v, 50, 0.0, k, side=side, passes=passes)
     if side == "right":
         K = np.stack([np.linalg.matrix_power(A @ P, i) @ b for i in range(k)], axis=1)
         Q, _ = np.linalg.qr(K)
