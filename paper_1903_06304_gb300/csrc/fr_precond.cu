@@ -423,50 +423,63 @@ template <class W> __device__ __forceinline__ W wabs(W x) { return x < 0 ? -x : 
 
 // In-place Gauss-Jordan inversion with partial (row) pivoting of the equilibrated block,
 // one CTA per element; writes the transposed scaled inverse and the scales.
-template <class W, class S>
-__global__ void k_factor(const double* __restrict__ Bin, int bs, S* __restrict__ Aout,
+template <class W, class S, int N>
+__global__ void k_factor(const double* __restrict__ Bin, S* __restrict__ Aout,
                          float* __restrict__ Dr, float* __restrict__ Dc, int* __restrict__ info,
                          Mesh M) {
+  constexpr int BS = 4 * N * N, LDA = BS + 1;       // padded rows: conflict-free columns
   extern __shared__ unsigned char smraw[];
-  W* A = reinterpret_cast<W*>(smraw);               // [bs][bs] row-major
-  W* col = A + bs * bs;                             // [bs]
-  float* dr = reinterpret_cast<float*>(col + bs);   // [bs]
-  float* dc = dr + bs;                              // [bs]
-  int* perm = reinterpret_cast<int*>(dc + bs);      // [bs]
+  W* A = reinterpret_cast<W*>(smraw);               // [BS][LDA] row-major
+  W* col = A + BS * LDA;                            // [BS]
+  float* dr = reinterpret_cast<float*>(col + BS);   // [BS]
+  float* dc = dr + BS;                              // [BS]
+  int* perm = reinterpret_cast<int*>(dc + BS);      // [BS]
   __shared__ int s_piv;
   __shared__ int s_bad;
   const int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   if (!M.on(e)) return;
-  const double* Be = Bin + (size_t)e * bs * bs;
+  const double* Be = Bin + (size_t)e * BS * BS;
   if (tid == 0) s_bad = 0;
-  // row scales: 2^-round(log2(max |B_ij|)) over the row
-  for (int r = tid; r < bs; r += nt) {
-    double m = 0.0;
-    for (int c2 = 0; c2 < bs; ++c2) m = fmax(m, fabs(Be[(size_t)r * bs + c2]));
-    int ex = 0;
-    if (m > 0.0) frexp(m, &ex);
-    dr[r] = m > 0.0 ? ldexpf(1.0f, -ex) : 1.0f;
+  // stage the block in the working precision (coalesced); the power-of-two scales below
+  // are exact in either precision
+  for (int idx = tid; idx < BS * BS; idx += nt) A[(idx / BS) * LDA + idx % BS] = (W)Be[idx];
+  __syncthreads();
+  // row scales 2^-e with e the exponent of the row's largest |entry|: a warp per row
+  for (int r = wid; r < BS; r += nw) {
+    W m = 0;
+    for (int c2 = lane; c2 < BS; c2 += 32) m = fmax(m, wabs(A[r * LDA + c2]));
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) {
+      int ex = 0;
+      if (m > (W)0) frexp(m, &ex);
+      dr[r] = m > (W)0 ? ldexpf(1.0f, -ex) : 1.0f;
+    }
   }
   __syncthreads();
-  for (int c2 = tid; c2 < bs; c2 += nt) {
-    double m = 0.0;
-    for (int r = 0; r < bs; ++r) m = fmax(m, fabs(Be[(size_t)r * bs + c2]) * (double)dr[r]);
-    int ex = 0;
-    if (m > 0.0) frexp(m, &ex);
-    dc[c2] = m > 0.0 ? ldexpf(1.0f, -ex) : 1.0f;
+  // column scales of the row-scaled block: a warp per column
+  for (int c2 = wid; c2 < BS; c2 += nw) {
+    W m = 0;
+    for (int r = lane; r < BS; r += 32) m = fmax(m, wabs(A[r * LDA + c2]) * (W)dr[r]);
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) {
+      int ex = 0;
+      if (m > (W)0) frexp(m, &ex);
+      dc[c2] = m > (W)0 ? ldexpf(1.0f, -ex) : 1.0f;
+    }
   }
   __syncthreads();
-  for (int idx = tid; idx < bs * bs; idx += nt) {
-    const int r = idx / bs, c2 = idx % bs;
-    A[idx] = (W)(Be[idx] * (double)dr[r] * (double)dc[c2]);
+  for (int idx = tid; idx < BS * BS; idx += nt) {
+    const int r = idx / BS, c2 = idx % BS;
+    A[r * LDA + c2] = A[r * LDA + c2] * (W)dr[r] * (W)dc[c2];
   }
   __syncthreads();
-  for (int k = 0; k < bs; ++k) {
-    if (tid < 32) {  // pivot search in column k, rows k..bs-1 (first max wins)
+  for (int k = 0; k < BS; ++k) {
+    if (tid < 32) {  // pivot search in column k, rows k..BS-1 (first max wins)
       W best = (W)-1;
       int bi = k;
-      for (int r = k + tid; r < bs; r += 32) {
-        const W a = wabs(A[r * bs + k]);
+      for (int r = k + tid; r < BS; r += 32) {
+        const W a = wabs(A[r * LDA + k]);
         if (a > best) { best = a; bi = r; }
       }
       for (int off = 16; off > 0; off >>= 1) {
@@ -479,37 +492,37 @@ __global__ void k_factor(const double* __restrict__ Bin, int bs, S* __restrict__
     __syncthreads();
     const int pr = s_piv;
     if (pr != k)
-      for (int c2 = tid; c2 < bs; c2 += nt) { const W t = A[k * bs + c2]; A[k * bs + c2] = A[pr * bs + c2]; A[pr * bs + c2] = t; }
+      for (int c2 = tid; c2 < BS; c2 += nt) { const W t = A[k * LDA + c2]; A[k * LDA + c2] = A[pr * LDA + c2]; A[pr * LDA + c2] = t; }
     __syncthreads();
-    const W piv = A[k * bs + k];
+    const W piv = A[k * LDA + k];
     const W rp = piv != (W)0 ? (W)1 / piv : (W)0;
-    for (int r = tid; r < bs; r += nt) col[r] = A[r * bs + k];
+    for (int r = tid; r < BS; r += nt) col[r] = A[r * LDA + k];
     __syncthreads();
-    for (int c2 = tid; c2 < bs; c2 += nt) A[k * bs + c2] = (c2 == k ? (W)1 : A[k * bs + c2]) * rp;
+    for (int c2 = tid; c2 < BS; c2 += nt) A[k * LDA + c2] = (c2 == k ? (W)1 : A[k * LDA + c2]) * rp;
     __syncthreads();
-    for (int idx = tid; idx < bs * bs; idx += nt) {
-      const int r = idx / bs, c2 = idx % bs;
+    for (int idx = tid; idx < BS * BS; idx += nt) {
+      const int r = idx / BS, c2 = idx % BS;
       if (r == k) continue;
       const W f = col[r];
-      const W akc = A[k * bs + c2];
-      A[idx] = (c2 == k ? (W)0 : A[idx]) - f * akc;
+      const W akc = A[k * LDA + c2];
+      A[r * LDA + c2] = (c2 == k ? (W)0 : A[r * LDA + c2]) - f * akc;
     }
     __syncthreads();
   }
   // undo the column interchanges in reverse order
-  for (int k = bs - 1; k >= 0; --k) {
+  for (int k = BS - 1; k >= 0; --k) {
     const int pr = perm[k];
     if (pr != k)
-      for (int r = tid; r < bs; r += nt) { const W t = A[r * bs + k]; A[r * bs + k] = A[r * bs + pr]; A[r * bs + pr] = t; }
+      for (int r = tid; r < BS; r += nt) { const W t = A[r * LDA + k]; A[r * LDA + k] = A[r * LDA + pr]; A[r * LDA + pr] = t; }
     __syncthreads();
   }
   // inverse of Dr B Dc is A; store A transposed: Aout[col][row]
-  S* Ae = Aout + (size_t)e * bs * bs;
-  for (int idx = tid; idx < bs * bs; idx += nt) {
-    const int r = idx / bs, c2 = idx % bs;
-    Ae[(size_t)c2 * bs + r] = (S)A[idx];
+  S* Ae = Aout + (size_t)e * BS * BS;
+  for (int idx = tid; idx < BS * BS; idx += nt) {
+    const int c2 = idx / BS, r = idx % BS;   // coalesced store of the transpose
+    Ae[idx] = (S)A[r * LDA + c2];
   }
-  for (int r = tid; r < bs; r += nt) { Dr[(size_t)e * bs + r] = dr[r]; Dc[(size_t)e * bs + r] = dc[r]; }
+  for (int r = tid; r < BS; r += nt) { Dr[(size_t)e * BS + r] = dr[r]; Dc[(size_t)e * BS + r] = dc[r]; }
   if (tid == 0) info[e] = s_bad;
 }
 
@@ -693,35 +706,44 @@ static int block_build_n(fr_ctx* c, const double* q, double inv_dtau, double a0_
   return FR_OK;
 }
 
-// Dynamic shared memory of k_factor<W, S> for block size bs.  The function attribute is
-// set to the largest block (p = 4, bs = 100): contexts of several degrees may build
-// blocks concurrently from different threads, and a per-call value would race.
+// Dynamic shared memory of k_factor<W, S, N> for block size bs = 4 N^2: the padded
+// matrix, the pivot column, the two scale vectors and the interchanges.
 template <class W>
-static size_t factor_smem(int bs) { return (size_t)bs * bs * sizeof(W) + bs * sizeof(W) + bs * 4 * 2 + bs * 4; }
-constexpr int kMaxBlock = 4 * 5 * 5;
+static size_t factor_smem(int bs) { return (size_t)bs * (bs + 1) * sizeof(W) + bs * sizeof(W) + bs * 4 * 2 + bs * 4; }
+
+template <class W, class S, int N>
+static int factor_n(fr_ctx* c, S* out, cudaStream_t s) {
+  constexpr int BS = 4 * N * N;
+  const size_t smem = factor_smem<W>(BS);
+  FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<W, S, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_factor<W, S, N><<<c->ne, 256, smem, s>>>(c->B64, out, c->Dr, c->Dc, c->info, c->mesh);
+  return FR_OK;
+}
+
+template <class W, class S>
+static int factor_t(fr_ctx* c, S* out, cudaStream_t s) {
+  switch (c->n) {
+    case 2: return factor_n<W, S, 2>(c, out, s);
+    case 3: return factor_n<W, S, 3>(c, out, s);
+    case 4: return factor_n<W, S, 4>(c, out, s);
+    case 5: return factor_n<W, S, 5>(c, out, s);
+  }
+  return FR_ERR_ARG;
+}
 
 static int factor(fr_ctx* c, cudaStream_t s) {
   const int bs = c->bsz;
-  const int nt = 256;
   // in-place Gauss-Jordan: bs steps of a rank-1 update of bs^2 entries (2 flops each)
   FR_ACCOUNT(c, KK_FACTOR, 2.0 * (double)bs * bs * bs * c->ne, 0.0);
   FR_PROF_BEGIN(c, s);
-  if (c->cfg.prec_dtype == FR_PREC_FP64) {
-    const size_t smem = factor_smem<double>(bs);
-    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)factor_smem<double>(kMaxBlock)));
-    k_factor<double, double><<<c->ne, nt, smem, s>>>(c->B64, bs, (double*)c->Binv, c->Dr, c->Dc, c->info, c->mesh);
-  } else if (c->cfg.prec_dtype == FR_PREC_FP32) {
-    const size_t smem = factor_smem<float>(bs);
-    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)factor_smem<float>(kMaxBlock)));
-    k_factor<float, float><<<c->ne, nt, smem, s>>>(c->B64, bs, (float*)c->Binv, c->Dr, c->Dc, c->info, c->mesh);
-  } else {
-    const size_t smem = factor_smem<float>(bs);
-    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor<float, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)factor_smem<float>(kMaxBlock)));
-    k_factor<float, __nv_bfloat16><<<c->ne, nt, smem, s>>>(c->B64, bs, (__nv_bfloat16*)c->Binv, c->Dr, c->Dc, c->info, c->mesh);
-  }
+  // each degree has its own instantiation and attribute value: contexts of several degrees
+  // building blocks concurrently from different threads never change one another's
+  if (c->cfg.prec_dtype == FR_PREC_FP64)
+    FR_TRY(factor_t<double>(c, (double*)c->Binv, s));
+  else if (c->cfg.prec_dtype == FR_PREC_FP32)
+    FR_TRY(factor_t<float>(c, (float*)c->Binv, s));
+  else
+    FR_TRY(factor_t<float>(c, (__nv_bfloat16*)c->Binv, s));
   FR_PROF_END(c, s, KK_FACTOR);
   FR_LAUNCH_CHECK(c);
   return FR_OK;

@@ -227,6 +227,31 @@ def test_block_apply(torch, prec, tol, accum):
         assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-3)])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_block_inverse_every_degree(torch, p, prec, tol):
+    """The factorisation is compiled per degree: at every degree B_e z_e = r_e in the
+    oracle's FP64 blocks, and the FP64 inverse equals numpy's."""
+    nx, ny, mach, re, kappa = 3, 3, 0.05, 10.0, 1.0
+    c, v, q = case(nx, ny, p, mach, re, kappa, True)
+    prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
+    Bo = sv.block_jacobian(prob, q, 0.0, 150.0)
+    r = inp.random_vector(q.shape, 5 + p)
+    S = solver_for(c, v, nx, ny, p, mach, re, kappa, prec=prec)
+    S.precond_build(to_dev(q), 0.0, 150.0)
+    z = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+    S.precond_apply(to_dev(r), z)
+    got = to_host(z)
+    ne, bs = Bo.shape[0], Bo.shape[1]
+    ge = got.transpose(1, 0, 2, 3).reshape(ne, bs)
+    re_ = r.transpose(1, 0, 2, 3).reshape(ne, bs)
+    rel = np.linalg.norm(np.einsum("eab,eb->ea", Bo, ge) - re_, axis=1) / np.linalg.norm(re_, axis=1)
+    assert rel.max() <= tol, rel.max()
+    if prec == "fp64":
+        want = sv.block_apply(np.linalg.inv(Bo), r)
+        assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_block_apply_double_float_is_linear(torch, prec):
     """With FP32/BF16-stored inverses and double-float accumulation the preconditioner is a
