@@ -260,12 +260,13 @@ def gpu_arm(args):
     corners, vel, q0 = inp.make_case(w)
     T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
 
-    def make_solver(prec):
+    def make_solver(prec, arith=None):
         cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=prec,
                         restart=args.restart, maxit_lin=args.maxit_lin, tol_res=w.tol_res,
                         tol_pseudo=w.tol_pseudo, maxit_newton=args.maxit_newton, lag=2,
                         line_search=args.line_search, graphs=args.graphs,
-                        apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog)
+                        apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog,
+                        krylov_arith=arith or args.krylov_arith)
         S = fr.Solver(cfg, w.nx, w.ny)
         S.update_mesh(T(corners), T(vel))
         return S
@@ -398,7 +399,8 @@ def gpu_arm(args):
     # per-iteration time does not depend on the Newton history
     gm_cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
                        restart=args.restart, maxit_lin=120, tol_res=1e-30, graphs=args.graphs,
-                       apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog)
+                       apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog,
+                       krylov_arith=args.krylov_arith)
     Sg = fr.Solver(gm_cfg, w.nx, w.ny)
     Sg.update_mesh(T(corners), T(vel))
     Sg.precond_build(run.q, 1e-20, 1.5 / w.dt)
@@ -415,15 +417,18 @@ def gpu_arm(args):
     us_per_gmres_it = 1e3 * ga.elapsed_time(gb) / its_g
     Sg.close()
 
-    # ---- precision comparison: the same steps from the same state per block precision;
-    # the final state of each against the FP64-block run (max over entries, relative to
-    # the per-variable magnitude of the state change)
+    # ---- precision comparison: the same steps from the same state per block precision
+    # (FP64 Krylov basis) and with FP32 blocks and the double-float basis; the final state
+    # of each against the all-FP64 run (max over entries, relative to the per-variable
+    # magnitude of the state change)
     compare = {}
     if not args.no_compare:
         finals = {}
         q_start = run.q.clone()
-        for prec in ("fp64", "fp32", "bf16"):
-            S2 = make_solver(prec)
+        variants = {"fp64": ("fp64", "fp64"), "fp32": ("fp32", "fp64"), "bf16": ("bf16", "fp64"),
+                    "fp32_df64_basis": ("fp32", "df64")}
+        for prec, (bprec, arith) in variants.items():
+            S2 = make_solver(bprec, arith)
             r2 = Run(S2)
             r2.q.copy_(run.q)
             r2.qc_n.copy_(run.qc_n)
@@ -495,7 +500,8 @@ def gpu_arm(args):
         "config": {"workload": w.name, "mesh": f"{w.nx}x{w.ny} periodic [0,10]^2",
                    "p": w.p, "dof": dof, "mach": w.mach, "re_ref": w.re, "kappa": w.kappa,
                    "dt": w.dt, "tol_pseudo": w.tol_pseudo, "tol_res": w.tol_res,
-                   "gmres": f"GMRES({args.restart}) left-preconditioned, {args.orthog}, maxit {args.maxit_lin}",
+                   "gmres": f"GMRES({args.restart}) left-preconditioned, {args.orthog}, "
+                            f"{args.krylov_arith} basis, maxit {args.maxit_lin}",
                    "newton": f"max {args.maxit_newton} iterations, backtracking {args.line_search} halvings",
                    "precond": f"element block-Jacobi, {args.prec} blocks, {args.apply_accum} apply accumulation",
                    "l2": "256 MiB write between timed steps, outside the per-step events",
@@ -574,7 +580,8 @@ def batch_arm(args):
     cases = [fr.Case(c.p, c.n, c.n, c.mach, c.re, c.kappa) for c in cs]
     cfg = fr.Config(prec=args.prec, restart=args.restart, maxit_lin=args.maxit_lin,
                     maxit_newton=args.maxit_newton, lag=2, line_search=args.line_search,
-                    graphs=args.graphs, apply_accum=args.apply_accum)
+                    graphs=args.graphs, apply_accum=args.apply_accum,
+                    krylov_arith=args.krylov_arith)
     B = fr.Batch(cfg, cases)
     corners = np.zeros((B.ne, 4, 2))
     q = np.zeros(B.ndof)
@@ -654,6 +661,9 @@ def main():
                     help="backtracking halvings per Newton update (0: plain Newton)")
     ap.add_argument("--apply-accum", dest="apply_accum", default="df64", choices=["df64", "fp32"],
                     help="block-apply arithmetic with FP32/BF16-stored inverses")
+    ap.add_argument("--krylov-arith", dest="krylov_arith", default="fp64", choices=["fp64", "df64"],
+                    help="Krylov basis and Gram-Schmidt arithmetic: FP64, or FP32 pairs "
+                         "(double-float on the FP32 pipe)")
     ap.add_argument("--orthog", default="cgs2", choices=["cgs2", "cgs"],
                     help="Arnoldi orthogonalisation: CGS2, or one classical pass (PETSc's default)")
     ap.add_argument("--tiles", type=int, default=0, choices=[0, 1, 2],

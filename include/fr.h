@@ -83,6 +83,12 @@ typedef struct fr_ctx fr_ctx;
  * orthog: Arnoldi orthogonalisation: FR_ORTHO_CGS2 (default) classical Gram-Schmidt with
  * one re-orthogonalisation; FR_ORTHO_CGS a single classical pass (PETSc's default
  * refinement setting, "never"), about half the Arnoldi work;
+ * krylov_arith: arithmetic of the device-resident Arnoldi cycle (restart <= 128):
+ * FR_KRYLOV_FP64 (default) keeps the basis in FP64 and runs the Gram-Schmidt products on
+ * the FP64 pipe; FR_KRYLOV_DF64 stores each basis entry as an FP32 pair (hi, lo) in the
+ * same 8 bytes and runs the products, sums and updates as double-float on the FP32 pipe
+ * (about 2^-48 relative, against 2^-53): w, the operator input, the Hessenberg matrix
+ * and the solution stay FP64.  Restarts above 128 always use FP64;
  * block_mode: how the element blocks are formed, both exact: FR_BLOCK_LINEARIZED
  * (default) composes them from the stored local Jacobians (fr_linearize, done by the
  * build), FR_BLOCK_DUAL differentiates each element's residual by dual numbers;
@@ -105,6 +111,8 @@ typedef struct fr_ctx fr_ctx;
 #define FR_BLOCK_DUAL 1
 #define FR_ORTHO_CGS2 0
 #define FR_ORTHO_CGS 1
+#define FR_KRYLOV_FP64 0
+#define FR_KRYLOV_DF64 1
 typedef struct fr_config {
   int p;
   double gamma, prandtl, mach, re, kappa, eps_floor;
@@ -122,6 +130,7 @@ typedef struct fr_config {
   int tiles;
   int block_mode;
   int orthog;
+  int krylov_arith;
 } fr_config;
 
 /* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).

@@ -540,6 +540,7 @@ void fr_default_config(fr_config* c) {
   c->tiles = 1;
   c->block_mode = FR_BLOCK_LINEARIZED;
   c->orthog = FR_ORTHO_CGS2;
+  c->krylov_arith = FR_KRYLOV_FP64;
 }
 
 int fr_create(const fr_config* cfg, fr_ctx** out) {
@@ -552,7 +553,8 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
       (cfg->apply_accum != FR_ACCUM_FP32 && cfg->apply_accum != FR_ACCUM_DF64) ||
       cfg->tiles < 0 || cfg->tiles > 2 ||
       (cfg->block_mode != FR_BLOCK_LINEARIZED && cfg->block_mode != FR_BLOCK_DUAL) ||
-      (cfg->orthog != FR_ORTHO_CGS2 && cfg->orthog != FR_ORTHO_CGS))
+      (cfg->orthog != FR_ORTHO_CGS2 && cfg->orthog != FR_ORTHO_CGS) ||
+      (cfg->krylov_arith != FR_KRYLOV_FP64 && cfg->krylov_arith != FR_KRYLOV_DF64))
     return FR_ERR_ARG;
   fr_ctx* c = new fr_ctx();
   c->cfg = *cfg;

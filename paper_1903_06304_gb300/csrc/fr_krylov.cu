@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdio>
 #include "fr_internal.h"
+#include "fr_df.cuh"
 
 namespace fr {
 
@@ -592,6 +593,263 @@ __global__ void k_bgm_status(const GmresState* gst, int ncases, int4* out) {
   }
 }
 
+// ---- Double-float Arnoldi (krylov_arith = FR_KRYLOV_DF64).  The basis is stored as FP32
+// pairs: entry i of vector q is the float2 (hi, lo) in the 8 bytes an FP64 entry would
+// take, so a pair of entries is one 16-byte float4 (h0, l0, h1, l1).  The products, sums
+// and updates of the Gram-Schmidt passes run on the FP32 pipe with error-free
+// transformations (about 2^-48 relative); the FP64 pipe only converts w on entry and
+// exit of a pass and sums the per-block partials.  w, next and the Hessenberg data stay
+// FP64.
+
+// One double-float per thread for each of NA values: warp sums, then the warps of the
+// block merged by thread q < nw into one FP64 partial[(k0 + q) * ld + pidx]; the last of
+// the `target` blocks sharing the ticket sums the partials as seg_reduce does.
+template <int NA>
+__device__ __forceinline__ bool seg_reduce_df(float (&ah)[NA], float (&al)[NA], int nw, int k0,
+                                              double* partial, size_t ld, size_t pidx, double* out,
+                                              int nout, unsigned int* ticket, unsigned int target,
+                                              size_t first, int count) {
+  __shared__ float2 sm[NA][RT / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    float h = ah[q], l = al[q];
+    df_warp_sum(h, l);
+    if (lane == 0) sm[q][wid] = make_float2(h, l);
+  }
+  __syncthreads();
+  if (threadIdx.x < nw) {
+    float h = 0.0f, l = 0.0f;
+#pragma unroll
+    for (int w = 0; w < RT / 32; ++w) df_merge(h, l, sm[threadIdx.x][w].x, sm[threadIdx.x][w].y);
+    partial[(size_t)(k0 + threadIdx.x) * ld + pidx] = df_value(h, l);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == target - 1;
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  for (int q = wid; q < nout; q += RT / 32) {
+    const double t = warp_sum_partials(partial + (size_t)q * ld + first, count);
+    if (lane == 0) out[q] = t;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  __threadfence_block();
+  __syncthreads();
+  return true;
+}
+
+__device__ __forceinline__ float4 df_split2(double2 x) {
+  const float2 a = df_split(x.x), b = df_split(x.y);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// k_vdots with a double-float basis.
+__global__ void __launch_bounds__(RT) k_vdots_df(const float4* __restrict__ V4, size_t ld,
+                                                 const double* __restrict__ w, BatchSegs sg,
+                                                 double* __restrict__ partial, double* dsc,
+                                                 int out_off, unsigned int* tickets,
+                                                 const GmresState* gst) {
+  const int b = blockIdx.x, g = blockIdx.y;
+  const int k = sg.bcase[b];
+  const GmresState* st = gst + k;
+  if (st->done) return;
+  const int nv = st->j + 1;
+  const int ng = (nv + KG - 1) / KG;
+  if (g >= ng) return;
+  const int k0 = g * KG, nw = min(KG, nv - k0);
+  float ah[KG] = {0.0f, 0.0f, 0.0f, 0.0f}, al[KG] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  const size_t ld2 = ld / 2;
+  const size_t lo = (size_t)sg.blo[b], hi = (size_t)sg.bhi[b];
+  for (size_t i = lo + threadIdx.x; i < hi; i += 2 * RT) {
+    const bool two = i + RT < hi;
+    const float4 xa = df_split2(w2[i]);
+    const float4 xb = two ? df_split2(w2[i + RT]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int q = 0; q < KG; ++q) {
+      if (q < nw) {
+        const float4 va = V4[(k0 + q) * ld2 + i];
+        const float4 vb = two ? V4[(k0 + q) * ld2 + i + RT] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        df_fma(ah[q], al[q], va.x, va.y, xa.x, xa.y);
+        df_fma(ah[q], al[q], va.z, va.w, xa.z, xa.w);
+        df_fma(ah[q], al[q], vb.x, vb.y, xb.x, xb.y);
+        df_fma(ah[q], al[q], vb.z, vb.w, xb.z, xb.w);
+      }
+    }
+  }
+  seg_reduce_df(ah, al, nw, k0, partial, gridDim.x, b, dsc + (size_t)k * BDS + out_off, nv,
+                tickets + k, (unsigned)(sg.cnb[k] * ng), (size_t)sg.cb0[k], sg.cnb[k]);
+}
+
+// x -= sum_{q < nv} h_q V_q for one pair of entries (x as two double-floats).
+__device__ __forceinline__ void df_pair_update(float4& x, const float2* hs, const float4* V4,
+                                               size_t ld2, size_t i, int nv) {
+  int q = 0;
+  for (; q + 2 <= nv; q += 2) {   // two independent loads in flight
+    const float4 v0 = V4[(q + 0) * ld2 + i], v1 = V4[(q + 1) * ld2 + i];
+    const float2 h0 = hs[q], h1 = hs[q + 1];
+    df_fms(x.x, x.y, h0.x, h0.y, v0.x, v0.y);
+    df_fms(x.z, x.w, h0.x, h0.y, v0.z, v0.w);
+    df_fms(x.x, x.y, h1.x, h1.y, v1.x, v1.y);
+    df_fms(x.z, x.w, h1.x, h1.y, v1.z, v1.w);
+  }
+  if (q < nv) {
+    const float4 v = V4[q * ld2 + i];
+    const float2 h = hs[q];
+    df_fms(x.x, x.y, h.x, h.y, v.x, v.y);
+    df_fms(x.z, x.w, h.x, h.y, v.z, v.w);
+  }
+}
+
+// k_vaxpy with a double-float basis.
+template <bool NORM>
+__global__ void __launch_bounds__(RT) k_vaxpy_df(const float4* __restrict__ V4, size_t ld, double* w,
+                                                 BatchSegs sg, double* __restrict__ partial,
+                                                 double* dsc, int h_off, unsigned int* tickets,
+                                                 GmresState* gst, int two_pass) {
+  __shared__ float2 hs[GmresState::LD + 1];
+  const int b = blockIdx.x, part = blockIdx.y;
+  const int k = sg.bcase[b];
+  GmresState* st = gst + k;
+  if (st->done) return;
+  const int nv = st->j + 1;
+  double* ds = dsc + (size_t)k * BDS;
+  for (int q = threadIdx.x; q < nv; q += RT) hs[q] = df_split(ds[h_off + q]);
+  __syncthreads();
+  const size_t lo0 = (size_t)sg.blo[b], hi0 = (size_t)sg.bhi[b], len = hi0 - lo0;
+  const size_t lo = lo0 + len * part / SPLIT, hi = lo0 + len * (part + 1) / SPLIT;
+  double2* w2 = reinterpret_cast<double2*>(w);
+  const size_t ld2 = ld / 2;
+  float nh[1] = {0.0f}, nl[1] = {0.0f};
+  for (size_t i = lo + threadIdx.x; i < hi; i += RT) {
+    float4 x = df_split2(w2[i]);
+    df_pair_update(x, hs, V4, ld2, i, nv);
+    w2[i] = make_double2(df_value(x.x, x.y), df_value(x.z, x.w));
+    if (NORM) {
+      df_fma(nh[0], nl[0], x.x, x.y, x.x, x.y);
+      df_fma(nh[0], nl[0], x.z, x.w, x.z, x.w);
+    }
+  }
+  if (!NORM) return;
+  const size_t pb = (size_t)b * SPLIT + part;
+  const bool last = seg_reduce_df(nh, nl, 1, 0, partial, (size_t)gridDim.x * SPLIT, pb, ds + 2 * BM, 1,
+                                  tickets + k, (unsigned)(sg.cnb[k] * SPLIT),
+                                  (size_t)sg.cb0[k] * SPLIT, sg.cnb[k] * SPLIT);
+  if (last && threadIdx.x == 0) gm_givens(st, ds, two_pass ? ds + BM : nullptr, ds + 2 * BM);
+}
+
+// k_vaxdots with a double-float basis: the updated part of w is kept in shared memory as
+// double-floats for the second projections.
+__global__ void __launch_bounds__(RT) k_vaxdots_df(const float4* __restrict__ V4, size_t ld, double* w,
+                                                   BatchSegs sg, double* __restrict__ partial,
+                                                   double* dsc, unsigned int* tickets,
+                                                   GmresState* gst) {
+  __shared__ float2 hs[GmresState::LD + 1];
+  __shared__ float4 ws[RT];
+  __shared__ double sums[GmresState::LD + 1];
+  __shared__ bool last;
+  const int b = blockIdx.x, part = blockIdx.y;
+  const int k = sg.bcase[b];
+  GmresState* st = gst + k;
+  if (st->done) return;
+  const int nv = st->j + 1;
+  double* ds = dsc + (size_t)k * BDS;
+  for (int q = threadIdx.x; q < nv; q += RT) hs[q] = df_split(ds[q]);
+  __syncthreads();
+  const size_t lo0 = (size_t)sg.blo[b], hi0 = (size_t)sg.bhi[b], len0 = hi0 - lo0;
+  const size_t lo = lo0 + len0 * part / SPLIT, hi = lo0 + len0 * (part + 1) / SPLIT;
+  const int len = (int)(hi - lo);   // <= RT: a range holds at most 4 RT pairs
+  double2* w2 = reinterpret_cast<double2*>(w);
+  const size_t ld2 = ld / 2;
+  if (threadIdx.x < len) {
+    const size_t i = lo + threadIdx.x;
+    float4 x = df_split2(w2[i]);
+    df_pair_update(x, hs, V4, ld2, i, nv);
+    w2[i] = make_double2(df_value(x.x, x.y), df_value(x.z, x.w));
+    ws[threadIdx.x] = x;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = wid; q < nv; q += RT / 32) {
+    const float4* vq = V4 + q * ld2 + lo;
+    float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+    int t = lane;
+    for (; t + 32 < len; t += 64) {
+      const float4 va = vq[t], vb = vq[t + 32];
+      const float4 xa = ws[t], xb = ws[t + 32];
+      df_fma(h0, l0, va.x, va.y, xa.x, xa.y);
+      df_fma(h0, l0, va.z, va.w, xa.z, xa.w);
+      df_fma(h1, l1, vb.x, vb.y, xb.x, xb.y);
+      df_fma(h1, l1, vb.z, vb.w, xb.z, xb.w);
+    }
+    if (t < len) {
+      const float4 va = vq[t], xa = ws[t];
+      df_fma(h0, l0, va.x, va.y, xa.x, xa.y);
+      df_fma(h0, l0, va.z, va.w, xa.z, xa.w);
+    }
+    df_merge(h0, l0, h1, l1);
+    df_warp_sum(h0, l0);
+    if (lane == 0) sums[q] = df_value(h0, l0);
+  }
+  __syncthreads();
+  const size_t ldp = (size_t)gridDim.x * SPLIT, pb = (size_t)b * SPLIT + part;
+  if (threadIdx.x < nv) partial[(size_t)threadIdx.x * ldp + pb] = sums[threadIdx.x];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(tickets + k, 1u) == (unsigned)(sg.cnb[k] * SPLIT) - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const size_t first = (size_t)sg.cb0[k] * SPLIT;
+  const int count = sg.cnb[k] * SPLIT;
+  for (int q = wid; q < nv; q += RT / 32) {
+    const double t = warp_sum_partials(partial + (size_t)q * ldp + first, count);
+    if (lane == 0) ds[BM + q] = t;
+  }
+  if (threadIdx.x == 0) tickets[k] = 0u;
+}
+
+// k_bgm_store with a double-float basis: next = w inv_hn in FP64, V[j] = its split.
+__global__ void k_bgm_store_df(const double* __restrict__ w, const GmresState* gst, float4* __restrict__ V4,
+                               size_t ld, double* __restrict__ next, BatchSegs sg, int init) {
+  const GmresState* st = gst + sg.bcase[blockIdx.x];
+  if (!init && st->done) return;
+  const double s = st->inv_hn;
+  const size_t base = (size_t)st->j * (ld / 2);
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  double2* n2 = reinterpret_cast<double2*>(next);
+  for (size_t i = (size_t)sg.blo[blockIdx.x] + threadIdx.x; i < (size_t)sg.bhi[blockIdx.x]; i += RT) {
+    const double2 x = w2[i];
+    const double2 y = make_double2(__dmul_rn(x.x, s), __dmul_rn(x.y, s));
+    V4[base + i] = df_split2(y);
+    n2[i] = y;
+  }
+}
+
+// k_blincomb with a double-float basis.
+__global__ void k_blincomb_df(const float4* __restrict__ V4, size_t ld, const GmresState* gst,
+                              double* __restrict__ u, BatchSegs sg) {
+  __shared__ float2 ys[GmresState::LD];
+  const GmresState* st = gst + sg.bcase[blockIdx.x];
+  const int nk = st->j;
+  for (int q = threadIdx.x; q < nk; q += blockDim.x) ys[q] = df_split(st->y[q]);
+  __syncthreads();
+  double2* u2 = reinterpret_cast<double2*>(u);
+  const size_t ld2 = ld / 2;
+  for (size_t i = (size_t)sg.blo[blockIdx.x] + threadIdx.x; i < (size_t)sg.bhi[blockIdx.x]; i += RT) {
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int q = 0; q < nk; ++q) {
+      const float4 v = V4[q * ld2 + i];
+      df_fma(acc.x, acc.y, ys[q].x, ys[q].y, v.x, v.y);
+      df_fma(acc.z, acc.w, ys[q].x, ys[q].y, v.z, v.w);
+    }
+    u2[i] = make_double2(df_value(acc.x, acc.y), df_value(acc.z, acc.w));
+  }
+}
+
 }  // namespace fr
 
 namespace frk {
@@ -741,6 +999,9 @@ int batch_setup(fr_ctx* c) {
   return FR_OK;
 }
 
+// The device-resident cycle stores its basis as double-floats when krylov_arith asks.
+static bool df_basis(const fr_ctx* c) { return c->cfg.krylov_arith == FR_KRYLOV_DF64; }
+
 int bk_norms(fr_ctx* c, const double* r, cudaStream_t s) {
   FR_ACCOUNT(c, KK_KRYLOV, 2.0 * c->ndof, 8.0 * c->ndof);
   FR_PROF_BEGIN(c, s);
@@ -753,7 +1014,11 @@ int bk_norms(fr_ctx* c, const double* r, cudaStream_t s) {
 int bk_init(fr_ctx* c, const double* r, double* next, cudaStream_t s) {
   FR_ACCOUNT(c, KK_VECTOR, 1.0 * c->ndof, 24.0 * c->ndof);
   FR_PROF_BEGIN(c, s);
-  k_bgm_store<<<c->bw.nblk, RT, 0, s>>>(r, c->bw.gst, c->V, c->ndof, next, c->bw.sg, 1);
+  if (df_basis(c))
+    k_bgm_store_df<<<c->bw.nblk, RT, 0, s>>>(r, c->bw.gst, reinterpret_cast<float4*>(c->V), c->ndof, next,
+                                             c->bw.sg, 1);
+  else
+    k_bgm_store<<<c->bw.nblk, RT, 0, s>>>(r, c->bw.gst, c->V, c->ndof, next, c->bw.sg, 1);
   FR_PROF_END(c, s, KK_VECTOR);
   FR_LAUNCH_CHECK(c);
   return FR_OK;
@@ -767,29 +1032,40 @@ int bk_orthogonalize(fr_ctx* c, double* w, double* next, int nv_bound, cudaStrea
   // CGS:  h1 = V^T w; (w -= V h1, ||w||, Givens); V[j+1] = w/||w||
   FR_ACCOUNT(c, KK_KRYLOV, (two ? 8.0 : 4.0) * nv_bound * c->ndof + 2.0 * c->ndof,
              8.0 * c->ndof * ((two ? 4.0 : 2.0) * nv_bound + 6.0));
+  const bool df = df_basis(c);
+  const float4* V4 = reinterpret_cast<const float4*>(c->V);
   {
     FR_PROF_BEGIN(c, s);
-    k_vdots<<<gdots, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, 0, b.tickets, b.gst);
+    if (df) k_vdots_df<<<gdots, RT, 0, s>>>(V4, c->ndof, w, b.sg, b.partial, b.dsc, 0, b.tickets, b.gst);
+    else k_vdots<<<gdots, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, 0, b.tickets, b.gst);
     FR_PROF_END(c, s, KK_KRYLOV);
     FR_LAUNCH_CHECK(c);
   }
   if (two) {
     FR_PROF_BEGIN(c, s);
-    k_vaxdots<<<gaxpy, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, b.tickets, b.gst);
+    if (df) k_vaxdots_df<<<gaxpy, RT, 0, s>>>(V4, c->ndof, w, b.sg, b.partial, b.dsc, b.tickets, b.gst);
+    else k_vaxdots<<<gaxpy, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, b.tickets, b.gst);
     FR_PROF_END(c, s, KK_KRYLOV);
     FR_LAUNCH_CHECK(c);
   }
   {
     FR_PROF_BEGIN(c, s);
-    k_vaxpy<true><<<gaxpy, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, two ? BM : 0,
-                                       b.tickets, b.gst, two ? 1 : 0);
+    if (df)
+      k_vaxpy_df<true><<<gaxpy, RT, 0, s>>>(V4, c->ndof, w, b.sg, b.partial, b.dsc, two ? BM : 0,
+                                            b.tickets, b.gst, two ? 1 : 0);
+    else
+      k_vaxpy<true><<<gaxpy, RT, 0, s>>>(c->V, c->ndof, w, b.sg, b.partial, b.dsc, two ? BM : 0,
+                                         b.tickets, b.gst, two ? 1 : 0);
     FR_PROF_END(c, s, KK_KRYLOV);
     FR_LAUNCH_CHECK(c);
   }
   {
     FR_ACCOUNT(c, KK_VECTOR, 1.0 * c->ndof, 24.0 * c->ndof);
     FR_PROF_BEGIN(c, s);
-    k_bgm_store<<<b.nblk, RT, 0, s>>>(w, b.gst, c->V, c->ndof, next, b.sg, 0);
+    if (df)
+      k_bgm_store_df<<<b.nblk, RT, 0, s>>>(w, b.gst, reinterpret_cast<float4*>(c->V), c->ndof, next, b.sg, 0);
+    else
+      k_bgm_store<<<b.nblk, RT, 0, s>>>(w, b.gst, c->V, c->ndof, next, b.sg, 0);
     FR_PROF_END(c, s, KK_VECTOR);
     FR_LAUNCH_CHECK(c);
   }
@@ -806,7 +1082,11 @@ int bk_finish(fr_ctx* c, double* u, cudaStream_t s) {
   {
     FR_ACCOUNT(c, KK_VECTOR, 2.0 * GmresState::LD * c->ndof, 8.0 * c->ndof * (GmresState::LD + 1));
     FR_PROF_BEGIN(c, s);
-    k_blincomb<<<c->bw.nblk, RT, 0, s>>>(c->V, c->ndof, c->bw.gst, u, c->bw.sg);
+    if (df_basis(c))
+      k_blincomb_df<<<c->bw.nblk, RT, 0, s>>>(reinterpret_cast<const float4*>(c->V), c->ndof, c->bw.gst, u,
+                                              c->bw.sg);
+    else
+      k_blincomb<<<c->bw.nblk, RT, 0, s>>>(c->V, c->ndof, c->bw.gst, u, c->bw.sg);
     FR_PROF_END(c, s, KK_VECTOR);
     FR_LAUNCH_CHECK(c);
   }

@@ -12,6 +12,7 @@
 #include <cuda_bf16.h>
 #include "fr_internal.h"
 #include "fr_kernels.cuh"
+#include "fr_df.cuh"
 
 namespace fr {
 
@@ -535,26 +536,6 @@ template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x
 // memory.  ACC: 0 FP64, 1 FP32, 2 double-float (FP32 pairs with error-free
 // transformations, linear to about 2^-44 of the summed magnitudes).
 constexpr int APPLY_PARTS = 4;
-
-// (sh, sl) += (bh, bl), both unevaluated FP32 pairs (two-sum of the high parts).
-__device__ __forceinline__ void df_merge(float& sh, float& sl, float bh, float bl) {
-  const float sn = sh + bh;
-  const float bv = sn - sh;
-  const float er = (sh - (sn - bv)) + (bh - bv);
-  sh = sn;
-  sl += bl + er;
-}
-
-__device__ __forceinline__ void df_add(float& sh, float& sl, float a, float2 xv) {
-  const float ph = a * xv.x;
-  float pl = fmaf(a, xv.x, -ph);   // exact low part of a x_hi
-  pl = fmaf(a, xv.y, pl);           // + a x_lo
-  const float sn = sh + ph;         // two-sum
-  const float bv = sn - sh;
-  const float er = (sh - (sn - bv)) + (ph - bv);
-  sh = sn;
-  sl += er + pl;
-}
 
 template <class S, int ACC, int N>
 __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,

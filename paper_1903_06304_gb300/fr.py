@@ -44,7 +44,8 @@ class _Config(ctypes.Structure):
                 ("ser_unsteady", ctypes.c_int), ("dtau0_unsteady", ctypes.c_double),
                 ("line_search", ctypes.c_int), ("jvp_mode", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("apply_accum", ctypes.c_int), ("tiles", ctypes.c_int),
-                ("block_mode", ctypes.c_int), ("orthog", ctypes.c_int)]
+                ("block_mode", ctypes.c_int), ("orthog", ctypes.c_int),
+                ("krylov_arith", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -191,6 +192,7 @@ class Config:
     tiles: int = 1
     block_mode: str = "linearized"
     orthog: str = "cgs2"
+    krylov_arith: str = "fp64"
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -204,6 +206,8 @@ class Config:
                 c.jvp_mode = {"dual": 0, "linearized": 1}[self.jvp_mode]
             elif f.name == "orthog":
                 c.orthog = {"cgs2": 0, "cgs": 1}[self.orthog]
+            elif f.name == "krylov_arith":
+                c.krylov_arith = {"fp64": 0, "df64": 1}[self.krylov_arith]
             elif f.name == "block_mode":
                 c.block_mode = {"linearized": 0, "dual": 1}[self.block_mode]
             elif f.name == "apply_accum":

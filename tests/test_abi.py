@@ -54,6 +54,13 @@ def test_bad_config_rejected_without_gpu():
     c.p = 7
     h = ctypes.c_void_p()
     assert lib.fr_create(ctypes.byref(c), ctypes.byref(h)) == -1
+    # every enumerated option is validated before any device call
+    for field, bad in (("orthog", 2), ("krylov_arith", 2), ("apply_accum", 5), ("block_mode", -1)):
+        lib.fr_default_config(ctypes.byref(c))
+        setattr(c, field, bad)
+        assert lib.fr_create(ctypes.byref(c), ctypes.byref(h)) == -1, field
+    lib.fr_default_config(ctypes.byref(c))
+    assert c.krylov_arith == 0 and c.orthog == 0
 
 
 def test_oracle_and_library_share_no_code():

@@ -109,15 +109,17 @@ def test_batch_conservative_matches_single(torch):
 SOLVE = dict(restart=30, tol_res=1e-6, maxit_lin=100, tol_pseudo=1e-8, maxit_newton=12, lag=2)
 
 
-@pytest.mark.parametrize("prec,side", [("fp64", "left"), ("fp32", "left"), ("fp64", "right")])
-def test_batch_bdf_step_matches_single_contexts(torch, prec, side):
+@pytest.mark.parametrize("prec,side,arith", [("fp64", "left", "fp64"), ("fp32", "left", "fp64"),
+                                             ("fp64", "right", "fp64"), ("fp32", "left", "df64"),
+                                             ("fp64", "right", "df64")])
+def test_batch_bdf_step_matches_single_contexts(torch, prec, side, arith):
     """BDF1 and BDF2 steps of different dt per case: per case the same Newton and GMRES
     iteration counts and the same state as a single-case context, to rounding."""
     specs = [MIXED[1], MIXED[2], MIXED[4]]
     # GMRES capped at 8 iterations: inexact Newton steps whose convergence rate depends on
     # the case, so the cases converge after different numbers of Newton iterations and
     # converged cases sit out the remaining ones
-    kw = dict(SOLVE, maxit_lin=8, maxit_newton=40, gmres_side=side)
+    kw = dict(SOLVE, maxit_lin=8, maxit_newton=40, gmres_side=side, krylov_arith=arith)
     B, states, qd = make_batch(specs, prec=prec, **kw)
     qc = torch.empty_like(qd)
     B.conservative(qd, qc)

@@ -276,12 +276,14 @@ def test_block_apply_double_float_is_linear(torch, prec):
 
 
 # restart <= 128: device-resident Arnoldi; restart 140: the host-Givens path; CGS2 (the
-# default) and one classical pass
-@pytest.mark.parametrize("side,restart,orthog", [("left", 10, "cgs2"), ("right", 10, "cgs2"),
-                                                 ("left", 40, "cgs2"), ("right", 40, "cgs2"),
-                                                 ("left", 140, "cgs2"), ("left", 10, "cgs"),
-                                                 ("right", 40, "cgs"), ("left", 140, "cgs")])
-def test_gmres_parity(torch, side, restart, orthog):
+# default) and one classical pass; FP64 or double-float basis (the latter only on the
+# device-resident cycle; restart 140 ignores it)
+@pytest.mark.parametrize("side,restart,orthog,arith", [
+    ("left", 10, "cgs2", "fp64"), ("right", 10, "cgs2", "fp64"), ("left", 40, "cgs2", "fp64"),
+    ("right", 40, "cgs2", "fp64"), ("left", 140, "cgs2", "fp64"), ("left", 10, "cgs", "fp64"),
+    ("right", 40, "cgs", "fp64"), ("left", 140, "cgs", "fp64"), ("left", 10, "cgs2", "df64"),
+    ("right", 40, "cgs2", "df64"), ("left", 40, "cgs", "df64"), ("left", 140, "cgs2", "df64")])
+def test_gmres_parity(torch, side, restart, orthog, arith):
     nx, ny, p, mach, re, kappa, deforming = 4, 4, 2, 0.05, 10.0, 1.0, True
     c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
     prob = oracle_problem(c, v, nx, ny, p, mach, re, kappa)
@@ -292,7 +294,7 @@ def test_gmres_parity(torch, side, restart, orthog):
     want = sv.gmres(lambda x: sv.apply_A(prob, q, x, inv_dtau, a0_dt), b, P, restart, 1e-8, 200,
                     side=side, passes=2 if orthog == "cgs2" else 1)
     S = solver_for(c, v, nx, ny, p, mach, re, kappa, restart=restart, maxit_lin=200,
-                   tol_res=1e-8, gmres_side=side, orthog=orthog)
+                   tol_res=1e-8, gmres_side=side, orthog=orthog, krylov_arith=arith)
     qd = to_dev(q)
     S.precond_build(qd, inv_dtau, a0_dt)
     x = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
@@ -318,8 +320,8 @@ def test_gmres_zero_rhs(torch):
     assert np.all(to_host(x) == 0.0)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_bdf2_step_parity(torch, prec):
+@pytest.mark.parametrize("prec,arith", [("fp64", "fp64"), ("fp32", "fp64"), ("fp64", "df64")])
+def test_bdf2_step_parity(torch, prec, arith):
     """One BDF2 step (BDF1 start) of the vortex: same Newton/GMRES iteration counts and
     Res_m history as the oracle, final states equal to the Newton tolerance."""
     w = inp.Workload("t", 4, 4, 2, 0.05, 10.0, 0.0, (0.0, 10.0, 0.0, 10.0), dt=0.01)
@@ -329,7 +331,8 @@ def test_bdf2_step_parity(torch, prec):
     q1, st = sv.bdf2_step(prob, q, qc, qc, w.dt, coeffs=sv.BDF1, restart=30, tol_res=1e-6,
                           maxit_lin=100, tol_pseudo=1e-8, maxit_newton=10, lag=2)
     S = solver_for(c, v, w.nx, w.ny, w.p, w.mach, w.re, w.kappa, prec=prec, restart=30,
-                   tol_res=1e-6, maxit_lin=100, tol_pseudo=1e-8, maxit_newton=10, lag=2)
+                   tol_res=1e-6, maxit_lin=100, tol_pseudo=1e-8, maxit_newton=10, lag=2,
+                   krylov_arith=arith)
     qd = to_dev(q)
     qcd = to_dev(qc)
     sg = S.bdf2_step(qd, qcd, qcd, w.dt, coeffs=(1.0, -1.0, 0.0)).summary()
@@ -427,6 +430,35 @@ def test_full_size_blocks_sampled(torch, w):
         want = Ax[:, e].reshape(bs)
         got = B[e] @ xe
         assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_full_size_gmres_double_float_basis(torch):
+    """The benchmark's linear systems at full size (64x64 p=3 vortex, GMRES(30) capped at
+    60 iterations, the regime of the BDF2 steps): with the double-float basis the solver
+    takes the same iterations and returns the FP64-basis solution to 1e-8, and its true
+    preconditioned residual (operator and block apply on the device) is the same."""
+    w = inp.NS_VORTEX_64
+    c, v, q = inp.make_case(w, t=0.13)
+    inv_dtau, a0_dt = 1e-20, 1.5 / w.dt
+    b = to_dev(inp.random_vector(q.shape, 23))
+    qd = to_dev(q)
+    out = {}
+    for arith in ("fp64", "df64"):
+        S = solver_for(c, v, w.nx, w.ny, w.p, w.mach, w.re, w.kappa, prec="fp32", restart=30,
+                       maxit_lin=60, tol_res=1e-12, krylov_arith=arith)
+        S.precond_build(qd, inv_dtau, a0_dt)
+        x = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+        its = S.gmres(qd, b, x, inv_dtau, a0_dt)
+        Ax = torch.empty_like(x)
+        S.jvp(qd, x, Ax, inv_dtau, a0_dt)
+        Pr, Pb = torch.empty_like(x), torch.empty_like(x)
+        S.precond_apply(b - Ax, Pr)
+        S.precond_apply(b, Pb)
+        out[arith] = (its, to_host(x), float(torch.linalg.norm(Pr) / torch.linalg.norm(Pb)))
+    (i64, x64, r64), (idf, xdf, rdf) = out["fp64"], out["df64"]
+    assert i64 == idf == 60
+    assert np.abs(xdf - x64).max() <= 1e-8 * np.abs(x64).max()
+    assert abs(rdf - r64) <= 1e-6 * r64
 
 
 def test_invalid_mesh_rejected(torch):
