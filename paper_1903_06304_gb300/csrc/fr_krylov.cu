@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(RT) k_krylov(const double* __restrict__ V, siz
                          nv, hk, acc, blockIdx.x * (size_t)RT + threadIdx.x, n / 2, stride);
   const bool last = block_reduce_store(acc, MODE == 2 ? 1 : nv, partial, out, ticket, 0, gridDim.x);
   // the norm pass of a device-resident Arnoldi step closes it with the Givens update
-  if (MODE == 2 && gst && last && threadIdx.x == 0) gm_givens(gst, h - FR_MAX_RESTART, h, out);
+  if (MODE == 2 && gst && last && threadIdx.x < 32) gm_givens(gst, h - FR_MAX_RESTART, h, out);
 }
 
 // out_0 = ||r[continuity row]||^2, out_1 = ||r||^2
@@ -240,30 +240,47 @@ __global__ void k_lincomb(const double* __restrict__ V, size_t ld, int nv, const
 // round trip.
 
 // Column j of H from the CGS2 projections h1 + h2 and ||w||, the previous rotations, a
-// new rotation, the residual estimate |g_{j+1}| and the stopping test (one thread).
+// new rotation, the residual estimate |g_{j+1}| and the stopping test.  Called by the 32
+// lanes of one warp: the column, cosines and sines are staged in shared memory in
+// parallel, lane 0 applies the rotations (the running entry in a register, no global
+// round trip per rotation), and the rotated column is written back in parallel.
 __device__ void gm_givens(GmresState* st, const double* h1, const double* h2, const double* nrm2) {
+  constexpr int L = GmresState::LD;
+  __shared__ double col[L + 1], rc[L], rs[L];
+  const int lane = threadIdx.x & 31;
   if (st->done) return;
   const int j = st->j;
-  constexpr int L = GmresState::LD;
   const double hn = sqrt(nrm2[0]);
-  if (!isfinite(hn)) { st->nonfinite = 1; st->done = 1; return; }
-  for (int i = 0; i <= j; ++i) st->H[i * L + j] = h2 ? h1[i] + h2[i] : h1[i];
-  st->H[(j + 1) * L + j] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double a = st->H[i * L + j], b = st->H[(i + 1) * L + j];
-    st->H[i * L + j] = st->cs[i] * a + st->sn[i] * b;
-    st->H[(i + 1) * L + j] = -st->sn[i] * a + st->cs[i] * b;
+  if (!isfinite(hn)) {
+    __syncwarp();
+    if (lane == 0) { st->nonfinite = 1; st->done = 1; }
+    return;
   }
-  const double den = hypot(st->H[j * L + j], st->H[(j + 1) * L + j]);
-  st->cs[j] = st->H[j * L + j] / den;
-  st->sn[j] = st->H[(j + 1) * L + j] / den;
-  st->H[j * L + j] = den;
-  st->H[(j + 1) * L + j] = 0.0;
-  st->g[j + 1] = -st->sn[j] * st->g[j];
-  st->g[j] = st->cs[j] * st->g[j];
-  st->j = j + 1;
-  st->inv_hn = hn > 0.0 ? 1.0 / hn : 0.0;
-  if (fabs(st->g[j + 1]) <= st->tol || hn == 0.0 || j + 1 >= st->jmax) st->done = 1;
+  for (int i = lane; i <= j; i += 32) col[i] = h2 ? h1[i] + h2[i] : h1[i];
+  for (int i = lane; i < j; i += 32) { rc[i] = st->cs[i]; rs[i] = st->sn[i]; }
+  __syncwarp();
+  if (lane == 0) {
+    double a = col[0];   // entry i of the column after rotations 0 .. i-1
+    for (int i = 0; i < j; ++i) {
+      const double b = col[i + 1];
+      col[i] = rc[i] * a + rs[i] * b;
+      a = -rs[i] * a + rc[i] * b;
+    }
+    const double den = hypot(a, hn);
+    const double cj = a / den, sj = hn / den;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    st->cs[j] = cj;
+    st->sn[j] = sj;
+    const double gj = st->g[j];
+    st->g[j + 1] = -sj * gj;
+    st->g[j] = cj * gj;
+    st->j = j + 1;
+    st->inv_hn = hn > 0.0 ? 1.0 / hn : 0.0;
+    if (fabs(st->g[j + 1]) <= st->tol || hn == 0.0 || j + 1 >= st->jmax) st->done = 1;
+  }
+  __syncwarp();
+  for (int i = lane; i <= j + 1; i += 32) st->H[i * L + j] = col[i];
 }
 
 // Back substitution H[0:k,0:k] y = g[0:k], k = j (one thread).
@@ -327,10 +344,28 @@ __device__ __forceinline__ bool seg_reduce(double (&acc)[NA], int nw, int k0, do
   __shared__ double sm[NA][RT / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if constexpr (NA == 4) {
+    // four values: the xor-16 and xor-8 exchanges each halve the set a lane carries, the
+    // last three sum over the remaining lane bits; lane 8 q ends with the warp sum of
+    // value q (6 additions per lane instead of 20)
+    const bool u16 = (lane & 16) != 0, u8 = (lane & 8) != 0;
+    double a0 = u16 ? acc[2] : acc[0], a1 = u16 ? acc[3] : acc[1];
+    const double s0 = u16 ? acc[0] : acc[2], s1 = u16 ? acc[1] : acc[3];
+    a0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+    a1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+    double v = u8 ? a1 : a0;
+    const double sv = u8 ? a0 : a1;
+    v += __shfl_xor_sync(0xffffffffu, sv, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    if ((lane & 7) == 0) sm[lane >> 3][wid] = v;
+  } else {
 #pragma unroll
-  for (int q = 0; q < NA; ++q) {
-    const double t = warp_sum(acc[q]);
-    if (lane == 0) sm[q][wid] = t;
+    for (int q = 0; q < NA; ++q) {
+      const double t = warp_sum(acc[q]);
+      if (lane == 0) sm[q][wid] = t;
+    }
   }
   __syncthreads();
   if (threadIdx.x < nw) {
@@ -442,7 +477,7 @@ __global__ void __launch_bounds__(RT) k_vaxpy(const double* __restrict__ V, size
   const bool last = seg_reduce(acc, 1, 0, partial, (size_t)gridDim.x * SPLIT, pb, ds + 2 * BM, 1,
                                tickets + k, (unsigned)(sg.cnb[k] * SPLIT),
                                (size_t)sg.cb0[k] * SPLIT, sg.cnb[k] * SPLIT);
-  if (last && threadIdx.x == 0) gm_givens(st, ds, two_pass ? ds + BM : nullptr, ds + 2 * BM);
+  if (last && threadIdx.x < 32) gm_givens(st, ds, two_pass ? ds + BM : nullptr, ds + 2 * BM);
 }
 
 // CGS2 middle step in one pass: w -= sum_k h1_k V_k over this block's part of a range
@@ -492,22 +527,37 @@ __global__ void __launch_bounds__(RT) k_vaxdots(const double* __restrict__ V, si
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int q = wid; q < nv; q += RT / 32) {
+  // warp wid takes vectors q = wid + 16 i and q2 = q + 8 together (each w pair loaded once
+  // for both); past nv the second stream repeats the first and is not stored
+  for (int q = wid; q < nv; q += 2 * (RT / 32)) {
+    const int q2 = q + RT / 32;
+    const bool has2 = q2 < nv;
     const double2* vq = V2 + q * ld2 + lo;
-    double a0 = 0.0, a1 = 0.0;
+    const double2* vr = V2 + (has2 ? q2 : q) * ld2 + lo;
+    double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
     int t = lane;
     for (; t + 32 < len; t += 64) {
-      const double2 va = vq[t], vb = vq[t + 32];
       const double2 xa = ws[t], xb = ws[t + 32];
+      const double2 va = vq[t], vb = vq[t + 32], ra = vr[t], rb = vr[t + 32];
       a0 = fma(va.x, xa.x, a0); a0 = fma(va.y, xa.y, a0);
       a1 = fma(vb.x, xb.x, a1); a1 = fma(vb.y, xb.y, a1);
+      b0 = fma(ra.x, xa.x, b0); b0 = fma(ra.y, xa.y, b0);
+      b1 = fma(rb.x, xb.x, b1); b1 = fma(rb.y, xb.y, b1);
     }
     if (t < len) {
-      const double2 va = vq[t], xa = ws[t];
+      const double2 xa = ws[t], va = vq[t], ra = vr[t];
       a0 = fma(va.x, xa.x, a0); a0 = fma(va.y, xa.y, a0);
+      b0 = fma(ra.x, xa.x, b0); b0 = fma(ra.y, xa.y, b0);
     }
-    const double s = warp_sum(a0 + a1);
-    if (lane == 0) sums[q] = s;
+    // two values: the xor-16 exchange leaves lanes 0-15 the first, 16-31 the second
+    const bool up = (lane & 16) != 0;
+    double v = up ? b0 + b1 : a0 + a1;
+    const double sv = up ? a0 + a1 : b0 + b1;
+    v += __shfl_xor_sync(0xffffffffu, sv, 16);
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) sums[q] = v;
+    if (lane == 16 && has2) sums[q2] = v;
   }
   __syncthreads();
   const size_t ldp = (size_t)gridDim.x * SPLIT, pb = (size_t)b * SPLIT + part;
@@ -738,7 +788,7 @@ __global__ void __launch_bounds__(RT) k_vaxpy_df(const float4* __restrict__ V4, 
   const bool last = seg_reduce_df(nh, nl, 1, 0, partial, (size_t)gridDim.x * SPLIT, pb, ds + 2 * BM, 1,
                                   tickets + k, (unsigned)(sg.cnb[k] * SPLIT),
                                   (size_t)sg.cb0[k] * SPLIT, sg.cnb[k] * SPLIT);
-  if (last && threadIdx.x == 0) gm_givens(st, ds, two_pass ? ds + BM : nullptr, ds + 2 * BM);
+  if (last && threadIdx.x < 32) gm_givens(st, ds, two_pass ? ds + BM : nullptr, ds + 2 * BM);
 }
 
 // k_vaxdots with a double-float basis: the updated part of w is kept in shared memory as
