@@ -58,9 +58,10 @@ ALU_KINDS = {"trace", "face", "elem", "trace_jvp", "face_jvp", "elem_jvp", "bloc
 # dram__bytes_write.sum averaged over the captured launches; the summary under profiles/
 # gives the command).  A class whose kernels changed since the capture is left out.
 NCU_TRAFFIC = {
-    # k_vdots / k_vaxdots / k_vaxpy<1>, one GMRES iteration of the 64x64 p=3 vortex at
-    # nv = 7 (16.8 + 16.8 + 15.2 MB): equal to the algorithmic bytes of those launches
-    "krylov_reduce": 16.28e6,
+    # k_vdots / k_vaxdots / k_vaxpy<1> over the first GMRES(30) cycle of the 64x64 p=3
+    # vortex (90 launches, nv = 1 .. 30): mean 34.8 MB per launch, equal to the
+    # algorithmic (nv + 1) x 2.1 MB averaged over the cycle
+    "krylov_reduce": 34.82e6,
 }
 
 
