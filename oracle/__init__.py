@@ -16,10 +16,11 @@ basis     Gauss points, Lagrange derivative/extrapolation, Radau corrections (Se
 physics   Eqs. convection, diffusion, shear_stress, jacobian, preconditioning,
           theta, eigenvalues(_para), eps_nonmove/eps_move, Rosanov (Secs. 2-3)
 geometry  bilinear element map, metrics and grid velocity (Sec. 2.3)
-residual  FR/CPR residual R(q^p), Eqs. cpr_ns / unsteady_pre_mov_cdomain_GCL (Sec. 3.1)
+residual  FR/CPR residual R(q^p), Eqs. cpr_ns / unsteady_pre_mov_cdomain_GCL (Sec. 3.1),
+          far-field and adiabatic no-slip wall faces (Sec. 3.3), wall force (Sec. 4)
 solver    JVP, element block Jacobian, restarted GMRES, BDF2 dual-time Newton and
-          steady PTC with SER (Sec. 3.2)
-norms     L2 and entropy errors (Sec. 4)
+          steady PTC with SER (Sec. 3.2); L2 and entropy errors (Sec. 4)
+scale     per-equation residual magnitudes that parity tolerances are stated in
 
 Functions whose result is pinned by tests against the paper or mathematics are
 listed in ``tests/test_oracle_*.py``.  Parity unpinned: none of the functions

@@ -31,6 +31,8 @@ def residual_scale(q, mesh: Mesh, p: int, gas: ph.Gas) -> np.ndarray:
     jmin = np.min(geo.sol.J)
     s_flux = np.max((np.abs(P.F) + np.abs(P.G)) / geo.sol.J, axis=(1, 2, 3))
     left, right, bottom, top = mesh.neighbours()
+    own = np.arange(mesh.ne)
+    top = np.where(top < 0, own, top)       # a boundary face: the element's own trace
     s_diss = np.zeros(4)
     for fm, fp, nb, along in ((FACE_R, FACE_L, right, True), (FACE_T, FACE_B, top, False)):
         qm = trace(b, q, fm)

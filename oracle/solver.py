@@ -104,7 +104,7 @@ def element_colouring(mesh: Mesh) -> np.ndarray:
     left, right, bottom, top = mesh.neighbours()
     colour = -np.ones(mesh.ne, dtype=int)
     for e in range(mesh.ne):
-        used = {colour[nb] for nb in (left[e], right[e], bottom[e], top[e])}
+        used = {colour[nb] for nb in (left[e], right[e], bottom[e], top[e]) if nb >= 0}
         c = 0
         while c in used:
             c += 1

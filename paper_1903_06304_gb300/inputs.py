@@ -70,6 +70,76 @@ def deform(ref_corners: np.ndarray, t: float, m: Motion) -> tuple[np.ndarray, np
     return pos, vel
 
 
+# ----------------------------------------------------------------------------- O-grids
+
+def naca0012_half_thickness(x: np.ndarray) -> np.ndarray:
+    """Half thickness of the NACA 0012 profile of Sec. 4.2, chord 1, with the closed
+    trailing edge (last coefficient -0.1036, so that it vanishes at x = 1)."""
+    return 0.6 * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x ** 2 + 0.2843 * x ** 3
+                  - 0.1036 * x ** 4)
+
+
+def _stretch_ratio(nj: int, first: float, span: float) -> float:
+    """Ratio r of a geometric distribution of nj cells over ``span`` whose first cell is
+    ``first`` long: first = span (r - 1) / (r^nj - 1), by bisection."""
+    lo, hi = 1.0 + 1e-12, 2.0
+    while (hi - 1.0) / (hi ** nj - 1.0) * span > first:
+        hi *= 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if (mid - 1.0) / (mid ** nj - 1.0) * span > first:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def naca_ogrid(ni: int = 256, nj: int = 96, r_far: float = 20.0, first: float = 1e-3) -> np.ndarray:
+    """Corners ``[ni*nj, 4, 2]`` of an algebraic O-grid around the NACA 0012 (chord 1,
+    leading edge at the origin): element e = j*ni + i, i around the body (periodic:
+    the wrap closes at the trailing edge), j from the wall (row 0) to the far field
+    (row nj-1), a circle of radius ``r_far`` chords about the mid-chord.
+
+    Around the body, x = (1 + cos s)/2 for s = 2 pi i/ni (cosine clustering at both
+    edges), the lower surface first so that (i, j) is right-handed; the far-field node
+    of column i sits at the angle -s.  Along each column the nodes follow a geometric
+    distribution from the wall node to the far-field node whose first cell is ``first``
+    of the wall-to-far-field distance at the mid-chord."""
+    s = 2.0 * math.pi * np.arange(ni) / ni
+    xw = 0.5 * (1.0 + np.cos(s))
+    yt = naca0012_half_thickness(xw)
+    yw = np.where(s <= math.pi, -yt, yt)
+    xf = 0.5 + r_far * np.cos(-s)
+    yf = r_far * np.sin(-s)
+    r = _stretch_ratio(nj, first, r_far)
+    frac = (r ** np.arange(nj + 1) - 1.0) / (r ** nj - 1.0)           # [nj+1], 0 .. 1
+    X = xw[None, :] + frac[:, None] * (xf - xw)[None, :]             # [nj+1, ni]
+    Y = yw[None, :] + frac[:, None] * (yf - yw)[None, :]
+    ip = (np.arange(ni) + 1) % ni
+    c = np.empty((nj, ni, 4, 2))
+    c[:, :, 0, 0], c[:, :, 0, 1] = X[:-1, :], Y[:-1, :]
+    c[:, :, 1, 0], c[:, :, 1, 1] = X[:-1, ip], Y[:-1, ip]
+    c[:, :, 2, 0], c[:, :, 2, 1] = X[1:, ip], Y[1:, ip]
+    c[:, :, 3, 0], c[:, :, 3, 1] = X[1:, :], Y[1:, :]
+    return c.reshape(ni * nj, 4, 2)
+
+
+def plunge(ref_corners: np.ndarray, t: float, h: float = 0.25, k: float = 1.0):
+    """Rigid plunge of Sec. 4.4 (chord 1, U_inf = 1): y = y_r + h sin(2 pi f t) with the
+    reduced frequency k = 2 pi f; the whole mesh moves.  Corners and velocities."""
+    f = k / (2.0 * math.pi)
+    pos = ref_corners.copy()
+    vel = np.zeros_like(ref_corners)
+    pos[..., 1] += h * math.sin(2.0 * math.pi * f * t)
+    vel[..., 1] = 2.0 * math.pi * f * h * math.cos(2.0 * math.pi * f * t)
+    return pos, vel
+
+
+def far_field_state(mach: float, u: float = 1.0, v: float = 0.0) -> tuple:
+    """Primitive free stream (p_inf, u, v, T_inf = 1) of the nondimensional gas."""
+    return (p_inf(mach), u, v, 1.0)
+
+
 def sample_points(corners: np.ndarray, p: int) -> tuple[np.ndarray, np.ndarray]:
     """Physical (x, y) ``[Ne, n, n]`` where initial conditions are sampled (Gauss points)."""
     g, _ = np.polynomial.legendre.leggauss(p + 1)
