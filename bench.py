@@ -396,6 +396,30 @@ def gpu_arm(args):
     if rank == 0 and not args.no_sweep:
         sweep = large_n_sweep(args.sweep, torch, fr, inp, flush)
 
+    # ---- the plunging NACA 0012 O-grid (bounded mesh: wall below row 0, far field above
+    # the last row), 256 x 96 elements at p = 3, Re = 1e4, kappa = sqrt(5): residual and
+    # dual-number JVP per call, warm L2 and flushed
+    ogrid = None
+    if rank == 0 and not args.no_ogrid:
+        ni, nj = 256, 96
+        c_o, v_o = inp.plunge(inp.naca_ogrid(ni, nj), 0.3)
+        qi = inp.far_field_state(w.mach)
+        So = fr.Solver(fr.Config(p=3, mach=w.mach, re=1e4, kappa=5 ** 0.5), ni, nj,
+                       bc=("wall", "farfield"), q_inf=qi)
+        So.update_mesh(T(c_o), T(v_o))
+        qo = T(inp.random_perturbation(inp.uniform_state(ni * nj, 3, w.mach), 7, 0.05, w.mach))
+        vo = torch.randn_like(qo)
+        oo = torch.empty_like(qo)
+        ogrid = {"workload": "naca0012_ogrid_256x96_p3 (plunging, wall + far field)",
+                 "dof": int(qo.numel())}
+        for name, fn in (("residual", lambda: So.residual(qo, oo)),
+                         ("jvp_dual", lambda: So.jvp(qo, vo, oo, 1e-20, 1.5 / w.dt))):
+            warm = time_calls(fn)
+            cold = time_calls(fn, flush_between=True)
+            ogrid[name] = {"warm_l2": qo.numel() / (warm * 1e-3) / 1e9,
+                           "flushed_l2": qo.numel() / (cold * 1e-3) / 1e9, "median_of": 50}
+        So.close()
+
     # ---- GMRES iteration cost at the final state: a fixed count (tol_res 1e-30), so the
     # per-iteration time does not depend on the Newton history
     gm_cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
@@ -520,6 +544,7 @@ def gpu_arm(args):
         "vjp_gdofs": call_gdofs["vjp"]["warm_l2"],
         "call_gdofs": call_gdofs,
         "large_n_sweep": sweep,
+        "bounded_ogrid_gdofs": ogrid,
         "linearize_ms": t_lin,
         "us_per_gmres_iteration": us_per_gmres_it,
         "precision_compare": compare,
@@ -662,6 +687,8 @@ def main():
                     help="backtracking halvings per Newton update (0: plain Newton)")
     ap.add_argument("--apply-accum", dest="apply_accum", default="df64", choices=["df64", "fp32"],
                     help="block-apply arithmetic with FP32/BF16-stored inverses")
+    ap.add_argument("--no-ogrid", action="store_true",
+                    help="skip the bounded NACA O-grid residual / JVP timings")
     ap.add_argument("--krylov-arith", dest="krylov_arith", default="fp64", choices=["fp64", "df64"],
                     help="Krylov basis and Gram-Schmidt arithmetic: FP64, or FP32 pairs "
                          "(double-float on the FP32 pipe)")

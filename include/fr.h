@@ -113,6 +113,8 @@ typedef struct fr_ctx fr_ctx;
 #define FR_ORTHO_CGS 1
 #define FR_KRYLOV_FP64 0
 #define FR_KRYLOV_DF64 1
+#define FR_BC_WALL 1
+#define FR_BC_FARFIELD 2
 typedef struct fr_config {
   int p;
   double gamma, prandtl, mach, re, kappa, eps_floor;
@@ -164,6 +166,23 @@ void fr_destroy(fr_ctx* ctx);
  * basis, blocks).  Must be called before any compute call; may be called again to
  * resize. */
 int fr_set_mesh(fr_ctx* ctx, int nx, int ny, int periodic_x, int periodic_y);
+
+/* Mesh topology periodic in xi and bounded in eta (Sec. 3.3 boundary conditions), e.g.
+ * an O-grid around a body: element e = j*nx + i, i around the body (periodic), the faces
+ * below row 0 of kind bc_below and above row ny-1 of kind bc_above, each FR_BC_WALL (an
+ * adiabatic no-slip wall moving with the grid: boundary state (p^-, v_g, T^-), dT/dn = 0)
+ * or FR_BC_FARFIELD (boundary state q_inf, through the approximate Riemann solver).
+ * q_inf_h: host array of 4 doubles, the far-field primitive state (p, u, v, T), p, T > 0;
+ * required when a side is a far field, may be NULL otherwise; copied.  Boundary faces
+ * take the interior trace's local gradient with the full one-sided BR2 lift of
+ * q_b - q^- (the boundary state is also q^com).  Allocates like fr_set_mesh plus 4
+ * arrays of nx*4*(p+1) doubles.  On a bounded mesh the available calls are
+ * fr_update_mesh, fr_residual, fr_bdf_rhs, fr_jvp (dual numbers), fr_conservative and
+ * fr_residual_norms; the linearised operator, element blocks, VJP, GMRES, the Newton
+ * loops and fr_param_vjp return FR_ERR_ARG (message in fr_last_error).  FR_ERR_ARG also
+ * for nx < 2, ny < 1, an unknown kind or a missing / non-positive q_inf. */
+int fr_set_mesh_bounded(fr_ctx* ctx, int nx, int ny, int bc_below, int bc_above,
+                        const double* q_inf_h);
 
 /* Update geometry at the current time (Sec. 2.3): corners_d and corner_vel_d are
  * device [Ne][4][2] FP64 (corner coordinates and their grid velocities); the library

@@ -181,7 +181,8 @@ void free_mesh(fr_ctx* c) {
                    &c->gl_d, &c->fn_d, &c->qcm_d, &c->B64, &c->V, &c->w_r, &c->w_z, &c->w_x,
                    &c->w_t, &c->w_u, &c->red, &c->JFQ, &c->JFG, &c->JP, &c->JG, &c->PP,
                    &c->adj_q, &c->adj_fn, &c->adj_qc, &c->sgs, &c->sdgs, &c->sgf, &c->sdgf,
-                   &c->seed, &c->edot, &c->zero, &c->rtan};
+                   &c->seed, &c->edot, &c->zero, &c->rtan, &c->fnb, &c->fnb_d, &c->qcb,
+                   &c->qcb_d};
   for (double** p : ds) if (*p) { cudaFree(*p); *p = nullptr; }
   if (c->Binv) { cudaFree(c->Binv); c->Binv = nullptr; }
   if (c->Dr) { cudaFree(c->Dr); c->Dr = nullptr; }
@@ -192,6 +193,7 @@ void free_mesh(fr_ctx* c) {
   if (c->ecase) { cudaFree(c->ecase); c->ecase = nullptr; }
   c->blocks_ready = 0;
   c->lin_ready = 0;
+  c->bounded = c->bc_below = c->bc_above = 0;
   frk::batch_free(c);
   graphs_free(c);
 }
@@ -203,6 +205,15 @@ int check_ready(fr_ctx* c) {
   if (!c) return FR_ERR_ARG;
   if (c->ne <= 0) { snprintf(c->err, sizeof(c->err), "fr_set_mesh has not been called"); return FR_ERR_ARG; }
   return FR_OK;
+}
+
+// The linearised operator, element blocks, the VJP, GMRES and the Newton loops do not
+// treat boundary faces yet: refused on bounded meshes before any launch.
+int need_periodic(fr_ctx* c, const char* what) {
+  if (!c->bounded) return FR_OK;
+  snprintf(c->err, sizeof(c->err), "%s: not available on bounded meshes (residual, "
+           "fr_bdf_rhs, fr_jvp and fr_conservative are)", what);
+  return FR_ERR_ARG;
 }
 
 // host copies of the small device scalars
@@ -604,6 +615,35 @@ int fr_set_mesh(fr_ctx* c, int nx, int ny, int px, int py) {
   return fr_setup_cases(c, 1, &nx, &ny, &c->cp_h);
 }
 
+int fr_set_mesh_bounded(fr_ctx* c, int nx, int ny, int bc_below, int bc_above, const double* q_inf_h) {
+  if (!c) return FR_ERR_ARG;
+  const bool kinds_ok = (bc_below == FR_BC_WALL || bc_below == FR_BC_FARFIELD) &&
+                        (bc_above == FR_BC_WALL || bc_above == FR_BC_FARFIELD);
+  const bool need_qinf = bc_below == FR_BC_FARFIELD || bc_above == FR_BC_FARFIELD;
+  if (nx < 2 || ny < 1 || !kinds_ok || (need_qinf && !q_inf_h)) {
+    snprintf(c->err, sizeof(c->err), "fr_set_mesh_bounded: need nx >= 2, ny >= 1, boundary kinds "
+             "FR_BC_WALL / FR_BC_FARFIELD and q_inf for a far field");
+    return FR_ERR_ARG;
+  }
+  if (need_qinf && !(q_inf_h[0] > 0.0 && q_inf_h[3] > 0.0)) {
+    snprintf(c->err, sizeof(c->err), "fr_set_mesh_bounded: q_inf needs p > 0 and T > 0");
+    return FR_ERR_ARG;
+  }
+  for (int k = 0; k < 4; ++k) c->cp_h.qinf[k] = need_qinf ? q_inf_h[k] : 0.0;
+  FR_TRY(fr_setup_cases(c, 1, &nx, &ny, &c->cp_h));
+  c->bounded = 1;
+  c->bc_below = bc_below;
+  c->bc_above = bc_above;
+  const size_t nb = (size_t)nx * 4 * c->n;
+  FR_TRY(dev_alloc(c, &c->fnb, nb));
+  FR_TRY(dev_alloc(c, &c->fnb_d, nb));
+  FR_TRY(dev_alloc(c, &c->qcb, nb));
+  FR_TRY(dev_alloc(c, &c->qcb_d, nb));
+  FR_TRY(frk::mark_bounds(c, nx, ny, bc_below, bc_above, 0));
+  FR_CUDA_CHECK(c, cudaStreamSynchronize(0));
+  return FR_OK;
+}
+
 }  // extern "C"
 
 int fr_setup_cases(fr_ctx* c, int ncases, const int* nxs, const int* nys,
@@ -723,12 +763,14 @@ int fr_jvp(fr_ctx* c, const double* q, const double* v, double inv_dtau, double 
 
 int fr_linearize(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, void* s) {
   FR_TRY(check_ready(c));
+  FR_TRY(need_periodic(c, "fr_linearize"));
   if (!q) return FR_ERR_ARG;
   return frk::linearize(c, q, inv_dtau, a0_dt, S(s));
 }
 
 int fr_apply_linear(fr_ctx* c, const double* v, double* out, int transpose, void* s) {
   FR_TRY(check_ready(c));
+  FR_TRY(need_periodic(c, "fr_apply_linear"));
   if (!v || !out) return FR_ERR_ARG;
   return frk::apply_linear(c, v, out, transpose != 0, S(s));
 }
@@ -736,6 +778,7 @@ int fr_apply_linear(fr_ctx* c, const double* v, double* out, int transpose, void
 int fr_vjp(fr_ctx* c, const double* q, const double* w, double inv_dtau, double a0_dt, double* out,
            void* s) {
   FR_TRY(check_ready(c));
+  FR_TRY(need_periodic(c, "fr_vjp"));
   if (!q || !w || !out) return FR_ERR_ARG;
   FR_TRY(frk::linearize(c, q, inv_dtau, a0_dt, S(s)));
   return frk::apply_linear(c, w, out, true, S(s));
@@ -743,6 +786,7 @@ int fr_vjp(fr_ctx* c, const double* q, const double* w, double inv_dtau, double 
 
 int fr_precond_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, void* s) {
   FR_TRY(check_ready(c));
+  FR_TRY(need_periodic(c, "fr_precond_build"));
   FR_TRY(frk::block_build(c, q, inv_dtau, a0_dt, S(s)));
   c->blocks_ready = 1;
   return FR_OK;
@@ -765,6 +809,7 @@ int fr_precond_apply(fr_ctx* c, const double* r, double* z, void* s) {
 int fr_gmres(fr_ctx* c, const double* q, const double* b, double inv_dtau, double a0_dt, double* x,
              int* iters, void* s) {
   FR_TRY(check_ready(c));
+  FR_TRY(need_periodic(c, "fr_gmres"));
   if (!c->blocks_ready) { snprintf(c->err, sizeof(c->err), "no preconditioner built"); return FR_ERR_ARG; }
   if (c->cfg.jvp_mode == FR_JVP_LINEARIZED) FR_TRY(frk::linearize(c, q, inv_dtau, a0_dt, S(s)));
   int its = 0;
@@ -776,12 +821,14 @@ int fr_gmres(fr_ctx* c, const double* q, const double* b, double inv_dtau, doubl
 int fr_bdf2_step(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, double a0, double a1,
                  double a2, double dt, fr_stats* st, void* s) {
   FR_TRY(check_ready(c));
+  FR_TRY(need_periodic(c, "fr_bdf2_step"));
   if (!q || !qcn || dt <= 0 || (a2 != 0.0 && !qcnm1)) return FR_ERR_ARG;
   return newton_loop(c, q, qcn, qcnm1, a0, a1, a2, dt, false, st, S(s));
 }
 
 int fr_ptc_solve(fr_ctx* c, double* q, fr_stats* st, void* s) {
   FR_TRY(check_ready(c));
+  FR_TRY(need_periodic(c, "fr_ptc_solve"));
   if (!q) return FR_ERR_ARG;
   return newton_loop(c, q, nullptr, nullptr, 0, 0, 0, 1.0, true, st, S(s));
 }

@@ -41,6 +41,9 @@ enum { GS_SXX, GS_SXY, GS_SEX, GS_SEY, GS_STX, GS_STE, GS_INVJ, GS_DIVST, GS_UG,
 // L/R faces and |J| grad(eta) on the B/T faces.
 enum { GF_SX, GF_SY, GF_J, GF_UG, GF_VG, GF_COUNT };
 enum { FACE_L = 0, FACE_R = 1, FACE_B = 2, FACE_T = 3 };
+// Boundary faces (Sec. 3.3): a face without a neighbour stores -kind in the neighbour
+// table.
+enum { BC_WALL = 1, BC_FARFIELD = 2 };
 
 // Parameters of one independent case (a batch holds several): its gas, the time terms of
 // the pseudo-step right-hand side r = R - (a0 q^c + a1 qc_n + a2 qc_nm1)/dt (per dt) and
@@ -54,8 +57,9 @@ struct CaseParams {
   // e0 is its first element in the launch's element numbering, sn = elements x points.
   long long off;
   int e0, sn;
-  int nx, ny;   // the case's periodic box: element e0 + j nx + i is at column i, row j
+  int nx, ny;   // the case's box: element e0 + j nx + i is at column i, row j
   int active;   // 0: the Newton loop of this case has stopped; its elements are skipped
+  double qinf[4];   // far-field primitive state (p, u, v, T) of far-field boundary faces
 };
 
 // Element topology of one launch: face neighbours (L, R, B, T) by global element index,
@@ -229,13 +233,13 @@ __device__ __forceinline__ void neg_viscous_flux(const T q[4], const T qx[4], co
 //   viscous (BR2, Sec. 3.1): q^com = (q+ + q-)/2, grad q^com = (grad q+ + r+ + grad q-
 //     + r-)/2 with r-+ = (q^com - q-+) S g'(end) / |J|-+, which sum to
 //     (q+ - q-) S g_R'(1) (1/|J|- + 1/|J|+) / 2;  |S| f_vis . n = f_vis . S.
+// Inviscid part alone: fnum = |S| f_n,inv^com from qm ('-' side) and qp ('+' side); also
+// returns dq = qp - qm and the averaged state qa.
 template <class T, class G, class GS>
-__device__ __forceinline__ void face_common(const T qm[4], const T qp[4], const T gm[8],
-                                            const T gp[8], G Sx, G Sy, G ug, G vg, G Jm, G Jp,
-                                            const GS& gs, double dgR_end, T fnum[4], T qcom[4]) {
-  T dq[4], qa[4];
+__device__ __forceinline__ void rusanov_common(const T qm[4], const T qp[4], G Sx, G Sy, G ug,
+                                               G vg, const GS& gs, T dq[4], T qa[4], T fnum[4]) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) { dq[k] = qp[k] - qm[k]; qa[k] = 0.5 * (qp[k] + qm[k]); qcom[k] = qa[k]; }
+  for (int k = 0; k < 4; ++k) { dq[k] = qp[k] - qm[k]; qa[k] = 0.5 * (qp[k] + qm[k]); }
   // --- normal fluxes of both sides
   T fm[4], fp[4];
   {
@@ -285,6 +289,16 @@ __device__ __forceinline__ void face_common(const T qm[4], const T qp[4], const 
   const T hl = 0.5 * lmax;
 #pragma unroll
   for (int k = 0; k < 4; ++k) fnum[k] = 0.5 * (fm[k] + fp[k]) - hl * diss[k];
+}
+
+template <class T, class G, class GS>
+__device__ __forceinline__ void face_common(const T qm[4], const T qp[4], const T gm[8],
+                                            const T gp[8], G Sx, G Sy, G ug, G vg, G Jm, G Jp,
+                                            const GS& gs, double dgR_end, T fnum[4], T qcom[4]) {
+  T dq[4], qa[4];
+  rusanov_common(qm, qp, Sx, Sy, ug, vg, gs, dq, qa, fnum);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) qcom[k] = qa[k];
   if (gs.viscous) {
     // (r- + r+)/2 = (q+ - q-) S g_R'(1) (1/|J|- + 1/|J|+) / 4
     const G lift = 0.25 * dgR_end * (inv(Jm) + inv(Jp));
@@ -297,6 +311,51 @@ __device__ __forceinline__ void face_common(const T qm[4], const T qp[4], const 
     }
     T fv[4], gv[4];
     neg_viscous_flux(qa, qx, qy, gs, fv, gv);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fnum[k] = fnum[k] + fv[k] * Sx + gv[k] * Sy;
+  }
+}
+
+// Boundary face (Sec. 3.3): the boundary state qb replaces the missing neighbour, far
+// field qb = q_inf, adiabatic no-slip wall qb = (p^-, v_g, T^-).  Inviscid: the
+// preconditioned Rusanov flux between the trace qe and qb, the element on the '-' side
+// when S points out of the domain (elem_minus), else on the '+' side.  Viscous: q^com =
+// qb, grad q^com = grad qe + r with the full one-sided lift r = (qb - qe) S g'(end)/|J|
+// (dg_end = g'(end) of the element's face: +g_R'(1) on a T face, g_L'(-1) = -g_R'(1) on a
+// B face); at a wall the component of grad T^com along S is removed (dT/dn = 0); the flux
+// f_vis(qb, grad q^com) . S.  Writes fnum = |S| f_n^com along +S and qb.
+template <class T, class G, class GS>
+__device__ __forceinline__ void face_boundary(const T qe[4], const T ge[8], G Sx, G Sy, G ug, G vg,
+                                              G Je, const GS& gs, double dg_end, bool elem_minus,
+                                              int kind, const double qinf[4], T fnum[4], T qb[4]) {
+  if (kind == BC_WALL) {
+    qb[0] = qe[0];
+    qb[1] = as_T<T>(ug);
+    qb[2] = as_T<T>(vg);
+    qb[3] = qe[3];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) qb[k] = as_T<T>(qinf[k]);
+  }
+  T dq[4], qa[4];
+  if (elem_minus) rusanov_common(qe, qb, Sx, Sy, ug, vg, gs, dq, qa, fnum);
+  else rusanov_common(qb, qe, Sx, Sy, ug, vg, gs, dq, qa, fnum);
+  if (gs.viscous) {
+    const G lift = dg_end * inv(Je);
+    T qx[4], qy[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const T jl = (qb[k] - qe[k]) * lift;
+      qx[k] = ge[k] + jl * Sx;
+      qy[k] = ge[4 + k] + jl * Sy;
+    }
+    if (kind == BC_WALL) {
+      const T gn = (qx[3] * Sx + qy[3] * Sy) * inv(Sx * Sx + Sy * Sy);
+      qx[3] = qx[3] - gn * Sx;
+      qy[3] = qy[3] - gn * Sy;
+    }
+    T fv[4], gv[4];
+    neg_viscous_flux(qb, qx, qy, gs, fv, gv);
 #pragma unroll
     for (int k = 0; k < 4; ++k) fnum[k] = fnum[k] + fv[k] * Sx + gv[k] * Sy;
   }

@@ -120,6 +120,10 @@ struct fr_ctx {
   // residual intermediates: value and tangent copies
   double *tq = nullptr, *tg = nullptr, *gl = nullptr, *fn = nullptr, *qcm = nullptr;
   double *tq_d = nullptr, *tg_d = nullptr, *gl_d = nullptr, *fn_d = nullptr, *qcm_d = nullptr;
+  // bounded meshes (fr_set_mesh_bounded): boundary kinds below row 0 / above row ny-1 and
+  // the common flux and state of the faces below row 0, [nx][4][n] (value and tangent)
+  int bounded = 0, bc_below = 0, bc_above = 0;
+  double *fnb = nullptr, *fnb_d = nullptr, *qcb = nullptr, *qcb_d = nullptr;
   // element blocks
   double* B64 = nullptr;     // [Ne][b][b] unfactored
   void* Binv = nullptr;      // scaled inverse, transposed, in the configured precision
@@ -196,6 +200,8 @@ int set_case_params(fr_ctx* c, int cid, const fr::CaseParams& p, cudaStream_t s)
 int set_time_terms(fr_ctx* c, double a0dt, double a1dt, double a2dt, cudaStream_t s);
 int set_operator_terms(fr_ctx* c, double inv_dtau, double a0_dt, cudaStream_t s);
 int fill_topology(fr_ctx* c, int nx, int ny, int e0, int cid, cudaStream_t s);
+// boundary faces below row 0 and above row ny-1 of the single case (neighbour -kind)
+int mark_bounds(fr_ctx* c, int nx, int ny, int below, int above, cudaStream_t s);
 int geometry(fr_ctx* c, const double* corners, const double* vel, cudaStream_t s);
 int residual(fr_ctx* c, const double* q, double* out, const double* qcn, const double* qcnm1,
              double a0dt, double a1dt, double a2dt, cudaStream_t s);

@@ -124,6 +124,15 @@ static __global__ void k_fill_topo(int nx, int ny, int e0, int cid, int* __restr
 
 static __global__ void k_set_case(CaseParams* cp, int cid, CaseParams value) { cp[cid] = value; }
 
+// Bounded in eta (one case from element 0): the faces below row 0 and above row ny-1
+// become boundary faces of the given kinds (neighbour -kind).
+static __global__ void k_mark_bounds(int nx, int ny, int below, int above, int* __restrict__ nbr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  nbr[4 * i + FACE_B] = -below;
+  nbr[4 * ((ny - 1) * nx + i) + FACE_T] = -above;
+}
+
 // ------------------------------------------------------------------ trace kernel
 // q^p (and the tangent) of EPB elements staged in shared memory; each thread owns one
 // solution point.  Outputs: gl[8][Ne*NP] local gradients (x comps then y comps),
@@ -210,6 +219,28 @@ __global__ void k_face(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ
   const int plus = dir == 0 ? M.right(e) : M.top(e);
   const int fm = dir == 0 ? FACE_R : FACE_T, fp = dir == 0 ? FACE_L : FACE_B;
   typename GasOf<G>::type gas = gas_for<G>(M.par(e).gas, dmach);
+  const size_t FNs = (size_t)M.ne * 4 * N;
+  if (plus < 0) {   // boundary face above the element (Sec. 3.3): the element is on the '-' side
+    T qe[4], ge[8];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qe[v] = TQ.ld((((size_t)e * 4 + fm) * 4 + v) * N + t);
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      ge[c] = M.viscous ? TG.ld((((size_t)e * 4 + fm) * 8 + c) * N + t) : from_parts<T>(0.0, 0.0);
+    const size_t om = ((size_t)e * 4 + fm) * N + t;
+    T fnum[4], qb[4];
+    face_boundary(qe, ge, geo<G>(gf, dgf, GF_SX * FNs + om), geo<G>(gf, dgf, GF_SY * FNs + om),
+                  geo<G>(gf, dgf, GF_UG * FNs + om), geo<G>(gf, dgf, GF_VG * FNs + om),
+                  geo<G>(gf, dgf, GF_J * FNs + om), gas, B.dgR_end, true, -plus, M.par(e).qinf,
+                  fnum, qb);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const size_t oo = (((size_t)e * 2 + dir) * 4 + v) * N + t;
+      FN.st(oo, fnum[v]);
+      QC.st(oo, qb[v]);
+    }
+    return;
+  }
   T qm[4], qp[4], gm[8], gp[8];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -223,7 +254,6 @@ __global__ void k_face(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ
       gp[c] = TG.ld((((size_t)plus * 4 + fp) * 8 + c) * N + t);
     }
   }
-  const size_t FNs = (size_t)M.ne * 4 * N;
   const size_t om = ((size_t)e * 4 + fm) * N + t, op = ((size_t)plus * 4 + fp) * N + t;
   T fnum[4], qcom[4];
   face_common(qm, qp, gm, gp, geo<G>(gf, dgf, GF_SX * FNs + om), geo<G>(gf, dgf, GF_SY * FNs + om),
@@ -235,6 +265,39 @@ __global__ void k_face(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ
     const size_t oo = (((size_t)e * 2 + dir) * 4 + v) * N + t;
     FN.st(oo, fnum[v]);
     QC.st(oo, qcom[v]);
+  }
+}
+
+// Boundary faces below row 0 (Sec. 3.3), which no element owns: one thread per flux
+// point of the first `nrow` elements, those whose bottom neighbour is a boundary; the
+// element is on the '+' side of +eta.  Outputs fb, qb [nrow][4][N].
+template <class T, int N, class G = double>
+__global__ void k_face_below(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ, Buf<T> TG,
+                             Buf<T> FB, Buf<T> QB, int nrow, const double* __restrict__ dgf = nullptr,
+                             double dmach = 0.0) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nrow * N) return;
+  const int e = idx / N, t = idx % N;
+  const int below = M.bottom(e);
+  if (below >= 0 || !M.on(e)) return;
+  typename GasOf<G>::type gas = gas_for<G>(M.par(e).gas, dmach);
+  const size_t FNs = (size_t)M.ne * 4 * N;
+  T qe[4], ge[8];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) qe[v] = TQ.ld((((size_t)e * 4 + FACE_B) * 4 + v) * N + t);
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    ge[c] = M.viscous ? TG.ld((((size_t)e * 4 + FACE_B) * 8 + c) * N + t) : from_parts<T>(0.0, 0.0);
+  const size_t of = ((size_t)e * 4 + FACE_B) * N + t;
+  T fnum[4], qb[4];
+  face_boundary(qe, ge, geo<G>(gf, dgf, GF_SX * FNs + of), geo<G>(gf, dgf, GF_SY * FNs + of),
+                geo<G>(gf, dgf, GF_UG * FNs + of), geo<G>(gf, dgf, GF_VG * FNs + of),
+                geo<G>(gf, dgf, GF_J * FNs + of), gas, -B.dgR_end, false, -below, M.par(e).qinf,
+                fnum, qb);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    FB.st(((size_t)e * 4 + v) * N + t, fnum[v]);
+    QB.st(((size_t)e * 4 + v) * N + t, qb[v]);
   }
 }
 
@@ -280,7 +343,8 @@ __global__ void __launch_bounds__(Tile<N, K>::THREADS)
 k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
        const double* __restrict__ gf, Buf<T> GL, Buf<T> TQ, Buf<T> FN, Buf<T> QC,
        double* __restrict__ out, TimeTerms tt, const double* __restrict__ dgs = nullptr,
-       const double* __restrict__ dgf = nullptr, double dmach = 0.0) {
+       const double* __restrict__ dgf = nullptr, double dmach = 0.0, Buf<T> FB = Buf<T>{},
+       Buf<T> QB = Buf<T>{}) {
   constexpr int NP = N * N, EPB = Tile<N, K>::EPB;
   __shared__ T sF[EPB][4][NP];
   __shared__ T sG[EPB][4][NP];
@@ -320,10 +384,13 @@ k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
                        : (f == FACE_B) ? B.dgL[j] : B.dgR[j];
         const size_t of = ((size_t)e * 4 + f) * N + s;
         const G sx = geo<G>(gf, dgf, GF_SX * FNs + of) * w * ij, sy = geo<G>(gf, dgf, GF_SY * FNs + of) * w * ij;
+        // below row 0 of a bounded mesh the common state comes from the boundary buffer
+        const bool bface = f == FACE_B && nbB < 0;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const T jump = QC.ld((((size_t)qsrc[f] * 2 + qdir[f]) * 4 + v) * N + s) -
-                         TQ.ld((((size_t)e * 4 + f) * 4 + v) * N + s);
+          const T qcf = bface ? QB.ld(((size_t)e * 4 + v) * N + s)
+                              : QC.ld((((size_t)qsrc[f] * 2 + qdir[f]) * 4 + v) * N + s);
+          const T jump = qcf - TQ.ld((((size_t)e * 4 + f) * 4 + v) * N + s);
           qx[v] = qx[v] + jump * sx;
           qy[v] = qy[v] + jump * sy;
         }
@@ -356,7 +423,8 @@ k_elem(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs,
     for (int k = 0; k < N; ++k) d = d + B.Dc[j][k] * sG[le][v][k * N + i];
     d = d + B.dgL[i] * FN.ld((((size_t)nbL * 2 + 0) * 4 + v) * N + j);
     d = d + B.dgR[i] * FN.ld((((size_t)e * 2 + 0) * 4 + v) * N + j);
-    d = d + B.dgL[j] * FN.ld((((size_t)nbB * 2 + 1) * 4 + v) * N + i);
+    d = d + B.dgL[j] * (nbB < 0 ? FB.ld(((size_t)e * 4 + v) * N + i)
+                                : FN.ld((((size_t)nbB * 2 + 1) * 4 + v) * N + i));
     d = d + B.dgR[j] * FN.ld((((size_t)e * 2 + 1) * 4 + v) * N + i);
     d = d - th.qc[v] * divst;
     R[v] = -(d * ij);

@@ -35,7 +35,8 @@ __global__ void k_conservative(const double* __restrict__ q, size_t SN, int np2,
 // ------------------------------------------------------------------ launchers
 template <class T, int N, int MODE>
 static int run_pipeline(fr_ctx* c, Buf<T> Q, Buf<T> GL, Buf<T> TQ, Buf<T> TG, Buf<T> FNb,
-                        Buf<T> QCb, double* out, TimeTerms tt, cudaStream_t s) {
+                        Buf<T> QCb, Buf<T> FBb, Buf<T> QBb, double* out, TimeTerms tt,
+                        cudaStream_t s) {
   constexpr bool jvp = MODE == MODE_JVP;
   const int kt = jvp ? c->tile.trace_d : c->tile.trace, ke = jvp ? c->tile.elem_d : c->tile.elem;
   const int nb1 = (c->ne + Tile<N, 1>::EPB - 1) / Tile<N, 1>::EPB;
@@ -61,14 +62,24 @@ static int run_pipeline(fr_ctx* c, Buf<T> Q, Buf<T> GL, Buf<T> TQ, Buf<T> TG, Bu
     FR_PROF_END(c, s, jvp ? KK_FACE_JVP : KK_FACE);
     FR_LAUNCH_CHECK(c);
   }
+  if (c->bounded) {   // the faces below row 0 (the faces above the last row are in k_face)
+    const int nbf = c->nx * N;
+    FR_PROF_BEGIN(c, s);
+    k_face_below<T, N><<<(nbf + 127) / 128, 128, 0, s>>>(c->mesh, c->basis, c->gf, TQ, TG, FBb, QBb,
+                                                         c->nx);
+    FR_PROF_END(c, s, jvp ? KK_FACE_JVP : KK_FACE);
+    FR_LAUNCH_CHECK(c);
+  }
   {
     FR_PROF_BEGIN(c, s);
     if (ke == 2)
       k_elem<T, N, MODE, double, 2><<<nb2, Tile<N, 2>::THREADS, 0, s>>>(
-          Q, c->mesh, c->basis, c->gs, c->gf, GL, TQ, FNb, QCb, out, tt);
+          Q, c->mesh, c->basis, c->gs, c->gf, GL, TQ, FNb, QCb, out, tt, nullptr, nullptr, 0.0,
+          FBb, QBb);
     else
       k_elem<T, N, MODE><<<nb1, Tile<N, 1>::THREADS, 0, s>>>(Q, c->mesh, c->basis, c->gs, c->gf,
-                                                            GL, TQ, FNb, QCb, out, tt);
+                                                            GL, TQ, FNb, QCb, out, tt, nullptr,
+                                                            nullptr, 0.0, FBb, QBb);
     FR_PROF_END(c, s, jvp ? KK_ELEM_JVP : KK_ELEM);
     FR_LAUNCH_CHECK(c);
   }
@@ -80,7 +91,8 @@ static int residual_n(fr_ctx* c, const double* q, double* out, TimeTerms tt, cud
   Buf<double> Q{const_cast<double*>(q)};
   return run_pipeline<double, N, MODE_RESID>(c, Q, Buf<double>{c->gl}, Buf<double>{c->tq},
                                              Buf<double>{c->tg}, Buf<double>{c->fn},
-                                             Buf<double>{c->qcm}, out, tt, s);
+                                             Buf<double>{c->qcm}, Buf<double>{c->fnb},
+                                             Buf<double>{c->qcb}, out, tt, s);
 }
 
 template <int N>
@@ -89,7 +101,8 @@ static int jvp_n(fr_ctx* c, const double* q, const double* v, double* out, cudaS
   TimeTerms tt{nullptr, nullptr};
   return run_pipeline<Dual, N, MODE_JVP>(c, Q, Buf<Dual>{c->gl, c->gl_d}, Buf<Dual>{c->tq, c->tq_d},
                                          Buf<Dual>{c->tg, c->tg_d}, Buf<Dual>{c->fn, c->fn_d},
-                                         Buf<Dual>{c->qcm, c->qcm_d}, out, tt, s);
+                                         Buf<Dual>{c->qcm, c->qcm_d}, Buf<Dual>{c->fnb, c->fnb_d},
+                                         Buf<Dual>{c->qcb, c->qcb_d}, out, tt, s);
 }
 
 }  // namespace fr
@@ -155,6 +168,12 @@ int upload_cases(fr_ctx* c, cudaStream_t s) {
 
 int fill_topology(fr_ctx* c, int nx, int ny, int e0, int cid, cudaStream_t s) {
   k_fill_topo<<<(nx * ny + 127) / 128, 128, 0, s>>>(nx, ny, e0, cid, c->nbr, c->ecase);
+  FR_LAUNCH_CHECK(c);
+  return FR_OK;
+}
+
+int mark_bounds(fr_ctx* c, int nx, int ny, int below, int above, cudaStream_t s) {
+  k_mark_bounds<<<(nx + 127) / 128, 128, 0, s>>>(nx, ny, below, above, c->nbr);
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }

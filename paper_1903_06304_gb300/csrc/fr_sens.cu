@@ -129,6 +129,7 @@ extern "C" int fr_param_vjp(fr_ctx* c, const double* q, const double* w, const d
   if (c->ne <= 0) { snprintf(c->err, sizeof(c->err), "fr_set_mesh has not been called"); return FR_ERR_ARG; }
   if (!q || !w || !corners || !vel) return FR_ERR_ARG;
   if (c->ncases != 1) { snprintf(c->err, sizeof(c->err), "fr_param_vjp: single-case contexts only"); return FR_ERR_ARG; }
+  if (c->bounded) { snprintf(c->err, sizeof(c->err), "fr_param_vjp: not available on bounded meshes"); return FR_ERR_ARG; }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t ne = c->ne, SN = ne * c->np2, FN = ne * 4 * c->n;
   FR_TRY(frk::lazy_alloc(c, &c->sgs, GS_COUNT * SN));

@@ -77,6 +77,7 @@ _SIGS = {
     "fr_create": (_I, [ctypes.POINTER(_Config), ctypes.POINTER(_P)]),
     "fr_destroy": (None, [_P]),
     "fr_set_mesh": (_I, [_P, _I, _I, _I, _I]),
+    "fr_set_mesh_bounded": (_I, [_P, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_double)]),
     "fr_update_mesh": (_I, [_P, _P, _P, _P]),
     "fr_residual": (_I, [_P, _P, _P, _P]),
     "fr_bdf_rhs": (_I, [_P, _P, _P, _P, _D, _D, _D, _D, _P, _P]),
@@ -334,10 +335,15 @@ class Batch:
                 for k in range(PROF_KINDS)}
 
 
-class Solver:
-    """One library context: a mesh of nx-by-ny periodic bilinear quads at degree p."""
+BC = {"wall": 1, "farfield": 2}
 
-    def __init__(self, cfg: Config, nx: int, ny: int):
+
+class Solver:
+    """One library context: a mesh of nx-by-ny bilinear quads at degree p, periodic in
+    both directions, or with ``bc=(below row 0, above row ny-1)`` (each "wall" or
+    "farfield", far-field state ``q_inf`` = (p, u, v, T)) periodic in xi only."""
+
+    def __init__(self, cfg: Config, nx: int, ny: int, bc=None, q_inf=None):
         self.lib = load()
         self.cfg = cfg
         self._cc = cfg.to_c()
@@ -345,7 +351,11 @@ class Solver:
         self._check(self.lib.fr_create(ctypes.byref(self._cc), ctypes.byref(h)), None)
         self.ctx = h
         self.nx, self.ny = nx, ny
-        self._check(self.lib.fr_set_mesh(self.ctx, nx, ny, 1, 1))
+        if bc is None:
+            self._check(self.lib.fr_set_mesh(self.ctx, nx, ny, 1, 1))
+        else:
+            qi = None if q_inf is None else (ctypes.c_double * 4)(*[float(x) for x in q_inf])
+            self._check(self.lib.fr_set_mesh_bounded(self.ctx, nx, ny, BC[bc[0]], BC[bc[1]], qi))
         self.n = cfg.p + 1
         self.ne = nx * ny
         self.ndof = int(self.lib.fr_num_dof(self.ctx))
