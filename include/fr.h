@@ -176,10 +176,10 @@ int fr_set_mesh(fr_ctx* ctx, int nx, int ny, int periodic_x, int periodic_y);
  * required when a side is a far field, may be NULL otherwise; copied.  Boundary faces
  * take the interior trace's local gradient with the full one-sided BR2 lift of
  * q_b - q^- (the boundary state is also q^com).  Allocates like fr_set_mesh plus 4
- * arrays of nx*4*(p+1) doubles.  On a bounded mesh the available calls are
- * fr_update_mesh, fr_residual, fr_bdf_rhs, fr_jvp (dual numbers), fr_conservative and
- * fr_residual_norms; the linearised operator, element blocks, VJP, GMRES, the Newton
- * loops and fr_param_vjp return FR_ERR_ARG (message in fr_last_error).  FR_ERR_ARG also
+ * arrays of nx*4*(p+1) doubles.  On a bounded mesh the Newton operator and the element
+ * blocks are formed by dual numbers whatever cfg.jvp_mode / cfg.block_mode say (the
+ * configured modes return with the next fr_set_mesh); fr_linearize, fr_apply_linear,
+ * fr_vjp and fr_param_vjp return FR_ERR_ARG (message in fr_last_error).  FR_ERR_ARG also
  * for nx < 2, ny < 1, an unknown kind or a missing / non-positive q_inf. */
 int fr_set_mesh_bounded(fr_ctx* ctx, int nx, int ny, int bc_below, int bc_above,
                         const double* q_inf_h);

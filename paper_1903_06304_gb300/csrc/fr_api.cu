@@ -193,6 +193,10 @@ void free_mesh(fr_ctx* c) {
   if (c->ecase) { cudaFree(c->ecase); c->ecase = nullptr; }
   c->blocks_ready = 0;
   c->lin_ready = 0;
+  if (c->bounded) {   // back to the configured operator and block modes
+    c->cfg.jvp_mode = c->user_jvp_mode;
+    c->cfg.block_mode = c->user_block_mode;
+  }
   c->bounded = c->bc_below = c->bc_above = 0;
   frk::batch_free(c);
   graphs_free(c);
@@ -207,12 +211,12 @@ int check_ready(fr_ctx* c) {
   return FR_OK;
 }
 
-// The linearised operator, element blocks, the VJP, GMRES and the Newton loops do not
-// treat boundary faces yet: refused on bounded meshes before any launch.
+// The stored local Jacobians (linearised operator, VJP) and the parameter sensitivities
+// do not treat boundary faces yet: refused on bounded meshes before any launch.
 int need_periodic(fr_ctx* c, const char* what) {
   if (!c->bounded) return FR_OK;
-  snprintf(c->err, sizeof(c->err), "%s: not available on bounded meshes (residual, "
-           "fr_bdf_rhs, fr_jvp and fr_conservative are)", what);
+  snprintf(c->err, sizeof(c->err), "%s: not available on bounded meshes (the residual, "
+           "dual-number JVP, element blocks, GMRES and Newton loops are)", what);
   return FR_ERR_ARG;
 }
 
@@ -634,6 +638,12 @@ int fr_set_mesh_bounded(fr_ctx* c, int nx, int ny, int bc_below, int bc_above, c
   c->bounded = 1;
   c->bc_below = bc_below;
   c->bc_above = bc_above;
+  // the stored local Jacobians do not cover boundary faces: the Newton operator and the
+  // element blocks are formed by dual numbers on a bounded mesh
+  c->user_jvp_mode = c->cfg.jvp_mode;
+  c->user_block_mode = c->cfg.block_mode;
+  c->cfg.jvp_mode = FR_JVP_DUAL;
+  c->cfg.block_mode = FR_BLOCK_DUAL;
   const size_t nb = (size_t)nx * 4 * c->n;
   FR_TRY(dev_alloc(c, &c->fnb, nb));
   FR_TRY(dev_alloc(c, &c->fnb_d, nb));
@@ -786,7 +796,6 @@ int fr_vjp(fr_ctx* c, const double* q, const double* w, double inv_dtau, double 
 
 int fr_precond_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, void* s) {
   FR_TRY(check_ready(c));
-  FR_TRY(need_periodic(c, "fr_precond_build"));
   FR_TRY(frk::block_build(c, q, inv_dtau, a0_dt, S(s)));
   c->blocks_ready = 1;
   return FR_OK;
@@ -809,7 +818,6 @@ int fr_precond_apply(fr_ctx* c, const double* r, double* z, void* s) {
 int fr_gmres(fr_ctx* c, const double* q, const double* b, double inv_dtau, double a0_dt, double* x,
              int* iters, void* s) {
   FR_TRY(check_ready(c));
-  FR_TRY(need_periodic(c, "fr_gmres"));
   if (!c->blocks_ready) { snprintf(c->err, sizeof(c->err), "no preconditioner built"); return FR_ERR_ARG; }
   if (c->cfg.jvp_mode == FR_JVP_LINEARIZED) FR_TRY(frk::linearize(c, q, inv_dtau, a0_dt, S(s)));
   int its = 0;
@@ -821,14 +829,12 @@ int fr_gmres(fr_ctx* c, const double* q, const double* b, double inv_dtau, doubl
 int fr_bdf2_step(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, double a0, double a1,
                  double a2, double dt, fr_stats* st, void* s) {
   FR_TRY(check_ready(c));
-  FR_TRY(need_periodic(c, "fr_bdf2_step"));
   if (!q || !qcn || dt <= 0 || (a2 != 0.0 && !qcnm1)) return FR_ERR_ARG;
   return newton_loop(c, q, qcn, qcnm1, a0, a1, a2, dt, false, st, S(s));
 }
 
 int fr_ptc_solve(fr_ctx* c, double* q, fr_stats* st, void* s) {
   FR_TRY(check_ready(c));
-  FR_TRY(need_periodic(c, "fr_ptc_solve"));
   if (!q) return FR_ERR_ARG;
   return newton_loop(c, q, nullptr, nullptr, 0, 0, 0, 1.0, true, st, S(s));
 }

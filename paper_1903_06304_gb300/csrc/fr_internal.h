@@ -123,6 +123,7 @@ struct fr_ctx {
   // bounded meshes (fr_set_mesh_bounded): boundary kinds below row 0 / above row ny-1 and
   // the common flux and state of the faces below row 0, [nx][4][n] (value and tangent)
   int bounded = 0, bc_below = 0, bc_above = 0;
+  int user_jvp_mode = 0, user_block_mode = 0;   // the configured modes while bounded
   double *fnb = nullptr, *fnb_d = nullptr, *qcb = nullptr, *qcb_d = nullptr;
   // element blocks
   double* B64 = nullptr;     // [Ne][b][b] unfactored

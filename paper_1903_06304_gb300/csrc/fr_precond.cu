@@ -114,6 +114,22 @@ k_block(const double* __restrict__ q, Mesh M, Basis B, const double* __restrict_
     //    geometry is that of the owning ('-') element, as in the residual.
     for (int t = pt; t < 4 * N; t += NP) {
       const int f = t / N, s = t % N;
+      const int nb_f = f == FACE_L ? nbL : f == FACE_R ? nbR : f == FACE_B ? nbB : nbT;
+      if (nb_f < 0) {   // boundary face (Sec. 3.3): a function of e's own trace alone
+        Dual qe[4], ge[8];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qe[v] = stq[(f * 4 + v) * N + s];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) ge[c] = M.viscous ? stg[(f * 8 + c) * N + s] : mk(0.0, 0.0);
+        const size_t of = ((size_t)e * 4 + f) * N + s;
+        Dual fnum[4], qb[4];
+        face_boundary(qe, ge, gf[GF_SX * FNs + of], gf[GF_SY * FNs + of], gf[GF_UG * FNs + of],
+                      gf[GF_VG * FNs + of], gf[GF_J * FNs + of], gas,
+                      f == FACE_T ? B.dgR_end : -B.dgR_end, f == FACE_T, -nb_f, cpar.qinf, fnum, qb);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { sfn[(f * 4 + v) * N + s] = fnum[v]; sqc[(f * 4 + v) * N + s] = qb[v]; }
+        continue;
+      }
       Dual qm[4], qp[4], gm[8], gp[8];
       int own_m;           // element owning the face (its R or T face)
       int fo, fother, other;

@@ -1,7 +1,8 @@
-"""Bounded meshes (fr_set_mesh_bounded): the residual and the dual-number JVP with wall and
-far-field faces (Sec. 3.3) against the oracle, on plunging NACA 0012 O-grids (Secs. 4.2,
-4.4) from a few elements up to the full 256 x 96 grid; and the calls that do not treat
-boundary faces yet refuse a bounded mesh."""
+"""Bounded meshes (fr_set_mesh_bounded): the residual, the dual-number JVP, the element
+blocks, GMRES and a BDF step with wall and far-field faces (Sec. 3.3) against the oracle,
+on plunging NACA 0012 O-grids (Secs. 4.2, 4.4) from a few elements up to the full
+256 x 96 grid; and the stored-Jacobian calls, which do not treat boundary faces yet,
+refuse a bounded mesh."""
 import numpy as np
 import pytest
 
@@ -11,7 +12,8 @@ from oracle import scale as sc
 from oracle import solver as sv
 from paper_1903_06304_gb300 import inputs as inp
 
-from gpu_helpers import JVP_TOL, RES_TOL, jvp_errors, residual_errors, to_dev, to_host
+from gpu_helpers import (BLK_TOL, JVP_TOL, RES_TOL, block_errors, jvp_errors, residual_errors,
+                         to_dev, to_host)
 
 pytestmark = pytest.mark.gpu
 
@@ -26,14 +28,14 @@ def torch():
     return torch
 
 
-def bounded_case(ni, nj, p, mach, re, kappa, bc, t=0.3, seed=7, rel=0.05):
+def bounded_case(ni, nj, p, mach, re, kappa, bc, t=0.3, seed=7, rel=0.05, first=1e-3, **kw):
     from paper_1903_06304_gb300 import fr
-    c, v = inp.plunge(inp.naca_ogrid(ni, nj), t)
+    c, v = inp.plunge(inp.naca_ogrid(ni, nj, first=first), t)
     qi = inp.far_field_state(mach)
     gas = ph.Gas(mach=mach, re=re, kappa=kappa)
     mesh = rs.Mesh(ni, nj, c, v, bc=(KIND[bc[0]], KIND[bc[1]]), q_inf=qi)
     q = inp.random_perturbation(inp.uniform_state(ni * nj, p, mach), seed, rel, mach)
-    S = fr.Solver(fr.Config(p=p, mach=mach, re=re, kappa=kappa), ni, nj, bc=bc, q_inf=qi)
+    S = fr.Solver(fr.Config(p=p, mach=mach, re=re, kappa=kappa, **kw), ni, nj, bc=bc, q_inf=qi)
     S.update_mesh(to_dev(c), to_dev(v))
     return S, sv.Problem(mesh, p, gas), q
 
@@ -108,18 +110,65 @@ def test_bounded_residual_full_naca_ogrid(torch):
     assert np.all(err <= RES_TOL), err
 
 
-def test_bounded_mesh_refuses_solver_paths(torch):
+@pytest.mark.parametrize("re", [0.0, 200.0])
+def test_bounded_blocks_parity(torch, re):
+    """Element blocks by dual numbers with wall and far-field faces (the boundary flux
+    depends on the element's own trace) against the oracle's complex-step blocks."""
+    S, prob, q = bounded_case(10, 4, 2, 0.1, re, 1.0, ("wall", "farfield"), first=0.05)
+    inv_dtau, a0_dt = 0.2, 150.0
+    S.precond_build(to_dev(q), inv_dtau, a0_dt)
+    B = torch.empty((prob.mesh.ne, S.block_size, S.block_size), dtype=torch.float64, device="cuda:0")
+    S.precond_blocks(B)
+    err = block_errors(to_host(B), sv.block_jacobian(prob, q, inv_dtau, a0_dt), 9)
+    assert np.all(err <= BLK_TOL), err
+
+
+@pytest.mark.parametrize("side", ["left", "right"])
+def test_bounded_gmres_parity(torch, side):
+    S, prob, q = bounded_case(10, 4, 2, 0.1, 200.0, 1.0, ("wall", "farfield"), first=0.05,
+                              restart=20, maxit_lin=200, tol_res=1e-8, gmres_side=side)
+    inv_dtau, a0_dt = 1e-20, 100.0
+    b = inp.random_vector(q.shape, 13)
+    Binv = np.linalg.inv(sv.block_jacobian(prob, q, inv_dtau, a0_dt))
+    P = lambda x: sv.block_apply(Binv, x)
+    want = sv.gmres(lambda x: sv.apply_A(prob, q, x, inv_dtau, a0_dt), b, P, 20, 1e-8, 200, side=side)
+    qd = to_dev(q)
+    S.precond_build(qd, inv_dtau, a0_dt)
+    x = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+    its = S.gmres(qd, to_dev(b), x, inv_dtau, a0_dt)
+    assert its == want.iterations
+    assert np.abs(to_host(x) - want.x).max() <= 1e-9 * np.abs(want.x).max()
+
+
+def test_bounded_bdf_step_parity(torch):
+    """One BDF1 step on a plunging O-grid with a wall and a far field: the Newton loop with
+    the dual-number operator and blocks takes the oracle's Newton and GMRES iterations."""
+    from paper_1903_06304_gb300 import fr
+    kw = dict(restart=30, tol_res=1e-6, maxit_lin=100, tol_pseudo=1e-8, maxit_newton=10, lag=2)
+    S, prob, q = bounded_case(10, 4, 2, 0.1, 200.0, 1.0, ("wall", "farfield"), first=0.05, rel=0.02,
+                              **kw)
+    qc = prob.qc(q)
+    q1, st = sv.bdf2_step(prob, q, qc, qc, 0.01, coeffs=sv.BDF1, **kw)
+    qd, qcd = to_dev(q), to_dev(qc)
+    sg = S.bdf2_step(qd, qcd, qcd, 0.01, coeffs=fr.BDF1).summary()
+    assert sg["converged"] and st.converged
+    assert sg["newton_iterations"] == st.newton_iterations
+    assert sg["gmres_iterations"] == st.gmres_iterations
+    np.testing.assert_allclose(sg["res_history"], st.res_history, rtol=1e-6,
+                               atol=1e-12 * st.res_history[0])
+    scale = np.abs(q1 - q).max(axis=(1, 2, 3))
+    assert np.all(np.abs(to_host(qd) - q1).max(axis=(1, 2, 3)) <= 1e-6 * scale)
+
+
+def test_bounded_mesh_refuses_stored_jacobian_paths(torch):
     from paper_1903_06304_gb300 import fr
     S, prob, q = bounded_case(8, 3, 2, 0.1, 50.0, 1.0, ("wall", "farfield"))
     qd = to_dev(q)
     with pytest.raises(fr.FrError, match="bounded"):
-        S.precond_build(qd, 0.0, 150.0)
-    with pytest.raises(fr.FrError, match="bounded"):
         S.linearize(qd, 0.0, 150.0)
-    qc = torch.empty_like(qd)
-    S.conservative(qd, qc)
+    out = torch.empty_like(qd)
     with pytest.raises(fr.FrError, match="bounded"):
-        S.bdf2_step(qd, qc, qc, 0.01, coeffs=fr.BDF1)
+        S.vjp(qd, qd, out, 0.0, 150.0)
     # the available calls still work after a refusal
     R = torch.empty_like(qd)
     S.residual(qd, R)
