@@ -184,6 +184,17 @@ int fr_set_mesh(fr_ctx* ctx, int nx, int ny, int periodic_x, int periodic_y);
 int fr_set_mesh_bounded(fr_ctx* ctx, int nx, int ny, int bc_below, int bc_above,
                         const double* q_inf_h);
 
+/* Force of the fluid on the wall faces of a bounded mesh (the numerator of the force
+ * coefficients of Sec. 4, per unit span): F = sum over wall faces of the integral of
+ * -(p - p_inf) n + tau . n, with n the unit normal out of the body, p_inf = 1/(gamma M^2),
+ * the pressure of the interior trace and the viscous stress of the wall's common
+ * gradient (the same as in the wall's viscous flux), Gauss quadrature on the flux
+ * points.  q_d: device state vector; force_h: host array receiving (F_x, F_y);
+ * deterministic.  C_d = F_x / (rho_inf U_inf^2 c / 2) for a free stream along +x, C_l
+ * likewise with F_y, C_t = -C_d.  Synchronises the stream.  FR_ERR_ARG if the mesh has
+ * no wall faces. */
+int fr_wall_force(fr_ctx* ctx, const double* q_d, double* force_h, void* stream);
+
 /* Update geometry at the current time (Sec. 2.3): corners_d and corner_vel_d are
  * device [Ne][4][2] FP64 (corner coordinates and their grid velocities); the library
  * evaluates |J|, |J| grad(xi), |J| grad(eta), v_g and |J| xi_t, |J| eta_t at solution and

@@ -49,6 +49,12 @@ fr::Basis fr_make_basis(int p) {
   double xs[fr::MAXN];
   gauss_points(n, xs);
   for (int i = 0; i < n; ++i) B.xs[i] = xs[i];
+  // Gauss weights w_i = 2 / ((1 - x_i^2) P_n'(x_i)^2)
+  for (int i = 0; i < n; ++i) {
+    double P, dP;
+    legendre(n, xs[i], &P, &dP);
+    B.ws[i] = 2.0 / ((1.0 - xs[i] * xs[i]) * dP * dP);
+  }
   // barycentric weights
   double bw[fr::MAXN];
   for (int k = 0; k < n; ++k) {
@@ -617,6 +623,16 @@ int fr_set_mesh(fr_ctx* c, int nx, int ny, int px, int py) {
     return FR_ERR_ARG;
   }
   return fr_setup_cases(c, 1, &nx, &ny, &c->cp_h);
+}
+
+int fr_wall_force(fr_ctx* c, const double* q, double* force_h, void* s) {
+  FR_TRY(check_ready(c));
+  if (!q || !force_h) return FR_ERR_ARG;
+  if (!c->bounded || (c->bc_below != FR_BC_WALL && c->bc_above != FR_BC_WALL)) {
+    snprintf(c->err, sizeof(c->err), "fr_wall_force: the mesh has no wall faces");
+    return FR_ERR_ARG;
+  }
+  return frk::wall_force(c, q, force_h, S(s));
 }
 
 int fr_set_mesh_bounded(fr_ctx* c, int nx, int ny, int bc_below, int bc_above, const double* q_inf_h) {

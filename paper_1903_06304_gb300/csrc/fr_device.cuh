@@ -24,6 +24,7 @@ struct Basis {
   double dgL[MAXN], dgR[MAXN];
   double dgR_end;         // g_R'(1) = (p+1)^2/2; g_L'(-1) = -g_R'(1)
   double xs[MAXN];        // solution points
+  double ws[MAXN];        // Gauss weights of the solution points
 };
 
 // Nondimensional gas of Sec. 2.1 and preconditioning cut-off (Eqs. eps_nonmove/move).

@@ -203,6 +203,8 @@ int set_operator_terms(fr_ctx* c, double inv_dtau, double a0_dt, cudaStream_t s)
 int fill_topology(fr_ctx* c, int nx, int ny, int e0, int cid, cudaStream_t s);
 // boundary faces below row 0 and above row ny-1 of the single case (neighbour -kind)
 int mark_bounds(fr_ctx* c, int nx, int ny, int below, int above, cudaStream_t s);
+// force on the wall faces of a bounded mesh into force_h[2] (host; synchronises s)
+int wall_force(fr_ctx* c, const double* q, double* force_h, cudaStream_t s);
 int geometry(fr_ctx* c, const double* corners, const double* vel, cudaStream_t s);
 int residual(fr_ctx* c, const double* q, double* out, const double* qcn, const double* qcnm1,
              double a0dt, double a1dt, double a2dt, cudaStream_t s);

@@ -78,6 +78,7 @@ _SIGS = {
     "fr_destroy": (None, [_P]),
     "fr_set_mesh": (_I, [_P, _I, _I, _I, _I]),
     "fr_set_mesh_bounded": (_I, [_P, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_double)]),
+    "fr_wall_force": (_I, [_P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "fr_update_mesh": (_I, [_P, _P, _P, _P]),
     "fr_residual": (_I, [_P, _P, _P, _P]),
     "fr_bdf_rhs": (_I, [_P, _P, _P, _P, _D, _D, _D, _D, _P, _P]),
@@ -399,6 +400,12 @@ class Solver:
     def residual(self, q, out, stream=None):
         self._check(self.lib.fr_residual(self.ctx, _ptr(q), _ptr(out), _stream(stream)))
         return out
+
+    def wall_force(self, q, stream=None):
+        """(F_x, F_y) of the fluid on the wall faces of a bounded mesh (per unit span)."""
+        f = (ctypes.c_double * 2)()
+        self._check(self.lib.fr_wall_force(self.ctx, _ptr(q), f, _stream(stream)))
+        return float(f[0]), float(f[1])
 
     def bdf_rhs(self, q, qc_n, qc_nm1, coeffs, dt, out, stream=None):
         a0, a1, a2 = coeffs

@@ -160,6 +160,45 @@ def test_bounded_bdf_step_parity(torch):
     assert np.all(np.abs(to_host(qd) - q1).max(axis=(1, 2, 3)) <= 1e-6 * scale)
 
 
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("re", [0.0, 200.0])
+@pytest.mark.parametrize("bc", [("wall", "farfield"), ("farfield", "wall"), ("wall", "wall")])
+def test_wall_force_parity(torch, p, re, bc):
+    """The device wall force against the oracle's (pressure and viscous traction of the
+    wall's common gradient, Gauss quadrature over the wall faces)."""
+    S, prob, q = bounded_case(13, 5, p, 0.1, re, 1.0, bc)
+    got = np.array(S.wall_force(to_dev(q)))
+    want = np.array(rs.wall_force(q, prob.mesh, p, prob.gas))
+    # the integrand sums terms of the size of p - p_inf and of the stress over the wall
+    scale = max(np.abs(want).max(), 1e-3)
+    assert np.all(np.abs(got - want) <= 1e-11 * scale), (got, want)
+
+
+def test_wall_force_of_linear_pressure_is_exact(torch):
+    """No flow, p = p_inf + a x + b y: F = -(a, b) x the area enclosed by the wall polygon."""
+    from paper_1903_06304_gb300 import fr
+    ni, nj, p, mach = 48, 4, 3, 0.05
+    c = inp.naca_ogrid(ni, nj)
+    qi = inp.far_field_state(mach)
+    S = fr.Solver(fr.Config(p=p, mach=mach, re=50.0, kappa=1.0), ni, nj, bc=("wall", "farfield"),
+                  q_inf=qi)
+    S.update_mesh(to_dev(c), to_dev(np.zeros_like(c)))
+    a, b = 0.3, -0.7
+    X, Y = inp.sample_points(c, p)
+    q = np.stack([inp.p_inf(mach) + a * X + b * Y, 0 * X, 0 * X, 1 + 0 * X])
+    Fx, Fy = S.wall_force(to_dev(q))
+    w = c[:ni, 0]
+    A = abs(0.5 * np.sum(w[:, 0] * np.roll(w[:, 1], -1) - np.roll(w[:, 0], -1) * w[:, 1]))
+    assert abs(Fx + a * A) <= 1e-11 and abs(Fy + b * A) <= 1e-11, (Fx, Fy, -a * A, -b * A)
+
+
+def test_wall_force_needs_a_wall(torch):
+    from paper_1903_06304_gb300 import fr
+    S, prob, q = bounded_case(8, 3, 2, 0.1, 50.0, 1.0, ("farfield", "farfield"))
+    with pytest.raises(fr.FrError, match="wall"):
+        S.wall_force(to_dev(q))
+
+
 def test_bounded_mesh_refuses_stored_jacobian_paths(torch):
     from paper_1903_06304_gb300 import fr
     S, prob, q = bounded_case(8, 3, 2, 0.1, 50.0, 1.0, ("wall", "farfield"))
