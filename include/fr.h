@@ -12,9 +12,10 @@
  *
  * Conventions shared by every call
  * --------------------------------
- * - Element e = j*nx + i on a structured nx-by-ny quad mesh (periodic in both
- *   directions); corners per element in the order (xi,eta) = (-1,-1), (1,-1), (1,1),
- *   (-1,1).
+ * - Element e = j*nx + i on a structured nx-by-ny quad mesh, periodic in both
+ *   directions (fr_set_mesh) or in xi only with boundary faces below row 0 and above
+ *   row ny-1 (fr_set_mesh_bounded); corners per element in the order (xi,eta) =
+ *   (-1,-1), (1,-1), (1,1), (-1,1).
  * - Solution vectors (q^p, R, v, A v, q^c histories) are FP64, structure of arrays
  *   [4][Ne][n][n] with n = p+1: variable, element, eta index j, xi index i.
  *   Their length is fr_num_dof().  The caller owns them (device memory).
