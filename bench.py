@@ -135,6 +135,32 @@ def replica_throughput(t_rank: float, units_per_rank: float, world: int, dist, d
     return t_max, units_per_rank * world / t_max / 1e9
 
 
+def shard_cases(dofs, world: int):
+    """Independent cases dealt to `world` ranks: largest first, each to the least loaded
+    rank (DOF as the load, ties to the lower rank).  Deterministic; every case exactly
+    once; each rank's list in case order."""
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for k in sorted(range(len(dofs)), key=lambda k: (-dofs[k], k)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        parts[r].append(k)
+        load[r] += dofs[k]
+    return [sorted(p) for p in parts]
+
+
+def sharded_throughput(t_rank: float, units_total: float, world: int, dist, device):
+    """Throughput of a fixed set of units shared by `world` ranks (strong scaling): the
+    slowest rank's time (all-reduce MAX) and all units per second over it, in billions.
+    Returns (t_max, value)."""
+    import torch
+    t_max = t_rank
+    if dist is not None and world > 1:
+        tt = torch.tensor([t_rank], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    return t_max, units_total / t_max / 1e9
+
+
 # ------------------------------------------------------------------ CPU oracle sample
 def oracle_sample(steps: int, warmup: int):
     """The oracle as it stands on a bounded sample: BDF2 steps on the 16x16 sub-box."""
@@ -596,13 +622,28 @@ def kernels_only(args):
 def batch_arm(args):
     """Independent cases advanced together (fr_batch_*): the seeded batch recipe (mesh
     side 32..128, p in {2,3,4}, M in [0.01, 0.3], vortex or bump, Re = 100 on the box),
-    one BDF2 step of every case per bench step; value = DOF of all cases x steps / time."""
+    one BDF2 step of every case per bench step; value = DOF of all cases x steps / time.
+    On N ranks the cases are sharded (shard_cases), no data-path collective: each rank
+    advances its own batch, the time is the slowest rank's (strong scaling)."""
     import numpy as np
     import torch
     from paper_1903_06304_gb300 import fr
     from paper_1903_06304_gb300 import inputs as inp
-    dev = "cuda:0"
-    cs = inp.batch_cases(seed=0, ncases=args.batch_cases)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    all_cs = inp.batch_cases(seed=0, ncases=args.batch_cases)
+    dof_all = [4 * c.n * c.n * (c.p + 1) ** 2 for c in all_cs]
+    mine = shard_cases(dof_all, world)[rank]
+    if not mine:
+        raise SystemExit(f"rank {rank}: no case of {len(all_cs)} left for it; use fewer ranks")
+    cs = [all_cs[k] for k in mine]
     cases = [fr.Case(c.p, c.n, c.n, c.mach, c.re, c.kappa) for c in cs]
     cfg = fr.Config(prec=args.prec, restart=args.restart, maxit_lin=args.maxit_lin,
                     maxit_newton=args.maxit_newton, lag=2, line_search=args.line_search,
@@ -632,12 +673,18 @@ def batch_arm(args):
         state["k"] += 1
         return st
 
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
     for _ in range(args.warmup):
         step()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     launches0 = B.kernel_launches
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(local)
     ms, stats = [], []
+    barrier()
     for _ in range(args.steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -647,26 +694,41 @@ def batch_arm(args):
         b.record()
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
+    barrier()
     clock_info = clocks.stop()
     launches = B.kernel_launches - launches0
-    t = sum(ms) / 1e3
+    t, value = sharded_throughput(sum(ms) / 1e3, float(sum(dof_all) * args.steps), world, dist, dev)
     newton = [s.newton_iterations for st in stats for s in st]
     gmres = [sum(s.gmres_iterations[:s.newton_iterations]) for st in stats for s in st]
     conv = [s.converged for st in stats for s in st]
+    # per-rank statistics summed (counts) or maxed over the ranks
+    agg = torch.tensor([sum(conv), sum(newton), len(newton), sum(gmres), launches],
+                       dtype=torch.float64, device=dev)
+    mx = torch.tensor([max(newton), max(gmres)], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(agg)
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    n_conv, n_newton, n_rows, n_gmres, all_launches = agg.tolist()
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
     out = {"metric": "batched BDF2 steps of independent cases (GDOF/s)", "impl": "ours",
-           "value": B.ndof * args.steps / t / 1e9, "unit": "GDOF/s", "n_gpus": 1,
+           "value": value, "unit": "GDOF/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
-           "higher_is_better": True, "scaling": "weak", "dtype": "f64 (blocks %s)" % args.prec,
+           "higher_is_better": True, "scaling": "strong", "dtype": "f64 (blocks %s)" % args.prec,
            "data": "synthetic",
-           "config": {"workload": f"batch of {len(cs)} cases (seed 0)", "cases": len(cs),
-                      "groups": B.num_groups, "dof": B.ndof, "elements": B.ne,
+           "config": {"workload": f"batch of {len(all_cs)} cases (seed 0)", "cases": len(all_cs),
+                      "cases_rank0": len(cs), "groups_rank0": B.num_groups, "dof": sum(dof_all),
+                      "elements": sum(c.n * c.n for c in all_cs),
                       "prec": args.prec, "restart": args.restart, "maxit_lin": args.maxit_lin,
                       "maxit_newton": args.maxit_newton, "line_search": args.line_search,
-                      "graphs": args.graphs, "l2": "256 MiB flush between steps"},
-           "cases_converged_per_step": sum(conv) / args.steps,
-           "newton_iterations": {"mean": statistics.mean(newton), "max": max(newton)},
-           "gmres_iterations": {"mean": statistics.mean(gmres), "max": max(gmres)},
-           "gpu_launches": launches, "clocks": clock_info}
+                      "graphs": args.graphs, "l2": "256 MiB flush between steps",
+                      "parallelism": f"cases sharded over {world} ranks" if world > 1 else "single"},
+           "cases_converged_per_step": n_conv / args.steps,
+           "newton_iterations": {"mean": n_newton / n_rows, "max": int(mx[0])},
+           "gmres_iterations": {"mean": n_gmres / n_rows, "max": int(mx[1])},
+           "gpu_launches": int(all_launches), "clocks": clock_info}
     print(json.dumps(out))
 
 

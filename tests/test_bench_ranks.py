@@ -58,3 +58,53 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     with redirect_stdout(buf):
         bench.reference_arm(argparse.Namespace(steps=1, warmup=3, gpus=2))
     assert buf.getvalue() == ""
+
+
+def test_shard_cases_partitions_and_balances():
+    """Every case on exactly one rank, each rank's cases in order, and the loads within one
+    case of each other (largest-first to the least loaded rank)."""
+    import bench
+    from paper_1903_06304_gb300 import inputs as inp
+    cs = inp.batch_cases(seed=0, ncases=64)
+    dofs = [4 * c.n * c.n * (c.p + 1) ** 2 for c in cs]
+    for world in (1, 2, 3, 4, 8):
+        parts = bench.shard_cases(dofs, world)
+        flat = sorted(k for p in parts for k in p)
+        assert flat == list(range(len(cs)))
+        assert all(p == sorted(p) for p in parts)
+        loads = [sum(dofs[k] for k in p) for p in parts]
+        assert max(loads) - min(loads) <= max(dofs), (world, loads)
+    assert bench.shard_cases(dofs, 1) == [list(range(len(cs)))]
+    assert bench.shard_cases([5, 5], 3)[2] == []          # more ranks than cases: one idles
+
+
+def _shard_rank(rank, world, port, out):
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # a fixed total of 6e9 units shared by the ranks; rank r needed 2 + r seconds
+    t_max, value = bench.sharded_throughput(2.0 + rank, 6.0e9, world, dist, "cpu")
+    out.put((rank, t_max, value))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_throughput_two_gloo_ranks():
+    torch = pytest.importorskip("torch")
+    import socket
+    mp = torch.multiprocessing.get_context("spawn")
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    q = mp.Queue()
+    procs = [mp.Process(target=_shard_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    # both ranks see the slowest rank's 3 s; the whole job did 6e9 units in it
+    assert [r[1] for r in res] == [3.0, 3.0]
+    assert all(abs(r[2] - 2.0) < 1e-12 for r in res)
