@@ -632,17 +632,20 @@ def batch_arm(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    all_cs = inp.batch_cases(seed=0, ncases=args.batch_cases)
+    dof_all = [4 * c.n * c.n * (c.p + 1) ** 2 for c in all_cs]
+    parts = shard_cases(dof_all, world)
+    # the partition is the same on every rank: all ranks refuse together, before any
+    # process group exists, rather than leaving the others waiting in a collective
+    if any(not part for part in parts):
+        raise SystemExit(f"{len(all_cs)} cases cannot give each of {world} ranks one; use fewer ranks")
+    mine = parts[rank]
     torch.cuda.set_device(local)
     dev = f"cuda:{local}"
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    all_cs = inp.batch_cases(seed=0, ncases=args.batch_cases)
-    dof_all = [4 * c.n * c.n * (c.p + 1) ** 2 for c in all_cs]
-    mine = shard_cases(dof_all, world)[rank]
-    if not mine:
-        raise SystemExit(f"rank {rank}: no case of {len(all_cs)} left for it; use fewer ranks")
     cs = [all_cs[k] for k in mine]
     cases = [fr.Case(c.p, c.n, c.n, c.mach, c.re, c.kappa) for c in cs]
     cfg = fr.Config(prec=args.prec, restart=args.restart, maxit_lin=args.maxit_lin,

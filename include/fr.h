@@ -310,8 +310,12 @@ const char* fr_profile_name(int kind);
  * current): make that first call before any stream capture.  Every call writes each
  * scratch entry it later reads, so nothing needs clearing, but all calls share the one
  * array: calls that overlap on the GPU (other streams, other threads) race and must be
- * serialised by the caller.  Asynchronous on `stream`; returns FR_OK, FR_ERR_ARG or
- * FR_ERR_CUDA (no error text: there is no context). */
+ * serialised by the caller.  The looked-up address is kept for the life of the process:
+ * after cudaDeviceReset on a device the library must be reloaded (a new process) before
+ * this entry point is used on that device again.  Asynchronous on `stream`; returns
+ * FR_OK, FR_ERR_ARG or FR_ERR_CUDA (no error text: there is no context); a CUDA error
+ * already pending when the call starts returns FR_ERR_CUDA before any launch and is left
+ * pending for its owner. */
 int fr_residual_noalloc(const fr_config* cfg, int nx, int ny, const double* corners_d,
                         const double* corner_vel_d, const double* qp_d, double* R_d,
                         void* stream);

@@ -20,7 +20,8 @@ residual  FR/CPR residual R(q^p), Eqs. cpr_ns / unsteady_pre_mov_cdomain_GCL (Se
           far-field and adiabatic no-slip wall faces (Sec. 3.3), wall force (Sec. 4)
 solver    JVP, element block Jacobian, restarted GMRES, BDF2 dual-time Newton and
           steady PTC with SER (Sec. 3.2); L2 and entropy errors (Sec. 4)
-scale     per-equation residual magnitudes that parity tolerances are stated in
+scale     per-equation residual magnitudes that parity tolerances are stated in (the
+          summed-terms scale sigma and the flux-divergence scale)
 adjoint   discrete adjoint of the BDF2 march for d(mean C_t)/d(plunge amplitude, Mach)
           of a plunging airfoil (Secs. 3.2, 4, 4.4; dense, small meshes)
 

@@ -13,13 +13,19 @@ unit round-off times the magnitude of those terms, not of R_k itself.  The scale
 collects the two largest kinds of terms (the computational fluxes of Eq.
 computational_flux differentiated along lines, and the preconditioned dissipation
 of Eq. Rosanov acting on face states).  Tolerances are stated as multiples of it.
+
+``divergence_scale`` is the smaller, flux-divergence scale
+max(||R_k||_inf, max_points max(|d F_k/d xi|, |d G_k/d eta|) / |J|): the size of the
+differentiated fluxes themselves rather than of the terms summed into them (a
+uniform pressure contributes nothing to it on a static mesh).  Errors are reported in
+both scales.
 """
 from __future__ import annotations
 
 import numpy as np
 
 from . import physics as ph
-from .residual import Mesh, residual, trace
+from .residual import Mesh, d_eta, d_xi, residual, trace
 from .basis import make_basis
 from .geometry import FACE_L, FACE_R, FACE_B, FACE_T, element_geometry
 
@@ -49,3 +55,21 @@ def residual_scale(q, mesh: Mesh, p: int, gas: ph.Gas) -> np.ndarray:
         mag = np.einsum("ij...,j...->i...", np.abs(G), np.abs(np.stack(qa)))
         s_diss = np.maximum(s_diss, np.max(Smag * lmax * mag, axis=(1, 2)) / jmin)
     return s_flux + s_diss
+
+
+def flux_derivative_scale(q, mesh: Mesh, p: int, gas: ph.Gas) -> np.ndarray:
+    """Per equation max over solution points of max(|d F_k/d xi|, |d G_k/d eta|) / |J|,
+    F and G the computational fluxes at the solution points differentiated along lines
+    (interpolant derivatives, element by element)."""
+    b = make_basis(p)
+    geo = element_geometry(mesh.corners, mesh.vel, b)
+    P = residual(q, mesh, p, gas, b, geo, parts=True)
+    dF = np.abs(d_xi(b, P.F)) / geo.sol.J
+    dG = np.abs(d_eta(b, P.G)) / geo.sol.J
+    return np.maximum(dF.max(axis=(1, 2, 3)), dG.max(axis=(1, 2, 3)))
+
+
+def divergence_scale(q, mesh: Mesh, p: int, gas: ph.Gas) -> np.ndarray:
+    """Per equation max(||R_k||_inf, flux_derivative_scale_k)."""
+    R = residual(q, mesh, p, gas)
+    return np.maximum(np.abs(R).max(axis=(1, 2, 3)), flux_derivative_scale(q, mesh, p, gas))

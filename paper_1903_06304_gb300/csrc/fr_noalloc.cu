@@ -44,6 +44,9 @@ int run(const fr_config* cfg, int nx, int ny, const double* corners, const doubl
   using namespace fr;
   constexpr int NP = N * N, EPB = Tile<N>::EPB, TH = Tile<N>::THREADS;
   const size_t ne = (size_t)nx * ny;
+  // every element needs well over 64 bytes of scratch: refusing larger meshes first keeps
+  // the byte counts below from wrapping around for absurd nx, ny
+  if (ne > kScratchBytes / 64) return FR_ERR_ARG;
   // scratch layout: geometry at solution and flux points, traces, local gradients,
   // common fluxes and common solutions of the owned faces
   const size_t b_gs = round256(sizeof(double) * GS_COUNT * ne * NP);
@@ -56,6 +59,9 @@ int run(const fr_config* cfg, int nx, int ny, const double* corners, const doubl
   const size_t b_cp = round256(sizeof(CaseParams));
   const size_t need = b_gs + b_gf + b_tq + b_tg + b_gl + 2 * b_fn + b_nb + b_cp;
   if (need > kScratchBytes) return FR_ERR_ARG;
+  // an error left pending by an earlier, unrelated call is reported as such (and left in
+  // place) rather than taken for a failure of this call's launches
+  if (cudaPeekAtLastError() != cudaSuccess) return FR_ERR_CUDA;
   void* base = nullptr;
   int rc = scratch_address(&base);
   if (rc != FR_OK) return rc;

@@ -108,3 +108,19 @@ def test_sharded_throughput_two_gloo_ranks():
     # both ranks see the slowest rank's 3 s; the whole job did 6e9 units in it
     assert [r[1] for r in res] == [3.0, 3.0]
     assert all(abs(r[2] - 2.0) < 1e-12 for r in res)
+
+
+def test_batch_arm_refuses_on_every_rank_before_any_collective(monkeypatch):
+    """Fewer cases than ranks: each rank reaches the same decision from the deterministic
+    partition and exits before a process group exists, so no rank is left waiting in a
+    barrier or all-reduce of the others."""
+    import argparse
+    import bench
+    import torch.distributed as dist
+    for rank in (0, 1):
+        monkeypatch.setenv("WORLD_SIZE", "2")
+        monkeypatch.setenv("RANK", str(rank))
+        monkeypatch.setenv("LOCAL_RANK", str(rank))
+        with pytest.raises(SystemExit):
+            bench.batch_arm(argparse.Namespace(batch_cases=1))
+        assert not dist.is_initialized()
