@@ -275,10 +275,14 @@ class StepStats:
 
 def newton_solve(prob: Problem, q, rhs, a0_dt: float, dtau0: float, restart: int,
                  tol_res: float, maxit_lin: int, tol_pseudo: float, maxit_newton: int,
-                 lag: int, ser=None, side: str = "left", line_search: int = 0):
+                 lag: int, ser=None, side: str = "left", line_search: int = 0,
+                 precond: str = "block"):
     """Pseudo-time Newton loop shared by BDF2 and PTC; ``ser`` = (dtau_min, dtau_max, r).
     line_search = k > 0: backtracking on the full residual 2-norm, lambda = 1, 1/2, ...,
-    2^-k (the paper takes plain Newton updates, k = 0)."""
+    2^-k (the paper takes plain Newton updates, k = 0).  precond: "block" (element
+    block Jacobi) or "twolevel" (``oracle.twolevel``: the blocks as smoother plus the
+    P1 coarse correction), either rebuilt every ``lag`` iterations."""
+    from . import twolevel as tl
     q = q.copy()
     r = rhs(q)
     res = [float(np.linalg.norm(r[0]))]
@@ -293,10 +297,17 @@ def newton_solve(prob: Problem, q, rhs, a0_dt: float, dtau0: float, restart: int
             break
         inv_dtau = 1.0 / dtau
         if m % lag == 0 or Binv is None or ser is not None:
-            Binv = np.linalg.inv(block_jacobian(prob, q, inv_dtau, a0_dt))
+            if precond == "twolevel":
+                Binv = tl.build(prob, q, inv_dtau, a0_dt)
+            else:
+                Binv = np.linalg.inv(block_jacobian(prob, q, inv_dtau, a0_dt))
         qm = q
-        out = gmres(lambda v: apply_A(prob, qm, v, inv_dtau, a0_dt), r,
-                    lambda v: block_apply(Binv, v), restart, tol_res, maxit_lin, side)
+        Aop = lambda v: apply_A(prob, qm, v, inv_dtau, a0_dt)
+        if precond == "twolevel":
+            Minv = lambda v, pc=Binv: pc.apply(v, Aop)
+        else:
+            Minv = lambda v, B=Binv: block_apply(B, v)
+        out = gmres(Aop, r, Minv, restart, tol_res, maxit_lin, side)
         its.append(out.iterations)
         prev_all = np.linalg.norm(r)
         lam = 1.0
@@ -321,14 +332,15 @@ def newton_solve(prob: Problem, q, rhs, a0_dt: float, dtau0: float, restart: int
 def bdf2_step(prob: Problem, q, qc_n, qc_nm1, dt: float, coeffs=BDF2, dtau: float = 1e20,
               restart: int = 30, tol_res: float = 1e-6, maxit_lin: int = 100,
               tol_pseudo: float = 1e-8, maxit_newton: int = 20, lag: int = 2,
-              side: str = "left", ser=None, line_search: int = 0):
+              side: str = "left", ser=None, line_search: int = 0, precond: str = "block"):
     """One physical BDF2 step (Eq. unsteady_pre_discretized_3) from q^n = q (initial guess).
     ser = (dtau_min, dtau_max, r_ser): adapt the pseudo step from dtau by the SER law
     (pseudo-transient continuation, the steady strategy of Sec. 3.2) instead of the fixed
     dtau of the paper's unsteady runs."""
     rhs = lambda s: time_rhs(prob, s, qc_n, qc_nm1, dt, coeffs)
     return newton_solve(prob, q, rhs, coeffs[0] / dt, dtau, restart, tol_res, maxit_lin,
-                        tol_pseudo, maxit_newton, lag, ser=ser, side=side, line_search=line_search)
+                        tol_pseudo, maxit_newton, lag, ser=ser, side=side, line_search=line_search,
+                        precond=precond)
 
 
 def ptc_solve(prob: Problem, q, dtau0: float = 0.01, dtau_min: float = 0.01,
