@@ -100,7 +100,23 @@ typedef struct fr_ctx fr_ctx;
  * relative), not bit for bit; a timed choice can therefore differ between runs;
  * graphs: if nonzero (default) and restart <= 128, GMRES iterations are issued in chunks of
  * up to 10 whose kernel launches are captured once into a CUDA graph and replayed (same
- * results; fewer launch overheads); ignored while fr_profile timing is on. */
+ * results; fewer launch overheads); ignored while fr_profile timing is on;
+ * precond: FR_PRECOND_BLOCK (default) element block Jacobi; FR_PRECOND_TWO_LEVEL adds a
+ * coarse correction before the block-Jacobi step (not in the paper, whose per-process
+ * ILU(0) of Sec. 4 this replaces: element blocks alone stall once the preconditioned
+ * dissipation's pressure coupling, growing as p^2/h, dominates the BDF2 term
+ * gamma M^2 a0/dt).  With r the vector to precondition and A the Newton operator GMRES
+ * applies, M^-1 r = z0 + B^-1 (r - A z0), z0 = P V(P^T r): P maps per element and
+ * variable the three coefficients of c0 + c1 xi + c2 eta (reference coordinates) to the
+ * solution points, and V is one multigrid V-cycle on the Galerkin operator P^T A P,
+ * agglomerating 2 x 2 cells per level within each case down to at most 4 cells, which are
+ * solved exactly; on each other level mg_sweeps damped block-Jacobi sweeps (12 x 12
+ * blocks, damping mg_omega) before and after the correction (defaults 2 and 0.7).  The
+ * coarse operators are rebuilt with the blocks (every `lag` Newton iterations) by
+ * coloured products of A with the P1 functions of the elements.  FP64 throughout the
+ * coarse levels; B^-1 in the configured block precision.  On a periodic mesh with a very
+ * large dtau and no time term (a0_dt = 0) the constant states make the coarsest operator
+ * singular: use it for BDF2 steps (a0_dt > 0) or on bounded meshes. */
 #define FR_MAX_RESTART 256
 #define FR_JVP_DUAL 0
 #define FR_JVP_LINEARIZED 1
@@ -116,6 +132,8 @@ typedef struct fr_ctx fr_ctx;
 #define FR_KRYLOV_DF64 1
 #define FR_BC_WALL 1
 #define FR_BC_FARFIELD 2
+#define FR_PRECOND_BLOCK 0
+#define FR_PRECOND_TWO_LEVEL 1
 typedef struct fr_config {
   int p;
   double gamma, prandtl, mach, re, kappa, eps_floor;
@@ -134,6 +152,9 @@ typedef struct fr_config {
   int block_mode;
   int orthog;
   int krylov_arith;
+  int precond;
+  int mg_sweeps;
+  double mg_omega;
 } fr_config;
 
 /* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).
@@ -286,7 +307,7 @@ int fr_residual_norms(fr_ctx* ctx, const double* r_d, double* res_mass, double* 
  * launches issued since the last reset (both counted whether or not timing is on);
  * reset != 0 clears the timing and the algorithmic totals.  Any output pointer may be
  * NULL.  fr_profile_name(k) names class k. */
-#define FR_PROF_KINDS 16
+#define FR_PROF_KINDS 17
 int fr_profile(fr_ctx* ctx, int enable);
 int fr_profile_read(fr_ctx* ctx, double* ms, long long* counts, long long* launches, double* flops,
                     double* bytes, int reset);

@@ -164,7 +164,7 @@ class Hierarchy:
 
 
 def build_hierarchy(A1: sp.csr_matrix, nx: int, ny: int, omega: float = 0.7,
-                    nu: int = 2, coarsest: int = 16) -> Hierarchy:
+                    nu: int = 2, coarsest: int = 4) -> Hierarchy:
     A, Q, Dinv = [A1.tocsr()], [], []
     while nx * ny > coarsest:
         Dinv.append(np.linalg.inv(block_diagonal(A[-1], 12)))
@@ -212,7 +212,7 @@ class TwoLevel:
 
 
 def build(prob: sv.Problem, q, inv_dtau: float, a0_dt: float, omega: float = 0.7, nu: int = 2,
-          coarsest: int = 16) -> TwoLevel:
+          coarsest: int = 4) -> TwoLevel:
     mesh = prob.mesh
     Binv = np.linalg.inv(sv.block_jacobian(prob, q, inv_dtau, a0_dt))
     P = p1_prolongation(mesh.ne, prob.p, prob.basis.xs)

@@ -205,6 +205,7 @@ void free_mesh(fr_ctx* c) {
   }
   c->bounded = c->bc_below = c->bc_above = 0;
   frk::batch_free(c);
+  frk::mg_free(c);
   graphs_free(c);
 }
 
@@ -312,7 +313,7 @@ int gmres_solve(fr_ctx* c, const double* q, const double* b, double inv_dtau, do
     *iters = its[0];
     return FR_OK;
   }
-  if (left) FR_TRY(frk::block_apply(c, b, r, s));
+  if (left) FR_TRY(frk::precond_apply(c, q, b, r, inv_dtau, a0_dt, s));
   else FR_CUDA_CHECK(c, cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   double bm, bnorm;
   FR_TRY(norms_host(c, r, &bm, &bnorm, s));
@@ -334,9 +335,9 @@ int gmres_solve(fr_ctx* c, const double* q, const double* b, double inv_dtau, do
       double* w = c->V + (size_t)(j + 1) * N;
       if (left) {
         FR_TRY(op_apply(c, q, Vj, inv_dtau, a0_dt, c->w_z, s));
-        FR_TRY(frk::block_apply(c, c->w_z, w, s));
+        FR_TRY(frk::precond_apply(c, q, c->w_z, w, inv_dtau, a0_dt, s));
       } else {
-        FR_TRY(frk::block_apply(c, Vj, c->w_z, s));
+        FR_TRY(frk::precond_apply(c, q, Vj, c->w_z, inv_dtau, a0_dt, s));
         FR_TRY(op_apply(c, q, c->w_z, inv_dtau, a0_dt, w, s));
       }
       FR_TRY(cgs2(c, j + 1, w, s));
@@ -376,13 +377,13 @@ int gmres_solve(fr_ctx* c, const double* q, const double* b, double inv_dtau, do
     if (left) {
       FR_TRY(frk::axpby(c, 1.0, c->w_u, 1.0, x, s));
     } else {
-      FR_TRY(frk::block_apply(c, c->w_u, c->w_z, s));
+      FR_TRY(frk::precond_apply(c, q, c->w_u, c->w_z, inv_dtau, a0_dt, s));
       FR_TRY(frk::axpby(c, 1.0, c->w_z, 1.0, x, s));
     }
     // residual of the restart: b - A x (left: preconditioned)
     FR_TRY(op_apply(c, q, x, inv_dtau, a0_dt, c->w_t, s));
     FR_TRY(frk::axpby(c, 1.0, b, -1.0, c->w_t, s));
-    if (left) FR_TRY(frk::block_apply(c, c->w_t, r, s));
+    if (left) FR_TRY(frk::precond_apply(c, q, c->w_t, r, inv_dtau, a0_dt, s));
     else FR_CUDA_CHECK(c, cudaMemcpyAsync(r, c->w_t, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     double rm;
     FR_TRY(norms_host(c, r, &rm, &beta, s));
@@ -419,14 +420,18 @@ int newton_loop(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, do
     if (rm <= c->cfg.tol_pseudo * res0) { conv = true; break; }
     const double inv_dtau = 1.0 / dtau;
     bool lin_done = false;   // a build from the local Jacobians leaves them stored at q
+    bool build = false;
     if (ser || m % std::max(1, c->cfg.lag) == 0) {
       FR_TRY(frk::block_build(c, q, inv_dtau, a0dt, s));
       c->blocks_ready = 1;
       st->block_builds++;
       lin_done = c->cfg.block_mode == FR_BLOCK_LINEARIZED;
+      build = true;
     }
     int its = 0;
     if (c->cfg.jvp_mode == FR_JVP_LINEARIZED && !lin_done) FR_TRY(frk::linearize(c, q, inv_dtau, a0dt, s));
+    // the coarse operators are products of the operator GMRES applies at this q
+    if (build) FR_TRY(frk::mg_build(c, q, inv_dtau, a0dt, s));
     FR_TRY(gmres_solve(c, q, r, inv_dtau, a0dt, c->w_x, &its, s));
     st->gmres_iterations[m] = its;
     const double prev = rm, prev_all = ra;
@@ -457,7 +462,7 @@ int newton_loop(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, do
 const char* kKernelNames[KK_COUNT] = {
     "geometry", "trace", "face", "elem", "trace_jvp", "face_jvp", "elem_jvp", "block_jacobian",
     "block_factor", "block_apply", "krylov_reduce", "vector", "conservative", "linearize",
-    "linear_apply", "linear_adjoint"};
+    "linear_apply", "linear_adjoint", "coarse"};
 
 // Fold the recorded event pairs into the per-kind totals (synchronises on the events).
 int prof_collect(fr_ctx* c) {
@@ -562,6 +567,9 @@ void fr_default_config(fr_config* c) {
   c->block_mode = FR_BLOCK_LINEARIZED;
   c->orthog = FR_ORTHO_CGS2;
   c->krylov_arith = FR_KRYLOV_FP64;
+  c->precond = FR_PRECOND_BLOCK;
+  c->mg_sweeps = 2;
+  c->mg_omega = 0.7;
 }
 
 int fr_create(const fr_config* cfg, fr_ctx** out) {
@@ -575,7 +583,9 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
       cfg->tiles < 0 || cfg->tiles > 2 ||
       (cfg->block_mode != FR_BLOCK_LINEARIZED && cfg->block_mode != FR_BLOCK_DUAL) ||
       (cfg->orthog != FR_ORTHO_CGS2 && cfg->orthog != FR_ORTHO_CGS) ||
-      (cfg->krylov_arith != FR_KRYLOV_FP64 && cfg->krylov_arith != FR_KRYLOV_DF64))
+      (cfg->krylov_arith != FR_KRYLOV_FP64 && cfg->krylov_arith != FR_KRYLOV_DF64) ||
+      (cfg->precond != FR_PRECOND_BLOCK && cfg->precond != FR_PRECOND_TWO_LEVEL) ||
+      cfg->mg_sweeps < 1 || cfg->mg_sweeps > 8 || !(cfg->mg_omega > 0.0 && cfg->mg_omega <= 1.5))
     return FR_ERR_ARG;
   fr_ctx* c = new fr_ctx();
   c->cfg = *cfg;
@@ -667,7 +677,8 @@ int fr_set_mesh_bounded(fr_ctx* c, int nx, int ny, int bc_below, int bc_above, c
   FR_TRY(dev_alloc(c, &c->qcb_d, nb));
   FR_TRY(frk::mark_bounds(c, nx, ny, bc_below, bc_above, 0));
   FR_CUDA_CHECK(c, cudaStreamSynchronize(0));
-  return FR_OK;
+  // the coarse hierarchy again, now without the wrap in eta
+  return frk::mg_setup(c);
 }
 
 }  // extern "C"
@@ -752,6 +763,8 @@ int fr_setup_cases(fr_ctx* c, int ncases, const int* nxs, const int* nys,
   FR_CUDA_CHECK(c, cudaMemset(c->ticket, 0, sizeof(unsigned int)));
   // per-case vector partition, GMRES states and staging (used by every context)
   FR_TRY(frk::batch_setup(c));
+  // coarse hierarchy of the two-level preconditioner (nothing unless configured)
+  FR_TRY(frk::mg_setup(c));
   // tile shapes of the point-parallel kernels (timed on these buffers unless forced)
   return frk::autotune_tiles(c);
 }
@@ -814,6 +827,11 @@ int fr_precond_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, 
   FR_TRY(check_ready(c));
   FR_TRY(frk::block_build(c, q, inv_dtau, a0_dt, S(s)));
   c->blocks_ready = 1;
+  if (c->cfg.precond == FR_PRECOND_TWO_LEVEL) {
+    if (c->cfg.jvp_mode == FR_JVP_LINEARIZED && c->cfg.block_mode != FR_BLOCK_LINEARIZED)
+      FR_TRY(frk::linearize(c, q, inv_dtau, a0_dt, S(s)));
+    FR_TRY(frk::mg_build(c, q, inv_dtau, a0_dt, S(s)));
+  }
   return FR_OK;
 }
 
@@ -828,7 +846,7 @@ int fr_precond_blocks(fr_ctx* c, double* B, void* s) {
 int fr_precond_apply(fr_ctx* c, const double* r, double* z, void* s) {
   FR_TRY(check_ready(c));
   if (!c->blocks_ready) { snprintf(c->err, sizeof(c->err), "no preconditioner built"); return FR_ERR_ARG; }
-  return frk::block_apply(c, r, z, S(s));
+  return frk::precond_apply(c, c->mg_q, r, z, c->mg_inv_dtau, c->mg_a0_dt, S(s));
 }
 
 int fr_gmres(fr_ctx* c, const double* q, const double* b, double inv_dtau, double a0_dt, double* x,

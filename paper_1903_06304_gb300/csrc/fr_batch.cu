@@ -109,7 +109,7 @@ int gmres_cases(fr_ctx* c, const double* q, const double* b, double* x, double i
   double* r = c->w_r;
   double* tmp = c->w_u;
   double* w = c->w_t;
-  if (left) FR_TRY(frk::block_apply(c, b, r, s));
+  if (left) FR_TRY(frk::precond_apply(c, q, b, r, inv_dtau, a0_dt, s));
   else FR_CUDA_CHECK(c, cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   std::vector<double> rm, bnorm, beta;
   std::vector<char> bad;
@@ -151,9 +151,9 @@ int gmres_cases(fr_ctx* c, const double* q, const double* b, double* x, double i
         for (int it = 0; it < nchunk; ++it) {
           if (left) {
             FR_TRY(op_apply(c, q, tmp, inv_dtau, a0_dt, c->w_z, cs));
-            FR_TRY(frk::block_apply(c, c->w_z, w, cs));
+            FR_TRY(frk::precond_apply(c, q, c->w_z, w, inv_dtau, a0_dt, cs));
           } else {
-            FR_TRY(frk::block_apply(c, tmp, c->w_z, cs));
+            FR_TRY(frk::precond_apply(c, q, tmp, c->w_z, inv_dtau, a0_dt, cs));
             FR_TRY(op_apply(c, q, c->w_z, inv_dtau, a0_dt, w, cs));
           }
           FR_TRY(frk::bk_orthogonalize(c, w, tmp, j0 + it + 1, cs));
@@ -182,7 +182,7 @@ int gmres_cases(fr_ctx* c, const double* q, const double* b, double* x, double i
     } else {
       // B^-1 u, added only for the cases that iterated (the block apply skips the elements
       // of stopped cases, whose entries of w_z are stale)
-      FR_TRY(frk::block_apply(c, c->w_u, c->w_z, s));
+      FR_TRY(frk::precond_apply(c, q, c->w_u, c->w_z, inv_dtau, a0_dt, s));
       std::vector<double> one(nc);
       for (int k = 0; k < nc; ++k) one[k] = cyc[k] ? 1.0 : 0.0;
       FR_TRY(upload_coef(c, one, s));
@@ -190,7 +190,7 @@ int gmres_cases(fr_ctx* c, const double* q, const double* b, double* x, double i
     }
     FR_TRY(op_apply(c, q, x, inv_dtau, a0_dt, c->w_t, s));
     FR_TRY(frk::axpby(c, 1.0, b, -1.0, c->w_t, s));
-    if (left) FR_TRY(frk::block_apply(c, c->w_t, r, s));
+    if (left) FR_TRY(frk::precond_apply(c, q, c->w_t, r, inv_dtau, a0_dt, s));
     else FR_CUDA_CHECK(c, cudaMemcpyAsync(r, c->w_t, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     FR_TRY(case_norms(c, r, rm, beta, bad, s));
     for (int k = 0; k < nc; ++k)
@@ -284,13 +284,16 @@ int batch_newton(fr_ctx* c, double* q, const double* qcn, const double* qcnm1,
     }
     FR_TRY(frk::upload_cases(c, s));
     bool lin_done = false;   // a build from the local Jacobians leaves them stored at q
+    bool build = false;
     if (ser || m % std::max(1, cfg.lag) == 0) {
       FR_TRY(frk::block_build(c, q, 0.0, 0.0, s));
       c->blocks_ready = 1;
       for (int k = 0; k < nc; ++k) S[k]->block_builds += active[k];
       lin_done = cfg.block_mode == FR_BLOCK_LINEARIZED;
+      build = true;
     }
     if (cfg.jvp_mode == FR_JVP_LINEARIZED && !lin_done) FR_TRY(frk::linearize(c, q, 0.0, 0.0, s));
+    if (build) FR_TRY(frk::mg_build(c, q, 0.0, 0.0, s));
     FR_TRY(frk::gmres_cases(c, q, r, c->w_x, 0.0, 0.0, active, its, failed, s));
     for (int k = 0; k < nc; ++k) {
       if (active[k]) S[k]->gmres_iterations[mk[k]] = its[k];

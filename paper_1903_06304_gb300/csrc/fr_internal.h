@@ -54,11 +54,32 @@ struct BatchWork {
   cudaEvent_t staged = nullptr;    // the last upload from pinned staging has completed
 };
 
+// One level of the two-level preconditioner's coarse hierarchy (fr_mg.cu): cells carry
+// 12 P1 coefficients (4 variables x mean, xi slope, eta slope).  Level 0 has one cell per
+// element; level l+1 agglomerates 2 x 2 cells of level l within each case.  A case whose
+// level has at most 4 cells is solved there exactly (dense inverse); its cells have
+// parent -1 and take no part in smoothing or transfers.
+struct MgLevel {
+  int nc = 0;                 // cells (all cases)
+  int *nb = nullptr;          // [nc][5] distinct stencil members, slot 0 = self, -1 unused
+  int *cell_case = nullptr;   // [nc]
+  double *A = nullptr;        // [nc][5][12][12] operator blocks by stencil slot
+  double *Dinv = nullptr;     // [nc][12][12] inverse diagonal blocks (continuing cells)
+  double *x = nullptr, *y = nullptr, *b = nullptr;   // [nc][12] cycle vectors
+  int *parent = nullptr;      // [nc] cell of level l+1, -1 for a case finishing here
+  double *qo = nullptr;       // [nc][4]: s_a f_x, s_b f_y, f_x, f_y of the cell in its parent
+  int *children = nullptr;    // [nc of level l+1][4], -1 unused
+  int *gslot = nullptr;       // [nc][5]: slot of parent(nb[c][s]) in parent(c)'s stencil
+  int nfin = 0;               // cases finishing at this level
+  int *fin = nullptr;         // [nfin][2]: first cell, cell count
+  double *Ainv = nullptr;     // [nfin][48][48] dense inverses (row-major, count*12 used)
+};
+
 // Kernel classes for the optional per-kernel timing (fr_profile) and launch counts.
 enum FrKernel {
   KK_GEOM, KK_TRACE, KK_FACE, KK_ELEM, KK_TRACE_JVP, KK_FACE_JVP, KK_ELEM_JVP, KK_BLOCK,
   KK_FACTOR, KK_APPLY, KK_KRYLOV, KK_VECTOR, KK_CONS, KK_LINEARIZE, KK_LIN_APPLY,
-  KK_LIN_ADJOINT, KK_COUNT
+  KK_LIN_ADJOINT, KK_COARSE, KK_COUNT
 };
 
 struct FrProfPair {
@@ -137,6 +158,15 @@ struct fr_ctx {
   double *JP = nullptr, *JG = nullptr, *PP = nullptr;  // point map: [32|64|16][Ne*n^2]
   double *adj_q = nullptr, *adj_fn = nullptr, *adj_qc = nullptr;  // transpose work
   int lin_ready = 0;
+  // two-level preconditioner (cfg.precond == FR_PRECOND_TWO_LEVEL, fr_mg.cu)
+  std::vector<MgLevel> mg;
+  int mg_ncol = 0;                 // colours of the level-0 Galerkin products
+  int *mg_colslot = nullptr;       // [Ne][ncol]: stencil slot of colour k's member, -1
+  double *mg_x = nullptr, *mg_y = nullptr;   // fine seeds and products of the build
+  double *mg_z0 = nullptr, *mg_t = nullptr;  // fine coarse correction and residual
+  int *mg_bad = nullptr;           // singular coarse blocks met by the builds (device)
+  const double* mg_q = nullptr;    // state of the last build (dual-number operator)
+  double mg_inv_dtau = 0.0, mg_a0_dt = 0.0;
   // Krylov workspace
   double* V = nullptr;       // [(m+1)][ndof]
   double *w_r = nullptr, *w_z = nullptr, *w_x = nullptr, *w_t = nullptr, *w_u = nullptr;
@@ -213,6 +243,15 @@ int jvp(fr_ctx* c, const double* q, const double* v, double inv_dtau, double a0_
 int conservative(fr_ctx* c, const double* q, double* qc, cudaStream_t s);
 int block_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s);
 int block_apply(fr_ctx* c, const double* r, double* z, cudaStream_t s);
+// Two-level preconditioner (fr_mg.cu): topology and workspace of the coarse hierarchy
+// (host-built, synchronous; nothing unless cfg.precond asks for it), its build at q after
+// the element blocks, and the configured preconditioner z = M^-1 r (block Jacobi, or the
+// coarse correction followed by block-Jacobi smoothing with the current operator at q).
+int mg_setup(fr_ctx* c);
+void mg_free(fr_ctx* c);
+int mg_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s);
+int precond_apply(fr_ctx* c, const double* q, const double* r, double* z, double inv_dtau,
+                  double a0_dt, cudaStream_t s);
 int linearize(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s);
 int apply_linear(fr_ctx* c, const double* v, double* out, bool transpose, cudaStream_t s);
 // Krylov primitives (deterministic reductions over a fixed grid)

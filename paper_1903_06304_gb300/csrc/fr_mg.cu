@@ -1,0 +1,742 @@
+// fr_mg.cu -- two-level preconditioner for the Newton operator of Sec. 3.2: a coarse
+// correction on the discontinuous linear (P1) space, solved by an agglomeration multigrid
+// V-cycle, followed by the element block-Jacobi step.
+//
+// The paper preconditions restarted GMRES with per-process ILU(0) (Sec. 4, parallel
+// setting); element blocks alone stall on low-Mach BDF2 steps once the preconditioned
+// dissipation's pressure coupling (growing as p^2/h) dominates the time term
+// gamma M^2 a0/dt, because element-local solves do not reach the smooth, domain-wide
+// pressure modes.  This adds them back:
+//
+//   M^-1 r = z0 + B^-1 (r - A z0),   z0 = P V(P^T r)
+//
+// P maps per element and variable the coefficients (c0, c1, c2) of c0 + c1 xi + c2 eta to
+// the solution points; V is one V-cycle on the Galerkin operators: A_0 = P^T A P from
+// coloured products of A with the P1 functions of the elements, A_{l+1} = Q^T A_l Q with
+// Q the exact map of a 2 x 2 agglomerate's P1 function to its children; damped 12 x 12
+// block-Jacobi sweeps on every level but the last, where each case (<= 4 cells) is solved
+// by its dense inverse.  Everything on the coarse levels is FP64 with fixed summation
+// orders (no atomics), so the preconditioner is a fixed linear map during a GMRES solve.
+//
+// Work per application at N elements: the restriction and prolongation read and write one
+// fine vector each; one extra operator product and block apply on the fine level; the
+// coarse levels do (4 nu + 1) passes over 5 x 144 coefficients per cell on level 0 and a
+// quarter of that per further level.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+#include "fr_internal.h"
+
+namespace {
+
+constexpr int NB = 12;          // P1 coefficients per cell (4 variables x 3)
+constexpr int SL = 5;           // stencil slots per cell (self + 4 neighbours)
+constexpr int BLK = NB * NB;    // entries of one 12 x 12 block
+constexpr int MAXFIN = 4;       // cells of a case solved exactly
+constexpr int DN = MAXFIN * NB; // leading dimension of the dense inverses
+constexpr int CPB = 16;         // cells per block of the row-parallel kernels
+
+// Reference-coordinate basis value of mode m (1, xi, eta) at point (i, j).
+__device__ __forceinline__ double phi(const fr::Basis& B, int m, int i, int j) {
+  return m == 0 ? 1.0 : (m == 1 ? B.xs[i] : B.xs[j]);
+}
+
+// ---------------------------------------------------------------- fine <-> level 0
+// Seeds of the level-0 Galerkin products: P1 function k of every element of colour col.
+template <int N>
+__global__ void k_p1_seed(fr::Mesh mesh, fr::Basis B, const int* __restrict__ colour, int col,
+                          int k, double* __restrict__ x) {
+  constexpr int NP = N * N;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)mesh.ne * NP) return;
+  const int e = (int)(t / NP), pt = (int)(t % NP);
+  const size_t base = mesh.qbase(e, NP), qs = mesh.qstride(e);
+  const double val = colour[e] == col ? phi(B, k % 3, pt % N, pt / N) : 0.0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) x[v * qs + base + pt] = v == k / 3 ? val : 0.0;
+}
+
+// Column k of the level-0 blocks: P^T y on every element whose stencil holds a member of
+// colour col (the seed's response on e comes from that member alone).
+template <int N>
+__global__ void k_p1_gather(fr::Mesh mesh, fr::Basis B, const int* __restrict__ colslot, int ncol,
+                            int col, int k, const double* __restrict__ y, double* __restrict__ A) {
+  constexpr int NP = N * N;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)mesh.ne * NB) return;
+  const int e = (int)(t / NB), r = (int)(t % NB);
+  const int s = colslot[(size_t)e * ncol + col];
+  if (s < 0) return;
+  const size_t base = mesh.qbase(e, NP), qs = mesh.qstride(e);
+  const int v = r / 3, m = r % 3;
+  double acc = 0.0;
+  for (int pt = 0; pt < NP; ++pt) acc = fma(phi(B, m, pt % N, pt / N), y[v * qs + base + pt], acc);
+  A[(((size_t)e * SL + s) * NB + r) * NB + k] = acc;
+}
+
+// b0 = P^T r (per element: 12 sums over its points)
+template <int N>
+__global__ void k_p1_restrict(fr::Mesh mesh, fr::Basis B, const double* __restrict__ r,
+                              double* __restrict__ b0) {
+  constexpr int NP = N * N;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)mesh.ne * NB) return;
+  const int e = (int)(t / NB), row = (int)(t % NB);
+  const size_t base = mesh.qbase(e, NP), qs = mesh.qstride(e);
+  const int v = row / 3, m = row % 3;
+  double acc = 0.0;
+  for (int pt = 0; pt < NP; ++pt) acc = fma(phi(B, m, pt % N, pt / N), r[v * qs + base + pt], acc);
+  b0[t] = acc;
+}
+
+// z = P x0
+template <int N>
+__global__ void k_p1_prolong(fr::Mesh mesh, fr::Basis B, const double* __restrict__ x0,
+                             double* __restrict__ z) {
+  constexpr int NP = N * N;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)mesh.ne * NP) return;
+  const int e = (int)(t / NP), pt = (int)(t % NP);
+  const size_t base = mesh.qbase(e, NP), qs = mesh.qstride(e);
+  const double xi = B.xs[pt % N], eta = B.xs[pt / N];
+  const double* c = x0 + (size_t)e * NB;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) z[v * qs + base + pt] = fma(c[3 * v + 2], eta, fma(c[3 * v + 1], xi, c[3 * v]));
+}
+
+// ---------------------------------------------------------------- V-cycle kernels
+struct LevelView {
+  int nc;
+  const int* nb;
+  const int* parent;
+  const double* A;
+  const double* Dinv;
+};
+
+// Row r of (A x)_c over the cell's stencil.
+__device__ __forceinline__ double row_product(const LevelView& L, int c, int r, const double* x) {
+  double acc = 0.0;
+  for (int s = 0; s < SL; ++s) {
+    const int f = L.nb[c * SL + s];
+    if (f < 0) continue;
+    const double* a = L.A + (((size_t)c * SL + s) * NB + r) * NB;
+    const double* xf = x + (size_t)f * NB;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc = fma(a[k], xf[k], acc);
+  }
+  return acc;
+}
+
+// One damped block-Jacobi sweep on the continuing cells: xo = xi + omega D^-1 (b - A xi)
+// (first sweep: xi = 0, so xo = omega D^-1 b).  Cells of cases solved on this level copy
+// their value through.  CPB cells of 12 rows per block.
+// (xi and xo may be the same buffer on the first sweep: each thread then reads and writes
+// only its own entry.)
+__global__ void __launch_bounds__(CPB * NB) k_mg_smooth(LevelView L, const double* __restrict__ b,
+                                                       const double* xi, double* xo, double omega,
+                                                       int first) {
+  __shared__ double res[CPB][NB];
+  const int lc = threadIdx.x / NB, r = threadIdx.x % NB;
+  const int c = blockIdx.x * CPB + lc;
+  const bool in = c < L.nc;
+  const bool cont = in && L.parent[c] >= 0;
+  if (cont) res[lc][r] = b[(size_t)c * NB + r] - (first ? 0.0 : row_product(L, c, r, xi));
+  __syncthreads();
+  if (!in) return;
+  if (!cont) {
+    xo[(size_t)c * NB + r] = xi[(size_t)c * NB + r];
+    return;
+  }
+  const double* d = L.Dinv + ((size_t)c * NB + r) * NB;
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) acc = fma(d[k], res[lc][k], acc);
+  xo[(size_t)c * NB + r] = (first ? 0.0 : xi[(size_t)c * NB + r]) + omega * acc;
+}
+
+// y = b - A x on the continuing cells
+__global__ void k_mg_residual(LevelView L, const double* __restrict__ b, const double* __restrict__ x,
+                              double* __restrict__ y) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)L.nc * NB) return;
+  const int c = (int)(t / NB), r = (int)(t % NB);
+  if (L.parent[c] < 0) return;
+  y[t] = b[t] - row_product(L, c, r, x);
+}
+
+// Q_m,a: coefficient of fine mode a in the child for coarse mode m (qo = s_a f_x, s_b f_y,
+// f_x, f_y): c0 + c1 X + c2 Y = (c0 + c1 s_a f_x + c2 s_b f_y) + c1 f_x xi + c2 f_y eta.
+__device__ __forceinline__ double qmap(const double* qo, int a, int m) {
+  if (a == 0) return m == 0 ? 1.0 : (m == 1 ? qo[0] : qo[1]);
+  if (a == 1) return m == 1 ? qo[2] : 0.0;
+  return m == 2 ? qo[3] : 0.0;
+}
+
+// b_next = Q^T y over each coarse cell's children (fixed child order)
+__global__ void k_mg_restrict(int nc_next, const int* __restrict__ children, const double* __restrict__ qo,
+                              const double* __restrict__ y, double* __restrict__ bn) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)nc_next * NB) return;
+  const int I = (int)(t / NB), r = (int)(t % NB);
+  const int v = r / 3, m = r % 3;
+  double acc = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    const int ch = children[I * 4 + q];
+    if (ch < 0) continue;
+    const double* o = qo + (size_t)ch * 4;
+    const double* yc = y + (size_t)ch * NB + 3 * v;
+    for (int a = 0; a < 3; ++a) acc = fma(qmap(o, a, m), yc[a], acc);
+  }
+  bn[t] = acc;
+}
+
+// x += Q x_next on the continuing cells
+__global__ void k_mg_prolong(LevelView L, const double* __restrict__ qo, const double* __restrict__ xn,
+                             double* __restrict__ x) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)L.nc * NB) return;
+  const int c = (int)(t / NB), r = (int)(t % NB);
+  const int P = L.parent[c];
+  if (P < 0) return;
+  const int v = r / 3, a = r % 3;
+  const double* o = qo + (size_t)c * 4;
+  const double* X = xn + (size_t)P * NB + 3 * v;
+  double acc = 0.0;
+  for (int m = 0; m < 3; ++m) acc = fma(qmap(o, a, m), X[m], acc);
+  x[t] += acc;
+}
+
+// Exact solve of the cases that finish on this level: x = Ainv b per case.
+__global__ void k_mg_dense(const int* __restrict__ fin, const double* __restrict__ Ainv,
+                           const double* __restrict__ b, double* __restrict__ x) {
+  const int f = blockIdx.x, c0 = fin[2 * f], m = fin[2 * f + 1] * NB;
+  const double* Ai = Ainv + (size_t)f * DN * DN;
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < m; ++k) acc = fma(Ai[r * DN + k], b[(size_t)c0 * NB + k], acc);
+    x[(size_t)c0 * NB + r] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- build kernels
+// Inverse of one 12 x 12 block by Gauss-Jordan with partial pivoting on [A | I] (one
+// thread); returns false on a zero pivot.
+__device__ bool gj_inverse12(double* a, double* inv) {
+  for (int i = 0; i < BLK; ++i) inv[i] = (i / NB == i % NB) ? 1.0 : 0.0;
+  for (int k = 0; k < NB; ++k) {
+    int p = k;
+    double best = fabs(a[k * NB + k]);
+    for (int i = k + 1; i < NB; ++i)
+      if (fabs(a[i * NB + k]) > best) { best = fabs(a[i * NB + k]); p = i; }
+    if (!(best > 0.0)) return false;
+    if (p != k) {
+      for (int j = 0; j < NB; ++j) {
+        double t = a[k * NB + j]; a[k * NB + j] = a[p * NB + j]; a[p * NB + j] = t;
+        t = inv[k * NB + j]; inv[k * NB + j] = inv[p * NB + j]; inv[p * NB + j] = t;
+      }
+    }
+    const double d = 1.0 / a[k * NB + k];
+    for (int j = 0; j < NB; ++j) { a[k * NB + j] *= d; inv[k * NB + j] *= d; }
+    for (int i = 0; i < NB; ++i) {
+      if (i == k) continue;
+      const double f = a[i * NB + k];
+      for (int j = 0; j < NB; ++j) {
+        a[i * NB + j] = fma(-f, a[k * NB + j], a[i * NB + j]);
+        inv[i * NB + j] = fma(-f, inv[k * NB + j], inv[i * NB + j]);
+      }
+    }
+  }
+  return true;
+}
+
+// Dinv = inverse of the diagonal (slot 0) block of every continuing cell; *bad counts
+// singular blocks.
+__global__ void k_mg_invert_diag(LevelView L, double* __restrict__ Dinv, int* __restrict__ bad) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.nc || L.parent[c] < 0) return;
+  double a[BLK], inv[BLK];
+  const double* src = L.A + (size_t)c * SL * BLK;
+  for (int i = 0; i < BLK; ++i) a[i] = src[i];
+  if (!gj_inverse12(a, inv)) atomicAdd(bad, 1);
+  double* dst = Dinv + (size_t)c * BLK;
+  for (int i = 0; i < BLK; ++i) dst[i] = inv[i];
+}
+
+// Dense inverse of each finishing case: its cells' blocks assembled into one (12 m)^2
+// matrix in shared memory (m <= 4) and inverted by Gauss-Jordan with partial pivoting,
+// the block's threads sharing each elimination step.
+__global__ void k_mg_coarsest(LevelView L, const int* __restrict__ fin, double* __restrict__ Ainv,
+                              int* __restrict__ bad) {
+  __shared__ double a[DN * DN];
+  __shared__ double inv[DN * DN];
+  __shared__ double col[DN];
+  __shared__ int piv;
+  const int f = blockIdx.x, c0 = fin[2 * f], cnt = fin[2 * f + 1], m = cnt * NB;
+  for (int t = threadIdx.x; t < DN * DN; t += blockDim.x) {
+    a[t] = 0.0;
+    inv[t] = (t / DN == t % DN) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // rows of cell c0 + i; one column block per distinct stencil member of the case
+  for (int t = threadIdx.x; t < cnt * SL * BLK; t += blockDim.x) {
+    const int i = t / (SL * BLK), s = (t / BLK) % SL, rk = t % BLK;
+    const int ci = c0 + i, fj = L.nb[ci * SL + s];
+    if (fj < 0) continue;
+    const int j = fj - c0, r = rk / NB, k = rk % NB;
+    a[(i * NB + r) * DN + j * NB + k] = L.A[((size_t)ci * SL + s) * BLK + rk];
+  }
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    if (threadIdx.x == 0) {
+      int p = k;
+      double best = fabs(a[k * DN + k]);
+      for (int i = k + 1; i < m; ++i)
+        if (fabs(a[i * DN + k]) > best) { best = fabs(a[i * DN + k]); p = i; }
+      if (!(best > 0.0)) { atomicAdd(bad, 1); p = -1; }
+      piv = p;
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p < 0) break;
+    if (p != k) {
+      for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double t = a[k * DN + j]; a[k * DN + j] = a[p * DN + j]; a[p * DN + j] = t;
+        t = inv[k * DN + j]; inv[k * DN + j] = inv[p * DN + j]; inv[p * DN + j] = t;
+      }
+    }
+    __syncthreads();
+    const double d = 1.0 / a[k * DN + k];
+    __syncthreads();   // every thread has read the pivot before row k is scaled
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      a[k * DN + j] *= d;
+      inv[k * DN + j] *= d;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) col[i] = a[i * DN + k];
+    __syncthreads();
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int i = t / m, j = t % m;
+      if (i == k) continue;
+      a[i * DN + j] = fma(-col[i], a[k * DN + j], a[i * DN + j]);
+      inv[i * DN + j] = fma(-col[i], inv[k * DN + j], inv[i * DN + j]);
+    }
+    __syncthreads();
+  }
+  double* dst = Ainv + (size_t)f * DN * DN;
+  for (int t = threadIdx.x; t < DN * DN; t += blockDim.x) dst[t] = inv[t];
+}
+
+// A_{l+1} = Q^T A_l Q: entry (r, k) of coarse block (I, S) sums, over the children c of I
+// and their slots s whose member's parent is slot S of I, Q_c^T A_l[c][s] Q_f.
+__global__ void k_mg_galerkin(LevelView L, const double* __restrict__ qo, const int* __restrict__ gslot,
+                              int nc_next, const int* __restrict__ nb_next,
+                              const int* __restrict__ children, double* __restrict__ An) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)nc_next * SL * BLK) return;
+  const int I = (int)(t / (SL * BLK)), S = (int)((t / BLK) % SL), rk = (int)(t % BLK);
+  if (nb_next[I * SL + S] < 0) { An[t] = 0.0; return; }
+  const int r = rk / NB, k = rk % NB;
+  const int v = r / 3, m = r % 3, w = k / 3, mk = k % 3;
+  double acc = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    const int c = children[I * 4 + q];
+    if (c < 0) continue;
+    const double* oc = qo + (size_t)c * 4;
+    for (int s = 0; s < SL; ++s) {
+      if (gslot[c * SL + s] != S) continue;
+      const int f = L.nb[c * SL + s];
+      const double* of = qo + (size_t)f * 4;
+      const double* a = L.A + ((size_t)c * SL + s) * BLK;
+      for (int ap = 0; ap < 3; ++ap) {
+        const double qa = qmap(oc, ap, m);
+        if (qa == 0.0) continue;
+        double inner = 0.0;
+        for (int bp = 0; bp < 3; ++bp) inner = fma(a[(3 * v + ap) * NB + 3 * w + bp], qmap(of, bp, mk), inner);
+        acc = fma(qa, inner, acc);
+      }
+    }
+  }
+  An[t] = acc;
+}
+
+unsigned blocks_for(long long n, int th) { return (unsigned)((n + th - 1) / th); }
+
+LevelView view(const MgLevel& l) { return LevelView{l.nc, l.nb, l.parent, l.A, l.Dinv}; }
+
+template <class T> int dalloc(fr_ctx* c, T** p, size_t count) {
+  if (*p) { cudaFree(*p); *p = nullptr; }
+  if (count == 0) return FR_OK;
+  FR_CUDA_CHECK(c, cudaMalloc((void**)p, count * sizeof(T)));
+  return FR_OK;
+}
+
+template <class T> int upload(fr_ctx* c, T** p, const std::vector<T>& h) {
+  FR_TRY(dalloc(c, p, h.size()));
+  if (!h.empty()) FR_CUDA_CHECK(c, cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return FR_OK;
+}
+
+int op_apply(fr_ctx* c, const double* q, const double* x, double inv_dtau, double a0_dt, double* out,
+             cudaStream_t s) {
+  if (c->cfg.jvp_mode == FR_JVP_LINEARIZED) return frk::apply_linear(c, x, out, false, s);
+  return frk::jvp(c, q, x, inv_dtau, a0_dt, out, s);
+}
+
+// Cells of one level of one case: an nx x ny grid (periodic in xi, in eta unless bounded).
+struct CaseGrid {
+  int nx, ny, off;
+};
+
+void stencil_of(const CaseGrid& g, bool bounded, int i, int j, int* out) {
+  int cand[5] = {g.off + j * g.nx + i, g.off + j * g.nx + (i + g.nx - 1) % g.nx,
+                 g.off + j * g.nx + (i + 1) % g.nx, -1, -1};
+  if (!bounded || j > 0) cand[3] = g.off + ((j + g.ny - 1) % g.ny) * g.nx + i;
+  if (!bounded || j < g.ny - 1) cand[4] = g.off + ((j + 1) % g.ny) * g.nx + i;
+  int n = 0;
+  for (int k = 0; k < 5; ++k) {
+    if (cand[k] < 0) continue;
+    bool dup = false;
+    for (int q = 0; q < n; ++q) dup = dup || out[q] == cand[k];
+    if (!dup) out[n++] = cand[k];
+  }
+  for (int k = n; k < SL; ++k) out[k] = -1;
+}
+
+template <int N>
+int build_level0(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s) {
+  constexpr int NP = N * N;
+  MgLevel& L0 = c->mg[0];
+  const long long npts = (long long)c->ne * NP;
+  // one operator product per colour and P1 function
+  for (int col = 0; col < c->mg_ncol; ++col) {
+    for (int k = 0; k < NB; ++k) {
+      {
+        FR_PROF_BEGIN(c, s);
+        k_p1_seed<N><<<blocks_for(npts, 256), 256, 0, s>>>(c->mesh, c->basis, c->mg_colslot, col, k, c->mg_x);
+        FR_PROF_END(c, s, KK_COARSE);
+        FR_LAUNCH_CHECK(c);
+      }
+      FR_TRY(op_apply(c, q, c->mg_x, inv_dtau, a0_dt, c->mg_y, s));
+      {
+        FR_PROF_BEGIN(c, s);
+        k_p1_gather<N><<<blocks_for((long long)c->ne * NB, 256), 256, 0, s>>>(
+            c->mesh, c->basis, c->mg_colslot + (size_t)c->ne, c->mg_ncol, col, k, c->mg_y, L0.A);
+        FR_PROF_END(c, s, KK_COARSE);
+        FR_LAUNCH_CHECK(c);
+      }
+    }
+  }
+  FR_ACCOUNT(c, KK_COARSE, (double)c->mg_ncol * NB * c->ne * NB * 2.0 * NP, 0.0);
+  return FR_OK;
+}
+
+template <int N>
+int restrict_prolong(fr_ctx* c, const double* r, double* z0, cudaStream_t s, bool down) {
+  constexpr int NP = N * N;
+  FR_PROF_BEGIN(c, s);
+  if (down)
+    k_p1_restrict<N><<<blocks_for((long long)c->ne * NB, 256), 256, 0, s>>>(c->mesh, c->basis, r, c->mg[0].b);
+  else
+    k_p1_prolong<N><<<blocks_for((long long)c->ne * NP, 256), 256, 0, s>>>(c->mesh, c->basis, c->mg[0].x, z0);
+  FR_PROF_END(c, s, KK_COARSE);
+  FR_LAUNCH_CHECK(c);
+  FR_ACCOUNT(c, KK_COARSE, 2.0 * NB * c->ne * NP / (down ? 1.0 : 4.0), 8.0 * (4.0 * c->ne * NP + NB * c->ne));
+  return FR_OK;
+}
+
+// One V-cycle from level l: b_l given, the result left in x_l.
+int vcycle(fr_ctx* c, size_t l, cudaStream_t s) {
+  MgLevel& L = c->mg[l];
+  const LevelView V = view(L);
+  const int nu = std::max(1, c->cfg.mg_sweeps);
+  const double om = c->cfg.mg_omega;
+  const double per_pass = 2.0 * SL * BLK * L.nc;   // upper bound: five full blocks per row
+  if (L.nfin > 0) {
+    FR_PROF_BEGIN(c, s);
+    k_mg_dense<<<L.nfin, 64, 0, s>>>(L.fin, L.Ainv, L.b, L.x);
+    FR_PROF_END(c, s, KK_COARSE);
+    FR_LAUNCH_CHECK(c);
+  }
+  if (l + 1 >= c->mg.size()) return FR_OK;
+  MgLevel& Nx = c->mg[l + 1];
+  const unsigned gs = blocks_for(L.nc, CPB);
+  // pre-smoothing: x (from zero), then ping-pong between x and y, ending in x
+  double* cur = L.x;
+  double* oth = L.y;
+  for (int it = 0; it < nu; ++it) {
+    FR_PROF_BEGIN(c, s);
+    k_mg_smooth<<<gs, CPB * NB, 0, s>>>(V, L.b, it == 0 ? L.x : cur, it == 0 ? L.x : oth, om, it == 0);
+    FR_PROF_END(c, s, KK_COARSE);
+    FR_LAUNCH_CHECK(c);
+    if (it > 0) std::swap(cur, oth);
+  }
+  {
+    FR_PROF_BEGIN(c, s);
+    k_mg_residual<<<blocks_for((long long)L.nc * NB, 256), 256, 0, s>>>(V, L.b, cur, oth);
+    k_mg_restrict<<<blocks_for((long long)Nx.nc * NB, 256), 256, 0, s>>>(Nx.nc, L.children, L.qo, oth, Nx.b);
+    FR_PROF_END(c, s, KK_COARSE);
+    FR_LAUNCH_CHECK(c);
+  }
+  FR_TRY(vcycle(c, l + 1, s));
+  {
+    FR_PROF_BEGIN(c, s);
+    k_mg_prolong<<<blocks_for((long long)L.nc * NB, 256), 256, 0, s>>>(V, L.qo, Nx.x, cur);
+    FR_PROF_END(c, s, KK_COARSE);
+    FR_LAUNCH_CHECK(c);
+  }
+  for (int it = 0; it < nu; ++it) {
+    FR_PROF_BEGIN(c, s);
+    k_mg_smooth<<<gs, CPB * NB, 0, s>>>(V, L.b, cur, oth, om, 0);
+    FR_PROF_END(c, s, KK_COARSE);
+    FR_LAUNCH_CHECK(c);
+    std::swap(cur, oth);
+  }
+  if (cur != L.x) {
+    FR_CUDA_CHECK(c, cudaMemcpyAsync(L.x, cur, (size_t)L.nc * NB * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, s));
+  }
+  FR_ACCOUNT(c, KK_COARSE, per_pass * (2.0 * nu + 1.0), 8.0 * SL * BLK * L.nc * (2.0 * nu + 1.0));
+  return FR_OK;
+}
+
+}  // namespace
+
+namespace frk {
+
+void mg_free(fr_ctx* c) {
+  for (MgLevel& l : c->mg) {
+    int* is[] = {l.nb, l.cell_case, l.parent, l.children, l.gslot, l.fin};
+    for (int* p : is) if (p) cudaFree(p);
+    double* ds[] = {l.A, l.Dinv, l.x, l.y, l.b, l.qo, l.Ainv};
+    for (double* p : ds) if (p) cudaFree(p);
+  }
+  c->mg.clear();
+  if (c->mg_colslot) { cudaFree(c->mg_colslot); c->mg_colslot = nullptr; }
+  double** fs[] = {&c->mg_x, &c->mg_y, &c->mg_z0, &c->mg_t};
+  for (double** p : fs) if (*p) { cudaFree(*p); *p = nullptr; }
+  if (c->mg_bad) { cudaFree(c->mg_bad); c->mg_bad = nullptr; }
+  c->mg_ncol = 0;
+  c->mg_q = nullptr;
+}
+
+int mg_setup(fr_ctx* c) {
+  mg_free(c);
+  if (c->cfg.precond != FR_PRECOND_TWO_LEVEL) return FR_OK;
+  const bool bounded = c->bounded != 0;
+  // level grids of every case, cells numbered case after case
+  std::vector<CaseGrid> grids(c->ncases);
+  int off = 0;
+  for (int k = 0; k < c->ncases; ++k) {
+    grids[k] = CaseGrid{c->cps[k].nx, c->cps[k].ny, off};
+    off += c->cps[k].nx * c->cps[k].ny;
+  }
+  std::vector<char> done(c->ncases, 0);
+  std::vector<std::vector<int>> h_nb, h_case, h_parent, h_children, h_gslot, h_fin;
+  std::vector<std::vector<double>> h_qo;
+  while (true) {
+    int nc = 0;
+    for (int k = 0; k < c->ncases; ++k) if (!done[k]) nc += grids[k].nx * grids[k].ny;
+    if (nc == 0) break;
+    std::vector<int> nb((size_t)nc * SL), cs(nc), parent(nc, -1), gsl((size_t)nc * SL, -1), fin;
+    std::vector<double> qo((size_t)nc * 4, 0.0);
+    // the next level's grids (cases continuing) and their offsets
+    std::vector<CaseGrid> next(c->ncases);
+    int noff = 0;
+    for (int k = 0; k < c->ncases; ++k) {
+      if (done[k]) continue;
+      const CaseGrid& g = grids[k];
+      if (g.nx * g.ny <= MAXFIN) {
+        fin.push_back(g.off);
+        fin.push_back(g.nx * g.ny);
+      } else {
+        next[k] = CaseGrid{(g.nx + 1) / 2, (g.ny + 1) / 2, noff};
+        noff += next[k].nx * next[k].ny;
+      }
+    }
+    for (int k = 0; k < c->ncases; ++k) {
+      if (done[k]) continue;
+      const CaseGrid& g = grids[k];
+      const bool cont = g.nx * g.ny > MAXFIN;
+      for (int j = 0; j < g.ny; ++j) {
+        for (int i = 0; i < g.nx; ++i) {
+          const int cell = g.off + j * g.nx + i;
+          stencil_of(g, bounded, i, j, &nb[(size_t)cell * SL]);
+          cs[cell] = k;
+          if (!cont) continue;
+          const CaseGrid& G = next[k];
+          const int I = i / 2, J = j / 2;
+          parent[cell] = G.off + J * G.nx + I;
+          const bool sx = 2 * I + 1 < g.nx, sy = 2 * J + 1 < g.ny;
+          const double fx = sx ? 0.5 : 1.0, fy = sy ? 0.5 : 1.0;
+          const double sa = sx ? (double)(2 * (i - 2 * I) - 1) : 0.0;
+          const double sb = sy ? (double)(2 * (j - 2 * J) - 1) : 0.0;
+          qo[(size_t)cell * 4 + 0] = sa * fx;
+          qo[(size_t)cell * 4 + 1] = sb * fy;
+          qo[(size_t)cell * 4 + 2] = fx;
+          qo[(size_t)cell * 4 + 3] = fy;
+        }
+      }
+    }
+    h_nb.push_back(nb);
+    h_case.push_back(cs);
+    h_parent.push_back(parent);
+    h_gslot.push_back(gsl);
+    h_qo.push_back(qo);
+    h_fin.push_back(fin);
+    for (int k = 0; k < c->ncases; ++k) {
+      if (done[k]) continue;
+      if (grids[k].nx * grids[k].ny <= MAXFIN) done[k] = 1;
+      else grids[k] = next[k];
+    }
+  }
+  const size_t nlev = h_nb.size();
+  // children and parent slots from the next level's stencils
+  for (size_t l = 0; l + 1 < nlev; ++l) {
+    const int ncn = (int)h_case[l + 1].size();
+    std::vector<int> ch((size_t)ncn * 4, -1);
+    const int nc = (int)h_case[l].size();
+    for (int cell = 0; cell < nc; ++cell) {
+      const int P = h_parent[l][cell];
+      if (P < 0) continue;
+      int q = 0;
+      while (q < 4 && ch[(size_t)P * 4 + q] >= 0) ++q;
+      if (q == 4) { snprintf(c->err, sizeof(c->err), "two-level set-up: more than 4 children"); return FR_ERR_ARG; }
+      ch[(size_t)P * 4 + q] = cell;
+      for (int s = 0; s < SL; ++s) {
+        const int f = h_nb[l][(size_t)cell * SL + s];
+        if (f < 0) continue;
+        const int F = h_parent[l][f];
+        int S = -1;
+        for (int t = 0; t < SL; ++t) if (h_nb[l + 1][(size_t)P * SL + t] == F) S = t;
+        if (S < 0) { snprintf(c->err, sizeof(c->err), "two-level set-up: parent stencil mismatch"); return FR_ERR_ARG; }
+        h_gslot[l][(size_t)cell * SL + s] = S;
+      }
+    }
+    h_children.push_back(ch);
+  }
+  h_children.push_back({});
+  c->mg.resize(nlev);
+  for (size_t l = 0; l < nlev; ++l) {
+    MgLevel& L = c->mg[l];
+    L.nc = (int)h_case[l].size();
+    L.nfin = (int)h_fin[l].size() / 2;
+    FR_TRY(upload(c, &L.nb, h_nb[l]));
+    FR_TRY(upload(c, &L.cell_case, h_case[l]));
+    FR_TRY(upload(c, &L.parent, h_parent[l]));
+    FR_TRY(upload(c, &L.gslot, h_gslot[l]));
+    FR_TRY(upload(c, &L.qo, h_qo[l]));
+    FR_TRY(upload(c, &L.children, h_children[l]));
+    FR_TRY(upload(c, &L.fin, h_fin[l]));
+    FR_TRY(dalloc(c, &L.A, (size_t)L.nc * SL * BLK));
+    FR_TRY(dalloc(c, &L.Dinv, (size_t)L.nc * BLK));
+    FR_TRY(dalloc(c, &L.x, (size_t)L.nc * NB));
+    FR_TRY(dalloc(c, &L.y, (size_t)L.nc * NB));
+    FR_TRY(dalloc(c, &L.b, (size_t)L.nc * NB));
+    FR_TRY(dalloc(c, &L.Ainv, (size_t)L.nfin * DN * DN));
+    FR_CUDA_CHECK(c, cudaMemset(L.A, 0, (size_t)L.nc * SL * BLK * sizeof(double)));
+    FR_CUDA_CHECK(c, cudaMemset(L.x, 0, (size_t)L.nc * NB * sizeof(double)));
+    FR_CUDA_CHECK(c, cudaMemset(L.y, 0, (size_t)L.nc * NB * sizeof(double)));
+  }
+  // level 0: greedy colouring in which no stencil holds two members of one colour
+  const int ne = c->ne;
+  const std::vector<int>& nb0 = h_nb[0];
+  std::vector<std::vector<int>> members_of(ne);
+  for (int e = 0; e < ne; ++e)
+    for (int s = 0; s < SL; ++s)
+      if (nb0[(size_t)e * SL + s] >= 0) members_of[nb0[(size_t)e * SL + s]].push_back(e);
+  std::vector<int> colour(ne, -1);
+  int ncol = 0;
+  for (int f = 0; f < ne; ++f) {
+    std::vector<char> used(64, 0);
+    for (int e : members_of[f])
+      for (int s = 0; s < SL; ++s) {
+        const int g = nb0[(size_t)e * SL + s];
+        if (g >= 0 && colour[g] >= 0 && colour[g] < 64) used[colour[g]] = 1;
+      }
+    int col = 0;
+    while (col < 64 && used[col]) ++col;
+    if (col == 64) { snprintf(c->err, sizeof(c->err), "two-level set-up: colouring failed"); return FR_ERR_ARG; }
+    colour[f] = col;
+    ncol = std::max(ncol, col + 1);
+  }
+  // colslot layout on the device: [Ne] colours, then [Ne][ncol] slots
+  std::vector<int> cslot((size_t)ne + (size_t)ne * ncol, -1);
+  for (int e = 0; e < ne; ++e) cslot[e] = colour[e];
+  for (int e = 0; e < ne; ++e)
+    for (int s = 0; s < SL; ++s) {
+      const int f = nb0[(size_t)e * SL + s];
+      if (f >= 0) cslot[(size_t)ne + (size_t)e * ncol + colour[f]] = s;
+    }
+  c->mg_ncol = ncol;
+  FR_TRY(upload(c, &c->mg_colslot, cslot));
+  FR_TRY(dalloc(c, &c->mg_x, c->ndof));
+  FR_TRY(dalloc(c, &c->mg_y, c->ndof));
+  FR_TRY(dalloc(c, &c->mg_z0, c->ndof));
+  FR_TRY(dalloc(c, &c->mg_t, c->ndof));
+  FR_TRY(dalloc(c, &c->mg_bad, 1));
+  FR_CUDA_CHECK(c, cudaMemset(c->mg_bad, 0, sizeof(int)));
+  return FR_OK;
+}
+
+int mg_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s) {
+  if (c->cfg.precond != FR_PRECOND_TWO_LEVEL) return FR_OK;
+  if (c->mg.empty()) { snprintf(c->err, sizeof(c->err), "two-level preconditioner not set up"); return FR_ERR_ARG; }
+  c->mg_q = q;
+  c->mg_inv_dtau = inv_dtau;
+  c->mg_a0_dt = a0_dt;
+  int rc;
+  switch (c->n) {
+    case 2: rc = build_level0<2>(c, q, inv_dtau, a0_dt, s); break;
+    case 3: rc = build_level0<3>(c, q, inv_dtau, a0_dt, s); break;
+    case 4: rc = build_level0<4>(c, q, inv_dtau, a0_dt, s); break;
+    case 5: rc = build_level0<5>(c, q, inv_dtau, a0_dt, s); break;
+    default: return FR_ERR_ARG;
+  }
+  if (rc != FR_OK) return rc;
+  for (size_t l = 0; l < c->mg.size(); ++l) {
+    MgLevel& L = c->mg[l];
+    const LevelView V = view(L);
+    FR_PROF_BEGIN(c, s);
+    k_mg_invert_diag<<<blocks_for(L.nc, 64), 64, 0, s>>>(V, L.Dinv, c->mg_bad);
+    if (L.nfin > 0) k_mg_coarsest<<<L.nfin, 128, 0, s>>>(V, L.fin, L.Ainv, c->mg_bad);
+    if (l + 1 < c->mg.size()) {
+      const MgLevel& Nx = c->mg[l + 1];
+      k_mg_galerkin<<<blocks_for((long long)Nx.nc * SL * BLK, 256), 256, 0, s>>>(
+          V, L.qo, L.gslot, Nx.nc, Nx.nb, L.children, Nx.A);
+    }
+    FR_PROF_END(c, s, KK_COARSE);
+    FR_LAUNCH_CHECK(c);
+    FR_ACCOUNT(c, KK_COARSE, 2.0 * NB * NB * NB * L.nc, 0.0);
+  }
+  return FR_OK;
+}
+
+int precond_apply(fr_ctx* c, const double* q, const double* r, double* z, double inv_dtau,
+                  double a0_dt, cudaStream_t s) {
+  if (c->cfg.precond != FR_PRECOND_TWO_LEVEL) return block_apply(c, r, z, s);
+  int rc;
+  switch (c->n) {
+    case 2: rc = restrict_prolong<2>(c, r, nullptr, s, true); break;
+    case 3: rc = restrict_prolong<3>(c, r, nullptr, s, true); break;
+    case 4: rc = restrict_prolong<4>(c, r, nullptr, s, true); break;
+    case 5: rc = restrict_prolong<5>(c, r, nullptr, s, true); break;
+    default: return FR_ERR_ARG;
+  }
+  if (rc != FR_OK) return rc;
+  FR_TRY(vcycle(c, 0, s));
+  switch (c->n) {
+    case 2: rc = restrict_prolong<2>(c, nullptr, c->mg_z0, s, false); break;
+    case 3: rc = restrict_prolong<3>(c, nullptr, c->mg_z0, s, false); break;
+    case 4: rc = restrict_prolong<4>(c, nullptr, c->mg_z0, s, false); break;
+    case 5: rc = restrict_prolong<5>(c, nullptr, c->mg_z0, s, false); break;
+  }
+  if (rc != FR_OK) return rc;
+  // z = z0 + B^-1 (r - A z0)
+  FR_TRY(op_apply(c, q, c->mg_z0, inv_dtau, a0_dt, c->mg_t, s));
+  FR_TRY(axpby(c, 1.0, r, -1.0, c->mg_t, s));
+  FR_TRY(block_apply(c, c->mg_t, z, s));
+  return axpby(c, 1.0, c->mg_z0, 1.0, z, s);
+}
+
+}  // namespace frk

@@ -45,7 +45,8 @@ class _Config(ctypes.Structure):
                 ("line_search", ctypes.c_int), ("jvp_mode", ctypes.c_int),
                 ("graphs", ctypes.c_int), ("apply_accum", ctypes.c_int), ("tiles", ctypes.c_int),
                 ("block_mode", ctypes.c_int), ("orthog", ctypes.c_int),
-                ("krylov_arith", ctypes.c_int)]
+                ("krylov_arith", ctypes.c_int), ("precond", ctypes.c_int),
+                ("mg_sweeps", ctypes.c_int), ("mg_omega", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -126,7 +127,7 @@ _SIGS = {
     "fr_batch_kernel_launches": (ctypes.c_longlong, [_P]),
     "fr_batch_last_error": (ctypes.c_char_p, [_P]),
 }
-PROF_KINDS = 16
+PROF_KINDS = 17
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -195,6 +196,9 @@ class Config:
     block_mode: str = "linearized"
     orthog: str = "cgs2"
     krylov_arith: str = "fp64"
+    precond: str = "block"
+    mg_sweeps: int = 2
+    mg_omega: float = 0.7
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -214,6 +218,8 @@ class Config:
                 c.block_mode = {"linearized": 0, "dual": 1}[self.block_mode]
             elif f.name == "apply_accum":
                 c.apply_accum = {"fp32": 0, "df64": 1}[self.apply_accum]
+            elif f.name == "precond":
+                c.precond = {"block": 0, "twolevel": 1}[self.precond]
             else:
                 setattr(c, f.name, getattr(self, f.name))
         return c
