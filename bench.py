@@ -40,18 +40,21 @@ UNIT = "GDOF/s"
 
 
 # ------------------------------------------------------------------ roofline peaks
-# FP64 pipe of one GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26 TFLOP/s nominal;
-# 1.20 TFLOP/s measured with a dependent-FMA probe at 2.0 GHz on this machine.  FP32 SIMT:
-# 152 x 128 x 2 x 2.07 GHz = 80.5 TFLOP/s nominal, 70.3 measured by the same probe.
-FP64_PEAK_TFLOPS = 1.20
-FP32_PEAK_TFLOPS = 70.3
-ALU_PEAK_SOURCE = "FMA-throughput probe on this pool's GB300 (nominal from unit counts x clock: 1.26 FP64, 80.5 FP32)"
+# ALU peaks from unit counts and the maximum SM clock (2.07 GHz): the FP64 pipe of a
+# GB300 does 2 FMA per clock per SM, 152 SMs x 2 x 2 flop x 2.07 GHz = 1.26 TFLOP/s; the FP32
+# SIMT pipe 152 x 128 x 2 x 2.07 GHz = 80.5 TFLOP/s.  HBM: the measured copy bandwidth.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+ALU_PEAK_SOURCE = ("nominal from unit counts and the maximum SM clock: FP64 152 SMs x 2 FMA/clk "
+                   "x 2 flop x 2.07 GHz = 1.26 TFLOP/s; FP32 152 x 128 FMA/clk x 2 x 2.07 GHz = "
+                   "80.5 TFLOP/s")
 # Bound of each kernel class as ncu measured it: every FP64 kernel, the Gram-Schmidt
-# reductions and vector updates included, saturates the FP64 pipe (1 FMA per 8 bytes
-# needs 1.7 TFLOP/s at full HBM bandwidth); the FP32/BF16 block apply streams DRAM.
+# reductions, vector updates and the coarse-level kernels included, saturates the FP64
+# pipe before DRAM (1 FMA per 8 bytes needs 1.7 TFLOP/s at full HBM bandwidth); the
+# FP32/BF16 block apply streams DRAM.
 ALU_KINDS = {"trace", "face", "elem", "trace_jvp", "face_jvp", "elem_jvp", "block_jacobian",
              "block_factor", "geometry", "krylov_reduce", "vector", "linearize", "linear_apply",
-             "linear_adjoint"}
+             "linear_adjoint", "coarse"}
 
 
 # DRAM bytes per launch of a kernel class from one ncu capture (dram__bytes_read.sum +
@@ -162,53 +165,119 @@ def sharded_throughput(t_rank: float, units_total: float, world: int, dist, devi
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(steps: int, warmup: int):
-    """The oracle as it stands on a bounded sample: BDF2 steps on the 16x16 sub-box."""
+# Per-step work profile of the headline steps (means over the timed steps of the GPU arm,
+# two-level preconditioner, 64x64 p=3 vortex): the reference arm, which runs before any GPU
+# measurement, prices these counts; the GPU arm prices its own.
+STEP_PROFILE = {"newton": 7.0, "gmres": 450.0, "builds": 4.0, "restart": 30,
+                "precond": "twolevel"}
+
+
+def oracle_unit_costs(w, precond: str):
+    """The oracle as it stands, timed per unit of a BDF2 step on a bounded sample: a
+    16 x 16 sub-box of workload w's element size (same p, M, Re, dt), seconds per call of
+    one residual, one exact Newton-operator product (complex step), one preconditioner
+    build (element blocks by coloured complex steps and their inverses, plus for the
+    two-level preconditioner the coloured Galerkin products and the hierarchy) and one
+    preconditioner apply, and one CGS2 Arnoldi step at the mean basis size of a restart
+    cycle.  Every unit is linear in the number of elements (the colour count does not
+    grow with the mesh), so the costs are returned per DOF."""
+    import numpy as np
     from oracle import physics as ph
     from oracle import residual as rs
     from oracle import solver as sv
+    from oracle import twolevel as tl
     from paper_1903_06304_gb300 import inputs as inp
-    w0 = inp.NS_VORTEX_64
-    w = inp.Workload("ns_vortex_16x16_p3_sample", 16, 16, w0.p, w0.mach, w0.re, w0.kappa,
-                     (0.0, 2.5, 0.0, 2.5), dt=w0.dt, restart=w0.restart)
-    c, v, q = inp.make_case(w)
-    prob = sv.Problem(rs.Mesh(w.nx, w.ny, c, v), w.p, ph.Gas(mach=w.mach, re=w.re, kappa=w.kappa))
-    qc_n = prob.qc(q)
-    qc_nm1 = qc_n
-    times = []
-    for k in range(warmup + steps):
+    n = 16
+    h = (w.box[1] - w.box[0]) / w.nx
+    c = inp.box_mesh(n, n, 0.0, n * h, 0.0, n * h)
+    q = inp.random_perturbation(inp.uniform_state(n * n, w.p, w.mach, 0.8, 0.3), 3, 0.05, w.mach)
+    prob = sv.Problem(rs.Mesh(n, n, c, np.zeros_like(c)), w.p, ph.Gas(mach=w.mach, re=w.re, kappa=w.kappa))
+    a0_dt = 1.5 / w.dt
+    x = inp.random_vector(q.shape, 4)
+    dof = q.size
+
+    def clock(fn, reps=1):
         t0 = time.perf_counter()
-        q1, st = sv.bdf2_step(prob, q, qc_n, qc_nm1, w.dt, coeffs=sv.BDF1 if k == 0 else sv.BDF2,
-                              restart=w.restart, tol_res=w.tol_res, maxit_lin=w.maxit_lin,
-                              tol_pseudo=w.tol_pseudo, maxit_newton=w.maxit_newton)
-        dt_s = time.perf_counter() - t0
-        qc_nm1, qc_n, q = qc_n, prob.qc(q1), q1
-        if k >= warmup:
-            times.append(dt_s)
-    dof = w.dof
-    sec = sum(times) / len(times)
-    return {"value": dof / sec / 1e9, "unit": UNIT, "sec_per_step": sec, "dof": dof,
-            "cores": 1, "kind": "oracle",
-            "sample": "oracle BDF2 steps (BDF1 first) on the 16x16 p=3 sub-box of the vortex "
-                      "box (same p, M, Re, dt; 1/16 of the DOF), numpy FP64, one thread"}
+        for _ in range(reps):
+            out = fn()
+        return (time.perf_counter() - t0) / reps, out
+
+    t_R, _ = clock(lambda: prob.R(q), 3)
+    Aop = lambda v: sv.apply_A(prob, q, v, 1e-20, a0_dt)
+    t_A, _ = clock(lambda: Aop(x), 3)
+    if precond == "twolevel":
+        t_build, pc = clock(lambda: tl.build(prob, q, 1e-20, a0_dt))
+        t_M, _ = clock(lambda: pc.apply(x, Aop), 2)
+    else:
+        t_build, Binv = clock(lambda: np.linalg.inv(sv.block_jacobian(prob, q, 1e-20, a0_dt)))
+        t_M, _ = clock(lambda: sv.block_apply(Binv, x), 3)
+    j = w.restart // 2
+    V = np.random.default_rng(5).standard_normal((j + 1, dof))
+    wv = x.ravel()
+
+    def arnoldi():
+        h1 = V @ wv
+        w2 = wv - V.T @ h1
+        h2 = V @ w2
+        return w2 - V.T @ h2
+
+    t_arn, _ = clock(arnoldi, 3)
+    return {"per_dof": {k: v / dof for k, v in (("residual", t_R), ("operator", t_A), ("build", t_build),
+                                                 ("precond", t_M), ("arnoldi", t_arn))},
+            "sample": f"{n}x{n} sub-box of the workload's element size, p={w.p}, {dof} DOF",
+            "cores": 1}
+
+
+def oracle_step_seconds(costs, profile, ndof):
+    """Oracle seconds for one BDF2 step of ndof DOF with the given operation counts: a
+    residual per Newton iteration (and one at the start), a preconditioner build per
+    build, per GMRES iteration an operator product, a preconditioner apply and an Arnoldi
+    step, and per restart cycle one more product and apply for the true residual."""
+    c = costs["per_dof"]
+    cycles = profile["gmres"] / profile["restart"] + profile["newton"]
+    per_dof = ((profile["newton"] + 1) * c["residual"] + profile["builds"] * c["build"]
+               + profile["gmres"] * (c["operator"] + c["precond"] + c["arnoldi"])
+               + cycles * (c["operator"] + c["precond"]))
+    return per_dof * ndof
+
+
+def oracle_sample(w, profile):
+    costs = oracle_unit_costs(w, profile["precond"])
+    sec = oracle_step_seconds(costs, profile, w.dof)
+    return {"value": w.dof / sec / 1e9, "unit": UNIT, "sec_per_step": sec, "dof": w.dof,
+            "cores": costs["cores"], "kind": "oracle", "unit_costs_per_dof_s": costs["per_dof"],
+            "profile": profile,
+            "sample": ("oracle (numpy FP64, one thread) timed per unit on a bounded sample, the "
+                       + costs["sample"] + ", scaled per DOF to the workload and priced with the "
+                       f"step's counts (Newton {profile['newton']:.1f}, GMRES {profile['gmres']:.0f}, "
+                       f"builds {profile['builds']:.1f}, {profile['precond']} preconditioner)")}
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    res = oracle_sample(args.steps, args.warmup)
-    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
+    from paper_1903_06304_gb300 import inputs as inp
+    w = inp.WORKLOADS[args.workload]
+    prof = dict(STEP_PROFILE, precond=args.precond)
+    times = []
+    res = None
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        res = oracle_sample(w, prof)
+        if k >= args.warmup:
+            times.append(res["sec_per_step"])
+    sec = sum(times) / len(times)
+    value = w.dof / sec / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": res["sec_per_step"] * 1e3, "higher_is_better": True,
+            "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "ns_vortex_64x64_p3",
-                       "sample": "ns_vortex_16x16_p3 sub-box (same element size, p, M, Re, dt)",
-                       "note": res["sample"]},
-            "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": res["cores"],
+            "config": {"workload": w.name, "note": res["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["cores"],
                              "kind": "oracle", "sample": res["sample"]},
-            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -261,6 +330,148 @@ def large_n_sweep(sizes, torch, fr, inp, flush):
     return out
 
 
+def march_inputs(w, nsteps, T):
+    """Device copies of the mesh of every step of a march (corners and corner velocities at
+    t = (k + 1) dt) for deforming workloads, made before any timed region; None for static
+    meshes (one geometry for the whole march)."""
+    if not w.deforming:
+        return None
+    from paper_1903_06304_gb300 import inputs as inp
+    out = []
+    for k in range(nsteps):
+        c, v, _ = inp.make_case(w, t=(k + 1) * w.dt)
+        out.append((T(c), T(v)))
+    return out
+
+
+class March:
+    """State of a BDF2 march on the device: q^n, q^c,n, q^c,n-1 and the step index; a
+    deforming mesh moves to t^(n+1) (the library's geometry kernel) before each step."""
+
+    def __init__(self, S, q0, meshes, fr):
+        import torch
+        self.S, self.fr, self.meshes = S, fr, meshes
+        self.q = q0.clone()
+        self.qc_n = torch.empty_like(self.q)
+        self.qc_nm1 = torch.empty_like(self.q)
+        S.conservative(self.q, self.qc_n)
+        self.qc_nm1.copy_(self.qc_n)
+        self.k = 0
+
+    def step(self):
+        if self.meshes is not None:
+            c, v = self.meshes[self.k]
+            self.S.update_mesh(c, v)
+        coeffs = self.fr.BDF1 if self.k == 0 else self.fr.BDF2
+        st = self.S.bdf2_step(self.q, self.qc_n, self.qc_nm1, self.S.dt, coeffs=coeffs,
+                              allow_unconverged=True)
+        self.qc_nm1.copy_(self.qc_n)
+        self.S.conservative(self.q, self.qc_n)
+        self.k += 1
+        return st.summary()
+
+    def save(self):
+        return (self.q.clone(), self.qc_n.clone(), self.qc_nm1.clone(), self.k)
+
+    def restore(self, snap):
+        q, a, b, k = snap
+        self.q.copy_(q)
+        self.qc_n.copy_(a)
+        self.qc_nm1.copy_(b)
+        self.k = k
+
+
+def timed_steps(run, K, flush, barrier):
+    """K steps with CUDA events around each on the current stream (L2 flushed before each,
+    outside the events); returns per-step ms, stats and the library launches inside."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    stats = []
+    launches0 = run.S.kernel_launches
+    barrier()
+    for k in range(K):
+        flush.zero_()
+        ev[k][0].record()
+        stats.append(run.step())
+        ev[k][1].record()
+    barrier()
+    return [a.elapsed_time(b) for a, b in ev], stats, run.S.kernel_launches - launches0
+
+
+def step_summary(stats):
+    return {"converged": [s["converged"] for s in stats],
+            "newton": [s["newton_iterations"] for s in stats],
+            "gmres": [sum(s["gmres_iterations"]) for s in stats],
+            "res_drop": [s["res_history"][-1] / s["res_history"][0] for s in stats]}
+
+
+def low_mach_deforming_report(args, torch, fr, inp, T, flush):
+    """The deforming 128 x 128, p = 3, M = 0.01 workload: the vortex march's first steps with
+    the two-level preconditioner and each block precision, free-stream preservation of the
+    uniform stream on the moving mesh, and the rounding floor of Res_m (the continuity
+    residual evaluated by the two tile shapes, whose FMA contractions differ)."""
+    w = inp.NS_DEFORM_128
+    c0, v0, q0 = inp.make_case(w, t=0.0)
+    meshes = march_inputs(w, args.c3_steps, T)
+    out = {"workload": w.name, "dof": w.dof, "newton_cap": args.c3_newton}
+
+    def solver(prec, precond, tiles=1):
+        S = fr.Solver(fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=prec,
+                                precond=precond, maxit_newton=args.c3_newton, restart=args.restart,
+                                maxit_lin=args.maxit_lin, graphs=args.graphs, tiles=tiles,
+                                apply_accum=args.apply_accum), w.nx, w.ny)
+        S.dt = w.dt
+        S.update_mesh(T(c0), T(v0))
+        return S
+
+    finals = {}
+    for prec in ("fp64", "fp32", "bf16"):
+        S = solver(prec, args.precond)
+        run = March(S, T(q0), meshes, fr)
+        ms, st, _ = timed_steps(run, args.c3_steps if prec == "fp32" else 1, flush, torch.cuda.synchronize)
+        out[f"march_{prec}"] = dict(step_summary(st), sec_per_step=[m / 1e3 for m in ms])
+        if prec != "fp32":
+            finals[prec] = run.q.clone()
+        else:
+            r1 = March(S, T(q0), meshes, fr)
+            r1.step()
+            finals[prec] = r1.q.clone()
+        S.close()
+    dq = (finals["fp64"] - T(q0)).view(4, -1).abs().amax(dim=1)
+    for prec in ("fp32", "bf16"):
+        diff = (finals[prec] - finals["fp64"]).view(4, -1).abs().amax(dim=1)
+        out[f"march_{prec}"]["state_diff_vs_fp64_step1"] = float((diff / dq).max())
+    # free stream on the moving mesh
+    S = solver("fp32", args.precond)
+    qu = T(inp.uniform_state(w.ne, w.p, w.mach))
+    R = torch.empty_like(qu)
+    worst = 0.0
+    for t in (0.05, 0.13, 0.21):
+        c, v, _ = inp.make_case(w, t=t)
+        S.update_mesh(T(c), T(v))
+        S.residual(qu, R)
+        worst = max(worst, float(R.abs().max()))
+    out["free_stream_max_abs_residual"] = worst
+    S.close()
+    # rounding floor of Res_m
+    rs_ = []
+    for tiles in (1, 2):
+        S = solver("fp32", "block", tiles=tiles)
+        c, v, _ = inp.make_case(w, t=w.dt)
+        S.update_mesh(T(c), T(v))
+        qd = T(q0)
+        qc = torch.empty_like(qd)
+        S.conservative(qd, qc)
+        r = torch.empty_like(qd)
+        S.bdf_rhs(qd, qc, qc, fr.BDF1, w.dt, r)
+        rs_.append(r.clone())
+        S.close()
+    res0 = float(torch.linalg.norm(rs_[0][0]))
+    out["res0_continuity"] = res0
+    out["rounding_floor_rel"] = float(torch.linalg.norm(rs_[0][0] - rs_[1][0])) / res0
+    return out
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -286,76 +497,52 @@ def gpu_arm(args):
     w = inp.WORKLOADS[args.workload]
     corners, vel, q0 = inp.make_case(w)
     T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    nsteps = args.startup + args.warmup + args.steps
+    meshes = march_inputs(w, nsteps, T)
 
-    def make_solver(prec, arith=None):
+    def make_solver(prec, arith=None, precond=None):
         cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=prec,
                         restart=args.restart, maxit_lin=args.maxit_lin, tol_res=w.tol_res,
                         tol_pseudo=w.tol_pseudo, maxit_newton=args.maxit_newton, lag=2,
                         line_search=args.line_search, graphs=args.graphs,
                         apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog,
-                        krylov_arith=arith or args.krylov_arith)
+                        krylov_arith=arith or args.krylov_arith, precond=precond or args.precond)
         S = fr.Solver(cfg, w.nx, w.ny)
+        S.dt = w.dt
         S.update_mesh(T(corners), T(vel))
         return S
 
-    class Run:
-        """State of a BDF2 march: q^n, q^c,n, q^c,n-1 resident on the device."""
-
-        def __init__(self, S):
-            self.S = S
-            self.q = T(q0)
-            self.qc_n = torch.empty_like(self.q)
-            self.qc_nm1 = torch.empty_like(self.q)
-            S.conservative(self.q, self.qc_n)
-            self.qc_nm1.copy_(self.qc_n)
-            self.k = 0
-
-        def step(self):
-            coeffs = fr.BDF1 if self.k == 0 else fr.BDF2
-            st = self.S.bdf2_step(self.q, self.qc_n, self.qc_nm1, w.dt, coeffs=coeffs,
-                                  allow_unconverged=True)
-            self.qc_nm1.copy_(self.qc_n)
-            self.S.conservative(self.q, self.qc_n)
-            self.k += 1
-            return st.summary()
-
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
-    def timed_steps(run, K):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(K)]
-        stats = []
-        launches0 = run.S.kernel_launches
-        barrier()
-        for k in range(K):
-            flush.zero_()
-            ev[k][0].record()
-            stats.append(run.step())
-            ev[k][1].record()
-        barrier()
-        ms = [a.elapsed_time(b) for a, b in ev]
-        return ms, stats, run.S.kernel_launches - launches0
-
-    # ---- headline: configured precision.  The march first runs --startup untimed steps:
-    # the sampled vortex is not a discrete solution of the scheme, and the first BDF2 steps
-    # carry a stiff pressure transient that the element block-Jacobi Newton-Krylov loop
-    # does not converge (see the design notes); warm-up and timed steps follow it.
+    # ---- the march: start-up steps (recorded, untimed), warm-up, then the timed steps.
+    # The sampled vortex is not a discrete solution of the scheme: the first BDF2 steps
+    # carry a stiff pressure transient that neither preconditioner converges (see the design
+    # notes); the start-up steps and their convergence are reported with the line.
     S = make_solver(args.prec)
-    run = Run(S)
-    for _ in range(args.startup + args.warmup):
+    run = March(S, T(q0), meshes, fr)
+    startup = []
+    for _ in range(args.startup):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = run.step()
+        torch.cuda.synchronize()
+        startup.append((time.perf_counter() - t0, st))
+    for _ in range(args.warmup):
         run.step()
+    snap = run.save()
     clocks = ClockSampler(local)
-    ms, stats, launches = timed_steps(run, args.steps)
+    ms, stats, launches = timed_steps(run, args.steps, flush, barrier)
     clock_info = clocks.stop()
     t_rank = sum(ms) / 1e3
     dof = S.ndof
     t_max, value = replica_throughput(t_rank, dof * args.steps, world, dist, dev)
     ms_per_step = t_max * 1e3 / args.steps
 
-    # ---- per-kernel device time over the same number of steps (profiling pass)
+    # ---- per-kernel device time over the same steps (profiling pass from the same state)
+    run.restore(snap)
     S.profile(True)
     S.profile_read(reset=True)
-    _ms_p, _st_p, _ = timed_steps(run, args.steps)
+    _ms_p, st_p, _ = timed_steps(run, args.steps, flush, barrier)
     prof = S.profile_read(reset=True)
     S.profile(False)
     hbm_gbs, hbm_src = hbm_peak()
@@ -380,8 +567,55 @@ def gpu_arm(args):
         e["frac"] = e["achieved"] / e["peak"]
         kernels[name] = e
     dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    same_steps = [s["newton_iterations"] for s in st_p] == [s["newton_iterations"] for s in stats]
 
-    # ---- kernel throughput: residual and JVP at the final state (CUDA events)
+    # ---- end-to-end through host buffers, the same steps from the same state: each step
+    # copies q^n, q^c,n, q^c,n-1 (and the step's mesh on a moving mesh) from pinned host
+    # memory and q^n+1, q^c,n+1, q^c,n back
+    e2e = None
+    if not args.no_e2e:
+        run.restore(snap)
+        hq = torch.empty_like(run.q, device="cpu").pin_memory()
+        hqn = torch.empty_like(hq).pin_memory()
+        hqm = torch.empty_like(hq).pin_memory()
+        hq.copy_(run.q)
+        hqn.copy_(run.qc_n)
+        hqm.copy_(run.qc_nm1)
+        hmesh = None
+        if meshes is not None:
+            hmesh = [(c.cpu().pin_memory(), v.cpu().pin_memory()) for c, v in meshes]
+        evs = []
+        barrier()
+        for k in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            run.q.copy_(hq, non_blocking=True)
+            run.qc_n.copy_(hqn, non_blocking=True)
+            run.qc_nm1.copy_(hqm, non_blocking=True)
+            if hmesh is not None:
+                c, v = meshes[run.k]
+                c.copy_(hmesh[run.k][0], non_blocking=True)
+                v.copy_(hmesh[run.k][1], non_blocking=True)
+            run.step()
+            hq.copy_(run.q, non_blocking=True)
+            hqn.copy_(run.qc_n, non_blocking=True)
+            hqm.copy_(run.qc_nm1, non_blocking=True)
+            b.record()
+            evs.append((a, b))
+        barrier()
+        t_e2e = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+        t_e2e, e2e_value = replica_throughput(t_e2e, dof * args.steps, world, dist, dev)
+        nb = run.q.numel() * 8
+        mb = 0 if meshes is None else 2 * meshes[0][0].numel() * 8
+        e2e = {"value": e2e_value, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * nb + mb, "d2h_bytes_per_step": 3 * nb,
+               "same_steps_as_value": True}
+
+    # ---- kernel throughput: residual and JVP at the start state of the timed steps
+    run.restore(snap)
+    if meshes is not None:
+        S.update_mesh(*meshes[run.k])
     out = torch.empty_like(run.q)
     vec = torch.randn_like(run.q)
 
@@ -446,95 +680,70 @@ def gpu_arm(args):
                            "flushed_l2": qo.numel() / (cold * 1e-3) / 1e9, "median_of": 50}
         So.close()
 
-    # ---- GMRES iteration cost at the final state: a fixed count (tol_res 1e-30), so the
+    # ---- GMRES iteration cost at the start state: a fixed count (tol_res 1e-30), so the
     # per-iteration time does not depend on the Newton history
-    gm_cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
-                       restart=args.restart, maxit_lin=120, tol_res=1e-30, graphs=args.graphs,
-                       apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog,
-                       krylov_arith=args.krylov_arith)
-    Sg = fr.Solver(gm_cfg, w.nx, w.ny)
-    Sg.update_mesh(T(corners), T(vel))
-    Sg.precond_build(run.q, 1e-20, 1.5 / w.dt)
-    rhs = torch.empty_like(run.q)
-    Sg.bdf_rhs(run.q, run.qc_n, run.qc_nm1, fr.BDF2, w.dt, rhs)
-    xg = torch.empty_like(run.q)
-    Sg.gmres(run.q, rhs, xg, 1e-20, 1.5 / w.dt)
-    torch.cuda.synchronize()
-    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ga.record()
-    its_g = Sg.gmres(run.q, rhs, xg, 1e-20, 1.5 / w.dt)
-    gb.record()
-    torch.cuda.synchronize()
-    us_per_gmres_it = 1e3 * ga.elapsed_time(gb) / its_g
-    Sg.close()
+    gm = {}
+    for precond in ("block", "twolevel"):
+        gm_cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
+                           restart=args.restart, maxit_lin=120, tol_res=1e-30, graphs=args.graphs,
+                           apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog,
+                           krylov_arith=args.krylov_arith, precond=precond)
+        Sg = fr.Solver(gm_cfg, w.nx, w.ny)
+        Sg.update_mesh(*(meshes[run.k] if meshes is not None else (T(corners), T(vel))))
+        Sg.precond_build(run.q, 1e-20, 1.5 / w.dt)
+        rhs = torch.empty_like(run.q)
+        Sg.bdf_rhs(run.q, run.qc_n, run.qc_nm1, fr.BDF2, w.dt, rhs)
+        xg = torch.empty_like(run.q)
+        Sg.gmres(run.q, rhs, xg, 1e-20, 1.5 / w.dt)
+        torch.cuda.synchronize()
+        ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ga.record()
+        its_g = Sg.gmres(run.q, rhs, xg, 1e-20, 1.5 / w.dt)
+        gb.record()
+        torch.cuda.synchronize()
+        gm[precond] = 1e3 * ga.elapsed_time(gb) / its_g
+        Sg.close()
 
-    # ---- precision comparison: the same steps from the same state per block precision
-    # (FP64 Krylov basis) and with FP32 blocks and the double-float basis; the final state
-    # of each against the all-FP64 run (max over entries, relative to the per-variable
-    # magnitude of the state change)
+    # ---- precision comparison: the timed steps again from the same state per block
+    # precision (FP64 Krylov basis) and with FP32 blocks and the double-float basis; the
+    # final state of each against the all-FP64 run (max over entries, relative to the
+    # per-variable magnitude of the state change)
     compare = {}
     if not args.no_compare:
         finals = {}
-        q_start = run.q.clone()
         variants = {"fp64": ("fp64", "fp64"), "fp32": ("fp32", "fp64"), "bf16": ("bf16", "fp64"),
                     "fp32_df64_basis": ("fp32", "df64")}
-        for prec, (bprec, arith) in variants.items():
+        for name, (bprec, arith) in variants.items():
             S2 = make_solver(bprec, arith)
-            r2 = Run(S2)
-            r2.q.copy_(run.q)
-            r2.qc_n.copy_(run.qc_n)
-            r2.qc_nm1.copy_(run.qc_nm1)
-            r2.k = run.k
-            ms2, st2, _ = timed_steps(r2, max(2, min(args.steps, 3)))
-            finals[prec] = r2.q.clone()
-            compare[prec] = {"sec_per_step": statistics.mean(ms2) / 1e3,
+            r2 = March(S2, snap[0], meshes, fr)
+            r2.restore(snap)
+            ms2, st2, _ = timed_steps(r2, args.steps, flush, torch.cuda.synchronize)
+            finals[name] = r2.q.clone()
+            compare[name] = {"sec_per_step": statistics.mean(ms2) / 1e3,
                              "newton": [s["newton_iterations"] for s in st2],
                              "gmres_total": [sum(s["gmres_iterations"]) for s in st2],
                              "converged": all(s["converged"] for s in st2)}
             S2.close()
-        nvar = 4
-        dq = (finals["fp64"] - q_start).view(nvar, -1).abs().amax(dim=1)
-        for prec in compare:
-            diff = (finals[prec] - finals["fp64"]).view(nvar, -1).abs().amax(dim=1)
-            compare[prec]["state_diff_vs_fp64"] = float((diff / dq).max())
+        dq = (finals["fp64"] - snap[0]).view(4, -1).abs().amax(dim=1)
+        for name in compare:
+            diff = (finals[name] - finals["fp64"]).view(4, -1).abs().amax(dim=1)
+            compare[name]["state_diff_vs_fp64"] = float((diff / dq).max())
 
-    # ---- end-to-end through host buffers
-    e2e = None
-    if not args.no_e2e:
-        hq = torch.empty_like(run.q, device="cpu").pin_memory()
-        hqn = torch.empty_like(hq).pin_memory()
-        hqm = torch.empty_like(hq).pin_memory()
-        hq.copy_(run.q)
-        hqn.copy_(run.qc_n)
-        hqm.copy_(run.qc_nm1)
-        evs = []
-        barrier()
-        for k in range(args.steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            run.q.copy_(hq, non_blocking=True)
-            run.qc_n.copy_(hqn, non_blocking=True)
-            run.qc_nm1.copy_(hqm, non_blocking=True)
-            run.step()
-            hq.copy_(run.q, non_blocking=True)
-            hqn.copy_(run.qc_n, non_blocking=True)
-            hqm.copy_(run.qc_nm1, non_blocking=True)
-            b.record()
-            evs.append((a, b))
-        barrier()
-        t_e2e = sum(a.elapsed_time(b) for a, b in evs) / 1e3
-        t_e2e, e2e_value = replica_throughput(t_e2e, dof * args.steps, world, dist, dev)
-        nb = run.q.numel() * 8
-        e2e = {"value": e2e_value, "unit": UNIT,
-               "h2d_bytes_per_step": 3 * nb, "d2h_bytes_per_step": 3 * nb}
+    low_mach = None
+    if rank == 0 and not args.no_c3:
+        low_mach = low_mach_deforming_report(args, torch, fr, inp, T, flush)
 
-    # ---- CPU baseline (rank 0, N = 1 only)
+    # ---- CPU baseline (rank 0, N = 1 only): the oracle's unit costs priced with the
+    # timed steps' own counts
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res = oracle_sample(1, 0)
+        profile = {"newton": statistics.mean(s["newton_iterations"] for s in stats),
+                   "gmres": statistics.mean(sum(s["gmres_iterations"]) for s in stats),
+                   "builds": statistics.mean(s["block_builds"] for s in stats),
+                   "restart": args.restart, "precond": args.precond}
+        res = oracle_sample(w, profile)
         cpu = {"value": res["value"], "unit": UNIT, "cores": res["cores"], "kind": "oracle",
-               "sample": res["sample"]}
+               "sample": res["sample"], "sec_per_step": res["sec_per_step"]}
 
     dk = kernels[dominant]
     roof = {"kernel": dominant, "bound": dk["bound"], "achieved": dk["achieved"],
@@ -549,16 +758,20 @@ def gpu_arm(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "mesh": f"{w.nx}x{w.ny} periodic [0,10]^2",
+                   "deforming": w.deforming,
                    "p": w.p, "dof": dof, "mach": w.mach, "re_ref": w.re, "kappa": w.kappa,
                    "dt": w.dt, "tol_pseudo": w.tol_pseudo, "tol_res": w.tol_res,
                    "gmres": f"GMRES({args.restart}) left-preconditioned, {args.orthog}, "
                             f"{args.krylov_arith} basis, maxit {args.maxit_lin}",
                    "newton": f"max {args.maxit_newton} iterations, backtracking {args.line_search} halvings",
-                   "precond": f"element block-Jacobi, {args.prec} blocks, {args.apply_accum} apply accumulation",
+                   "precond": f"{args.precond} ({args.prec} element blocks, {args.apply_accum} apply accumulation)",
+                   "march": f"{args.startup} start-up + {args.warmup} warm-up steps before the timed steps",
                    "l2": "256 MiB write between timed steps, outside the per-step events",
                    "tiles": S.tiles,
                    "parallelism": "replicas" if world > 1 else "single"},
-        "startup_steps": args.startup,
+        "startup_steps": {"count": args.startup,
+                          "sec_per_step": [round(t, 4) for t, _ in startup],
+                          **step_summary([s for _, s in startup])},
         "sec_per_bdf2_step": ms_per_step / 1e3,
         "converged_all": all(s["converged"] for s in stats),
         "newton_iterations": [s["newton_iterations"] for s in stats],
@@ -572,9 +785,11 @@ def gpu_arm(args):
         "large_n_sweep": sweep,
         "bounded_ogrid_gdofs": ogrid,
         "linearize_ms": t_lin,
-        "us_per_gmres_iteration": us_per_gmres_it,
+        "us_per_gmres_iteration": gm,
         "precision_compare": compare,
+        "low_mach_deforming": low_mach,
         "kernels": kernels,
+        "kernels_same_steps": same_steps,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -740,15 +955,21 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--startup", type=int, default=8,
-                    help="untimed BDF2 steps of the march before the warm-up steps")
+    ap.add_argument("--startup", type=int, default=5,
+                    help="BDF2 steps of the march (recorded, untimed) before the warm-up steps")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ns_vortex_64x64_p3")
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--precond", default="twolevel", choices=["block", "twolevel"],
+                    help="element block Jacobi, or with the P1 coarse correction")
+    ap.add_argument("--no-c3", dest="no_c3", action="store_true",
+                    help="skip the deforming 128x128 M = 0.01 report")
+    ap.add_argument("--c3-steps", dest="c3_steps", type=int, default=3)
+    ap.add_argument("--c3-newton", dest="c3_newton", type=int, default=10)
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--maxit-lin", dest="maxit_lin", type=int, default=100)
     ap.add_argument("--maxit-newton", dest="maxit_newton", type=int, default=40)
-    ap.add_argument("--line-search", dest="line_search", type=int, default=4,
+    ap.add_argument("--line-search", dest="line_search", type=int, default=0,
                     help="backtracking halvings per Newton update (0: plain Newton)")
     ap.add_argument("--apply-accum", dest="apply_accum", default="df64", choices=["df64", "fp32"],
                     help="block-apply arithmetic with FP32/BF16-stored inverses")

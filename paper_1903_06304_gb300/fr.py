@@ -307,15 +307,19 @@ class Batch:
         self._check(self.lib.fr_batch_conservative(self.b, _ptr(q), _ptr(out), _stream(stream)))
         return out
 
-    def bdf2_step(self, q, qc_n, qc_nm1, coef, stream=None, allow_unconverged=False):
-        """coef: per case (a0, a1, a2, dt).  Returns the per-case Stats list."""
+    def bdf2_step(self, q, qc_n, qc_nm1, coef, stream=None, allow_unconverged=False,
+                  allow_nonfinite=False):
+        """coef: per case (a0, a1, a2, dt).  Returns the per-case Stats list; the call's
+        status code is kept in ``last_rc`` (FR_ERR_NOT_CONVERGED and FR_ERR_NONFINITE are
+        returned instead of raised when allowed: the other cases still advanced)."""
         nc = len(self.cases)
         flat = (ctypes.c_double * (4 * nc))(*[float(x) for row in coef for x in row])
         st = (Stats * nc)()
         pnm1 = _ptr(qc_nm1) if qc_nm1 is not None else None
         rc = self.lib.fr_batch_bdf2_step(self.b, _ptr(q), _ptr(qc_n), pnm1, flat,
                                          ctypes.cast(st, _P), _stream(stream))
-        if not (allow_unconverged and rc == -4):
+        self.last_rc = rc
+        if not ((allow_unconverged and rc == -4) or (allow_nonfinite and rc == -3)):
             self._check(rc)
         return list(st)
 

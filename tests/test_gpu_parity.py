@@ -465,3 +465,37 @@ def test_invalid_mesh_rejected(torch):
     from paper_1903_06304_gb300 import fr
     with pytest.raises(fr.FrError):
         fr.Solver(fr.Config(p=3), 1, 4)
+
+
+@pytest.mark.parametrize("w", [inp.NS_VORTEX_64], ids=lambda w: w.name)
+def test_full_size_vjp_sampled(torch, w):
+    """The transposed operator at full size (all of the adjoint kernels' blocks), sampled:
+    w is supported on mutually distant elements e_k (cyclic distance >= 5 in i or j), so the
+    stencils of different e_k do not meet and, for every x, the identity
+    sum over g in stencil(e_k) of (A^T w)_g . x_g = w_e_k . (A x)_e_k holds per pick, with A x
+    from the oracle's complex step."""
+    c, v, q = inp.make_case(w, t=0.13)
+    prob = oracle_problem(c, v, w.nx, w.ny, w.p, w.mach, w.re, w.kappa)
+    S = solver_for(c, v, w.nx, w.ny, w.p, w.mach, w.re, w.kappa)
+    a0_dt = 1.5 / w.dt
+    rng = np.random.default_rng(29)
+    picks = [j * w.nx + i for j in range(2, w.ny, 9) for i in range(4 * (j % 2) + 2, w.nx, 9)]
+    picks = rng.choice(picks, size=min(24, len(picks)), replace=False)
+    wv = np.zeros(q.shape)
+    for e in picks:
+        wv[:, e] = rng.standard_normal(wv[:, e].shape)
+    qd = to_dev(q)
+    out = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+    S.vjp(qd, to_dev(wv), out, 1e-20, a0_dt)
+    ATw = to_host(out)
+    left, right, bottom, top = prob.mesh.neighbours()
+    for trial in range(6):
+        x = rng.standard_normal(q.shape)
+        x[0] *= prob.gas.R * 1e-2
+        Ax = sv.apply_A(prob, q, x, 1e-20, a0_dt)
+        for e in picks:
+            st = {int(e), int(left[e]), int(right[e]), int(bottom[e]), int(top[e])}
+            lhs = sum(float(np.sum(ATw[:, g] * x[:, g])) for g in st)
+            rhs = float(np.sum(wv[:, e] * Ax[:, e]))
+            scale = sum(float(np.sum(np.abs(ATw[:, g] * x[:, g]))) for g in st)
+            assert abs(lhs - rhs) <= 1e-11 * scale, (trial, e, lhs, rhs)
