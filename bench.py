@@ -815,7 +815,8 @@ def kernels_only(args):
     c, v, q = inp.make_case(w, t=0.13 if w.deforming else 0.0)
     T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda:0")
     S = fr.Solver(fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
-                            restart=args.restart, maxit_lin=args.maxit_lin), w.nx, w.ny)
+                            restart=args.restart, maxit_lin=args.maxit_lin,
+                            precond=args.precond, graphs=args.graphs), w.nx, w.ny)
     S.update_mesh(T(c), T(v))
     qd = T(q)
     out = torch.empty_like(qd)

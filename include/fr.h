@@ -113,8 +113,10 @@ typedef struct fr_ctx fr_ctx;
  * solved exactly; on each other level mg_sweeps damped block-Jacobi sweeps (12 x 12
  * blocks, damping mg_omega) before and after the correction (defaults 2 and 0.7).  The
  * coarse operators are rebuilt with the blocks (every `lag` Newton iterations) by
- * coloured products of A with the P1 functions of the elements.  FP64 throughout the
- * coarse levels; B^-1 in the configured block precision.  On a periodic mesh with a very
+ * coloured products of A with the P1 functions of the elements.  mg_prec: storage and
+ * sweep arithmetic of the coarse levels, FR_PREC_FP32 (default) or FR_PREC_FP64 (the
+ * builds and the transfers to and from the solution points are FP64 either way); B^-1 in
+ * the configured block precision.  On a periodic mesh with a very
  * large dtau and no time term (a0_dt = 0) the constant states make the coarsest operator
  * singular: use it for BDF2 steps (a0_dt > 0) or on bounded meshes. */
 #define FR_MAX_RESTART 256
@@ -155,6 +157,7 @@ typedef struct fr_config {
   int precond;
   int mg_sweeps;
   double mg_omega;
+  int mg_prec;
 } fr_config;
 
 /* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).

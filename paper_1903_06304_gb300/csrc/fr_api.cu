@@ -570,6 +570,7 @@ void fr_default_config(fr_config* c) {
   c->precond = FR_PRECOND_BLOCK;
   c->mg_sweeps = 2;
   c->mg_omega = 0.7;
+  c->mg_prec = FR_PREC_FP32;
 }
 
 int fr_create(const fr_config* cfg, fr_ctx** out) {
@@ -585,7 +586,8 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
       (cfg->orthog != FR_ORTHO_CGS2 && cfg->orthog != FR_ORTHO_CGS) ||
       (cfg->krylov_arith != FR_KRYLOV_FP64 && cfg->krylov_arith != FR_KRYLOV_DF64) ||
       (cfg->precond != FR_PRECOND_BLOCK && cfg->precond != FR_PRECOND_TWO_LEVEL) ||
-      cfg->mg_sweeps < 1 || cfg->mg_sweeps > 8 || !(cfg->mg_omega > 0.0 && cfg->mg_omega <= 1.5))
+      cfg->mg_sweeps < 1 || cfg->mg_sweeps > 8 || !(cfg->mg_omega > 0.0 && cfg->mg_omega <= 1.5) ||
+      (cfg->mg_prec != FR_PREC_FP64 && cfg->mg_prec != FR_PREC_FP32))
     return FR_ERR_ARG;
   fr_ctx* c = new fr_ctx();
   c->cfg = *cfg;

@@ -58,21 +58,27 @@ struct BatchWork {
 // 12 P1 coefficients (4 variables x mean, xi slope, eta slope).  Level 0 has one cell per
 // element; level l+1 agglomerates 2 x 2 cells of level l within each case.  A case whose
 // level has at most 4 cells is solved there exactly (dense inverse); its cells have
-// parent -1 and take no part in smoothing or transfers.
+// parent -1.  The coefficient arrays hold the coarse precision (cfg.mg_prec: float or
+// double); mode[c] = 1 marks the cells that this level's multi-block kernels sweep (the
+// rest belong to a case whose remaining levels run in its single-block kernel).
 struct MgLevel {
   int nc = 0;                 // cells (all cases)
+  int nsweep = 0;             // cells with mode 1
   int *nb = nullptr;          // [nc][5] distinct stencil members, slot 0 = self, -1 unused
   int *cell_case = nullptr;   // [nc]
-  double *A = nullptr;        // [nc][5][12][12] operator blocks by stencil slot
-  double *Dinv = nullptr;     // [nc][12][12] inverse diagonal blocks (continuing cells)
-  double *x = nullptr, *y = nullptr, *b = nullptr;   // [nc][12] cycle vectors
+  int *mode = nullptr;        // [nc]
+  void *A = nullptr;          // [nc][5][12][12] operator blocks by stencil slot
+  void *Dinv = nullptr;       // [nc][12][12] inverse diagonal blocks (cells with a parent)
+  void *x = nullptr, *y = nullptr, *b = nullptr;   // [nc][12] cycle vectors
   int *parent = nullptr;      // [nc] cell of level l+1, -1 for a case finishing here
   double *qo = nullptr;       // [nc][4]: s_a f_x, s_b f_y, f_x, f_y of the cell in its parent
   int *children = nullptr;    // [nc of level l+1][4], -1 unused
   int *gslot = nullptr;       // [nc][5]: slot of parent(nb[c][s]) in parent(c)'s stencil
   int nfin = 0;               // cases finishing at this level
   int *fin = nullptr;         // [nfin][2]: first cell, cell count
-  double *Ainv = nullptr;     // [nfin][48][48] dense inverses (row-major, count*12 used)
+  void *Ainv = nullptr;       // [nfin][48][48] dense inverses (row-major, count*12 used)
+  int ntail = 0;              // cases whose single-block kernel starts at this level
+  int *tail = nullptr;        // [ntail] their case indices
 };
 
 // Kernel classes for the optional per-kernel timing (fr_profile) and launch counts.
@@ -165,6 +171,8 @@ struct fr_ctx {
   double *mg_x = nullptr, *mg_y = nullptr;   // fine seeds and products of the build
   double *mg_z0 = nullptr, *mg_t = nullptr;  // fine coarse correction and residual
   int *mg_bad = nullptr;           // singular coarse blocks met by the builds (device)
+  void *mg_views = nullptr;        // device copies of the level views (single-block kernels)
+  void *mg_tc = nullptr;           // [ncases] per-case level ranges of the single-block kernels
   const double* mg_q = nullptr;    // state of the last build (dual-number operator)
   double mg_inv_dtau = 0.0, mg_a0_dt = 0.0;
   // Krylov workspace
@@ -243,6 +251,9 @@ int jvp(fr_ctx* c, const double* q, const double* v, double inv_dtau, double a0_
 int conservative(fr_ctx* c, const double* q, double* qc, cudaStream_t s);
 int block_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s);
 int block_apply(fr_ctx* c, const double* r, double* z, cudaStream_t s);
+// z = z0 + B^-1 (r - t) in one pass (the smoothing step of the two-level preconditioner)
+int block_apply_fused(fr_ctx* c, const double* r, const double* t, const double* z0, double* z,
+                      cudaStream_t s);
 // Two-level preconditioner (fr_mg.cu): topology and workspace of the coarse hierarchy
 // (host-built, synchronous; nothing unless cfg.precond asks for it), its build at q after
 // the element blocks, and the configured preconditioner z = M^-1 r (block Jacobi, or the

@@ -14,14 +14,18 @@
 // the solution points; V is one V-cycle on the Galerkin operators: A_0 = P^T A P from
 // coloured products of A with the P1 functions of the elements, A_{l+1} = Q^T A_l Q with
 // Q the exact map of a 2 x 2 agglomerate's P1 function to its children; damped 12 x 12
-// block-Jacobi sweeps on every level but the last, where each case (<= 4 cells) is solved
-// by its dense inverse.  Everything on the coarse levels is FP64 with fixed summation
-// orders (no atomics), so the preconditioner is a fixed linear map during a GMRES solve.
+// block-Jacobi sweeps on every level but a case's last, which (<= 4 cells) is solved by
+// its dense inverse.  Fixed summation orders, no atomics on data: the preconditioner is a
+// fixed linear map during a GMRES solve (up to the rounding of the coarse arithmetic).
 //
-// Work per application at N elements: the restriction and prolongation read and write one
-// fine vector each; one extra operator product and block apply on the fine level; the
-// coarse levels do (4 nu + 1) passes over 5 x 144 coefficients per cell on level 0 and a
-// quarter of that per further level.
+// Layout for GB300: the coarse levels are stored and swept in the configured coarse
+// precision (FP32 by default: a coarse sweep is 72 multiply-adds per coefficient, which
+// the FP64 pipe -- 2 FMA per clock per SM -- would make the largest cost of an iteration;
+// the build arithmetic stays FP64).  Levels with more than TAIL cells of a case run as one
+// launch per sweep over all SMs (16 cells per block, a cell's residual staged in shared
+// memory for its 12 x 12 inverse); the remaining small levels of each case, with the dense
+// solve, run in one block per case, the phases separated by block barriers, so that the
+// latency of a launch is paid once instead of once per phase.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -35,11 +39,50 @@ constexpr int SL = 5;           // stencil slots per cell (self + 4 neighbours)
 constexpr int BLK = NB * NB;    // entries of one 12 x 12 block
 constexpr int MAXFIN = 4;       // cells of a case solved exactly
 constexpr int DN = MAXFIN * NB; // leading dimension of the dense inverses
-constexpr int CPB = 16;         // cells per block of the row-parallel kernels
+constexpr int CPB = 16;         // cells per block of the multi-block kernels
+constexpr int TAIL = 64;        // levels of a case with at most this many cells: one block
+constexpr int TAIL_THREADS = 256;
 
 // Reference-coordinate basis value of mode m (1, xi, eta) at point (i, j).
 __device__ __forceinline__ double phi(const fr::Basis& B, int m, int i, int j) {
   return m == 0 ? 1.0 : (m == 1 ? B.xs[i] : B.xs[j]);
+}
+
+// Q_m,a: coefficient of fine mode a in the child for coarse mode m (qo = s_a f_x, s_b f_y,
+// f_x, f_y): c0 + c1 X + c2 Y = (c0 + c1 s_a f_x + c2 s_b f_y) + c1 f_x xi + c2 f_y eta.
+__device__ __forceinline__ double qmap(const double* qo, int a, int m) {
+  if (a == 0) return m == 0 ? 1.0 : (m == 1 ? qo[0] : qo[1]);
+  if (a == 1) return m == 1 ? qo[2] : 0.0;
+  return m == 2 ? qo[3] : 0.0;
+}
+
+// Device view of one level; the coefficient arrays hold S (float or double).
+template <class S>
+struct Lv {
+  int nc;
+  const int* nb;        // [nc][5]
+  const int* mode;      // [nc]: 1 = swept by the multi-block kernels of this level
+  const int* parent;    // [nc]
+  const int* children;  // [nc of the next level][4]
+  const double* qo;     // [nc][4]
+  const S* A;           // [nc][5][12][12]
+  const S* Dinv;        // [nc][12][12]
+  S *x, *y, *b;         // [nc][12]
+  const S* Ainv;        // [nfin][48][48]
+};
+
+template <class S>
+__device__ __forceinline__ S row_product(const Lv<S>& L, int c, int r, const S* x) {
+  S acc = S(0);
+  for (int s = 0; s < SL; ++s) {
+    const int f = L.nb[c * SL + s];
+    if (f < 0) continue;
+    const S* a = L.A + (((size_t)c * SL + s) * NB + r) * NB;
+    const S* xf = x + (size_t)f * NB;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc = fma(a[k], xf[k], acc);
+  }
+  return acc;
 }
 
 // ---------------------------------------------------------------- fine <-> level 0
@@ -59,9 +102,9 @@ __global__ void k_p1_seed(fr::Mesh mesh, fr::Basis B, const int* __restrict__ co
 
 // Column k of the level-0 blocks: P^T y on every element whose stencil holds a member of
 // colour col (the seed's response on e comes from that member alone).
-template <int N>
+template <int N, class S>
 __global__ void k_p1_gather(fr::Mesh mesh, fr::Basis B, const int* __restrict__ colslot, int ncol,
-                            int col, int k, const double* __restrict__ y, double* __restrict__ A) {
+                            int col, int k, const double* __restrict__ y, S* __restrict__ A) {
   constexpr int NP = N * N;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)mesh.ne * NB) return;
@@ -72,13 +115,13 @@ __global__ void k_p1_gather(fr::Mesh mesh, fr::Basis B, const int* __restrict__ 
   const int v = r / 3, m = r % 3;
   double acc = 0.0;
   for (int pt = 0; pt < NP; ++pt) acc = fma(phi(B, m, pt % N, pt / N), y[v * qs + base + pt], acc);
-  A[(((size_t)e * SL + s) * NB + r) * NB + k] = acc;
+  A[(((size_t)e * SL + s) * NB + r) * NB + k] = (S)acc;
 }
 
-// b0 = P^T r (per element: 12 sums over its points)
-template <int N>
+// b0 = P^T r (per element: 12 sums over its points, FP64, stored in S)
+template <int N, class S>
 __global__ void k_p1_restrict(fr::Mesh mesh, fr::Basis B, const double* __restrict__ r,
-                              double* __restrict__ b0) {
+                              S* __restrict__ b0) {
   constexpr int NP = N * N;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)mesh.ne * NB) return;
@@ -87,12 +130,12 @@ __global__ void k_p1_restrict(fr::Mesh mesh, fr::Basis B, const double* __restri
   const int v = row / 3, m = row % 3;
   double acc = 0.0;
   for (int pt = 0; pt < NP; ++pt) acc = fma(phi(B, m, pt % N, pt / N), r[v * qs + base + pt], acc);
-  b0[t] = acc;
+  b0[t] = (S)acc;
 }
 
-// z = P x0
-template <int N>
-__global__ void k_p1_prolong(fr::Mesh mesh, fr::Basis B, const double* __restrict__ x0,
+// z = P x0 (FP64 out)
+template <int N, class S>
+__global__ void k_p1_prolong(fr::Mesh mesh, fr::Basis B, const S* __restrict__ x0,
                              double* __restrict__ z) {
   constexpr int NP = N * N;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -100,128 +143,177 @@ __global__ void k_p1_prolong(fr::Mesh mesh, fr::Basis B, const double* __restric
   const int e = (int)(t / NP), pt = (int)(t % NP);
   const size_t base = mesh.qbase(e, NP), qs = mesh.qstride(e);
   const double xi = B.xs[pt % N], eta = B.xs[pt / N];
-  const double* c = x0 + (size_t)e * NB;
+  const S* c = x0 + (size_t)e * NB;
 #pragma unroll
-  for (int v = 0; v < 4; ++v) z[v * qs + base + pt] = fma(c[3 * v + 2], eta, fma(c[3 * v + 1], xi, c[3 * v]));
+  for (int v = 0; v < 4; ++v)
+    z[v * qs + base + pt] = fma((double)c[3 * v + 2], eta, fma((double)c[3 * v + 1], xi, (double)c[3 * v]));
 }
 
-// ---------------------------------------------------------------- V-cycle kernels
-struct LevelView {
-  int nc;
-  const int* nb;
-  const int* parent;
-  const double* A;
-  const double* Dinv;
-};
-
-// Row r of (A x)_c over the cell's stencil.
-__device__ __forceinline__ double row_product(const LevelView& L, int c, int r, const double* x) {
-  double acc = 0.0;
-  for (int s = 0; s < SL; ++s) {
-    const int f = L.nb[c * SL + s];
-    if (f < 0) continue;
-    const double* a = L.A + (((size_t)c * SL + s) * NB + r) * NB;
-    const double* xf = x + (size_t)f * NB;
-#pragma unroll
-    for (int k = 0; k < NB; ++k) acc = fma(a[k], xf[k], acc);
-  }
-  return acc;
-}
-
-// One damped block-Jacobi sweep on the continuing cells: xo = xi + omega D^-1 (b - A xi)
-// (first sweep: xi = 0, so xo = omega D^-1 b).  Cells of cases solved on this level copy
-// their value through.  CPB cells of 12 rows per block.
-// (xi and xo may be the same buffer on the first sweep: each thread then reads and writes
-// only its own entry.)
-__global__ void __launch_bounds__(CPB * NB) k_mg_smooth(LevelView L, const double* __restrict__ b,
-                                                       const double* xi, double* xo, double omega,
-                                                       int first) {
-  __shared__ double res[CPB][NB];
+// ---------------------------------------------------------------- multi-block levels
+// One damped block-Jacobi sweep on the cells this level sweeps (mode 1):
+// xo = xi + omega D^-1 (b - A xi); the first sweep starts from xi = 0 (xo = omega D^-1 b).
+// The other cells copy their value through (xi may equal xo on the first sweep: each
+// thread then reads and writes only its own entry).
+template <class S>
+__global__ void __launch_bounds__(CPB * NB) k_mg_smooth(Lv<S> L, const S* xi, S* xo, S omega, int first) {
+  __shared__ S res[CPB][NB];
   const int lc = threadIdx.x / NB, r = threadIdx.x % NB;
   const int c = blockIdx.x * CPB + lc;
   const bool in = c < L.nc;
-  const bool cont = in && L.parent[c] >= 0;
-  if (cont) res[lc][r] = b[(size_t)c * NB + r] - (first ? 0.0 : row_product(L, c, r, xi));
+  const bool sw = in && L.mode[c] == 1;
+  if (sw) res[lc][r] = L.b[(size_t)c * NB + r] - (first ? S(0) : row_product(L, c, r, xi));
   __syncthreads();
   if (!in) return;
-  if (!cont) {
+  if (!sw) {
     xo[(size_t)c * NB + r] = xi[(size_t)c * NB + r];
     return;
   }
-  const double* d = L.Dinv + ((size_t)c * NB + r) * NB;
-  double acc = 0.0;
+  const S* d = L.Dinv + ((size_t)c * NB + r) * NB;
+  S acc = S(0);
 #pragma unroll
   for (int k = 0; k < NB; ++k) acc = fma(d[k], res[lc][k], acc);
-  xo[(size_t)c * NB + r] = (first ? 0.0 : xi[(size_t)c * NB + r]) + omega * acc;
+  xo[(size_t)c * NB + r] = (first ? S(0) : xi[(size_t)c * NB + r]) + omega * acc;
 }
 
-// y = b - A x on the continuing cells
-__global__ void k_mg_residual(LevelView L, const double* __restrict__ b, const double* __restrict__ x,
-                              double* __restrict__ y) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)L.nc * NB) return;
-  const int c = (int)(t / NB), r = (int)(t % NB);
-  if (L.parent[c] < 0) return;
-  y[t] = b[t] - row_product(L, c, r, x);
-}
-
-// Q_m,a: coefficient of fine mode a in the child for coarse mode m (qo = s_a f_x, s_b f_y,
-// f_x, f_y): c0 + c1 X + c2 Y = (c0 + c1 s_a f_x + c2 s_b f_y) + c1 f_x xi + c2 f_y eta.
-__device__ __forceinline__ double qmap(const double* qo, int a, int m) {
-  if (a == 0) return m == 0 ? 1.0 : (m == 1 ? qo[0] : qo[1]);
-  if (a == 1) return m == 1 ? qo[2] : 0.0;
-  return m == 2 ? qo[3] : 0.0;
-}
-
-// b_next = Q^T y over each coarse cell's children (fixed child order)
-__global__ void k_mg_restrict(int nc_next, const int* __restrict__ children, const double* __restrict__ qo,
-                              const double* __restrict__ y, double* __restrict__ bn) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)nc_next * NB) return;
-  const int I = (int)(t / NB), r = (int)(t % NB);
+// b_next = Q^T (b - A x) over each coarse cell's children (fixed child order), for the
+// coarse cells whose children this level sweeps: 48 threads per coarse cell compute the
+// children's residual rows, 12 of them then sum the transposed transfer.
+template <class S>
+__global__ void __launch_bounds__(4 * 4 * NB) k_mg_resid_restrict(Lv<S> L, const S* __restrict__ x,
+                                                                 int nc_next, S* __restrict__ bn) {
+  constexpr int CELLS = 4;   // coarse cells per block
+  __shared__ S res[CELLS][4][NB];
+  const int lc = threadIdx.x / (4 * NB), q = (threadIdx.x / NB) % 4, r = threadIdx.x % NB;
+  const int I = blockIdx.x * CELLS + lc;
+  int ch = -1;
+  if (I < nc_next) ch = L.children[I * 4 + q];
+  const bool act = ch >= 0 && L.mode[ch] == 1;
+  res[lc][q][r] = act ? L.b[(size_t)ch * NB + r] - row_product(L, ch, r, x) : S(0);
+  __syncthreads();
+  if (I >= nc_next || q != 0) return;
+  // only coarse cells whose children are swept here are written (the others belong to a
+  // case handled by its own single-block kernel)
+  const int c0 = L.children[I * 4];
+  if (c0 < 0 || L.mode[c0] != 1) return;
   const int v = r / 3, m = r % 3;
   double acc = 0.0;
-  for (int q = 0; q < 4; ++q) {
-    const int ch = children[I * 4 + q];
-    if (ch < 0) continue;
-    const double* o = qo + (size_t)ch * 4;
-    const double* yc = y + (size_t)ch * NB + 3 * v;
-    for (int a = 0; a < 3; ++a) acc = fma(qmap(o, a, m), yc[a], acc);
+  for (int qq = 0; qq < 4; ++qq) {
+    const int c = L.children[I * 4 + qq];
+    if (c < 0) continue;
+    const double* o = L.qo + (size_t)c * 4;
+    for (int a = 0; a < 3; ++a) acc = fma(qmap(o, a, m), (double)res[lc][qq][3 * v + a], acc);
   }
-  bn[t] = acc;
+  bn[(size_t)I * NB + r] = (S)acc;
 }
 
-// x += Q x_next on the continuing cells
-__global__ void k_mg_prolong(LevelView L, const double* __restrict__ qo, const double* __restrict__ xn,
-                             double* __restrict__ x) {
+// x += Q x_next on the swept cells
+template <class S>
+__global__ void k_mg_prolong(Lv<S> L, const S* __restrict__ xn, S* __restrict__ x) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)L.nc * NB) return;
   const int c = (int)(t / NB), r = (int)(t % NB);
+  if (L.mode[c] != 1) return;
   const int P = L.parent[c];
-  if (P < 0) return;
   const int v = r / 3, a = r % 3;
-  const double* o = qo + (size_t)c * 4;
-  const double* X = xn + (size_t)P * NB + 3 * v;
+  const double* o = L.qo + (size_t)c * 4;
+  const S* X = xn + (size_t)P * NB + 3 * v;
   double acc = 0.0;
-  for (int m = 0; m < 3; ++m) acc = fma(qmap(o, a, m), X[m], acc);
-  x[t] += acc;
+  for (int m = 0; m < 3; ++m) acc = fma(qmap(o, a, m), (double)X[m], acc);
+  x[t] += (S)acc;
 }
 
-// Exact solve of the cases that finish on this level: x = Ainv b per case.
-__global__ void k_mg_dense(const int* __restrict__ fin, const double* __restrict__ Ainv,
-                           const double* __restrict__ b, double* __restrict__ x) {
-  const int f = blockIdx.x, c0 = fin[2 * f], m = fin[2 * f + 1] * NB;
-  const double* Ai = Ainv + (size_t)f * DN * DN;
-  for (int r = threadIdx.x; r < m; r += blockDim.x) {
-    double acc = 0.0;
-    for (int k = 0; k < m; ++k) acc = fma(Ai[r * DN + k], b[(size_t)c0 * NB + k], acc);
-    x[(size_t)c0 * NB + r] = acc;
+// ---------------------------------------------------------------- single-block tail
+// The levels of one case from `lev0` on (each at most TAIL cells) and its exact solve, in
+// one block: down (pre-smoothing, residual, restriction), the dense solve on the case's
+// last level, up (prolongation, post-smoothing).  A sweep is two phases: y = b - A x for
+// every cell, then x += omega D^-1 y in place (a phase reads only what the previous one
+// wrote).
+struct TailCase {
+  int lev0, nlev;             // first level of the tail, levels of the case in total
+  int off[16], cnt[16];       // the case's cells on each level
+  int fin;                    // index of the case's dense inverse on its last level
+};
+
+template <class S>
+__device__ void tail_sweep(const Lv<S>& L, int off, int cnt, S omega, bool first) {
+  for (int t = threadIdx.x; t < cnt * NB; t += blockDim.x) {
+    const int c = off + t / NB, r = t % NB;
+    L.y[(size_t)c * NB + r] = L.b[(size_t)c * NB + r] - (first ? S(0) : row_product(L, c, r, L.x));
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < cnt * NB; t += blockDim.x) {
+    const int c = off + t / NB, r = t % NB;
+    const S* d = L.Dinv + ((size_t)c * NB + r) * NB;
+    const S* yc = L.y + (size_t)c * NB;
+    S acc = S(0);
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc = fma(d[k], yc[k], acc);
+    L.x[(size_t)c * NB + r] = (first ? S(0) : L.x[(size_t)c * NB + r]) + omega * acc;
+  }
+  __syncthreads();
+}
+
+template <class S>
+__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(const Lv<S>* __restrict__ lev,
+                                                         const TailCase* __restrict__ tc,
+                                                         const int* __restrict__ cases, int nu,
+                                                         S omega) {
+  const TailCase T = tc[cases[blockIdx.x]];
+  const int last = T.nlev - 1;
+  for (int l = T.lev0; l < last; ++l) {
+    const Lv<S> L = lev[l];
+    const int off = T.off[l], cnt = T.cnt[l];
+    for (int it = 0; it < nu; ++it) tail_sweep(L, off, cnt, omega, it == 0);
+    for (int t = threadIdx.x; t < cnt * NB; t += blockDim.x) {
+      const int c = off + t / NB, r = t % NB;
+      L.y[(size_t)c * NB + r] = L.b[(size_t)c * NB + r] - row_product(L, c, r, L.x);
+    }
+    __syncthreads();
+    const Lv<S> Nn = lev[l + 1];
+    for (int t = threadIdx.x; t < T.cnt[l + 1] * NB; t += blockDim.x) {
+      const int I = T.off[l + 1] + t / NB, r = t % NB, v = r / 3, m = r % 3;
+      double acc = 0.0;
+      for (int q = 0; q < 4; ++q) {
+        const int c = L.children[I * 4 + q];
+        if (c < 0) continue;
+        const double* o = L.qo + (size_t)c * 4;
+        for (int a = 0; a < 3; ++a) acc = fma(qmap(o, a, m), (double)L.y[(size_t)c * NB + 3 * v + a], acc);
+      }
+      Nn.b[(size_t)I * NB + r] = (S)acc;
+    }
+    __syncthreads();
+  }
+  {
+    const Lv<S> L = lev[last];
+    const int off = T.off[last], m = T.cnt[last] * NB;
+    const S* Ai = L.Ainv + (size_t)T.fin * DN * DN;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+      S acc = S(0);
+      for (int k = 0; k < m; ++k) acc = fma(Ai[r * DN + k], L.b[(size_t)off * NB + k], acc);
+      L.x[(size_t)off * NB + r] = acc;
+    }
+    __syncthreads();
+  }
+  for (int l = last - 1; l >= T.lev0; --l) {
+    const Lv<S> L = lev[l];
+    const Lv<S> Nn = lev[l + 1];
+    const int off = T.off[l], cnt = T.cnt[l];
+    for (int t = threadIdx.x; t < cnt * NB; t += blockDim.x) {
+      const int c = off + t / NB, r = t % NB, v = r / 3, a = r % 3;
+      const double* o = L.qo + (size_t)c * 4;
+      const S* X = Nn.x + (size_t)L.parent[c] * NB + 3 * v;
+      double acc = 0.0;
+      for (int m = 0; m < 3; ++m) acc = fma(qmap(o, a, m), (double)X[m], acc);
+      L.x[(size_t)c * NB + r] += (S)acc;
+    }
+    __syncthreads();
+    for (int it = 0; it < nu; ++it) tail_sweep(L, off, cnt, omega, false);
   }
 }
 
 // ---------------------------------------------------------------- build kernels
 // Inverse of one 12 x 12 block by Gauss-Jordan with partial pivoting on [A | I] (one
-// thread); returns false on a zero pivot.
+// thread, FP64); returns false on a zero pivot.
 __device__ bool gj_inverse12(double* a, double* inv) {
   for (int i = 0; i < BLK; ++i) inv[i] = (i / NB == i % NB) ? 1.0 : 0.0;
   for (int k = 0; k < NB; ++k) {
@@ -250,23 +342,25 @@ __device__ bool gj_inverse12(double* a, double* inv) {
   return true;
 }
 
-// Dinv = inverse of the diagonal (slot 0) block of every continuing cell; *bad counts
-// singular blocks.
-__global__ void k_mg_invert_diag(LevelView L, double* __restrict__ Dinv, int* __restrict__ bad) {
+// Dinv = inverse of the diagonal (slot 0) block of every cell that is smoothed (parent
+// >= 0); *bad counts singular blocks.
+template <class S>
+__global__ void k_mg_invert_diag(Lv<S> L, S* __restrict__ Dinv, int* __restrict__ bad) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.nc || L.parent[c] < 0) return;
   double a[BLK], inv[BLK];
-  const double* src = L.A + (size_t)c * SL * BLK;
-  for (int i = 0; i < BLK; ++i) a[i] = src[i];
+  const S* src = L.A + (size_t)c * SL * BLK;
+  for (int i = 0; i < BLK; ++i) a[i] = (double)src[i];
   if (!gj_inverse12(a, inv)) atomicAdd(bad, 1);
-  double* dst = Dinv + (size_t)c * BLK;
-  for (int i = 0; i < BLK; ++i) dst[i] = inv[i];
+  S* dst = Dinv + (size_t)c * BLK;
+  for (int i = 0; i < BLK; ++i) dst[i] = (S)inv[i];
 }
 
 // Dense inverse of each finishing case: its cells' blocks assembled into one (12 m)^2
-// matrix in shared memory (m <= 4) and inverted by Gauss-Jordan with partial pivoting,
-// the block's threads sharing each elimination step.
-__global__ void k_mg_coarsest(LevelView L, const int* __restrict__ fin, double* __restrict__ Ainv,
+// matrix in shared memory (m <= 4) and inverted by Gauss-Jordan with partial pivoting in
+// FP64, the block's threads sharing each elimination step.
+template <class S>
+__global__ void k_mg_coarsest(Lv<S> L, const int* __restrict__ fin, S* __restrict__ Ainv,
                               int* __restrict__ bad) {
   __shared__ double a[DN * DN];
   __shared__ double inv[DN * DN];
@@ -284,7 +378,7 @@ __global__ void k_mg_coarsest(LevelView L, const int* __restrict__ fin, double* 
     const int ci = c0 + i, fj = L.nb[ci * SL + s];
     if (fj < 0) continue;
     const int j = fj - c0, r = rk / NB, k = rk % NB;
-    a[(i * NB + r) * DN + j * NB + k] = L.A[((size_t)ci * SL + s) * BLK + rk];
+    a[(i * NB + r) * DN + j * NB + k] = (double)L.A[((size_t)ci * SL + s) * BLK + rk];
   }
   __syncthreads();
   for (int k = 0; k < m; ++k) {
@@ -323,46 +417,45 @@ __global__ void k_mg_coarsest(LevelView L, const int* __restrict__ fin, double* 
     }
     __syncthreads();
   }
-  double* dst = Ainv + (size_t)f * DN * DN;
-  for (int t = threadIdx.x; t < DN * DN; t += blockDim.x) dst[t] = inv[t];
+  S* dst = Ainv + (size_t)f * DN * DN;
+  for (int t = threadIdx.x; t < DN * DN; t += blockDim.x) dst[t] = (S)inv[t];
 }
 
 // A_{l+1} = Q^T A_l Q: entry (r, k) of coarse block (I, S) sums, over the children c of I
-// and their slots s whose member's parent is slot S of I, Q_c^T A_l[c][s] Q_f.
-__global__ void k_mg_galerkin(LevelView L, const double* __restrict__ qo, const int* __restrict__ gslot,
-                              int nc_next, const int* __restrict__ nb_next,
-                              const int* __restrict__ children, double* __restrict__ An) {
+// and their slots s whose member's parent is slot S of I, Q_c^T A_l[c][s] Q_f (FP64).
+template <class S>
+__global__ void k_mg_galerkin(Lv<S> L, const int* __restrict__ gslot, int nc_next,
+                              const int* __restrict__ nb_next, S* __restrict__ An) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)nc_next * SL * BLK) return;
-  const int I = (int)(t / (SL * BLK)), S = (int)((t / BLK) % SL), rk = (int)(t % BLK);
-  if (nb_next[I * SL + S] < 0) { An[t] = 0.0; return; }
+  const int I = (int)(t / (SL * BLK)), Sl = (int)((t / BLK) % SL), rk = (int)(t % BLK);
+  if (nb_next[I * SL + Sl] < 0) { An[t] = S(0); return; }
   const int r = rk / NB, k = rk % NB;
   const int v = r / 3, m = r % 3, w = k / 3, mk = k % 3;
   double acc = 0.0;
   for (int q = 0; q < 4; ++q) {
-    const int c = children[I * 4 + q];
+    const int c = L.children[I * 4 + q];
     if (c < 0) continue;
-    const double* oc = qo + (size_t)c * 4;
+    const double* oc = L.qo + (size_t)c * 4;
     for (int s = 0; s < SL; ++s) {
-      if (gslot[c * SL + s] != S) continue;
+      if (gslot[c * SL + s] != Sl) continue;
       const int f = L.nb[c * SL + s];
-      const double* of = qo + (size_t)f * 4;
-      const double* a = L.A + ((size_t)c * SL + s) * BLK;
+      const double* of = L.qo + (size_t)f * 4;
+      const S* a = L.A + ((size_t)c * SL + s) * BLK;
       for (int ap = 0; ap < 3; ++ap) {
         const double qa = qmap(oc, ap, m);
         if (qa == 0.0) continue;
         double inner = 0.0;
-        for (int bp = 0; bp < 3; ++bp) inner = fma(a[(3 * v + ap) * NB + 3 * w + bp], qmap(of, bp, mk), inner);
+        for (int bp = 0; bp < 3; ++bp)
+          inner = fma((double)a[(3 * v + ap) * NB + 3 * w + bp], qmap(of, bp, mk), inner);
         acc = fma(qa, inner, acc);
       }
     }
   }
-  An[t] = acc;
+  An[t] = (S)acc;
 }
 
 unsigned blocks_for(long long n, int th) { return (unsigned)((n + th - 1) / th); }
-
-LevelView view(const MgLevel& l) { return LevelView{l.nc, l.nb, l.parent, l.A, l.Dinv}; }
 
 template <class T> int dalloc(fr_ctx* c, T** p, size_t count) {
   if (*p) { cudaFree(*p); *p = nullptr; }
@@ -381,6 +474,24 @@ int op_apply(fr_ctx* c, const double* q, const double* x, double inv_dtau, doubl
              cudaStream_t s) {
   if (c->cfg.jvp_mode == FR_JVP_LINEARIZED) return frk::apply_linear(c, x, out, false, s);
   return frk::jvp(c, q, x, inv_dtau, a0_dt, out, s);
+}
+
+template <class S>
+Lv<S> view(const MgLevel& l) {
+  Lv<S> v;
+  v.nc = l.nc;
+  v.nb = l.nb;
+  v.mode = l.mode;
+  v.parent = l.parent;
+  v.children = l.children;
+  v.qo = l.qo;
+  v.A = (const S*)l.A;
+  v.Dinv = (const S*)l.Dinv;
+  v.x = (S*)l.x;
+  v.y = (S*)l.y;
+  v.b = (S*)l.b;
+  v.Ainv = (const S*)l.Ainv;
+  return v;
 }
 
 // Cells of one level of one case: an nx x ny grid (periodic in xi, in eta unless bounded).
@@ -403,7 +514,7 @@ void stencil_of(const CaseGrid& g, bool bounded, int i, int j, int* out) {
   for (int k = n; k < SL; ++k) out[k] = -1;
 }
 
-template <int N>
+template <int N, class S>
 int build_level0(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s) {
   constexpr int NP = N * N;
   MgLevel& L0 = c->mg[0];
@@ -420,8 +531,8 @@ int build_level0(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cuda
       FR_TRY(op_apply(c, q, c->mg_x, inv_dtau, a0_dt, c->mg_y, s));
       {
         FR_PROF_BEGIN(c, s);
-        k_p1_gather<N><<<blocks_for((long long)c->ne * NB, 256), 256, 0, s>>>(
-            c->mesh, c->basis, c->mg_colslot + (size_t)c->ne, c->mg_ncol, col, k, c->mg_y, L0.A);
+        k_p1_gather<N, S><<<blocks_for((long long)c->ne * NB, 256), 256, 0, s>>>(
+            c->mesh, c->basis, c->mg_colslot + (size_t)c->ne, c->mg_ncol, col, k, c->mg_y, (S*)L0.A);
         FR_PROF_END(c, s, KK_COARSE);
         FR_LAUNCH_CHECK(c);
       }
@@ -431,72 +542,132 @@ int build_level0(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cuda
   return FR_OK;
 }
 
-template <int N>
-int restrict_prolong(fr_ctx* c, const double* r, double* z0, cudaStream_t s, bool down) {
-  constexpr int NP = N * N;
-  FR_PROF_BEGIN(c, s);
-  if (down)
-    k_p1_restrict<N><<<blocks_for((long long)c->ne * NB, 256), 256, 0, s>>>(c->mesh, c->basis, r, c->mg[0].b);
-  else
-    k_p1_prolong<N><<<blocks_for((long long)c->ne * NP, 256), 256, 0, s>>>(c->mesh, c->basis, c->mg[0].x, z0);
-  FR_PROF_END(c, s, KK_COARSE);
-  FR_LAUNCH_CHECK(c);
-  FR_ACCOUNT(c, KK_COARSE, 2.0 * NB * c->ne * NP / (down ? 1.0 : 4.0), 8.0 * (4.0 * c->ne * NP + NB * c->ne));
+template <class S>
+int build_levels(fr_ctx* c, cudaStream_t s) {
+  for (size_t l = 0; l < c->mg.size(); ++l) {
+    MgLevel& L = c->mg[l];
+    const Lv<S> V = view<S>(L);
+    FR_PROF_BEGIN(c, s);
+    k_mg_invert_diag<S><<<blocks_for(L.nc, 64), 64, 0, s>>>(V, (S*)L.Dinv, c->mg_bad);
+    if (L.nfin > 0) k_mg_coarsest<S><<<L.nfin, 128, 0, s>>>(V, L.fin, (S*)L.Ainv, c->mg_bad);
+    if (l + 1 < c->mg.size()) {
+      const MgLevel& Nx = c->mg[l + 1];
+      k_mg_galerkin<S><<<blocks_for((long long)Nx.nc * SL * BLK, 256), 256, 0, s>>>(
+          V, L.gslot, Nx.nc, Nx.nb, (S*)Nx.A);
+    }
+    FR_PROF_END(c, s, KK_COARSE);
+    FR_LAUNCH_CHECK(c);
+    FR_ACCOUNT(c, KK_COARSE, 2.0 * NB * NB * NB * L.nc, 0.0);
+  }
   return FR_OK;
 }
 
-// One V-cycle from level l: b_l given, the result left in x_l.
+template <int N, class S>
+int fine_transfer(fr_ctx* c, const double* r, double* z0, cudaStream_t s, bool down) {
+  constexpr int NP = N * N;
+  FR_PROF_BEGIN(c, s);
+  if (down)
+    k_p1_restrict<N, S><<<blocks_for((long long)c->ne * NB, 256), 256, 0, s>>>(c->mesh, c->basis, r, (S*)c->mg[0].b);
+  else
+    k_p1_prolong<N, S><<<blocks_for((long long)c->ne * NP, 256), 256, 0, s>>>(c->mesh, c->basis, (const S*)c->mg[0].x, z0);
+  FR_PROF_END(c, s, KK_COARSE);
+  FR_LAUNCH_CHECK(c);
+  FR_ACCOUNT(c, KK_COARSE, 2.0 * NB * c->ne * NP / (down ? 1.0 : 4.0),
+             8.0 * 4.0 * c->ne * NP + (double)sizeof(S) * NB * c->ne);
+  return FR_OK;
+}
+
+template <class S>
+int launch_tail(fr_ctx* c, const MgLevel& L, cudaStream_t s) {
+  FR_PROF_BEGIN(c, s);
+  k_mg_tail<S><<<L.ntail, TAIL_THREADS, 0, s>>>((const Lv<S>*)c->mg_views, (const TailCase*)c->mg_tc,
+                                                 L.tail, c->cfg.mg_sweeps, (S)c->cfg.mg_omega);
+  FR_PROF_END(c, s, KK_COARSE);
+  FR_LAUNCH_CHECK(c);
+  return FR_OK;
+}
+
+// One V-cycle from level l over the cells the multi-block kernels sweep there (b_l given,
+// the result in x_l); the cases whose single-block tail starts at level l+1 run theirs
+// between the restriction and the prolongation.
+template <class S>
 int vcycle(fr_ctx* c, size_t l, cudaStream_t s) {
   MgLevel& L = c->mg[l];
-  const LevelView V = view(L);
-  const int nu = std::max(1, c->cfg.mg_sweeps);
-  const double om = c->cfg.mg_omega;
-  const double per_pass = 2.0 * SL * BLK * L.nc;   // upper bound: five full blocks per row
-  if (L.nfin > 0) {
-    FR_PROF_BEGIN(c, s);
-    k_mg_dense<<<L.nfin, 64, 0, s>>>(L.fin, L.Ainv, L.b, L.x);
-    FR_PROF_END(c, s, KK_COARSE);
-    FR_LAUNCH_CHECK(c);
-  }
-  if (l + 1 >= c->mg.size()) return FR_OK;
+  if (l == 0 && L.ntail > 0) FR_TRY(launch_tail<S>(c, L, s));   // cases that are small throughout
+  if (L.nsweep == 0) return FR_OK;
+  const Lv<S> V = view<S>(L);
   MgLevel& Nx = c->mg[l + 1];
+  const int nu = c->cfg.mg_sweeps;
+  const S om = (S)c->cfg.mg_omega;
   const unsigned gs = blocks_for(L.nc, CPB);
-  // pre-smoothing: x (from zero), then ping-pong between x and y, ending in x
-  double* cur = L.x;
-  double* oth = L.y;
+  S* cur = (S*)L.x;
+  S* oth = (S*)L.y;
   for (int it = 0; it < nu; ++it) {
     FR_PROF_BEGIN(c, s);
-    k_mg_smooth<<<gs, CPB * NB, 0, s>>>(V, L.b, it == 0 ? L.x : cur, it == 0 ? L.x : oth, om, it == 0);
+    k_mg_smooth<S><<<gs, CPB * NB, 0, s>>>(V, cur, it == 0 ? cur : oth, om, it == 0);
     FR_PROF_END(c, s, KK_COARSE);
     FR_LAUNCH_CHECK(c);
     if (it > 0) std::swap(cur, oth);
   }
   {
     FR_PROF_BEGIN(c, s);
-    k_mg_residual<<<blocks_for((long long)L.nc * NB, 256), 256, 0, s>>>(V, L.b, cur, oth);
-    k_mg_restrict<<<blocks_for((long long)Nx.nc * NB, 256), 256, 0, s>>>(Nx.nc, L.children, L.qo, oth, Nx.b);
+    k_mg_resid_restrict<S><<<blocks_for(Nx.nc, 4), 4 * 4 * NB, 0, s>>>(V, cur, Nx.nc, (S*)Nx.b);
     FR_PROF_END(c, s, KK_COARSE);
     FR_LAUNCH_CHECK(c);
   }
-  FR_TRY(vcycle(c, l + 1, s));
+  if (Nx.ntail > 0) FR_TRY(launch_tail<S>(c, Nx, s));
+  FR_TRY(vcycle<S>(c, l + 1, s));
   {
     FR_PROF_BEGIN(c, s);
-    k_mg_prolong<<<blocks_for((long long)L.nc * NB, 256), 256, 0, s>>>(V, L.qo, Nx.x, cur);
+    k_mg_prolong<S><<<blocks_for((long long)L.nc * NB, 256), 256, 0, s>>>(V, (const S*)Nx.x, cur);
     FR_PROF_END(c, s, KK_COARSE);
     FR_LAUNCH_CHECK(c);
   }
   for (int it = 0; it < nu; ++it) {
     FR_PROF_BEGIN(c, s);
-    k_mg_smooth<<<gs, CPB * NB, 0, s>>>(V, L.b, cur, oth, om, 0);
+    k_mg_smooth<S><<<gs, CPB * NB, 0, s>>>(V, cur, oth, om, 0);
     FR_PROF_END(c, s, KK_COARSE);
     FR_LAUNCH_CHECK(c);
     std::swap(cur, oth);
   }
-  if (cur != L.x) {
-    FR_CUDA_CHECK(c, cudaMemcpyAsync(L.x, cur, (size_t)L.nc * NB * sizeof(double),
-                                     cudaMemcpyDeviceToDevice, s));
+  if (cur != (S*)L.x)
+    FR_CUDA_CHECK(c, cudaMemcpyAsync(L.x, cur, (size_t)L.nc * NB * sizeof(S), cudaMemcpyDeviceToDevice, s));
+  const double rows = (double)L.nsweep * NB;
+  FR_ACCOUNT(c, KK_COARSE, rows * 2.0 * (SL * NB + NB) * (2.0 * nu + 1.0),
+             (double)sizeof(S) * L.nsweep * (SL * BLK + BLK) * (2.0 * nu + 1.0));
+  return FR_OK;
+}
+
+template <class S>
+int apply_t(fr_ctx* c, const double* q, const double* r, double* z, double inv_dtau, double a0_dt,
+            cudaStream_t s) {
+  int rc;
+  switch (c->n) {
+    case 2: rc = fine_transfer<2, S>(c, r, nullptr, s, true); break;
+    case 3: rc = fine_transfer<3, S>(c, r, nullptr, s, true); break;
+    case 4: rc = fine_transfer<4, S>(c, r, nullptr, s, true); break;
+    case 5: rc = fine_transfer<5, S>(c, r, nullptr, s, true); break;
+    default: return FR_ERR_ARG;
   }
-  FR_ACCOUNT(c, KK_COARSE, per_pass * (2.0 * nu + 1.0), 8.0 * SL * BLK * L.nc * (2.0 * nu + 1.0));
+  if (rc != FR_OK) return rc;
+  FR_TRY(vcycle<S>(c, 0, s));
+  switch (c->n) {
+    case 2: rc = fine_transfer<2, S>(c, nullptr, c->mg_z0, s, false); break;
+    case 3: rc = fine_transfer<3, S>(c, nullptr, c->mg_z0, s, false); break;
+    case 4: rc = fine_transfer<4, S>(c, nullptr, c->mg_z0, s, false); break;
+    case 5: rc = fine_transfer<5, S>(c, nullptr, c->mg_z0, s, false); break;
+  }
+  if (rc != FR_OK) return rc;
+  // z = z0 + B^-1 (r - A z0): the block apply forms r - A z0 and adds z0 itself
+  FR_TRY(op_apply(c, q, c->mg_z0, inv_dtau, a0_dt, c->mg_t, s));
+  return frk::block_apply_fused(c, r, c->mg_t, c->mg_z0, z, s);
+}
+
+template <class S>
+int upload_views(fr_ctx* c) {
+  std::vector<Lv<S>> views;
+  for (const MgLevel& L : c->mg) views.push_back(view<S>(L));
+  FR_CUDA_CHECK(c, cudaMemcpy(c->mg_views, views.data(), views.size() * sizeof(Lv<S>), cudaMemcpyHostToDevice));
   return FR_OK;
 }
 
@@ -506,16 +677,19 @@ namespace frk {
 
 void mg_free(fr_ctx* c) {
   for (MgLevel& l : c->mg) {
-    int* is[] = {l.nb, l.cell_case, l.parent, l.children, l.gslot, l.fin};
+    int* is[] = {l.nb, l.cell_case, l.parent, l.children, l.gslot, l.fin, l.mode, l.tail};
     for (int* p : is) if (p) cudaFree(p);
-    double* ds[] = {l.A, l.Dinv, l.x, l.y, l.b, l.qo, l.Ainv};
-    for (double* p : ds) if (p) cudaFree(p);
+    void* vs[] = {l.A, l.Dinv, l.x, l.y, l.b, l.Ainv};
+    for (void* p : vs) if (p) cudaFree(p);
+    if (l.qo) cudaFree(l.qo);
   }
   c->mg.clear();
   if (c->mg_colslot) { cudaFree(c->mg_colslot); c->mg_colslot = nullptr; }
   double** fs[] = {&c->mg_x, &c->mg_y, &c->mg_z0, &c->mg_t};
   for (double** p : fs) if (*p) { cudaFree(*p); *p = nullptr; }
   if (c->mg_bad) { cudaFree(c->mg_bad); c->mg_bad = nullptr; }
+  if (c->mg_views) { cudaFree(c->mg_views); c->mg_views = nullptr; }
+  if (c->mg_tc) { cudaFree(c->mg_tc); c->mg_tc = nullptr; }
   c->mg_ncol = 0;
   c->mg_q = nullptr;
 }
@@ -524,6 +698,8 @@ int mg_setup(fr_ctx* c) {
   mg_free(c);
   if (c->cfg.precond != FR_PRECOND_TWO_LEVEL) return FR_OK;
   const bool bounded = c->bounded != 0;
+  const bool f64 = c->cfg.mg_prec == FR_PREC_FP64;
+  const size_t esz = f64 ? sizeof(double) : sizeof(float);
   // level grids of every case, cells numbered case after case
   std::vector<CaseGrid> grids(c->ncases);
   int off = 0;
@@ -532,23 +708,39 @@ int mg_setup(fr_ctx* c) {
     off += c->cps[k].nx * c->cps[k].ny;
   }
   std::vector<char> done(c->ncases, 0);
-  std::vector<std::vector<int>> h_nb, h_case, h_parent, h_children, h_gslot, h_fin;
+  std::vector<TailCase> tcs(c->ncases);
+  for (int k = 0; k < c->ncases; ++k) {
+    std::memset(&tcs[k], 0, sizeof(TailCase));
+    tcs[k].lev0 = -1;
+    tcs[k].fin = -1;
+  }
+  std::vector<std::vector<int>> h_nb, h_case, h_parent, h_children, h_gslot, h_fin, h_mode, h_tail;
   std::vector<std::vector<double>> h_qo;
+  std::vector<int> h_nsweep;
   while (true) {
+    const int lev = (int)h_nb.size();
     int nc = 0;
     for (int k = 0; k < c->ncases; ++k) if (!done[k]) nc += grids[k].nx * grids[k].ny;
     if (nc == 0) break;
+    if (lev >= 16) { snprintf(c->err, sizeof(c->err), "two-level set-up: too many levels"); return FR_ERR_ARG; }
     std::vector<int> nb((size_t)nc * SL), cs(nc), parent(nc, -1), gsl((size_t)nc * SL, -1), fin;
+    std::vector<int> mode(nc, 0), tail;
     std::vector<double> qo((size_t)nc * 4, 0.0);
-    // the next level's grids (cases continuing) and their offsets
     std::vector<CaseGrid> next(c->ncases);
-    int noff = 0;
+    int noff = 0, nsweep = 0;
     for (int k = 0; k < c->ncases; ++k) {
       if (done[k]) continue;
       const CaseGrid& g = grids[k];
-      if (g.nx * g.ny <= MAXFIN) {
+      const int cnt = g.nx * g.ny;
+      TailCase& T = tcs[k];
+      T.off[lev] = g.off;
+      T.cnt[lev] = cnt;
+      T.nlev = lev + 1;
+      if (cnt <= TAIL && T.lev0 < 0) { T.lev0 = lev; tail.push_back(k); }
+      if (cnt <= MAXFIN) {
+        T.fin = (int)fin.size() / 2;
         fin.push_back(g.off);
-        fin.push_back(g.nx * g.ny);
+        fin.push_back(cnt);
       } else {
         next[k] = CaseGrid{(g.nx + 1) / 2, (g.ny + 1) / 2, noff};
         noff += next[k].nx * next[k].ny;
@@ -558,11 +750,14 @@ int mg_setup(fr_ctx* c) {
       if (done[k]) continue;
       const CaseGrid& g = grids[k];
       const bool cont = g.nx * g.ny > MAXFIN;
+      const bool swept = tcs[k].lev0 < 0;   // not yet in the case's single-block kernel
       for (int j = 0; j < g.ny; ++j) {
         for (int i = 0; i < g.nx; ++i) {
           const int cell = g.off + j * g.nx + i;
           stencil_of(g, bounded, i, j, &nb[(size_t)cell * SL]);
           cs[cell] = k;
+          mode[cell] = swept ? 1 : 0;
+          nsweep += swept ? 1 : 0;
           if (!cont) continue;
           const CaseGrid& G = next[k];
           const int I = i / 2, J = j / 2;
@@ -584,6 +779,9 @@ int mg_setup(fr_ctx* c) {
     h_gslot.push_back(gsl);
     h_qo.push_back(qo);
     h_fin.push_back(fin);
+    h_mode.push_back(mode);
+    h_tail.push_back(tail);
+    h_nsweep.push_back(nsweep);
     for (int k = 0; k < c->ncases; ++k) {
       if (done[k]) continue;
       if (grids[k].nx * grids[k].ny <= MAXFIN) done[k] = 1;
@@ -607,10 +805,10 @@ int mg_setup(fr_ctx* c) {
         const int f = h_nb[l][(size_t)cell * SL + s];
         if (f < 0) continue;
         const int F = h_parent[l][f];
-        int S = -1;
-        for (int t = 0; t < SL; ++t) if (h_nb[l + 1][(size_t)P * SL + t] == F) S = t;
-        if (S < 0) { snprintf(c->err, sizeof(c->err), "two-level set-up: parent stencil mismatch"); return FR_ERR_ARG; }
-        h_gslot[l][(size_t)cell * SL + s] = S;
+        int Sl = -1;
+        for (int t = 0; t < SL; ++t) if (h_nb[l + 1][(size_t)P * SL + t] == F) Sl = t;
+        if (Sl < 0) { snprintf(c->err, sizeof(c->err), "two-level set-up: parent stencil mismatch"); return FR_ERR_ARG; }
+        h_gslot[l][(size_t)cell * SL + s] = Sl;
       }
     }
     h_children.push_back(ch);
@@ -621,6 +819,8 @@ int mg_setup(fr_ctx* c) {
     MgLevel& L = c->mg[l];
     L.nc = (int)h_case[l].size();
     L.nfin = (int)h_fin[l].size() / 2;
+    L.ntail = (int)h_tail[l].size();
+    L.nsweep = h_nsweep[l];
     FR_TRY(upload(c, &L.nb, h_nb[l]));
     FR_TRY(upload(c, &L.cell_case, h_case[l]));
     FR_TRY(upload(c, &L.parent, h_parent[l]));
@@ -628,16 +828,21 @@ int mg_setup(fr_ctx* c) {
     FR_TRY(upload(c, &L.qo, h_qo[l]));
     FR_TRY(upload(c, &L.children, h_children[l]));
     FR_TRY(upload(c, &L.fin, h_fin[l]));
-    FR_TRY(dalloc(c, &L.A, (size_t)L.nc * SL * BLK));
-    FR_TRY(dalloc(c, &L.Dinv, (size_t)L.nc * BLK));
-    FR_TRY(dalloc(c, &L.x, (size_t)L.nc * NB));
-    FR_TRY(dalloc(c, &L.y, (size_t)L.nc * NB));
-    FR_TRY(dalloc(c, &L.b, (size_t)L.nc * NB));
-    FR_TRY(dalloc(c, &L.Ainv, (size_t)L.nfin * DN * DN));
-    FR_CUDA_CHECK(c, cudaMemset(L.A, 0, (size_t)L.nc * SL * BLK * sizeof(double)));
-    FR_CUDA_CHECK(c, cudaMemset(L.x, 0, (size_t)L.nc * NB * sizeof(double)));
-    FR_CUDA_CHECK(c, cudaMemset(L.y, 0, (size_t)L.nc * NB * sizeof(double)));
+    FR_TRY(upload(c, &L.mode, h_mode[l]));
+    FR_TRY(upload(c, &L.tail, h_tail[l]));
+    const size_t n12 = (size_t)L.nc * NB;
+    void** bufs[] = {&L.A, &L.Dinv, &L.x, &L.y, &L.b, &L.Ainv};
+    const size_t counts[] = {n12 * SL * NB, n12 * NB, n12, n12, n12, (size_t)L.nfin * DN * DN};
+    for (int i = 0; i < 6; ++i) {
+      if (counts[i] == 0) continue;
+      FR_CUDA_CHECK(c, cudaMalloc(bufs[i], counts[i] * esz));
+      FR_CUDA_CHECK(c, cudaMemset(*bufs[i], 0, counts[i] * esz));
+    }
   }
+  FR_CUDA_CHECK(c, cudaMalloc(&c->mg_tc, tcs.size() * sizeof(TailCase)));
+  FR_CUDA_CHECK(c, cudaMemcpy(c->mg_tc, tcs.data(), tcs.size() * sizeof(TailCase), cudaMemcpyHostToDevice));
+  FR_CUDA_CHECK(c, cudaMalloc(&c->mg_views, nlev * std::max(sizeof(Lv<double>), sizeof(Lv<float>))));
+  FR_TRY(f64 ? upload_views<double>(c) : upload_views<float>(c));
   // level 0: greedy colouring in which no stencil holds two members of one colour
   const int ne = c->ne;
   const std::vector<int>& nb0 = h_nb[0];
@@ -685,58 +890,28 @@ int mg_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStre
   c->mg_q = q;
   c->mg_inv_dtau = inv_dtau;
   c->mg_a0_dt = a0_dt;
+  const bool f64 = c->cfg.mg_prec == FR_PREC_FP64;
   int rc;
-  switch (c->n) {
-    case 2: rc = build_level0<2>(c, q, inv_dtau, a0_dt, s); break;
-    case 3: rc = build_level0<3>(c, q, inv_dtau, a0_dt, s); break;
-    case 4: rc = build_level0<4>(c, q, inv_dtau, a0_dt, s); break;
-    case 5: rc = build_level0<5>(c, q, inv_dtau, a0_dt, s); break;
+  switch (c->n * 2 + (f64 ? 1 : 0)) {
+    case 4: rc = build_level0<2, float>(c, q, inv_dtau, a0_dt, s); break;
+    case 5: rc = build_level0<2, double>(c, q, inv_dtau, a0_dt, s); break;
+    case 6: rc = build_level0<3, float>(c, q, inv_dtau, a0_dt, s); break;
+    case 7: rc = build_level0<3, double>(c, q, inv_dtau, a0_dt, s); break;
+    case 8: rc = build_level0<4, float>(c, q, inv_dtau, a0_dt, s); break;
+    case 9: rc = build_level0<4, double>(c, q, inv_dtau, a0_dt, s); break;
+    case 10: rc = build_level0<5, float>(c, q, inv_dtau, a0_dt, s); break;
+    case 11: rc = build_level0<5, double>(c, q, inv_dtau, a0_dt, s); break;
     default: return FR_ERR_ARG;
   }
   if (rc != FR_OK) return rc;
-  for (size_t l = 0; l < c->mg.size(); ++l) {
-    MgLevel& L = c->mg[l];
-    const LevelView V = view(L);
-    FR_PROF_BEGIN(c, s);
-    k_mg_invert_diag<<<blocks_for(L.nc, 64), 64, 0, s>>>(V, L.Dinv, c->mg_bad);
-    if (L.nfin > 0) k_mg_coarsest<<<L.nfin, 128, 0, s>>>(V, L.fin, L.Ainv, c->mg_bad);
-    if (l + 1 < c->mg.size()) {
-      const MgLevel& Nx = c->mg[l + 1];
-      k_mg_galerkin<<<blocks_for((long long)Nx.nc * SL * BLK, 256), 256, 0, s>>>(
-          V, L.qo, L.gslot, Nx.nc, Nx.nb, L.children, Nx.A);
-    }
-    FR_PROF_END(c, s, KK_COARSE);
-    FR_LAUNCH_CHECK(c);
-    FR_ACCOUNT(c, KK_COARSE, 2.0 * NB * NB * NB * L.nc, 0.0);
-  }
-  return FR_OK;
+  return f64 ? build_levels<double>(c, s) : build_levels<float>(c, s);
 }
 
 int precond_apply(fr_ctx* c, const double* q, const double* r, double* z, double inv_dtau,
                   double a0_dt, cudaStream_t s) {
   if (c->cfg.precond != FR_PRECOND_TWO_LEVEL) return block_apply(c, r, z, s);
-  int rc;
-  switch (c->n) {
-    case 2: rc = restrict_prolong<2>(c, r, nullptr, s, true); break;
-    case 3: rc = restrict_prolong<3>(c, r, nullptr, s, true); break;
-    case 4: rc = restrict_prolong<4>(c, r, nullptr, s, true); break;
-    case 5: rc = restrict_prolong<5>(c, r, nullptr, s, true); break;
-    default: return FR_ERR_ARG;
-  }
-  if (rc != FR_OK) return rc;
-  FR_TRY(vcycle(c, 0, s));
-  switch (c->n) {
-    case 2: rc = restrict_prolong<2>(c, nullptr, c->mg_z0, s, false); break;
-    case 3: rc = restrict_prolong<3>(c, nullptr, c->mg_z0, s, false); break;
-    case 4: rc = restrict_prolong<4>(c, nullptr, c->mg_z0, s, false); break;
-    case 5: rc = restrict_prolong<5>(c, nullptr, c->mg_z0, s, false); break;
-  }
-  if (rc != FR_OK) return rc;
-  // z = z0 + B^-1 (r - A z0)
-  FR_TRY(op_apply(c, q, c->mg_z0, inv_dtau, a0_dt, c->mg_t, s));
-  FR_TRY(axpby(c, 1.0, r, -1.0, c->mg_t, s));
-  FR_TRY(block_apply(c, c->mg_t, z, s));
-  return axpby(c, 1.0, c->mg_z0, 1.0, z, s);
+  if (c->cfg.mg_prec == FR_PREC_FP64) return apply_t<double>(c, q, r, z, inv_dtau, a0_dt, s);
+  return apply_t<float>(c, q, r, z, inv_dtau, a0_dt, s);
 }
 
 }  // namespace frk

@@ -553,10 +553,12 @@ template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x
 // transformations, linear to about 2^-44 of the summed magnitudes).
 constexpr int APPLY_PARTS = 4;
 
+// With rsub and zadd (both nullable) the same pass forms z_e = zadd_e + B_e^-1 (r - rsub)_e.
 template <class S, int ACC, int N>
 __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
                          const float* __restrict__ Dc, const double* __restrict__ r, Mesh M,
-                         double* __restrict__ z) {
+                         double* __restrict__ z, const double* __restrict__ rsub,
+                         const double* __restrict__ zadd) {
   constexpr int NP = N * N, BS = 4 * NP, BSR = (BS + 31) / 32 * 32;
   constexpr int COLS = (BS + APPLY_PARTS - 1) / APPLY_PARTS;   // columns per thread
   __shared__ double xd[ACC == 0 ? BS : 1];
@@ -579,7 +581,8 @@ __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
   const size_t qo = M.qbase(e, NP), qs = M.qstride(e);
   for (int t = threadIdx.x; t < BS; t += blockDim.x) {
     const int v = t / NP, pt = t % NP;
-    const double u = r[v * qs + qo + pt] * (double)Dr[(size_t)e * BS + t];
+    const size_t gi = v * qs + qo + pt;
+    const double u = (rsub ? r[gi] - rsub[gi] : r[gi]) * (double)Dr[(size_t)e * BS + t];
     if (ACC == 0) xd[t] = u;
     else if (ACC == 1) xf[t] = (float)u;
     else {
@@ -646,7 +649,9 @@ __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
     for (int q = 1; q < APPLY_PARTS; ++q) acc += pd[q][row];
   }
   const int v = row / NP, pt = row % NP;
-  z[v * qs + qo + pt] = acc * (double)Dc[(size_t)e * BS + row];
+  const size_t gi = v * qs + qo + pt;
+  const double zr = acc * (double)Dc[(size_t)e * BS + row];
+  z[gi] = zadd ? zadd[gi] + zr : zr;
 }
 
 }  // namespace fr
@@ -759,11 +764,25 @@ int block_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaS
   return factor(c, s);
 }
 
+static int apply_impl(fr_ctx* c, const double* r, double* z, const double* rsub,
+                      const double* zadd, cudaStream_t s);
+
 int block_apply(fr_ctx* c, const double* r, double* z, cudaStream_t s) {
+  return apply_impl(c, r, z, nullptr, nullptr, s);
+}
+
+int block_apply_fused(fr_ctx* c, const double* r, const double* t, const double* z0, double* z,
+                      cudaStream_t s) {
+  return apply_impl(c, r, z, t, z0, s);
+}
+
+static int apply_impl(fr_ctx* c, const double* r, double* z, const double* rsub,
+                      const double* zadd, cudaStream_t s) {
   const int bs = c->bsz;
   const double esz = c->cfg.prec_dtype == FR_PREC_FP64 ? 8.0 : c->cfg.prec_dtype == FR_PREC_FP32 ? 4.0 : 2.0;
   FR_ACCOUNT(c, KK_APPLY, 2.0 * (double)bs * bs * c->ne,
-             c->ne * ((double)bs * bs * esz + 2.0 * bs * 4.0) + 2.0 * 8.0 * c->ndof);
+             c->ne * ((double)bs * bs * esz + 2.0 * bs * 4.0) +
+                 (2.0 + (rsub ? 1.0 : 0.0) + (zadd ? 1.0 : 0.0)) * 8.0 * c->ndof);
   FR_PROF_BEGIN(c, s);
   // Double-float accumulation keeps the preconditioner linear to near FP64 round-off (the
   // stored inverse rounded once); plain FP32 accumulation also rounds the input and every
@@ -774,14 +793,14 @@ int block_apply(fr_ctx* c, const double* r, double* z, cudaStream_t s) {
   const int acc = c->cfg.prec_dtype == FR_PREC_FP64 ? 0 : df ? 2 : 1;
   switch (c->n * 10 + acc) {
 #define FR_APPLY_CASE(NN)                                                                      \
-    case NN * 10 + 0: k_apply4<double, 0, NN><<<c->ne, nt4, 0, s>>>((const double*)c->Binv, c->Dr, c->Dc, r, c->mesh, z); break; \
+    case NN * 10 + 0: k_apply4<double, 0, NN><<<c->ne, nt4, 0, s>>>((const double*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd); break; \
     case NN * 10 + 1: if (c->cfg.prec_dtype == FR_PREC_FP32)                                  \
-        k_apply4<float, 1, NN><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z); \
-      else k_apply4<__nv_bfloat16, 1, NN><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z); \
+        k_apply4<float, 1, NN><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd); \
+      else k_apply4<__nv_bfloat16, 1, NN><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd); \
       break;                                                                                   \
     case NN * 10 + 2: if (c->cfg.prec_dtype == FR_PREC_FP32)                                  \
-        k_apply4<float, 2, NN><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z); \
-      else k_apply4<__nv_bfloat16, 2, NN><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z); \
+        k_apply4<float, 2, NN><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd); \
+      else k_apply4<__nv_bfloat16, 2, NN><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd); \
       break;
     FR_APPLY_CASE(2) FR_APPLY_CASE(3) FR_APPLY_CASE(4) FR_APPLY_CASE(5)
 #undef FR_APPLY_CASE

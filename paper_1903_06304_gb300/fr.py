@@ -46,7 +46,8 @@ class _Config(ctypes.Structure):
                 ("graphs", ctypes.c_int), ("apply_accum", ctypes.c_int), ("tiles", ctypes.c_int),
                 ("block_mode", ctypes.c_int), ("orthog", ctypes.c_int),
                 ("krylov_arith", ctypes.c_int), ("precond", ctypes.c_int),
-                ("mg_sweeps", ctypes.c_int), ("mg_omega", ctypes.c_double)]
+                ("mg_sweeps", ctypes.c_int), ("mg_omega", ctypes.c_double),
+                ("mg_prec", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -199,6 +200,7 @@ class Config:
     precond: str = "block"
     mg_sweeps: int = 2
     mg_omega: float = 0.7
+    mg_prec: str = "fp32"
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -218,6 +220,8 @@ class Config:
                 c.block_mode = {"linearized": 0, "dual": 1}[self.block_mode]
             elif f.name == "apply_accum":
                 c.apply_accum = {"fp32": 0, "df64": 1}[self.apply_accum]
+            elif f.name == "mg_prec":
+                c.mg_prec = PREC[self.mg_prec]
             elif f.name == "precond":
                 c.precond = {"block": 0, "twolevel": 1}[self.precond]
             else:
