@@ -407,16 +407,18 @@ def step_summary(stats):
 
 def low_mach_deforming_report(args, torch, fr, inp, T, flush):
     """The deforming 128 x 128, p = 3, M = 0.01 workload: the vortex march's first steps with
-    the two-level preconditioner and each block precision, free-stream preservation of the
-    uniform stream on the moving mesh, and the rounding floor of Res_m (the continuity
-    residual evaluated by the two tile shapes, whose FMA contractions differ)."""
+    the two-level preconditioner and each block precision (BF16 blocks also factored on
+    the tensor cores), and free-stream preservation of the uniform stream on the moving
+    mesh."""
     w = inp.NS_DEFORM_128
     c0, v0, q0 = inp.make_case(w, t=0.0)
     meshes = march_inputs(w, args.c3_steps, T)
     out = {"workload": w.name, "dof": w.dof, "newton_cap": args.c3_newton}
 
     def solver(prec, precond, tiles=1):
-        S = fr.Solver(fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=prec,
+        factor = "tc_bf16" if prec == "bf16_tc" else "simt"
+        prec = "bf16" if prec == "bf16_tc" else prec
+        S = fr.Solver(fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=prec, factor=factor,
                                 precond=precond, maxit_newton=args.c3_newton, restart=args.restart,
                                 maxit_lin=args.maxit_lin, graphs=args.graphs, tiles=tiles,
                                 apply_accum=args.apply_accum), w.nx, w.ny)
@@ -425,7 +427,7 @@ def low_mach_deforming_report(args, torch, fr, inp, T, flush):
         return S
 
     finals = {}
-    for prec in ("fp64", "fp32", "bf16"):
+    for prec in ("fp64", "fp32", "bf16", "bf16_tc"):
         S = solver(prec, args.precond)
         run = March(S, T(q0), meshes, fr)
         ms, st, _ = timed_steps(run, args.c3_steps if prec == "fp32" else 1, flush, torch.cuda.synchronize)
@@ -438,7 +440,7 @@ def low_mach_deforming_report(args, torch, fr, inp, T, flush):
             finals[prec] = r1.q.clone()
         S.close()
     dq = (finals["fp64"] - T(q0)).view(4, -1).abs().amax(dim=1)
-    for prec in ("fp32", "bf16"):
+    for prec in ("fp32", "bf16", "bf16_tc"):
         diff = (finals[prec] - finals["fp64"]).view(4, -1).abs().amax(dim=1)
         out[f"march_{prec}"]["state_diff_vs_fp64_step1"] = float((diff / dq).max())
     # free stream on the moving mesh
@@ -453,22 +455,6 @@ def low_mach_deforming_report(args, torch, fr, inp, T, flush):
         worst = max(worst, float(R.abs().max()))
     out["free_stream_max_abs_residual"] = worst
     S.close()
-    # rounding floor of Res_m
-    rs_ = []
-    for tiles in (1, 2):
-        S = solver("fp32", "block", tiles=tiles)
-        c, v, _ = inp.make_case(w, t=w.dt)
-        S.update_mesh(T(c), T(v))
-        qd = T(q0)
-        qc = torch.empty_like(qd)
-        S.conservative(qd, qc)
-        r = torch.empty_like(qd)
-        S.bdf_rhs(qd, qc, qc, fr.BDF1, w.dt, r)
-        rs_.append(r.clone())
-        S.close()
-    res0 = float(torch.linalg.norm(rs_[0][0]))
-    out["res0_continuity"] = res0
-    out["rounding_floor_rel"] = float(torch.linalg.norm(rs_[0][0] - rs_[1][0])) / res0
     return out
 
 
@@ -500,8 +486,8 @@ def gpu_arm(args):
     nsteps = args.startup + args.warmup + args.steps
     meshes = march_inputs(w, nsteps, T)
 
-    def make_solver(prec, arith=None, precond=None):
-        cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=prec,
+    def make_solver(prec, arith=None, precond=None, factor="simt"):
+        cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=prec, factor=factor,
                         restart=args.restart, maxit_lin=args.maxit_lin, tol_res=w.tol_res,
                         tol_pseudo=w.tol_pseudo, maxit_newton=args.maxit_newton, lag=2,
                         line_search=args.line_search, graphs=args.graphs,
@@ -704,6 +690,23 @@ def gpu_arm(args):
         gm[precond] = 1e3 * ga.elapsed_time(gb) / its_g
         Sg.close()
 
+    # ---- element-block inversion per method at the start state: device time of the
+    # factorisation launch (event pair, profiling on), SIMT Gauss-Jordan against the
+    # tensor-core blocked forms
+    factor_ms = {}
+    for prec, factor in (("fp32", "simt"), ("bf16", "tc_bf16"), ("fp32", "tc_bf16x3")):
+        Sf = make_solver(prec, factor=factor)
+        Sf.precond_build(run.q, 1e-20, 1.5 / w.dt)
+        Sf.profile(True)
+        Sf.profile_read(reset=True)
+        for _ in range(3):
+            Sf.precond_build(run.q, 1e-20, 1.5 / w.dt)
+        pr = Sf.profile_read(reset=True)["block_factor"]
+        Sf.profile(False)
+        factor_ms[f"{factor}_{prec}"] = {"ms": pr["ms"] / max(1, pr["launches"]),
+                                         "tflops": pr["flops"] / (pr["ms"] * 1e-3) / 1e12 if pr["ms"] else None}
+        Sf.close()
+
     # ---- precision comparison: the timed steps again from the same state per block
     # precision (FP64 Krylov basis) and with FP32 blocks and the double-float basis; the
     # final state of each against the all-FP64 run (max over entries, relative to the
@@ -711,10 +714,12 @@ def gpu_arm(args):
     compare = {}
     if not args.no_compare:
         finals = {}
-        variants = {"fp64": ("fp64", "fp64"), "fp32": ("fp32", "fp64"), "bf16": ("bf16", "fp64"),
-                    "fp32_df64_basis": ("fp32", "df64")}
-        for name, (bprec, arith) in variants.items():
-            S2 = make_solver(bprec, arith)
+        variants = {"fp64": ("fp64", "fp64", "simt"), "fp32": ("fp32", "fp64", "simt"),
+                    "bf16": ("bf16", "fp64", "simt"), "fp32_df64_basis": ("fp32", "df64", "simt"),
+                    "bf16_tensor_core": ("bf16", "fp64", "tc_bf16"),
+                    "fp32_tensor_core_split": ("fp32", "fp64", "tc_bf16x3")}
+        for name, (bprec, arith, factor) in variants.items():
+            S2 = make_solver(bprec, arith, factor=factor)
             r2 = March(S2, snap[0], meshes, fr)
             r2.restore(snap)
             ms2, st2, _ = timed_steps(r2, args.steps, flush, torch.cuda.synchronize)
@@ -787,6 +792,7 @@ def gpu_arm(args):
         "linearize_ms": t_lin,
         "us_per_gmres_iteration": gm,
         "precision_compare": compare,
+        "block_factor_ms": factor_ms,
         "low_mach_deforming": low_mach,
         "kernels": kernels,
         "kernels_same_steps": same_steps,

@@ -116,7 +116,15 @@ typedef struct fr_ctx fr_ctx;
  * coloured products of A with the P1 functions of the elements.  mg_prec: storage and
  * sweep arithmetic of the coarse levels, FR_PREC_FP32 (default) or FR_PREC_FP64 (the
  * builds and the transfers to and from the solution points are FP64 either way); B^-1 in
- * the configured block precision.  On a periodic mesh with a very
+ * the configured block precision;
+ * factor_tc: how the element blocks are inverted: FR_FACTOR_SIMT (default) Gauss-Jordan
+ * with partial pivoting in FP32 (FP64 for FP64 blocks) on the SIMT pipe;
+ * FR_FACTOR_TC_BF16 blocked Gauss-Jordan on [B | I] in FP32 shared memory whose rank-16
+ * panel updates run on the tensor cores with BF16 operands and FP32 accumulation (the
+ * the benchmark spec's mixed-precision factorisation: about 2^-9 relative per update, the outer
+ * FP64 Krylov iteration absorbs it); FR_FACTOR_TC_BF16X3 the same with every operand split
+ * into two BF16 numbers and three products per update (about 2^-16 relative).  Panel
+ * pivoting and elimination stay FP32 SIMT; the inverse is stored in prec_dtype.  On a periodic mesh with a very
  * large dtau and no time term (a0_dt = 0) the constant states make the coarsest operator
  * singular: use it for BDF2 steps (a0_dt > 0) or on bounded meshes. */
 #define FR_MAX_RESTART 256
@@ -136,6 +144,9 @@ typedef struct fr_ctx fr_ctx;
 #define FR_BC_FARFIELD 2
 #define FR_PRECOND_BLOCK 0
 #define FR_PRECOND_TWO_LEVEL 1
+#define FR_FACTOR_SIMT 0
+#define FR_FACTOR_TC_BF16 1
+#define FR_FACTOR_TC_BF16X3 2
 typedef struct fr_config {
   int p;
   double gamma, prandtl, mach, re, kappa, eps_floor;
@@ -158,6 +169,7 @@ typedef struct fr_config {
   int mg_sweeps;
   double mg_omega;
   int mg_prec;
+  int factor_tc;
 } fr_config;
 
 /* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).

@@ -571,6 +571,7 @@ void fr_default_config(fr_config* c) {
   c->mg_sweeps = 2;
   c->mg_omega = 0.7;
   c->mg_prec = FR_PREC_FP32;
+  c->factor_tc = FR_FACTOR_SIMT;
 }
 
 int fr_create(const fr_config* cfg, fr_ctx** out) {
@@ -587,7 +588,8 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
       (cfg->krylov_arith != FR_KRYLOV_FP64 && cfg->krylov_arith != FR_KRYLOV_DF64) ||
       (cfg->precond != FR_PRECOND_BLOCK && cfg->precond != FR_PRECOND_TWO_LEVEL) ||
       cfg->mg_sweeps < 1 || cfg->mg_sweeps > 8 || !(cfg->mg_omega > 0.0 && cfg->mg_omega <= 1.5) ||
-      (cfg->mg_prec != FR_PREC_FP64 && cfg->mg_prec != FR_PREC_FP32))
+      (cfg->mg_prec != FR_PREC_FP64 && cfg->mg_prec != FR_PREC_FP32) ||
+      cfg->factor_tc < FR_FACTOR_SIMT || cfg->factor_tc > FR_FACTOR_TC_BF16X3)
     return FR_ERR_ARG;
   fr_ctx* c = new fr_ctx();
   c->cfg = *cfg;

@@ -543,6 +543,226 @@ __global__ void k_factor(const double* __restrict__ Bin, S* __restrict__ Aout,
   if (tid == 0) info[e] = s_bad;
 }
 
+// ------------------------------------------------------------------ factor on the tensor cores
+// Blocked Gauss-Jordan inversion of the equilibrated block on the augmented matrix
+// M = [A | I] (FP32 in shared memory, BP = the block size rounded up to 16, the padding an
+// identity), panel width 16: the panel's pivots and its elimination run on the FP32 SIMT
+// pipe (the panel columns only), then every row of M right of the panel receives the
+// rank-16 update M += U M[panel rows] on the tensor cores (mma.sync m16n8k16, BF16
+// operands, FP32 accumulation), U the panel's multipliers.  SPLIT = 1 rounds U and the
+// panel rows to BF16 once (about 2^-9 relative per update); SPLIT = 3 writes each as a
+// sum of two BF16 numbers and accumulates hi*hi + hi*lo + lo*hi (about 2^-16).  The result
+// is stored like k_factor's: the transposed inverse of Dr B Dc and the scales.
+constexpr int TC_THREADS = 128;
+template <int N> struct TcDims {
+  static constexpr int BS = 4 * N * N;
+  static constexpr int BP = (BS + 15) / 16 * 16;   // padded block size
+  static constexpr int LDM = 2 * BP + 4;           // FP32 row stride of M (shifts banks by 4)
+  static constexpr int LDW = 33;                   // panel workspace stride (16 + 16 columns)
+  static constexpr size_t BYTES = sizeof(float) * ((size_t)BP * LDM + (size_t)BP * LDW + 2 * BP) +
+                                  sizeof(int) * BP + 2 * sizeof(__nv_bfloat16) * ((size_t)BP * 16 + 2 * (size_t)BP * 16);
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float& c0, float& c1, float& c2, float& c3, uint32_t a0, uint32_t a1,
+                                         uint32_t a2, uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <class S, int N, int SPLIT>
+__global__ void __launch_bounds__(TC_THREADS) k_factor_tc(const double* __restrict__ Bin, S* __restrict__ Aout,
+                                                           float* __restrict__ Dr, float* __restrict__ Dc,
+                                                           int* __restrict__ info, Mesh Msh) {
+  using D = TcDims<N>;
+  constexpr int BS = D::BS, BP = D::BP, LDM = D::LDM, LDW = D::LDW;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* Mx = reinterpret_cast<float*>(smraw);           // [BP][LDM]
+  float* Wk = Mx + (size_t)BP * LDM;                      // [BP][LDW]: panel columns | K tracker
+  float* dr = Wk + (size_t)BP * LDW;                      // [BP]
+  float* dc = dr + BP;                                     // [BP]
+  int* piv = reinterpret_cast<int*>(dc + BP);              // [16] (BP reserved)
+  __nv_bfloat16* Uh = reinterpret_cast<__nv_bfloat16*>(piv + BP);   // [2][BP][16] (hi, lo)
+  __nv_bfloat16* Vt = Uh + 2 * BP * 16;                              // [2][2BP][16] transposed panel rows
+  __shared__ int s_piv, s_bad;
+  const int e = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  if (!Msh.on(e)) return;
+  const double* Be = Bin + (size_t)e * BS * BS;
+  if (tid == 0) s_bad = 0;
+  for (int idx = tid; idx < BP * 2 * BP; idx += TC_THREADS) {
+    const int r = idx / (2 * BP), c2 = idx % (2 * BP);
+    float v;
+    if (c2 < BP) v = (r < BS && c2 < BS) ? (float)Be[r * BS + c2] : (r == c2 ? 1.f : 0.f);
+    else v = (c2 - BP == r) ? 1.f : 0.f;
+    Mx[r * LDM + c2] = v;
+  }
+  __syncthreads();
+  // equilibration (powers of two, exact): row scales, then column scales of the row-scaled block
+  for (int r = wid; r < BP; r += TC_THREADS / 32) {
+    float m = 0.f;
+    for (int c2 = lane; c2 < BS; c2 += 32) m = fmaxf(m, fabsf(Mx[r * LDM + c2]));
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) {
+      int ex = 0;
+      if (m > 0.f && r < BS) frexpf(m, &ex);
+      dr[r] = (m > 0.f && r < BS) ? ldexpf(1.0f, -ex) : 1.0f;
+    }
+  }
+  __syncthreads();
+  for (int c2 = wid; c2 < BP; c2 += TC_THREADS / 32) {
+    float m = 0.f;
+    for (int r = lane; r < BS; r += 32) m = fmaxf(m, fabsf(Mx[r * LDM + c2]) * dr[r]);
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) {
+      int ex = 0;
+      if (m > 0.f && c2 < BS) frexpf(m, &ex);
+      dc[c2] = (m > 0.f && c2 < BS) ? ldexpf(1.0f, -ex) : 1.0f;
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < BS * BS; idx += TC_THREADS) {
+    const int r = idx / BS, c2 = idx % BS;
+    Mx[r * LDM + c2] *= dr[r] * dc[c2];
+  }
+  __syncthreads();
+  for (int k0 = 0; k0 < BP; k0 += 16) {
+    // (a) pivots of the panel: Gauss-Jordan steps on a copy of its 16 columns
+    for (int idx = tid; idx < BP * 16; idx += TC_THREADS) Wk[(idx / 16) * LDW + idx % 16] = Mx[(idx / 16) * LDM + k0 + idx % 16];
+    __syncthreads();
+    for (int i = 0; i < 16; ++i) {
+      const int k = k0 + i;
+      if (tid < 32) {
+        float best = -1.f;
+        int bi = k;
+        for (int r = k + tid; r < BP; r += 32) {
+          const float a = fabsf(Wk[r * LDW + i]);
+          if (a > best) { best = a; bi = r; }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          const float ob = __shfl_down_sync(0xffffffffu, best, off);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (tid == 0) { s_piv = bi; piv[i] = bi; if (!(best > 0.f)) s_bad = 1; }
+      }
+      __syncthreads();
+      const int pr = s_piv;
+      if (pr != k)
+        for (int c2 = tid; c2 < 16; c2 += TC_THREADS) { const float t = Wk[k * LDW + c2]; Wk[k * LDW + c2] = Wk[pr * LDW + c2]; Wk[pr * LDW + c2] = t; }
+      __syncthreads();
+      const float d = Wk[k * LDW + i];
+      const float rp = d != 0.f ? 1.f / d : 0.f;
+      __syncthreads();
+      for (int c2 = tid; c2 < 16; c2 += TC_THREADS) Wk[k * LDW + c2] *= rp;
+      __syncthreads();
+      for (int idx = tid; idx < BP * 16; idx += TC_THREADS) {
+        const int r = idx / 16, c2 = idx % 16;
+        if (r == k || c2 == i) continue;
+        Wk[r * LDW + c2] = fmaf(-Wk[r * LDW + i], Wk[k * LDW + c2], Wk[r * LDW + c2]);
+      }
+      __syncthreads();
+      for (int r = tid; r < BP; r += TC_THREADS) if (r != k) Wk[r * LDW + i] = 0.f;
+      __syncthreads();
+    }
+    // (b) the interchanges on the whole rows of M, in order
+    for (int i = 0; i < 16; ++i) {
+      const int k = k0 + i, pr = piv[i];
+      if (pr != k)
+        for (int c2 = tid; c2 < 2 * BP; c2 += TC_THREADS) { const float t = Mx[k * LDM + c2]; Mx[k * LDM + c2] = Mx[pr * LDM + c2]; Mx[pr * LDM + c2] = t; }
+      __syncthreads();
+    }
+    // (c) the elimination again without interchanges on [panel | K]: K (the panel's unit
+    // columns) becomes T K, and U = T K - K are the multipliers of the rank-16 update
+    for (int idx = tid; idx < BP * 32; idx += TC_THREADS) {
+      const int r = idx / 32, c2 = idx % 32;
+      Wk[r * LDW + c2] = c2 < 16 ? Mx[r * LDM + k0 + c2] : (r == k0 + c2 - 16 ? 1.f : 0.f);
+    }
+    __syncthreads();
+    for (int i = 0; i < 16; ++i) {
+      const int k = k0 + i;
+      const float d = Wk[k * LDW + i];
+      const float rp = d != 0.f ? 1.f / d : 0.f;
+      __syncthreads();
+      for (int c2 = tid; c2 < 32; c2 += TC_THREADS) Wk[k * LDW + c2] *= rp;
+      __syncthreads();
+      for (int idx = tid; idx < BP * 32; idx += TC_THREADS) {
+        const int r = idx / 32, c2 = idx % 32;
+        if (r == k || c2 == i) continue;
+        Wk[r * LDW + c2] = fmaf(-Wk[r * LDW + i], Wk[k * LDW + c2], Wk[r * LDW + c2]);
+      }
+      __syncthreads();
+      for (int r = tid; r < BP; r += TC_THREADS) if (r != k) Wk[r * LDW + i] = 0.f;
+      __syncthreads();
+    }
+    // (d) operands in BF16: U (row-major [BP][16]) and the panel rows transposed ([2BP][16])
+    const int c0 = k0 + 16, ncols = 2 * BP - c0;
+    for (int idx = tid; idx < BP * 16; idx += TC_THREADS) {
+      const int r = idx / 16, i = idx % 16;
+      const float u = Wk[r * LDW + 16 + i] - (r == k0 + i ? 1.f : 0.f);
+      const __nv_bfloat16 hi = __float2bfloat16_rn(u);
+      Uh[idx] = hi;
+      if (SPLIT == 3) Uh[BP * 16 + idx] = __float2bfloat16_rn(u - __bfloat162float(hi));
+    }
+    for (int idx = tid; idx < ncols * 16; idx += TC_THREADS) {
+      const int n = idx / 16, i = idx % 16;
+      const float v = Mx[(k0 + i) * LDM + c0 + n];
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      Vt[idx] = hi;
+      if (SPLIT == 3) Vt[2 * BP * 16 + idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+    __syncthreads();
+    // (e) the panel's columns become unit columns; everything right of it gets M += U V
+    for (int idx = tid; idx < BP * 16; idx += TC_THREADS) {
+      const int r = idx / 16, i = idx % 16;
+      Mx[r * LDM + k0 + i] = (r == k0 + i) ? 1.f : 0.f;
+    }
+    const int g = lane >> 2, t4 = lane & 3;
+    const int ntiles = (BP / 16) * (ncols / 8);
+    for (int tile = wid; tile < ntiles; tile += TC_THREADS / 32) {
+      const int mt = tile / (ncols / 8), nt8 = tile % (ncols / 8);
+      const int r0 = mt * 16, n0 = nt8 * 8;
+      float* C0 = Mx + (r0 + g) * LDM + c0 + n0 + 2 * t4;
+      float* C1 = Mx + (r0 + g + 8) * LDM + c0 + n0 + 2 * t4;
+      float c_0 = C0[0], c_1 = C0[1], c_2 = C1[0], c_3 = C1[1];
+#pragma unroll
+      for (int ha = 0; ha < (SPLIT == 3 ? 2 : 1); ++ha) {
+#pragma unroll
+        for (int hb = 0; hb < (SPLIT == 3 ? 2 : 1); ++hb) {
+          if (ha == 1 && hb == 1) continue;   // lo x lo is below the split's accuracy
+          const __nv_bfloat16* U = Uh + ha * BP * 16;
+          const __nv_bfloat16* V = Vt + hb * 2 * BP * 16;
+          const uint32_t a0 = *reinterpret_cast<const uint32_t*>(U + (r0 + g) * 16 + 2 * t4);
+          const uint32_t a1 = *reinterpret_cast<const uint32_t*>(U + (r0 + g + 8) * 16 + 2 * t4);
+          const uint32_t a2 = *reinterpret_cast<const uint32_t*>(U + (r0 + g) * 16 + 2 * t4 + 8);
+          const uint32_t a3 = *reinterpret_cast<const uint32_t*>(U + (r0 + g + 8) * 16 + 2 * t4 + 8);
+          const uint32_t b0 = *reinterpret_cast<const uint32_t*>(V + (n0 + g) * 16 + 2 * t4);
+          const uint32_t b1 = *reinterpret_cast<const uint32_t*>(V + (n0 + g) * 16 + 2 * t4 + 8);
+          mma_bf16(c_0, c_1, c_2, c_3, a0, a1, a2, a3, b0, b1);
+        }
+      }
+      C0[0] = c_0; C0[1] = c_1; C1[0] = c_2; C1[1] = c_3;
+    }
+    __syncthreads();
+  }
+  // the right half of M is the inverse of the equilibrated (padded) block; store it
+  // transposed: Aout[col][row]
+  S* Ae = Aout + (size_t)e * BS * BS;
+  for (int idx = tid; idx < BS * BS; idx += TC_THREADS) {
+    const int c2 = idx / BS, r = idx % BS;
+    Ae[idx] = (S)Mx[r * LDM + BP + c2];
+  }
+  for (int r = tid; r < BS; r += TC_THREADS) { Dr[(size_t)e * BS + r] = dr[r]; Dc[(size_t)e * BS + r] = dc[r]; }
+  if (tid == 0) info[e] = s_bad;
+}
+
 template <class S> __device__ __forceinline__ float to_f(S x) { return (float)x; }
 template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
 
@@ -733,8 +953,52 @@ static int factor_t(fr_ctx* c, S* out, cudaStream_t s) {
   return FR_ERR_ARG;
 }
 
+template <class S, int N, int SPLIT>
+static int factor_tc_n(fr_ctx* c, S* out, cudaStream_t s) {
+  const size_t smem = TcDims<N>::BYTES;
+  FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_factor_tc<S, N, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_factor_tc<S, N, SPLIT><<<c->ne, TC_THREADS, smem, s>>>(c->B64, out, c->Dr, c->Dc, c->info, c->mesh);
+  return FR_OK;
+}
+
+template <class S>
+static int factor_tc(fr_ctx* c, S* out, cudaStream_t s) {
+  const bool split = c->cfg.factor_tc == FR_FACTOR_TC_BF16X3;
+  switch (c->n * 2 + (split ? 1 : 0)) {
+    case 4: return factor_tc_n<S, 2, 1>(c, out, s);
+    case 5: return factor_tc_n<S, 2, 3>(c, out, s);
+    case 6: return factor_tc_n<S, 3, 1>(c, out, s);
+    case 7: return factor_tc_n<S, 3, 3>(c, out, s);
+    case 8: return factor_tc_n<S, 4, 1>(c, out, s);
+    case 9: return factor_tc_n<S, 4, 3>(c, out, s);
+    case 10: return factor_tc_n<S, 5, 1>(c, out, s);
+    case 11: return factor_tc_n<S, 5, 3>(c, out, s);
+  }
+  return FR_ERR_ARG;
+}
+
 static int factor(fr_ctx* c, cudaStream_t s) {
   const int bs = c->bsz;
+  if (c->cfg.factor_tc != FR_FACTOR_SIMT) {
+    // blocked Gauss-Jordan on [A | I] padded to bp: per panel of 16 the SIMT elimination of
+    // its columns twice (2 x 16 rank-1 updates of bp x 16 and bp x 32) and the rank-16
+    // update of the columns right of it on the tensor cores (2 bp x 16 x width flops, three
+    // products with the split operands)
+    const int bp = (bs + 15) / 16 * 16;
+    double tc = 0.0, simt = 0.0;
+    for (int k0 = 0; k0 < bp; k0 += 16) {
+      tc += 2.0 * bp * 16.0 * (2.0 * bp - k0 - 16) * (c->cfg.factor_tc == FR_FACTOR_TC_BF16X3 ? 3.0 : 1.0);
+      simt += 2.0 * 16.0 * bp * 48.0;
+    }
+    FR_ACCOUNT(c, KK_FACTOR, (tc + simt) * c->ne, 0.0);
+    FR_PROF_BEGIN(c, s);
+    if (c->cfg.prec_dtype == FR_PREC_FP64) FR_TRY(factor_tc<double>(c, (double*)c->Binv, s));
+    else if (c->cfg.prec_dtype == FR_PREC_FP32) FR_TRY(factor_tc<float>(c, (float*)c->Binv, s));
+    else FR_TRY(factor_tc<__nv_bfloat16>(c, (__nv_bfloat16*)c->Binv, s));
+    FR_PROF_END(c, s, KK_FACTOR);
+    FR_LAUNCH_CHECK(c);
+    return FR_OK;
+  }
   // in-place Gauss-Jordan: bs steps of a rank-1 update of bs^2 entries (2 flops each)
   FR_ACCOUNT(c, KK_FACTOR, 2.0 * (double)bs * bs * bs * c->ne, 0.0);
   FR_PROF_BEGIN(c, s);

@@ -47,7 +47,7 @@ class _Config(ctypes.Structure):
                 ("block_mode", ctypes.c_int), ("orthog", ctypes.c_int),
                 ("krylov_arith", ctypes.c_int), ("precond", ctypes.c_int),
                 ("mg_sweeps", ctypes.c_int), ("mg_omega", ctypes.c_double),
-                ("mg_prec", ctypes.c_int)]
+                ("mg_prec", ctypes.c_int), ("factor_tc", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -201,6 +201,7 @@ class Config:
     mg_sweeps: int = 2
     mg_omega: float = 0.7
     mg_prec: str = "fp32"
+    factor: str = "simt"
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -220,6 +221,8 @@ class Config:
                 c.block_mode = {"linearized": 0, "dual": 1}[self.block_mode]
             elif f.name == "apply_accum":
                 c.apply_accum = {"fp32": 0, "df64": 1}[self.apply_accum]
+            elif f.name == "factor":
+                c.factor_tc = {"simt": 0, "tc_bf16": 1, "tc_bf16x3": 2}[self.factor]
             elif f.name == "mg_prec":
                 c.mg_prec = PREC[self.mg_prec]
             elif f.name == "precond":
