@@ -110,8 +110,8 @@ typedef struct fr_ctx fr_ctx;
  * variable the three coefficients of c0 + c1 xi + c2 eta (reference coordinates) to the
  * solution points, and V is one multigrid V-cycle on the Galerkin operator P^T A P,
  * agglomerating 2 x 2 cells per level within each case down to at most 4 cells, which are
- * solved exactly; on each other level mg_sweeps damped block-Jacobi sweeps (12 x 12
- * blocks, damping mg_omega) before and after the correction (defaults 2 and 0.7).  The
+ * solved exactly; on each other level mg_sweeps (1 or 2) damped block-Jacobi sweeps
+ * (12 x 12 blocks, damping mg_omega) before and after the correction (defaults 2, 0.7).  The
  * coarse operators are rebuilt with the blocks (every `lag` Newton iterations) by
  * coloured products of A with the P1 functions of the elements.  mg_prec: storage and
  * sweep arithmetic of the coarse levels, FR_PREC_FP32 (default) or FR_PREC_FP64 (the

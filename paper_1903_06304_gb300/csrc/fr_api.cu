@@ -587,7 +587,7 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
       (cfg->orthog != FR_ORTHO_CGS2 && cfg->orthog != FR_ORTHO_CGS) ||
       (cfg->krylov_arith != FR_KRYLOV_FP64 && cfg->krylov_arith != FR_KRYLOV_DF64) ||
       (cfg->precond != FR_PRECOND_BLOCK && cfg->precond != FR_PRECOND_TWO_LEVEL) ||
-      cfg->mg_sweeps < 1 || cfg->mg_sweeps > 8 || !(cfg->mg_omega > 0.0 && cfg->mg_omega <= 1.5) ||
+      cfg->mg_sweeps < 1 || cfg->mg_sweeps > 2 || !(cfg->mg_omega > 0.0 && cfg->mg_omega <= 1.5) ||
       (cfg->mg_prec != FR_PREC_FP64 && cfg->mg_prec != FR_PREC_FP32) ||
       cfg->factor_tc < FR_FACTOR_SIMT || cfg->factor_tc > FR_FACTOR_TC_BF16X3)
     return FR_ERR_ARG;

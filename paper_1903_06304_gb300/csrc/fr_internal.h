@@ -79,6 +79,9 @@ struct MgLevel {
   void *Ainv = nullptr;       // [nfin][48][48] dense inverses (row-major, count*12 used)
   int ntail = 0;              // cases whose single-block kernel starts at this level
   int *tail = nullptr;        // [ntail] their case indices
+  int ntiles = 0;             // tiles of the tiled kernels on this level
+  void *tiles = nullptr;      // [ntiles] (case, first column, first row)
+  void *cl = nullptr;         // [ncases] each case's grid on this level
 };
 
 // Kernel classes for the optional per-kernel timing (fr_profile) and launch counts.

@@ -21,11 +21,12 @@
 // Layout for GB300: the coarse levels are stored and swept in the configured coarse
 // precision (FP32 by default: a coarse sweep is 72 multiply-adds per coefficient, which
 // the FP64 pipe -- 2 FMA per clock per SM -- would make the largest cost of an iteration;
-// the build arithmetic stays FP64).  Levels with more than TAIL cells of a case run as one
-// launch per sweep over all SMs (16 cells per block, a cell's residual staged in shared
-// memory for its 12 x 12 inverse); the remaining small levels of each case, with the dense
-// solve, run in one block per case, the phases separated by block barriers, so that the
-// latency of a launch is paid once instead of once per phase.
+// the build arithmetic stays FP64).  Levels with more than TAIL cells of a case run in
+// tiles over all SMs, two launches per level and cycle (sweeps, residual and restriction
+// on the way down; prolongation and sweeps on the way up), each block recomputing the
+// halo its sweeps need; the remaining small levels of each case, with the dense solve, run
+// in one block per case, the phases separated by block barriers.  A cycle thus costs
+// 2 L + 3 launches for L tiled levels, whatever the number of sweeps.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -39,8 +40,7 @@ constexpr int SL = 5;           // stencil slots per cell (self + 4 neighbours)
 constexpr int BLK = NB * NB;    // entries of one 12 x 12 block
 constexpr int MAXFIN = 4;       // cells of a case solved exactly
 constexpr int DN = MAXFIN * NB; // leading dimension of the dense inverses
-constexpr int CPB = 16;         // cells per block of the multi-block kernels
-constexpr int TAIL = 64;        // levels of a case with at most this many cells: one block
+constexpr int TAIL = 16;        // levels of a case with at most this many cells: one block
 constexpr int TAIL_THREADS = 256;
 
 // Reference-coordinate basis value of mode m (1, xi, eta) at point (i, j).
@@ -150,76 +150,220 @@ __global__ void k_p1_prolong(fr::Mesh mesh, fr::Basis B, const S* __restrict__ x
 }
 
 // ---------------------------------------------------------------- multi-block levels
-// One damped block-Jacobi sweep on the cells this level sweeps (mode 1):
-// xo = xi + omega D^-1 (b - A xi); the first sweep starts from xi = 0 (xo = omega D^-1 b).
-// The other cells copy their value through (xi may equal xo on the first sweep: each
-// thread then reads and writes only its own entry).
-template <class S>
-__global__ void __launch_bounds__(CPB * NB) k_mg_smooth(Lv<S> L, const S* xi, S* xo, S omega, int first) {
-  __shared__ S res[CPB][NB];
-  const int lc = threadIdx.x / NB, r = threadIdx.x % NB;
-  const int c = blockIdx.x * CPB + lc;
-  const bool in = c < L.nc;
-  const bool sw = in && L.mode[c] == 1;
-  if (sw) res[lc][r] = L.b[(size_t)c * NB + r] - (first ? S(0) : row_product(L, c, r, xi));
-  __syncthreads();
-  if (!in) return;
-  if (!sw) {
-    xo[(size_t)c * NB + r] = xi[(size_t)c * NB + r];
-    return;
+// A level of a case with more than TAIL cells (and at least 3 in each direction, so that a
+// cell's four neighbours are distinct) runs in tiles of TX x TX cells, one block per tile
+// with one thread per row of every cell of the tile and its halo, two launches per V-cycle:
+//   down: the NU smoothing sweeps, the residual and the restriction to the parents;
+//   up:   the prolongation of the parents' correction and the NU smoothing sweeps.
+// A Jacobi sweep reads the neighbours' previous values, so each block recomputes a halo of
+// NU cells around its tile (each sweep one cell less), in shared memory, instead of
+// waiting for the other blocks: identical arithmetic on every copy, one launch per phase
+// group instead of one per sweep.  The down pass writes the smoothed values to x and the
+// parents' right-hand sides; the up pass reads x and the parents' results and writes the
+// level's result to y (a block never reads what another block of the same launch writes).
+constexpr int TX = 4;   // tile side: (TX + 2 NU)^2 x 12 threads, one per region row
+
+struct CaseLevel {
+  int nx, ny, off, bounded;
+};
+
+// Global cell at tile position (a, b) of a region with halo h: -1 outside a bounded mesh.
+__device__ __forceinline__ int region_cell(const CaseLevel& g, int i0, int j0, int h, int a, int b) {
+  int i = i0 - h + a, j = j0 - h + b;
+  i = ((i % g.nx) + g.nx) % g.nx;
+  if (g.bounded) {
+    if (j < 0 || j >= g.ny) return -1;
+  } else {
+    j = ((j % g.ny) + g.ny) % g.ny;
   }
-  const S* d = L.Dinv + ((size_t)c * NB + r) * NB;
-  S acc = S(0);
+  return g.off + j * g.nx + i;
+}
+
+// Stencil slot of direction d (0 self, 1 left, 2 right, 3 below, 4 above) of a cell in row
+// j: the slots list the distinct members in this order with absent ones left out.
+__device__ __forceinline__ int dir_slot(const CaseLevel& g, int j, int d) {
+  if (d < 3) return d;
+  const bool below = !g.bounded || j > 0;
+  const bool above = !g.bounded || j < g.ny - 1;
+  if (d == 3) return below ? 3 : -1;
+  return above ? (below ? 4 : 3) : -1;
+}
+
+// r-th row of b - A x at region position (a, b) (cell c, row j of its case) with the
+// neighbours' values in the region array xs (stride RX).
+template <class S, int RX>
+__device__ __forceinline__ S region_residual(const Lv<S>& L, const CaseLevel& g, int c, int j, int a, int bb,
+                                             int r, const S* bs, const S (*xs)[NB]) {
+  const int da[5] = {0, -1, 1, 0, 0}, db[5] = {0, 0, 0, -1, 1};
+  S acc = bs[r];
 #pragma unroll
-  for (int k = 0; k < NB; ++k) acc = fma(d[k], res[lc][k], acc);
-  xo[(size_t)c * NB + r] = (first ? S(0) : xi[(size_t)c * NB + r]) + omega * acc;
-}
-
-// b_next = Q^T (b - A x) over each coarse cell's children (fixed child order), for the
-// coarse cells whose children this level sweeps: 48 threads per coarse cell compute the
-// children's residual rows, 12 of them then sum the transposed transfer.
-template <class S>
-__global__ void __launch_bounds__(4 * 4 * NB) k_mg_resid_restrict(Lv<S> L, const S* __restrict__ x,
-                                                                 int nc_next, S* __restrict__ bn) {
-  constexpr int CELLS = 4;   // coarse cells per block
-  __shared__ S res[CELLS][4][NB];
-  const int lc = threadIdx.x / (4 * NB), q = (threadIdx.x / NB) % 4, r = threadIdx.x % NB;
-  const int I = blockIdx.x * CELLS + lc;
-  int ch = -1;
-  if (I < nc_next) ch = L.children[I * 4 + q];
-  const bool act = ch >= 0 && L.mode[ch] == 1;
-  res[lc][q][r] = act ? L.b[(size_t)ch * NB + r] - row_product(L, ch, r, x) : S(0);
-  __syncthreads();
-  if (I >= nc_next || q != 0) return;
-  // only coarse cells whose children are swept here are written (the others belong to a
-  // case handled by its own single-block kernel)
-  const int c0 = L.children[I * 4];
-  if (c0 < 0 || L.mode[c0] != 1) return;
-  const int v = r / 3, m = r % 3;
-  double acc = 0.0;
-  for (int qq = 0; qq < 4; ++qq) {
-    const int c = L.children[I * 4 + qq];
-    if (c < 0) continue;
-    const double* o = L.qo + (size_t)c * 4;
-    for (int a = 0; a < 3; ++a) acc = fma(qmap(o, a, m), (double)res[lc][qq][3 * v + a], acc);
+  for (int d = 0; d < 5; ++d) {
+    const int s = dir_slot(g, j, d);
+    if (s < 0) continue;
+    const S* arow = L.A + (((size_t)c * SL + s) * NB + r) * NB;
+    const S* xn = xs[(bb + db[d]) * RX + a + da[d]];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc = fma(-arow[k], xn[k], acc);
   }
-  bn[(size_t)I * NB + r] = (S)acc;
+  return acc;
 }
 
-// x += Q x_next on the swept cells
-template <class S>
-__global__ void k_mg_prolong(Lv<S> L, const S* __restrict__ xn, S* __restrict__ x) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)L.nc * NB) return;
-  const int c = (int)(t / NB), r = (int)(t % NB);
-  if (L.mode[c] != 1) return;
-  const int P = L.parent[c];
-  const int v = r / 3, a = r % 3;
-  const double* o = L.qo + (size_t)c * 4;
-  const S* X = xn + (size_t)P * NB + 3 * v;
-  double acc = 0.0;
-  for (int m = 0; m < 3; ++m) acc = fma(qmap(o, a, m), (double)X[m], acc);
-  x[t] += (S)acc;
+struct Tile {
+  int k, i0, j0, pad;
+};
+
+// Dynamic shared memory of the tiled kernels: four region arrays of 12 coefficients and
+// the region's cell indices.
+template <class S, int NU>
+constexpr size_t tile_smem() {
+  return (size_t)4 * (TX + 2 * NU) * (TX + 2 * NU) * NB * sizeof(S) + (size_t)(TX + 2 * NU) * (TX + 2 * NU) * sizeof(int);
+}
+
+template <class S, int NU>
+__global__ void __launch_bounds__((TX + 2 * NU) * (TX + 2 * NU) * NB) k_mg_down(Lv<S> L, const CaseLevel* __restrict__ cl, const Tile* __restrict__ tiles,
+                                                 S omega, S* __restrict__ bn) {
+  constexpr int RX = TX + 2 * NU, RN = RX * RX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S (*sb)[NB] = reinterpret_cast<S (*)[NB]>(smem_raw);
+  S (*x0)[NB] = sb + RN;
+  S (*x1)[NB] = x0 + RN;
+  S (*res)[NB] = x1 + RN;
+  int* cell = reinterpret_cast<int*>(res + RN);
+  const Tile T = tiles[blockIdx.x];
+  const CaseLevel g = cl[T.k];
+  for (int p = threadIdx.x; p < RN; p += blockDim.x) cell[p] = region_cell(g, T.i0, T.j0, NU, p % RX, p / RX);
+  __syncthreads();
+  for (int t = threadIdx.x; t < RN * NB; t += blockDim.x) {
+    const int p = t / NB, r = t % NB, c = cell[p];
+    sb[p][r] = c >= 0 ? L.b[(size_t)c * NB + r] : S(0);
+  }
+  __syncthreads();
+  // sweep 1 from zero: x = omega D^-1 b on the whole region
+  for (int t = threadIdx.x; t < RN * NB; t += blockDim.x) {
+    const int p = t / NB, r = t % NB, c = cell[p];
+    S acc = S(0);
+    if (c >= 0) {
+      const S* d = L.Dinv + ((size_t)c * NB + r) * NB;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) acc = fma(d[k], sb[p][k], acc);
+    }
+    x0[p][r] = omega * acc;
+  }
+  __syncthreads();
+  S (*cur)[NB] = x0;
+  S (*nxt)[NB] = x1;
+  for (int sw = 1; sw < NU; ++sw) {
+    // residual on the positions at least sw cells inside the region, then the update
+    for (int t = threadIdx.x; t < RN * NB; t += blockDim.x) {
+      const int p = t / NB, r = t % NB, a = p % RX, b = p / RX, c = cell[p];
+      if (a < sw || a >= RX - sw || b < sw || b >= RX - sw || c < 0) continue;
+      const int j = (c - g.off) / g.nx;
+      res[p][r] = region_residual<S, RX>(L, g, c, j, a, b, r, sb[p], cur);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < RN * NB; t += blockDim.x) {
+      const int p = t / NB, r = t % NB, a = p % RX, b = p / RX, c = cell[p];
+      if (a < sw || a >= RX - sw || b < sw || b >= RX - sw || c < 0) continue;
+      const S* d = L.Dinv + ((size_t)c * NB + r) * NB;
+      S acc = S(0);
+#pragma unroll
+      for (int k = 0; k < NB; ++k) acc = fma(d[k], res[p][k], acc);
+      nxt[p][r] = cur[p][r] + omega * acc;
+    }
+    __syncthreads();
+    S (*tmp)[NB] = cur; cur = nxt; nxt = tmp;
+  }
+  // residual and smoothed values on the tile's own cells
+  for (int t = threadIdx.x; t < TX * TX * NB; t += blockDim.x) {
+    const int q = t / NB, r = t % NB, a = NU + q % TX, b = NU + q / TX, p = b * RX + a;
+    const int i = T.i0 + q % TX, jj = T.j0 + q / TX, c = cell[p];
+    if (i >= g.nx || jj >= g.ny || c < 0) continue;
+    res[p][r] = region_residual<S, RX>(L, g, c, jj, a, b, r, sb[p], cur);
+    L.x[(size_t)c * NB + r] = cur[p][r];
+  }
+  __syncthreads();
+  // restriction to the parents of the tile (tiles start at even cells and have an even
+  // side: a parent's children are all in its tile)
+  constexpr int PX = TX / 2;
+  for (int t = threadIdx.x; t < PX * PX * NB; t += blockDim.x) {
+    const int q = t / NB, r = t % NB;
+    const int i = T.i0 + 2 * (q % PX), jj = T.j0 + 2 * (q / PX);
+    if (i >= g.nx || jj >= g.ny) continue;
+    const int c00 = g.off + jj * g.nx + i;
+    const int P = L.parent[c00];
+    const int v = r / 3, m = r % 3;
+    double acc = 0.0;
+    for (int qq = 0; qq < 4; ++qq) {
+      const int ch = L.children[P * 4 + qq];
+      if (ch < 0) continue;
+      const int ci = (ch - g.off) % g.nx, cj = (ch - g.off) / g.nx;
+      const int p = (cj - T.j0 + NU) * RX + (ci - T.i0 + NU);
+      const double* o = L.qo + (size_t)ch * 4;
+      for (int a = 0; a < 3; ++a) acc = fma(qmap(o, a, m), (double)res[p][3 * v + a], acc);
+    }
+    bn[(size_t)P * NB + r] = (S)acc;
+  }
+}
+
+template <class S, int NU>
+__global__ void __launch_bounds__((TX + 2 * NU) * (TX + 2 * NU) * NB) k_mg_up(Lv<S> L, const CaseLevel* __restrict__ cl, const Tile* __restrict__ tiles,
+                                               S omega, const S* __restrict__ xp) {
+  constexpr int RX = TX + 2 * NU, RN = RX * RX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S (*sb)[NB] = reinterpret_cast<S (*)[NB]>(smem_raw);
+  S (*x0)[NB] = sb + RN;
+  S (*x1)[NB] = x0 + RN;
+  S (*res)[NB] = x1 + RN;
+  int* cell = reinterpret_cast<int*>(res + RN);
+  const Tile T = tiles[blockIdx.x];
+  const CaseLevel g = cl[T.k];
+  for (int p = threadIdx.x; p < RN; p += blockDim.x) cell[p] = region_cell(g, T.i0, T.j0, NU, p % RX, p / RX);
+  __syncthreads();
+  // the smoothed values plus the parents' correction, on the whole region
+  for (int t = threadIdx.x; t < RN * NB; t += blockDim.x) {
+    const int p = t / NB, r = t % NB, c = cell[p];
+    S val = S(0), bv = S(0);
+    if (c >= 0) {
+      const int v = r / 3, a = r % 3;
+      const double* o = L.qo + (size_t)c * 4;
+      const S* X = xp + (size_t)L.parent[c] * NB + 3 * v;
+      double acc = 0.0;
+      for (int m = 0; m < 3; ++m) acc = fma(qmap(o, a, m), (double)X[m], acc);
+      val = L.x[(size_t)c * NB + r] + (S)acc;
+      bv = L.b[(size_t)c * NB + r];
+    }
+    x0[p][r] = val;
+    sb[p][r] = bv;
+  }
+  __syncthreads();
+  S (*cur)[NB] = x0;
+  S (*nxt)[NB] = x1;
+  for (int sw = 1; sw <= NU; ++sw) {
+    for (int t = threadIdx.x; t < RN * NB; t += blockDim.x) {
+      const int p = t / NB, r = t % NB, a = p % RX, b = p / RX, c = cell[p];
+      if (a < sw || a >= RX - sw || b < sw || b >= RX - sw || c < 0) continue;
+      const int j = (c - g.off) / g.nx;
+      res[p][r] = region_residual<S, RX>(L, g, c, j, a, b, r, sb[p], cur);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < RN * NB; t += blockDim.x) {
+      const int p = t / NB, r = t % NB, a = p % RX, b = p / RX, c = cell[p];
+      if (a < sw || a >= RX - sw || b < sw || b >= RX - sw || c < 0) continue;
+      const S* d = L.Dinv + ((size_t)c * NB + r) * NB;
+      S acc = S(0);
+#pragma unroll
+      for (int k = 0; k < NB; ++k) acc = fma(d[k], res[p][k], acc);
+      nxt[p][r] = cur[p][r] + omega * acc;
+    }
+    __syncthreads();
+    S (*tmp)[NB] = cur; cur = nxt; nxt = tmp;
+  }
+  for (int t = threadIdx.x; t < TX * TX * NB; t += blockDim.x) {
+    const int q = t / NB, r = t % NB, a = NU + q % TX, b = NU + q / TX, p = b * RX + a;
+    const int i = T.i0 + q % TX, jj = T.j0 + q / TX, c = cell[p];
+    if (i >= g.nx || jj >= g.ny || c < 0) continue;
+    L.y[(size_t)c * NB + r] = cur[p][r];
+  }
 }
 
 // ---------------------------------------------------------------- single-block tail
@@ -308,6 +452,13 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(const Lv<S>* __restric
     }
     __syncthreads();
     for (int it = 0; it < nu; ++it) tail_sweep(L, off, cnt, omega, false);
+  }
+  // the result of the first level of the tail goes to y, where the tiled levels and the
+  // prolongation to the solution points read each level's result
+  {
+    const Lv<S> L = lev[T.lev0];
+    for (int t = threadIdx.x; t < T.cnt[T.lev0] * NB; t += blockDim.x)
+      L.y[(size_t)T.off[T.lev0] * NB + t] = L.x[(size_t)T.off[T.lev0] * NB + t];
   }
 }
 
@@ -569,7 +720,7 @@ int fine_transfer(fr_ctx* c, const double* r, double* z0, cudaStream_t s, bool d
   if (down)
     k_p1_restrict<N, S><<<blocks_for((long long)c->ne * NB, 256), 256, 0, s>>>(c->mesh, c->basis, r, (S*)c->mg[0].b);
   else
-    k_p1_prolong<N, S><<<blocks_for((long long)c->ne * NP, 256), 256, 0, s>>>(c->mesh, c->basis, (const S*)c->mg[0].x, z0);
+    k_p1_prolong<N, S><<<blocks_for((long long)c->ne * NP, 256), 256, 0, s>>>(c->mesh, c->basis, (const S*)c->mg[0].y, z0);
   FR_PROF_END(c, s, KK_COARSE);
   FR_LAUNCH_CHECK(c);
   FR_ACCOUNT(c, KK_COARSE, 2.0 * NB * c->ne * NP / (down ? 1.0 : 4.0),
@@ -587,55 +738,51 @@ int launch_tail(fr_ctx* c, const MgLevel& L, cudaStream_t s) {
   return FR_OK;
 }
 
-// One V-cycle from level l over the cells the multi-block kernels sweep there (b_l given,
-// the result in x_l); the cases whose single-block tail starts at level l+1 run theirs
-// between the restriction and the prolongation.
-template <class S>
-int vcycle(fr_ctx* c, size_t l, cudaStream_t s) {
-  MgLevel& L = c->mg[l];
-  if (l == 0 && L.ntail > 0) FR_TRY(launch_tail<S>(c, L, s));   // cases that are small throughout
-  if (L.nsweep == 0) return FR_OK;
-  const Lv<S> V = view<S>(L);
-  MgLevel& Nx = c->mg[l + 1];
-  const int nu = c->cfg.mg_sweeps;
+// One V-cycle: the tails of the cases that are small from level 0 on, then per tiled level
+// the down pass (and the tails of the cases whose single-block part starts below it), then
+// the up passes in reverse order; every level's result ends in y.
+template <class S, int NU>
+int vcycle_n(fr_ctx* c, cudaStream_t s) {
   const S om = (S)c->cfg.mg_omega;
-  const unsigned gs = blocks_for(L.nc, CPB);
-  S* cur = (S*)L.x;
-  S* oth = (S*)L.y;
-  for (int it = 0; it < nu; ++it) {
+  if (tile_smem<S, NU>() > 48 * 1024) {
+    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_mg_down<S, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<S, NU>()));
+    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_mg_up<S, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<S, NU>()));
+  }
+  if (c->mg[0].ntail > 0) FR_TRY(launch_tail<S>(c, c->mg[0], s));
+  size_t ltop = 0;
+  while (ltop < c->mg.size() && c->mg[ltop].ntiles > 0) ++ltop;
+  for (size_t l = 0; l < ltop; ++l) {
+    MgLevel& L = c->mg[l];
+    MgLevel& Nx = c->mg[l + 1];
+    {
+      FR_PROF_BEGIN(c, s);
+      k_mg_down<S, NU><<<L.ntiles, (TX + 2 * NU) * (TX + 2 * NU) * NB, tile_smem<S, NU>(), s>>>(view<S>(L), (const CaseLevel*)L.cl, (const Tile*)L.tiles, om, (S*)Nx.b);
+      FR_PROF_END(c, s, KK_COARSE);
+      FR_LAUNCH_CHECK(c);
+    }
+    if (Nx.ntail > 0) FR_TRY(launch_tail<S>(c, Nx, s));
+  }
+  for (size_t l = ltop; l-- > 0;) {
+    MgLevel& L = c->mg[l];
+    MgLevel& Nx = c->mg[l + 1];
     FR_PROF_BEGIN(c, s);
-    k_mg_smooth<S><<<gs, CPB * NB, 0, s>>>(V, cur, it == 0 ? cur : oth, om, it == 0);
+    k_mg_up<S, NU><<<L.ntiles, (TX + 2 * NU) * (TX + 2 * NU) * NB, tile_smem<S, NU>(), s>>>(view<S>(L), (const CaseLevel*)L.cl, (const Tile*)L.tiles, om, (const S*)Nx.y);
     FR_PROF_END(c, s, KK_COARSE);
     FR_LAUNCH_CHECK(c);
-    if (it > 0) std::swap(cur, oth);
   }
-  {
-    FR_PROF_BEGIN(c, s);
-    k_mg_resid_restrict<S><<<blocks_for(Nx.nc, 4), 4 * 4 * NB, 0, s>>>(V, cur, Nx.nc, (S*)Nx.b);
-    FR_PROF_END(c, s, KK_COARSE);
-    FR_LAUNCH_CHECK(c);
+  for (size_t l = 0; l < ltop; ++l) {
+    const MgLevel& L = c->mg[l];
+    const double cells = (double)L.nsweep;
+    // per cycle and cell: (2 NU + 1) residual rows of 5 blocks and 2 NU inverse rows of 12
+    FR_ACCOUNT(c, KK_COARSE, cells * NB * 2.0 * ((2.0 * NU + 1.0) * SL * NB + 2.0 * NU * NB),
+               (double)sizeof(S) * cells * ((2.0 * NU + 1.0) * SL * BLK + 2.0 * NU * BLK));
   }
-  if (Nx.ntail > 0) FR_TRY(launch_tail<S>(c, Nx, s));
-  FR_TRY(vcycle<S>(c, l + 1, s));
-  {
-    FR_PROF_BEGIN(c, s);
-    k_mg_prolong<S><<<blocks_for((long long)L.nc * NB, 256), 256, 0, s>>>(V, (const S*)Nx.x, cur);
-    FR_PROF_END(c, s, KK_COARSE);
-    FR_LAUNCH_CHECK(c);
-  }
-  for (int it = 0; it < nu; ++it) {
-    FR_PROF_BEGIN(c, s);
-    k_mg_smooth<S><<<gs, CPB * NB, 0, s>>>(V, cur, oth, om, 0);
-    FR_PROF_END(c, s, KK_COARSE);
-    FR_LAUNCH_CHECK(c);
-    std::swap(cur, oth);
-  }
-  if (cur != (S*)L.x)
-    FR_CUDA_CHECK(c, cudaMemcpyAsync(L.x, cur, (size_t)L.nc * NB * sizeof(S), cudaMemcpyDeviceToDevice, s));
-  const double rows = (double)L.nsweep * NB;
-  FR_ACCOUNT(c, KK_COARSE, rows * 2.0 * (SL * NB + NB) * (2.0 * nu + 1.0),
-             (double)sizeof(S) * L.nsweep * (SL * BLK + BLK) * (2.0 * nu + 1.0));
   return FR_OK;
+}
+
+template <class S>
+int vcycle(fr_ctx* c, cudaStream_t s) {
+  return c->cfg.mg_sweeps == 1 ? vcycle_n<S, 1>(c, s) : vcycle_n<S, 2>(c, s);
 }
 
 template <class S>
@@ -650,7 +797,7 @@ int apply_t(fr_ctx* c, const double* q, const double* r, double* z, double inv_d
     default: return FR_ERR_ARG;
   }
   if (rc != FR_OK) return rc;
-  FR_TRY(vcycle<S>(c, 0, s));
+  FR_TRY(vcycle<S>(c, s));
   switch (c->n) {
     case 2: rc = fine_transfer<2, S>(c, nullptr, c->mg_z0, s, false); break;
     case 3: rc = fine_transfer<3, S>(c, nullptr, c->mg_z0, s, false); break;
@@ -679,7 +826,7 @@ void mg_free(fr_ctx* c) {
   for (MgLevel& l : c->mg) {
     int* is[] = {l.nb, l.cell_case, l.parent, l.children, l.gslot, l.fin, l.mode, l.tail};
     for (int* p : is) if (p) cudaFree(p);
-    void* vs[] = {l.A, l.Dinv, l.x, l.y, l.b, l.Ainv};
+    void* vs[] = {l.A, l.Dinv, l.x, l.y, l.b, l.Ainv, l.tiles, l.cl};
     for (void* p : vs) if (p) cudaFree(p);
     if (l.qo) cudaFree(l.qo);
   }
@@ -717,6 +864,8 @@ int mg_setup(fr_ctx* c) {
   std::vector<std::vector<int>> h_nb, h_case, h_parent, h_children, h_gslot, h_fin, h_mode, h_tail;
   std::vector<std::vector<double>> h_qo;
   std::vector<int> h_nsweep;
+  std::vector<std::vector<Tile>> h_tiles;
+  std::vector<std::vector<CaseLevel>> h_cls;
   while (true) {
     const int lev = (int)h_nb.size();
     int nc = 0;
@@ -725,6 +874,8 @@ int mg_setup(fr_ctx* c) {
     if (lev >= 16) { snprintf(c->err, sizeof(c->err), "two-level set-up: too many levels"); return FR_ERR_ARG; }
     std::vector<int> nb((size_t)nc * SL), cs(nc), parent(nc, -1), gsl((size_t)nc * SL, -1), fin;
     std::vector<int> mode(nc, 0), tail;
+    std::vector<Tile> tiles;
+    std::vector<CaseLevel> cls(c->ncases, CaseLevel{0, 0, 0, 0});
     std::vector<double> qo((size_t)nc * 4, 0.0);
     std::vector<CaseGrid> next(c->ncases);
     int noff = 0, nsweep = 0;
@@ -736,7 +887,7 @@ int mg_setup(fr_ctx* c) {
       T.off[lev] = g.off;
       T.cnt[lev] = cnt;
       T.nlev = lev + 1;
-      if (cnt <= TAIL && T.lev0 < 0) { T.lev0 = lev; tail.push_back(k); }
+      if ((cnt <= TAIL || g.nx < 3 || g.ny < 3) && T.lev0 < 0) { T.lev0 = lev; tail.push_back(k); }
       if (cnt <= MAXFIN) {
         T.fin = (int)fin.size() / 2;
         fin.push_back(g.off);
@@ -751,6 +902,10 @@ int mg_setup(fr_ctx* c) {
       const CaseGrid& g = grids[k];
       const bool cont = g.nx * g.ny > MAXFIN;
       const bool swept = tcs[k].lev0 < 0;   // not yet in the case's single-block kernel
+      cls[k] = CaseLevel{g.nx, g.ny, g.off, bounded ? 1 : 0};
+      if (swept)
+        for (int j0 = 0; j0 < g.ny; j0 += TX)
+          for (int i0 = 0; i0 < g.nx; i0 += TX) tiles.push_back(Tile{k, i0, j0, 0});
       for (int j = 0; j < g.ny; ++j) {
         for (int i = 0; i < g.nx; ++i) {
           const int cell = g.off + j * g.nx + i;
@@ -782,6 +937,8 @@ int mg_setup(fr_ctx* c) {
     h_mode.push_back(mode);
     h_tail.push_back(tail);
     h_nsweep.push_back(nsweep);
+    h_tiles.push_back(tiles);
+    h_cls.push_back(cls);
     for (int k = 0; k < c->ncases; ++k) {
       if (done[k]) continue;
       if (grids[k].nx * grids[k].ny <= MAXFIN) done[k] = 1;
@@ -830,6 +987,13 @@ int mg_setup(fr_ctx* c) {
     FR_TRY(upload(c, &L.fin, h_fin[l]));
     FR_TRY(upload(c, &L.mode, h_mode[l]));
     FR_TRY(upload(c, &L.tail, h_tail[l]));
+    L.ntiles = (int)h_tiles[l].size();
+    if (L.ntiles > 0) {
+      FR_CUDA_CHECK(c, cudaMalloc(&L.tiles, h_tiles[l].size() * sizeof(Tile)));
+      FR_CUDA_CHECK(c, cudaMemcpy(L.tiles, h_tiles[l].data(), h_tiles[l].size() * sizeof(Tile), cudaMemcpyHostToDevice));
+    }
+    FR_CUDA_CHECK(c, cudaMalloc(&L.cl, h_cls[l].size() * sizeof(CaseLevel)));
+    FR_CUDA_CHECK(c, cudaMemcpy(L.cl, h_cls[l].data(), h_cls[l].size() * sizeof(CaseLevel), cudaMemcpyHostToDevice));
     const size_t n12 = (size_t)L.nc * NB;
     void** bufs[] = {&L.A, &L.Dinv, &L.x, &L.y, &L.b, &L.Ainv};
     const size_t counts[] = {n12 * SL * NB, n12 * NB, n12, n12, n12, (size_t)L.nfin * DN * DN};
