@@ -873,7 +873,7 @@ def batch_arm(args):
     cfg = fr.Config(prec=args.prec, restart=args.restart, maxit_lin=args.maxit_lin,
                     maxit_newton=args.maxit_newton, lag=2, line_search=args.line_search,
                     graphs=args.graphs, apply_accum=args.apply_accum,
-                    krylov_arith=args.krylov_arith)
+                    krylov_arith=args.krylov_arith, precond=args.precond)
     B = fr.Batch(cfg, cases)
     corners = np.zeros((B.ne, 4, 2))
     q = np.zeros(B.ndof)
@@ -946,7 +946,8 @@ def batch_arm(args):
            "config": {"workload": f"batch of {len(all_cs)} cases (seed 0)", "cases": len(all_cs),
                       "cases_rank0": len(cs), "groups_rank0": B.num_groups, "dof": sum(dof_all),
                       "elements": sum(c.n * c.n for c in all_cs),
-                      "prec": args.prec, "restart": args.restart, "maxit_lin": args.maxit_lin,
+                      "prec": args.prec, "precond": args.precond, "restart": args.restart,
+                      "maxit_lin": args.maxit_lin,
                       "maxit_newton": args.maxit_newton, "line_search": args.line_search,
                       "graphs": args.graphs, "l2": "256 MiB flush between steps",
                       "parallelism": f"cases sharded over {world} ranks" if world > 1 else "single"},
