@@ -458,6 +458,44 @@ def low_mach_deforming_report(args, torch, fr, inp, T, flush):
     return out
 
 
+def steady_ptc_study(args, torch, fr, inp, T):
+    """Steady pseudo-transient continuation with SER (Eqs. steady_pre_discretized_1, SER)
+    on a cylinder O-grid, the kind of study of Sec. 4.1 with a viscous body (the paper's
+    inviscid slip-wall cylinder needs a wall condition not built here): 64 x 32 cells to 20
+    diameters, p = 2, M = 0.1, Re = 20 on the diameter, impulsively started free stream,
+    PTC to Res_m/Res_0 <= 1e-8 with GMRES(100); per variant the pseudo steps, GMRES
+    iterations, wall time, final drop and drag coefficient C_d = F_x / (rho U^2 D / 2):
+    tol_res 1e-3 / 1e-6 / 1e-9, the SER cap dtau_max 1e20 / 100 / 10, and kappa 1 / sqrt 5 / 3."""
+    ni, nj, p, mach, re = 64, 32, 2, 0.1, 20.0
+    c = inp.cylinder_ogrid(ni, nj, 20.0, 1e-2)
+    v = 0.0 * c
+    qi = inp.far_field_state(mach)
+    q0 = inp.uniform_state(ni * nj, p, mach)
+    base = dict(p=p, mach=mach, re=re, kappa=1.0, restart=100, maxit_lin=300, tol_res=1e-6,
+                tol_pseudo=1e-8, maxit_newton=64, precond=args.precond, prec=args.prec)
+    variants = [("tol_res=1e-3", {"tol_res": 1e-3}), ("tol_res=1e-6", {}), ("tol_res=1e-9", {"tol_res": 1e-9}),
+                ("dtau_max=100", {"dtau_max": 100.0}), ("dtau_max=10", {"dtau_max": 10.0}),
+                ("kappa=sqrt5", {"kappa": 5 ** 0.5}), ("kappa=3", {"kappa": 3.0})]
+    out = {"workload": f"cylinder O-grid {ni}x{nj} p={p} M={mach} Re={re} (wall + far field)",
+           "dof": 4 * ni * nj * (p + 1) ** 2}
+    for name, over in variants:
+        S = fr.Solver(fr.Config(**{**base, **over}), ni, nj, bc=("wall", "farfield"), q_inf=qi)
+        S.update_mesh(T(c), T(v))
+        q = T(q0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = S.ptc_solve(q, allow_unconverged=True).summary()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        fx, _fy = S.wall_force(q)
+        h = st["res_history"]
+        out[name] = {"converged": st["converged"], "pseudo_steps": st["newton_iterations"],
+                     "gmres_total": sum(st["gmres_iterations"]), "seconds": t1 - t0,
+                     "res_drop": h[-1] / h[0], "c_d": 2.0 * fx}
+        S.close()
+    return out
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -737,6 +775,9 @@ def gpu_arm(args):
     low_mach = None
     if rank == 0 and not args.no_c3:
         low_mach = low_mach_deforming_report(args, torch, fr, inp, T, flush)
+    ptc = None
+    if rank == 0 and not args.no_ptc:
+        ptc = steady_ptc_study(args, torch, fr, inp, T)
 
     # ---- CPU baseline (rank 0, N = 1 only): the oracle's unit costs priced with the
     # timed steps' own counts
@@ -794,6 +835,7 @@ def gpu_arm(args):
         "precision_compare": compare,
         "block_factor_ms": factor_ms,
         "low_mach_deforming": low_mach,
+        "steady_ptc_cylinder": ptc,
         "kernels": kernels,
         "kernels_same_steps": same_steps,
         "roofline": roof,
@@ -972,6 +1014,8 @@ def main():
                     help="element block Jacobi, or with the P1 coarse correction")
     ap.add_argument("--no-c3", dest="no_c3", action="store_true",
                     help="skip the deforming 128x128 M = 0.01 report")
+    ap.add_argument("--no-ptc", dest="no_ptc", action="store_true",
+                    help="skip the steady PTC study on the cylinder O-grid")
     ap.add_argument("--c3-steps", dest="c3_steps", type=int, default=3)
     ap.add_argument("--c3-newton", dest="c3_newton", type=int, default=10)
     ap.add_argument("--restart", type=int, default=30)

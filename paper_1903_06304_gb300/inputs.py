@@ -124,6 +124,26 @@ def naca_ogrid(ni: int = 256, nj: int = 96, r_far: float = 20.0, first: float = 
     return c.reshape(ni * nj, 4, 2)
 
 
+def cylinder_ogrid(ni: int = 64, nj: int = 32, r_far: float = 20.0, first: float = 1e-2) -> np.ndarray:
+    """Corners ``[ni*nj, 4, 2]`` of an O-grid around a circular cylinder of diameter 1
+    centred at the origin (the body of Sec. 4.1): element e = j*ni + i, i around the body
+    clockwise (periodic), j from the wall (row 0) to a circle of radius ``r_far`` diameters;
+    straight radial lines with a geometric distribution whose first cell is ``first``
+    diameters, equal angles around the body."""
+    ang = -2.0 * math.pi * np.arange(ni) / ni
+    r = _stretch_ratio(nj, first, r_far - 0.5)
+    rad = 0.5 + (r_far - 0.5) * (r ** np.arange(nj + 1) - 1.0) / (r ** nj - 1.0)   # [nj+1]
+    X = rad[:, None] * np.cos(ang)[None, :]
+    Y = rad[:, None] * np.sin(ang)[None, :]
+    ip = (np.arange(ni) + 1) % ni
+    c = np.empty((nj, ni, 4, 2))
+    c[:, :, 0, 0], c[:, :, 0, 1] = X[:-1, :], Y[:-1, :]
+    c[:, :, 1, 0], c[:, :, 1, 1] = X[:-1, ip], Y[:-1, ip]
+    c[:, :, 2, 0], c[:, :, 2, 1] = X[1:, ip], Y[1:, ip]
+    c[:, :, 3, 0], c[:, :, 3, 1] = X[1:, :], Y[1:, :]
+    return c.reshape(ni * nj, 4, 2)
+
+
 def plunge(ref_corners: np.ndarray, t: float, h: float = 0.25, k: float = 1.0):
     """Rigid plunge of Sec. 4.4 (chord 1, U_inf = 1): y = y_r + h sin(2 pi f t) with the
     reduced frequency k = 2 pi f; the whole mesh moves.  Corners and velocities."""

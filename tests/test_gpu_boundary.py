@@ -224,3 +224,32 @@ def test_bad_boundaries_rejected(torch):
         fr.Solver(cfg, 8, 3, bc=("wall", "farfield"), q_inf=(-1.0, 1.0, 0.0, 1.0))
     with pytest.raises(fr.FrError):
         fr.Solver(cfg, 1, 3, bc=("wall", "wall"))
+
+
+@pytest.mark.parametrize("precond", ["block", "twolevel"])
+def test_steady_ptc_on_a_cylinder_matches_oracle(torch, precond):
+    """Steady pseudo-transient continuation with SER (Eqs. steady_pre_discretized_1, SER)
+    on a small cylinder O-grid (no-slip adiabatic wall, far field at 20 diameters,
+    Re = 20, M = 0.1) from the impulsively started free stream: the GPU takes the
+    oracle's pseudo steps and GMRES iterations and follows its Res_m history, with the
+    element blocks or with the coarse correction."""
+    from paper_1903_06304_gb300 import fr
+    ni, nj, p, mach, re = 12, 4, 1, 0.1, 20.0
+    c = inp.cylinder_ogrid(ni, nj, 20.0, 0.05)
+    v = np.zeros_like(c)
+    qi = inp.far_field_state(mach)
+    q = inp.uniform_state(ni * nj, p, mach)
+    mesh = rs.Mesh(ni, nj, c, v, bc=(rs.WALL, rs.FARFIELD), q_inf=qi)
+    prob = sv.Problem(mesh, p, ph.Gas(mach=mach, re=re, kappa=1.0))
+    rhs = lambda s: prob.R(s)
+    _, sto = sv.newton_solve(prob, q, rhs, 0.0, 0.01, 20, 1e-6, 100, 1e-6, 12, 1,
+                             ser=(0.01, 1e20, 2.0), precond=precond)
+    S = fr.Solver(fr.Config(p=p, mach=mach, re=re, kappa=1.0, restart=20, tol_pseudo=1e-6,
+                            maxit_newton=12, precond=precond, mg_prec="fp64"), ni, nj,
+                  bc=("wall", "farfield"), q_inf=qi)
+    S.update_mesh(to_dev(c), to_dev(v))
+    st = S.ptc_solve(to_dev(q), allow_unconverged=True).summary()
+    assert st["newton_iterations"] == sto.newton_iterations
+    assert st["gmres_iterations"] == sto.gmres_iterations
+    np.testing.assert_allclose(st["res_history"], sto.res_history, rtol=1e-6)
+    S.close()

@@ -343,3 +343,22 @@ def test_complex_step_through_boundary_faces_matches_central_differences():
     fd = (prob.R(q + h * d) - prob.R(q - h * d)) / (2 * h)
     s = np.abs(jv).max(axis=(1, 2, 3))
     assert np.all(np.abs(jv - fd).max(axis=(1, 2, 3)) <= 1e-5 * s), np.abs(jv - fd).max(axis=(1, 2, 3)) / s
+
+
+def test_cylinder_ogrid_geometry():
+    """The cylinder O-grid input: wall nodes on the circle of diameter 1, outer nodes on the
+    far-field circle, the first radial cell of the requested size, every element with
+    positive area (right-handed), and the wrap closing the grid around the body."""
+    ni, nj, rf, first = 24, 10, 20.0, 1e-2
+    c = inp.cylinder_ogrid(ni, nj, rf, first)
+    r_wall = np.hypot(c[:ni, 0, 0], c[:ni, 0, 1])
+    r_far = np.hypot(c[-ni:, 3, 0], c[-ni:, 3, 1])
+    np.testing.assert_allclose(r_wall, 0.5, rtol=1e-14)
+    np.testing.assert_allclose(r_far, rf, rtol=1e-12)
+    r1 = np.hypot(c[:ni, 3, 0], c[:ni, 3, 1])
+    np.testing.assert_allclose(r1 - 0.5, first, rtol=1e-6)
+    a = c[:, 2] - c[:, 0]
+    b = c[:, 3] - c[:, 1]
+    assert np.all(a[:, 0] * b[:, 1] - a[:, 1] * b[:, 0] > 0)
+    # element ni-1's right edge is element 0's left edge
+    np.testing.assert_allclose(c[ni - 1, 1], c[0, 0], atol=1e-15)
