@@ -496,6 +496,76 @@ def steady_ptc_study(args, torch, fr, inp, T):
     return out
 
 
+def plunge_march_report(args, torch, fr, inp, T):
+    """The plunging NACA 0012 of Sec. 4.4 in the benchmark's configuration: O-grid of
+    ``--plunge-grid`` cells (256 x 96) to 20 chords, cosine clustering at the edges blended
+    half with a uniform distribution, first cell 1e-3 chords; p = 3, Re = 1e4 on the chord,
+    kappa = sqrt 5; rigid plunge y = 0.25 sin(k t), k = 1 (Sec. 4.4); dt = T/200; BDF1 then
+    BDF2 from the impulsively started free stream, Newton to Res_m/Res_0 <= 1e-8 with
+    GMRES(100), tol_res 1e-6 and the configured preconditioner.  Per Mach number: wall
+    time, convergence, Newton and GMRES counts and C_l = 2 F_y, C_t = -2 F_x of each
+    step (rho = U = c = 1).  With ``--plunge-periods P`` the march runs P periods and
+    reports the last period's mean C_t, C_l rms and C_l max (Sec. 4.4's force table)."""
+    import math
+    ni, nj = (int(x) for x in args.plunge_grid.split("x"))
+    p, re, kappa, h, k = 3, 1e4, 5 ** 0.5, 0.25, 1.0
+    period = 2 * math.pi / k
+    dt = period / 200
+    ref = inp.naca_ogrid(ni, nj)
+    nsteps = args.plunge_periods * 200 if args.plunge_periods > 0 else args.plunge_steps
+    out = {"workload": f"naca0012_ogrid_{ni}x{nj}_p{p} plunge h={h} k={k} Re={re:g} dt=T/200",
+           "dof": 4 * ni * nj * (p + 1) ** 2, "steps": nsteps, "precond": args.precond,
+           "blocks": args.prec, "coarse": "fp64"}
+    for mach in args.plunge_mach:
+        qi = inp.far_field_state(mach)
+        # FP64 coarse levels: on this stretched O-grid at M <= 0.1 the FP32 coarse
+        # operators leave left-preconditioned GMRES a near-singular map, whose unconverged
+        # Newton updates drive T negative within two iterations
+        cfg = fr.Config(p=p, mach=mach, re=re, kappa=kappa, precond=args.precond, prec=args.prec,
+                        mg_prec="fp64", restart=100, maxit_lin=100, tol_res=1e-6, tol_pseudo=1e-8,
+                        maxit_newton=20, graphs=args.graphs)
+        S = fr.Solver(cfg, ni, nj, bc=("wall", "farfield"), q_inf=qi)
+        c0, v0 = inp.plunge(ref, 0.0, h, k)
+        S.update_mesh(T(c0), T(v0))
+        q = T(inp.uniform_state(ni * nj, p, mach))
+        qn = torch.empty_like(q)
+        S.conservative(q, qn)
+        qm = qn.clone()
+        rec = {"sec_per_step": [], "converged": [], "newton": [], "gmres": [], "c_l": [], "c_t": []}
+        for n in range(nsteps):
+            c1, v1 = inp.plunge(ref, (n + 1) * dt, h, k)
+            S.update_mesh(T(c1), T(v1))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                st = S.bdf2_step(q, qn, qm, dt, coeffs=fr.BDF1 if n == 0 else fr.BDF2,
+                                 allow_unconverged=True).summary()
+            except fr.FrError as e:
+                rec["error"] = f"step {n}: {e}"
+                break
+            torch.cuda.synchronize()
+            rec["sec_per_step"].append(round(time.perf_counter() - t0, 4))
+            qm.copy_(qn)
+            S.conservative(q, qn)
+            fx, fy = S.wall_force(q)
+            rec["converged"].append(st["converged"])
+            rec["newton"].append(st["newton_iterations"])
+            rec["gmres"].append(sum(st["gmres_iterations"]))
+            rec["c_l"].append(2.0 * fy)
+            rec["c_t"].append(-2.0 * fx)
+        S.close()
+        if args.plunge_periods > 0 and len(rec["c_t"]) == nsteps:
+            ct, cl = rec["c_t"][-200:], rec["c_l"][-200:]
+            rec["last_period"] = {"c_t_mean": sum(ct) / 200,
+                                  "c_l_rms": math.sqrt(sum(x * x for x in cl) / 200),
+                                  "c_l_max": max(cl)}
+            for key in ("sec_per_step", "newton", "gmres", "c_l", "c_t", "converged"):
+                rec[key] = {"mean": sum(rec[key]) / nsteps, "n": nsteps} if key != "converged" \
+                    else all(rec[key])
+        out[f"M={mach:g}"] = rec
+    return out
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -778,6 +848,9 @@ def gpu_arm(args):
     ptc = None
     if rank == 0 and not args.no_ptc:
         ptc = steady_ptc_study(args, torch, fr, inp, T)
+    plunge = None
+    if rank == 0 and not args.no_plunge:
+        plunge = plunge_march_report(args, torch, fr, inp, T)
 
     # ---- CPU baseline (rank 0, N = 1 only): the oracle's unit costs priced with the
     # timed steps' own counts
@@ -836,6 +909,7 @@ def gpu_arm(args):
         "block_factor_ms": factor_ms,
         "low_mach_deforming": low_mach,
         "steady_ptc_cylinder": ptc,
+        "plunging_naca": plunge,
         "kernels": kernels,
         "kernels_same_steps": same_steps,
         "roofline": roof,
@@ -1016,6 +1090,14 @@ def main():
                     help="skip the deforming 128x128 M = 0.01 report")
     ap.add_argument("--no-ptc", dest="no_ptc", action="store_true",
                     help="skip the steady PTC study on the cylinder O-grid")
+    ap.add_argument("--no-plunge", dest="no_plunge", action="store_true",
+                    help="skip the plunging NACA 0012 march")
+    ap.add_argument("--plunge-steps", dest="plunge_steps", type=int, default=3)
+    ap.add_argument("--plunge-periods", dest="plunge_periods", type=int, default=0,
+                    help="march whole periods (200 steps each) and report the last one's forces")
+    ap.add_argument("--plunge-mach", dest="plunge_mach", type=lambda t: [float(x) for x in t.split(",")],
+                    default=[0.05, 0.1, 0.2, 0.3])
+    ap.add_argument("--plunge-grid", dest="plunge_grid", default="256x96")
     ap.add_argument("--c3-steps", dest="c3_steps", type=int, default=3)
     ap.add_argument("--c3-newton", dest="c3_newton", type=int, default=10)
     ap.add_argument("--restart", type=int, default=30)

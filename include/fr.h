@@ -213,11 +213,13 @@ int fr_set_mesh(fr_ctx* ctx, int nx, int ny, int periodic_x, int periodic_y);
  * required when a side is a far field, may be NULL otherwise; copied.  Boundary faces
  * take the interior trace's local gradient with the full one-sided BR2 lift of
  * q_b - q^- (the boundary state is also q^com).  Allocates like fr_set_mesh plus 4
- * arrays of nx*4*(p+1) doubles.  On a bounded mesh the Newton operator and the element
- * blocks are formed by dual numbers whatever cfg.jvp_mode / cfg.block_mode say (the
- * configured modes return with the next fr_set_mesh); fr_linearize, fr_apply_linear,
- * fr_vjp and fr_param_vjp return FR_ERR_ARG (message in fr_last_error).  FR_ERR_ARG also
- * for nx < 2, ny < 1, an unknown kind or a missing / non-positive q_inf. */
+ * arrays of nx*4*(p+1) doubles and the boundary faces' local Jacobians (48 nx (p+1)
+ * doubles).  Every operator mode works on a bounded mesh: the stored linearisation
+ * holds the boundary map's Jacobian in (q^-, grad q^-) at each boundary flux point, and
+ * the common solution there varies as D_b q^- (D_b = diag(1, 0, 0, 1) at a wall, 0 at a
+ * far field), so fr_linearize, fr_apply_linear (both ways), fr_vjp and the linearised
+ * element blocks include the boundary faces.  FR_ERR_ARG for nx < 2, ny < 1, an unknown
+ * kind or a missing / non-positive q_inf. */
 int fr_set_mesh_bounded(fr_ctx* ctx, int nx, int ny, int bc_below, int bc_above,
                         const double* q_inf_h);
 
@@ -369,11 +371,64 @@ int fr_residual_noalloc(const fr_config* cfg, int nx, int ny, const double* corn
  * A node shared by several elements appears once per element: its sensitivity is the sum
  * over its copies.  Any of dmach, dcorners_d, dvel_d may be NULL (skipped).  Exact
  * forward mode over colour classes of elements (9 to 25 classes, 8 directions each for
- * corners and again for velocities).  Single-case contexts.  Synchronises when dmach is
- * requested; otherwise asynchronous on stream. */
+ * corners and again for velocities).  Single-case contexts, periodic or bounded (a far
+ * field's q_inf is held fixed in dmach; fr_param_jvp takes its tangent).  Synchronises
+ * when dmach is requested; otherwise asynchronous on stream. */
 int fr_param_vjp(fr_ctx* ctx, const double* qp_d, const double* w_d, const double* corners_d,
                  const double* corner_vel_d, double* dmach, double* dcorners_d, double* dvel_d,
                  void* stream);
+
+/* Directional derivative of the residual and of the wall force along one parameter
+ * direction at a fixed state (the forward counterpart of fr_param_vjp, for a few
+ * parameters such as a plunge amplitude and the Mach number): corners_d / corner_vel_d
+ * give the mesh again (as passed to fr_update_mesh), dcorners_d / dvel_d (device
+ * [Ne][4][2], either may be NULL = zero) the direction of the corners and of their
+ * velocities, dmach the Mach tangent (moving R, C_p, k and kappa M_inf as in fr_param_vjp)
+ * and dqinf_h (host, 4 doubles, may be NULL = zero) the tangent of the far-field state.
+ *   *wdR_h (host, may be NULL)   = w . R'   (w_d device, state layout; needed if wdR_h);
+ *   dforce_h[0..1] (host, may be NULL) = (F_x', F_y') of fr_wall_force (needs a wall).
+ * Exact forward mode (dual-number geometry, gas and boundary states), bounded or periodic
+ * single-case meshes.  Synchronises the stream. */
+int fr_param_jvp(fr_ctx* ctx, const double* qp_d, const double* w_d, const double* corners_d,
+                 const double* corner_vel_d, const double* dcorners_d, const double* dvel_d,
+                 double dmach, const double* dqinf_h, double* wdR_h, double* dforce_h,
+                 void* stream);
+
+/* ---------------------------------------------------------------- discrete adjoint
+ * Building blocks of the reverse sweep of the BDF2 march (Sec. 3.2) for force objectives
+ * (Sec. 4), e.g. the mean thrust coefficient J = (1/K) sum_n -2 F_x(q^n) of a plunging
+ * airfoil (Sec. 4.4).  With G^n(q^n, q^{n-1}, q^{n-2}) = R(q^n) - (a0 q^c(q^n) +
+ * a1 q^c(q^{n-1}) + a2 q^c(q^{n-2}))/dt the step equations, the adjoint states solve, for
+ * n = K .. 1 with the mesh of t^n set,
+ *   (dG^n/dq^n)^T lam^n = -dJ/dq^n + (a1^{n+1}/dt) Mq(q^n)^T lam^{n+1}
+ *                                   + (a2^{n+2}/dt) Mq(q^n)^T lam^{n+2},
+ * Mq = dq^c/dq^p, and dJ/dtheta = dJ/dtheta|_q + sum_n lam^n . dG^n/dtheta|_q.  Since
+ * dG^n/dq^n = -A(inv_dtau = 0, a0_dt = a0/dt) (the Newton operator of fr_jvp), a step is
+ * fr_wall_force_vjp and fr_conservative_vjp into g, then fr_adjoint_solve of A^T lam = -g;
+ * the parameter part is fr_param_jvp (R' and F') and fr_conservative_dmach. */
+
+/* Solve A^T lam = g at state q, A the Newton operator at (inv_dtau, a0_dt) as in fr_gmres:
+ * builds the element blocks and the stored linearisation at q, then restarted GMRES with
+ * the configured side, restart and tolerance on A^T, preconditioned by the transposed
+ * element blocks B_e^-T (the coarse correction of FR_PRECOND_TWO_LEVEL is not used here).
+ * lam_d receives the solution (zero initial guess), *iters (host, may be NULL) the
+ * iteration count.  Single-case contexts.  Synchronises the stream. */
+int fr_adjoint_solve(fr_ctx* ctx, const double* qp_d, const double* g_d, double inv_dtau,
+                     double a0_dt, double* lam_d, int* iters, void* stream);
+/* out = beta out + alpha d(wx F_x + wy F_y)/dq at q (F of fr_wall_force): the weighted
+ * tractions differentiated in the wall faces' traces and local gradients (forward mode)
+ * and mapped back by the transposed traces and gradients.  beta = 0 ignores out's
+ * contents.  FR_ERR_ARG if the mesh has no wall faces. */
+int fr_wall_force_vjp(fr_ctx* ctx, const double* qp_d, double wx, double wy, double alpha,
+                      double beta, double* out_d, void* stream);
+/* out = beta out + alpha (dq^c/dq^p)(q)^T w, pointwise (the conservative map of Sec. 2.1);
+ * beta = 0 ignores out's contents. */
+int fr_conservative_vjp(fr_ctx* ctx, const double* qp_d, const double* w_d, double alpha,
+                        double beta, double* out_d, void* stream);
+/* *out_h (host) = sum of w . dq^c/dM_inf at fixed q^p (rho = p/(R T), R = 1/(gamma M^2)).
+ * Synchronises the stream. */
+int fr_conservative_dmach(fr_ctx* ctx, const double* qp_d, const double* w_d, double* out_h,
+                          void* stream);
 
 /* ---------------------------------------------------------------- batches
  * Many independent problems solved together (the paper solves one at a time; Sec. 3.2's

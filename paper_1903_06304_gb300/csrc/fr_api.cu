@@ -188,7 +188,7 @@ void free_mesh(fr_ctx* c) {
                    &c->w_t, &c->w_u, &c->red, &c->JFQ, &c->JFG, &c->JP, &c->JG, &c->PP,
                    &c->adj_q, &c->adj_fn, &c->adj_qc, &c->sgs, &c->sdgs, &c->sgf, &c->sdgf,
                    &c->seed, &c->edot, &c->zero, &c->rtan, &c->fnb, &c->fnb_d, &c->qcb,
-                   &c->qcb_d};
+                   &c->qcb_d, &c->JFQb, &c->JFGb};
   for (double** p : ds) if (*p) { cudaFree(*p); *p = nullptr; }
   if (c->Binv) { cudaFree(c->Binv); c->Binv = nullptr; }
   if (c->Dr) { cudaFree(c->Dr); c->Dr = nullptr; }
@@ -199,10 +199,6 @@ void free_mesh(fr_ctx* c) {
   if (c->ecase) { cudaFree(c->ecase); c->ecase = nullptr; }
   c->blocks_ready = 0;
   c->lin_ready = 0;
-  if (c->bounded) {   // back to the configured operator and block modes
-    c->cfg.jvp_mode = c->user_jvp_mode;
-    c->cfg.block_mode = c->user_block_mode;
-  }
   c->bounded = c->bc_below = c->bc_above = 0;
   frk::batch_free(c);
   frk::mg_free(c);
@@ -216,15 +212,6 @@ int check_ready(fr_ctx* c) {
   if (!c) return FR_ERR_ARG;
   if (c->ne <= 0) { snprintf(c->err, sizeof(c->err), "fr_set_mesh has not been called"); return FR_ERR_ARG; }
   return FR_OK;
-}
-
-// The stored local Jacobians (linearised operator, VJP) and the parameter sensitivities
-// do not treat boundary faces yet: refused on bounded meshes before any launch.
-int need_periodic(fr_ctx* c, const char* what) {
-  if (!c->bounded) return FR_OK;
-  snprintf(c->err, sizeof(c->err), "%s: not available on bounded meshes (the residual, "
-           "dual-number JVP, element blocks, GMRES and Newton loops are)", what);
-  return FR_ERR_ARG;
 }
 
 // host copies of the small device scalars
@@ -289,6 +276,7 @@ int cgs2(fr_ctx* c, int nv, double* w, cudaStream_t s) {
 // dual-number JVP at q.
 int op_apply(fr_ctx* c, const double* q, const double* x, double inv_dtau, double a0_dt,
              double* out, cudaStream_t s) {
+  if (c->transposed) return frk::apply_linear(c, x, out, true, s);
   if (c->cfg.jvp_mode == FR_JVP_LINEARIZED) return frk::apply_linear(c, x, out, false, s);
   return frk::jvp(c, q, x, inv_dtau, a0_dt, out, s);
 }
@@ -668,17 +656,15 @@ int fr_set_mesh_bounded(fr_ctx* c, int nx, int ny, int bc_below, int bc_above, c
   c->bounded = 1;
   c->bc_below = bc_below;
   c->bc_above = bc_above;
-  // the stored local Jacobians do not cover boundary faces: the Newton operator and the
-  // element blocks are formed by dual numbers on a bounded mesh
-  c->user_jvp_mode = c->cfg.jvp_mode;
-  c->user_block_mode = c->cfg.block_mode;
-  c->cfg.jvp_mode = FR_JVP_DUAL;
-  c->cfg.block_mode = FR_BLOCK_DUAL;
   const size_t nb = (size_t)nx * 4 * c->n;
   FR_TRY(dev_alloc(c, &c->fnb, nb));
   FR_TRY(dev_alloc(c, &c->fnb_d, nb));
   FR_TRY(dev_alloc(c, &c->qcb, nb));
   FR_TRY(dev_alloc(c, &c->qcb_d, nb));
+  // local Jacobians of the boundary faces below row 0 (those above the last row are owned
+  // faces of the stored face map)
+  FR_TRY(dev_alloc(c, &c->JFQb, (size_t)nx * c->n * 16));
+  FR_TRY(dev_alloc(c, &c->JFGb, (size_t)nx * c->n * 32));
   FR_TRY(frk::mark_bounds(c, nx, ny, bc_below, bc_above, 0));
   FR_CUDA_CHECK(c, cudaStreamSynchronize(0));
   // the coarse hierarchy again, now without the wrap in eta
@@ -806,14 +792,12 @@ int fr_jvp(fr_ctx* c, const double* q, const double* v, double inv_dtau, double 
 
 int fr_linearize(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, void* s) {
   FR_TRY(check_ready(c));
-  FR_TRY(need_periodic(c, "fr_linearize"));
   if (!q) return FR_ERR_ARG;
   return frk::linearize(c, q, inv_dtau, a0_dt, S(s));
 }
 
 int fr_apply_linear(fr_ctx* c, const double* v, double* out, int transpose, void* s) {
   FR_TRY(check_ready(c));
-  FR_TRY(need_periodic(c, "fr_apply_linear"));
   if (!v || !out) return FR_ERR_ARG;
   return frk::apply_linear(c, v, out, transpose != 0, S(s));
 }
@@ -821,7 +805,6 @@ int fr_apply_linear(fr_ctx* c, const double* v, double* out, int transpose, void
 int fr_vjp(fr_ctx* c, const double* q, const double* w, double inv_dtau, double a0_dt, double* out,
            void* s) {
   FR_TRY(check_ready(c));
-  FR_TRY(need_periodic(c, "fr_vjp"));
   if (!q || !w || !out) return FR_ERR_ARG;
   FR_TRY(frk::linearize(c, q, inv_dtau, a0_dt, S(s)));
   return frk::apply_linear(c, w, out, true, S(s));
@@ -862,6 +845,47 @@ int fr_gmres(fr_ctx* c, const double* q, const double* b, double inv_dtau, doubl
   FR_TRY(gmres_solve(c, q, b, inv_dtau, a0_dt, x, &its, S(s)));
   if (iters) *iters = its;
   return FR_OK;
+}
+
+int fr_adjoint_solve(fr_ctx* c, const double* q, const double* g, double inv_dtau, double a0_dt,
+                     double* lam, int* iters, void* s) {
+  FR_TRY(check_ready(c));
+  if (!q || !g || !lam) return FR_ERR_ARG;
+  if (c->ncases != 1) { snprintf(c->err, sizeof(c->err), "fr_adjoint_solve: single-case contexts only"); return FR_ERR_ARG; }
+  // the element blocks at q (applied transposed) and the operator's local Jacobians at q
+  FR_TRY(frk::block_build(c, q, inv_dtau, a0_dt, S(s)));
+  c->blocks_ready = 1;
+  if (c->cfg.block_mode != FR_BLOCK_LINEARIZED) FR_TRY(frk::linearize(c, q, inv_dtau, a0_dt, S(s)));
+  c->transposed = 1;
+  int its = 0;
+  const int rc = gmres_solve(c, q, g, inv_dtau, a0_dt, lam, &its, S(s));
+  c->transposed = 0;
+  if (iters) *iters = its;
+  return rc;
+}
+
+int fr_wall_force_vjp(fr_ctx* c, const double* q, double wx, double wy, double alpha, double beta,
+                      double* out, void* s) {
+  FR_TRY(check_ready(c));
+  if (!q || !out) return FR_ERR_ARG;
+  if (!c->bounded || (c->bc_below != FR_BC_WALL && c->bc_above != FR_BC_WALL)) {
+    snprintf(c->err, sizeof(c->err), "fr_wall_force_vjp: the mesh has no wall faces");
+    return FR_ERR_ARG;
+  }
+  return frk::wall_force_vjp(c, q, wx, wy, alpha, beta, out, S(s));
+}
+
+int fr_conservative_vjp(fr_ctx* c, const double* q, const double* w, double alpha, double beta,
+                        double* out, void* s) {
+  FR_TRY(check_ready(c));
+  if (!q || !w || !out) return FR_ERR_ARG;
+  return frk::conservative_vjp(c, q, w, alpha, beta, out, S(s));
+}
+
+int fr_conservative_dmach(fr_ctx* c, const double* q, const double* w, double* out_h, void* s) {
+  FR_TRY(check_ready(c));
+  if (!q || !w || !out_h) return FR_ERR_ARG;
+  return frk::conservative_dmach(c, q, w, out_h, S(s));
 }
 
 int fr_bdf2_step(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, double a0, double a1,

@@ -91,6 +91,7 @@ static int upload_gmres(fr_ctx* c, cudaStream_t s) {
 
 static int op_apply(fr_ctx* c, const double* q, const double* x, double inv_dtau, double a0_dt,
                     double* out, cudaStream_t s) {
+  if (c->transposed) return frk::apply_linear(c, x, out, true, s);
   if (c->cfg.jvp_mode == FR_JVP_LINEARIZED) return frk::apply_linear(c, x, out, false, s);
   return frk::jvp(c, q, x, inv_dtau, a0_dt, out, s);
 }
@@ -160,9 +161,9 @@ int gmres_cases(fr_ctx* c, const double* q, const double* b, double* x, double i
         }
         return FR_OK;
       };
-      const bool dual = c->cfg.jvp_mode == FR_JVP_DUAL;
-      FR_TRY(gm_chunk(c, j0, nchunk, 4 + (left ? 2 : 0) + (dual ? 1 : 0), dual ? q : nullptr,
-                      issue, s));
+      const bool dual = c->cfg.jvp_mode == FR_JVP_DUAL && !c->transposed;
+      FR_TRY(gm_chunk(c, j0, nchunk, 4 + (left ? 2 : 0) + (dual ? 1 : 0) + (c->transposed ? 8 : 0),
+                      dual ? q : nullptr, issue, s));
       issued += nchunk;
       FR_TRY(frk::bk_status(c, s));
       FR_CUDA_CHECK(c, cudaStreamSynchronize(s));

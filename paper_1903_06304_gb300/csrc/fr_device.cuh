@@ -325,10 +325,12 @@ __device__ __forceinline__ void face_common(const T qm[4], const T qp[4], const 
 // (dg_end = g'(end) of the element's face: +g_R'(1) on a T face, g_L'(-1) = -g_R'(1) on a
 // B face); at a wall the component of grad T^com along S is removed (dT/dn = 0); the flux
 // f_vis(qb, grad q^com) . S.  Writes fnum = |S| f_n^com along +S and qb.
+// dqinf (nullable): tangent of q_inf carried by dual-number T (parameter sensitivities).
 template <class T, class G, class GS>
 __device__ __forceinline__ void face_boundary(const T qe[4], const T ge[8], G Sx, G Sy, G ug, G vg,
                                               G Je, const GS& gs, double dg_end, bool elem_minus,
-                                              int kind, const double qinf[4], T fnum[4], T qb[4]) {
+                                              int kind, const double qinf[4], T fnum[4], T qb[4],
+                                              const double* dqinf = nullptr) {
   if (kind == BC_WALL) {
     qb[0] = qe[0];
     qb[1] = as_T<T>(ug);
@@ -336,7 +338,7 @@ __device__ __forceinline__ void face_boundary(const T qe[4], const T ge[8], G Sx
     qb[3] = qe[3];
   } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) qb[k] = as_T<T>(qinf[k]);
+    for (int k = 0; k < 4; ++k) qb[k] = from_parts<T>(qinf[k], dqinf ? dqinf[k] : 0.0);
   }
   T dq[4], qa[4];
   if (elem_minus) rusanov_common(qe, qb, Sx, Sy, ug, vg, gs, dq, qa, fnum);
@@ -361,6 +363,11 @@ __device__ __forceinline__ void face_boundary(const T qe[4], const T ge[8], G Sx
     for (int k = 0; k < 4; ++k) fnum[k] = fnum[k] + fv[k] * Sx + gv[k] * Sy;
   }
 }
+
+// Four doubles passed by value to a kernel (the far-field state's tangent).
+struct Vec4 {
+  double v[4];
+};
 
 // ---------------------------------------------------------------- launch geometry
 // Elements per block for the point-parallel kernels (one thread per solution point):

@@ -153,7 +153,6 @@ struct fr_ctx {
   // bounded meshes (fr_set_mesh_bounded): boundary kinds below row 0 / above row ny-1 and
   // the common flux and state of the faces below row 0, [nx][4][n] (value and tangent)
   int bounded = 0, bc_below = 0, bc_above = 0;
-  int user_jvp_mode = 0, user_block_mode = 0;   // the configured modes while bounded
   double *fnb = nullptr, *fnb_d = nullptr, *qcb = nullptr, *qcb_d = nullptr;
   // element blocks
   double* B64 = nullptr;     // [Ne][b][b] unfactored
@@ -165,8 +164,10 @@ struct fr_ctx {
   // stored local Jacobians of the Newton operator (fr_linear.cu)
   double *JFQ = nullptr, *JFG = nullptr;           // face map: [32|64][Ne*2n]
   double *JP = nullptr, *JG = nullptr, *PP = nullptr;  // point map: [32|64|16][Ne*n^2]
+  double *JFQb = nullptr, *JFGb = nullptr;         // faces below row 0: [16|32][nx*n]
   double *adj_q = nullptr, *adj_fn = nullptr, *adj_qc = nullptr;  // transpose work
   int lin_ready = 0;
+  int transposed = 0;   // set during fr_adjoint_solve: GMRES applies A^T and B^-T
   // two-level preconditioner (cfg.precond == FR_PRECOND_TWO_LEVEL, fr_mg.cu)
   std::vector<MgLevel> mg;
   int mg_ncol = 0;                 // colours of the level-0 Galerkin products
@@ -268,6 +269,16 @@ int precond_apply(fr_ctx* c, const double* q, const double* r, double* z, double
                   double a0_dt, cudaStream_t s);
 int linearize(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s);
 int apply_linear(fr_ctx* c, const double* v, double* out, bool transpose, cudaStream_t s);
+// out = transposed traces and local gradients of the trace adjoints in tq_d / tg_d plus
+// the point adjoints adj_q and gradient adjoints gl_d (the last pass of the VJP)
+int trace_adjoint(fr_ctx* c, double* out, cudaStream_t s);
+// Adjoint building blocks (fr_adjoint.cu): out = beta out + alpha d(wx F_x + wy F_y)/dq
+// (uses w_t), out = beta out + alpha (dq^c/dq)^T w, and sum of w . dq^c/dM at fixed q.
+int wall_force_vjp(fr_ctx* c, const double* q, double wx, double wy, double alpha, double beta,
+                   double* out, cudaStream_t s);
+int conservative_vjp(fr_ctx* c, const double* q, const double* w, double alpha, double beta,
+                     double* out, cudaStream_t s);
+int conservative_dmach(fr_ctx* c, const double* q, const double* w, double* out_h, cudaStream_t s);
 // Krylov primitives (deterministic reductions over a fixed grid)
 int dots(fr_ctx* c, const double* V, int nv, const double* w, double* out_dev, cudaStream_t s);
 int axpy_dots(fr_ctx* c, const double* V, int nv, const double* h_dev, double* w, double* out_dev,

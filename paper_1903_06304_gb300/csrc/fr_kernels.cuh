@@ -211,7 +211,7 @@ k_trace(Buf<T> Q, Mesh M, Basis B, const double* __restrict__ gs, Buf<T> GL, Buf
 template <class T, int N, class G = double>
 __global__ void k_face(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ,
                        Buf<T> TG, Buf<T> FN, Buf<T> QC, const double* __restrict__ dgf = nullptr,
-                       double dmach = 0.0) {
+                       double dmach = 0.0, Vec4 dqinf = Vec4{}) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= M.ne * 2 * N) return;
   const int e = idx / (2 * N), rem = idx % (2 * N), dir = rem / N, t = rem % N;
@@ -232,7 +232,7 @@ __global__ void k_face(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ
     face_boundary(qe, ge, geo<G>(gf, dgf, GF_SX * FNs + om), geo<G>(gf, dgf, GF_SY * FNs + om),
                   geo<G>(gf, dgf, GF_UG * FNs + om), geo<G>(gf, dgf, GF_VG * FNs + om),
                   geo<G>(gf, dgf, GF_J * FNs + om), gas, B.dgR_end, true, -plus, M.par(e).qinf,
-                  fnum, qb);
+                  fnum, qb, dqinf.v);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const size_t oo = (((size_t)e * 2 + dir) * 4 + v) * N + t;
@@ -274,7 +274,7 @@ __global__ void k_face(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ
 template <class T, int N, class G = double>
 __global__ void k_face_below(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ, Buf<T> TG,
                              Buf<T> FB, Buf<T> QB, int nrow, const double* __restrict__ dgf = nullptr,
-                             double dmach = 0.0) {
+                             double dmach = 0.0, Vec4 dqinf = Vec4{}) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nrow * N) return;
   const int e = idx / N, t = idx % N;
@@ -293,11 +293,120 @@ __global__ void k_face_below(Mesh M, Basis B, const double* __restrict__ gf, Buf
   face_boundary(qe, ge, geo<G>(gf, dgf, GF_SX * FNs + of), geo<G>(gf, dgf, GF_SY * FNs + of),
                 geo<G>(gf, dgf, GF_UG * FNs + of), geo<G>(gf, dgf, GF_VG * FNs + of),
                 geo<G>(gf, dgf, GF_J * FNs + of), gas, -B.dgR_end, false, -below, M.par(e).qinf,
-                fnum, qb);
+                fnum, qb, dqinf.v);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     FB.st(((size_t)e * 4 + v) * N + t, fnum[v]);
     QB.st(((size_t)e * 4 + v) * N + t, qb[v]);
+  }
+}
+
+// ------------------------------------------------------------------ wall traction
+// Weighted traction of one wall flux point (the integrand of the force of Sec. 4):
+// w (t_x, t_y) with t = -(p - p_inf) n + tau . n, n = sgn S / |S| the unit normal out of
+// the body (sgn = +1 below row 0, -1 above the last row), p_inf = R (rho_inf = T_inf = 1),
+// tau from grad q^com of the wall (the interior local gradient ge plus the one-sided lift
+// of q_b - q^e with q_b = (p^e, v_g, T^e), the component of grad T along S removed), and
+// w = wq |S| (wq the Gauss weight).  T is the arithmetic type (dual numbers carry state
+// or parameter tangents), G the geometry's type, GS the gas.
+template <class T> __device__ __forceinline__ T div_(T a, T b) { return a * inv(b); }
+__device__ __forceinline__ double div_(double a, double b) { return a / b; }
+
+template <class T, class G, class GS>
+__device__ __forceinline__ void wall_traction(const T qe[4], const T ge[8], G Sx_, G Sy_, G ug, G vg,
+                                              G J, const GS& gas, double dg_end, double sgn,
+                                              double wq, bool viscous, T& fx, T& fy) {
+  const T Sx = as_T<T>(Sx_), Sy = as_T<T>(Sy_);
+  const T qb[4] = {qe[0], as_T<T>(ug), as_T<T>(vg), qe[3]};
+  const T s2 = Sx * Sx + Sy * Sy;
+  const T smag = sqrt_(s2);
+  const T nbx = div_(sgn * Sx, smag), nby = div_(sgn * Sy, smag);
+  const T dp = qb[0] - as_T<T>(gas.R);
+  T tx = -(dp * nbx), ty = -(dp * nby);
+  if (viscous) {
+    const T lift = div_(as_T<T>(dg_end), as_T<T>(J));
+    T gx[4], gy[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const T jl = (qb[k] - qe[k]) * lift;
+      gx[k] = ge[k] + jl * Sx;
+      gy[k] = ge[4 + k] + jl * Sy;
+    }
+    const T gn = div_(gx[3] * Sx + gy[3] * Sy, s2);
+    gx[3] = gx[3] - gn * Sx;
+    gy[3] = gy[3] - gn * Sy;
+    T fv[4], gv[4];
+    neg_viscous_flux(qb, gx, gy, gas, fv, gv);   // -f_vis, -g_vis
+    tx = tx - (fv[1] * nbx + gv[1] * nby);
+    ty = ty - (fv[2] * nbx + gv[2] * nby);
+  }
+  const T w = wq * smag;
+  fx = w * tx;
+  fy = w * ty;
+}
+
+// Force on the wall faces (the numerator of the force coefficients of Sec. 4): the
+// weighted tractions of every wall flux point (wall_traction), summed by one block:
+// every thread sums a fixed set of flux points and the block sums in a fixed order
+// (deterministic).  out[0..1] = (F_x, F_y); with G = Dual (geometry tangents dgf, the
+// Mach tangent dmach and the traces' tangents dtq, dtg, e.g. of the local gradients under
+// a moving geometry) also out[2..3] = their tangents.
+template <int N, class G = double>
+__global__ void __launch_bounds__(256) k_wall_force(Mesh M, Basis B, const double* __restrict__ gf,
+                                                    const double* __restrict__ tq,
+                                                    const double* __restrict__ tg, int nx, int ny,
+                                                    int wall_below, int wall_above,
+                                                    double* __restrict__ out,
+                                                    const double* __restrict__ dgf = nullptr,
+                                                    double dmach = 0.0,
+                                                    const double* __restrict__ dtq = nullptr,
+                                                    const double* __restrict__ dtg = nullptr) {
+  __shared__ double red[4][256 / 32];
+  typename GasOf<G>::type gas = gas_for<G>(M.par(0).gas, dmach);
+  const size_t FNs = (size_t)M.ne * 4 * N;
+  G fx = as_T<G>(0.0), fy = as_T<G>(0.0);
+  for (int idx = threadIdx.x; idx < 2 * nx * N; idx += blockDim.x) {
+    const int side = idx / (nx * N), rem = idx % (nx * N), i = rem / N, t = rem % N;
+    if (side == 0 ? !wall_below : !wall_above) continue;
+    const int e = side == 0 ? i : (ny - 1) * nx + i;
+    const int f = side == 0 ? FACE_B : FACE_T;
+    G qe[4], ge[8];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const size_t k = (((size_t)e * 4 + f) * 4 + v) * N + t;
+      qe[v] = from_parts<G>(tq[k], dtq ? dtq[k] : 0.0);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const size_t k = (((size_t)e * 4 + f) * 8 + c) * N + t;
+      ge[c] = M.viscous ? from_parts<G>(tg[k], dtg ? dtg[k] : 0.0) : as_T<G>(0.0);
+    }
+    const size_t of = ((size_t)e * 4 + f) * N + t;
+    G px, py;
+    wall_traction(qe, ge, geo<G>(gf, dgf, GF_SX * FNs + of), geo<G>(gf, dgf, GF_SY * FNs + of),
+                  geo<G>(gf, dgf, GF_UG * FNs + of), geo<G>(gf, dgf, GF_VG * FNs + of),
+                  geo<G>(gf, dgf, GF_J * FNs + of), gas, side == 0 ? -B.dgR_end : B.dgR_end,
+                  side == 0 ? 1.0 : -1.0, B.ws[t], M.viscous, px, py);
+    fx = fx + px;
+    fy = fy + py;
+  }
+  double part[4] = {val(fx), val(fy), tan_(fx), tan_(fy)};
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part[k] += __shfl_down_sync(0xffffffffu, part[k], off);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[k][wid] = part[k];
+  }
+  __syncthreads();
+  const int nout = sizeof(G) == sizeof(double) ? 2 : 4;
+  if (threadIdx.x < nout) {
+    double acc = 0.0;
+    for (int w2 = 0; w2 < 256 / 32; ++w2) acc += red[threadIdx.x][w2];
+    out[threadIdx.x] = acc;
   }
 }
 

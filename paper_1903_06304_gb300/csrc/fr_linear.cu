@@ -35,6 +35,38 @@ __global__ void k_lin_face(Mesh M, Basis B, const double* __restrict__ gf,
   const int plus = dir == 0 ? M.right(e) : M.top(e);
   const int fm = dir == 0 ? FACE_R : FACE_T, fp = dir == 0 ? FACE_L : FACE_B;
   const Gas& gas = M.par(e).gas;
+  const size_t FNs = (size_t)M.ne * 4 * N;
+  if (plus < 0) {   // boundary face above the element: the boundary map's Jacobian in (q-, g-)
+    const size_t om = ((size_t)e * 4 + fm) * N + t;
+    double qe[4], ge[8];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qe[v] = tq[(((size_t)e * 4 + fm) * 4 + v) * N + t];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) ge[c] = M.viscous ? tg[(((size_t)e * 4 + fm) * 8 + c) * N + t] : 0.0;
+    const double Sx = gf[GF_SX * FNs + om], Sy = gf[GF_SY * FNs + om];
+    const double ug = gf[GF_UG * FNs + om], vg = gf[GF_VG * FNs + om], Jm = gf[GF_J * FNs + om];
+    const int ndir = M.viscous ? 12 : 4;
+#pragma unroll 1
+    for (int dd = 0; dd < ndir; ++dd) {
+      Dual dq[4], dg[8], fnum[4], qb[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) dq[v] = mk(qe[v], dd == v ? 1.0 : 0.0);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) dg[c] = mk(ge[c], dd == 4 + c ? 1.0 : 0.0);
+      face_boundary(dq, dg, Sx, Sy, ug, vg, Jm, gas, B.dgR_end, true, -plus, M.par(e).qinf, fnum, qb);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (dd < 4) {
+          JFQ[(size_t)(r * 8 + dd) * nf + idx] = fnum[r].d;
+          JFQ[(size_t)(r * 8 + 4 + dd) * nf + idx] = 0.0;
+        } else {
+          JFG[(size_t)(r * 16 + dd - 4) * nf + idx] = fnum[r].d;
+          JFG[(size_t)(r * 16 + 8 + dd - 4) * nf + idx] = 0.0;
+        }
+      }
+    }
+    return;
+  }
   double qm[4], qp[4], gm[8], gp[8];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -46,7 +78,6 @@ __global__ void k_lin_face(Mesh M, Basis B, const double* __restrict__ gf,
     gm[c] = M.viscous ? tg[(((size_t)e * 4 + fm) * 8 + c) * N + t] : 0.0;
     gp[c] = M.viscous ? tg[(((size_t)plus * 4 + fp) * 8 + c) * N + t] : 0.0;
   }
-  const size_t FNs = (size_t)M.ne * 4 * N;
   const size_t om = ((size_t)e * 4 + fm) * N + t, op = ((size_t)plus * 4 + fp) * N + t;
   const double Sx = gf[GF_SX * FNs + om], Sy = gf[GF_SY * FNs + om];
   const double ug = gf[GF_UG * FNs + om], vg = gf[GF_VG * FNs + om];
@@ -74,6 +105,53 @@ __global__ void k_lin_face(Mesh M, Basis B, const double* __restrict__ gf,
   }
 }
 
+// Boundary faces below row 0 of a bounded mesh (the element on the '+' side), flux point
+// b = e*N + t of the first nrow elements:
+//   JFQb[r*4 + c][b] = d fnum_r / d qe_c,  JFGb[r*8 + c][b] = d fnum_r / d ge_c.
+template <int N>
+__global__ void k_lin_face_below(Mesh M, Basis B, const double* __restrict__ gf,
+                                 const double* __restrict__ tq, const double* __restrict__ tg,
+                                 int nrow, double* __restrict__ JFQb, double* __restrict__ JFGb) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nb = nrow * N;
+  if (idx >= nb) return;
+  const int e = idx / N, t = idx % N;
+  const int below = M.bottom(e);
+  if (below >= 0 || !M.on(e)) return;
+  const Gas& gas = M.par(e).gas;
+  const size_t FNs = (size_t)M.ne * 4 * N;
+  const size_t of = ((size_t)e * 4 + FACE_B) * N + t;
+  double qe[4], ge[8];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) qe[v] = tq[(((size_t)e * 4 + FACE_B) * 4 + v) * N + t];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) ge[c] = M.viscous ? tg[(((size_t)e * 4 + FACE_B) * 8 + c) * N + t] : 0.0;
+  const double Sx = gf[GF_SX * FNs + of], Sy = gf[GF_SY * FNs + of];
+  const double ug = gf[GF_UG * FNs + of], vg = gf[GF_VG * FNs + of], Je = gf[GF_J * FNs + of];
+  const int ndir = M.viscous ? 12 : 4;
+#pragma unroll 1
+  for (int dd = 0; dd < ndir; ++dd) {
+    Dual dq[4], dg[8], fnum[4], qb[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) dq[v] = mk(qe[v], dd == v ? 1.0 : 0.0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) dg[c] = mk(ge[c], dd == 4 + c ? 1.0 : 0.0);
+    face_boundary(dq, dg, Sx, Sy, ug, vg, Je, gas, -B.dgR_end, false, -below, M.par(e).qinf, fnum, qb);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (dd < 4) JFQb[(size_t)(r * 4 + dd) * nb + idx] = fnum[r].d;
+      else JFGb[(size_t)(r * 8 + dd - 4) * nb + idx] = fnum[r].d;
+    }
+  }
+}
+
+// The common solution of a boundary face varies as D_b times the element's trace
+// (Sec. 3.3: a far field fixes all of q_b; an adiabatic no-slip wall takes p and T from
+// the trace and prescribes the velocity): the diagonal of D_b for variable v.
+__device__ __forceinline__ double bc_pass(int kind, int v) {
+  return (kind == BC_WALL && (v == 0 || v == 3)) ? 1.0 : 0.0;
+}
+
 // Point map Jacobian at solution point o = e*NP + pt:
 //   JP[r*4 + c][o] = d (F_r (r<4) | G_{r-4}) / d q_c,
 //   JG[r*8 + c][o] = d (F, G)_r / d (corrected grad q)_c (x comps c<4, y comps c>=4),
@@ -83,7 +161,8 @@ __global__ void __launch_bounds__(Tile<N>::THREADS)
 k_lin_point(const double* __restrict__ q, Mesh M, Basis B, const double* __restrict__ gs,
             const double* __restrict__ gf, const double* __restrict__ gl,
             const double* __restrict__ tq, const double* __restrict__ qcm,
-            double* __restrict__ JP, double* __restrict__ JG, double* __restrict__ PP) {
+            const double* __restrict__ qcb, double* __restrict__ JP, double* __restrict__ JG,
+            double* __restrict__ PP) {
   constexpr int NP = N * N, EPB = Tile<N>::EPB;
   const int le = threadIdx.x / NP, pt = threadIdx.x % NP;
   const int e = blockIdx.x * EPB + le;
@@ -112,10 +191,13 @@ k_lin_point(const double* __restrict__ q, Mesh M, Basis B, const double* __restr
                      : (f == FACE_B) ? B.dgL[j] : B.dgR[j];
       const size_t of = ((size_t)e * 4 + f) * N + s;
       const double sx = gf[GF_SX * FNs + of] * w * ij, sy = gf[GF_SY * FNs + of] * w * ij;
+      // below row 0 of a bounded mesh the common state comes from the boundary buffer
+      const bool bface = f == FACE_B && qsrc[f] < 0;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        const double jump = qcm[(((size_t)qsrc[f] * 2 + qdir[f]) * 4 + v) * N + s] -
-                            tq[(((size_t)e * 4 + f) * 4 + v) * N + s];
+        const double qc = bface ? qcb[((size_t)e * 4 + v) * N + s]
+                                : qcm[(((size_t)qsrc[f] * 2 + qdir[f]) * 4 + v) * N + s];
+        const double jump = qc - tq[(((size_t)e * 4 + f) * 4 + v) * N + s];
         gc[v] += jump * sx;
         gc[4 + v] += jump * sy;
       }
@@ -187,11 +269,12 @@ __global__ void k_lin_face_apply(Mesh M, const double* __restrict__ tqv,
   if (!M.on(e)) return;
   const int plus = dir == 0 ? M.right(e) : M.top(e);
   const int fm = dir == 0 ? FACE_R : FACE_T, fp = dir == 0 ? FACE_L : FACE_B;
+  const bool bnd = plus < 0;   // boundary face above the element: no '+' side
   double x[8];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     x[v] = tqv[(((size_t)e * 4 + fm) * 4 + v) * N + t];
-    x[4 + v] = tqv[(((size_t)plus * 4 + fp) * 4 + v) * N + t];
+    x[4 + v] = bnd ? 0.0 : tqv[(((size_t)plus * 4 + fp) * 4 + v) * N + t];
   }
   double out[4];
 #pragma unroll
@@ -208,7 +291,7 @@ __global__ void k_lin_face_apply(Mesh M, const double* __restrict__ tqv,
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       g[c] = c % 4 ? tgv[(((size_t)e * 4 + fm) * 8 + c) * N + t] : 0.0;
-      g[8 + c] = c % 4 ? tgv[(((size_t)plus * 4 + fp) * 8 + c) * N + t] : 0.0;
+      g[8 + c] = (c % 4 && !bnd) ? tgv[(((size_t)plus * 4 + fp) * 8 + c) * N + t] : 0.0;
     }
 #pragma unroll
     for (int r = 1; r < 4; ++r) {
@@ -223,7 +306,50 @@ __global__ void k_lin_face_apply(Mesh M, const double* __restrict__ tqv,
   for (int v = 0; v < 4; ++v) {
     const size_t oo = (((size_t)e * 2 + dir) * 4 + v) * N + t;
     fnv[oo] = out[v];
-    qcv[oo] = 0.5 * (x[v] + x[4 + v]);
+    qcv[oo] = bnd ? bc_pass(-plus, v) * x[v] : 0.5 * (x[v] + x[4 + v]);
+  }
+}
+
+// Boundary faces below row 0: dfnum = JFQb dqe + JFGb dge, dqcom = D_b dqe, into
+// fbv, qbv [nrow][4][N].
+template <int N>
+__global__ void k_lin_face_below_apply(Mesh M, const double* __restrict__ tqv,
+                                       const double* __restrict__ tgv, const double* __restrict__ JFQb,
+                                       const double* __restrict__ JFGb, int nrow,
+                                       double* __restrict__ fbv, double* __restrict__ qbv) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nb = nrow * N;
+  if (idx >= nb) return;
+  const int e = idx / N, t = idx % N;
+  const int below = M.bottom(e);
+  if (below >= 0 || !M.on(e)) return;
+  double x[4], out[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) x[v] = tqv[(((size_t)e * 4 + FACE_B) * 4 + v) * N + t];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) s = fma(JFQb[(size_t)(r * 4 + c) * nb + idx], x[c], s);
+    out[r] = s;
+  }
+  if (M.viscous) {
+    double g[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) g[c] = c % 4 ? tgv[(((size_t)e * 4 + FACE_B) * 8 + c) * N + t] : 0.0;
+#pragma unroll
+    for (int r = 1; r < 4; ++r) {
+      double s = out[r];
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (c % 4) s = fma(JFGb[(size_t)(r * 8 + c) * nb + idx], g[c], s);
+      out[r] = s;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    fbv[((size_t)e * 4 + v) * N + t] = out[v];
+    qbv[((size_t)e * 4 + v) * N + t] = bc_pass(-below, v) * x[v];
   }
 }
 
@@ -236,7 +362,8 @@ k_lin_elem_apply(const double* __restrict__ v, Mesh M, Basis B,
                  const double* __restrict__ glv, const double* __restrict__ tqv,
                  const double* __restrict__ fnv, const double* __restrict__ qcv,
                  const double* __restrict__ JP, const double* __restrict__ JG,
-                 const double* __restrict__ PP, double* __restrict__ out) {
+                 const double* __restrict__ PP, const double* __restrict__ fbv,
+                 const double* __restrict__ qbv, double* __restrict__ out) {
   constexpr int NP = N * N, EPB = Tile<N, K>::EPB;
   __shared__ double sF[EPB][4][NP];
   __shared__ double sG[EPB][4][NP];
@@ -274,10 +401,12 @@ k_lin_elem_apply(const double* __restrict__ v, Mesh M, Basis B,
                        : (f == FACE_B) ? B.dgL[j] : B.dgR[j];
         const size_t of = ((size_t)e * 4 + f) * N + s;
         const double sx = gf[GF_SX * FNs + of] * w * ij, sy = gf[GF_SY * FNs + of] * w * ij;
+        const bool bface = f == FACE_B && qsrc[f] < 0;   // below row 0 of a bounded mesh
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const double jump = qcv[(((size_t)qsrc[f] * 2 + qdir[f]) * 4 + c) * N + s] -
-                              tqv[(((size_t)e * 4 + f) * 4 + c) * N + s];
+          const double qc = bface ? qbv[((size_t)e * 4 + c) * N + s]
+                                  : qcv[(((size_t)qsrc[f] * 2 + qdir[f]) * 4 + c) * N + s];
+          const double jump = qc - tqv[(((size_t)e * 4 + f) * 4 + c) * N + s];
           g[c] += jump * sx;
           g[4 + c] += jump * sy;
         }
@@ -309,7 +438,8 @@ k_lin_elem_apply(const double* __restrict__ v, Mesh M, Basis B,
     for (int k = 0; k < N; ++k) d = fma(B.Dc[j][k], sG[le][r][k * N + i], d);
     d = fma(B.dgL[i], fnv[(((size_t)nbL * 2 + 0) * 4 + r) * N + j], d);
     d = fma(B.dgR[i], fnv[(((size_t)e * 2 + 0) * 4 + r) * N + j], d);
-    d = fma(B.dgL[j], fnv[(((size_t)nbB * 2 + 1) * 4 + r) * N + i], d);
+    d = fma(B.dgL[j], nbB < 0 ? fbv[((size_t)e * 4 + r) * N + i]
+                              : fnv[(((size_t)nbB * 2 + 1) * 4 + r) * N + i], d);
     d = fma(B.dgR[j], fnv[(((size_t)e * 2 + 1) * 4 + r) * N + i], d);
     double p = 0.0;
 #pragma unroll
@@ -425,6 +555,33 @@ __global__ void k_lin_face_adjoint(Mesh M, const double* __restrict__ JFQ,
   const int e = idx / (2 * N), rem = idx % (2 * N), dir = rem / N, t = rem % N;
   const int plus = dir == 0 ? M.right(e) : M.top(e);
   const int fm = dir == 0 ? FACE_R : FACE_T, fp = dir == 0 ? FACE_L : FACE_B;
+  if (plus < 0) {   // boundary face above the element: q^com = D_b q-, no '+' side
+    double af[4], aqe[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const size_t im = (((size_t)e * 4 + fm) * 4 + r) * N + t;
+      af[r] = afn[im];
+      aqe[r] = (bc_pass(-plus, r) - 1.0) * aqc[im];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      double sm = aqe[c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) sm = fma(JFQ[(size_t)(r * 8 + c) * nf + idx], af[r], sm);
+      atq[(((size_t)e * 4 + fm) * 4 + c) * N + t] = sm;
+    }
+    if (M.viscous) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        double sm = 0.0;
+#pragma unroll
+        for (int r = 1; r < 4; ++r)
+          if (c % 4) sm = fma(JFG[(size_t)(r * 16 + c) * nf + idx], af[r], sm);
+        atg[(((size_t)e * 4 + fm) * 8 + c) * N + t] = sm;
+      }
+    }
+    return;
+  }
   double afs[4], aqm[4], aqp[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
@@ -460,6 +617,45 @@ __global__ void k_lin_face_adjoint(Mesh M, const double* __restrict__ JFQ,
       }
       atg[(((size_t)e * 4 + fm) * 8 + c) * N + t] = sm;
       atg[(((size_t)plus * 4 + fp) * 8 + c) * N + t] = sp;
+    }
+  }
+}
+
+// Boundary faces below row 0: the adjoints of the element's B-face trace and gradient
+// trace (no other element shares the face).
+template <int N>
+__global__ void k_lin_face_below_adjoint(Mesh M, const double* __restrict__ JFQb,
+                                         const double* __restrict__ JFGb, int nrow,
+                                         const double* __restrict__ afn, const double* __restrict__ aqc,
+                                         double* __restrict__ atq, double* __restrict__ atg) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nb = nrow * N;
+  if (idx >= nb) return;
+  const int e = idx / N, t = idx % N;
+  const int below = M.bottom(e);
+  if (below >= 0) return;
+  double af[4], aqe[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const size_t ib = (((size_t)e * 4 + FACE_B) * 4 + r) * N + t;
+    af[r] = afn[ib];
+    aqe[r] = (bc_pass(-below, r) - 1.0) * aqc[ib];
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    double sm = aqe[c];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) sm = fma(JFQb[(size_t)(r * 4 + c) * nb + idx], af[r], sm);
+    atq[(((size_t)e * 4 + FACE_B) * 4 + c) * N + t] = sm;
+  }
+  if (M.viscous) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      double sm = 0.0;
+#pragma unroll
+      for (int r = 1; r < 4; ++r)
+        if (c % 4) sm = fma(JFGb[(size_t)(r * 8 + c) * nb + idx], af[r], sm);
+      atg[(((size_t)e * 4 + FACE_B) * 8 + c) * N + t] = sm;
     }
   }
 }
@@ -558,6 +754,26 @@ static int linearize_n(fr_ctx* c, const double* q, cudaStream_t s) {
     FR_PROF_END(c, s, KK_FACE);
     FR_LAUNCH_CHECK(c);
   }
+  const int nbf = c->bounded ? c->nx * N : 0;   // flux points of the faces below row 0
+  if (nbf > 0) {
+    {
+      FR_PROF_BEGIN(c, s);
+      k_face_below<double, N><<<(nbf + 127) / 128, 128, 0, s>>>(c->mesh, c->basis, c->gf,
+                                                                Buf<double>{c->tq}, Buf<double>{c->tg},
+                                                                Buf<double>{c->fnb}, Buf<double>{c->qcb},
+                                                                c->nx);
+      FR_PROF_END(c, s, KK_FACE);
+      FR_LAUNCH_CHECK(c);
+    }
+    {
+      FR_ACCOUNT(c, KK_LINEARIZE, (visc ? 12.0 : 4.0) * nbf * FR_JVP_FLOP_FACTOR * fr_flops_face_point(visc), 0.0);
+      FR_PROF_BEGIN(c, s);
+      k_lin_face_below<N><<<(nbf + 127) / 128, 128, 0, s>>>(c->mesh, c->basis, c->gf, c->tq, c->tg,
+                                                            c->nx, c->JFQb, c->JFGb);
+      FR_PROF_END(c, s, KK_LINEARIZE);
+      FR_LAUNCH_CHECK(c);
+    }
+  }
   {
     FR_ACCOUNT(c, KK_LINEARIZE, (visc ? 24.0 : 8.0) * nf * FR_JVP_FLOP_FACTOR * fr_flops_face_point(visc), 0.0);
     FR_PROF_BEGIN(c, s);
@@ -570,7 +786,7 @@ static int linearize_n(fr_ctx* c, const double* q, cudaStream_t s) {
     FR_ACCOUNT(c, KK_LINEARIZE, (double)c->ne * N * N * (visc ? 12.0 : 4.0) * FR_JVP_FLOP_FACTOR * 95.0, 0.0);
     FR_PROF_BEGIN(c, s);
     k_lin_point<N><<<nblk, TH, 0, s>>>(q, c->mesh, c->basis, c->gs, c->gf, c->gl, c->tq,
-                                       c->qcm, c->JP, c->JG, c->PP);
+                                       c->qcm, c->qcb, c->JP, c->JG, c->PP);
     FR_PROF_END(c, s, KK_LINEARIZE);
     FR_LAUNCH_CHECK(c);
   }
@@ -583,6 +799,7 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
   constexpr int EPB = Tile<N>::EPB, TH = Tile<N>::THREADS;
   const int nblk = (c->ne + EPB - 1) / EPB;
   const int nf = c->ne * 2 * N;
+  const int nbf = c->bounded ? c->nx * N : 0;   // flux points of the faces below row 0
   const bool visc = c->mesh.viscous;
   const double np = (double)c->ne * N * N;
   // algorithmic flops of the linear operator per solution point and per owned flux point
@@ -615,16 +832,26 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
       FR_PROF_END(c, s, KK_LIN_APPLY);
       FR_LAUNCH_CHECK(c);
     }
+    if (nbf > 0) {
+      FR_ACCOUNT(c, KK_LIN_APPLY, nbf * fl_face, 0.0);
+      FR_PROF_BEGIN(c, s);
+      k_lin_face_below_apply<N><<<(nbf + 127) / 128, 128, 0, s>>>(c->mesh, c->tq_d, c->tg_d, c->JFQb,
+                                                                  c->JFGb, c->nx, c->fnb_d, c->qcb_d);
+      FR_PROF_END(c, s, KK_LIN_APPLY);
+      FR_LAUNCH_CHECK(c);
+    }
     {
       FR_ACCOUNT(c, KK_LIN_APPLY, np * fl_elem, 0.0);
       FR_PROF_BEGIN(c, s);
       if (c->tile.lin_elem == 2)
         k_lin_elem_apply<N, 2><<<(c->ne + Tile<N, 2>::EPB - 1) / Tile<N, 2>::EPB, Tile<N, 2>::THREADS,
                                  0, s>>>(v, c->mesh, c->basis, c->gs, c->gf, c->gl_d, c->tq_d,
-                                         c->fn_d, c->qcm_d, c->JP, c->JG, c->PP, out);
+                                         c->fn_d, c->qcm_d, c->JP, c->JG, c->PP, c->fnb_d,
+                                         c->qcb_d, out);
       else
         k_lin_elem_apply<N><<<nblk, TH, 0, s>>>(v, c->mesh, c->basis, c->gs, c->gf, c->gl_d,
-                                                c->tq_d, c->fn_d, c->qcm_d, c->JP, c->JG, c->PP, out);
+                                                c->tq_d, c->fn_d, c->qcm_d, c->JP, c->JG, c->PP,
+                                                c->fnb_d, c->qcb_d, out);
       FR_PROF_END(c, s, KK_LIN_APPLY);
       FR_LAUNCH_CHECK(c);
     }
@@ -642,6 +869,14 @@ static int apply_n(fr_ctx* c, const double* v, double* out, bool transpose, cuda
       FR_PROF_BEGIN(c, s);
       k_lin_face_adjoint<N><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->JFQ, c->JFG, c->adj_fn,
                                                              c->adj_qc, c->tq_d, c->tg_d);
+      FR_PROF_END(c, s, KK_LIN_ADJOINT);
+      FR_LAUNCH_CHECK(c);
+    }
+    if (nbf > 0) {
+      FR_ACCOUNT(c, KK_LIN_ADJOINT, nbf * fl_face, 0.0);
+      FR_PROF_BEGIN(c, s);
+      k_lin_face_below_adjoint<N><<<(nbf + 127) / 128, 128, 0, s>>>(c->mesh, c->JFQb, c->JFGb, c->nx,
+                                                                    c->adj_fn, c->adj_qc, c->tq_d, c->tg_d);
       FR_PROF_END(c, s, KK_LIN_ADJOINT);
       FR_LAUNCH_CHECK(c);
     }
@@ -666,6 +901,29 @@ int linearize(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStr
     case 3: return linearize_n<3>(c, q, s);
     case 4: return linearize_n<4>(c, q, s);
     case 5: return linearize_n<5>(c, q, s);
+  }
+  return FR_ERR_ARG;
+}
+
+template <int N>
+static int trace_adjoint_n(fr_ctx* c, double* out, cudaStream_t s) {
+  constexpr int EPB = Tile<N>::EPB, TH = Tile<N>::THREADS;
+  const int nblk = (c->ne + EPB - 1) / EPB;
+  FR_ACCOUNT(c, KK_LIN_ADJOINT, (double)c->ne * N * N * fr_flops_trace(N, c->mesh.viscous), 0.0);
+  FR_PROF_BEGIN(c, s);
+  k_lin_trace_adjoint<N><<<nblk, TH, 0, s>>>(c->mesh, c->basis, c->gs, c->adj_q, c->gl_d, c->tq_d,
+                                             c->tg_d, out);
+  FR_PROF_END(c, s, KK_LIN_ADJOINT);
+  FR_LAUNCH_CHECK(c);
+  return FR_OK;
+}
+
+int trace_adjoint(fr_ctx* c, double* out, cudaStream_t s) {
+  switch (c->n) {
+    case 2: return trace_adjoint_n<2>(c, out, s);
+    case 3: return trace_adjoint_n<3>(c, out, s);
+    case 4: return trace_adjoint_n<4>(c, out, s);
+    case 5: return trace_adjoint_n<5>(c, out, s);
   }
   return FR_ERR_ARG;
 }
@@ -752,8 +1010,8 @@ static int autotune_n(fr_ctx* c) {
   FR_TRY(time_launches(c, [&] { k_elem<Dual, N, MODE_JVP><<<nb1, T1>>>(QD, M, B, c->gs, c->gf, GLD, TQD, FND, QCD, c->w_t, tt); }, &a));
   FR_TRY(time_launches(c, [&] { k_elem<Dual, N, MODE_JVP, double, 2><<<nb2, T2>>>(QD, M, B, c->gs, c->gf, GLD, TQD, FND, QCD, c->w_t, tt); }, &b));
   pick(&c->tile.elem_d);
-  FR_TRY(time_launches(c, [&] { k_lin_elem_apply<N><<<nb1, T1>>>(c->w_r, M, B, c->gs, c->gf, c->gl_d, c->tq_d, c->fn_d, c->qcm_d, c->JP, c->JG, c->PP, c->w_t); }, &a));
-  FR_TRY(time_launches(c, [&] { k_lin_elem_apply<N, 2><<<nb2, T2>>>(c->w_r, M, B, c->gs, c->gf, c->gl_d, c->tq_d, c->fn_d, c->qcm_d, c->JP, c->JG, c->PP, c->w_t); }, &b));
+  FR_TRY(time_launches(c, [&] { k_lin_elem_apply<N><<<nb1, T1>>>(c->w_r, M, B, c->gs, c->gf, c->gl_d, c->tq_d, c->fn_d, c->qcm_d, c->JP, c->JG, c->PP, c->fnb_d, c->qcb_d, c->w_t); }, &a));
+  FR_TRY(time_launches(c, [&] { k_lin_elem_apply<N, 2><<<nb2, T2>>>(c->w_r, M, B, c->gs, c->gf, c->gl_d, c->tq_d, c->fn_d, c->qcm_d, c->JP, c->JG, c->PP, c->fnb_d, c->qcb_d, c->w_t); }, &b));
   pick(&c->tile.lin_elem);
   FR_CUDA_CHECK(c, cudaDeviceSynchronize());
   return FR_OK;

@@ -1073,7 +1073,8 @@ int mg_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStre
 
 int precond_apply(fr_ctx* c, const double* q, const double* r, double* z, double inv_dtau,
                   double a0_dt, cudaStream_t s) {
-  if (c->cfg.precond != FR_PRECOND_TWO_LEVEL) return block_apply(c, r, z, s);
+  // the adjoint solve (A^T) takes the transposed element blocks alone
+  if (c->cfg.precond != FR_PRECOND_TWO_LEVEL || c->transposed) return block_apply(c, r, z, s);
   if (c->cfg.mg_prec == FR_PREC_FP64) return apply_t<double>(c, q, r, z, inv_dtau, a0_dt, s);
   return apply_t<float>(c, q, r, z, inv_dtau, a0_dt, s);
 }

@@ -250,7 +250,8 @@ __global__ void __launch_bounds__(BG * N * N)
 k_block_lin(Mesh M, Basis B, const double* __restrict__ gs, const double* __restrict__ gf,
             const double* __restrict__ JFQ, const double* __restrict__ JFG,
             const double* __restrict__ JP, const double* __restrict__ JG,
-            const double* __restrict__ PP, double* __restrict__ Bout) {
+            const double* __restrict__ PP, const double* __restrict__ JFQb,
+            const double* __restrict__ JFGb, int nbf, double* __restrict__ Bout) {
   constexpr int NP = N * N, BS = 4 * NP;
   using L = BlkLinSmem<N>;
   extern __shared__ double smd[];
@@ -278,8 +279,15 @@ k_block_lin(Mesh M, Basis B, const double* __restrict__ gs, const double* __rest
     const bool minus = (f == FACE_R || f == FACE_T);     // e owns its R and T faces
     const int owner = f == FACE_R || f == FACE_T ? e : f == FACE_L ? M.left(e) : M.bottom(e);
     const int dir = (f == FACE_R || f == FACE_L) ? 0 : 1;
-    const size_t idx = ((size_t)owner * 2 + dir) * N + sp;
     double val;
+    if (owner < 0) {   // boundary face below row 0 of a bounded mesh: e's own trace
+      const size_t ib = (size_t)e * N + sp;
+      if (k < 16) val = JFQb[(size_t)k * nbf + ib];
+      else val = visc ? JFGb[(size_t)(k - 16) * nbf + ib] : 0.0;
+      sJF[t] = val;
+      continue;
+    }
+    const size_t idx = ((size_t)owner * 2 + dir) * N + sp;
     if (k < 16) {
       const int r = k / 4, cc = k % 4;
       val = JFQ[(size_t)(r * 8 + (minus ? cc : 4 + cc)) * nf + idx];
@@ -301,6 +309,16 @@ k_block_lin(Mesh M, Basis B, const double* __restrict__ gs, const double* __rest
   const double ij = gs[GS_INVJ * SN + o];
   // lifting weights of the four faces at this point: S_f g_f' / |J|
   double lsx[4], lsy[4];
+  // share of e's trace in each face's common solution: 1/2 inside, D_b on a boundary face
+  double cs[4][4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const int nbf_ = f == FACE_L ? M.left(e) : f == FACE_R ? M.right(e)
+                   : f == FACE_B ? M.bottom(e) : M.top(e);
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      cs[f][v] = nbf_ >= 0 ? 0.5 : ((-nbf_ == BC_WALL && (v == 0 || v == 3)) ? 1.0 : 0.0);
+  }
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
     const int sp = (f < 2) ? j : i;
@@ -374,7 +392,8 @@ k_block_lin(Mesh M, Basis B, const double* __restrict__ gs, const double* __rest
       }
     }
     __syncthreads();
-    // E: corrected gradient (the common solution holds half of e's trace), point fluxes
+    // E: corrected gradient (the common solution holds the share cs of e's trace), point
+    // fluxes
     double dq[4], g[8];
 #pragma unroll
     for (int v = 0; v < 4; ++v) dq[v] = sq[v * NP + pt];
@@ -394,7 +413,7 @@ k_block_lin(Mesh M, Basis B, const double* __restrict__ gs, const double* __rest
         const int sp = (f < 2) ? j : i;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const double jump = -0.5 * stq[(f * 4 + v) * N + sp];
+          const double jump = (cs[f][v] - 1.0) * stq[(f * 4 + v) * N + sp];
           g[v] = fma(jump, lsx[f], g[v]);
           g[4 + v] = fma(jump, lsy[f], g[4 + v]);
         }
@@ -778,7 +797,7 @@ template <class S, int ACC, int N>
 __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
                          const float* __restrict__ Dc, const double* __restrict__ r, Mesh M,
                          double* __restrict__ z, const double* __restrict__ rsub,
-                         const double* __restrict__ zadd) {
+                         const double* __restrict__ zadd, bool tr) {
   constexpr int NP = N * N, BS = 4 * NP, BSR = (BS + 31) / 32 * 32;
   constexpr int COLS = (BS + APPLY_PARTS - 1) / APPLY_PARTS;   // columns per thread
   __shared__ double xd[ACC == 0 ? BS : 1];
@@ -796,13 +815,16 @@ __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
 #pragma unroll
   for (int k = 0; k < COLS; ++k) {
     const int c2 = part + APPLY_PARTS * k;
-    av[k] = (row < BS && c2 < BS) ? A[(size_t)c2 * BS + row] : S(0.0f);
+    av[k] = (row < BS && c2 < BS) ? A[tr ? (size_t)row * BS + c2 : (size_t)c2 * BS + row] : S(0.0f);
   }
+  // B^-1 = Dc Ainv Dr from the stored transpose of Ainv; B^-T = Dr Ainv^T Dc
+  const float* Din = tr ? Dc : Dr;
+  const float* Dout = tr ? Dr : Dc;
   const size_t qo = M.qbase(e, NP), qs = M.qstride(e);
   for (int t = threadIdx.x; t < BS; t += blockDim.x) {
     const int v = t / NP, pt = t % NP;
     const size_t gi = v * qs + qo + pt;
-    const double u = (rsub ? r[gi] - rsub[gi] : r[gi]) * (double)Dr[(size_t)e * BS + t];
+    const double u = (rsub ? r[gi] - rsub[gi] : r[gi]) * (double)Din[(size_t)e * BS + t];
     if (ACC == 0) xd[t] = u;
     else if (ACC == 1) xf[t] = (float)u;
     else {
@@ -870,7 +892,7 @@ __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
   }
   const int v = row / NP, pt = row % NP;
   const size_t gi = v * qs + qo + pt;
-  const double zr = acc * (double)Dc[(size_t)e * BS + row];
+  const double zr = acc * (double)Dout[(size_t)e * BS + row];
   z[gi] = zadd ? zadd[gi] + zr : zr;
 }
 
@@ -892,7 +914,8 @@ static int block_build_n(fr_ctx* c, const double* q, double inv_dtau, double a0_
     FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_block_lin<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FR_PROF_BEGIN(c, s);
     k_block_lin<N><<<c->ne, BG * N * N, smem, s>>>(c->mesh, c->basis, c->gs, c->gf, c->JFQ, c->JFG,
-                                                   c->JP, c->JG, c->PP, c->B64);
+                                                   c->JP, c->JG, c->PP, c->JFQb, c->JFGb,
+                                                   c->bounded ? c->nx * N : 0, c->B64);
     FR_PROF_END(c, s, KK_BLOCK);
     FR_LAUNCH_CHECK(c);
     return FR_OK;
@@ -1053,18 +1076,19 @@ static int apply_impl(fr_ctx* c, const double* r, double* z, const double* rsub,
   // partial sum, a state-dependent perturbation that left-preconditioned GMRES cannot get
   // below on stiff cases
   const bool df = c->cfg.apply_accum == FR_ACCUM_DF64;
+  const bool tr = c->transposed != 0;   // B^-T in the adjoint solve
   const int nt4 = APPLY_PARTS * ((bs + 31) / 32 * 32);
   const int acc = c->cfg.prec_dtype == FR_PREC_FP64 ? 0 : df ? 2 : 1;
   switch (c->n * 10 + acc) {
 #define FR_APPLY_CASE(NN)                                                                      \
-    case NN * 10 + 0: k_apply4<double, 0, NN><<<c->ne, nt4, 0, s>>>((const double*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd); break; \
+    case NN * 10 + 0: k_apply4<double, 0, NN><<<c->ne, nt4, 0, s>>>((const double*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr); break; \
     case NN * 10 + 1: if (c->cfg.prec_dtype == FR_PREC_FP32)                                  \
-        k_apply4<float, 1, NN><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd); \
-      else k_apply4<__nv_bfloat16, 1, NN><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd); \
+        k_apply4<float, 1, NN><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr); \
+      else k_apply4<__nv_bfloat16, 1, NN><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr); \
       break;                                                                                   \
     case NN * 10 + 2: if (c->cfg.prec_dtype == FR_PREC_FP32)                                  \
-        k_apply4<float, 2, NN><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd); \
-      else k_apply4<__nv_bfloat16, 2, NN><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd); \
+        k_apply4<float, 2, NN><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr); \
+      else k_apply4<__nv_bfloat16, 2, NN><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr); \
       break;
     FR_APPLY_CASE(2) FR_APPLY_CASE(3) FR_APPLY_CASE(4) FR_APPLY_CASE(5)
 #undef FR_APPLY_CASE

@@ -32,76 +32,6 @@ __global__ void k_conservative(const double* __restrict__ q, size_t SN, int np2,
   for (int v = 0; v < 4; ++v) qc[v * qs + qo] = th.qc[v];
 }
 
-// Force on the wall faces (the numerator of the force coefficients of Sec. 4):
-// F = sum over wall faces of the integral of -(p - p_inf) n + tau . n, n the unit normal
-// out of the body (+eta below row 0, -eta above row ny-1), p_inf = R (rho_inf = T_inf =
-// 1), tau from grad q^com of the wall (interior local gradient plus the one-sided lift
-// of q_b - q^-, normal temperature gradient removed), Gauss quadrature over the flux
-// points with ds = |S| dxi.  One block: every thread sums a fixed set of flux points and
-// the block sums in a fixed order (deterministic).  out[0..1] = (F_x, F_y).
-template <int N>
-__global__ void __launch_bounds__(256) k_wall_force(Mesh M, Basis B, const double* __restrict__ gf,
-                                                    const double* __restrict__ tq,
-                                                    const double* __restrict__ tg, int nx, int ny,
-                                                    int wall_below, int wall_above,
-                                                    double* __restrict__ out) {
-  __shared__ double red[2][256 / 32];
-  const Gas& gas = M.par(0).gas;
-  const size_t FNs = (size_t)M.ne * 4 * N;
-  double fx = 0.0, fy = 0.0;
-  for (int idx = threadIdx.x; idx < 2 * nx * N; idx += blockDim.x) {
-    const int side = idx / (nx * N), rem = idx % (nx * N), i = rem / N, t = rem % N;
-    if (side == 0 ? !wall_below : !wall_above) continue;
-    const int e = side == 0 ? i : (ny - 1) * nx + i;
-    const int f = side == 0 ? FACE_B : FACE_T;
-    double qe[4], ge[8];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) qe[v] = tq[(((size_t)e * 4 + f) * 4 + v) * N + t];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) ge[c] = M.viscous ? tg[(((size_t)e * 4 + f) * 8 + c) * N + t] : 0.0;
-    const size_t of = ((size_t)e * 4 + f) * N + t;
-    const double Sx = gf[GF_SX * FNs + of], Sy = gf[GF_SY * FNs + of];
-    const double qb[4] = {qe[0], gf[GF_UG * FNs + of], gf[GF_VG * FNs + of], qe[3]};
-    const double smag = sqrt(Sx * Sx + Sy * Sy);
-    const double sgn = side == 0 ? 1.0 : -1.0;
-    const double nbx = sgn * Sx / smag, nby = sgn * Sy / smag;
-    double tx = -(qb[0] - gas.R) * nbx, ty = -(qb[0] - gas.R) * nby;
-    if (M.viscous) {
-      const double lift = (side == 0 ? -B.dgR_end : B.dgR_end) / gf[GF_J * FNs + of];
-      double gx[4], gy[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const double jl = (qb[k] - qe[k]) * lift;
-        gx[k] = ge[k] + jl * Sx;
-        gy[k] = ge[4 + k] + jl * Sy;
-      }
-      const double gn = (gx[3] * Sx + gy[3] * Sy) / (Sx * Sx + Sy * Sy);
-      gx[3] -= gn * Sx;
-      gy[3] -= gn * Sy;
-      double fv[4], gv[4];
-      neg_viscous_flux(qb, gx, gy, gas, fv, gv);   // -f_vis, -g_vis
-      tx -= fv[1] * nbx + gv[1] * nby;
-      ty -= fv[2] * nbx + gv[2] * nby;
-    }
-    const double w = B.ws[t] * smag;
-    fx += w * tx;
-    fy += w * ty;
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    fx += __shfl_down_sync(0xffffffffu, fx, off);
-    fy += __shfl_down_sync(0xffffffffu, fy, off);
-  }
-  if (lane == 0) { red[0][wid] = fx; red[1][wid] = fy; }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    double acc = 0.0;
-    for (int w2 = 0; w2 < 256 / 32; ++w2) acc += red[threadIdx.x][w2];
-    out[threadIdx.x] = acc;
-  }
-}
-
 // ------------------------------------------------------------------ launchers
 template <class T, int N, int MODE>
 static int run_pipeline(fr_ctx* c, Buf<T> Q, Buf<T> GL, Buf<T> TQ, Buf<T> TG, Buf<T> FNb,

@@ -65,7 +65,7 @@ __global__ void k_sens_gather(Mesh M, int k, int a, int xy, const double* __rest
   double s = edot[e];
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
-    bool dup = nb[f] == e;
+    bool dup = nb[f] == e || nb[f] < 0;   // a boundary face has no neighbour
     for (int g = 0; g < f; ++g) dup = dup || nb[g] == nb[f];
     if (!dup) s += edot[nb[f]];
   }
@@ -77,11 +77,12 @@ __global__ void k_sens_gather(Mesh M, int k, int a, int xy, const double* __rest
 namespace frk {
 using namespace fr;
 
-// R' = tangent of R for the corner / velocity tangents (dcorn, dvel, either may be null)
-// and the Mach tangent dmach, into c->rtan.
+// R' = tangent of R for the corner / velocity tangents (dcorn, dvel, either may be null),
+// the Mach tangent dmach and the far-field state's tangent dqinf, into c->rtan.
 template <int N>
 static int tangent_pass(fr_ctx* c, const double* q, const double* corners, const double* vel,
-                        const double* dcorn, const double* dvel, double dmach, cudaStream_t s) {
+                        const double* dcorn, const double* dvel, double dmach, Vec4 dqinf,
+                        cudaStream_t s) {
   constexpr int EPB = Tile<N>::EPB, TH = Tile<N>::THREADS;
   const int ne = c->ne, nblk = (ne + EPB - 1) / EPB, nf = ne * 2 * N;
   k_geometry<N, Dual><<<(ne + 63) / 64, 64, 0, s>>>(corners, vel, ne, c->basis, Buf<Dual>{c->sgs, c->sdgs},
@@ -93,22 +94,53 @@ static int tangent_pass(fr_ctx* c, const double* q, const double* corners, const
   k_trace<Dual, N, Dual><<<nblk, TH, 0, s>>>(Q, c->mesh, c->basis, c->sgs, GL, TQ, TG, c->sdgs);
   FR_LAUNCH_CHECK(c);
   k_face<Dual, N, Dual><<<(nf + 127) / 128, 128, 0, s>>>(c->mesh, c->basis, c->sgf, TQ, TG, FN, QC,
-                                                         c->sdgf, dmach);
+                                                         c->sdgf, dmach, dqinf);
   FR_LAUNCH_CHECK(c);
+  const Buf<Dual> FB{c->fnb, c->fnb_d}, QB{c->qcb, c->qcb_d};
+  if (c->bounded) {   // the faces below row 0
+    const int nbf = c->nx * N;
+    k_face_below<Dual, N, Dual><<<(nbf + 127) / 128, 128, 0, s>>>(c->mesh, c->basis, c->sgf, TQ, TG, FB,
+                                                                  QB, c->nx, c->sdgf, dmach, dqinf);
+    FR_LAUNCH_CHECK(c);
+  }
   k_elem<Dual, N, MODE_TAN, Dual><<<nblk, TH, 0, s>>>(Q, c->mesh, c->basis, c->sgs, c->sgf, GL, TQ, FN,
                                                       QC, c->rtan, TimeTerms{nullptr, nullptr},
-                                                      c->sdgs, c->sdgf, dmach);
+                                                      c->sdgs, c->sdgf, dmach, FB, QB);
   FR_LAUNCH_CHECK(c);
   return FR_OK;
 }
 
 static int tangent(fr_ctx* c, const double* q, const double* corners, const double* vel,
-                   const double* dcorn, const double* dvel, double dmach, cudaStream_t s) {
+                   const double* dcorn, const double* dvel, double dmach, cudaStream_t s,
+                   Vec4 dqinf = Vec4{}) {
   switch (c->n) {
-    case 2: return tangent_pass<2>(c, q, corners, vel, dcorn, dvel, dmach, s);
-    case 3: return tangent_pass<3>(c, q, corners, vel, dcorn, dvel, dmach, s);
-    case 4: return tangent_pass<4>(c, q, corners, vel, dcorn, dvel, dmach, s);
-    case 5: return tangent_pass<5>(c, q, corners, vel, dcorn, dvel, dmach, s);
+    case 2: return tangent_pass<2>(c, q, corners, vel, dcorn, dvel, dmach, dqinf, s);
+    case 3: return tangent_pass<3>(c, q, corners, vel, dcorn, dvel, dmach, dqinf, s);
+    case 4: return tangent_pass<4>(c, q, corners, vel, dcorn, dvel, dmach, dqinf, s);
+    case 5: return tangent_pass<5>(c, q, corners, vel, dcorn, dvel, dmach, dqinf, s);
+  }
+  return FR_ERR_ARG;
+}
+
+// Tangents (F_x', F_y') of the wall force at fixed q along the direction of the last
+// tangent pass: its geometry (sgf, sdgf) and dual traces (tq, tg with their tangents, the
+// local gradients moving with the geometry), and the Mach tangent dmach; into out[0..3]
+// (values, tangents).
+template <int N>
+static int wall_force_tangent_n(fr_ctx* c, double dmach, double* out, cudaStream_t s) {
+  k_wall_force<N, Dual><<<1, 256, 0, s>>>(c->mesh, c->basis, c->sgf, c->tq, c->tg, c->nx, c->ny,
+                                          c->bc_below == FR_BC_WALL, c->bc_above == FR_BC_WALL, out,
+                                          c->sdgf, dmach, c->tq_d, c->tg_d);
+  FR_LAUNCH_CHECK(c);
+  return FR_OK;
+}
+
+static int wall_force_tangent(fr_ctx* c, double dmach, double* out, cudaStream_t s) {
+  switch (c->n) {
+    case 2: return wall_force_tangent_n<2>(c, dmach, out, s);
+    case 3: return wall_force_tangent_n<3>(c, dmach, out, s);
+    case 4: return wall_force_tangent_n<4>(c, dmach, out, s);
+    case 5: return wall_force_tangent_n<5>(c, dmach, out, s);
   }
   return FR_ERR_ARG;
 }
@@ -116,6 +148,35 @@ static int tangent(fr_ctx* c, const double* q, const double* corners, const doub
 template <class T> static int lazy_alloc(fr_ctx* c, T** p, size_t n) {
   if (*p) return FR_OK;
   FR_CUDA_CHECK(c, cudaMalloc((void**)p, n * sizeof(T)));
+  return FR_OK;
+}
+
+// workspace of the tangent passes (allocated once per mesh), zero state tangent
+static int sens_alloc(fr_ctx* c, cudaStream_t s) {
+  const size_t ne = c->ne, SN = ne * c->np2, FN = ne * 4 * c->n;
+  FR_TRY(lazy_alloc(c, &c->sgs, GS_COUNT * SN));
+  FR_TRY(lazy_alloc(c, &c->sdgs, GS_COUNT * SN));
+  FR_TRY(lazy_alloc(c, &c->sgf, GF_COUNT * FN));
+  FR_TRY(lazy_alloc(c, &c->sdgf, GF_COUNT * FN));
+  FR_TRY(lazy_alloc(c, &c->seed, 8 * ne));
+  FR_TRY(lazy_alloc(c, &c->edot, ne));
+  FR_TRY(lazy_alloc(c, &c->zero, c->ndof));
+  FR_TRY(lazy_alloc(c, &c->rtan, c->ndof));
+  FR_CUDA_CHECK(c, cudaMemsetAsync(c->zero, 0, c->ndof * sizeof(double), s));
+  return FR_OK;
+}
+
+// sum of w . r over the elements, added on the host in element order (deterministic)
+static int wdot(fr_ctx* c, const double* w, const double* r, double* out_h, cudaStream_t s) {
+  const int wb = (int)(((size_t)c->ne * 32 + 255) / 256);
+  k_sens_edot<<<wb, 256, 0, s>>>(c->mesh, c->np2, w, r, c->edot);
+  FR_LAUNCH_CHECK(c);
+  std::vector<double> h(c->ne);
+  FR_CUDA_CHECK(c, cudaMemcpyAsync(h.data(), c->edot, (size_t)c->ne * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FR_CUDA_CHECK(c, cudaStreamSynchronize(s));
+  double acc = 0.0;
+  for (double x : h) acc += x;
+  *out_h = acc;
   return FR_OK;
 }
 
@@ -129,30 +190,13 @@ extern "C" int fr_param_vjp(fr_ctx* c, const double* q, const double* w, const d
   if (c->ne <= 0) { snprintf(c->err, sizeof(c->err), "fr_set_mesh has not been called"); return FR_ERR_ARG; }
   if (!q || !w || !corners || !vel) return FR_ERR_ARG;
   if (c->ncases != 1) { snprintf(c->err, sizeof(c->err), "fr_param_vjp: single-case contexts only"); return FR_ERR_ARG; }
-  if (c->bounded) { snprintf(c->err, sizeof(c->err), "fr_param_vjp: not available on bounded meshes"); return FR_ERR_ARG; }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const size_t ne = c->ne, SN = ne * c->np2, FN = ne * 4 * c->n;
-  FR_TRY(frk::lazy_alloc(c, &c->sgs, GS_COUNT * SN));
-  FR_TRY(frk::lazy_alloc(c, &c->sdgs, GS_COUNT * SN));
-  FR_TRY(frk::lazy_alloc(c, &c->sgf, GF_COUNT * FN));
-  FR_TRY(frk::lazy_alloc(c, &c->sdgf, GF_COUNT * FN));
-  FR_TRY(frk::lazy_alloc(c, &c->seed, 8 * ne));
-  FR_TRY(frk::lazy_alloc(c, &c->edot, ne));
-  FR_TRY(frk::lazy_alloc(c, &c->zero, c->ndof));
-  FR_TRY(frk::lazy_alloc(c, &c->rtan, c->ndof));
-  FR_CUDA_CHECK(c, cudaMemsetAsync(c->zero, 0, c->ndof * sizeof(double), s));
+  FR_TRY(frk::sens_alloc(c, s));
+  const size_t ne = c->ne;
   const int eb = (int)((ne + 127) / 128), wb = (int)((ne * 32 + 255) / 256);
   if (dmach) {
     FR_TRY(frk::tangent(c, q, corners, vel, nullptr, nullptr, 1.0, s));
-    k_sens_edot<<<wb, 256, 0, s>>>(c->mesh, c->np2, w, c->rtan, c->edot);
-    FR_LAUNCH_CHECK(c);
-    // the elements' dot products summed on the host in element order (deterministic)
-    std::vector<double> h(ne);
-    FR_CUDA_CHECK(c, cudaMemcpyAsync(h.data(), c->edot, ne * sizeof(double), cudaMemcpyDeviceToHost, s));
-    FR_CUDA_CHECK(c, cudaStreamSynchronize(s));
-    double acc = 0.0;
-    for (size_t e = 0; e < ne; ++e) acc += h[e];
-    *dmach = acc;
+    FR_TRY(frk::wdot(c, w, c->rtan, dmach, s));
   }
   const int ncol = ncolour1d(c->cps[0].nx) * 5;   // colour ids i * 5 + j, j < ncolour1d(ny)
   const int ncj = ncolour1d(c->cps[0].ny);
@@ -174,6 +218,36 @@ extern "C" int fr_param_vjp(fr_ctx* c, const double* q, const double* w, const d
         }
       }
     }
+  }
+  return FR_OK;
+}
+
+extern "C" int fr_param_jvp(fr_ctx* c, const double* q, const double* w, const double* corners,
+                            const double* vel, const double* dcorners, const double* dvel,
+                            double dmach, const double* dqinf_h, double* wdR_h, double* dforce_h,
+                            void* stream) {
+  using namespace fr;
+  if (!c) return FR_ERR_ARG;
+  if (c->ne <= 0) { snprintf(c->err, sizeof(c->err), "fr_set_mesh has not been called"); return FR_ERR_ARG; }
+  if (!q || !corners || !vel || (wdR_h && !w)) return FR_ERR_ARG;
+  if (c->ncases != 1) { snprintf(c->err, sizeof(c->err), "fr_param_jvp: single-case contexts only"); return FR_ERR_ARG; }
+  if (dforce_h && (!c->bounded || (c->bc_below != FR_BC_WALL && c->bc_above != FR_BC_WALL))) {
+    snprintf(c->err, sizeof(c->err), "fr_param_jvp: the mesh has no wall faces");
+    return FR_ERR_ARG;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  FR_TRY(frk::sens_alloc(c, s));
+  Vec4 dq{};
+  if (dqinf_h) for (int k = 0; k < 4; ++k) dq.v[k] = dqinf_h[k];
+  FR_TRY(frk::tangent(c, q, corners, vel, dcorners, dvel, dmach, s, dq));
+  if (wdR_h) FR_TRY(frk::wdot(c, w, c->rtan, wdR_h, s));
+  if (dforce_h) {
+    FR_TRY(frk::wall_force_tangent(c, dmach, c->red, s));
+    double h4[4];
+    FR_CUDA_CHECK(c, cudaMemcpyAsync(h4, c->red, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FR_CUDA_CHECK(c, cudaStreamSynchronize(s));
+    dforce_h[0] = h4[2];
+    dforce_h[1] = h4[3];
   }
   return FR_OK;
 }

@@ -109,6 +109,12 @@ _SIGS = {
     "fr_vjp": (_I, [_P, _P, _P, _D, _D, _P, _P]),
     "fr_tiles": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "fr_param_vjp": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_D), _P, _P, _P]),
+    "fr_param_jvp": (_I, [_P, _P, _P, _P, _P, _P, _P, _D, ctypes.POINTER(_D), ctypes.POINTER(_D),
+                          ctypes.POINTER(_D), _P]),
+    "fr_adjoint_solve": (_I, [_P, _P, _P, _D, _D, _P, ctypes.POINTER(_I), _P]),
+    "fr_wall_force_vjp": (_I, [_P, _P, _D, _D, _D, _D, _P, _P]),
+    "fr_conservative_vjp": (_I, [_P, _P, _P, _D, _D, _P, _P]),
+    "fr_conservative_dmach": (_I, [_P, _P, _P, ctypes.POINTER(_D), _P]),
     "fr_batch_create": (_I, [ctypes.POINTER(_Config), _P, _I, ctypes.POINTER(_P)]),
     "fr_batch_destroy": (None, [_P]),
     "fr_batch_case_info": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
@@ -463,6 +469,46 @@ class Solver:
             _ptr(dcorners) if dcorners is not None else None,
             _ptr(dvel) if dvel is not None else None, _stream(stream)))
         return dm.value if mach else None
+
+    def param_jvp(self, q, corners, vel, dcorners=None, dvel=None, dmach=0.0, dqinf=None, w=None,
+                  force=False, stream=None):
+        """Directional derivative at fixed q along (dcorners, dvel, dmach, dqinf): returns
+        (w . R' or None, (F_x', F_y') or None)."""
+        wd = ctypes.c_double(0.0)
+        f = (ctypes.c_double * 2)()
+        dq = (ctypes.c_double * 4)(*dqinf) if dqinf is not None else None
+        self._check(self.lib.fr_param_jvp(
+            self.ctx, _ptr(q), _ptr(w) if w is not None else None, _ptr(corners), _ptr(vel),
+            _ptr(dcorners) if dcorners is not None else None,
+            _ptr(dvel) if dvel is not None else None, float(dmach), dq,
+            ctypes.byref(wd) if w is not None else None, f if force else None, _stream(stream)))
+        return (wd.value if w is not None else None), ((float(f[0]), float(f[1])) if force else None)
+
+    def adjoint_solve(self, q, g, lam, inv_dtau=0.0, a0_dt=0.0, stream=None) -> int:
+        """A^T lam = g at q (transposed GMRES with the transposed element blocks)."""
+        its = ctypes.c_int(0)
+        self._check(self.lib.fr_adjoint_solve(self.ctx, _ptr(q), _ptr(g), inv_dtau, a0_dt,
+                                              _ptr(lam), ctypes.byref(its), _stream(stream)))
+        return its.value
+
+    def wall_force_vjp(self, q, wx, wy, out, alpha=1.0, beta=0.0, stream=None):
+        """out = beta out + alpha d(wx F_x + wy F_y)/dq."""
+        self._check(self.lib.fr_wall_force_vjp(self.ctx, _ptr(q), float(wx), float(wy), float(alpha),
+                                               float(beta), _ptr(out), _stream(stream)))
+        return out
+
+    def conservative_vjp(self, q, w, out, alpha=1.0, beta=0.0, stream=None):
+        """out = beta out + alpha (dq^c/dq)^T w."""
+        self._check(self.lib.fr_conservative_vjp(self.ctx, _ptr(q), _ptr(w), float(alpha),
+                                                 float(beta), _ptr(out), _stream(stream)))
+        return out
+
+    def conservative_dmach(self, q, w, stream=None) -> float:
+        """sum of w . dq^c/dM at fixed q."""
+        d = ctypes.c_double(0.0)
+        self._check(self.lib.fr_conservative_dmach(self.ctx, _ptr(q), _ptr(w), ctypes.byref(d),
+                                                   _stream(stream)))
+        return d.value
 
     def precond_build(self, q, inv_dtau=0.0, a0_dt=0.0, stream=None):
         self._check(self.lib.fr_precond_build(self.ctx, _ptr(q), inv_dtau, a0_dt, _stream(stream)))

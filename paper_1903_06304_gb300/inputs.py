@@ -94,19 +94,22 @@ def _stretch_ratio(nj: int, first: float, span: float) -> float:
     return 0.5 * (lo + hi)
 
 
-def naca_ogrid(ni: int = 256, nj: int = 96, r_far: float = 20.0, first: float = 1e-3) -> np.ndarray:
+def naca_ogrid(ni: int = 256, nj: int = 96, r_far: float = 20.0, first: float = 1e-3,
+               blend: float = 0.5) -> np.ndarray:
     """Corners ``[ni*nj, 4, 2]`` of an algebraic O-grid around the NACA 0012 (chord 1,
     leading edge at the origin): element e = j*ni + i, i around the body (periodic:
     the wrap closes at the trailing edge), j from the wall (row 0) to the far field
     (row nj-1), a circle of radius ``r_far`` chords about the mid-chord.
 
-    Around the body, x = (1 + cos s)/2 for s = 2 pi i/ni (cosine clustering at both
-    edges), the lower surface first so that (i, j) is right-handed; the far-field node
-    of column i sits at the angle -s.  Along each column the nodes follow a geometric
+    Around the body, x = (1 - blend) (1 + cos s)/2 + blend |1 - s/pi| for s = 2 pi i/ni:
+    cosine clustering at both edges (smallest chordwise spacing about (pi/ni)^2 at
+    ``blend`` = 0) blended with a uniform distribution (about 2 ``blend``/ni at the edges
+    when ``blend`` > 0), the lower surface first so that (i, j) is right-handed; the
+    far-field node of column i sits at the angle -s.  Along each column the nodes follow a geometric
     distribution from the wall node to the far-field node whose first cell is ``first``
     of the wall-to-far-field distance at the mid-chord."""
     s = 2.0 * math.pi * np.arange(ni) / ni
-    xw = 0.5 * (1.0 + np.cos(s))
+    xw = (1.0 - blend) * 0.5 * (1.0 + np.cos(s)) + blend * np.abs(1.0 - s / math.pi)
     yt = naca0012_half_thickness(xw)
     yw = np.where(s <= math.pi, -yt, yt)
     xf = 0.5 + r_far * np.cos(-s)

@@ -44,6 +44,13 @@ def test_naca_ogrid_geometry():
     d0 = np.hypot(*(c[col, 3] - c[col, 0]))
     dall = np.hypot(*(c[(nj - 1) * ni + col, 3] - c[col, 0]))
     assert abs(d0 / dall * r_far - first) <= 1e-6 * first
+    # the blended chordwise distribution: every wall spacing in x is at least the uniform
+    # part's 2 blend / ni (cosine clustering alone gives (pi/ni)^2 at the edges)
+    blend = 0.5
+    dx = np.abs(np.diff(np.append(wall[:, 0], wall[0, 0])))
+    assert dx.min() >= 2 * blend / ni * (1 - 1e-12) and dx.min() < 1.1 * 2 * blend / ni
+    cc = inp.naca_ogrid(ni, nj, r_far, first, blend=0.0)[:ni, 0]
+    assert np.abs(np.diff(cc[:, 0])).min() < (math.pi / ni) ** 2 * 1.01
     # positive Jacobian at every solution and flux point (p = 3)
     geo = element_geometry(c, np.zeros_like(c), make_basis(3))
     assert geo.sol.J.min() > 0 and min(f.J.min() for f in geo.faces) > 0
@@ -52,7 +59,7 @@ def test_naca_ogrid_geometry():
     exact = 1.2 * (0.2969 * 2 / 3 - 0.1260 / 2 - 0.3516 / 3 + 0.2843 / 4 - 0.1036 / 5)
     errs = []
     for n in (64, 128, 256):
-        w = inp.naca_ogrid(n, 4)[:n, 0]
+        w = inp.naca_ogrid(n, 4, blend=0.0)[:n, 0]
         errs.append(abs(_polygon_area(w[:, 0], w[:, 1]) - exact) / exact)
     assert errs[-1] < 2e-4 and errs[0] / errs[-1] > 12, errs   # second order in 1/ni
 
