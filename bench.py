@@ -937,7 +937,7 @@ def kernels_only(args):
     c, v, q = inp.make_case(w, t=0.13 if w.deforming else 0.0)
     T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda:0")
     S = fr.Solver(fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
-                            restart=args.restart, maxit_lin=args.maxit_lin,
+                            factor=args.factor, restart=args.restart, maxit_lin=args.maxit_lin,
                             precond=args.precond, graphs=args.graphs), w.nx, w.ny)
     S.update_mesh(T(c), T(v))
     qd = T(q)
@@ -1084,6 +1084,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ns_vortex_64x64_p3")
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--factor", default="simt", choices=["simt", "tc_bf16", "tc_bf16x3"],
+                    help="block inversion of --kernels-only: SIMT or on the tensor cores")
     ap.add_argument("--precond", default="twolevel", choices=["block", "twolevel"],
                     help="element block Jacobi, or with the P1 coarse correction")
     ap.add_argument("--no-c3", dest="no_c3", action="store_true",
