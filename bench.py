@@ -600,7 +600,8 @@ def gpu_arm(args):
                         tol_pseudo=w.tol_pseudo, maxit_newton=args.maxit_newton, lag=2,
                         line_search=args.line_search, graphs=args.graphs,
                         apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog,
-                        krylov_arith=arith or args.krylov_arith, precond=precond or args.precond)
+                        krylov_arith=arith or args.krylov_arith, precond=precond or args.precond,
+                        mg_prec=args.mg_prec)
         S = fr.Solver(cfg, w.nx, w.ny)
         S.dt = w.dt
         S.update_mesh(T(corners), T(vel))
@@ -883,7 +884,8 @@ def gpu_arm(args):
                    "gmres": f"GMRES({args.restart}) left-preconditioned, {args.orthog}, "
                             f"{args.krylov_arith} basis, maxit {args.maxit_lin}",
                    "newton": f"max {args.maxit_newton} iterations, backtracking {args.line_search} halvings",
-                   "precond": f"{args.precond} ({args.prec} element blocks, {args.apply_accum} apply accumulation)",
+                   "precond": f"{args.precond} ({args.prec} element blocks, {args.apply_accum} apply accumulation"
+                              + (f", {args.mg_prec} coarse levels)" if args.precond == "twolevel" else ")"),
                    "march": f"{args.startup} start-up + {args.warmup} warm-up steps before the timed steps",
                    "l2": "256 MiB write between timed steps, outside the per-step events",
                    "tiles": S.tiles,
@@ -989,7 +991,7 @@ def batch_arm(args):
     cfg = fr.Config(prec=args.prec, restart=args.restart, maxit_lin=args.maxit_lin,
                     maxit_newton=args.maxit_newton, lag=2, line_search=args.line_search,
                     graphs=args.graphs, apply_accum=args.apply_accum,
-                    krylov_arith=args.krylov_arith, precond=args.precond)
+                    krylov_arith=args.krylov_arith, precond=args.precond, mg_prec=args.mg_prec)
     B = fr.Batch(cfg, cases)
     corners = np.zeros((B.ne, 4, 2))
     q = np.zeros(B.ndof)
@@ -1086,6 +1088,8 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--factor", default="simt", choices=["simt", "tc_bf16", "tc_bf16x3"],
                     help="block inversion of --kernels-only: SIMT or on the tensor cores")
+    ap.add_argument("--mg-prec", dest="mg_prec", default="fp32", choices=["fp32", "fp64"],
+                    help="arithmetic of the two-level preconditioner's coarse levels")
     ap.add_argument("--precond", default="twolevel", choices=["block", "twolevel"],
                     help="element block Jacobi, or with the P1 coarse correction")
     ap.add_argument("--no-c3", dest="no_c3", action="store_true",

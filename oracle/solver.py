@@ -281,7 +281,8 @@ def newton_solve(prob: Problem, q, rhs, a0_dt: float, dtau0: float, restart: int
     line_search = k > 0: backtracking on the full residual 2-norm, lambda = 1, 1/2, ...,
     2^-k (the paper takes plain Newton updates, k = 0).  precond: "block" (element
     block Jacobi) or "twolevel" (``oracle.twolevel``: the blocks as smoother plus the
-    P1 coarse correction), either rebuilt every ``lag`` iterations."""
+    P1 coarse correction, its smoothing step with the Newton operator of the build),
+    either rebuilt every ``lag`` iterations."""
     from . import twolevel as tl
     q = q.copy()
     r = rhs(q)
@@ -299,12 +300,14 @@ def newton_solve(prob: Problem, q, rhs, a0_dt: float, dtau0: float, restart: int
         if m % lag == 0 or Binv is None or ser is not None:
             if precond == "twolevel":
                 Binv = tl.build(prob, q, inv_dtau, a0_dt)
+                # the smoothing step applies the operator of the build
+                Abuild = lambda v, qb=q, ib=inv_dtau: apply_A(prob, qb, v, ib, a0_dt)
             else:
                 Binv = np.linalg.inv(block_jacobian(prob, q, inv_dtau, a0_dt))
         qm = q
         Aop = lambda v: apply_A(prob, qm, v, inv_dtau, a0_dt)
         if precond == "twolevel":
-            Minv = lambda v, pc=Binv: pc.apply(v, Aop)
+            Minv = lambda v, pc=Binv, Ab=Abuild: pc.apply(v, Ab)
         else:
             Minv = lambda v, B=Binv: block_apply(B, v)
         out = gmres(Aop, r, Minv, restart, tol_res, maxit_lin, side)

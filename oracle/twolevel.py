@@ -32,11 +32,12 @@ preconditioner adds them back.  Definition (every step plain linear algebra):
   smoothing sweeps, e = V-cycle(l+1, Q^T (b - A_l x)), x = x + Q e, nu sweeps.
 * Preconditioner ("coarse, then smooth"): z0 = P V-cycle(1, P^T r),
   M^-1 r = z0 + B^-1 (r - A z0), B^-1 the element block-Jacobi inverse of the fine
-  operator (``solver.block_jacobian``) and A the operator GMRES is solving with.  The
-  blocks and the coarse operators are built at one linearisation and kept for ``lag``
-  Newton iterations like the blocks alone; A in the correction is the current one.
+  operator (``solver.block_jacobian``) and A the Newton operator of the build.  The
+  blocks, the coarse operators and this A are built at one linearisation and kept for
+  ``lag`` Newton iterations like the blocks alone (on the device, the products of A with
+  the P1 functions that form A_0 are kept, so A z0 needs no operator product).
 
-It is a fixed linear map during one GMRES solve, as GMRES requires.
+It is one fixed linear map between builds, as GMRES requires.
 """
 from __future__ import annotations
 
@@ -205,8 +206,8 @@ class TwoLevel:
         return (self.P @ vcycle(self.h, 0, self.P.T @ r.ravel())).reshape(r.shape)
 
     def apply(self, r, Aop):
-        """M^-1 r with Aop the current Newton operator (a function of a state-shaped
-        vector)."""
+        """M^-1 r with Aop the Newton operator of the build (a function of a state-shaped
+        vector): the preconditioner is one fixed linear map between builds."""
         z0 = self.coarse(r)
         return z0 + sv.block_apply(self.Binv, r - Aop(z0))
 

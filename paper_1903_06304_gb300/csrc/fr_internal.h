@@ -84,6 +84,16 @@ struct MgLevel {
   void *cl = nullptr;         // [ncases] each case's grid on this level
 };
 
+// Input of the block apply fused with the coarse correction (level-0 cells are the
+// elements): z = P y0 + B^-1 (r - (A P) y0), with AP [Ne][5][12][b] and y0 [Ne][12] in
+// the coarse precision, the level-0 stencils nb [Ne][5] and the solution points xs.
+struct CoarseIn {
+  const void* AP = nullptr;
+  const void* y0 = nullptr;
+  const int* nb = nullptr;
+  double xs[5] = {0, 0, 0, 0, 0};
+};
+
 // Kernel classes for the optional per-kernel timing (fr_profile) and launch counts.
 enum FrKernel {
   KK_GEOM, KK_TRACE, KK_FACE, KK_ELEM, KK_TRACE_JVP, KK_FACE_JVP, KK_ELEM_JVP, KK_BLOCK,
@@ -173,7 +183,10 @@ struct fr_ctx {
   int mg_ncol = 0;                 // colours of the level-0 Galerkin products
   int *mg_colslot = nullptr;       // [Ne][ncol]: stencil slot of colour k's member, -1
   double *mg_x = nullptr, *mg_y = nullptr;   // fine seeds and products of the build
-  double *mg_z0 = nullptr, *mg_t = nullptr;  // fine coarse correction and residual
+  // the build's Newton operator applied to the P1 functions of each stencil member,
+  // restricted to the element's rows, [Ne][5][12][b] in the coarse precision (the
+  // smoothing step's A z0 = (A P) y0 without an operator product)
+  void *mg_ap = nullptr;
   int *mg_bad = nullptr;           // singular coarse blocks met by the builds (device)
   void *mg_views = nullptr;        // device copies of the level views (single-block kernels)
   void *mg_tc = nullptr;           // [ncases] per-case level ranges of the single-block kernels
@@ -258,6 +271,9 @@ int block_apply(fr_ctx* c, const double* r, double* z, cudaStream_t s);
 // z = z0 + B^-1 (r - t) in one pass (the smoothing step of the two-level preconditioner)
 int block_apply_fused(fr_ctx* c, const double* r, const double* t, const double* z0, double* z,
                       cudaStream_t s);
+// z = P y0 + B^-1 (r - (A P) y0) in one pass (co = 1: FP32 coarse arrays, 2: FP64)
+int block_apply_coarse(fr_ctx* c, const double* r, double* z, const CoarseIn& ci, int co,
+                       cudaStream_t s);
 // Two-level preconditioner (fr_mg.cu): topology and workspace of the coarse hierarchy
 // (host-built, synchronous; nothing unless cfg.precond asks for it), its build at q after
 // the element blocks, and the configured preconditioner z = M^-1 r (block Jacobi, or the

@@ -15,8 +15,11 @@
 // coloured products of A with the P1 functions of the elements, A_{l+1} = Q^T A_l Q with
 // Q the exact map of a 2 x 2 agglomerate's P1 function to its children; damped 12 x 12
 // block-Jacobi sweeps on every level but a case's last, which (<= 4 cells) is solved by
-// its dense inverse.  Fixed summation orders, no atomics on data: the preconditioner is a
-// fixed linear map during a GMRES solve (up to the rounding of the coarse arithmetic).
+// its dense inverse.  A in the smoothing step is the operator of the build: the coloured
+// products that form A_0 also give the columns A P of every element's stencil members on
+// its own rows, which are stored, so A z0 = (A P) y0 costs no operator product.  Fixed
+// summation orders, no atomics on data: the preconditioner is a fixed linear map between
+// builds (up to the rounding of the coarse arithmetic).
 //
 // Layout for GB300: the coarse levels are stored and swept in the configured coarse
 // precision (FP32 by default: a coarse sweep is 72 multiply-adds per coefficient, which
@@ -25,8 +28,10 @@
 // tiles over all SMs, two launches per level and cycle (sweeps, residual and restriction
 // on the way down; prolongation and sweeps on the way up), each block recomputing the
 // halo its sweeps need; the remaining small levels of each case, with the dense solve, run
-// in one block per case, the phases separated by block barriers.  A cycle thus costs
-// 2 L + 3 launches for L tiled levels, whatever the number of sweeps.
+// in one block per case, the phases separated by block barriers; the restriction from the
+// solution points is one launch, and the prolongation back, A z0 and the block-Jacobi
+// step are the block apply's single pass.  An application thus costs 2 L + 3 launches for
+// L tiled levels, whatever the number of sweeps.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -101,17 +106,22 @@ __global__ void k_p1_seed(fr::Mesh mesh, fr::Basis B, const int* __restrict__ co
 }
 
 // Column k of the level-0 blocks: P^T y on every element whose stencil holds a member of
-// colour col (the seed's response on e comes from that member alone).
+// colour col (the seed's response on e comes from that member alone), and the response
+// itself, the column (A P)_{e,s} e_k of the smoothing step, into AP [Ne][5][12][4 n^2].
+// One thread per element row; the first 12 of an element also form the block column.
 template <int N, class S>
 __global__ void k_p1_gather(fr::Mesh mesh, fr::Basis B, const int* __restrict__ colslot, int ncol,
-                            int col, int k, const double* __restrict__ y, S* __restrict__ A) {
-  constexpr int NP = N * N;
+                            int col, int k, const double* __restrict__ y, S* __restrict__ A,
+                            S* __restrict__ AP) {
+  constexpr int NP = N * N, BS = 4 * NP;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)mesh.ne * NB) return;
-  const int e = (int)(t / NB), r = (int)(t % NB);
+  if (t >= (long long)mesh.ne * BS) return;
+  const int e = (int)(t / BS), r = (int)(t % BS);
   const int s = colslot[(size_t)e * ncol + col];
   if (s < 0) return;
   const size_t base = mesh.qbase(e, NP), qs = mesh.qstride(e);
+  AP[(((size_t)e * SL + s) * NB + k) * BS + r] = (S)y[(r / NP) * qs + base + r % NP];
+  if (r >= NB) return;
   const int v = r / 3, m = r % 3;
   double acc = 0.0;
   for (int pt = 0; pt < NP; ++pt) acc = fma(phi(B, m, pt % N, pt / N), y[v * qs + base + pt], acc);
@@ -131,22 +141,6 @@ __global__ void k_p1_restrict(fr::Mesh mesh, fr::Basis B, const double* __restri
   double acc = 0.0;
   for (int pt = 0; pt < NP; ++pt) acc = fma(phi(B, m, pt % N, pt / N), r[v * qs + base + pt], acc);
   b0[t] = (S)acc;
-}
-
-// z = P x0 (FP64 out)
-template <int N, class S>
-__global__ void k_p1_prolong(fr::Mesh mesh, fr::Basis B, const S* __restrict__ x0,
-                             double* __restrict__ z) {
-  constexpr int NP = N * N;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)mesh.ne * NP) return;
-  const int e = (int)(t / NP), pt = (int)(t % NP);
-  const size_t base = mesh.qbase(e, NP), qs = mesh.qstride(e);
-  const double xi = B.xs[pt % N], eta = B.xs[pt / N];
-  const S* c = x0 + (size_t)e * NB;
-#pragma unroll
-  for (int v = 0; v < 4; ++v)
-    z[v * qs + base + pt] = fma((double)c[3 * v + 2], eta, fma((double)c[3 * v + 1], xi, (double)c[3 * v]));
 }
 
 // ---------------------------------------------------------------- multi-block levels
@@ -682,8 +676,9 @@ int build_level0(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cuda
       FR_TRY(op_apply(c, q, c->mg_x, inv_dtau, a0_dt, c->mg_y, s));
       {
         FR_PROF_BEGIN(c, s);
-        k_p1_gather<N, S><<<blocks_for((long long)c->ne * NB, 256), 256, 0, s>>>(
-            c->mesh, c->basis, c->mg_colslot + (size_t)c->ne, c->mg_ncol, col, k, c->mg_y, (S*)L0.A);
+        k_p1_gather<N, S><<<blocks_for((long long)c->ne * 4 * NP, 256), 256, 0, s>>>(
+            c->mesh, c->basis, c->mg_colslot + (size_t)c->ne, c->mg_ncol, col, k, c->mg_y, (S*)L0.A,
+            (S*)c->mg_ap);
         FR_PROF_END(c, s, KK_COARSE);
         FR_LAUNCH_CHECK(c);
       }
@@ -713,18 +708,15 @@ int build_levels(fr_ctx* c, cudaStream_t s) {
   return FR_OK;
 }
 
+// b0 = P^T r (the prolongation back is fused into the block apply)
 template <int N, class S>
-int fine_transfer(fr_ctx* c, const double* r, double* z0, cudaStream_t s, bool down) {
+int fine_restrict(fr_ctx* c, const double* r, cudaStream_t s) {
   constexpr int NP = N * N;
   FR_PROF_BEGIN(c, s);
-  if (down)
-    k_p1_restrict<N, S><<<blocks_for((long long)c->ne * NB, 256), 256, 0, s>>>(c->mesh, c->basis, r, (S*)c->mg[0].b);
-  else
-    k_p1_prolong<N, S><<<blocks_for((long long)c->ne * NP, 256), 256, 0, s>>>(c->mesh, c->basis, (const S*)c->mg[0].y, z0);
+  k_p1_restrict<N, S><<<blocks_for((long long)c->ne * NB, 256), 256, 0, s>>>(c->mesh, c->basis, r, (S*)c->mg[0].b);
   FR_PROF_END(c, s, KK_COARSE);
   FR_LAUNCH_CHECK(c);
-  FR_ACCOUNT(c, KK_COARSE, 2.0 * NB * c->ne * NP / (down ? 1.0 : 4.0),
-             8.0 * 4.0 * c->ne * NP + (double)sizeof(S) * NB * c->ne);
+  FR_ACCOUNT(c, KK_COARSE, 2.0 * NB * c->ne * NP, 8.0 * 4.0 * c->ne * NP + (double)sizeof(S) * NB * c->ne);
   return FR_OK;
 }
 
@@ -790,24 +782,22 @@ int apply_t(fr_ctx* c, const double* q, const double* r, double* z, double inv_d
             cudaStream_t s) {
   int rc;
   switch (c->n) {
-    case 2: rc = fine_transfer<2, S>(c, r, nullptr, s, true); break;
-    case 3: rc = fine_transfer<3, S>(c, r, nullptr, s, true); break;
-    case 4: rc = fine_transfer<4, S>(c, r, nullptr, s, true); break;
-    case 5: rc = fine_transfer<5, S>(c, r, nullptr, s, true); break;
+    case 2: rc = fine_restrict<2, S>(c, r, s); break;
+    case 3: rc = fine_restrict<3, S>(c, r, s); break;
+    case 4: rc = fine_restrict<4, S>(c, r, s); break;
+    case 5: rc = fine_restrict<5, S>(c, r, s); break;
     default: return FR_ERR_ARG;
   }
   if (rc != FR_OK) return rc;
   FR_TRY(vcycle<S>(c, s));
-  switch (c->n) {
-    case 2: rc = fine_transfer<2, S>(c, nullptr, c->mg_z0, s, false); break;
-    case 3: rc = fine_transfer<3, S>(c, nullptr, c->mg_z0, s, false); break;
-    case 4: rc = fine_transfer<4, S>(c, nullptr, c->mg_z0, s, false); break;
-    case 5: rc = fine_transfer<5, S>(c, nullptr, c->mg_z0, s, false); break;
-  }
-  if (rc != FR_OK) return rc;
-  // z = z0 + B^-1 (r - A z0): the block apply forms r - A z0 and adds z0 itself
-  FR_TRY(op_apply(c, q, c->mg_z0, inv_dtau, a0_dt, c->mg_t, s));
-  return frk::block_apply_fused(c, r, c->mg_t, c->mg_z0, z, s);
+  // z = z0 + B^-1 (r - A z0) with z0 = P y0: the block apply prolongs y0 and forms A z0 from
+  // the build's stored columns A P, in one pass
+  CoarseIn ci;
+  ci.AP = c->mg_ap;
+  ci.y0 = c->mg[0].y;
+  ci.nb = c->mg[0].nb;
+  for (int i = 0; i < c->n; ++i) ci.xs[i] = c->basis.xs[i];
+  return frk::block_apply_coarse(c, r, z, ci, sizeof(S) == sizeof(float) ? 1 : 2, s);
 }
 
 template <class S>
@@ -832,8 +822,9 @@ void mg_free(fr_ctx* c) {
   }
   c->mg.clear();
   if (c->mg_colslot) { cudaFree(c->mg_colslot); c->mg_colslot = nullptr; }
-  double** fs[] = {&c->mg_x, &c->mg_y, &c->mg_z0, &c->mg_t};
+  double** fs[] = {&c->mg_x, &c->mg_y};
   for (double** p : fs) if (*p) { cudaFree(*p); *p = nullptr; }
+  if (c->mg_ap) { cudaFree(c->mg_ap); c->mg_ap = nullptr; }
   if (c->mg_bad) { cudaFree(c->mg_bad); c->mg_bad = nullptr; }
   if (c->mg_views) { cudaFree(c->mg_views); c->mg_views = nullptr; }
   if (c->mg_tc) { cudaFree(c->mg_tc); c->mg_tc = nullptr; }
@@ -1041,8 +1032,10 @@ int mg_setup(fr_ctx* c) {
   FR_TRY(upload(c, &c->mg_colslot, cslot));
   FR_TRY(dalloc(c, &c->mg_x, c->ndof));
   FR_TRY(dalloc(c, &c->mg_y, c->ndof));
-  FR_TRY(dalloc(c, &c->mg_z0, c->ndof));
-  FR_TRY(dalloc(c, &c->mg_t, c->ndof));
+  // the build's A P columns, zero where a stencil slot is unused
+  const size_t nap = (size_t)ne * SL * NB * c->bsz;
+  FR_CUDA_CHECK(c, cudaMalloc(&c->mg_ap, nap * esz));
+  FR_CUDA_CHECK(c, cudaMemset(c->mg_ap, 0, nap * esz));
   FR_TRY(dalloc(c, &c->mg_bad, 1));
   FR_CUDA_CHECK(c, cudaMemset(c->mg_bad, 0, sizeof(int)));
   return FR_OK;

@@ -793,11 +793,15 @@ template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x
 constexpr int APPLY_PARTS = 4;
 
 // With rsub and zadd (both nullable) the same pass forms z_e = zadd_e + B_e^-1 (r - rsub)_e.
-template <class S, int ACC, int N>
+// CO = 1 (FP32) or 2 (FP64 coarse arrays): the smoothing step of the two-level
+// preconditioner from the coarse solution y0 instead, z_e = (P y0)_e + B_e^-1 (r - A P y0)_e
+// with the stored columns A P of the element's stencil members (ci): the four parts of a
+// row each sum 15 of its 60 terms (double-float for FP32 arrays, FP64 otherwise).
+template <class S, int ACC, int N, int CO = 0>
 __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
                          const float* __restrict__ Dc, const double* __restrict__ r, Mesh M,
                          double* __restrict__ z, const double* __restrict__ rsub,
-                         const double* __restrict__ zadd, bool tr) {
+                         const double* __restrict__ zadd, bool tr, CoarseIn ci = CoarseIn{}) {
   constexpr int NP = N * N, BS = 4 * NP, BSR = (BS + 31) / 32 * 32;
   constexpr int COLS = (BS + APPLY_PARTS - 1) / APPLY_PARTS;   // columns per thread
   __shared__ double xd[ACC == 0 ? BS : 1];
@@ -821,10 +825,50 @@ __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
   const float* Din = tr ? Dc : Dr;
   const float* Dout = tr ? Dr : Dc;
   const size_t qo = M.qbase(e, NP), qs = M.qstride(e);
+  constexpr int CT = 5 * 12;   // coarse terms of a row: 5 stencil members x 12 P1 coefficients
+  __shared__ double cyd[CO == 2 ? CT : 1];
+  __shared__ float cyf[CO == 1 ? CT : 1];
+  __shared__ double cpd[CO == 2 ? APPLY_PARTS : 1][CO == 2 ? BSR : 1];
+  __shared__ float2 cpf[CO == 1 ? APPLY_PARTS : 1][CO == 1 ? BSR : 1];
+  if constexpr (CO != 0) {
+    for (int t = threadIdx.x; t < CT; t += blockDim.x) {
+      const int cell = ci.nb[(size_t)e * 5 + t / 12];
+      if constexpr (CO == 2) cyd[t] = cell >= 0 ? ((const double*)ci.y0)[(size_t)cell * 12 + t % 12] : 0.0;
+      else cyf[t] = cell >= 0 ? ((const float*)ci.y0)[(size_t)cell * 12 + t % 12] : 0.0f;
+    }
+    __syncthreads();
+    if (row < BS) {
+      if constexpr (CO == 2) {
+        const double* ap = (const double*)ci.AP + (size_t)e * CT * BS + row;
+        double a0 = 0.0;
+#pragma unroll
+        for (int k = part; k < CT; k += APPLY_PARTS) a0 = fma(ap[(size_t)k * BS], cyd[k], a0);
+        cpd[part][row] = a0;
+      } else {
+        const float* ap = (const float*)ci.AP + (size_t)e * CT * BS + row;
+        float h0 = 0.f, l0 = 0.f;
+#pragma unroll
+        for (int k = part; k < CT; k += APPLY_PARTS) df_add(h0, l0, ap[(size_t)k * BS], make_float2(cyf[k], 0.f));
+        cpf[part][row] = make_float2(h0, l0);
+      }
+    }
+    __syncthreads();
+  }
   for (int t = threadIdx.x; t < BS; t += blockDim.x) {
     const int v = t / NP, pt = t % NP;
     const size_t gi = v * qs + qo + pt;
-    const double u = (rsub ? r[gi] - rsub[gi] : r[gi]) * (double)Din[(size_t)e * BS + t];
+    double rs = rsub ? rsub[gi] : 0.0;
+    if constexpr (CO == 2) {
+      rs = cpd[0][t];
+#pragma unroll
+      for (int q = 1; q < APPLY_PARTS; ++q) rs += cpd[q][t];
+    } else if constexpr (CO == 1) {
+      float sh = cpf[0][t].x, sl = cpf[0][t].y;
+#pragma unroll
+      for (int q = 1; q < APPLY_PARTS; ++q) df_merge(sh, sl, cpf[q][t].x, cpf[q][t].y);
+      rs = (double)sh + (double)sl;
+    }
+    const double u = (r[gi] - rs) * (double)Din[(size_t)e * BS + t];
     if (ACC == 0) xd[t] = u;
     else if (ACC == 1) xf[t] = (float)u;
     else {
@@ -893,7 +937,16 @@ __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
   const int v = row / NP, pt = row % NP;
   const size_t gi = v * qs + qo + pt;
   const double zr = acc * (double)Dout[(size_t)e * BS + row];
-  z[gi] = zadd ? zadd[gi] + zr : zr;
+  if constexpr (CO != 0) {
+    // P y0 at this point: c0 + c1 xi + c2 eta of the element's own coefficients (slot 0)
+    const int i = pt % N, j = pt / N;
+    double c[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) c[m] = CO == 2 ? cyd[3 * v + m] : (double)cyf[3 * v + m];
+    z[gi] = fma(c[2], ci.xs[j], fma(c[1], ci.xs[i], c[0])) + zr;
+  } else {
+    z[gi] = zadd ? zadd[gi] + zr : zr;
+  }
 }
 
 }  // namespace fr
@@ -1051,24 +1104,16 @@ int block_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaS
   return factor(c, s);
 }
 
+template <int CO>
 static int apply_impl(fr_ctx* c, const double* r, double* z, const double* rsub,
-                      const double* zadd, cudaStream_t s);
-
-int block_apply(fr_ctx* c, const double* r, double* z, cudaStream_t s) {
-  return apply_impl(c, r, z, nullptr, nullptr, s);
-}
-
-int block_apply_fused(fr_ctx* c, const double* r, const double* t, const double* z0, double* z,
-                      cudaStream_t s) {
-  return apply_impl(c, r, z, t, z0, s);
-}
-
-static int apply_impl(fr_ctx* c, const double* r, double* z, const double* rsub,
-                      const double* zadd, cudaStream_t s) {
+                      const double* zadd, const CoarseIn& ci, cudaStream_t s) {
   const int bs = c->bsz;
   const double esz = c->cfg.prec_dtype == FR_PREC_FP64 ? 8.0 : c->cfg.prec_dtype == FR_PREC_FP32 ? 4.0 : 2.0;
-  FR_ACCOUNT(c, KK_APPLY, 2.0 * (double)bs * bs * c->ne,
-             c->ne * ((double)bs * bs * esz + 2.0 * bs * 4.0) +
+  // the coarse form also reads the 60 stored columns of A P per row
+  const double co_flops = CO ? 2.0 * 60.0 * bs * c->ne : 0.0;
+  const double co_bytes = CO ? 60.0 * bs * c->ne * (CO == 1 ? 4.0 : 8.0) : 0.0;
+  FR_ACCOUNT(c, KK_APPLY, 2.0 * (double)bs * bs * c->ne + co_flops,
+             c->ne * ((double)bs * bs * esz + 2.0 * bs * 4.0) + co_bytes +
                  (2.0 + (rsub ? 1.0 : 0.0) + (zadd ? 1.0 : 0.0)) * 8.0 * c->ndof);
   FR_PROF_BEGIN(c, s);
   // Double-float accumulation keeps the preconditioner linear to near FP64 round-off (the
@@ -1081,14 +1126,14 @@ static int apply_impl(fr_ctx* c, const double* r, double* z, const double* rsub,
   const int acc = c->cfg.prec_dtype == FR_PREC_FP64 ? 0 : df ? 2 : 1;
   switch (c->n * 10 + acc) {
 #define FR_APPLY_CASE(NN)                                                                      \
-    case NN * 10 + 0: k_apply4<double, 0, NN><<<c->ne, nt4, 0, s>>>((const double*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr); break; \
+    case NN * 10 + 0: k_apply4<double, 0, NN, CO><<<c->ne, nt4, 0, s>>>((const double*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr, ci); break; \
     case NN * 10 + 1: if (c->cfg.prec_dtype == FR_PREC_FP32)                                  \
-        k_apply4<float, 1, NN><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr); \
-      else k_apply4<__nv_bfloat16, 1, NN><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr); \
+        k_apply4<float, 1, NN, CO><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr, ci); \
+      else k_apply4<__nv_bfloat16, 1, NN, CO><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr, ci); \
       break;                                                                                   \
     case NN * 10 + 2: if (c->cfg.prec_dtype == FR_PREC_FP32)                                  \
-        k_apply4<float, 2, NN><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr); \
-      else k_apply4<__nv_bfloat16, 2, NN><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr); \
+        k_apply4<float, 2, NN, CO><<<c->ne, nt4, 0, s>>>((const float*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr, ci); \
+      else k_apply4<__nv_bfloat16, 2, NN, CO><<<c->ne, nt4, 0, s>>>((const __nv_bfloat16*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr, ci); \
       break;
     FR_APPLY_CASE(2) FR_APPLY_CASE(3) FR_APPLY_CASE(4) FR_APPLY_CASE(5)
 #undef FR_APPLY_CASE
@@ -1097,6 +1142,21 @@ static int apply_impl(fr_ctx* c, const double* r, double* z, const double* rsub,
   FR_PROF_END(c, s, KK_APPLY);
   FR_LAUNCH_CHECK(c);
   return FR_OK;
+}
+
+int block_apply(fr_ctx* c, const double* r, double* z, cudaStream_t s) {
+  return apply_impl<0>(c, r, z, nullptr, nullptr, CoarseIn{}, s);
+}
+
+int block_apply_fused(fr_ctx* c, const double* r, const double* t, const double* z0, double* z,
+                      cudaStream_t s) {
+  return apply_impl<0>(c, r, z, t, z0, CoarseIn{}, s);
+}
+
+int block_apply_coarse(fr_ctx* c, const double* r, double* z, const CoarseIn& ci, int co,
+                       cudaStream_t s) {
+  if (co == 1) return apply_impl<1>(c, r, z, nullptr, nullptr, ci, s);
+  return apply_impl<2>(c, r, z, nullptr, nullptr, ci, s);
 }
 
 }  // namespace frk
