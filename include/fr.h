@@ -120,13 +120,23 @@ typedef struct fr_ctx fr_ctx;
  * factor_tc: how the element blocks are inverted: FR_FACTOR_SIMT (default) Gauss-Jordan
  * with partial pivoting in FP32 (FP64 for FP64 blocks) on the SIMT pipe;
  * FR_FACTOR_TC_BF16 blocked Gauss-Jordan on [B | I] in FP32 shared memory whose rank-16
- * panel updates run on the tensor cores with BF16 operands and FP32 accumulation (the
- * the benchmark spec's mixed-precision factorisation: about 2^-9 relative per update, the outer
- * FP64 Krylov iteration absorbs it); FR_FACTOR_TC_BF16X3 the same with every operand split
+ * panel updates run on the tensor cores with BF16 operands and FP32 accumulation (a
+ * mixed-precision factorisation: about 2^-9 relative per update, which the outer FP64
+ * Krylov iteration absorbs); FR_FACTOR_TC_BF16X3 the same with every operand split
  * into two BF16 numbers and three products per update (about 2^-16 relative).  Panel
  * pivoting and elimination stay FP32 SIMT; the inverse is stored in prec_dtype.  On a periodic mesh with a very
  * large dtau and no time term (a0_dt = 0) the constant states make the coarsest operator
- * singular: use it for BDF2 steps (a0_dt > 0) or on bounded meshes. */
+ * singular: use it for BDF2 steps (a0_dt > 0) or on bounded meshes;
+ * apply_bulk: 0 (default) applies the blocks with one thread block per element;
+ * k = 2, 3 or 4 runs the block apply (and the two-level smoothing step) as a persistent
+ * kernel whose blocks stream each element's stored inverse into a k-slab shared ring by
+ * bulk asynchronous copies, k - 1 elements in flight behind the one being computed (where
+ * k slabs fit in shared memory; the transposed apply always uses one block per element);
+ * wait_spins: budget of the device's bounded waits on those copies: 0 = the default
+ * (4,194,304 potentially blocking tries), k > 0 = k tries, k < 0 = one non-blocking test
+ * (a diagnostic setting under which a wait all but surely runs out).  A wait that runs
+ * out makes the call that launched it return FR_ERR_TIMEOUT after the block has waited,
+ * again bounded, for its copies in flight; the context stays usable. */
 #define FR_MAX_RESTART 256
 #define FR_JVP_DUAL 0
 #define FR_JVP_LINEARIZED 1
@@ -170,6 +180,8 @@ typedef struct fr_config {
   double mg_omega;
   int mg_prec;
   int factor_tc;
+  int apply_bulk;
+  long long wait_spins;
 } fr_config;
 
 /* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).
@@ -290,7 +302,9 @@ int fr_precond_build(fr_ctx* ctx, const double* qp_d, double inv_dtau, double a0
                      void* stream);
 /* Copy the unfactored FP64 blocks of the last build to B_d[Ne][b][b] (b = 4 n^2). */
 int fr_precond_blocks(fr_ctx* ctx, double* B_d, void* stream);
-/* z_e = B_e^-1 r_e for every element (FP64 in and out). */
+/* z = M^-1 r with the configured preconditioner (FP64 in and out): z_e = B_e^-1 r_e for
+ * every element, or the two-level map.  Synchronises the stream (a bounded device wait
+ * that ran out returns FR_ERR_TIMEOUT). */
 int fr_precond_apply(fr_ctx* ctx, const double* r_d, double* z_d, void* stream);
 
 /* Restarted block-Jacobi-preconditioned GMRES(m) with CGS2 (Sec. 3.2, PETSc's solver

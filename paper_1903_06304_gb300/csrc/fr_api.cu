@@ -195,6 +195,7 @@ void free_mesh(fr_ctx* c) {
   if (c->Dc) { cudaFree(c->Dc); c->Dc = nullptr; }
   if (c->info) { cudaFree(c->info); c->info = nullptr; }
   if (c->ticket) { cudaFree(c->ticket); c->ticket = nullptr; }
+  if (c->dev_err) { cudaFree(c->dev_err); c->dev_err = nullptr; }
   if (c->nbr) { cudaFree(c->nbr); c->nbr = nullptr; }
   if (c->ecase) { cudaFree(c->ecase); c->ecase = nullptr; }
   c->blocks_ready = 0;
@@ -281,8 +282,19 @@ int op_apply(fr_ctx* c, const double* q, const double* x, double inv_dtau, doubl
   return frk::jvp(c, q, x, inv_dtau, a0_dt, out, s);
 }
 
+static int gmres_solve_impl(fr_ctx* c, const double* q, const double* b, double inv_dtau,
+                            double a0_dt, double* x, int* iters, cudaStream_t s);
+
+// GMRES (below), then the report of any device wait that ran out during it
 int gmres_solve(fr_ctx* c, const double* q, const double* b, double inv_dtau, double a0_dt,
                 double* x, int* iters, cudaStream_t s) {
+  const int rc = gmres_solve_impl(c, q, b, inv_dtau, a0_dt, x, iters, s);
+  const int wc = frk::check_device_waits(c, s);
+  return wc != FR_OK ? wc : rc;
+}
+
+static int gmres_solve_impl(fr_ctx* c, const double* q, const double* b, double inv_dtau,
+                            double a0_dt, double* x, int* iters, cudaStream_t s) {
   const size_t N = c->ndof;
   const int m = c->cfg.restart;
   const double tol = c->cfg.tol_res;
@@ -560,6 +572,8 @@ void fr_default_config(fr_config* c) {
   c->mg_omega = 0.7;
   c->mg_prec = FR_PREC_FP32;
   c->factor_tc = FR_FACTOR_SIMT;
+  c->apply_bulk = 0;
+  c->wait_spins = 0;
 }
 
 int fr_create(const fr_config* cfg, fr_ctx** out) {
@@ -577,7 +591,8 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
       (cfg->precond != FR_PRECOND_BLOCK && cfg->precond != FR_PRECOND_TWO_LEVEL) ||
       cfg->mg_sweeps < 1 || cfg->mg_sweeps > 2 || !(cfg->mg_omega > 0.0 && cfg->mg_omega <= 1.5) ||
       (cfg->mg_prec != FR_PREC_FP64 && cfg->mg_prec != FR_PREC_FP32) ||
-      cfg->factor_tc < FR_FACTOR_SIMT || cfg->factor_tc > FR_FACTOR_TC_BF16X3)
+      cfg->factor_tc < FR_FACTOR_SIMT || cfg->factor_tc > FR_FACTOR_TC_BF16X3 ||
+      cfg->apply_bulk < 0 || cfg->apply_bulk == 1 || cfg->apply_bulk > 4)
     return FR_ERR_ARG;
   fr_ctx* c = new fr_ctx();
   c->cfg = *cfg;
@@ -751,6 +766,8 @@ int fr_setup_cases(fr_ctx* c, int ncases, const int* nxs, const int* nys,
   FR_TRY(dev_alloc(c, &c->adj_qc, ne * 16 * n));
   FR_TRY(dev_alloc(c, &c->ticket, 1));
   FR_CUDA_CHECK(c, cudaMemset(c->ticket, 0, sizeof(unsigned int)));
+  FR_TRY(dev_alloc(c, &c->dev_err, 1));
+  FR_CUDA_CHECK(c, cudaMemset(c->dev_err, 0, sizeof(int)));
   // per-case vector partition, GMRES states and staging (used by every context)
   FR_TRY(frk::batch_setup(c));
   // coarse hierarchy of the two-level preconditioner (nothing unless configured)
@@ -833,7 +850,8 @@ int fr_precond_blocks(fr_ctx* c, double* B, void* s) {
 int fr_precond_apply(fr_ctx* c, const double* r, double* z, void* s) {
   FR_TRY(check_ready(c));
   if (!c->blocks_ready) { snprintf(c->err, sizeof(c->err), "no preconditioner built"); return FR_ERR_ARG; }
-  return frk::precond_apply(c, c->mg_q, r, z, c->mg_inv_dtau, c->mg_a0_dt, S(s));
+  FR_TRY(frk::precond_apply(c, c->mg_q, r, z, c->mg_inv_dtau, c->mg_a0_dt, S(s)));
+  return frk::check_device_waits(c, S(s));
 }
 
 int fr_gmres(fr_ctx* c, const double* q, const double* b, double inv_dtau, double a0_dt, double* x,

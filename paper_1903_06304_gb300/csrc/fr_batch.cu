@@ -296,6 +296,7 @@ int batch_newton(fr_ctx* c, double* q, const double* qcn, const double* qcnm1,
     if (cfg.jvp_mode == FR_JVP_LINEARIZED && !lin_done) FR_TRY(frk::linearize(c, q, 0.0, 0.0, s));
     if (build) FR_TRY(frk::mg_build(c, q, 0.0, 0.0, s));
     FR_TRY(frk::gmres_cases(c, q, r, c->w_x, 0.0, 0.0, active, its, failed, s));
+    FR_TRY(frk::check_device_waits(c, s));
     for (int k = 0; k < nc; ++k) {
       if (active[k]) S[k]->gmres_iterations[mk[k]] = its[k];
       prev[k] = rm[k];

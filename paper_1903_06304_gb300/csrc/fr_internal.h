@@ -178,6 +178,9 @@ struct fr_ctx {
   double *adj_q = nullptr, *adj_fn = nullptr, *adj_qc = nullptr;  // transpose work
   int lin_ready = 0;
   int transposed = 0;   // set during fr_adjoint_solve: GMRES applies A^T and B^-T
+  int* dev_err = nullptr;   // set by a device wait that ran out of its budget (read by
+                            // check_device_waits, which clears it)
+  int apply_grid[3] = {0, 0, 0};   // persistent grid of the bulk-copy apply, per coarse form
   // two-level preconditioner (cfg.precond == FR_PRECOND_TWO_LEVEL, fr_mg.cu)
   std::vector<MgLevel> mg;
   int mg_ncol = 0;                 // colours of the level-0 Galerkin products
@@ -316,6 +319,9 @@ int bk_finish(fr_ctx* c, double* u, cudaStream_t s);              // trisolve + 
 int bk_status(fr_ctx* c, cudaStream_t s);                         // -> bw.status_h (async)
 int bk_axpy_case(fr_ctx* c, const double* coef_dev, const double* x, double* y, cudaStream_t s);
 int upload_cases(fr_ctx* c, cudaStream_t s);                      // c->cps -> device
+// FR_ERR_TIMEOUT (and the flag cleared) if a device wait ran out of its budget since the
+// last check (synchronises s).
+int check_device_waits(fr_ctx* c, cudaStream_t s);
 // Tile shapes: forced by cfg.tiles (1 or 2) or timed on the context's own buffers
 // (cfg.tiles = 0).  Synchronous; called once at mesh set-up.
 int autotune_tiles(fr_ctx* c);

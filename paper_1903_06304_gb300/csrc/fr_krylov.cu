@@ -945,6 +945,16 @@ int axpy_dots(fr_ctx* c, const double* V, int nv, const double* h, double* w, do
 int axpy_norm(fr_ctx* c, const double* V, int nv, const double* h, double* w, double* out, cudaStream_t s) {
   return krylov<2>(c, V, nv, h, w, out, s);
 }
+int check_device_waits(fr_ctx* c, cudaStream_t s) {
+  int h = 0;
+  FR_CUDA_CHECK(c, cudaMemcpyAsync(&h, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FR_CUDA_CHECK(c, cudaStreamSynchronize(s));
+  if (h == 0) return FR_OK;
+  FR_CUDA_CHECK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), s));
+  snprintf(c->err, sizeof(c->err), "a bounded device wait ran out of its budget (wait_spins)");
+  return FR_ERR_TIMEOUT;
+}
+
 int norms(fr_ctx* c, const double* r, double* out, cudaStream_t s) {
   const int g = grid_for(c);
   FR_ACCOUNT(c, KK_KRYLOV, 2.0 * c->ndof, 8.0 * c->ndof);

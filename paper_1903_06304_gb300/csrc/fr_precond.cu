@@ -8,6 +8,7 @@
 //         BF16 (the FP32 inverse rounded).
 // Apply:  z_e = Dc (B~_e^-1 (Dr r_e)), FP64 in/out; FP32/BF16 inverses applied with
 //         double-float accumulation on the FP32 pipe (default) or in plain FP32.
+#include <algorithm>
 #include <cstdio>
 #include <cuda_bf16.h>
 #include "fr_internal.h"
@@ -797,11 +798,15 @@ constexpr int APPLY_PARTS = 4;
 // preconditioner from the coarse solution y0 instead, z_e = (P y0)_e + B_e^-1 (r - A P y0)_e
 // with the stored columns A P of the element's stencil members (ci): the four parts of a
 // row each sum 15 of its 60 terms (double-float for FP32 arrays, FP64 otherwise).
-template <class S, int ACC, int N, int CO = 0>
-__global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
-                         const float* __restrict__ Dc, const double* __restrict__ r, Mesh M,
-                         double* __restrict__ z, const double* __restrict__ rsub,
-                         const double* __restrict__ zadd, bool tr, CoarseIn ci = CoarseIn{}) {
+// One element e by the whole block: A is the element's stored inverse and APe its A P
+// columns (CO != 0), in global or shared memory (generic pointers).
+template <class S, int ACC, int N, int CO>
+__device__ __forceinline__ void apply_elem(int e, const S* __restrict__ A, const void* __restrict__ APe,
+                                           const float* __restrict__ Dr, const float* __restrict__ Dc,
+                                           const double* __restrict__ r, const Mesh& M,
+                                           double* __restrict__ z, const double* __restrict__ rsub,
+                                           const double* __restrict__ zadd, bool tr,
+                                           const CoarseIn& ci) {
   constexpr int NP = N * N, BS = 4 * NP, BSR = (BS + 31) / 32 * 32;
   constexpr int COLS = (BS + APPLY_PARTS - 1) / APPLY_PARTS;   // columns per thread
   __shared__ double xd[ACC == 0 ? BS : 1];
@@ -810,10 +815,8 @@ __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
   __shared__ double pd[ACC == 0 ? APPLY_PARTS : 1][BSR];
   __shared__ float pf[ACC == 1 ? APPLY_PARTS : 1][BSR];
   __shared__ float2 p2[ACC == 2 ? APPLY_PARTS : 1][BSR];
-  const int e = blockIdx.x;
   if (!M.on(e)) return;
   const int part = threadIdx.x / BSR, row = threadIdx.x % BSR;
-  const S* A = AT + (size_t)e * BS * BS;
   // every load of this thread's columns issued before any arithmetic
   S av[COLS];
 #pragma unroll
@@ -839,13 +842,13 @@ __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
     __syncthreads();
     if (row < BS) {
       if constexpr (CO == 2) {
-        const double* ap = (const double*)ci.AP + (size_t)e * CT * BS + row;
+        const double* ap = (const double*)APe + row;
         double a0 = 0.0;
 #pragma unroll
         for (int k = part; k < CT; k += APPLY_PARTS) a0 = fma(ap[(size_t)k * BS], cyd[k], a0);
         cpd[part][row] = a0;
       } else {
-        const float* ap = (const float*)ci.AP + (size_t)e * CT * BS + row;
+        const float* ap = (const float*)APe + row;
         float h0 = 0.f, l0 = 0.f;
 #pragma unroll
         for (int k = part; k < CT; k += APPLY_PARTS) df_add(h0, l0, ap[(size_t)k * BS], make_float2(cyf[k], 0.f));
@@ -946,6 +949,123 @@ __global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
     z[gi] = fma(c[2], ci.xs[j], fma(c[1], ci.xs[i], c[0])) + zr;
   } else {
     z[gi] = zadd ? zadd[gi] + zr : zr;
+  }
+}
+
+template <class S, int ACC, int N, int CO = 0>
+__global__ void k_apply4(const S* __restrict__ AT, const float* __restrict__ Dr,
+                         const float* __restrict__ Dc, const double* __restrict__ r, Mesh M,
+                         double* __restrict__ z, const double* __restrict__ rsub,
+                         const double* __restrict__ zadd, bool tr, CoarseIn ci = CoarseIn{}) {
+  constexpr int BS = 4 * N * N;
+  const int e = blockIdx.x;
+  apply_elem<S, ACC, N, CO>(e, AT + (size_t)e * BS * BS,
+                            CO ? (const char*)ci.AP + (size_t)e * 60 * BS * (CO == 2 ? 8 : 4) : nullptr,
+                            Dr, Dc, r, M, z, rsub, zadd, tr, ci);
+}
+
+// ------------------------------------------------------------------ bulk-copy pipeline
+// mbarrier and bulk-copy (TMA, 1-D cp.async.bulk) primitives in inline PTX.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Waits for phase `parity` of the barrier: spins > 0 potentially blocking tries, spins < 0
+// one non-blocking test.  False if the phase has not completed within the budget.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long spins) {
+  const unsigned a = smem_u32(bar);
+  if (spins < 0) {
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+  }
+  for (long long i = 0; i < spins; ++i) {
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Bytes of one element's slab in the pipeline: the stored inverse, then the A P columns,
+// rounded up to 128 bytes.
+template <class S, int N, int CO>
+struct BulkSlab {
+  static constexpr unsigned A = 16u * N * N * N * N * (unsigned)sizeof(S);   // (4 n^2)^2 entries
+  static constexpr unsigned P = CO == 0 ? 0u : 60u * 4u * N * N * (CO == 2 ? 8u : 4u);
+  static constexpr unsigned SLAB = (A + P + 127u) / 128u * 128u;
+};
+
+// The block apply as a persistent kernel fed by bulk copies: each block walks the elements
+// e = blockIdx.x, + gridDim.x, ...; one thread keeps the next nst - 1 elements' inverses
+// (and A P columns) in flight into an nst-slab shared ring while the block computes the
+// current one, so the HBM stream of the stored inverses runs under the arithmetic.  The
+// copy sizes and addresses are multiples of 16 bytes for every degree and precision.
+// A wait that runs out of its budget sets *err, waits (bounded) for this block's copies
+// in flight, and ends the block.
+template <class S, int ACC, int N, int CO>
+__global__ void k_apply_bulk(const S* __restrict__ AT, const float* __restrict__ Dr,
+                             const float* __restrict__ Dc, const double* __restrict__ r, Mesh M,
+                             double* __restrict__ z, CoarseIn ci, int nst, long long spins, int* err) {
+  using L = BulkSlab<S, N, CO>;
+  constexpr int BS = 4 * N * N;
+  extern __shared__ __align__(128) unsigned char slab[];
+  __shared__ __align__(8) unsigned long long bar[4];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int i = 0; i < nst; ++i) mbar_init(&bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto elem = [&](int k) { return blockIdx.x + k * (int)gridDim.x; };
+  auto issue = [&](int k) {
+    const int e = elem(k), st = k % nst;
+    unsigned char* dst = slab + (size_t)st * L::SLAB;
+    mbar_expect_tx(&bar[st], L::A + L::P);
+    bulk_g2s(dst, AT + (size_t)e * BS * BS, L::A, &bar[st]);
+    if (CO) bulk_g2s(dst + L::A, (const char*)ci.AP + (size_t)e * L::P, L::P, &bar[st]);
+  };
+  if (tid == 0)
+    for (int k = 0; k < nst - 1 && elem(k) < M.ne; ++k) issue(k);
+  int k = 0;
+  bool bad = false;
+  for (; elem(k) < M.ne; ++k) {
+    const int st = k % nst;
+    if (tid == 0 && elem(k + nst - 1) < M.ne) issue(k + nst - 1);
+    const bool ok = mbar_wait(&bar[st], (unsigned)(k / nst) & 1u, spins);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    const unsigned char* cur = slab + (size_t)st * L::SLAB;
+    apply_elem<S, ACC, N, CO>(elem(k), (const S*)cur, cur + L::A, Dr, Dc, r, M, z, nullptr, nullptr,
+                              false, ci);
+    __syncthreads();   // the slab is refilled nst - 1 elements later
+  }
+  if (bad && tid == 0) {
+    atomicExch(err, 1);
+    // copies issued and not consumed: elements k .. k + nst - 1
+    for (int j = k; j < k + nst && elem(j) < M.ne; ++j)
+      mbar_wait(&bar[j % nst], (unsigned)(j / nst) & 1u, 1LL << 22);
   }
 }
 
@@ -1104,6 +1224,36 @@ int block_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaS
   return factor(c, s);
 }
 
+// The bulk-copy pipeline for one instantiation: its persistent grid (blocks per SM at
+// this slab size times the SMs, cached per context) and launch.  False if two slabs do not
+// fit in shared memory (the caller falls back to one block per element).
+template <class S, int ACC, int N, int CO>
+static bool launch_bulk(fr_ctx* c, const double* r, double* z, const CoarseIn& ci, int threads,
+                        cudaStream_t s, int* rc) {
+  const int nst = c->cfg.apply_bulk;
+  const size_t smem = (size_t)nst * BulkSlab<S, N, CO>::SLAB;
+  if (smem > 200 * 1024) return false;
+  int& grid = c->apply_grid[CO];
+  auto kern = k_apply_bulk<S, ACC, N, CO>;
+  if (grid == 0) {
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem) != cudaSuccess || per < 1) {
+      *rc = FR_ERR_CUDA;
+      snprintf(c->err, sizeof(c->err), "bulk apply: launch configuration");
+      return true;
+    }
+    grid = per * nsm;
+  }
+  const long long spins = c->cfg.wait_spins == 0 ? (1LL << 22) : c->cfg.wait_spins;
+  kern<<<std::min(grid, c->ne), threads, smem, s>>>((const S*)c->Binv, c->Dr, c->Dc, r, c->mesh, z,
+                                                   ci, nst, spins, c->dev_err);
+  *rc = FR_OK;
+  return true;
+}
+
 template <int CO>
 static int apply_impl(fr_ctx* c, const double* r, double* z, const double* rsub,
                       const double* zadd, const CoarseIn& ci, cudaStream_t s) {
@@ -1124,6 +1274,28 @@ static int apply_impl(fr_ctx* c, const double* r, double* z, const double* rsub,
   const bool tr = c->transposed != 0;   // B^-T in the adjoint solve
   const int nt4 = APPLY_PARTS * ((bs + 31) / 32 * 32);
   const int acc = c->cfg.prec_dtype == FR_PREC_FP64 ? 0 : df ? 2 : 1;
+  if (c->cfg.apply_bulk && !tr && !rsub && !zadd) {
+    int rc = FR_OK;
+    bool done = false;
+    const bool f32 = c->cfg.prec_dtype == FR_PREC_FP32;
+    switch (c->n * 10 + acc) {
+#define FR_BULK_CASE(NN)                                                                            \
+      case NN * 10 + 0: done = launch_bulk<double, 0, NN, CO>(c, r, z, ci, nt4, s, &rc); break;      \
+      case NN * 10 + 1: done = f32 ? launch_bulk<float, 1, NN, CO>(c, r, z, ci, nt4, s, &rc)         \
+                                   : launch_bulk<__nv_bfloat16, 1, NN, CO>(c, r, z, ci, nt4, s, &rc); break; \
+      case NN * 10 + 2: done = f32 ? launch_bulk<float, 2, NN, CO>(c, r, z, ci, nt4, s, &rc)         \
+                                   : launch_bulk<__nv_bfloat16, 2, NN, CO>(c, r, z, ci, nt4, s, &rc); break;
+      FR_BULK_CASE(2) FR_BULK_CASE(3) FR_BULK_CASE(4) FR_BULK_CASE(5)
+#undef FR_BULK_CASE
+      default: return FR_ERR_ARG;
+    }
+    if (done) {
+      if (rc != FR_OK) return rc;
+      FR_PROF_END(c, s, KK_APPLY);
+      FR_LAUNCH_CHECK(c);
+      return FR_OK;
+    }
+  }
   switch (c->n * 10 + acc) {
 #define FR_APPLY_CASE(NN)                                                                      \
     case NN * 10 + 0: k_apply4<double, 0, NN, CO><<<c->ne, nt4, 0, s>>>((const double*)c->Binv, c->Dr, c->Dc, r, c->mesh, z, rsub, zadd, tr, ci); break; \

@@ -47,7 +47,8 @@ class _Config(ctypes.Structure):
                 ("block_mode", ctypes.c_int), ("orthog", ctypes.c_int),
                 ("krylov_arith", ctypes.c_int), ("precond", ctypes.c_int),
                 ("mg_sweeps", ctypes.c_int), ("mg_omega", ctypes.c_double),
-                ("mg_prec", ctypes.c_int), ("factor_tc", ctypes.c_int)]
+                ("mg_prec", ctypes.c_int), ("factor_tc", ctypes.c_int),
+                ("apply_bulk", ctypes.c_int), ("wait_spins", ctypes.c_longlong)]
 
 
 class Stats(ctypes.Structure):
@@ -208,6 +209,8 @@ class Config:
     mg_omega: float = 0.7
     mg_prec: str = "fp32"
     factor: str = "simt"
+    apply_bulk: int = 0
+    wait_spins: int = 0
 
     def to_c(self) -> _Config:
         c = _Config()

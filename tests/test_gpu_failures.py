@@ -85,3 +85,50 @@ def test_batch_isolates_the_non_finite_case(torch):
         assert np.abs(got[B.case_slice(k)] - to_host(q1).ravel()).max() <= 1e-9 * dq
         S.close()
     B.close()
+
+
+@pytest.mark.parametrize("precond", ["block", "twolevel"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_bulk_copy_apply_equals_one_block_per_element(torch, precond, prec):
+    """The persistent block apply fed by bulk copies (apply_bulk = 3) computes the same
+    arithmetic as the one-block-per-element kernel: equal bit for bit."""
+    nx, ny, p, mach = 9, 7, 3, 0.05
+    c, q = _vortex(nx, ny, p, mach)
+    r = inp.random_vector(q.shape, 17)
+    out = []
+    for bulk in (3, 0):
+        S = solver_for(c, np.zeros_like(c), nx, ny, p, mach, 10.0, 1.0, precond=precond,
+                       prec=prec, apply_bulk=bulk)
+        qd = to_dev(q)
+        S.precond_build(qd, 1e-20, 150.0)
+        z = torch.empty_like(qd)
+        S.precond_apply(to_dev(r), z)
+        out.append(to_host(z))
+        S.close()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_a_device_wait_that_runs_out_returns_timeout(torch):
+    """A bounded device wait (the bulk copies of the block apply) given no budget: the
+    call returns FR_ERR_TIMEOUT after the blocks have waited for their copies, and the
+    context keeps working."""
+    from paper_1903_06304_gb300 import fr
+    nx, ny, p, mach = 16, 12, 3, 0.05
+    c, q = _vortex(nx, ny, p, mach)
+    S = solver_for(c, np.zeros_like(c), nx, ny, p, mach, 10.0, 1.0, apply_bulk=2, wait_spins=-1)
+    qd = to_dev(q)
+    S.precond_build(qd, 1e-20, 150.0)
+    r = to_dev(inp.random_vector(q.shape, 18))
+    z = torch.empty_like(qd)
+    with pytest.raises(fr.FrError) as ex:
+        S.precond_apply(r, z)
+    assert ex.value.code == -5   # FR_ERR_TIMEOUT
+    # the context is intact: the residual, and the same apply with a budget, still run
+    R = torch.empty_like(qd)
+    S.residual(qd, R)
+    assert bool(torch.isfinite(R).all())
+    S2 = solver_for(c, np.zeros_like(c), nx, ny, p, mach, 10.0, 1.0)
+    S2.precond_build(qd, 1e-20, 150.0)
+    z2 = torch.empty_like(qd)
+    S2.precond_apply(r, z2)
+    assert bool(torch.isfinite(z2).all())
