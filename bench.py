@@ -601,7 +601,7 @@ def gpu_arm(args):
                         line_search=args.line_search, graphs=args.graphs,
                         apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog,
                         krylov_arith=arith or args.krylov_arith, precond=precond or args.precond,
-                        mg_prec=args.mg_prec)
+                        mg_prec=args.mg_prec, mg_sweeps=args.mg_sweeps, mg_omega=args.mg_omega)
         S = fr.Solver(cfg, w.nx, w.ny)
         S.dt = w.dt
         S.update_mesh(T(corners), T(vel))
@@ -1090,6 +1090,10 @@ def main():
                     help="block inversion of --kernels-only: SIMT or on the tensor cores")
     ap.add_argument("--mg-prec", dest="mg_prec", default="fp32", choices=["fp32", "fp64"],
                     help="arithmetic of the two-level preconditioner's coarse levels")
+    ap.add_argument("--mg-sweeps", dest="mg_sweeps", type=int, default=2, choices=[1, 2],
+                    help="smoothing sweeps per coarse level and direction")
+    ap.add_argument("--mg-omega", dest="mg_omega", type=float, default=0.7,
+                    help="damping of the coarse block-Jacobi sweeps")
     ap.add_argument("--precond", default="twolevel", choices=["block", "twolevel"],
                     help="element block Jacobi, or with the P1 coarse correction")
     ap.add_argument("--no-c3", dest="no_c3", action="store_true",

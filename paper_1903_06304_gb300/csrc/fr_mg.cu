@@ -11,13 +11,15 @@
 //   M^-1 r = z0 + B^-1 (r - A z0),   z0 = P V(P^T r)
 //
 // P maps per element and variable the coefficients (c0, c1, c2) of c0 + c1 xi + c2 eta to
-// the solution points; V is one V-cycle on the Galerkin operators: A_0 = P^T A P from
-// coloured products of A with the P1 functions of the elements, A_{l+1} = Q^T A_l Q with
+// the solution points; V is one V-cycle on the Galerkin operators: A_0 = P^T A P (from the
+// stored local Jacobians: each element's response to a neighbour's P1 function through
+// their shared face, and its diagonal block times its own; or, with the dual-number
+// operator, from coloured products of A with the elements' P1 functions), A_{l+1} = Q^T A_l Q with
 // Q the exact map of a 2 x 2 agglomerate's P1 function to its children; damped 12 x 12
 // block-Jacobi sweeps on every level but a case's last, which (<= 4 cells) is solved by
-// its dense inverse.  A in the smoothing step is the operator of the build: the coloured
-// products that form A_0 also give the columns A P of every element's stencil members on
-// its own rows, which are stored, so A z0 = (A P) y0 costs no operator product.  Fixed
+// its dense inverse.  A in the smoothing step is the operator of the build: the columns
+// A P of every element's stencil members on its own rows, which form A_0, are stored, so
+// A z0 = (A P) y0 costs no operator product.  Fixed
 // summation orders, no atomics on data: the preconditioner is a fixed linear map between
 // builds (up to the rounding of the coarse arithmetic).
 //
@@ -126,6 +128,216 @@ __global__ void k_p1_gather(fr::Mesh mesh, fr::Basis B, const int* __restrict__ 
   double acc = 0.0;
   for (int pt = 0; pt < NP; ++pt) acc = fma(phi(B, m, pt % N, pt / N), y[v * qs + base + pt], acc);
   A[(((size_t)e * SL + s) * NB + r) * NB + k] = (S)acc;
+}
+
+// Level-0 operators and A P columns from the stored local Jacobians (the build without
+// operator products).  Element e's rows respond to the P1 function (mode k) of a stencil
+// member f != e only through their shared face: f's trace and local-gradient trace on it
+// (by the basis' derivative and interpolation weights and f's metrics), the face Jacobian
+// of f's side gives the change of the common flux, the common solution moves by half of
+// f's trace and lifts into e's corrected gradient, and e's point Jacobians and corrected
+// divergence give the rows.  A member reached through two faces (a 2-wide periodic
+// direction) sums both.  The self columns are e's diagonal block times its own P1
+// functions.  Each column is projected in FP64 onto e's P1 functions for the block of A_0
+// and stored rounded to S for the smoothing step.  One block per element, G groups of n^2
+// threads, one (member, mode) column per group and round.
+template <int N> struct GalSmem {
+  static constexpr int NP = N * N, BS = 4 * NP;
+  static constexpr int G = 128 / NP > 0 ? 128 / NP : 1;
+  static constexpr int JF = 4 * N * 48;            // neighbour side of e's four faces
+  static constexpr int JGE = 64 * NP;              // e's point Jacobians in the corrected gradient
+  static constexpr int SELF = 12 * BS;             // self columns
+  // per group: f's gradient (x, y) at its points, traces (value, gx, gy), flux change,
+  // F, G and the column
+  static constexpr int GX = 0, GY = GX + NP, TQ = GY + NP, TGX = TQ + N, TGY = TGX + N,
+                       DF = TGY + N, F = DF + 4 * N, GG = F + 4 * NP, COL = GG + 4 * NP,
+                       PER = COL + 4 * NP;
+  static constexpr size_t BYTES = sizeof(double) * (JF + JGE + SELF + (size_t)G * PER);
+};
+
+template <int N, class S>
+__global__ void __launch_bounds__(GalSmem<N>::G * N * N)
+k_mg_galerkin_lin(fr::Mesh M, fr::Basis B, const double* __restrict__ gs, const double* __restrict__ gf,
+                  const double* __restrict__ JFQ, const double* __restrict__ JFG,
+                  const double* __restrict__ JG, const double* __restrict__ B64,
+                  const int* __restrict__ nb0, S* __restrict__ A0, S* __restrict__ AP) {
+  using namespace fr;
+  using L = GalSmem<N>;
+  constexpr int NP = L::NP, BS = L::BS, G = L::G;
+  extern __shared__ double smg[];
+  double* sJF = smg;
+  double* sJG = sJF + L::JF;
+  double* sSelf = sJG + L::JGE;
+  const int e = blockIdx.x;
+  if (!M.on(e)) return;
+  const int grp = threadIdx.x / NP, pt = threadIdx.x % NP;
+  const int i = pt % N, j = pt / N;
+  double* W = sSelf + L::SELF + (size_t)grp * L::PER;
+  const bool visc = M.viscous;
+  const int nf = M.ne * 2 * N;
+  const size_t SN = (size_t)M.ne * NP, FNs = (size_t)M.ne * 4 * N;
+  const int nbf[4] = {M.left(e), M.right(e), M.bottom(e), M.top(e)};   // FACE_L, R, B, T
+  // neighbour side of each face's Jacobian: q entries (r, c) then g entries (r, c)
+  for (int t = threadIdx.x; t < L::JF; t += blockDim.x) {
+    const int f = t / (N * 48), rem = t % (N * 48), sp = rem / 48, k = rem % 48;
+    double val = 0.0;
+    if (nbf[f] >= 0) {
+      const bool own = (f == FACE_R || f == FACE_T);   // e owns it: the neighbour is '+'
+      const int owner = own ? e : nbf[f];
+      const int dir = (f == FACE_R || f == FACE_L) ? 0 : 1;
+      const size_t idx = ((size_t)owner * 2 + dir) * N + sp;
+      if (k < 16) {
+        const int r = k / 4, cc = k % 4;
+        val = JFQ[(size_t)(r * 8 + (own ? 4 + cc : cc)) * nf + idx];
+      } else if (visc) {
+        const int r = (k - 16) / 8, cc = (k - 16) % 8;
+        val = JFG[(size_t)(r * 16 + (own ? 8 + cc : cc)) * nf + idx];
+      }
+    }
+    sJF[t] = val;
+  }
+  for (int t = threadIdx.x; t < L::JGE; t += blockDim.x)
+    sJG[t] = visc ? JG[(size_t)(t / NP) * SN + (size_t)e * NP + t % NP] : 0.0;
+  // self columns: B_e P_e (FP64)
+  for (int t = threadIdx.x; t < L::SELF; t += blockDim.x) {
+    const int k = t / BS, row = t % BS, v = k / 3, m = k % 3;
+    const double* brow = B64 + ((size_t)e * BS + row) * BS + (size_t)v * NP;
+    double acc = 0.0;
+    for (int q = 0; q < NP; ++q) acc = fma(brow[q], phi(B, m, q % N, q / N), acc);
+    sSelf[t] = acc;
+  }
+  // e's lifting weights at this point
+  const size_t o = (size_t)e * NP + pt;
+  const double ij = gs[GS_INVJ * SN + o];
+  double lsx[4], lsy[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const int sp = (f < 2) ? j : i;
+    const double w = (f == FACE_L) ? B.dgL[i] : (f == FACE_R) ? B.dgR[i]
+                   : (f == FACE_B) ? B.dgL[j] : B.dgR[j];
+    const size_t of = ((size_t)e * 4 + f) * N + sp;
+    lsx[f] = gf[GF_SX * FNs + of] * w * ij;
+    lsy[f] = gf[GF_SY * FNs + of] * w * ij;
+  }
+  __syncthreads();
+  // the self slot: A_0 block and stored columns
+  for (int t = threadIdx.x; t < NB * BS; t += blockDim.x) {
+    const int k = t / BS, row = t % BS;
+    AP[(((size_t)e * SL + 0) * NB + k) * BS + row] = (S)sSelf[t];
+  }
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+    const int r = t / NB, k = t % NB, v = r / 3, m = r % 3;
+    double acc = 0.0;
+    for (int q = 0; q < NP; ++q) acc = fma(phi(B, m, q % N, q / N), sSelf[k * BS + v * NP + q], acc);
+    A0[(((size_t)e * SL + 0) * NB + r) * NB + k] = (S)acc;
+  }
+  // neighbour slots: tasks (slot 1..4, mode) in rounds of G
+  for (int t0 = 0; t0 < 4 * NB; t0 += G) {
+    const int task = t0 + grp;
+    const int slot = 1 + task / NB, k = task % NB, v = k / 3, m = k % 3;
+    const int cell = task < 4 * NB ? nb0[(size_t)e * SL + slot] : -1;
+    double col[4] = {0.0, 0.0, 0.0, 0.0};   // this point's rows (variables 0..3)
+    for (int fe = 0; fe < 4; ++fe) {
+      const bool act = cell >= 0 && nbf[fe] == cell;
+      const int f = act ? cell : e;
+      // f's face opposite fe, and the line of f's points ending at each face point
+      const int fp = fe == FACE_L ? FACE_R : fe == FACE_R ? FACE_L : fe == FACE_B ? FACE_T : FACE_B;
+      // 1: local gradient of the P1 function on f (variable v only)
+      if (act && visc) {
+        const size_t of = (size_t)f * NP + pt;
+        double dxi = 0.0, deta = 0.0;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          dxi = fma(B.D[i][q], phi(B, m, q, j), dxi);
+          deta = fma(B.D[j][q], phi(B, m, i, q), deta);
+        }
+        const double fij = gs[GS_INVJ * SN + of];
+        W[L::GX + pt] = (gs[GS_SXX * SN + of] * dxi + gs[GS_SEX * SN + of] * deta) * fij;
+        W[L::GY + pt] = (gs[GS_SXY * SN + of] * dxi + gs[GS_SEY * SN + of] * deta) * fij;
+      }
+      __syncthreads();
+      // 2: traces on f's face fp
+      if (act && pt < N) {
+        const int sp = pt;
+        const double* w = (fp == FACE_L || fp == FACE_B) ? B.lL : B.lR;
+        const bool row = (fp == FACE_L || fp == FACE_R);
+        double tq = 0.0, tx = 0.0, ty = 0.0;
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          const int ii = row ? q : sp, jj = row ? sp : q;
+          tq = fma(w[q], phi(B, m, ii, jj), tq);
+          if (visc) {
+            tx = fma(w[q], W[L::GX + jj * N + ii], tx);
+            ty = fma(w[q], W[L::GY + jj * N + ii], ty);
+          }
+        }
+        W[L::TQ + sp] = tq;
+        W[L::TGX + sp] = tx;
+        W[L::TGY + sp] = ty;
+      }
+      __syncthreads();
+      // 3: change of the common flux on the shared face (only variable v's columns)
+      for (int t = pt; act && t < 4 * N; t += NP) {
+        const int r = t / N, sp = t % N;
+        const double* jf = sJF + (fe * N + sp) * 48;
+        double acc = jf[r * 4 + v] * W[L::TQ + sp];
+        if (visc && r > 0) {
+          acc = fma(jf[16 + r * 8 + v], W[L::TGX + sp], acc);
+          acc = fma(jf[16 + r * 8 + 4 + v], W[L::TGY + sp], acc);
+        }
+        W[L::DF + r * N + sp] = acc;
+      }
+      // 4: e's fluxes from its corrected gradient (half of f's trace lifted through fe)
+      if (act && visc) {
+        const int sp = (fe < 2) ? j : i;
+        const double half = 0.5 * W[L::TQ + sp];
+        const double gx = half * lsx[fe], gy = half * lsy[fe];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const double val = (r % 4 == 0) ? 0.0
+                           : fma(sJG[(r * 8 + v) * NP + pt], gx, sJG[(r * 8 + 4 + v) * NP + pt] * gy);
+          if (r < 4) W[L::F + r * NP + pt] = val;
+          else W[L::GG + (r - 4) * NP + pt] = val;
+        }
+      }
+      __syncthreads();
+      // 5: e's rows: corrected divergence of the fluxes and the face term of fe
+      if (act) {
+        const double dgw = (fe == FACE_L) ? B.dgL[i] : (fe == FACE_R) ? B.dgR[i]
+                         : (fe == FACE_B) ? B.dgL[j] : B.dgR[j];
+        const int sp = (fe < 2) ? j : i;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          double d = 0.0;
+          if (visc) {
+#pragma unroll
+            for (int q = 0; q < N; ++q) d = fma(B.Dc[i][q], W[L::F + r * NP + j * N + q], d);
+#pragma unroll
+            for (int q = 0; q < N; ++q) d = fma(B.Dc[j][q], W[L::GG + r * NP + q * N + i], d);
+          }
+          d = fma(dgw, W[L::DF + r * N + sp], d);
+          col[r] = fma(ij, d, col[r]);
+        }
+      }
+      __syncthreads();
+    }
+    // the column to shared memory, stored and projected
+    if (cell >= 0) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        W[L::COL + r * NP + pt] = col[r];
+        AP[(((size_t)e * SL + slot) * NB + k) * BS + r * NP + pt] = (S)col[r];
+      }
+    }
+    __syncthreads();
+    for (int t = pt; cell >= 0 && t < NB; t += NP) {
+      const int rv = t / 3, rm = t % 3;
+      double acc = 0.0;
+      for (int q = 0; q < NP; ++q) acc = fma(phi(B, rm, q % N, q / N), W[L::COL + rv * NP + q], acc);
+      A0[(((size_t)e * SL + slot) * NB + t) * NB + k] = (S)acc;
+    }
+    __syncthreads();
+  }
 }
 
 // b0 = P^T r (per element: 12 sums over its points, FP64, stored in S)
@@ -457,48 +669,60 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(const Lv<S>* __restric
 }
 
 // ---------------------------------------------------------------- build kernels
-// Inverse of one 12 x 12 block by Gauss-Jordan with partial pivoting on [A | I] (one
-// thread, FP64); returns false on a zero pivot.
-__device__ bool gj_inverse12(double* a, double* inv) {
-  for (int i = 0; i < BLK; ++i) inv[i] = (i / NB == i % NB) ? 1.0 : 0.0;
-  for (int k = 0; k < NB; ++k) {
-    int p = k;
-    double best = fabs(a[k * NB + k]);
-    for (int i = k + 1; i < NB; ++i)
-      if (fabs(a[i * NB + k]) > best) { best = fabs(a[i * NB + k]); p = i; }
-    if (!(best > 0.0)) return false;
-    if (p != k) {
-      for (int j = 0; j < NB; ++j) {
-        double t = a[k * NB + j]; a[k * NB + j] = a[p * NB + j]; a[p * NB + j] = t;
-        t = inv[k * NB + j]; inv[k * NB + j] = inv[p * NB + j]; inv[p * NB + j] = t;
-      }
-    }
-    const double d = 1.0 / a[k * NB + k];
-    for (int j = 0; j < NB; ++j) { a[k * NB + j] *= d; inv[k * NB + j] *= d; }
-    for (int i = 0; i < NB; ++i) {
-      if (i == k) continue;
-      const double f = a[i * NB + k];
-      for (int j = 0; j < NB; ++j) {
-        a[i * NB + j] = fma(-f, a[k * NB + j], a[i * NB + j]);
-        inv[i * NB + j] = fma(-f, inv[k * NB + j], inv[i * NB + j]);
-      }
-    }
-  }
-  return true;
-}
-
 // Dinv = inverse of the diagonal (slot 0) block of every cell that is smoothed (parent
-// >= 0); *bad counts singular blocks.
+// >= 0); *bad counts singular blocks.  One warp per cell: Gauss-Jordan with partial
+// pivoting on [A | I] in FP64, lane c < 24 holding column c of the 12 x 24 array in
+// registers (the pivot search by the pivot column's lane, the row operations by every
+// lane on its own column with the multipliers broadcast from that lane).
 template <class S>
 __global__ void k_mg_invert_diag(Lv<S> L, S* __restrict__ Dinv, int* __restrict__ bad) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (c >= L.nc || L.parent[c] < 0) return;
-  double a[BLK], inv[BLK];
-  const S* src = L.A + (size_t)c * SL * BLK;
-  for (int i = 0; i < BLK; ++i) a[i] = (double)src[i];
-  if (!gj_inverse12(a, inv)) atomicAdd(bad, 1);
+  const S* src = L.A + (size_t)c * SL * BLK;   // slot 0: the diagonal block
+  double col[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i)
+    col[i] = lane < NB ? (double)src[i * NB + lane] : (lane < 2 * NB && i == lane - NB ? 1.0 : 0.0);
+  bool singular = false;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    // pivot row: the largest |a[i][k]|, i >= k (lane k searches its column)
+    int p = k;
+    double best = 0.0;
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+      if (i >= k && fabs(col[i]) > best) { best = fabs(col[i]); p = i; }
+    p = __shfl_sync(0xffffffffu, p, k);
+    best = __shfl_sync(0xffffffffu, best, k);
+    if (!(best > 0.0)) { singular = true; break; }
+    // swap rows k and p in every column
+    double rk = 0.0, rp = 0.0;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) { if (i == k) rk = col[i]; if (i == p) rp = col[i]; }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) { if (i == k) col[i] = rp; else if (i == p) col[i] = rk; }
+    // scale row k by the pivot, then eliminate column k from every other row
+    const double piv = __shfl_sync(0xffffffffu, rp, k);
+    const double inv = 1.0 / piv;
+    double rowk = 0.0;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) if (i == k) { col[i] *= inv; rowk = col[i]; }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const double f = __shfl_sync(0xffffffffu, col[i], k);   // a[i][k] after the swap
+      if (i != k) col[i] = fma(-f, rowk, col[i]);
+    }
+  }
+  if (singular) {
+    if (lane == 0) atomicAdd(bad, 1);
+    return;
+  }
   S* dst = Dinv + (size_t)c * BLK;
-  for (int i = 0; i < BLK; ++i) dst[i] = (S)inv[i];
+  if (lane >= NB && lane < 2 * NB) {
+#pragma unroll
+    for (int i = 0; i < NB; ++i) dst[i * NB + (lane - NB)] = (S)col[i];
+  }
 }
 
 // Dense inverse of each finishing case: its cells' blocks assembled into one (12 m)^2
@@ -663,6 +887,23 @@ template <int N, class S>
 int build_level0(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s) {
   constexpr int NP = N * N;
   MgLevel& L0 = c->mg[0];
+  if (c->cfg.jvp_mode == FR_JVP_LINEARIZED) {
+    // from the local Jacobians stored at q (the operator GMRES applies) and the element
+    // blocks of the same build
+    using GL = GalSmem<N>;
+    FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_mg_galerkin_lin<N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)GL::BYTES));
+    FR_PROF_BEGIN(c, s);
+    k_mg_galerkin_lin<N, S><<<c->ne, GL::G * NP, GL::BYTES, s>>>(c->mesh, c->basis, c->gs, c->gf, c->JFQ,
+                                                                c->JFG, c->JG, c->B64, L0.nb, (S*)L0.A,
+                                                                (S*)c->mg_ap);
+    FR_PROF_END(c, s, KK_COARSE);
+    FR_LAUNCH_CHECK(c);
+    // per element: 48 neighbour columns (traces, face products, lifted fluxes, divergence)
+    // and 12 self columns, each projected on 12 P1 functions
+    FR_ACCOUNT(c, KK_COARSE, 2.0 * c->ne * (48.0 * NP * (4.0 * N + 24.0 + 2.0 * NB) + 12.0 * 4 * NP * NP + 60.0 * NB * NP), 0.0);
+    return FR_OK;
+  }
   const long long npts = (long long)c->ne * NP;
   // one operator product per colour and P1 function
   for (int col = 0; col < c->mg_ncol; ++col) {
@@ -694,7 +935,7 @@ int build_levels(fr_ctx* c, cudaStream_t s) {
     MgLevel& L = c->mg[l];
     const Lv<S> V = view<S>(L);
     FR_PROF_BEGIN(c, s);
-    k_mg_invert_diag<S><<<blocks_for(L.nc, 64), 64, 0, s>>>(V, (S*)L.Dinv, c->mg_bad);
+    k_mg_invert_diag<S><<<blocks_for((long long)L.nc * 32, 128), 128, 0, s>>>(V, (S*)L.Dinv, c->mg_bad);
     if (L.nfin > 0) k_mg_coarsest<S><<<L.nfin, 128, 0, s>>>(V, L.fin, (S*)L.Ainv, c->mg_bad);
     if (l + 1 < c->mg.size()) {
       const MgLevel& Nx = c->mg[l + 1];

@@ -240,3 +240,39 @@ def test_fp32_coarse_levels_against_fp64(torch, cfg):
     assert abs(its["fp32"] - its["fp64"]) <= max(2, 0.15 * its["fp64"]), its
     # both true residuals at the level GMRES was asked for
     assert xs["fp32"] <= 10 * max(xs["fp64"], 1e-7), xs
+
+
+@pytest.mark.parametrize("cfg", APPLY_CASES)
+@pytest.mark.parametrize("bounded", [False, True])
+def test_local_galerkin_build_equals_operator_products(torch, cfg, bounded):
+    """The level-0 operators and A P columns formed from the stored local Jacobians (face
+    couplings and the element blocks: the build of the linearised operator mode) against
+    those formed by coloured products of the dual-number operator: the same preconditioner
+    to the rounding of the two evaluation orders."""
+    from paper_1903_06304_gb300 import fr
+    nx, ny, p, mach, re, kappa, deforming = cfg
+    inv_dtau, a0_dt = 0.3, 150.0
+    if bounded:
+        nx, ny = max(nx, 4), max(ny, 3)
+        c, v = inp.plunge(inp.naca_ogrid(nx, ny, first=0.05), 0.3)
+        qi = inp.far_field_state(mach)
+        q = inp.random_perturbation(inp.uniform_state(nx * ny, p, mach), 5, 0.02, mach)
+    else:
+        c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
+    r = to_dev(inp.random_vector(q.shape, 19))
+    outs = []
+    for mode in ("dual", "linearized"):
+        kw = dict(p=p, mach=mach, re=re, kappa=kappa, precond="twolevel", mg_prec="fp64",
+                  jvp_mode=mode, block_mode=mode)
+        if bounded:
+            S = fr.Solver(fr.Config(**kw), nx, ny, bc=("wall", "farfield"), q_inf=qi)
+        else:
+            S = fr.Solver(fr.Config(**kw), nx, ny)
+        S.update_mesh(to_dev(c), to_dev(v))
+        S.precond_build(to_dev(q), inv_dtau, a0_dt)
+        out = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
+        S.precond_apply(r, out)
+        outs.append(to_host(out))
+        S.close()
+    err = np.abs(outs[1] - outs[0]).max() / np.abs(outs[0]).max()
+    assert err <= APPLY_TOL, err
