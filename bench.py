@@ -782,7 +782,8 @@ def gpu_arm(args):
         gm_cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
                            restart=args.restart, maxit_lin=120, tol_res=1e-30, graphs=args.graphs,
                            apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog,
-                           krylov_arith=args.krylov_arith, precond=precond)
+                           krylov_arith=args.krylov_arith, precond=precond, mg_prec=args.mg_prec,
+                           mg_sweeps=args.mg_sweeps, mg_omega=args.mg_omega)
         Sg = fr.Solver(gm_cfg, w.nx, w.ny)
         Sg.update_mesh(*(meshes[run.k] if meshes is not None else (T(corners), T(vel))))
         Sg.precond_build(run.q, 1e-20, 1.5 / w.dt)
@@ -885,7 +886,8 @@ def gpu_arm(args):
                             f"{args.krylov_arith} basis, maxit {args.maxit_lin}",
                    "newton": f"max {args.maxit_newton} iterations, backtracking {args.line_search} halvings",
                    "precond": f"{args.precond} ({args.prec} element blocks, {args.apply_accum} apply accumulation"
-                              + (f", {args.mg_prec} coarse levels)" if args.precond == "twolevel" else ")"),
+                              + (f", {args.mg_prec} coarse levels, {args.mg_sweeps} sweep(s) of"
+                                 f" damping {args.mg_omega})" if args.precond == "twolevel" else ")"),
                    "march": f"{args.startup} start-up + {args.warmup} warm-up steps before the timed steps",
                    "l2": "256 MiB write between timed steps, outside the per-step events",
                    "tiles": S.tiles,
@@ -1092,8 +1094,9 @@ def main():
                     help="arithmetic of the two-level preconditioner's coarse levels")
     ap.add_argument("--mg-sweeps", dest="mg_sweeps", type=int, default=2, choices=[1, 2],
                     help="smoothing sweeps per coarse level and direction")
-    ap.add_argument("--mg-omega", dest="mg_omega", type=float, default=0.7,
-                    help="damping of the coarse block-Jacobi sweeps")
+    ap.add_argument("--mg-omega", dest="mg_omega", type=float, default=0.8,
+                    help="damping of the coarse block-Jacobi sweeps (0.8: the fastest of "
+                         "0.7 .. 1.0 with 1 or 2 sweeps on the benchmark workload)")
     ap.add_argument("--precond", default="twolevel", choices=["block", "twolevel"],
                     help="element block Jacobi, or with the P1 coarse correction")
     ap.add_argument("--no-c3", dest="no_c3", action="store_true",
