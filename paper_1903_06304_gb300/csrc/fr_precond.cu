@@ -9,6 +9,7 @@
 // Apply:  z_e = Dc (B~_e^-1 (Dr r_e)), FP64 in/out; FP32/BF16 inverses applied with
 //         double-float accumulation on the FP32 pipe (default) or in plain FP32.
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 #include <cuda_bf16.h>
 #include "fr_internal.h"
@@ -829,6 +830,24 @@ __device__ __forceinline__ void apply_elem(int e, const S* __restrict__ A, const
   const float* Dout = tr ? Dr : Dc;
   const size_t qo = M.qbase(e, NP), qs = M.qstride(e);
   constexpr int CT = 5 * 12;   // coarse terms of a row: 5 stencil members x 12 P1 coefficients
+  constexpr int CPT = (CT + APPLY_PARTS - 1) / APPLY_PARTS;   // coarse terms per thread
+  using SC = typename std::conditional<CO == 2, double, float>::type;
+  // this thread's A P entries, its input row and scale, loaded with the inverse's columns
+  SC apv[CO ? CPT : 1];
+  if constexpr (CO != 0) {
+    const SC* ap = (const SC*)APe + row;
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+      const int kk = part + APPLY_PARTS * k;
+      apv[k] = (row < BS && kk < CT) ? ap[(size_t)kk * BS] : SC(0);
+    }
+  }
+  double rin = 0.0, din = 0.0;
+  if (threadIdx.x < BS) {
+    const int t = threadIdx.x;
+    rin = r[(t / NP) * qs + qo + t % NP];
+    din = (double)Din[(size_t)e * BS + t];
+  }
   __shared__ double cyd[CO == 2 ? CT : 1];
   __shared__ float cyf[CO == 1 ? CT : 1];
   __shared__ double cpd[CO == 2 ? APPLY_PARTS : 1][CO == 2 ? BSR : 1];
@@ -842,22 +861,28 @@ __device__ __forceinline__ void apply_elem(int e, const S* __restrict__ A, const
     __syncthreads();
     if (row < BS) {
       if constexpr (CO == 2) {
-        const double* ap = (const double*)APe + row;
         double a0 = 0.0;
 #pragma unroll
-        for (int k = part; k < CT; k += APPLY_PARTS) a0 = fma(ap[(size_t)k * BS], cyd[k], a0);
+        for (int k = 0; k < CPT; ++k) {
+          const int kk = part + APPLY_PARTS * k;
+          if (kk < CT) a0 = fma(apv[k], cyd[kk], a0);
+        }
         cpd[part][row] = a0;
       } else {
-        const float* ap = (const float*)APe + row;
         float h0 = 0.f, l0 = 0.f;
 #pragma unroll
-        for (int k = part; k < CT; k += APPLY_PARTS) df_add(h0, l0, ap[(size_t)k * BS], make_float2(cyf[k], 0.f));
+        for (int k = 0; k < CPT; ++k) {
+          const int kk = part + APPLY_PARTS * k;
+          if (kk < CT) df_add(h0, l0, apv[k], make_float2(cyf[kk], 0.f));
+        }
         cpf[part][row] = make_float2(h0, l0);
       }
     }
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < BS; t += blockDim.x) {
+  // the block has at least BS threads: thread t < BS stages input row t
+  if (threadIdx.x < BS) {
+    const int t = threadIdx.x;
     const int v = t / NP, pt = t % NP;
     const size_t gi = v * qs + qo + pt;
     double rs = rsub ? rsub[gi] : 0.0;
@@ -871,7 +896,7 @@ __device__ __forceinline__ void apply_elem(int e, const S* __restrict__ A, const
       for (int q = 1; q < APPLY_PARTS; ++q) df_merge(sh, sl, cpf[q][t].x, cpf[q][t].y);
       rs = (double)sh + (double)sl;
     }
-    const double u = (r[gi] - rs) * (double)Din[(size_t)e * BS + t];
+    const double u = (rin - rs) * din;
     if (ACC == 0) xd[t] = u;
     else if (ACC == 1) xf[t] = (float)u;
     else {
