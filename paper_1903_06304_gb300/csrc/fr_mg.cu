@@ -437,23 +437,21 @@ __global__ void __launch_bounds__((TX + 2 * NU) * (TX + 2 * NU) * NB) k_mg_down(
   int* cell = reinterpret_cast<int*>(res + RN);
   const Tile T = tiles[blockIdx.x];
   const CaseLevel g = cl[T.k];
-  for (int p = threadIdx.x; p < RN; p += blockDim.x) cell[p] = region_cell(g, T.i0, T.j0, NU, p % RX, p / RX);
-  __syncthreads();
-  for (int t = threadIdx.x; t < RN * NB; t += blockDim.x) {
-    const int p = t / NB, r = t % NB, c = cell[p];
-    sb[p][r] = c >= 0 ? L.b[(size_t)c * NB + r] : S(0);
-  }
+  // one thread per region row (RN * NB == blockDim): its row of D^-1 and of b, loaded first
+  const int tp = threadIdx.x / NB, tr = threadIdx.x % NB;
+  const int tc = region_cell(g, T.i0, T.j0, NU, tp % RX, tp / RX);
+  S drow[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) drow[k] = tc >= 0 ? L.Dinv[((size_t)tc * NB + tr) * NB + k] : S(0);
+  sb[tp][tr] = tc >= 0 ? L.b[(size_t)tc * NB + tr] : S(0);
+  if (tr == 0) cell[tp] = tc;
   __syncthreads();
   // sweep 1 from zero: x = omega D^-1 b on the whole region
-  for (int t = threadIdx.x; t < RN * NB; t += blockDim.x) {
-    const int p = t / NB, r = t % NB, c = cell[p];
+  {
     S acc = S(0);
-    if (c >= 0) {
-      const S* d = L.Dinv + ((size_t)c * NB + r) * NB;
 #pragma unroll
-      for (int k = 0; k < NB; ++k) acc = fma(d[k], sb[p][k], acc);
-    }
-    x0[p][r] = omega * acc;
+    for (int k = 0; k < NB; ++k) acc = fma(drow[k], sb[tp][k], acc);
+    x0[tp][tr] = omega * acc;
   }
   __syncthreads();
   S (*cur)[NB] = x0;
@@ -467,14 +465,14 @@ __global__ void __launch_bounds__((TX + 2 * NU) * (TX + 2 * NU) * NB) k_mg_down(
       res[p][r] = region_residual<S, RX>(L, g, c, j, a, b, r, sb[p], cur);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < RN * NB; t += blockDim.x) {
-      const int p = t / NB, r = t % NB, a = p % RX, b = p / RX, c = cell[p];
-      if (a < sw || a >= RX - sw || b < sw || b >= RX - sw || c < 0) continue;
-      const S* d = L.Dinv + ((size_t)c * NB + r) * NB;
-      S acc = S(0);
+    {
+      const int a = tp % RX, b = tp / RX;
+      if (!(a < sw || a >= RX - sw || b < sw || b >= RX - sw || tc < 0)) {
+        S acc = S(0);
 #pragma unroll
-      for (int k = 0; k < NB; ++k) acc = fma(d[k], res[p][k], acc);
-      nxt[p][r] = cur[p][r] + omega * acc;
+        for (int k = 0; k < NB; ++k) acc = fma(drow[k], res[tp][k], acc);
+        nxt[tp][tr] = cur[tp][tr] + omega * acc;
+      }
     }
     __syncthreads();
     S (*tmp)[NB] = cur; cur = nxt; nxt = tmp;
@@ -523,7 +521,13 @@ __global__ void __launch_bounds__((TX + 2 * NU) * (TX + 2 * NU) * NB) k_mg_up(Lv
   int* cell = reinterpret_cast<int*>(res + RN);
   const Tile T = tiles[blockIdx.x];
   const CaseLevel g = cl[T.k];
-  for (int p = threadIdx.x; p < RN; p += blockDim.x) cell[p] = region_cell(g, T.i0, T.j0, NU, p % RX, p / RX);
+  // one thread per region row (RN * NB == blockDim): its row of D^-1, loaded first
+  const int tp = threadIdx.x / NB, tr = threadIdx.x % NB;
+  const int tc = region_cell(g, T.i0, T.j0, NU, tp % RX, tp / RX);
+  S drow[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k) drow[k] = tc >= 0 ? L.Dinv[((size_t)tc * NB + tr) * NB + k] : S(0);
+  if (tr == 0) cell[tp] = tc;
   __syncthreads();
   // the smoothed values plus the parents' correction, on the whole region
   for (int t = threadIdx.x; t < RN * NB; t += blockDim.x) {
@@ -552,14 +556,14 @@ __global__ void __launch_bounds__((TX + 2 * NU) * (TX + 2 * NU) * NB) k_mg_up(Lv
       res[p][r] = region_residual<S, RX>(L, g, c, j, a, b, r, sb[p], cur);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < RN * NB; t += blockDim.x) {
-      const int p = t / NB, r = t % NB, a = p % RX, b = p / RX, c = cell[p];
-      if (a < sw || a >= RX - sw || b < sw || b >= RX - sw || c < 0) continue;
-      const S* d = L.Dinv + ((size_t)c * NB + r) * NB;
-      S acc = S(0);
+    {
+      const int a = tp % RX, b = tp / RX;
+      if (!(a < sw || a >= RX - sw || b < sw || b >= RX - sw || tc < 0)) {
+        S acc = S(0);
 #pragma unroll
-      for (int k = 0; k < NB; ++k) acc = fma(d[k], res[p][k], acc);
-      nxt[p][r] = cur[p][r] + omega * acc;
+        for (int k = 0; k < NB; ++k) acc = fma(drow[k], res[tp][k], acc);
+        nxt[tp][tr] = cur[tp][tr] + omega * acc;
+      }
     }
     __syncthreads();
     S (*tmp)[NB] = cur; cur = nxt; nxt = tmp;
