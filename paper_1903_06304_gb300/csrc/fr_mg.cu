@@ -395,21 +395,52 @@ __device__ __forceinline__ int dir_slot(const CaseLevel& g, int j, int d) {
   return above ? (below ? 4 : 3) : -1;
 }
 
+// Row r of the operator block in stencil slot s of cell c (12 contiguous entries at a
+// 48- or 96-byte multiple: 16-byte aligned), zeros for an absent slot (s < 0).
+__device__ __forceinline__ void load_row12(const float* A, int c, int s, int r, float out[NB]) {
+  if (s < 0) {
+#pragma unroll
+    for (int k = 0; k < NB; ++k) out[k] = 0.f;
+    return;
+  }
+  const float4* p = reinterpret_cast<const float4*>(A + (((size_t)c * SL + s) * NB + r) * NB);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float4 v = p[q];
+    out[4 * q] = v.x; out[4 * q + 1] = v.y; out[4 * q + 2] = v.z; out[4 * q + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void load_row12(const double* A, int c, int s, int r, double out[NB]) {
+  if (s < 0) {
+#pragma unroll
+    for (int k = 0; k < NB; ++k) out[k] = 0.0;
+    return;
+  }
+  const double2* p = reinterpret_cast<const double2*>(A + (((size_t)c * SL + s) * NB + r) * NB);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const double2 v = p[q];
+    out[2 * q] = v.x; out[2 * q + 1] = v.y;
+  }
+}
+
 // r-th row of b - A x at region position (a, b) (cell c, row j of its case) with the
 // neighbours' values in the region array xs (stride RX).
 template <class S, int RX>
 __device__ __forceinline__ S region_residual(const Lv<S>& L, const CaseLevel& g, int c, int j, int a, int bb,
                                              int r, const S* bs, const S (*xs)[NB]) {
   const int da[5] = {0, -1, 1, 0, 0}, db[5] = {0, 0, 0, -1, 1};
+  // the five operator rows first (16-byte vector loads, absent members as zeros), then the
+  // products: one round trip to memory instead of five
+  S av[5][NB];
+#pragma unroll
+  for (int d = 0; d < 5; ++d) load_row12(L.A, c, dir_slot(g, j, d), r, av[d]);
   S acc = bs[r];
 #pragma unroll
   for (int d = 0; d < 5; ++d) {
-    const int s = dir_slot(g, j, d);
-    if (s < 0) continue;
-    const S* arow = L.A + (((size_t)c * SL + s) * NB + r) * NB;
     const S* xn = xs[(bb + db[d]) * RX + a + da[d]];
 #pragma unroll
-    for (int k = 0; k < NB; ++k) acc = fma(-arow[k], xn[k], acc);
+    for (int k = 0; k < NB; ++k) acc = fma(-av[d][k], xn[k], acc);
   }
   return acc;
 }
@@ -426,7 +457,7 @@ constexpr size_t tile_smem() {
 }
 
 template <class S, int NU>
-__global__ void __launch_bounds__((TX + 2 * NU) * (TX + 2 * NU) * NB) k_mg_down(Lv<S> L, const CaseLevel* __restrict__ cl, const Tile* __restrict__ tiles,
+__global__ void __launch_bounds__((TX + 2 * NU) * (TX + 2 * NU) * NB, 2) k_mg_down(Lv<S> L, const CaseLevel* __restrict__ cl, const Tile* __restrict__ tiles,
                                                  S omega, S* __restrict__ bn) {
   constexpr int RX = TX + 2 * NU, RN = RX * RX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -510,7 +541,7 @@ __global__ void __launch_bounds__((TX + 2 * NU) * (TX + 2 * NU) * NB) k_mg_down(
 }
 
 template <class S, int NU>
-__global__ void __launch_bounds__((TX + 2 * NU) * (TX + 2 * NU) * NB) k_mg_up(Lv<S> L, const CaseLevel* __restrict__ cl, const Tile* __restrict__ tiles,
+__global__ void __launch_bounds__((TX + 2 * NU) * (TX + 2 * NU) * NB, 2) k_mg_up(Lv<S> L, const CaseLevel* __restrict__ cl, const Tile* __restrict__ tiles,
                                                S omega, const S* __restrict__ xp) {
   constexpr int RX = TX + 2 * NU, RN = RX * RX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
