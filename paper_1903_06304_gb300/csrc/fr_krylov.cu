@@ -453,6 +453,13 @@ __global__ void __launch_bounds__(RT) k_vaxpy(const double* __restrict__ V, size
   for (size_t i = lo + threadIdx.x; i < hi; i += RT) {
     double2 x = w2[i];
     int q = 0;
+    for (; q + 8 <= nv; q += 8) {   // eight independent loads in flight, the sums in order
+      double2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = V2[(q + u) * ld2 + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) { x.x = fma(-hs[q + u], v[u].x, x.x); x.y = fma(-hs[q + u], v[u].y, x.y); }
+    }
     for (; q + 4 <= nv; q += 4) {   // four independent loads in flight
       const double2 v0 = V2[(q + 0) * ld2 + i], v1 = V2[(q + 1) * ld2 + i];
       const double2 v2 = V2[(q + 2) * ld2 + i], v3 = V2[(q + 3) * ld2 + i];
@@ -509,6 +516,13 @@ __global__ void __launch_bounds__(RT) k_vaxdots(const double* __restrict__ V, si
     const size_t i = lo + threadIdx.x;
     double2 x = w2[i];
     int q = 0;
+    for (; q + 8 <= nv; q += 8) {   // eight independent loads in flight, the sums in order
+      double2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = V2[(q + u) * ld2 + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) { x.x = fma(-hs[q + u], v[u].x, x.x); x.y = fma(-hs[q + u], v[u].y, x.y); }
+    }
     for (; q + 4 <= nv; q += 4) {
       const double2 v0 = V2[(q + 0) * ld2 + i], v1 = V2[(q + 1) * ld2 + i];
       const double2 v2 = V2[(q + 2) * ld2 + i], v3 = V2[(q + 3) * ld2 + i];

@@ -78,19 +78,7 @@ struct Lv {
   const S* Ainv;        // [nfin][48][48]
 };
 
-template <class S>
-__device__ __forceinline__ S row_product(const Lv<S>& L, int c, int r, const S* x) {
-  S acc = S(0);
-  for (int s = 0; s < SL; ++s) {
-    const int f = L.nb[c * SL + s];
-    if (f < 0) continue;
-    const S* a = L.A + (((size_t)c * SL + s) * NB + r) * NB;
-    const S* xf = x + (size_t)f * NB;
-#pragma unroll
-    for (int k = 0; k < NB; ++k) acc = fma(a[k], xf[k], acc);
-  }
-  return acc;
-}
+
 
 // ---------------------------------------------------------------- fine <-> level 0
 // Seeds of the level-0 Galerkin products: P1 function k of every element of colour col.
@@ -422,6 +410,27 @@ __device__ __forceinline__ void load_row12(const double* A, int c, int s, int r,
     const double2 v = p[q];
     out[2 * q] = v.x; out[2 * q + 1] = v.y;
   }
+}
+
+// Row r of (A x)_c: the five operator rows loaded first (vector loads), then the products.
+template <class S>
+__device__ __forceinline__ S row_product(const Lv<S>& L, int c, int r, const S* x) {
+  S av[SL][NB];
+  int nb[SL];
+#pragma unroll
+  for (int s = 0; s < SL; ++s) {
+    nb[s] = L.nb[c * SL + s];
+    load_row12(L.A, c, nb[s] >= 0 ? s : -1, r, av[s]);
+  }
+  S acc = S(0);
+#pragma unroll
+  for (int s = 0; s < SL; ++s) {
+    if (nb[s] < 0) continue;
+    const S* xf = x + (size_t)nb[s] * NB;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) acc = fma(av[s][k], xf[k], acc);
+  }
+  return acc;
 }
 
 // r-th row of b - A x at region position (a, b) (cell c, row j of its case) with the
