@@ -424,11 +424,16 @@ int fr_param_jvp(fr_ctx* ctx, const double* qp_d, const double* w_d, const doubl
 /* Solve A^T lam = g at state q, A the Newton operator at (inv_dtau, a0_dt) as in fr_gmres:
  * builds the element blocks and the stored linearisation at q, then restarted GMRES with
  * the configured side, restart and tolerance on A^T, preconditioned by the transposed
- * element blocks B_e^-T (the coarse correction of FR_PRECOND_TWO_LEVEL is not used here).
+ * element blocks B_e^-T, or with FR_PRECOND_TWO_LEVEL by the transposed two-level map
+ * M^-T r = u + P V'(P^T r - (A P)^T u), u = B^-T r, V' the V-cycle on the transposed coarse
+ * operators (those of A^T).
  * lam_d receives the solution (zero initial guess), *iters (host, may be NULL) the
  * iteration count.  Single-case contexts.  Synchronises the stream. */
 int fr_adjoint_solve(fr_ctx* ctx, const double* qp_d, const double* g_d, double inv_dtau,
                      double a0_dt, double* lam_d, int* iters, void* stream);
+/* z = M^-T r with the preconditioner of the last build (the transpose of
+ * fr_precond_apply's map: <y, M^-1 x> = <M^-T y, x>).  Synchronises the stream. */
+int fr_precond_apply_transposed(fr_ctx* ctx, const double* r_d, double* z_d, void* stream);
 /* out = beta out + alpha d(wx F_x + wy F_y)/dq at q (F of fr_wall_force): the weighted
  * tractions differentiated in the wall faces' traces and local gradients (forward mode)
  * and mapped back by the transposed traces and gradients.  beta = 0 ignores out's

@@ -870,16 +870,33 @@ int fr_adjoint_solve(fr_ctx* c, const double* q, const double* g, double inv_dta
   FR_TRY(check_ready(c));
   if (!q || !g || !lam) return FR_ERR_ARG;
   if (c->ncases != 1) { snprintf(c->err, sizeof(c->err), "fr_adjoint_solve: single-case contexts only"); return FR_ERR_ARG; }
-  // the element blocks at q (applied transposed) and the operator's local Jacobians at q
+  // the element blocks at q (applied transposed), the operator's local Jacobians at q and,
+  // with the two-level preconditioner, its hierarchy at q and the transposed hierarchy
   FR_TRY(frk::block_build(c, q, inv_dtau, a0_dt, S(s)));
   c->blocks_ready = 1;
   if (c->cfg.block_mode != FR_BLOCK_LINEARIZED) FR_TRY(frk::linearize(c, q, inv_dtau, a0_dt, S(s)));
+  if (c->cfg.precond == FR_PRECOND_TWO_LEVEL) {
+    FR_TRY(frk::mg_build(c, q, inv_dtau, a0_dt, S(s)));
+    FR_TRY(frk::mg_transpose(c, S(s)));
+  }
   c->transposed = 1;
   int its = 0;
   const int rc = gmres_solve(c, q, g, inv_dtau, a0_dt, lam, &its, S(s));
   c->transposed = 0;
   if (iters) *iters = its;
   return rc;
+}
+
+int fr_precond_apply_transposed(fr_ctx* c, const double* r, double* z, void* s) {
+  FR_TRY(check_ready(c));
+  if (!r || !z) return FR_ERR_ARG;
+  if (!c->blocks_ready) { snprintf(c->err, sizeof(c->err), "no preconditioner built"); return FR_ERR_ARG; }
+  if (c->cfg.precond == FR_PRECOND_TWO_LEVEL && !c->mg_t_ready) FR_TRY(frk::mg_transpose(c, S(s)));
+  c->transposed = 1;
+  const int rc = frk::precond_apply(c, c->mg_q, r, z, c->mg_inv_dtau, c->mg_a0_dt, S(s));
+  c->transposed = 0;
+  FR_TRY(rc);
+  return frk::check_device_waits(c, S(s));
 }
 
 int fr_wall_force_vjp(fr_ctx* c, const double* q, double wx, double wy, double alpha, double beta,

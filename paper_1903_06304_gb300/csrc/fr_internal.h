@@ -82,6 +82,11 @@ struct MgLevel {
   int ntiles = 0;             // tiles of the tiled kernels on this level
   void *tiles = nullptr;      // [ntiles] (case, first column, first row)
   void *cl = nullptr;         // [ncases] each case's grid on this level
+  // the transposed hierarchy (A^T's Galerkin operators are the transposes of A's): the
+  // slot of c in the stencil of each member, and A^T's blocks, diagonal inverses and dense
+  // inverses, built on demand for the adjoint solve
+  int *rslot = nullptr;       // [nc][5]
+  void *AT = nullptr, *DinvT = nullptr, *AinvT = nullptr;
 };
 
 // Input of the block apply fused with the coarse correction (level-0 cells are the
@@ -192,6 +197,8 @@ struct fr_ctx {
   void *mg_ap = nullptr;
   int *mg_bad = nullptr;           // singular coarse blocks met by the builds (device)
   void *mg_views = nullptr;        // device copies of the level views (single-block kernels)
+  void *mg_views_t = nullptr;      // the same for the transposed hierarchy
+  int mg_t_ready = 0;              // the transposed hierarchy matches the last build
   void *mg_tc = nullptr;           // [ncases] per-case level ranges of the single-block kernels
   const double* mg_q = nullptr;    // state of the last build (dual-number operator)
   double mg_inv_dtau = 0.0, mg_a0_dt = 0.0;
@@ -284,6 +291,8 @@ int block_apply_coarse(fr_ctx* c, const double* r, double* z, const CoarseIn& ci
 int mg_setup(fr_ctx* c);
 void mg_free(fr_ctx* c);
 int mg_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s);
+// the transposed hierarchy of the last build (for M^-T in the adjoint solve)
+int mg_transpose(fr_ctx* c, cudaStream_t s);
 int precond_apply(fr_ctx* c, const double* q, const double* r, double* z, double inv_dtau,
                   double a0_dt, cudaStream_t s);
 int linearize(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s);

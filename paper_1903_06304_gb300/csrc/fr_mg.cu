@@ -343,6 +343,80 @@ __global__ void k_p1_restrict(fr::Mesh mesh, fr::Basis B, const double* __restri
   b0[t] = (S)acc;
 }
 
+// ---------------------------------------------------------------- transposed preconditioner
+// M^-1 = B^-1 + (I - B^-1 A) P V P^T with V the V-cycle on A's Galerkin operators, so
+//   M^-T r = u + P V' (P^T r - (A P)^T u),   u = B^-T r,
+// where V' = V^T is the same V-cycle on the transposed operators (the Galerkin operators of
+// A^T are the transposes of A's, and a cycle with equal pre- and post-smoothing by damped
+// block Jacobi transposes into the cycle on the transposed blocks).
+
+// A^T's stencil blocks: block s of cell c is the transpose of block s' of member f = nb(c, s)
+// (s' = the slot of c in f's stencil); diagonal inverses transposed for the smoothed cells.
+template <class S>
+__global__ void k_mg_transpose(Lv<S> L, const int* __restrict__ rslot, S* __restrict__ AT,
+                               S* __restrict__ DinvT) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)L.nc * SL * BLK) return;
+  const int c = (int)(t / (SL * BLK)), s = (int)(t / BLK % SL), ij = (int)(t % BLK);
+  const int i = ij / NB, j = ij % NB;
+  const int f = L.nb[c * SL + s];
+  AT[t] = f >= 0 ? L.A[(((size_t)f * SL + rslot[c * SL + s]) * NB + j) * NB + i] : S(0);
+  if (s == 0 && L.parent[c] >= 0) DinvT[((size_t)c * NB + i) * NB + j] = L.Dinv[((size_t)c * NB + j) * NB + i];
+}
+
+// Dense inverses of the finishing cases, transposed in their (12 m)^2 corner.
+template <class S>
+__global__ void k_mg_transpose_dense(const S* __restrict__ Ainv, const int* __restrict__ fin, int nfin,
+                                     S* __restrict__ AinvT) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)nfin * DN * DN) return;
+  const int f = (int)(t / (DN * DN)), ij = (int)(t % (DN * DN)), i = ij / DN, j = ij % DN;
+  const int m = fin[2 * f + 1] * NB;
+  AinvT[t] = (i < m && j < m) ? Ainv[(size_t)f * DN * DN + (size_t)j * DN + i] : S(0);
+}
+
+// b0 = P^T r - (A P)^T u: row (e, k) sums the P1 projection of r and, over the stencil
+// members g of e, the stored column of e's mode k on g's rows against u on g (FP64 sums).
+template <int N, class S>
+__global__ void k_p1_restrict_t(fr::Mesh mesh, fr::Basis B, const double* __restrict__ r,
+                                const double* __restrict__ u, const S* __restrict__ AP,
+                                const int* __restrict__ nb0, const int* __restrict__ rslot0,
+                                S* __restrict__ b0) {
+  constexpr int NP = N * N, BS = 4 * NP;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)mesh.ne * NB) return;
+  const int e = (int)(t / NB), k = (int)(t % NB), v = k / 3, m = k % 3;
+  const size_t base = mesh.qbase(e, NP), qs = mesh.qstride(e);
+  double acc = 0.0;
+  for (int pt = 0; pt < NP; ++pt) acc = fma(phi(B, m, pt % N, pt / N), r[v * qs + base + pt], acc);
+  for (int jj = 0; jj < SL; ++jj) {
+    const int g = nb0[(size_t)e * SL + jj];
+    if (g < 0) continue;
+    const S* ap = AP + (((size_t)g * SL + rslot0[(size_t)e * SL + jj]) * NB + k) * BS;
+    const size_t gb = mesh.qbase(g, NP), gs = mesh.qstride(g);
+    for (int row = 0; row < BS; ++row) acc = fma(-(double)ap[row], u[(row / NP) * gs + gb + row % NP], acc);
+  }
+  b0[t] = (S)acc;
+}
+
+// z = u + P y0 (FP64 out)
+template <int N, class S>
+__global__ void k_p1_prolong_add(fr::Mesh mesh, fr::Basis B, const S* __restrict__ y0,
+                                 const double* __restrict__ u, double* __restrict__ z) {
+  constexpr int NP = N * N;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)mesh.ne * NP) return;
+  const int e = (int)(t / NP), pt = (int)(t % NP);
+  const size_t base = mesh.qbase(e, NP), qs = mesh.qstride(e);
+  const double xi = B.xs[pt % N], eta = B.xs[pt / N];
+  const S* c = y0 + (size_t)e * NB;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const size_t gi = v * qs + base + pt;
+    z[gi] = u[gi] + fma((double)c[3 * v + 2], eta, fma((double)c[3 * v + 1], xi, (double)c[3 * v]));
+  }
+}
+
 // ---------------------------------------------------------------- multi-block levels
 // A level of a case with more than TAIL cells (and at least 3 in each direction, so that a
 // cell's four neighbours are distinct) runs in tiles of TX x TX cells, one block per tile
@@ -889,8 +963,9 @@ int op_apply(fr_ctx* c, const double* q, const double* x, double inv_dtau, doubl
   return frk::jvp(c, q, x, inv_dtau, a0_dt, out, s);
 }
 
+// The level as the kernels see it: A's operators, or with tr the transposed hierarchy's.
 template <class S>
-Lv<S> view(const MgLevel& l) {
+Lv<S> view(const MgLevel& l, bool tr = false) {
   Lv<S> v;
   v.nc = l.nc;
   v.nb = l.nb;
@@ -898,12 +973,12 @@ Lv<S> view(const MgLevel& l) {
   v.parent = l.parent;
   v.children = l.children;
   v.qo = l.qo;
-  v.A = (const S*)l.A;
-  v.Dinv = (const S*)l.Dinv;
+  v.A = (const S*)(tr ? l.AT : l.A);
+  v.Dinv = (const S*)(tr ? l.DinvT : l.Dinv);
   v.x = (S*)l.x;
   v.y = (S*)l.y;
   v.b = (S*)l.b;
-  v.Ainv = (const S*)l.Ainv;
+  v.Ainv = (const S*)(tr ? l.AinvT : l.Ainv);
   return v;
 }
 
@@ -1006,9 +1081,9 @@ int fine_restrict(fr_ctx* c, const double* r, cudaStream_t s) {
 }
 
 template <class S>
-int launch_tail(fr_ctx* c, const MgLevel& L, cudaStream_t s) {
+int launch_tail(fr_ctx* c, const MgLevel& L, cudaStream_t s, bool tr) {
   FR_PROF_BEGIN(c, s);
-  k_mg_tail<S><<<L.ntail, TAIL_THREADS, 0, s>>>((const Lv<S>*)c->mg_views, (const TailCase*)c->mg_tc,
+  k_mg_tail<S><<<L.ntail, TAIL_THREADS, 0, s>>>((const Lv<S>*)(tr ? c->mg_views_t : c->mg_views), (const TailCase*)c->mg_tc,
                                                  L.tail, c->cfg.mg_sweeps, (S)c->cfg.mg_omega);
   FR_PROF_END(c, s, KK_COARSE);
   FR_LAUNCH_CHECK(c);
@@ -1019,13 +1094,13 @@ int launch_tail(fr_ctx* c, const MgLevel& L, cudaStream_t s) {
 // the down pass (and the tails of the cases whose single-block part starts below it), then
 // the up passes in reverse order; every level's result ends in y.
 template <class S, int NU>
-int vcycle_n(fr_ctx* c, cudaStream_t s) {
+int vcycle_n(fr_ctx* c, cudaStream_t s, bool tr) {
   const S om = (S)c->cfg.mg_omega;
   if (tile_smem<S, NU>() > 48 * 1024) {
     FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_mg_down<S, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<S, NU>()));
     FR_CUDA_CHECK(c, cudaFuncSetAttribute(k_mg_up<S, NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<S, NU>()));
   }
-  if (c->mg[0].ntail > 0) FR_TRY(launch_tail<S>(c, c->mg[0], s));
+  if (c->mg[0].ntail > 0) FR_TRY(launch_tail<S>(c, c->mg[0], s, tr));
   size_t ltop = 0;
   while (ltop < c->mg.size() && c->mg[ltop].ntiles > 0) ++ltop;
   for (size_t l = 0; l < ltop; ++l) {
@@ -1033,17 +1108,17 @@ int vcycle_n(fr_ctx* c, cudaStream_t s) {
     MgLevel& Nx = c->mg[l + 1];
     {
       FR_PROF_BEGIN(c, s);
-      k_mg_down<S, NU><<<L.ntiles, (TX + 2 * NU) * (TX + 2 * NU) * NB, tile_smem<S, NU>(), s>>>(view<S>(L), (const CaseLevel*)L.cl, (const Tile*)L.tiles, om, (S*)Nx.b);
+      k_mg_down<S, NU><<<L.ntiles, (TX + 2 * NU) * (TX + 2 * NU) * NB, tile_smem<S, NU>(), s>>>(view<S>(L, tr), (const CaseLevel*)L.cl, (const Tile*)L.tiles, om, (S*)Nx.b);
       FR_PROF_END(c, s, KK_COARSE);
       FR_LAUNCH_CHECK(c);
     }
-    if (Nx.ntail > 0) FR_TRY(launch_tail<S>(c, Nx, s));
+    if (Nx.ntail > 0) FR_TRY(launch_tail<S>(c, Nx, s, tr));
   }
   for (size_t l = ltop; l-- > 0;) {
     MgLevel& L = c->mg[l];
     MgLevel& Nx = c->mg[l + 1];
     FR_PROF_BEGIN(c, s);
-    k_mg_up<S, NU><<<L.ntiles, (TX + 2 * NU) * (TX + 2 * NU) * NB, tile_smem<S, NU>(), s>>>(view<S>(L), (const CaseLevel*)L.cl, (const Tile*)L.tiles, om, (const S*)Nx.y);
+    k_mg_up<S, NU><<<L.ntiles, (TX + 2 * NU) * (TX + 2 * NU) * NB, tile_smem<S, NU>(), s>>>(view<S>(L, tr), (const CaseLevel*)L.cl, (const Tile*)L.tiles, om, (const S*)Nx.y);
     FR_PROF_END(c, s, KK_COARSE);
     FR_LAUNCH_CHECK(c);
   }
@@ -1058,8 +1133,8 @@ int vcycle_n(fr_ctx* c, cudaStream_t s) {
 }
 
 template <class S>
-int vcycle(fr_ctx* c, cudaStream_t s) {
-  return c->cfg.mg_sweeps == 1 ? vcycle_n<S, 1>(c, s) : vcycle_n<S, 2>(c, s);
+int vcycle(fr_ctx* c, cudaStream_t s, bool tr = false) {
+  return c->cfg.mg_sweeps == 1 ? vcycle_n<S, 1>(c, s, tr) : vcycle_n<S, 2>(c, s, tr);
 }
 
 template <class S>
@@ -1085,6 +1160,71 @@ int apply_t(fr_ctx* c, const double* q, const double* r, double* z, double inv_d
   return frk::block_apply_coarse(c, r, z, ci, sizeof(S) == sizeof(float) ? 1 : 2, s);
 }
 
+// z = M^-T r: u = B^-T r, b0 = P^T r - (A P)^T u, the cycle on the transposed hierarchy,
+// z = u + P y0 (the transposed hierarchy built by mg_transpose for this build)
+template <int N, class S>
+int apply_tr_n(fr_ctx* c, const double* r, double* z, cudaStream_t s) {
+  constexpr int NP = N * N;
+  double* u = c->mg_x;
+  FR_TRY(frk::block_apply(c, r, u, s));   // c->transposed: B^-T
+  MgLevel& L0 = c->mg[0];
+  {
+    FR_PROF_BEGIN(c, s);
+    k_p1_restrict_t<N, S><<<blocks_for((long long)c->ne * NB, 256), 256, 0, s>>>(
+        c->mesh, c->basis, r, u, (const S*)c->mg_ap, L0.nb, L0.rslot, (S*)L0.b);
+    FR_PROF_END(c, s, KK_COARSE);
+    FR_LAUNCH_CHECK(c);
+  }
+  FR_TRY(vcycle<S>(c, s, true));
+  {
+    FR_PROF_BEGIN(c, s);
+    k_p1_prolong_add<N, S><<<blocks_for((long long)c->ne * NP, 256), 256, 0, s>>>(c->mesh, c->basis,
+                                                                                (const S*)L0.y, u, z);
+    FR_PROF_END(c, s, KK_COARSE);
+    FR_LAUNCH_CHECK(c);
+  }
+  return FR_OK;
+}
+
+template <class S>
+int apply_tr(fr_ctx* c, const double* r, double* z, cudaStream_t s) {
+  switch (c->n) {
+    case 2: return apply_tr_n<2, S>(c, r, z, s);
+    case 3: return apply_tr_n<3, S>(c, r, z, s);
+    case 4: return apply_tr_n<4, S>(c, r, z, s);
+    case 5: return apply_tr_n<5, S>(c, r, z, s);
+  }
+  return FR_ERR_ARG;
+}
+
+template <class S>
+int transpose_levels(fr_ctx* c, cudaStream_t s) {
+  std::vector<Lv<S>> views;
+  for (MgLevel& L : c->mg) {
+    const size_t esz = sizeof(S), n12 = (size_t)L.nc * NB;
+    if (!L.AT) FR_CUDA_CHECK(c, cudaMalloc(&L.AT, n12 * SL * NB * esz));
+    if (!L.DinvT) {
+      FR_CUDA_CHECK(c, cudaMalloc(&L.DinvT, n12 * NB * esz));
+      FR_CUDA_CHECK(c, cudaMemset(L.DinvT, 0, n12 * NB * esz));
+    }
+    if (L.nfin > 0 && !L.AinvT) FR_CUDA_CHECK(c, cudaMalloc(&L.AinvT, (size_t)L.nfin * DN * DN * esz));
+    FR_PROF_BEGIN(c, s);
+    k_mg_transpose<S><<<blocks_for((long long)L.nc * SL * BLK, 256), 256, 0, s>>>(view<S>(L), L.rslot,
+                                                                                 (S*)L.AT, (S*)L.DinvT);
+    if (L.nfin > 0)
+      k_mg_transpose_dense<S><<<blocks_for((long long)L.nfin * DN * DN, 256), 256, 0, s>>>(
+          (const S*)L.Ainv, L.fin, L.nfin, (S*)L.AinvT);
+    FR_PROF_END(c, s, KK_COARSE);
+    FR_LAUNCH_CHECK(c);
+    views.push_back(view<S>(L, true));
+  }
+  FR_CUDA_CHECK(c, cudaMemcpyAsync(c->mg_views_t, views.data(), views.size() * sizeof(Lv<S>),
+                                   cudaMemcpyHostToDevice, s));
+  FR_CUDA_CHECK(c, cudaStreamSynchronize(s));   // views is a host temporary
+  c->mg_t_ready = 1;
+  return FR_OK;
+}
+
 template <class S>
 int upload_views(fr_ctx* c) {
   std::vector<Lv<S>> views;
@@ -1099,9 +1239,9 @@ namespace frk {
 
 void mg_free(fr_ctx* c) {
   for (MgLevel& l : c->mg) {
-    int* is[] = {l.nb, l.cell_case, l.parent, l.children, l.gslot, l.fin, l.mode, l.tail};
+    int* is[] = {l.nb, l.cell_case, l.parent, l.children, l.gslot, l.fin, l.mode, l.tail, l.rslot};
     for (int* p : is) if (p) cudaFree(p);
-    void* vs[] = {l.A, l.Dinv, l.x, l.y, l.b, l.Ainv, l.tiles, l.cl};
+    void* vs[] = {l.A, l.Dinv, l.x, l.y, l.b, l.Ainv, l.tiles, l.cl, l.AT, l.DinvT, l.AinvT};
     for (void* p : vs) if (p) cudaFree(p);
     if (l.qo) cudaFree(l.qo);
   }
@@ -1112,6 +1252,8 @@ void mg_free(fr_ctx* c) {
   if (c->mg_ap) { cudaFree(c->mg_ap); c->mg_ap = nullptr; }
   if (c->mg_bad) { cudaFree(c->mg_bad); c->mg_bad = nullptr; }
   if (c->mg_views) { cudaFree(c->mg_views); c->mg_views = nullptr; }
+  if (c->mg_views_t) { cudaFree(c->mg_views_t); c->mg_views_t = nullptr; }
+  c->mg_t_ready = 0;
   if (c->mg_tc) { cudaFree(c->mg_tc); c->mg_tc = nullptr; }
   c->mg_ncol = 0;
   c->mg_q = nullptr;
@@ -1255,6 +1397,22 @@ int mg_setup(fr_ctx* c) {
     L.ntail = (int)h_tail[l].size();
     L.nsweep = h_nsweep[l];
     FR_TRY(upload(c, &L.nb, h_nb[l]));
+    {
+      // the slot of each cell in the stencil of each of its members
+      std::vector<int> rs(h_nb[l].size(), -1);
+      for (int cell = 0; cell < (int)h_case[l].size(); ++cell)
+        for (int s2 = 0; s2 < SL; ++s2) {
+          const int f = h_nb[l][(size_t)cell * SL + s2];
+          if (f < 0) continue;
+          for (int t = 0; t < SL; ++t)
+            if (h_nb[l][(size_t)f * SL + t] == cell) rs[(size_t)cell * SL + s2] = t;
+          if (rs[(size_t)cell * SL + s2] < 0) {
+            snprintf(c->err, sizeof(c->err), "two-level set-up: stencils not symmetric");
+            return FR_ERR_ARG;
+          }
+        }
+      FR_TRY(upload(c, &L.rslot, rs));
+    }
     FR_TRY(upload(c, &L.cell_case, h_case[l]));
     FR_TRY(upload(c, &L.parent, h_parent[l]));
     FR_TRY(upload(c, &L.gslot, h_gslot[l]));
@@ -1282,6 +1440,7 @@ int mg_setup(fr_ctx* c) {
   FR_CUDA_CHECK(c, cudaMalloc(&c->mg_tc, tcs.size() * sizeof(TailCase)));
   FR_CUDA_CHECK(c, cudaMemcpy(c->mg_tc, tcs.data(), tcs.size() * sizeof(TailCase), cudaMemcpyHostToDevice));
   FR_CUDA_CHECK(c, cudaMalloc(&c->mg_views, nlev * std::max(sizeof(Lv<double>), sizeof(Lv<float>))));
+  FR_CUDA_CHECK(c, cudaMalloc(&c->mg_views_t, nlev * std::max(sizeof(Lv<double>), sizeof(Lv<float>))));
   FR_TRY(f64 ? upload_views<double>(c) : upload_views<float>(c));
   // level 0: greedy colouring in which no stencil holds two members of one colour
   const int ne = c->ne;
@@ -1328,6 +1487,7 @@ int mg_setup(fr_ctx* c) {
 
 int mg_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStream_t s) {
   if (c->cfg.precond != FR_PRECOND_TWO_LEVEL) return FR_OK;
+  c->mg_t_ready = 0;
   if (c->mg.empty()) { snprintf(c->err, sizeof(c->err), "two-level preconditioner not set up"); return FR_ERR_ARG; }
   c->mg_q = q;
   c->mg_inv_dtau = inv_dtau;
@@ -1349,10 +1509,20 @@ int mg_build(fr_ctx* c, const double* q, double inv_dtau, double a0_dt, cudaStre
   return f64 ? build_levels<double>(c, s) : build_levels<float>(c, s);
 }
 
+int mg_transpose(fr_ctx* c, cudaStream_t s) {
+  if (c->cfg.precond != FR_PRECOND_TWO_LEVEL || c->mg.empty()) return FR_OK;
+  return c->cfg.mg_prec == FR_PREC_FP64 ? transpose_levels<double>(c, s) : transpose_levels<float>(c, s);
+}
+
 int precond_apply(fr_ctx* c, const double* q, const double* r, double* z, double inv_dtau,
                   double a0_dt, cudaStream_t s) {
-  // the adjoint solve (A^T) takes the transposed element blocks alone
-  if (c->cfg.precond != FR_PRECOND_TWO_LEVEL || c->transposed) return block_apply(c, r, z, s);
+  if (c->cfg.precond != FR_PRECOND_TWO_LEVEL) return block_apply(c, r, z, s);
+  if (c->transposed) {
+    // M^-T with the transposed hierarchy of the last build, else the transposed blocks alone
+    if (!c->mg_t_ready) return block_apply(c, r, z, s);
+    if (c->cfg.mg_prec == FR_PREC_FP64) return apply_tr<double>(c, r, z, s);
+    return apply_tr<float>(c, r, z, s);
+  }
   if (c->cfg.mg_prec == FR_PREC_FP64) return apply_t<double>(c, q, r, z, inv_dtau, a0_dt, s);
   return apply_t<float>(c, q, r, z, inv_dtau, a0_dt, s);
 }

@@ -113,6 +113,7 @@ _SIGS = {
     "fr_param_jvp": (_I, [_P, _P, _P, _P, _P, _P, _P, _D, ctypes.POINTER(_D), ctypes.POINTER(_D),
                           ctypes.POINTER(_D), _P]),
     "fr_adjoint_solve": (_I, [_P, _P, _P, _D, _D, _P, ctypes.POINTER(_I), _P]),
+    "fr_precond_apply_transposed": (_I, [_P, _P, _P, _P]),
     "fr_wall_force_vjp": (_I, [_P, _P, _D, _D, _D, _D, _P, _P]),
     "fr_conservative_vjp": (_I, [_P, _P, _P, _D, _D, _P, _P]),
     "fr_conservative_dmach": (_I, [_P, _P, _P, ctypes.POINTER(_D), _P]),
@@ -493,6 +494,11 @@ class Solver:
         self._check(self.lib.fr_adjoint_solve(self.ctx, _ptr(q), _ptr(g), inv_dtau, a0_dt,
                                               _ptr(lam), ctypes.byref(its), _stream(stream)))
         return its.value
+
+    def precond_apply_transposed(self, r, out, stream=None):
+        """out = M^-T r with the preconditioner of the last build."""
+        self._check(self.lib.fr_precond_apply_transposed(self.ctx, _ptr(r), _ptr(out), _stream(stream)))
+        return out
 
     def wall_force_vjp(self, q, wx, wy, out, alpha=1.0, beta=0.0, stream=None):
         """out = beta out + alpha d(wx F_x + wy F_y)/dq."""

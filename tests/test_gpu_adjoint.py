@@ -142,8 +142,9 @@ def test_param_jvp_matches_complex_step(torch, which):
     assert np.all(np.abs(np.array(F) - want_F) <= 1e-11 * fscale), (F, want_F)
 
 
+@pytest.mark.parametrize("precond", ["block", "twolevel"])
 @pytest.mark.parametrize("side", ["left", "right"])
-def test_adjoint_solve_matches_dense_transpose(torch, side):
+def test_adjoint_solve_matches_dense_transpose(torch, side, precond):
     case = plunge_case(None)
     q = perturbed_state(rel=0.05)
     prob = ad.problem(case, 0.4, H, MACH)
@@ -151,7 +152,7 @@ def test_adjoint_solve_matches_dense_transpose(torch, side):
     A = sv.dense_operator(prob, q, 0.0, a0_dt)
     g = inp.random_vector(q.shape, 10)
     want = np.linalg.solve(A.T, g.ravel()).reshape(q.shape)
-    S = solver(gmres_side=side)
+    S = solver(gmres_side=side, precond=precond, mg_prec="fp64")
     c, v, _, _ = mesh_at(case, 0.4, H)
     S.update_mesh(to_dev(c), to_dev(v))
     lam = torch.empty(S.shape, dtype=torch.float64, device="cuda:0")
@@ -197,14 +198,16 @@ def gpu_reverse_sweep(torch, S, case, qs, h, mach):
     return grad, its
 
 
-def test_adjoint_sweep_matches_oracle_adjoint(torch):
+@pytest.mark.parametrize("precond", ["block", "twolevel"])
+def test_adjoint_sweep_matches_oracle_adjoint(torch, precond):
     """On the oracle's converged states, the device sweep reproduces the oracle's
-    d(mean C_t)/dh and d(mean C_t)/dM."""
+    d(mean C_t)/dh and d(mean C_t)/dM, with the transposed element blocks or the
+    transposed two-level preconditioner in the adjoint solves."""
     q0 = inp.random_perturbation(inp.uniform_state(NI * NJ, P, MACH), 3, 0.01, MACH)
     case = plunge_case(q0)
     J, gh, gm = ad.adjoint_gradient(case, H, MACH)
     qs = [to_dev(x) for x in ad.march(case, H, MACH)]
-    S = solver()
+    S = solver(precond=precond, mg_prec="fp64")
     grad, its = gpu_reverse_sweep(torch, S, case, qs, H, MACH)
     assert all(i > 0 for i in its)
     assert abs(grad[0] - gh) <= 1e-9 * abs(gh), (grad[0], gh)

@@ -276,3 +276,37 @@ def test_local_galerkin_build_equals_operator_products(torch, cfg, bounded):
         S.close()
     err = np.abs(outs[1] - outs[0]).max() / np.abs(outs[0]).max()
     assert err <= APPLY_TOL, err
+
+
+@pytest.mark.parametrize("cfg", APPLY_CASES)
+@pytest.mark.parametrize("bounded", [False, True])
+def test_transposed_two_level_is_the_transpose(torch, cfg, bounded):
+    """<y, M^-1 x> = <M^-T y, x>: the transposed map (transposed blocks, the transposed
+    coarse hierarchy and the transposed smoothing step) against the forward one, FP64
+    blocks and coarse levels."""
+    from paper_1903_06304_gb300 import fr
+    nx, ny, p, mach, re, kappa, deforming = cfg
+    inv_dtau, a0_dt = 0.3, 150.0
+    kw = dict(p=p, mach=mach, re=re, kappa=kappa, precond="twolevel", mg_prec="fp64", prec="fp64")
+    if bounded:
+        nx, ny = max(nx, 4), max(ny, 3)
+        c, v = inp.plunge(inp.naca_ogrid(nx, ny, first=0.05), 0.3)
+        q = inp.random_perturbation(inp.uniform_state(nx * ny, p, mach), 5, 0.02, mach)
+        S = fr.Solver(fr.Config(**kw), nx, ny, bc=("wall", "farfield"), q_inf=inp.far_field_state(mach))
+    else:
+        c, v, q = case(nx, ny, p, mach, re, kappa, deforming)
+        S = fr.Solver(fr.Config(**kw), nx, ny)
+    S.update_mesh(to_dev(c), to_dev(v))
+    S.precond_build(to_dev(q), inv_dtau, a0_dt)
+    rng = np.random.default_rng(41)
+    for _ in range(2):
+        x = to_dev(rng.standard_normal(q.shape))
+        y = to_dev(rng.standard_normal(q.shape))
+        Mx = torch.empty_like(x)
+        MTy = torch.empty_like(x)
+        S.precond_apply(x, Mx)
+        S.precond_apply_transposed(y, MTy)
+        lhs, rhs = float((y * Mx).sum()), float((MTy * x).sum())
+        scale = float((y.abs() * Mx.abs()).sum())
+        assert abs(lhs - rhs) <= 1e-11 * scale, (lhs, rhs, scale)
+    S.close()
