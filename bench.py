@@ -566,6 +566,114 @@ def plunge_march_report(args, torch, fr, inp, T):
     return out
 
 
+def plunge_adjoint_report(args, torch, fr, inp, T):
+    """The discrete adjoint of the plunging-airfoil march (Sec. 3.2 march, Sec. 4.4 plunge):
+    J = mean C_t over the first ``--adjoint-steps`` BDF steps of the ``--plunge-grid``
+    O-grid at M = 0.2 (the configuration of ``plunging_naca``), its gradient in the plunge
+    amplitude h and the Mach number by one reverse sweep (per step the wall-force
+    gradient, the BDF coupling to the next two steps, the transposed GMRES solve with the
+    transposed two-level preconditioner, and the parameter directional derivatives), timed
+    against the forward march, and central differences of the whole march (h +- 1e-3 h,
+    M +- 1e-3 M, the initial state held at the nominal free stream as in the adjoint's
+    definition) as a check."""
+    import math
+    ni, nj = (int(x) for x in args.plunge_grid.split("x"))
+    p, re, kappa, h, k, mach = 3, 1e4, 5 ** 0.5, 0.25, 1.0, 0.2
+    dt = 2 * math.pi / k / 200
+    K = args.adjoint_steps
+    ref = inp.naca_ogrid(ni, nj)
+
+    def mesh_at(t, hh):
+        c1, v1 = inp.plunge(ref, t, 1.0, k)
+        return ref + hh * (c1 - ref), hh * v1, c1 - ref, v1
+
+    def solver(m, maxit_lin=100):
+        cfg = fr.Config(p=p, mach=m, re=re, kappa=kappa, precond="twolevel", prec=args.prec,
+                        mg_prec="fp64", restart=100, maxit_lin=maxit_lin, tol_res=1e-6,
+                        tol_pseudo=1e-8, maxit_newton=20, graphs=args.graphs)
+        return fr.Solver(cfg, ni, nj, bc=("wall", "farfield"), q_inf=inp.far_field_state(m))
+
+    q_start = inp.uniform_state(ni * nj, p, mach)   # the nominal free stream, fixed
+
+    def march(S, hh, m):
+        c0, v0, _, _ = mesh_at(0.0, hh)
+        S.update_mesh(T(c0), T(v0))
+        q = T(q_start)
+        qn = torch.empty_like(q)
+        S.conservative(q, qn)
+        qm = qn.clone()
+        qs, J, conv = [q.clone()], 0.0, True
+        for n in range(1, K + 1):
+            c1, v1, _, _ = mesh_at(n * dt, hh)
+            S.update_mesh(T(c1), T(v1))
+            st = S.bdf2_step(q, qn, qm, dt, coeffs=fr.BDF1 if n == 1 else fr.BDF2,
+                             allow_unconverged=True).summary()
+            conv = conv and st["converged"]
+            qm.copy_(qn)
+            S.conservative(q, qn)
+            qs.append(q.clone())
+            J += -2.0 * S.wall_force(q)[0] / K
+        return qs, J, conv
+
+    coeffs = lambda n: fr.BDF1 if n == 1 else fr.BDF2
+    S = solver(mach)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    qs, J, conv = march(S, h, mach)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    S.close()
+    S = solver(mach, maxit_lin=400)   # the adjoint solves: one linear system per step
+    # reverse sweep
+    wx = -2.0 / K
+    dq_inf = (-2.0 / (inp.GAMMA * mach ** 3), 0.0, 0.0, 0.0)
+    lam = [None] * (K + 3)
+    grad = [0.0, 0.0]
+    its = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for n in range(K, 0, -1):
+        c, v, dc, dv = mesh_at(n * dt, h)
+        cd, vd = T(c), T(v)
+        S.update_mesh(cd, vd)
+        g = torch.empty_like(qs[n])
+        S.wall_force_vjp(qs[n], wx, 0.0, g)
+        for m_, kk in ((n + 1, 1), (n + 2, 2)):
+            if m_ <= K and coeffs(m_)[kk] != 0.0:
+                S.conservative_vjp(qs[n], lam[m_], g, alpha=-coeffs(m_)[kk] / dt, beta=1.0)
+        lam[n] = torch.empty_like(g)
+        its.append(S.adjoint_solve(qs[n], g, lam[n], 0.0, coeffs(n)[0] / dt))
+        wRh, Fh = S.param_jvp(qs[n], cd, vd, dcorners=T(dc), dvel=T(dv), w=lam[n], force=True)
+        wRm, Fm = S.param_jvp(qs[n], cd, vd, dmach=1.0, dqinf=dq_inf, w=lam[n], force=True)
+        grad[0] += wRh + wx * Fh[0]
+        grad[1] += wRm + wx * Fm[0]
+        for j, a in enumerate(coeffs(n)):
+            if a != 0.0:
+                grad[1] -= a / dt * S.conservative_dmach(qs[n - j], lam[n])
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    S.close()
+    # central differences of the whole march
+    eh, em = 1e-3 * h, 1e-3 * mach
+    S = solver(mach)
+    jh = [march(S, h + s * eh, mach)[1] for s in (1, -1)]
+    S.close()
+    jm = []
+    for s in (1, -1):
+        Sm = solver(mach + s * em)
+        jm.append(march(Sm, h, mach + s * em)[1])
+        Sm.close()
+    fd = [(jh[0] - jh[1]) / (2 * eh), (jm[0] - jm[1]) / (2 * em)]
+    return {"workload": f"naca0012_ogrid_{ni}x{nj}_p{p} plunge M={mach} h={h} k={k} dt=T/200",
+            "steps": K, "J_mean_c_t": J, "forward_converged": conv,
+            "dJ_dh": grad[0], "dJ_dM": grad[1], "fd_dJ_dh": fd[0], "fd_dJ_dM": fd[1],
+            "rel_diff_h": abs(grad[0] - fd[0]) / max(abs(fd[0]), 1e-300),
+            "rel_diff_M": abs(grad[1] - fd[1]) / max(abs(fd[1]), 1e-300),
+            "sec_forward": t_fwd, "sec_reverse": t_adj, "adjoint_gmres_per_step": its[::-1],
+            "note": "the differences carry the march's Newton tolerance (1e-8) over the step "
+                    "1e-3 of the parameter, and the adjoint's GMRES tolerance (1e-6)"}
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -853,6 +961,9 @@ def gpu_arm(args):
     plunge = None
     if rank == 0 and not args.no_plunge:
         plunge = plunge_march_report(args, torch, fr, inp, T)
+    adjoint = None
+    if rank == 0 and not args.no_adjoint:
+        adjoint = plunge_adjoint_report(args, torch, fr, inp, T)
 
     # ---- CPU baseline (rank 0, N = 1 only): the oracle's unit costs priced with the
     # timed steps' own counts
@@ -914,6 +1025,7 @@ def gpu_arm(args):
         "low_mach_deforming": low_mach,
         "steady_ptc_cylinder": ptc,
         "plunging_naca": plunge,
+        "plunging_adjoint": adjoint,
         "kernels": kernels,
         "kernels_same_steps": same_steps,
         "roofline": roof,
@@ -1111,6 +1223,9 @@ def main():
     ap.add_argument("--plunge-mach", dest="plunge_mach", type=lambda t: [float(x) for x in t.split(",")],
                     default=[0.05, 0.1, 0.2, 0.3])
     ap.add_argument("--plunge-grid", dest="plunge_grid", default="256x96")
+    ap.add_argument("--no-adjoint", dest="no_adjoint", action="store_true",
+                    help="skip the plunging march's discrete adjoint")
+    ap.add_argument("--adjoint-steps", dest="adjoint_steps", type=int, default=4)
     ap.add_argument("--c3-steps", dest="c3_steps", type=int, default=3)
     ap.add_argument("--c3-newton", dest="c3_newton", type=int, default=10)
     ap.add_argument("--restart", type=int, default=30)
