@@ -420,7 +420,7 @@ def low_mach_deforming_report(args, torch, fr, inp, T, flush):
         prec = "bf16" if prec == "bf16_tc" else prec
         S = fr.Solver(fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=prec, factor=factor,
                                 precond=precond, maxit_newton=args.c3_newton, restart=args.restart,
-                                maxit_lin=args.maxit_lin, graphs=args.graphs, tiles=tiles,
+                                maxit_lin=args.maxit_lin, graphs=args.graphs, arnoldi_fused=args.arnoldi_fused, tiles=tiles,
                                 apply_accum=args.apply_accum), w.nx, w.ny)
         S.dt = w.dt
         S.update_mesh(T(c0), T(v0))
@@ -523,7 +523,7 @@ def plunge_march_report(args, torch, fr, inp, T):
         # Newton updates drive T negative within two iterations
         cfg = fr.Config(p=p, mach=mach, re=re, kappa=kappa, precond=args.precond, prec=args.prec,
                         mg_prec="fp64", restart=100, maxit_lin=100, tol_res=1e-6, tol_pseudo=1e-8,
-                        maxit_newton=20, graphs=args.graphs)
+                        maxit_newton=20, graphs=args.graphs, arnoldi_fused=args.arnoldi_fused)
         S = fr.Solver(cfg, ni, nj, bc=("wall", "farfield"), q_inf=qi)
         c0, v0 = inp.plunge(ref, 0.0, h, k)
         S.update_mesh(T(c0), T(v0))
@@ -590,7 +590,7 @@ def plunge_adjoint_report(args, torch, fr, inp, T):
     def solver(m, maxit_lin=100):
         cfg = fr.Config(p=p, mach=m, re=re, kappa=kappa, precond="twolevel", prec=args.prec,
                         mg_prec="fp64", restart=100, maxit_lin=maxit_lin, tol_res=1e-6,
-                        tol_pseudo=1e-8, maxit_newton=20, graphs=args.graphs)
+                        tol_pseudo=1e-8, maxit_newton=20, graphs=args.graphs, arnoldi_fused=args.arnoldi_fused)
         return fr.Solver(cfg, ni, nj, bc=("wall", "farfield"), q_inf=inp.far_field_state(m))
 
     q_start = inp.uniform_state(ni * nj, p, mach)   # the nominal free stream, fixed
@@ -706,7 +706,7 @@ def gpu_arm(args):
         cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=prec, factor=factor,
                         restart=args.restart, maxit_lin=args.maxit_lin, tol_res=w.tol_res,
                         tol_pseudo=w.tol_pseudo, maxit_newton=args.maxit_newton, lag=2,
-                        line_search=args.line_search, graphs=args.graphs,
+                        line_search=args.line_search, graphs=args.graphs, arnoldi_fused=args.arnoldi_fused,
                         apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog,
                         krylov_arith=arith or args.krylov_arith, precond=precond or args.precond,
                         mg_prec=args.mg_prec, mg_sweeps=args.mg_sweeps, mg_omega=args.mg_omega)
@@ -888,7 +888,7 @@ def gpu_arm(args):
     gm = {}
     for precond in ("block", "twolevel"):
         gm_cfg = fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
-                           restart=args.restart, maxit_lin=120, tol_res=1e-30, graphs=args.graphs,
+                           restart=args.restart, maxit_lin=120, tol_res=1e-30, graphs=args.graphs, arnoldi_fused=args.arnoldi_fused,
                            apply_accum=args.apply_accum, tiles=args.tiles, orthog=args.orthog,
                            krylov_arith=args.krylov_arith, precond=precond, mg_prec=args.mg_prec,
                            mg_sweeps=args.mg_sweeps, mg_omega=args.mg_omega)
@@ -994,7 +994,8 @@ def gpu_arm(args):
                    "p": w.p, "dof": dof, "mach": w.mach, "re_ref": w.re, "kappa": w.kappa,
                    "dt": w.dt, "tol_pseudo": w.tol_pseudo, "tol_res": w.tol_res,
                    "gmres": f"GMRES({args.restart}) left-preconditioned, {args.orthog}, "
-                            f"{args.krylov_arith} basis, maxit {args.maxit_lin}",
+                            f"{args.krylov_arith} basis, maxit {args.maxit_lin}, "
+                            + ("fused Arnoldi step" if args.arnoldi_fused else "split Arnoldi passes"),
                    "newton": f"max {args.maxit_newton} iterations, backtracking {args.line_search} halvings",
                    "precond": f"{args.precond} ({args.prec} element blocks, {args.apply_accum} apply accumulation"
                               + (f", {args.mg_prec} coarse levels, {args.mg_sweeps} sweep(s) of"
@@ -1054,7 +1055,7 @@ def kernels_only(args):
     T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda:0")
     S = fr.Solver(fr.Config(p=w.p, mach=w.mach, re=w.re, kappa=w.kappa, prec=args.prec,
                             factor=args.factor, restart=args.restart, maxit_lin=args.maxit_lin,
-                            precond=args.precond, graphs=args.graphs), w.nx, w.ny)
+                            precond=args.precond, graphs=args.graphs, arnoldi_fused=args.arnoldi_fused), w.nx, w.ny)
     S.update_mesh(T(c), T(v))
     qd = T(q)
     out = torch.empty_like(qd)
@@ -1104,7 +1105,7 @@ def batch_arm(args):
     cases = [fr.Case(c.p, c.n, c.n, c.mach, c.re, c.kappa) for c in cs]
     cfg = fr.Config(prec=args.prec, restart=args.restart, maxit_lin=args.maxit_lin,
                     maxit_newton=args.maxit_newton, lag=2, line_search=args.line_search,
-                    graphs=args.graphs, apply_accum=args.apply_accum,
+                    graphs=args.graphs, arnoldi_fused=args.arnoldi_fused, apply_accum=args.apply_accum,
                     krylov_arith=args.krylov_arith, precond=args.precond, mg_prec=args.mg_prec)
     B = fr.Batch(cfg, cases)
     corners = np.zeros((B.ne, 4, 2))
@@ -1209,6 +1210,9 @@ def main():
     ap.add_argument("--mg-omega", dest="mg_omega", type=float, default=0.8,
                     help="damping of the coarse block-Jacobi sweeps (0.8: the fastest of "
                          "0.7 .. 1.0 with 1 or 2 sweeps on the benchmark workload)")
+    ap.add_argument("--arnoldi-fused", dest="arnoldi_fused", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="each Arnoldi step in one launch with bounded barriers (1: part size "
+                         "chosen by occupancy; 2, 4: pairs per thread) or as split passes (0)")
     ap.add_argument("--precond", default="twolevel", choices=["block", "twolevel"],
                     help="element block Jacobi, or with the P1 coarse correction")
     ap.add_argument("--no-c3", dest="no_c3", action="store_true",

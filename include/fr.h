@@ -136,7 +136,16 @@ typedef struct fr_ctx fr_ctx;
  * (4,194,304 potentially blocking tries), k > 0 = k tries, k < 0 = one non-blocking test
  * (a diagnostic setting under which a wait all but surely runs out).  A wait that runs
  * out makes the call that launched it return FR_ERR_TIMEOUT after the block has waited,
- * again bounded, for its copies in flight; the context stays usable. */
+ * again bounded, for its copies in flight; the context stays usable;
+ * arnoldi_fused: 0 (default) runs each Arnoldi step of the device-resident GMRES cycle as
+ * split passes (V^T w; w -= V h1 with V^T w; w -= V h2 with ||w|| and the Givens update;
+ * the scaled store); 1 runs the whole step in one launch of 512-thread blocks, each
+ * keeping a part of w in registers, the blocks of a case meeting at bounded barriers for
+ * the three reductions (the smallest part size with one block per SM, else the smallest
+ * whose blocks the GPU holds at once; 2 or 4 force 2 or 4 pairs of entries per thread).
+ * Where no part size fits (vectors above about 0.6 M pairs of entries) or the basis is
+ * double-float, the split passes run.  Its barrier waits use the wait_spins budget: a
+ * wait that runs out ends the solve with FR_ERR_TIMEOUT and the context stays usable. */
 #define FR_MAX_RESTART 256
 #define FR_JVP_DUAL 0
 #define FR_JVP_LINEARIZED 1
@@ -182,6 +191,7 @@ typedef struct fr_config {
   int factor_tc;
   int apply_bulk;
   long long wait_spins;
+  int arnoldi_fused;
 } fr_config;
 
 /* Statistics of one fr_bdf2_step / fr_ptc_solve (host memory, filled on return).
@@ -448,6 +458,13 @@ int fr_conservative_vjp(fr_ctx* ctx, const double* qp_d, const double* w_d, doub
  * Synchronises the stream. */
 int fr_conservative_dmach(fr_ctx* ctx, const double* qp_d, const double* w_d, double* out_h,
                           void* stream);
+
+/* Failure injection on the host, for tests of the bounded waits (arnoldi_fused): adds n
+ * arrivals to every case's barrier counter of the fused Arnoldi step, so that the next
+ * barrier of a case with two or more blocks cannot complete for one of its blocks; that
+ * block's wait runs out (wait_spins), the solve returns FR_ERR_TIMEOUT and the counters
+ * are reset.  Synchronises the device.  FR_ERR_ARG when the fused step is not in use. */
+int fr_inject_barrier_offset(fr_ctx* ctx, long long n);
 
 /* ---------------------------------------------------------------- batches
  * Many independent problems solved together (the paper solves one at a time; Sec. 3.2's

@@ -574,6 +574,7 @@ void fr_default_config(fr_config* c) {
   c->factor_tc = FR_FACTOR_SIMT;
   c->apply_bulk = 0;
   c->wait_spins = 0;
+  c->arnoldi_fused = 0;
 }
 
 int fr_create(const fr_config* cfg, fr_ctx** out) {
@@ -592,7 +593,9 @@ int fr_create(const fr_config* cfg, fr_ctx** out) {
       cfg->mg_sweeps < 1 || cfg->mg_sweeps > 2 || !(cfg->mg_omega > 0.0 && cfg->mg_omega <= 1.5) ||
       (cfg->mg_prec != FR_PREC_FP64 && cfg->mg_prec != FR_PREC_FP32) ||
       cfg->factor_tc < FR_FACTOR_SIMT || cfg->factor_tc > FR_FACTOR_TC_BF16X3 ||
-      cfg->apply_bulk < 0 || cfg->apply_bulk == 1 || cfg->apply_bulk > 4)
+      cfg->apply_bulk < 0 || cfg->apply_bulk == 1 || cfg->apply_bulk > 4 ||
+      (cfg->arnoldi_fused != 0 && cfg->arnoldi_fused != 1 && cfg->arnoldi_fused != 2 &&
+       cfg->arnoldi_fused != 4))
     return FR_ERR_ARG;
   fr_ctx* c = new fr_ctx();
   c->cfg = *cfg;
@@ -921,6 +924,19 @@ int fr_conservative_dmach(fr_ctx* c, const double* q, const double* w, double* o
   FR_TRY(check_ready(c));
   if (!q || !w || !out_h) return FR_ERR_ARG;
   return frk::conservative_dmach(c, q, w, out_h, S(s));
+}
+
+int fr_inject_barrier_offset(fr_ctx* c, long long n) {
+  FR_TRY(check_ready(c));
+  if (c->bw.fz_pt == 0 || !c->bw.fz_arrive || n < 0) return FR_ERR_ARG;
+  std::vector<unsigned long long> h(c->ncases);
+  FR_CUDA_CHECK(c, cudaDeviceSynchronize());
+  FR_CUDA_CHECK(c, cudaMemcpy(h.data(), c->bw.fz_arrive, h.size() * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost));
+  for (unsigned long long& v : h) v += (unsigned long long)n;
+  FR_CUDA_CHECK(c, cudaMemcpy(c->bw.fz_arrive, h.data(), h.size() * sizeof(unsigned long long),
+                              cudaMemcpyHostToDevice));
+  return FR_OK;
 }
 
 int fr_bdf2_step(fr_ctx* c, double* q, const double* qcn, const double* qcnm1, double a0, double a1,

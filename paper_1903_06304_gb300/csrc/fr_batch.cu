@@ -167,6 +167,11 @@ int gmres_cases(fr_ctx* c, const double* q, const double* b, double* x, double i
       issued += nchunk;
       FR_TRY(frk::bk_status(c, s));
       FR_CUDA_CHECK(c, cudaStreamSynchronize(s));
+      if (c->bw.status_h[nc].x) {
+        // a bounded wait ran out: the cycle's state is not to be trusted
+        snprintf(c->err, sizeof(c->err), "a bounded device wait ran out of its budget (wait_spins)");
+        return FR_ERR_TIMEOUT;
+      }
       bool all_done = true;
       for (int k = 0; k < nc; ++k) {
         const int4 st = c->bw.status_h[k];

@@ -46,8 +46,15 @@ struct BatchWork {
   double* hsc = nullptr;           // pinned mirror
   GmresState* gst = nullptr;       // [ncases]
   GmresState* gst_h = nullptr;     // pinned mirror
-  int4* status = nullptr;          // [ncases] (j, jmax, done, nonfinite)
+  int4* status = nullptr;          // [ncases] (j, jmax, done, nonfinite), [ncases].x = error flag
   int4* status_h = nullptr;
+  // fused Arnoldi step (arnoldi_fused, fr_krylov.cu): pairs per thread (0: the step does
+  // not fit the resident blocks and runs as split passes), block table, sums, barrier state
+  int fz_pt = 0, fz_G = 0;
+  int *fz_case = nullptr, *fz_b0 = nullptr, *fz_nb = nullptr;
+  long long *fz_lo = nullptr, *fz_hi = nullptr;
+  double* fz_part = nullptr;               // [3][BM][G] block sums of the three barriers
+  unsigned long long* fz_arrive = nullptr;  // [ncases] barrier arrivals
   double* coef = nullptr;          // [ncases] per-case coefficients
   double* coef_h = nullptr;        // pinned staging
   fr::CaseParams* cp_stage = nullptr;   // pinned staging of the case table
@@ -320,6 +327,7 @@ int axpy(fr_ctx* c, const double* V, int nv, const double* h_dev, double* w, cud
 int axpby(fr_ctx* c, double a, const double* x, double b, double* y, cudaStream_t s);
 // Batched (per-case) forms; scalars of case k at bw.dsc + k * 128.
 int batch_setup(fr_ctx* c);
+int fused_reset(fr_ctx* c, cudaStream_t s);   // fused Arnoldi barriers back to rest
 void batch_free(fr_ctx* c);
 int bk_norms(fr_ctx* c, const double* r, cudaStream_t s);         // -> [k][96..97]
 int bk_init(fr_ctx* c, const double* r, double* next, cudaStream_t s);

@@ -650,10 +650,299 @@ __global__ void k_baxpy_case(const double* __restrict__ coef, const double* __re
 __global__ void k_bgm_trisolve(GmresState* gst) {
   if (threadIdx.x == 0) gm_trisolve(gst + blockIdx.x);
 }
-__global__ void k_bgm_status(const GmresState* gst, int ncases, int4* out) {
+// out[k] = (j, jmax, done, nonfinite) of case k; out[ncases].x = the context's error flag
+// (a bounded device wait that ran out).
+__global__ void k_bgm_status(const GmresState* gst, int ncases, int4* out, const int* err) {
   for (int k = threadIdx.x; k < ncases; k += blockDim.x) {
     const GmresState* st = gst + k;
     out[k] = make_int4(st->j, st->jmax, st->done, st->nonfinite);
+  }
+  if (threadIdx.x == 0) out[ncases] = make_int4(*err, 0, 0, 0);
+}
+
+// ---- Fused Arnoldi step (arnoldi_fused): the whole CGS2 (or CGS) step of every case in
+// one launch.  Block g owns a contiguous part [flo[g], fhi[g]) of one case's pairs, thread
+// t the pairs t + FT i (i < PT), held in registers for the whole step: w is read once and
+// V[j+1] and next are written once.  The step's reductions (V^T w once or twice, ||w||^2)
+// meet at barriers of the case's blocks: each block writes its sums, arrives with one
+// atomic add on the case's counter and waits until the case's nb blocks have arrived;
+// then every block adds the nb blocks' sums itself, in a fixed order, so no block has to
+// release the others and all of them hold identical bits.  The Givens update of the
+// column is computed by every block in the same arithmetic; the case's first block writes
+// it to the GMRES state.  Blocks of FT threads, at most as many as the GPU holds at once
+// (occupancy x SMs), so a case's blocks are all resident while they wait on one another;
+// every wait is bounded (wait_spins), and a wait that runs out sets the context's error
+// flag and ends its block.
+constexpr int FT = 512;    // threads per block of the fused step (two blocks per SM)
+constexpr int FW = FT / 32;
+
+struct FusedSegs {
+  const int* fcase;              // [G] case of block g
+  const long long* flo;          // [G] first pair of block g
+  const long long* fhi;          // [G] one past its last pair
+  const int* fb0;                // [ncases] first block of case k
+  const int* fnb;                // [ncases] its block count
+  double* part;                  // [3][BM][G] block sums of the step's three barriers
+  unsigned long long* arrive;    // [ncases] arrivals at the case's barriers (a multiple of
+                                 // the case's block count between launches)
+  int G;
+};
+
+// Barrier `phase` (0, 1, 2 of a step) of the blocks of case k carrying the sums vals[q]
+// (shared, q < nv): on a true return out[q] (shared) holds the sum over the case's blocks,
+// added in block order.  Barrier b of a case ends when the counter reaches (b + 1) nb; each
+// phase has its own buffer of sums, written once per launch.  False: this block's wait ran
+// out (error flag set) and the block must leave.
+__device__ bool fused_barrier_sum(const double* vals, int nv, int k, int phase, const FusedSegs& F,
+                                  double* out, long long spins, int* err) {
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int gb0 = F.fb0[k], nb = F.fnb[k];
+  const size_t G = (size_t)F.G;
+  double* P = F.part + (size_t)phase * BM * G;
+  if (tid < nv) P[(size_t)tid * G + blockIdx.x] = vals[tid];
+  __syncthreads();
+  if (tid == 0) {
+    // the block's sums are ordered before its arrival by the block barrier and this fence
+    __threadfence();
+    const unsigned long long old = atomicAdd(F.arrive + k, 1ull);
+    const unsigned long long target = old - old % (unsigned long long)nb + (unsigned long long)nb;
+    int ok = 1;
+    if (old + 1 != target) {
+      ok = 0;
+      const long long n = spins < 0 ? 1 : spins;
+      for (long long i = 0; i < n; ++i) {
+        if (*(volatile unsigned long long*)(F.arrive + k) >= target) { ok = 1; break; }
+        if (spins >= 0) __nanosleep(20);
+      }
+      if (!ok) atomicExch(err, 1);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  if (!s_ok) return false;
+  for (int q = wid; q < nv; q += FW) {
+    const double v = warp_sum_partials(P + (size_t)q * G + gb0, nb);
+    if (lane == 0) out[q] = v;
+  }
+  __syncthreads();
+  return true;
+}
+
+// Warp sums of eight values per lane by recursive halving (bits 16, 8, 4 of the lane
+// index pick the half a lane keeps), then the last two lane bits: lane l with l % 4 == 0
+// ends with the sum of value 4 b16 + 2 b8 + b4 (9 additions per lane instead of 40).
+__device__ __forceinline__ double warp_sum8(double (&a)[8]) {
+  const int lane = threadIdx.x & 31;
+  const bool u16 = (lane & 16) != 0, u8 = (lane & 8) != 0, u4 = (lane & 4) != 0;
+  double b[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const double keep = u16 ? a[m + 4] : a[m], send = u16 ? a[m] : a[m + 4];
+    b[m] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  double c[2];
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const double keep = u8 ? b[m + 2] : b[m], send = u8 ? b[m] : b[m + 2];
+    c[m] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const double keep = u4 ? c[1] : c[0], send = u4 ? c[0] : c[1];
+  double v = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
+// This block's sums of <V_q, x> over its pairs (thread t: pairs t + FT i, i < PT) for
+// q < nv into sums[q]: eight vectors at a time per thread, warp sums by warp_sum8, the
+// FW warp sums of each vector added in warp order.
+template <int PT>
+__device__ __forceinline__ void fused_dots(const double2* V2, size_t ld2, size_t lo, int len,
+                                           const double2 (&x)[PT], int nv,
+                                           double (*wsum)[FW], double* sums) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int q0 = 0; q0 < nv; q0 += 8) {
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < PT; ++i) {
+      const int t = tid + FT * i;
+      if (t < len) {
+        double2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          v[u] = q0 + u < nv ? V2[(size_t)(q0 + u) * ld2 + lo + t] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          acc[u] = fma(v[u].x, x[i].x, acc[u]);
+          acc[u] = fma(v[u].y, x[i].y, acc[u]);
+        }
+      }
+    }
+    const double s = warp_sum8(acc);
+    const int u = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    if ((lane & 3) == 0 && q0 + u < nv) wsum[q0 + u][wid] = s;
+  }
+  __syncthreads();
+  for (int q = wid; q < nv; q += FW) {
+    const double t = warp_sum(lane < FW ? wsum[q][lane] : 0.0);
+    if (lane == 0) sums[q] = t;
+  }
+  __syncthreads();
+}
+
+// x -= sum_{q < nv} h[q] V_q over this thread's pairs (eight loads in flight, the sums in
+// order of q).
+template <int PT>
+__device__ __forceinline__ void fused_axpy(const double2* V2, size_t ld2, size_t lo, int len,
+                                           double2 (&x)[PT], int nv, const double* h) {
+#pragma unroll
+  for (int i = 0; i < PT; ++i) {
+    const int t = threadIdx.x + FT * i;
+    if (t >= len) continue;
+    const size_t p = lo + t;
+    double2 y = x[i];
+    int q = 0;
+    for (; q + 8 <= nv; q += 8) {
+      double2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = V2[(size_t)(q + u) * ld2 + p];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) { y.x = fma(-h[q + u], v[u].x, y.x); y.y = fma(-h[q + u], v[u].y, y.y); }
+    }
+    for (; q < nv; ++q) {
+      const double2 v = V2[(size_t)q * ld2 + p];
+      y.x = fma(-h[q], v.x, y.x);
+      y.y = fma(-h[q], v.y, y.y);
+    }
+    x[i] = y;
+  }
+}
+
+// One Arnoldi step of every case whose cycle runs: h1 = V^T w; (CGS2) w -= V h1, h2 = V^T w;
+// w -= V h2 (h1 for CGS); ||w||^2; the Givens update of column j (the arithmetic of
+// gm_givens, in every block; the case's first block writes the state); V[j+1] = next =
+// w / ||w|| unless the cycle stopped.
+template <int PT>
+__global__ void __launch_bounds__(FT, 2) k_arnoldi_fused(double* V, size_t ld, const double* __restrict__ w,
+                                                         double* __restrict__ next, FusedSegs F,
+                                                         GmresState* gst, int two_pass, long long spins,
+                                                         int* err) {
+  constexpr int L = GmresState::LD;
+  __shared__ double wsum[BM][FW];
+  __shared__ double h1[BM], h2[BM], sums[BM], col[L + 1], rc[L], rs[L];
+  __shared__ double s_g, s_tol, s_inv_hn;
+  __shared__ int s_jmax, s_done, s_nonfinite;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int k = F.fcase[blockIdx.x];
+  GmresState* st = gst + k;
+  if (st->done) return;
+  const int j = st->j, nv = j + 1;
+  const size_t lo = (size_t)F.flo[blockIdx.x];
+  const int len = (int)((size_t)F.fhi[blockIdx.x] - lo);
+  const double2* V2 = reinterpret_cast<const double2*>(V);
+  const size_t ld2 = ld / 2;
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  double2 x[PT];
+#pragma unroll
+  for (int i = 0; i < PT; ++i) {
+    const int t = tid + FT * i;
+    x[i] = t < len ? w2[lo + t] : make_double2(0.0, 0.0);
+  }
+  // the rotation inputs, read before this block's first arrival: the case's first block
+  // rewrites them only after every block has passed the last barrier
+  for (int i = tid; i < j; i += FT) { rc[i] = st->cs[i]; rs[i] = st->sn[i]; }
+  if (tid == 0) { s_g = st->g[j]; s_tol = st->tol; s_jmax = st->jmax; }
+  // h1 = V^T w
+  fused_dots<PT>(V2, ld2, lo, len, x, nv, wsum, sums);
+  if (!fused_barrier_sum(sums, nv, k, 0, F, h1, spins, err)) return;
+  const double* h = h1;
+  int phase = 1;
+  if (two_pass) {
+    // w -= V h1; h2 = V^T w
+    fused_axpy<PT>(V2, ld2, lo, len, x, nv, h1);
+    fused_dots<PT>(V2, ld2, lo, len, x, nv, wsum, sums);
+    if (!fused_barrier_sum(sums, nv, k, 1, F, h2, spins, err)) return;
+    h = h2;
+    phase = 2;
+  }
+  // w -= V h; ||w||^2
+  fused_axpy<PT>(V2, ld2, lo, len, x, nv, h);
+  double a = 0.0;
+#pragma unroll
+  for (int i = 0; i < PT; ++i) {
+    a = fma(x[i].x, x[i].x, a);   // pairs past len hold zeros
+    a = fma(x[i].y, x[i].y, a);
+  }
+  a = warp_sum(a);
+  if (lane == 0) wsum[0][wid] = a;
+  __syncthreads();
+  if (wid == 0) {
+    const double t = warp_sum(lane < FW ? wsum[0][lane] : 0.0);
+    if (lane == 0) sums[0] = t;
+  }
+  __syncthreads();
+  double* nrm = sums + 1;
+  if (!fused_barrier_sum(sums, 1, k, phase, F, nrm, spins, err)) return;
+  // Givens update of column j
+  for (int i = tid; i <= j; i += FT) col[i] = two_pass ? h1[i] + h2[i] : h1[i];
+  __syncthreads();
+  if (tid == 0) {
+    const double hn = sqrt(nrm[0]);
+    s_nonfinite = !isfinite(hn);
+    if (s_nonfinite) {
+      s_done = 1;
+    } else {
+      double aa = col[0];
+      for (int i = 0; i < j; ++i) {
+        const double bb = col[i + 1];
+        col[i] = rc[i] * aa + rs[i] * bb;
+        aa = -rs[i] * aa + rc[i] * bb;
+      }
+      const double den = hypot(aa, hn);
+      const double cj = aa / den, sj = hn / den;
+      col[j] = den;
+      col[j + 1] = 0.0;
+      rc[j] = cj;
+      rs[j] = sj;
+      const double g1 = -sj * s_g;
+      s_g = cj * s_g;
+      sums[0] = g1;
+      s_inv_hn = hn > 0.0 ? 1.0 / hn : 0.0;
+      s_done = (fabs(g1) <= s_tol || hn == 0.0 || j + 1 >= s_jmax) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == F.fb0[k]) {
+    if (s_nonfinite) {
+      if (tid == 0) { st->nonfinite = 1; st->done = 1; }
+    } else {
+      if (tid == 0) {
+        st->cs[j] = rc[j];
+        st->sn[j] = rs[j];
+        st->g[j + 1] = sums[0];
+        st->g[j] = s_g;
+        st->j = j + 1;
+        st->inv_hn = s_inv_hn;
+        st->done = s_done;
+      }
+      for (int i = tid; i <= j + 1; i += FT) st->H[i * L + j] = col[i];
+    }
+  }
+  if (s_done) return;
+  // V[j+1] = next = w / ||w||
+  const double s = s_inv_hn;
+  double2* Vw = reinterpret_cast<double2*>(V) + (size_t)(j + 1) * ld2;
+  double2* n2 = reinterpret_cast<double2*>(next);
+#pragma unroll
+  for (int i = 0; i < PT; ++i) {
+    const int t = tid + FT * i;
+    if (t < len) {
+      const double2 y = make_double2(x[i].x * s, x[i].y * s);
+      Vw[lo + t] = y;
+      n2[lo + t] = y;
+    }
   }
 }
 
@@ -965,6 +1254,7 @@ int check_device_waits(fr_ctx* c, cudaStream_t s) {
   FR_CUDA_CHECK(c, cudaStreamSynchronize(s));
   if (h == 0) return FR_OK;
   FR_CUDA_CHECK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), s));
+  FR_TRY(fused_reset(c, s));
   snprintf(c->err, sizeof(c->err), "a bounded device wait ran out of its budget (wait_spins)");
   return FR_ERR_TIMEOUT;
 }
@@ -1022,12 +1312,102 @@ template <class T> static int bw_alloc_host(fr_ctx* c, T** p, size_t n) {
 void batch_free(fr_ctx* c) {
   BatchWork& b = c->bw;
   void* dev[] = {b.bcase, b.cb0, b.cnb, b.blo, b.bhi, b.mend, b.partial, b.tickets, b.dsc, b.gst,
-                 b.status, b.coef};
+                 b.status, b.coef, b.fz_case, b.fz_b0, b.fz_nb, b.fz_lo, b.fz_hi, b.fz_part,
+                 b.fz_arrive};
   for (void* p : dev) if (p) cudaFree(p);
   void* host[] = {b.hsc, b.gst_h, b.status_h, b.coef_h, b.cp_stage};
   for (void* p : host) if (p) cudaFreeHost(p);
   if (b.staged) cudaEventDestroy(b.staged);
   b = BatchWork();
+}
+
+// Block table of the fused Arnoldi step: the smallest PT (pairs per thread, or the one
+// arnoldi_fused names) whose blocks (each case's pairs split evenly, at most PT FT pairs
+// a block) the GPU holds at once; fz_pt = 0 when none does.
+// (the largest shared-memory carveout is requested first, so that the launch has the
+// shared memory the occupancy figure assumes)
+template <int PT> static cudaError_t fused_occupancy(int* out) {
+  const cudaError_t e = cudaFuncSetAttribute(k_arnoldi_fused<PT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_arnoldi_fused<PT>, FT, 0);
+}
+static int fused_blocks_per_sm(int pt, int* out) {
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (pt) {
+    case 1: e = fused_occupancy<1>(out); break;
+    case 2: e = fused_occupancy<2>(out); break;
+    case 4: e = fused_occupancy<4>(out); break;
+  }
+  return e == cudaSuccess ? 0 : 1;
+}
+
+static int fused_setup(fr_ctx* c) {
+  BatchWork& b = c->bw;
+  b.fz_pt = b.fz_G = 0;
+  if (c->cfg.arnoldi_fused == 0) return FR_OK;
+  const int nc = c->ncases;
+  int dev = 0, nsm = 0;
+  FR_CUDA_CHECK(c, cudaGetDevice(&dev));
+  FR_CUDA_CHECK(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int want = c->cfg.arnoldi_fused;
+  int pt = 0, G = 0;
+  // first the smallest part size with at most one block per SM (fewer blocks per barrier,
+  // two pairs per thread in flight: measured the faster shape), else the smallest that
+  // the GPU holds at once
+  for (int pass = 0; pass < 2 && pt == 0; ++pass) {
+    for (int cand : {1, 2, 4}) {
+      if (want > 1 && cand != want) continue;
+      int per_sm = 0;
+      if (fused_blocks_per_sm(cand, &per_sm)) {
+        snprintf(c->err, sizeof(c->err), "fused Arnoldi: occupancy query failed");
+        return FR_ERR_CUDA;
+      }
+      long long g = 0;
+      for (int k = 0; k < nc; ++k) {
+        const long long np = 2LL * c->cps[k].sn;
+        g += std::max<long long>(1, (np + (long long)cand * FT - 1) / ((long long)cand * FT));
+      }
+      const long long cap = pass == 0 ? std::min<long long>(nsm, (long long)per_sm * nsm) : (long long)per_sm * nsm;
+      if (g <= cap) { pt = cand; G = (int)g; break; }
+    }
+  }
+  if (pt == 0) return FR_OK;
+  std::vector<int> fcase, fb0(nc), fnb(nc);
+  std::vector<long long> flo, fhi;
+  for (int k = 0; k < nc; ++k) {
+    const long long p0 = c->cps[k].off / 2, np = 2LL * c->cps[k].sn;
+    const int nb = (int)std::max<long long>(1, (np + (long long)pt * FT - 1) / ((long long)pt * FT));
+    fb0[k] = (int)fcase.size();
+    fnb[k] = nb;
+    for (int q = 0; q < nb; ++q) {
+      fcase.push_back(k);
+      flo.push_back(p0 + np * q / nb);
+      fhi.push_back(p0 + np * (q + 1) / nb);
+    }
+  }
+  if (bw_alloc(c, &b.fz_case, G) || bw_alloc(c, &b.fz_lo, G) || bw_alloc(c, &b.fz_hi, G) ||
+      bw_alloc(c, &b.fz_b0, nc) || bw_alloc(c, &b.fz_nb, nc) ||
+      bw_alloc(c, &b.fz_part, (size_t)3 * BM * G) || bw_alloc(c, &b.fz_arrive, nc))
+    return FR_ERR_CUDA;
+  FR_CUDA_CHECK(c, cudaMemcpy(b.fz_case, fcase.data(), G * sizeof(int), cudaMemcpyHostToDevice));
+  FR_CUDA_CHECK(c, cudaMemcpy(b.fz_lo, flo.data(), G * sizeof(long long), cudaMemcpyHostToDevice));
+  FR_CUDA_CHECK(c, cudaMemcpy(b.fz_hi, fhi.data(), G * sizeof(long long), cudaMemcpyHostToDevice));
+  FR_CUDA_CHECK(c, cudaMemcpy(b.fz_b0, fb0.data(), nc * sizeof(int), cudaMemcpyHostToDevice));
+  FR_CUDA_CHECK(c, cudaMemcpy(b.fz_nb, fnb.data(), nc * sizeof(int), cudaMemcpyHostToDevice));
+  FR_CUDA_CHECK(c, cudaMemset(b.fz_arrive, 0, nc * sizeof(unsigned long long)));
+  b.fz_pt = pt;
+  b.fz_G = G;
+  return FR_OK;
+}
+
+// The barrier counters of the fused step back to their resting value after a wait ran out
+// and left a barrier half passed.
+int fused_reset(fr_ctx* c, cudaStream_t s) {
+  BatchWork& b = c->bw;
+  if (!b.fz_arrive) return FR_OK;
+  FR_CUDA_CHECK(c, cudaMemsetAsync(b.fz_arrive, 0, c->ncases * sizeof(unsigned long long), s));
+  return FR_OK;
 }
 
 // Blocks of each case in proportion to its length: at most 4 pairs per thread (a range
@@ -1055,9 +1435,9 @@ int batch_setup(fr_ctx* c) {
       bw_alloc(c, &b.cb0, nc) || bw_alloc(c, &b.cnb, nc) || bw_alloc(c, &b.mend, nc) ||
       bw_alloc(c, &b.partial, (size_t)GmresState::LD * SPLIT * b.nblk) || bw_alloc(c, &b.tickets, nc) ||
       bw_alloc(c, &b.dsc, (size_t)BDS * nc) || bw_alloc(c, &b.gst, nc) ||
-      bw_alloc(c, &b.status, nc) || bw_alloc(c, &b.coef, nc) ||
+      bw_alloc(c, &b.status, nc + 1) || bw_alloc(c, &b.coef, nc) ||
       bw_alloc_host(c, &b.hsc, (size_t)BDS * nc) || bw_alloc_host(c, &b.gst_h, nc) ||
-      bw_alloc_host(c, &b.status_h, nc) || bw_alloc_host(c, &b.coef_h, nc) ||
+      bw_alloc_host(c, &b.status_h, nc + 1) || bw_alloc_host(c, &b.coef_h, nc) ||
       bw_alloc_host(c, &b.cp_stage, nc))
     return FR_ERR_CUDA;
   FR_CUDA_CHECK(c, cudaEventCreateWithFlags(&b.staged, cudaEventDisableTiming));
@@ -1070,7 +1450,7 @@ int batch_setup(fr_ctx* c) {
   FR_CUDA_CHECK(c, cudaMemset(b.tickets, 0, nc * sizeof(unsigned int)));
   FR_CUDA_CHECK(c, cudaMemset(b.gst, 0, nc * sizeof(GmresState)));
   b.sg = BatchSegs{b.bcase, b.blo, b.bhi, b.cb0, b.cnb};
-  return FR_OK;
+  return fused_setup(c);
 }
 
 // The device-resident cycle stores its basis as double-floats when krylov_arith asks.
@@ -1107,6 +1487,28 @@ int bk_orthogonalize(fr_ctx* c, double* w, double* next, int nv_bound, cudaStrea
   FR_ACCOUNT(c, KK_KRYLOV, (two ? 8.0 : 4.0) * nv_bound * c->ndof + 2.0 * c->ndof,
              8.0 * c->ndof * ((two ? 4.0 : 2.0) * nv_bound + 6.0));
   const bool df = df_basis(c);
+  if (!df && b.fz_pt > 0) {
+    // the whole step in one launch: V read once per pass, w once, V[j+1] and next written once
+    FR_ACCOUNT(c, KK_KRYLOV, (two ? 8.0 : 4.0) * nv_bound * c->ndof + 3.0 * c->ndof,
+               8.0 * c->ndof * ((two ? 4.0 : 2.0) * nv_bound + 3.0));
+    const FusedSegs F{b.fz_case, b.fz_lo, b.fz_hi, b.fz_b0, b.fz_nb, b.fz_part, b.fz_arrive, b.fz_G};
+    const long long spins = c->cfg.wait_spins == 0 ? (1LL << 22) : c->cfg.wait_spins;
+    FR_PROF_BEGIN(c, s);
+    switch (b.fz_pt) {
+#define FR_FUSED_CASE(P)                                                                          \
+  case P:                                                                                         \
+    k_arnoldi_fused<P><<<b.fz_G, FT, 0, s>>>(c->V, c->ndof, w, next, F, b.gst, two ? 1 : 0,       \
+                                             spins, c->dev_err);                                  \
+    break;
+      FR_FUSED_CASE(1)
+      FR_FUSED_CASE(2)
+      FR_FUSED_CASE(4)
+#undef FR_FUSED_CASE
+    }
+    FR_PROF_END(c, s, KK_KRYLOV);
+    FR_LAUNCH_CHECK(c);
+    return FR_OK;
+  }
   const float4* V4 = reinterpret_cast<const float4*>(c->V);
   {
     FR_PROF_BEGIN(c, s);
@@ -1170,11 +1572,11 @@ int bk_finish(fr_ctx* c, double* u, cudaStream_t s) {
 int bk_status(fr_ctx* c, cudaStream_t s) {
   {
     FR_PROF_BEGIN(c, s);
-    k_bgm_status<<<1, 256, 0, s>>>(c->bw.gst, c->ncases, c->bw.status);
+    k_bgm_status<<<1, 256, 0, s>>>(c->bw.gst, c->ncases, c->bw.status, c->dev_err);
     FR_PROF_END(c, s, KK_KRYLOV);
     FR_LAUNCH_CHECK(c);
   }
-  FR_CUDA_CHECK(c, cudaMemcpyAsync(c->bw.status_h, c->bw.status, c->ncases * sizeof(int4),
+  FR_CUDA_CHECK(c, cudaMemcpyAsync(c->bw.status_h, c->bw.status, (c->ncases + 1) * sizeof(int4),
                                    cudaMemcpyDeviceToHost, s));
   return FR_OK;
 }

@@ -48,7 +48,8 @@ class _Config(ctypes.Structure):
                 ("krylov_arith", ctypes.c_int), ("precond", ctypes.c_int),
                 ("mg_sweeps", ctypes.c_int), ("mg_omega", ctypes.c_double),
                 ("mg_prec", ctypes.c_int), ("factor_tc", ctypes.c_int),
-                ("apply_bulk", ctypes.c_int), ("wait_spins", ctypes.c_longlong)]
+                ("apply_bulk", ctypes.c_int), ("wait_spins", ctypes.c_longlong),
+                ("arnoldi_fused", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -117,6 +118,7 @@ _SIGS = {
     "fr_wall_force_vjp": (_I, [_P, _P, _D, _D, _D, _D, _P, _P]),
     "fr_conservative_vjp": (_I, [_P, _P, _P, _D, _D, _P, _P]),
     "fr_conservative_dmach": (_I, [_P, _P, _P, ctypes.POINTER(_D), _P]),
+    "fr_inject_barrier_offset": (_I, [_P, ctypes.c_longlong]),
     "fr_batch_create": (_I, [ctypes.POINTER(_Config), _P, _I, ctypes.POINTER(_P)]),
     "fr_batch_destroy": (None, [_P]),
     "fr_batch_case_info": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
@@ -212,6 +214,7 @@ class Config:
     factor: str = "simt"
     apply_bulk: int = 0
     wait_spins: int = 0
+    arnoldi_fused: int = 0
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -518,6 +521,10 @@ class Solver:
         self._check(self.lib.fr_conservative_dmach(self.ctx, _ptr(q), _ptr(w), ctypes.byref(d),
                                                    _stream(stream)))
         return d.value
+
+    def inject_barrier_offset(self, n: int):
+        """Test hook: n extra arrivals on the fused Arnoldi step's barrier counters."""
+        self._check(self.lib.fr_inject_barrier_offset(self.ctx, n))
 
     def precond_build(self, q, inv_dtau=0.0, a0_dt=0.0, stream=None):
         self._check(self.lib.fr_precond_build(self.ctx, _ptr(q), inv_dtau, a0_dt, _stream(stream)))
