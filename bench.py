@@ -471,8 +471,11 @@ def steady_ptc_study(args, torch, fr, inp, T):
     v = 0.0 * c
     qi = inp.far_field_state(mach)
     q0 = inp.uniform_state(ni * nj, p, mach)
+    # FP64 coarse levels, as on the NACA O-grid: the stretched grid at M = 0.1 is where FP32
+    # coarse operators have given non-finite Krylov vectors
     base = dict(p=p, mach=mach, re=re, kappa=1.0, restart=100, maxit_lin=300, tol_res=1e-6,
-                tol_pseudo=1e-8, maxit_newton=64, precond=args.precond, prec=args.prec)
+                tol_pseudo=1e-8, maxit_newton=64, precond=args.precond, prec=args.prec,
+                mg_prec="fp64")
     variants = [("tol_res=1e-3", {"tol_res": 1e-3}), ("tol_res=1e-6", {}), ("tol_res=1e-9", {"tol_res": 1e-9}),
                 ("dtau_max=100", {"dtau_max": 100.0}), ("dtau_max=10", {"dtau_max": 10.0}),
                 ("kappa=sqrt5", {"kappa": 5 ** 0.5}), ("kappa=3", {"kappa": 3.0})]
@@ -484,7 +487,12 @@ def steady_ptc_study(args, torch, fr, inp, T):
         q = T(q0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st = S.ptc_solve(q, allow_unconverged=True).summary()
+        try:
+            st = S.ptc_solve(q, allow_unconverged=True).summary()
+        except fr.FrError as e:
+            out[name] = {"converged": False, "error": str(e)}
+            S.close()
+            continue
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         fx, _fy = S.wall_force(q)
@@ -952,18 +960,26 @@ def gpu_arm(args):
             diff = (finals[name] - finals["fp64"]).view(4, -1).abs().amax(dim=1)
             compare[name]["state_diff_vs_fp64"] = float((diff / dq).max())
 
+    # the side reports: a failure in one of them is recorded in its entry, never ends the run
+    def side_report(fn, *a):
+        try:
+            return fn(*a)
+        except fr.FrError as e:
+            torch.cuda.synchronize()
+            return {"error": str(e)}
+
     low_mach = None
     if rank == 0 and not args.no_c3:
-        low_mach = low_mach_deforming_report(args, torch, fr, inp, T, flush)
+        low_mach = side_report(low_mach_deforming_report, args, torch, fr, inp, T, flush)
     ptc = None
     if rank == 0 and not args.no_ptc:
-        ptc = steady_ptc_study(args, torch, fr, inp, T)
+        ptc = side_report(steady_ptc_study, args, torch, fr, inp, T)
     plunge = None
     if rank == 0 and not args.no_plunge:
-        plunge = plunge_march_report(args, torch, fr, inp, T)
+        plunge = side_report(plunge_march_report, args, torch, fr, inp, T)
     adjoint = None
     if rank == 0 and not args.no_adjoint:
-        adjoint = plunge_adjoint_report(args, torch, fr, inp, T)
+        adjoint = side_report(plunge_adjoint_report, args, torch, fr, inp, T)
 
     # ---- CPU baseline (rank 0, N = 1 only): the oracle's unit costs priced with the
     # timed steps' own counts
@@ -1246,8 +1262,11 @@ def main():
                          "(double-float on the FP32 pipe)")
     ap.add_argument("--orthog", default="cgs2", choices=["cgs2", "cgs"],
                     help="Arnoldi orthogonalisation: CGS2, or one classical pass (PETSc's default)")
-    ap.add_argument("--tiles", type=int, default=0, choices=[0, 1, 2],
-                    help="elements per CTA of the point kernels: 0 autotuned at set-up, 1 or 2 fixed")
+    ap.add_argument("--tiles", type=int, default=1, choices=[0, 1, 2],
+                    help="elements per CTA of the point kernels: 1 or 2 fixed (1, the library's "
+                         "default: reproducible arithmetic), 0 autotuned at set-up by timing (the "
+                         "two shapes contract the same formulas into FMAs differently, and the "
+                         "march's unconverged start-up steps amplify that rounding)")
     ap.add_argument("--graphs", type=int, default=1,
                     help="replay GMRES chunks from captured CUDA graphs (1) or launch each kernel (0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
