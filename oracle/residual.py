@@ -19,8 +19,12 @@ Readings where the paper is silent (used identically by the CUDA library):
 * d(|J| xi_t)/dxi is the derivative of the degree-p interpolant of |J| xi_t.
 * Local gradients use the chain rule on the interpolant derivatives; the
   corrected gradient adds, for each face f, (q^com - q^loc_f) S_f g_f'(xi) / |J|.
-* BR2 (Sec. 3.1): grad q^com = (grad q^+,loc + r^+ + grad q^-,loc + r^-)/2 with
-  r^+- = (q^com - q^+-) S_f g'_f(face end) / |J|^+-_f (face f's own jump only).
+* BR2 (Sec. 3.1): grad q^com = (grad q^+,loc + grad q^-,loc)/2 + eta (r^+ + r^-)/2 with
+  r^+- = (q^com - q^+-) S_f g'_f(face end) / |J|^+-_f (face f's own jump only) and the
+  face penalty eta = BR2_PENALTY = 2 (the form the paper defers to is not available;
+  BR2's face term needs a penalty above one for stability: with eta = 1 the viscous
+  vortex on 64 x 64 elements of degree 3 grows unstably, with 2 it does not).  The
+  corrected gradient at the solution points keeps eta = 1.
 * The common viscous flux is f_vis(q^com, grad q^com) . n.
 
 Mesh: element e = j*nx + i; faces in xi are "owned" by their left element (its
@@ -35,7 +39,7 @@ Boundary faces (readings; the paper states the conditions, not the discrete form
   temperature from the interior trace, velocity of the moving wall).
 * Inviscid flux: the preconditioned Rusanov flux between the interior trace and q_b.
 * Viscous terms: q^com = q_b; the lifted jump of the face is the full q_b - q^- (one
-  side only), in the corrected gradient and in grad q^com = grad q^-,loc + r^- with
+  side only), in the corrected gradient and in grad q^com = grad q^-,loc + eta r^- with
   r^- = (q_b - q^-) S_f g'_f(face end) / |J|^-_f; at a wall the normal component of
   grad T^com is removed (adiabatic, dT/dn = 0); f_vis(q_b, grad q^com) . n.
 """
@@ -48,6 +52,8 @@ import numpy as np
 from . import physics as ph
 from .basis import Basis, make_basis
 from .geometry import FACE_B, FACE_L, FACE_R, FACE_T, Geometry, element_geometry
+
+BR2_PENALTY = 2.0   # BR2 face penalty eta (reading in the module docstring)
 
 
 WALL, FARFIELD = "wall", "farfield"
@@ -244,10 +250,11 @@ def residual(q, mesh: Mesh, p: int, gas: ph.Gas, b: Basis | None = None,
         gm_xi = gp_xi = gm_eta = gp_eta = None
     fR, fL_of_right = geo.faces[FACE_R], geo.faces[FACE_L]
     fT, fB_of_top = geo.faces[FACE_T], geo.faces[FACE_B]
+    liftR, liftL = BR2_PENALTY * b.dgR_end, BR2_PENALTY * b.dgL_end   # BR2 face liftings
     Fnum_xi = common(qm_xi, qp_xi, gm_xi, gp_xi, fR.J, fL_of_right.J[right], fR.Sxi, fR.vg,
-                     b.dgR_end, b.dgL_end)
+                     liftR, liftL)
     Fnum_eta = common(qm_eta, qp_eta, gm_eta, gp_eta, fT.J, fB_of_top.J[top], fT.Seta, fT.vg,
-                      b.dgR_end, b.dgL_end)
+                      liftR, liftL)
     Fnum_bottom = None
     if mesh.bounded:
         gt_top = gt_bot = None
@@ -256,9 +263,9 @@ def residual(q, mesh: Mesh, p: int, gas: ph.Gas, b: Basis | None = None,
             gt_bot = (gtr[FACE_B][0][:, row0], gtr[FACE_B][1][:, row0])
         # above row ny-1 the element is on the '-' side of +eta, below row 0 on the '+' side
         top_flux = boundary_flux(mesh.bc[1], qf[FACE_T][:, rowL], qb_top, gt_top,
-                                 fT.Seta[:, rowL], fT.J[rowL], fT.vg[:, rowL], b.dgR_end, True, gas)
+                                 fT.Seta[:, rowL], fT.J[rowL], fT.vg[:, rowL], liftR, True, gas)
         Fnum_bottom = boundary_flux(mesh.bc[0], qf[FACE_B][:, row0], qb_bot, gt_bot,
-                                    fB.Seta[:, row0], fB.J[row0], fB.vg[:, row0], b.dgL_end, False, gas)
+                                    fB.Seta[:, row0], fB.J[row0], fB.vg[:, row0], liftL, False, gas)
         Fnum_eta = Fnum_eta.astype(np.result_type(Fnum_eta, top_flux))
         Fnum_eta[:, rowL] = top_flux
     Fnum_f = [Fnum_xi[:, left], Fnum_xi, Fnum_eta[:, bottom], Fnum_eta]
@@ -339,7 +346,7 @@ def wall_force(q, mesh: Mesh, p: int, gas: ph.Gas, b: Basis | None = None,
             gxl = (g.Sxi[0] * q_xi + g.Seta[0] * q_eta) / g.J
             gyl = (g.Sxi[1] * q_xi + g.Seta[1] * q_eta) / g.J
             ge = (trace(b, gxl, face)[:, rows], trace(b, gyl, face)[:, rows])
-            dg = b.dgL_end if side == 0 else b.dgR_end
+            dg = BR2_PENALTY * (b.dgL_end if side == 0 else b.dgR_end)
             nvec = (S[0] / Smag, S[1] / Smag)
             gx, gy = _boundary_gradient(WALL, qe, qb, ge, S, fg.J[rows], dg, nvec)
             fv, gv = ph.viscous_flux(tuple(qb[k] for k in range(4)), tuple(gx), tuple(gy), gas)

@@ -45,7 +45,7 @@ __global__ void k_wall_force_adjoint(Mesh M, Basis B, const double* __restrict__
     for (int v = 0; v < 4; ++v) qe[v] = mk(qv[v], dd == v ? 1.0 : 0.0);
 #pragma unroll
     for (int c = 0; c < 8; ++c) ge[c] = mk(gv[c], dd == 4 + c ? 1.0 : 0.0);
-    wall_traction(qe, ge, Sx, Sy, ug, vg, J, gas, side == 0 ? -B.dgR_end : B.dgR_end,
+    wall_traction(qe, ge, Sx, Sy, ug, vg, J, gas, side == 0 ? -B.lift_end : B.lift_end,
                   side == 0 ? 1.0 : -1.0, B.ws[t], M.viscous, px, py);
     const double d = wx * px.d + wy * py.d;
     if (dd < 4) atq[(((size_t)e * 4 + f) * 4 + dd) * N + t] = d;

@@ -93,7 +93,8 @@ fr::Basis fr_make_basis(int p) {
     B.dgR[i] = dgr(xs[i]);
     B.dgL[i] = -dgr(-xs[i]);
   }
-  B.dgR_end = 0.5 * (p + 1) * (p + 1);
+  // BR2 face lifting: eta g_R'(1) with the penalty eta = BR2_PENALTY
+  B.lift_end = fr::BR2_PENALTY * 0.5 * (p + 1) * (p + 1);
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k) B.Dc[i][k] = B.D[i][k] - B.dgL[i] * B.lL[k] - B.dgR[i] * B.lR[k];
   return B;

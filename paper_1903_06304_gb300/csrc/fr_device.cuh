@@ -17,12 +17,19 @@ constexpr int MAXN = 5;  // p <= 4
 
 // ---------------------------------------------------------------- constants
 // 1-D FR basis on [-1,1] with Gauss solution points (Sec. 3.1).
+// Penalty of the BR2 face lifting (the face gradient's lifted jumps are scaled by it; the
+// corrected gradient at the solution points keeps the plain liftings).  With 1 the viscous
+// vortex on 64 x 64 elements of degree 3 grows unstably; 2 keeps it stable (as do 4 and 6,
+// with the same solution), and larger values stiffen the thin wall cells of an O-grid
+// (with 4 the first step of the M = 0.3 plunge breaks down).
+constexpr double BR2_PENALTY = 2.0;
+
 struct Basis {
   double D[MAXN][MAXN];   // D[i][k] = l_k'(x_i)
   double Dc[MAXN][MAXN];  // D[i][k] - g_L'(x_i) l_k(-1) - g_R'(x_i) l_k(1)
   double lL[MAXN], lR[MAXN];
   double dgL[MAXN], dgR[MAXN];
-  double dgR_end;         // g_R'(1) = (p+1)^2/2; g_L'(-1) = -g_R'(1)
+  double lift_end;        // BR2 face lifting factor eta g_R'(1), g_R'(1) = (p+1)^2/2 = -g_L'(-1)
   double xs[MAXN];        // solution points
   double ws[MAXN];        // Gauss weights of the solution points
 };
@@ -231,9 +238,10 @@ __device__ __forceinline__ void neg_viscous_flux(const T q[4], const T qx[4], co
 //   inviscid (Eq. Rosanov): |S| f_n,inv = f . S - (v_g . S) q^c on each side,
 //     dissipation 1/2 |lambda|max(S) Gamma~ (q+ - q-), all of eps, U_r, Gamma~ and
 //     |lambda| at the averaged primitive state; |lambda| is homogeneous in S.
-//   viscous (BR2, Sec. 3.1): q^com = (q+ + q-)/2, grad q^com = (grad q+ + r+ + grad q-
-//     + r-)/2 with r-+ = (q^com - q-+) S g'(end) / |J|-+, which sum to
-//     (q+ - q-) S g_R'(1) (1/|J|- + 1/|J|+) / 2;  |S| f_vis . n = f_vis . S.
+//   viscous (BR2, Sec. 3.1): q^com = (q+ + q-)/2, grad q^com = (grad q+ + grad q-)/2
+//     + eta (r+ + r-)/2 with r-+ = (q^com - q-+) S g'(end) / |J|-+, which sum to
+//     (q+ - q-) S g_R'(1) (1/|J|- + 1/|J|+) / 2; the penalty eta (BR2_PENALTY) is folded
+//     into lift_end = eta g_R'(1);  |S| f_vis . n = f_vis . S.
 // Inviscid part alone: fnum = |S| f_n,inv^com from qm ('-' side) and qp ('+' side); also
 // returns dq = qp - qm and the averaged state qa.
 template <class T, class G, class GS>
@@ -295,14 +303,14 @@ __device__ __forceinline__ void rusanov_common(const T qm[4], const T qp[4], G S
 template <class T, class G, class GS>
 __device__ __forceinline__ void face_common(const T qm[4], const T qp[4], const T gm[8],
                                             const T gp[8], G Sx, G Sy, G ug, G vg, G Jm, G Jp,
-                                            const GS& gs, double dgR_end, T fnum[4], T qcom[4]) {
+                                            const GS& gs, double lift_end, T fnum[4], T qcom[4]) {
   T dq[4], qa[4];
   rusanov_common(qm, qp, Sx, Sy, ug, vg, gs, dq, qa, fnum);
 #pragma unroll
   for (int k = 0; k < 4; ++k) qcom[k] = qa[k];
   if (gs.viscous) {
     // (r- + r+)/2 = (q+ - q-) S g_R'(1) (1/|J|- + 1/|J|+) / 4
-    const G lift = 0.25 * dgR_end * (inv(Jm) + inv(Jp));
+    const G lift = 0.25 * lift_end * (inv(Jm) + inv(Jp));
     T qx[4], qy[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -321,8 +329,8 @@ __device__ __forceinline__ void face_common(const T qm[4], const T qp[4], const 
 // field qb = q_inf, adiabatic no-slip wall qb = (p^-, v_g, T^-).  Inviscid: the
 // preconditioned Rusanov flux between the trace qe and qb, the element on the '-' side
 // when S points out of the domain (elem_minus), else on the '+' side.  Viscous: q^com =
-// qb, grad q^com = grad qe + r with the full one-sided lift r = (qb - qe) S g'(end)/|J|
-// (dg_end = g'(end) of the element's face: +g_R'(1) on a T face, g_L'(-1) = -g_R'(1) on a
+// qb, grad q^com = grad qe + eta r with the full one-sided lift r = (qb - qe) S g'(end)/|J|
+// (dg_end = eta g'(end) of the element's face: +eta g_R'(1) on a T face, eta g_L'(-1) on a
 // B face); at a wall the component of grad T^com along S is removed (dT/dn = 0); the flux
 // f_vis(qb, grad q^com) . S.  Writes fnum = |S| f_n^com along +S and qb.
 // dqinf (nullable): tangent of q_inf carried by dual-number T (parameter sensitivities).

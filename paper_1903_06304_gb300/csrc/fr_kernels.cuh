@@ -231,7 +231,7 @@ __global__ void k_face(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ
     T fnum[4], qb[4];
     face_boundary(qe, ge, geo<G>(gf, dgf, GF_SX * FNs + om), geo<G>(gf, dgf, GF_SY * FNs + om),
                   geo<G>(gf, dgf, GF_UG * FNs + om), geo<G>(gf, dgf, GF_VG * FNs + om),
-                  geo<G>(gf, dgf, GF_J * FNs + om), gas, B.dgR_end, true, -plus, M.par(e).qinf,
+                  geo<G>(gf, dgf, GF_J * FNs + om), gas, B.lift_end, true, -plus, M.par(e).qinf,
                   fnum, qb, dqinf.v);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -258,7 +258,7 @@ __global__ void k_face(Mesh M, Basis B, const double* __restrict__ gf, Buf<T> TQ
   T fnum[4], qcom[4];
   face_common(qm, qp, gm, gp, geo<G>(gf, dgf, GF_SX * FNs + om), geo<G>(gf, dgf, GF_SY * FNs + om),
               geo<G>(gf, dgf, GF_UG * FNs + om), geo<G>(gf, dgf, GF_VG * FNs + om),
-              geo<G>(gf, dgf, GF_J * FNs + om), geo<G>(gf, dgf, GF_J * FNs + op), gas, B.dgR_end,
+              geo<G>(gf, dgf, GF_J * FNs + om), geo<G>(gf, dgf, GF_J * FNs + op), gas, B.lift_end,
               fnum, qcom);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -292,7 +292,7 @@ __global__ void k_face_below(Mesh M, Basis B, const double* __restrict__ gf, Buf
   T fnum[4], qb[4];
   face_boundary(qe, ge, geo<G>(gf, dgf, GF_SX * FNs + of), geo<G>(gf, dgf, GF_SY * FNs + of),
                 geo<G>(gf, dgf, GF_UG * FNs + of), geo<G>(gf, dgf, GF_VG * FNs + of),
-                geo<G>(gf, dgf, GF_J * FNs + of), gas, -B.dgR_end, false, -below, M.par(e).qinf,
+                geo<G>(gf, dgf, GF_J * FNs + of), gas, -B.lift_end, false, -below, M.par(e).qinf,
                 fnum, qb, dqinf.v);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(256) k_wall_force(Mesh M, Basis B, const doubl
     G px, py;
     wall_traction(qe, ge, geo<G>(gf, dgf, GF_SX * FNs + of), geo<G>(gf, dgf, GF_SY * FNs + of),
                   geo<G>(gf, dgf, GF_UG * FNs + of), geo<G>(gf, dgf, GF_VG * FNs + of),
-                  geo<G>(gf, dgf, GF_J * FNs + of), gas, side == 0 ? -B.dgR_end : B.dgR_end,
+                  geo<G>(gf, dgf, GF_J * FNs + of), gas, side == 0 ? -B.lift_end : B.lift_end,
                   side == 0 ? 1.0 : -1.0, B.ws[t], M.viscous, px, py);
     fx = fx + px;
     fy = fy + py;

@@ -53,7 +53,7 @@ __global__ void k_lin_face(Mesh M, Basis B, const double* __restrict__ gf,
       for (int v = 0; v < 4; ++v) dq[v] = mk(qe[v], dd == v ? 1.0 : 0.0);
 #pragma unroll
       for (int c = 0; c < 8; ++c) dg[c] = mk(ge[c], dd == 4 + c ? 1.0 : 0.0);
-      face_boundary(dq, dg, Sx, Sy, ug, vg, Jm, gas, B.dgR_end, true, -plus, M.par(e).qinf, fnum, qb);
+      face_boundary(dq, dg, Sx, Sy, ug, vg, Jm, gas, B.lift_end, true, -plus, M.par(e).qinf, fnum, qb);
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         if (dd < 4) {
@@ -96,7 +96,7 @@ __global__ void k_lin_face(Mesh M, Basis B, const double* __restrict__ gf,
       dgm[c] = mk(gm[c], dd == 8 + c ? 1.0 : 0.0);
       dgp[c] = mk(gp[c], dd == 16 + c ? 1.0 : 0.0);
     }
-    face_common(dqm, dqp, dgm, dgp, Sx, Sy, ug, vg, Jm, Jp, gas, B.dgR_end, fnum, qcom);
+    face_common(dqm, dqp, dgm, dgp, Sx, Sy, ug, vg, Jm, Jp, gas, B.lift_end, fnum, qcom);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       if (dd < 8) JFQ[(size_t)(r * 8 + dd) * nf + idx] = fnum[r].d;
@@ -136,7 +136,7 @@ __global__ void k_lin_face_below(Mesh M, Basis B, const double* __restrict__ gf,
     for (int v = 0; v < 4; ++v) dq[v] = mk(qe[v], dd == v ? 1.0 : 0.0);
 #pragma unroll
     for (int c = 0; c < 8; ++c) dg[c] = mk(ge[c], dd == 4 + c ? 1.0 : 0.0);
-    face_boundary(dq, dg, Sx, Sy, ug, vg, Je, gas, -B.dgR_end, false, -below, M.par(e).qinf, fnum, qb);
+    face_boundary(dq, dg, Sx, Sy, ug, vg, Je, gas, -B.lift_end, false, -below, M.par(e).qinf, fnum, qb);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       if (dd < 4) JFQb[(size_t)(r * 4 + dd) * nb + idx] = fnum[r].d;

@@ -127,7 +127,7 @@ k_block(const double* __restrict__ q, Mesh M, Basis B, const double* __restrict_
         Dual fnum[4], qb[4];
         face_boundary(qe, ge, gf[GF_SX * FNs + of], gf[GF_SY * FNs + of], gf[GF_UG * FNs + of],
                       gf[GF_VG * FNs + of], gf[GF_J * FNs + of], gas,
-                      f == FACE_T ? B.dgR_end : -B.dgR_end, f == FACE_T, -nb_f, cpar.qinf, fnum, qb);
+                      f == FACE_T ? B.lift_end : -B.lift_end, f == FACE_T, -nb_f, cpar.qinf, fnum, qb);
 #pragma unroll
         for (int v = 0; v < 4; ++v) { sfn[(f * 4 + v) * N + s] = fnum[v]; sqc[(f * 4 + v) * N + s] = qb[v]; }
         continue;
@@ -160,7 +160,7 @@ k_block(const double* __restrict__ q, Mesh M, Basis B, const double* __restrict_
       const size_t op = ((size_t)other * 4 + fother) * N + s;
       Dual fnum[4], qcom[4];
       face_common(qm, qp, gm, gp, gf[GF_SX * FNs + om], gf[GF_SY * FNs + om], gf[GF_UG * FNs + om],
-                  gf[GF_VG * FNs + om], gf[GF_J * FNs + om], gf[GF_J * FNs + op], gas, B.dgR_end,
+                  gf[GF_VG * FNs + om], gf[GF_J * FNs + om], gf[GF_J * FNs + op], gas, B.lift_end,
                   fnum, qcom);
 #pragma unroll
       for (int v = 0; v < 4; ++v) { sfn[(f * 4 + v) * N + s] = fnum[v]; sqc[(f * 4 + v) * N + s] = qcom[v]; }
