@@ -168,7 +168,7 @@ def sharded_throughput(t_rank: float, units_total: float, world: int, dist, devi
 # Per-step work profile of the headline steps (means over the timed steps of the GPU arm,
 # two-level preconditioner, 64x64 p=3 vortex): the reference arm, which runs before any GPU
 # measurement, prices these counts; the GPU arm prices its own.
-STEP_PROFILE = {"newton": 7.0, "gmres": 450.0, "builds": 4.0, "restart": 30,
+STEP_PROFILE = {"newton": 3.2, "gmres": 228.0, "builds": 2.0, "restart": 30,
                 "precond": "twolevel"}
 
 
