@@ -234,7 +234,7 @@ int fr_set_mesh(fr_ctx* ctx, int nx, int ny, int periodic_x, int periodic_y);
  * q_inf_h: host array of 4 doubles, the far-field primitive state (p, u, v, T), p, T > 0;
  * required when a side is a far field, may be NULL otherwise; copied.  Boundary faces
  * take the interior trace's local gradient with the full one-sided BR2 lift of
- * q_b - q^- (the boundary state is also q^com).  Allocates like fr_set_mesh plus 4
+ * q_b - q^- (times the face penalty 2; the boundary state is also q^com).  Allocates like fr_set_mesh plus 4
  * arrays of nx*4*(p+1) doubles and the boundary faces' local Jacobians (48 nx (p+1)
  * doubles).  Every operator mode works on a bounded mesh: the stored linearisation
  * holds the boundary map's Jacobian in (q^-, grad q^-) at each boundary flux point, and
@@ -267,7 +267,9 @@ int fr_update_mesh(fr_ctx* ctx, const double* corners_d, const double* corner_ve
 /* R(q^p) of Sec. 3.1 (Eq. cpr_ns in its computational-domain form Eq.
  * unsteady_pre_mov_cdomain_GCL): R_d[4][Ne][n][n] = -(1/|J|)(dF/dxi + dG/deta -
  * q^c div(|J| xi_t, |J| eta_t)) with FR correction by Radau g_L, g_R, preconditioned
- * Rusanov (Eq. Rosanov) and BR2 viscous common fluxes. */
+ * Rusanov (Eq. Rosanov) and BR2 viscous common fluxes (face gradient: the mean of the
+ * two local gradients plus twice the mean of the two lifted jumps, a face penalty of 2;
+ * the corrected gradient at the solution points adds the lifted jumps once). */
 int fr_residual(fr_ctx* ctx, const double* qp_d, double* R_d, void* stream);
 
 /* Pseudo-step right-hand side of Eq. unsteady_pre_discretized_3:
