@@ -432,6 +432,10 @@ def low_mach_deforming_report(args, torch, fr, inp, T, flush):
         run = March(S, T(q0), meshes, fr)
         ms, st, _ = timed_steps(run, args.c3_steps if prec == "fp32" else 1, flush, torch.cuda.synchronize)
         out[f"march_{prec}"] = dict(step_summary(st), sec_per_step=[m / 1e3 for m in ms])
+        if prec == "fp64":
+            # Res_m/Res_0 per Newton iteration of the first step: where it levels off
+            h = st[0]["res_history"]
+            out["march_fp64"]["res_history_step1"] = [float("%.3g" % (x / h[0])) for x in h]
         if prec != "fp32":
             finals[prec] = run.q.clone()
         else:
@@ -1249,7 +1253,8 @@ def main():
                     help="skip the plunging march's discrete adjoint")
     ap.add_argument("--adjoint-steps", dest="adjoint_steps", type=int, default=4)
     ap.add_argument("--c3-steps", dest="c3_steps", type=int, default=3)
-    ap.add_argument("--c3-newton", dest="c3_newton", type=int, default=10)
+    ap.add_argument("--c3-newton", dest="c3_newton", type=int, default=20,
+                    help="Newton cap of the deforming 128x128 M = 0.01 steps")
     ap.add_argument("--restart", type=int, default=30)
     ap.add_argument("--maxit-lin", dest="maxit_lin", type=int, default=100)
     ap.add_argument("--maxit-newton", dest="maxit_newton", type=int, default=40)
