@@ -49,9 +49,9 @@ ALU_PEAK_SOURCE = ("nominal from unit counts and the maximum SM clock: FP64 152 
                    "x 2 flop x 2.07 GHz = 1.26 TFLOP/s; FP32 152 x 128 FMA/clk x 2 x 2.07 GHz = "
                    "80.5 TFLOP/s")
 # Bound of each kernel class as ncu measured it: every FP64 kernel, the Gram-Schmidt
-# reductions, vector updates and the coarse-level kernels included, saturates the FP64
-# pipe before DRAM (1 FMA per 8 bytes needs 1.7 TFLOP/s at full HBM bandwidth); the
-# FP32/BF16 block apply streams DRAM.
+# reductions, vector updates and FP64 coarse levels included, saturates the FP64 pipe
+# before DRAM (1 FMA per 8 bytes needs 1.7 TFLOP/s at full HBM bandwidth); the FP32/BF16
+# block apply and FP32 coarse levels stream DRAM.
 ALU_KINDS = {"trace", "face", "elem", "trace_jvp", "face_jvp", "elem_jvp", "block_jacobian",
              "block_factor", "geometry", "krylov_reduce", "vector", "linearize", "linear_apply",
              "linear_adjoint", "coarse"}
@@ -770,7 +770,10 @@ def gpu_arm(args):
         e = {"ms_total": v["ms"], "launches": v["launches"],
              "us_per_launch": 1e3 * v["ms"] / v["launches"],
              "share": v["ms"] / tot_ms if tot_ms else None}
-        if name in ALU_KINDS or (name == "block_apply" and args.prec == "fp64"):
+        # FP32 coarse levels carry 0.5 flop per byte, far below the FP32 pipe's balance
+        # (~12 flop/B): rated against HBM; FP64 coarse levels against the FP64 pipe
+        alu = name in ALU_KINDS and not (name == "coarse" and args.mg_prec != "fp64")
+        if alu or (name == "block_apply" and args.prec == "fp64"):
             fp32 = name == "block_factor" and args.prec != "fp64"
             peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
             e.update(bound="alu", pipe="fp32" if fp32 else "fp64", unit="TFLOP/s",
